@@ -1,0 +1,221 @@
+/*
+ * psatd_rz.h -- C ABI of the GB300 quasi-cylindrical arbitrary-order PSATD PIC cycle.
+ *
+ * Paper: S. Jalas et al., "Accurate modeling of plasma acceleration with arbitrary
+ * order pseudo-spectral particle-in-cell methods", arXiv:1611.05712.
+ *   - Cartesian PSATD update: Eq. psatd-eqE / psatd-eqB (section "Finite order
+ *     pseudo-spectral solvers").
+ *   - Quasi-cylindrical form: fields split into azimuthal modes m on separate (z, r)
+ *     grids, Hankel transform along r and Fourier transform along z, operators of the
+ *     table that follows Eq. psatd-eqB ("qcyl-ops").
+ *   - Arbitrary order: k_z replaced by the modified wavenumber [k_z] of the order-2n
+ *     centred stencil (Eq. finite_difference and the [k_z] equation), including inside
+ *     k, C and S.
+ *
+ * Conventions (fixed by this library where the paper is silent):
+ *   - SI units.  Grid nodes z_i = i*dz (periodic, i < Nz) and r_j = (j+1/2)*dr (j < Nr).
+ *   - F(r,theta,z) = Re[F_0 + 2 sum_{m>=1} F_m e^{-i m theta}];  F_+/- = (F_r -/+ i F_theta)/2.
+ *   - Complex grids are interleaved (re, im) pairs, layout [comp][m][r][z] with z fastest.
+ *     Real-space vector comps are (r, theta, z); spectral comps are (+, -, z).  Spectral
+ *     grids use the index n of the radial wavenumber k_{m,n} in place of r and the FFT
+ *     order of k_z in place of z.
+ *   - Particles are electrons-like macroparticles of one species (charge q, mass m given
+ *     in pic_config), SoA float64 x, y, z [m], ux, uy, uz [m/s, u = gamma v], w
+ *     (physical particles per macroparticle) plus an int32 id that follows the sort.
+ *
+ * Ownership: the caller allocates ONE device workspace of pic_required_bytes() bytes
+ * (e.g. a torch uint8 tensor) and passes its pointer and a cudaStream_t; the library
+ * carves every grid, table and particle array out of it and never allocates or frees
+ * device memory itself.  It owns only the opaque host handle (freed by pic_destroy).
+ *
+ * Errors: every call returns a pic_status; no exception, abort or exit crosses the ABI.
+ * pic_last_error() returns a thread-local text for the last failure.  Device-side
+ * checks (non-finite or out-of-range particle coordinates, iteration caps) raise a
+ * device error word that the synchronising calls report as PIC_ERR_NUMERIC or
+ * PIC_ERR_TIMEOUT.
+ *
+ * Asynchrony: all calls enqueue work on the handle's stream and return, except
+ * pic_init (synchronises once after setup), pic_diagnostics, pic_read_particles,
+ * pic_copy_buffer with a host destination, and pic_sync.
+ */
+#ifndef PSATD_RZ_H
+#define PSATD_RZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PIC_OK = 0,
+  PIC_ERR_ARG = 1,      /* invalid argument or configuration                       */
+  PIC_ERR_CUDA = 2,     /* a CUDA runtime call failed (text in pic_last_error)      */
+  PIC_ERR_OOM = 3,      /* workspace smaller than pic_required_bytes()              */
+  PIC_ERR_TIMEOUT = 4,  /* a device loop hit its iteration cap                      */
+  PIC_ERR_NUMERIC = 5,  /* non-finite or out-of-range values detected on the device */
+  PIC_ERR_STATE = 6     /* call out of order (e.g. stepping before particles exist) */
+} pic_status;
+
+typedef enum {
+  PIC_FP64 = 0,         /* every stage in float64                                            */
+  PIC_MIXED_TF32X3 = 1  /* float32 grids and particles (cell-relative), DHT as 3-term TF32
+                           tcgen05 products with float32 accumulation; FP64 setup and diags  */
+} pic_precision;
+
+typedef struct pic_config {
+  int32_t Nz;          /* z nodes (FFT length): 7-smooth, 8 <= Nz <= 4096 (FP64) / 8192 (mixed) */
+  int32_t Nr;          /* r nodes, 4 <= Nr <= 1024                                          */
+  int32_t Nm;          /* azimuthal modes m = 0..Nm-1, 1 <= Nm <= 4                         */
+  int32_t order_p;     /* stencil order p = 2n (even, 2..512); 0 = infinite order           */
+  double dz, dr, dt;   /* [m], [m], [s]                                                     */
+  int32_t filter;      /* 1: binomial source filter cos^2(k_z dz/2) cos^2(k_perp dr/2)      */
+  int32_t precision;   /* pic_precision                                                     */
+  int64_t np_capacity; /* maximum number of macroparticles                                  */
+  double q, mass;      /* species charge [C] and mass [kg]                                  */
+} pic_config;
+
+typedef struct pic_sim pic_sim;   /* opaque */
+
+/* Beam-quality diagnostics of one beam (section "Accurate modeling ...": transverse
+ * emittance and slice energy spread over 0.5 um slices within +/- 3 sigma_z). */
+typedef struct pic_diag {
+  double W;                  /* sum of weights                                           */
+  double x_mean, y_mean, z_mean, sigma_z, gamma_mean;
+  double emit_nx, emit_ny;   /* normalised rms emittance sqrt(<dx^2><dux^2>-<dx dux>^2)/c */
+  double sigma_gamma_mean;   /* mean over non-empty slices of the weighted std of gamma  */
+  int32_t n_slices;          /* non-empty slices                                         */
+  int32_t n_particles;       /* particles with id in [id_lo, id_hi)                     */
+} pic_diag;
+
+/* Buffer identifiers for pic_copy_buffer / pic_load_buffer / pic_buffer_bytes.
+ * Element type is float64 (complex = 2 x float64) in PIC_FP64 mode and float32 in
+ * mixed mode for grids; tables (KPERP, HANKEL_*, KZ_MOD) are float64 in both modes. */
+typedef enum {
+  PIC_BUF_E = 0,          /* real-space E  [3 (r,th,z)][Nm][Nr][Nz] complex            */
+  PIC_BUF_B = 1,          /* real-space B  [3][Nm][Nr][Nz] complex                      */
+  PIC_BUF_EH = 2,         /* spectral E    [3 (+,-,z)][Nm][Nr][Nz] complex              */
+  PIC_BUF_BH = 3,         /* spectral B    [3 (+,-,z)][Nm][Nr][Nz] complex              */
+  PIC_BUF_DEP = 4,        /* real-space deposit [4 (rho, J_r, J_th, J_z)][Nm][Nr][Nz]  */
+  PIC_BUF_SRC_H = 5,      /* spectral sources   [4 (rho, J_+, J_-, J_z)][Nm][Nr][Nz]   */
+  PIC_BUF_RHO_PREV_H = 6, /* filtered spectral rho^n [Nm][Nr][Nz] complex              */
+  PIC_BUF_RHO_ION = 7,    /* real-space immobile background [Nm][Nr][Nz] complex       */
+  PIC_BUF_KPERP = 8,      /* k_{m,n} [Nm][Nr] float64                                   */
+  PIC_BUF_HANKEL_INV = 9, /* B_p[j][n] = J_p(k_{m,n} r_j), [Nm][3 (p=m-1,m,m+1)][Nr][Nr]  */
+  PIC_BUF_HANKEL_FWD = 10,/* pseudo-inverses M_p[n][j], same shape                      */
+  PIC_BUF_KZ_MOD = 11,    /* [k_z]_p per FFT bin [Nz] float64                           */
+  PIC_BUF_KEYS = 12,      /* int32 cell keys iz*Nr+ir of the last sort [np]             */
+  PIC_BUF_PERM = 13,      /* int32 stable sort permutation of the last sort [np]        */
+  PIC_BUF_COUNT_ = 14
+} pic_buffer_id;
+
+/* Deposit selectors for pic_deposit. */
+#define PIC_DEP_RHO 1   /* rho at the current positions, plus the ion background */
+#define PIC_DEP_J   2   /* J at the current positions with v = u/gamma           */
+
+/* ---- lifecycle ------------------------------------------------------------------ */
+
+/* Bytes of device workspace a configuration needs.  Errors: PIC_ERR_ARG. */
+pic_status pic_required_bytes(const pic_config* cfg, size_t* bytes);
+
+/* Validate cfg, carve the workspace and run the setup stage on the GPU (FP64, once):
+ * Bessel zeros alpha_{m,n} (Newton from McMahon's expansion), Hankel matrices
+ * B_p = J_p(k_{m,n} r_j), their pseudo-inverses (one-sided Jacobi SVD, singular values
+ * <= 1e-3 sigma_max dropped), [k_z]_p (Eq. finite_difference / [k_z]) and the PSATD
+ * coefficient tables C, S/K, (1-C)/K^2, ... (Eq. psatd-eqE/eqB with [k_z]).
+ * workspace: device pointer, >= pic_required_bytes, 256-byte aligned.  stream: a
+ * cudaStream_t (NULL = legacy default stream).  Fields start at zero, no particles.
+ * Errors: PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CUDA, PIC_ERR_TIMEOUT (SVD did not converge). */
+pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes,
+                    void* stream, pic_sim** out);
+
+/* Free the host handle (the workspace stays the caller's). */
+pic_status pic_destroy(pic_sim* sim);
+
+/* Text of the last error on this thread ("" if none).  Never NULL. */
+const char* pic_last_error(void);
+
+/* ---- particles and initial state ----------------------------------------------- */
+
+/* Copy n particles in (replacing all): soa[0..6] = x, y, z, ux, uy, uz, w (float64),
+ * id (int32).  on_host != 0: the pointers are host memory (copied synchronously);
+ * else device pointers (stream-ordered copy).  z must lie in [0, Nz dz) and
+ * x^2 + y^2 < (Nr dr)^2.  Errors: PIC_ERR_ARG (n > capacity or negative). */
+pic_status pic_write_particles(pic_sim* sim, const double* const soa[7], const int32_t* id,
+                               int64_t n, int32_t on_host);
+
+/* Copy the current particles out in the current (sorted) order, same layout. Synchronises. */
+pic_status pic_read_particles(pic_sim* sim, double* const soa[7], int32_t* id, int64_t n,
+                              int32_t on_host);
+
+/* Number of particles currently held. */
+pic_status pic_num_particles(pic_sim* sim, int64_t* n);
+
+/* Immobile neutralising background: rho_ion = -rho(particles with id < n_neutral). */
+pic_status pic_init_background(pic_sim* sim, int32_t n_neutral);
+
+/* Add the space-charge fields of the particles with id in [id_lo, id_hi), moving along
+ * +z with Lorentz factor gamma, to the spectral E and B: relativistic Poisson solve
+ * phi = rho/(eps0 (k_perp^2 + K_z^2/gamma^2)), E = -grad-like, B = curl(0,0,beta phi/c). */
+pic_status pic_add_beam_fields(pic_sim* sim, int32_t id_lo, int32_t id_hi, double gamma);
+
+/* Deposit rho^0 (+ background), transform and filter it into rho^n, and inverse-
+ * transform the spectral E, B into the real-space grids.  Call once before stepping. */
+pic_status pic_init_fields(pic_sim* sim);
+
+/* ---- the PIC cycle ------------------------------------------------------------ */
+
+/* a1: cell keys iz*Nr+ir (iz = floor(z/dz), ir = floor(sqrt(x*x+y*y)/dr), clamped) and a
+ * stable counting sort of every particle array by key (ties keep the input order). */
+pic_status pic_sort(pic_sim* sim);
+
+/* a4 at the current positions (no move): what = PIC_DEP_RHO and/or PIC_DEP_J.
+ * Linear weights in z and r, ghost node r_{-1} folded into node 0 with sign (-1)^m
+ * (scalars, z) or (-1)^{m+1} (r, theta), node Nr dropped, volume 2 pi r_j dr dz,
+ * mode weight e^{+i m theta}.  Results in PIC_BUF_DEP (the J part is zeroed/overwritten
+ * only when selected). */
+pic_status pic_deposit(pic_sim* sim, int32_t what);
+
+/* a2 + a3: gather E^n, B^n at x^n (mode sum, linear weights), relativistic Boris push
+ * u^{n-1/2} -> u^{n+1/2}, x^n -> x^{n+1/2} -> x^{n+1} (periodic z, specular reflection at
+ * r >= R).  fuse_current != 0 also deposits J^{n+1/2} at x^{n+1/2} into PIC_BUF_DEP. */
+pic_status pic_gather_push(pic_sim* sim, int32_t fuse_current);
+
+/* a5..a9: forward z-FFT + DHT of PIC_BUF_DEP, PSATD update with [k_z]_p (filter,
+ * global spectral current correction), rho^n <- rho^{n+1}, inverse DHT + z-FFT into
+ * PIC_BUF_E / PIC_BUF_B.  order_p >= 0 selects the stencil order (0 = infinite),
+ * rebuilding the coefficient tables when it differs from the current one; -1 keeps it. */
+pic_status pic_field_step(pic_sim* sim, int32_t order_p);
+
+/* Stage pieces of pic_field_step, for stage-wise checking:
+ *   pic_forward_transform: PIC_BUF_DEP -> PIC_BUF_SRC_H (a5, a6)
+ *   pic_psatd:             PIC_BUF_SRC_H, EH, BH, RHO_PREV_H -> EH, BH, RHO_PREV_H (a7)
+ *   pic_inverse_transform: PIC_BUF_EH, BH -> PIC_BUF_E, B (a8, a9) */
+pic_status pic_forward_transform(pic_sim* sim);
+pic_status pic_psatd(pic_sim* sim);
+pic_status pic_inverse_transform(pic_sim* sim);
+
+/* n full cycles: gather_push(fused J) -> sort -> deposit(rho) -> field_step. */
+pic_status pic_step(pic_sim* sim, int32_t n_steps);
+
+/* a10: FP64 diagnostics of the particles with id in [id_lo, id_hi).  slice_sigma (host,
+ * may be NULL) receives up to max_slices per-slice std of gamma.  Synchronises. */
+pic_status pic_diagnostics(pic_sim* sim, int32_t id_lo, int32_t id_hi, pic_diag* out,
+                           double* slice_sigma, int32_t max_slices);
+
+/* ---- buffers ------------------------------------------------------------------- */
+pic_status pic_buffer_bytes(pic_sim* sim, int32_t buffer_id, size_t* bytes);
+pic_status pic_copy_buffer(pic_sim* sim, int32_t buffer_id, void* dst, size_t bytes,
+                           int32_t dst_on_host);
+pic_status pic_load_buffer(pic_sim* sim, int32_t buffer_id, const void* src, size_t bytes,
+                           int32_t src_on_host);
+
+/* Wait for the stream and report any device error word.  Errors: PIC_ERR_CUDA,
+ * PIC_ERR_NUMERIC, PIC_ERR_TIMEOUT. */
+pic_status pic_sync(pic_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSATD_RZ_H */
