@@ -199,6 +199,25 @@ pic_status pic_inverse_transform(pic_sim* sim);
 /* n full cycles: gather_push(fused J) -> sort -> deposit(rho) -> field_step. */
 pic_status pic_step(pic_sim* sim, int32_t n_steps);
 
+/* Stages of one cycle, in order, as timed by pic_step_timed. */
+typedef enum {
+  PIC_STAGE_GATHER_PUSH = 0,  /* a2 + a3 + a4 (J at x^{n+1/2})          */
+  PIC_STAGE_SORT = 1,         /* a1                                     */
+  PIC_STAGE_DEPOSIT = 2,      /* a4 (rho at x^{n+1})                    */
+  PIC_STAGE_FFT_FWD = 3,      /* a5                                     */
+  PIC_STAGE_DHT_FWD = 4,      /* a6                                     */
+  PIC_STAGE_PSATD = 5,        /* a7                                     */
+  PIC_STAGE_DHT_INV = 6,      /* a8                                     */
+  PIC_STAGE_FFT_INV = 7,      /* a9                                     */
+  PIC_NSTAGES = 8
+} pic_stage;
+
+/* pic_step with CUDA events recorded on the handle's stream between the stages.
+ * stage_ms[PIC_NSTAGES + 1] (host) receives the summed device time of each stage over the
+ * n_steps cycles and, in stage_ms[PIC_NSTAGES], the time from the first to the last event.
+ * 1 <= n_steps <= 4096.  Synchronises. */
+pic_status pic_step_timed(pic_sim* sim, int32_t n_steps, double* stage_ms);
+
 /* a10: FP64 diagnostics of the particles with id in [id_lo, id_hi).  slice_sigma (host,
  * may be NULL) receives up to max_slices per-slice std of gamma.  Synchronises. */
 pic_status pic_diagnostics(pic_sim* sim, int32_t id_lo, int32_t id_hi, pic_diag* out,
@@ -214,6 +233,9 @@ pic_status pic_load_buffer(pic_sim* sim, int32_t buffer_id, const void* src, siz
 /* Wait for the stream and report any device error word.  Errors: PIC_ERR_CUDA,
  * PIC_ERR_NUMERIC, PIC_ERR_TIMEOUT. */
 pic_status pic_sync(pic_sim* sim);
+
+/* Number of kernels this handle has launched so far (host-side count, for accounting). */
+pic_status pic_launch_count(pic_sim* sim, int64_t* launches);
 
 #ifdef __cplusplus
 }

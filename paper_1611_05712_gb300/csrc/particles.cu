@@ -1,0 +1,637 @@
+// Particle stages of the PIC cycle (the PIC loop of the introduction; deposition,
+// gather and push are the particle side of the quasi-cylindrical scheme of section
+// "Finite order pseudo-spectral solvers"):
+//   a1 cell keys + stable counting sort, a2 gather with mode reconstruction,
+//   a3 relativistic Boris push, a4 charge / current deposition per mode,
+//   a10 FP64 beam diagnostics (emittance, slice energy spread; section "Accurate
+//   modeling of plasma accelerators in finite order PSATD").
+// Conventions: F = Re[F_0 + 2 sum_{m>=1} F_m e^{-i m theta}], deposit weight e^{+i m theta},
+// linear weights in z (periodic) and r (nodes r_j = (j+1/2) dr), ghost node j = -1
+// folded into node 0 with sign (-1)^m (scalar, z) or (-1)^{m+1} (r, theta), node Nr
+// dropped, cell volume 2 pi r_j dr dz.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+namespace {
+
+struct Parts {
+  double* x; double* y; double* z; double* ux; double* uy; double* uz; double* w;
+  int32_t* id;
+};
+
+Parts parts_of(Sim* s, int which) {
+  Parts p;
+  double** a = &p.x;
+  for (int k = 0; k < 7; ++k) a[k] = s->at<double>(s->lay.part[which][k]);
+  p.id = s->at<int32_t>(s->lay.pid[which]);
+  return p;
+}
+
+struct GridGeom {
+  int Nz, Nr, Nm;
+  double dz, dr, L, R;
+  size_t G;   // Nm*Nr*Nz
+};
+
+GridGeom geom_of(const Sim* s) {
+  const pic_config& c = s->cfg;
+  GridGeom g{c.Nz, c.Nr, c.Nm, c.dz, c.dr, c.Nz * c.dz, c.Nr * c.dr, s->grid_elems()};
+  return g;
+}
+
+__device__ __forceinline__ void polar(double x, double y, double& r, double& c, double& s) {
+  r = sqrt(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
+  if (r > 0.0) { c = x / r; s = y / r; } else { c = 1.0; s = 0.0; }
+}
+
+struct Stencil {
+  int i0, i1, j0;
+  double wz0, wz1, wr0, wr1;
+};
+
+__device__ __forceinline__ Stencil stencil(const GridGeom& g, double z, double r) {
+  Stencil st;
+  double u = z / g.dz;
+  double fi = floor(u);
+  double sz = u - fi;
+  long long i0 = (long long)fi % g.Nz;
+  if (i0 < 0) i0 += g.Nz;
+  st.i0 = (int)i0;
+  st.i1 = (int)((i0 + 1) % g.Nz);
+  st.wz0 = 1.0 - sz;
+  st.wz1 = sz;
+  double v = r / g.dr - 0.5;
+  double fj = floor(v);
+  double t = v - fj;
+  // r >= 0 gives fj >= -1; beyond the last node every weight is dropped anyway
+  st.j0 = (int)fmin(fmax(fj, -1.0), (double)g.Nr);
+  st.wr0 = 1.0 - t;
+  st.wr1 = t;
+  return st;
+}
+
+// Atomically add val * weight at node (j, i) of a complex grid [Nr][Nz] with the fold.
+__device__ __forceinline__ void dep_node(double2* grid, const GridGeom& g, int j, int i, double wgt,
+                                         double fold, double vre, double vim, const double* invV) {
+  if (j < 0) { j = -1 - j; wgt *= fold; }
+  if (j >= g.Nr) return;
+  const double f = wgt * invV[j];
+  double* p = reinterpret_cast<double*>(grid + (size_t)j * g.Nz + i);
+  atomicAdd(p, vre * f);
+  atomicAdd(p + 1, vim * f);
+}
+
+__device__ __forceinline__ double2 interp(const double2* grid, const GridGeom& g, const Stencil& st,
+                                          double fold) {
+  double re = 0.0, im = 0.0;
+#pragma unroll
+  for (int dj = 0; dj < 2; ++dj) {
+    int j = st.j0 + dj;
+    double wr = dj ? st.wr1 : st.wr0;
+    if (j < 0) { j = -1 - j; wr *= fold; }
+    if (j >= g.Nr) continue;
+    double2 a = grid[(size_t)j * g.Nz + st.i0];
+    double2 b = grid[(size_t)j * g.Nz + st.i1];
+    re += wr * (st.wz0 * a.x + st.wz1 * b.x);
+    im += wr * (st.wz0 * a.y + st.wz1 * b.y);
+  }
+  return make_double2(re, im);
+}
+
+// ------------------------------------------------------------------ a1: keys and sort
+__global__ void k_keys(const Parts p, int64_t np, GridGeom g, int32_t* keys, int32_t* count,
+                       int32_t* err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double x = p.x[i], y = p.y[i], z = p.z[i];
+    double r = sqrt(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
+    double fz = floor(z / g.dz), fr = floor(r / g.dr);
+    if (!(fz == fz) || !(fr == fr) || isinf(fz) || isinf(fr)) {
+      atomicOr(err, kErrNumeric);
+      fz = 0.0; fr = 0.0;
+    }
+    int iz = (int)fmin(fmax(fz, 0.0), (double)(g.Nz - 1));
+    int ir = (int)fmin(fmax(fr, 0.0), (double)(g.Nr - 1));
+    int key = iz * g.Nr + ir;
+    keys[i] = key;
+    atomicAdd(count + key, 1);
+  }
+}
+
+// exclusive scan of count[0..n) into start[0..n], 4096 elements per block
+constexpr int kScanThreads = 1024, kScanPer = 4, kScanBlock = kScanThreads * kScanPer;
+
+__device__ int32_t block_exclusive_scan(int32_t v, int32_t* total) {
+  __shared__ int32_t warp_sums[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int32_t x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int32_t w = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      int32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    warp_sums[lane] = w;
+  }
+  __syncthreads();
+  int32_t excl = x - v + (warp > 0 ? warp_sums[warp - 1] : 0);
+  if (total) *total = warp_sums[(blockDim.x >> 5) - 1];
+  __syncthreads();
+  return excl;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_local(const int32_t* count, int32_t* start,
+                                                              int32_t* blk, int n) {
+  const int base = blockIdx.x * kScanBlock + threadIdx.x * kScanPer;
+  int32_t v[kScanPer], sum = 0;
+  for (int q = 0; q < kScanPer; ++q) {
+    v[q] = (base + q < n) ? count[base + q] : 0;
+    sum += v[q];
+  }
+  int32_t tot;
+  int32_t ex = block_exclusive_scan(sum, &tot);
+  for (int q = 0; q < kScanPer; ++q) {
+    if (base + q < n) start[base + q] = ex;
+    ex += v[q];
+  }
+  if (threadIdx.x == 0) blk[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_blocks(int32_t* blk, int nblk, int32_t* start,
+                                                               int n) {
+  // one block: exclusive scan of up to 4096 block totals
+  const int base = threadIdx.x * kScanPer;
+  int32_t v[kScanPer], sum = 0;
+  for (int q = 0; q < kScanPer; ++q) {
+    v[q] = (base + q < nblk) ? blk[base + q] : 0;
+    sum += v[q];
+  }
+  int32_t tot;
+  int32_t ex = block_exclusive_scan(sum, &tot);
+  for (int q = 0; q < kScanPer; ++q) {
+    if (base + q < nblk) blk[base + q] = ex;
+    ex += v[q];
+  }
+  if (threadIdx.x == 0) start[n] = tot;
+}
+
+__global__ void k_scan_add(int32_t* start, const int32_t* blk, int n, int32_t* cursor) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int32_t v = start[i] + blk[i / kScanBlock];
+    start[i] = v;
+    cursor[i] = v;
+  }
+}
+
+__global__ void k_scatter(const int32_t* keys, int64_t np, int32_t* cursor, int32_t* tmp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t pos = atomicAdd(cursor + keys[i], 1);
+    tmp[pos] = (int32_t)i;
+  }
+}
+
+// Within each cell, order the particle indices ascending (this makes the counting sort
+// stable and deterministic).  Cells with <= 16 particles: insertion sort by one thread;
+// larger ones are queued for the warp kernel.
+constexpr int kSmallCell = 16;
+__global__ void k_cell_sort_small(const int32_t* start, const int32_t* tmp, int32_t* perm, int ncell,
+                                  int32_t* big_list, int32_t* big_count) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < ncell; c += gridDim.x * blockDim.x) {
+    const int s0 = start[c], n = start[c + 1] - s0;
+    if (n == 0) continue;
+    if (n > kSmallCell) {
+      int slot = atomicAdd(big_count, 1);
+      big_list[slot] = c;
+      continue;
+    }
+    int32_t v[kSmallCell];
+    for (int k = 0; k < n; ++k) {
+      int32_t e = tmp[s0 + k];
+      int q = k;
+      while (q > 0 && v[q - 1] > e) { v[q] = v[q - 1]; --q; }
+      v[q] = e;
+    }
+    for (int k = 0; k < n; ++k) perm[s0 + k] = v[k];
+  }
+}
+
+__global__ void k_cell_sort_big(const int32_t* start, const int32_t* tmp, int32_t* perm,
+                                const int32_t* big_list, const int32_t* big_count) {
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int nbig = *big_count;
+  for (int b = gw; b < nbig; b += nw) {
+    const int c = big_list[b];
+    const int s0 = start[c], n = start[c + 1] - s0;
+    for (int k = lane; k < n; k += 32) {
+      const int32_t e = tmp[s0 + k];
+      int rank = 0;
+      for (int q = 0; q < n; ++q) rank += (tmp[s0 + q] < e);
+      perm[s0 + rank] = e;
+    }
+  }
+}
+
+__global__ void k_permute(const Parts src, Parts dst, const int32_t* perm, int64_t np) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = perm[i];
+    dst.x[i] = src.x[k]; dst.y[i] = src.y[k]; dst.z[i] = src.z[k];
+    dst.ux[i] = src.ux[k]; dst.uy[i] = src.uy[k]; dst.uz[i] = src.uz[k];
+    dst.w[i] = src.w[k]; dst.id[i] = src.id[k];
+  }
+}
+
+// ------------------------------------------------------------------ a4: deposit
+struct DepArgs {
+  double2* rho;   // [Nm][Nr][Nz] or null
+  double2* J;     // [3][Nm][Nr][Nz] or null
+  double q;
+  int32_t id_lo, id_hi;
+};
+
+__device__ void deposit_one(const GridGeom& g, const DepArgs& a, const double* invV, double x,
+                            double y, double z, double w, double vx, double vy, double vz,
+                            bool do_rho, bool do_J) {
+  double r, c, s;
+  polar(x, y, r, c, s);
+  const Stencil st = stencil(g, z, r);
+  const double vr = c * vx + s * vy, vt = c * vy - s * vx;
+  double phr = 1.0, phi = 0.0;   // e^{+i m theta}
+  for (int m = 0; m < g.Nm; ++m) {
+    const double qre = a.q * w * phr, qim = a.q * w * phi;
+    const double fs = (m & 1) ? -1.0 : 1.0;   // scalar / z fold (-1)^m
+    const double fv = -fs;                     // r / theta fold (-1)^{m+1}
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz) {
+      const int i = dz ? st.i1 : st.i0;
+      const double wz = dz ? st.wz1 : st.wz0;
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj) {
+        const int j = st.j0 + dj;
+        const double wgt = wz * (dj ? st.wr1 : st.wr0);
+        if (do_rho) dep_node(a.rho + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fs, qre, qim, invV);
+        if (do_J) {
+          dep_node(a.J + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fv, qre * vr, qim * vr, invV);
+          dep_node(a.J + g.G + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fv, qre * vt, qim * vt, invV);
+          dep_node(a.J + 2 * g.G + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fs, qre * vz, qim * vz, invV);
+        }
+      }
+    }
+    const double nr = phr * c - phi * s, ni = phr * s + phi * c;
+    phr = nr; phi = ni;
+  }
+}
+
+__global__ void k_deposit(const Parts p, int64_t np, GridGeom g, DepArgs a, const double* invV,
+                          int32_t* err) {
+  const bool do_rho = a.rho != nullptr, do_J = a.J != nullptr;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t id = p.id[i];
+    if (id < a.id_lo || id >= a.id_hi) continue;
+    double vx = 0.0, vy = 0.0, vz = 0.0;
+    if (do_J) {
+      const double ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
+      const double ig = 1.0 / sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+      vx = ux * ig; vy = uy * ig; vz = uz * ig;
+    }
+    const double x = p.x[i], y = p.y[i], z = p.z[i];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) { atomicOr(err, kErrNumeric); continue; }
+    deposit_one(g, a, invV, x, y, z, p.w[i], vx, vy, vz, do_rho, do_J);
+  }
+}
+
+__global__ void k_inv_volume(double* invV, int Nr, double dr, double dz) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < Nr) invV[j] = 1.0 / (2.0 * kPi * ((j + 0.5) * dr) * dr * dz);
+}
+
+// ------------------------------------------------------------------ a2 + a3 (+ a4 J)
+__global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __restrict__ E,
+                              const double2* __restrict__ B, double q, double mass, double dt,
+                              DepArgs dep, const double* invV, int fuse, int32_t* err) {
+  const size_t RZ = (size_t)g.Nr * g.Nz;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double x = p.x[i], y = p.y[i], z = p.z[i];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) { atomicOr(err, kErrNumeric); continue; }
+    double ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
+    const double w = p.w[i];
+    double r, c, s;
+    polar(x, y, r, c, s);
+    const Stencil st = stencil(g, z, r);
+    double F[6] = {0, 0, 0, 0, 0, 0};   // E_r, E_t, E_z, B_r, B_t, B_z
+    double phr = 1.0, phi = 0.0;        // e^{-i m theta}
+    for (int m = 0; m < g.Nm; ++m) {
+      const double fs = (m & 1) ? -1.0 : 1.0, fv = -fs;
+      const double mult = m == 0 ? 1.0 : 2.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const double2* base = (k < 3 ? E : B) + (size_t)(k % 3) * g.G + (size_t)m * RZ;
+        const double2 v = interp(base, g, st, (k % 3) == 2 ? fs : fv);
+        F[k] += mult * (v.x * phr - v.y * phi);
+      }
+      const double nr = phr * c + phi * s, ni = phi * c - phr * s;   // times e^{-i theta}
+      phr = nr; phi = ni;
+    }
+    const double Ex = F[0] * c - F[1] * s, Ey = F[0] * s + F[1] * c, Ez = F[2];
+    const double Bx = F[3] * c - F[4] * s, By = F[3] * s + F[4] * c, Bz = F[5];
+    // Boris
+    const double k = q * dt / (2.0 * mass);
+    const double umx = ux + k * Ex, umy = uy + k * Ey, umz = uz + k * Ez;
+    const double gm = sqrt(1.0 + (umx * umx + umy * umy + umz * umz) / (kC * kC));
+    const double tx = k * Bx / gm, ty = k * By / gm, tz = k * Bz / gm;
+    const double upx = umx + (umy * tz - umz * ty);
+    const double upy = umy + (umz * tx - umx * tz);
+    const double upz = umz + (umx * ty - umy * tx);
+    const double f = 2.0 / (1.0 + tx * tx + ty * ty + tz * tz);
+    const double sx = f * tx, sy = f * ty, sz = f * tz;
+    ux = umx + (upy * sz - upz * sy) + k * Ex;
+    uy = umy + (upz * sx - upx * sz) + k * Ey;
+    uz = umz + (upx * sy - upy * sx) + k * Ez;
+    const double ig = 1.0 / sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+    const double vx = ux * ig, vy = uy * ig, vz = uz * ig;
+    const double hdt = 0.5 * dt;
+    x = x + hdt * vx;
+    y = y + hdt * vy;
+    z = z + hdt * vz;
+    if (z >= g.L) z -= g.L;
+    if (z < 0.0) z += g.L;
+    if (fuse) deposit_one(g, dep, invV, x, y, z, w, vx, vy, vz, false, true);
+    x = x + hdt * vx;
+    y = y + hdt * vy;
+    z = z + hdt * vz;
+    if (z >= g.L) z -= g.L;
+    if (z < 0.0) z += g.L;
+    const double r1 = sqrt(x * x + y * y);
+    if (r1 >= g.R) {
+      const double cx = x / r1, cy = y / r1;
+      const double fr = (2.0 * g.R - r1) / r1;
+      const double ur = ux * cx + uy * cy;
+      ux = ux - 2.0 * ur * cx;
+      uy = uy - 2.0 * ur * cy;
+      x *= fr;
+      y *= fr;
+    }
+    p.x[i] = x; p.y[i] = y; p.z[i] = z;
+    p.ux[i] = ux; p.uy[i] = uy; p.uz[i] = uz;
+  }
+}
+
+// ------------------------------------------------------------------ a10: diagnostics
+constexpr int kDiagThreads = 256;
+constexpr int kMaxSlices = 1 << 16;
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// pass 1: sum w, w x, w y, w z, w ux, w uy, w gamma, count
+__global__ void k_diag_moments(const Parts p, int64_t np, int32_t lo, int32_t hi, double* acc) {
+  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t id = p.id[i];
+    if (id < lo || id >= hi) continue;
+    const double w = p.w[i], ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
+    const double gam = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+    v[0] += w; v[1] += w * p.x[i]; v[2] += w * p.y[i]; v[3] += w * p.z[i];
+    v[4] += w * ux; v[5] += w * uy; v[6] += w * gam; v[7] += 1.0;
+  }
+  for (int k = 0; k < 8; ++k) {
+    const double t = warp_sum(v[k]);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc + k, t);
+  }
+}
+
+// pass 2: centred second moments w dx^2, w dux^2, w dx dux, (y), w dz^2
+__global__ void k_diag_central(const Parts p, int64_t np, int32_t lo, int32_t hi, const double* mean,
+                               double* acc) {
+  double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t id = p.id[i];
+    if (id < lo || id >= hi) continue;
+    const double w = p.w[i];
+    const double dx = p.x[i] - mean[0], dy = p.y[i] - mean[1], dz = p.z[i] - mean[2];
+    const double dux = p.ux[i] - mean[3], duy = p.uy[i] - mean[4];
+    v[0] += w * (dx * dx); v[1] += w * (dux * dux); v[2] += w * (dx * dux);
+    v[3] += w * (dy * dy); v[4] += w * (duy * duy); v[5] += w * (dy * duy);
+    v[6] += w * (dz * dz);
+  }
+  for (int k = 0; k < 7; ++k) {
+    const double t = warp_sum(v[k]);
+    if ((threadIdx.x & 31) == 0) atomicAdd(acc + k, t);
+  }
+}
+
+// pass 3 (stage 0): per-slice sum w and sum w gamma; (stage 1): sum w (gamma - gbar_s)^2
+__global__ void k_diag_slices(const Parts p, int64_t np, int32_t lo, int32_t hi, double zstart,
+                              double zspan, double slen, int ns, double* sw, double* sg, double* sv,
+                              int stage) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t id = p.id[i];
+    if (id < lo || id >= hi) continue;
+    const double d = p.z[i] - zstart;
+    if (!(d >= 0.0 && d < zspan)) continue;
+    int k = (int)floor(d / slen);
+    if (k > ns - 1) k = ns - 1;
+    const double w = p.w[i], ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
+    const double gam = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+    if (stage == 0) {
+      atomicAdd(sw + k, w);
+      atomicAdd(sg + k, w * gam);
+    } else {
+      const double gb = sg[k] / sw[k];
+      const double dg = gam - gb;
+      atomicAdd(sv + k, w * (dg * dg));
+    }
+  }
+}
+
+inline int pgrid(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
+}
+
+}  // namespace
+
+pic_status launch_sort(Sim* s) {
+  const GridGeom g = geom_of(s);
+  const int64_t np = s->np;
+  const int ncell = g.Nz * g.Nr;
+  int32_t* keys = s->at<int32_t>(s->lay.keys);
+  int32_t* count = s->at<int32_t>(s->lay.count);
+  int32_t* start = s->at<int32_t>(s->lay.start);
+  int32_t* blk = s->at<int32_t>(s->lay.scan_blk);
+  int32_t* tmp = s->at<int32_t>(s->lay.perm_tmp);
+  int32_t* perm = s->at<int32_t>(s->lay.perm);
+  int32_t* big_list = s->at<int32_t>(s->lay.big_list);
+  int32_t* big_count = s->at<int32_t>(s->lay.big_count);
+  int32_t* err = s->at<int32_t>(s->lay.err);
+  int32_t* cursor = reinterpret_cast<int32_t*>(s->at<char>(s->lay.scan_blk) + 4 * 4096 * sizeof(int32_t));
+  PIC_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * (ncell + 1), s->stream));
+  PIC_CUDA(cudaMemsetAsync(big_count, 0, sizeof(int32_t), s->stream));
+  if (np == 0) return PIC_OK;
+  Parts src = parts_of(s, s->cur), dst = parts_of(s, 1 - s->cur);
+  k_keys<<<pgrid(np), 256, 0, s->stream>>>(src, np, g, keys, count, err);
+  PIC_LAUNCHED(s);
+  const int nblk = (ncell + kScanBlock - 1) / kScanBlock;
+  k_scan_local<<<nblk, kScanThreads, 0, s->stream>>>(count, start, blk, ncell);
+  PIC_LAUNCHED(s);
+  k_scan_blocks<<<1, kScanThreads, 0, s->stream>>>(blk, nblk, start, ncell);
+  PIC_LAUNCHED(s);
+  k_scan_add<<<pgrid(ncell), 256, 0, s->stream>>>(start, blk, ncell, cursor);
+  PIC_LAUNCHED(s);
+  k_scatter<<<pgrid(np), 256, 0, s->stream>>>(keys, np, cursor, tmp);
+  PIC_LAUNCHED(s);
+  k_cell_sort_small<<<pgrid(ncell), 256, 0, s->stream>>>(start, tmp, perm, ncell, big_list, big_count);
+  PIC_LAUNCHED(s);
+  k_cell_sort_big<<<152 * 4, 256, 0, s->stream>>>(start, tmp, perm, big_list, big_count);
+  PIC_LAUNCHED(s);
+  k_permute<<<pgrid(np), 256, 0, s->stream>>>(src, dst, perm, np);
+  PIC_LAUNCHED(s);
+  s->cur = 1 - s->cur;
+  return PIC_OK;
+}
+
+static pic_status ensure_inv_volume(Sim* s, double** invV) {
+  // the inverse ring volumes live at the tail of the diagnostics accumulator block
+  *invV = s->at<double>(s->lay.diag_acc) + 64 + 3 * (size_t)kMaxSlices;
+  k_inv_volume<<<(s->cfg.Nr + 127) / 128, 128, 0, s->stream>>>(*invV, s->cfg.Nr, s->cfg.dr, s->cfg.dz);
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
+pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, void* rho_out) {
+  const GridGeom g = geom_of(s);
+  double* invV;
+  pic_status st = ensure_inv_volume(s, &invV);
+  if (st != PIC_OK) return st;
+  DepArgs a;
+  a.q = s->cfg.q;
+  a.id_lo = id_lo;
+  a.id_hi = id_hi;
+  a.rho = (what & PIC_DEP_RHO) ? (rho_out ? (double2*)rho_out : s->at<double2>(s->lay.dep)) : nullptr;
+  a.J = (what & PIC_DEP_J) ? s->at<double2>(s->lay.dep) + g.G : nullptr;
+  if (a.J) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * g.G * sizeof(double2), s->stream));
+  if (s->np == 0) return PIC_OK;
+  k_deposit<<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, g, a, invV,
+                                                  s->at<int32_t>(s->lay.err));
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
+pic_status launch_gather_push(Sim* s, int32_t fuse_current) {
+  const GridGeom g = geom_of(s);
+  double* invV;
+  pic_status st = ensure_inv_volume(s, &invV);
+  if (st != PIC_OK) return st;
+  DepArgs a;
+  a.q = s->cfg.q;
+  a.id_lo = INT32_MIN;
+  a.id_hi = INT32_MAX;
+  a.rho = nullptr;
+  a.J = s->at<double2>(s->lay.dep) + g.G;
+  if (fuse_current) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * g.G * sizeof(double2), s->stream));
+  if (s->np == 0) return PIC_OK;
+  k_gather_push<<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, g,
+                                                      s->at<double2>(s->lay.E), s->at<double2>(s->lay.B),
+                                                      s->cfg.q, s->cfg.mass, s->cfg.dt, a, invV,
+                                                      fuse_current, s->at<int32_t>(s->lay.err));
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
+pic_status launch_diag(Sim* s, int32_t lo, int32_t hi, pic_diag* out, double* slice_sigma,
+                       int32_t max_slices) {
+  const int64_t np = s->np;
+  double* acc = s->at<double>(s->lay.diag_acc);
+  double* sw = acc + 64;
+  double* sg = sw + kMaxSlices;
+  double* sv = sg + kMaxSlices;
+  Parts p = parts_of(s, s->cur);
+  PIC_CUDA(cudaMemsetAsync(acc, 0, 64 * sizeof(double), s->stream));
+  int grid = pgrid(np);
+  if (np > 0) {
+    k_diag_moments<<<grid, kDiagThreads, 0, s->stream>>>(p, np, lo, hi, acc);
+    PIC_LAUNCHED(s);
+  }
+  double h[8];
+  PIC_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  PIC_CUDA(cudaStreamSynchronize(s->stream));
+  *out = pic_diag{};
+  out->n_particles = (int32_t)h[7];
+  out->W = h[0];
+  if (h[7] == 0 || h[0] <= 0.0) return PIC_OK;
+  double mean[5] = {h[1] / h[0], h[2] / h[0], h[3] / h[0], h[4] / h[0], h[5] / h[0]};
+  out->x_mean = mean[0]; out->y_mean = mean[1]; out->z_mean = mean[2];
+  out->gamma_mean = h[6] / h[0];
+  double* dmean = acc + 16;
+  PIC_CUDA(cudaMemcpyAsync(dmean, mean, sizeof(mean), cudaMemcpyHostToDevice, s->stream));
+  k_diag_central<<<grid, kDiagThreads, 0, s->stream>>>(p, np, lo, hi, dmean, acc + 32);
+  PIC_LAUNCHED(s);
+  double c2[7];
+  PIC_CUDA(cudaMemcpyAsync(c2, acc + 32, sizeof(c2), cudaMemcpyDeviceToHost, s->stream));
+  PIC_CUDA(cudaStreamSynchronize(s->stream));
+  const double W = h[0];
+  const double xx = c2[0] / W, uu = c2[1] / W, xu = c2[2] / W;
+  const double yy = c2[3] / W, vv = c2[4] / W, yv = c2[5] / W;
+  out->emit_nx = std::sqrt(std::max(xx * uu - xu * xu, 0.0)) / kC;
+  out->emit_ny = std::sqrt(std::max(yy * vv - yv * yv, 0.0)) / kC;
+  const double sz = std::sqrt(c2[6] / W);
+  out->sigma_z = sz;
+  if (!(sz > 0.0)) return PIC_OK;
+  const double span = 6.0 * sz;
+  const double ns_d = std::ceil(span / kSliceLen);
+  if (ns_d > kMaxSlices) {
+    set_error("diagnostics: %g slices exceed the maximum %d", ns_d, kMaxSlices);
+    return PIC_ERR_ARG;
+  }
+  const int ns = (int)ns_d;
+  const double zstart = mean[2] - 3.0 * sz;
+  PIC_CUDA(cudaMemsetAsync(sw, 0, 3 * sizeof(double) * kMaxSlices, s->stream));
+  k_diag_slices<<<grid, kDiagThreads, 0, s->stream>>>(p, np, lo, hi, zstart, span, kSliceLen, ns, sw, sg,
+                                                       sv, 0);
+  PIC_LAUNCHED(s);
+  k_diag_slices<<<grid, kDiagThreads, 0, s->stream>>>(p, np, lo, hi, zstart, span, kSliceLen, ns, sw, sg,
+                                                       sv, 1);
+  PIC_LAUNCHED(s);
+  std::vector<double> hw(ns), hv(ns);
+  PIC_CUDA(cudaMemcpyAsync(hw.data(), sw, ns * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  PIC_CUDA(cudaMemcpyAsync(hv.data(), sv, ns * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  PIC_CUDA(cudaStreamSynchronize(s->stream));
+  int ne = 0;
+  double sum = 0.0;
+  for (int k = 0; k < ns; ++k) {
+    if (hw[k] > 0.0) {
+      const double sg_k = std::sqrt(hv[k] / hw[k]);
+      if (slice_sigma && ne < max_slices) slice_sigma[ne] = sg_k;
+      sum += sg_k;
+      ++ne;
+    }
+  }
+  out->n_slices = ne;
+  out->sigma_gamma_mean = ne ? sum / ne : 0.0;
+  return PIC_OK;
+}
+
+size_t diag_acc_doubles() { return 64 + 3 * (size_t)kMaxSlices + kMaxNr; }
+
+}  // namespace pic

@@ -1,0 +1,588 @@
+// C ABI of libpsatd_rz.so (declared in include/psatd_rz.h): configuration checks,
+// workspace layout, and the order of the stages of one quasi-cylindrical PSATD PIC cycle
+// (section "Finite order pseudo-spectral solvers" of arXiv:1611.05712).
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+pic_status cuda_status(cudaError_t e, const char* what) {
+  set_error("%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+  return PIC_ERR_CUDA;
+}
+
+bool plan_radix(int N, int32_t* radix, int32_t* n_pass);
+size_t diag_acc_doubles();
+pic_status launch_filter_copy(Sim* s, void* dst, const void* src);
+pic_status launch_scale_copy(Sim* s, void* dst, const void* src, double a, size_t n_cplx);
+
+namespace {
+
+pic_status validate(const pic_config* c, int32_t* radix, int32_t* n_pass) {
+  if (!c) { set_error("config is NULL"); return PIC_ERR_ARG; }
+  if (c->precision != PIC_FP64) {
+    set_error("precision %d is not available in this build", c->precision);
+    return PIC_ERR_ARG;
+  }
+  const int max_nz = 4096;
+  if (c->Nz < 8 || c->Nz > max_nz || !plan_radix(c->Nz, radix, n_pass)) {
+    set_error("Nz=%d must be a 7-smooth integer in [8, %d]", c->Nz, max_nz);
+    return PIC_ERR_ARG;
+  }
+  if (c->Nr < 4 || c->Nr > kMaxNr) { set_error("Nr=%d must be in [4, %d]", c->Nr, kMaxNr); return PIC_ERR_ARG; }
+  if (c->Nm < 1 || c->Nm > kMaxModes) { set_error("Nm=%d must be in [1, %d]", c->Nm, kMaxModes); return PIC_ERR_ARG; }
+  if (c->order_p != 0 && (c->order_p < 2 || c->order_p > 512 || (c->order_p & 1))) {
+    set_error("order_p=%d must be 0 (infinite) or even in [2, 512]", c->order_p);
+    return PIC_ERR_ARG;
+  }
+  if (!(c->dz > 0) || !(c->dr > 0) || !(c->dt > 0)) { set_error("dz, dr, dt must be > 0"); return PIC_ERR_ARG; }
+  if (c->np_capacity < 0 || c->np_capacity > INT32_MAX) {
+    set_error("np_capacity=%lld out of range", (long long)c->np_capacity);
+    return PIC_ERR_ARG;
+  }
+  if (!(c->mass > 0) || !(c->q == c->q)) { set_error("species charge/mass invalid"); return PIC_ERR_ARG; }
+  return PIC_OK;
+}
+
+Layout make_layout(const pic_config& c) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t cb = 16;   // complex float64
+  const size_t G = (size_t)c.Nm * c.Nr * c.Nz;
+  const size_t Nr2 = (size_t)c.Nr * c.Nr;
+  const size_t cap = (size_t)std::max<int64_t>(c.np_capacity, 1);
+  const size_t ncell = (size_t)c.Nz * c.Nr;
+  L.E = take(6 * G * cb);   // E then B, adjacent
+  L.B = L.E + 3 * G * cb;
+  L.Eh = take(6 * G * cb);  // Eh then Bh, adjacent
+  L.Bh = L.Eh + 3 * G * cb;
+  L.dep = take(4 * G * cb);
+  L.srch = take(4 * G * cb);
+  L.tmp = take(6 * G * cb);
+  L.rho_prev_h = take(G * cb);
+  L.rho_ion = take(G * cb);
+  L.kperp = take((size_t)c.Nm * c.Nr * 8);
+  L.binv = take((size_t)c.Nm * 3 * Nr2 * 8);
+  L.mfwd = take((size_t)c.Nm * 3 * Nr2 * 8);
+  L.svd_w = take((size_t)c.Nm * 3 * Nr2 * 8);
+  L.svd_v = take((size_t)c.Nm * 3 * Nr2 * 8);
+  L.svd_d = take((size_t)c.Nm * 3 * c.Nr * 8);
+  L.kzmod = take((size_t)c.Nz * 8);
+  L.tz = take((size_t)c.Nz * 8);
+  L.tr = take((size_t)c.Nm * c.Nr * 8);
+  L.coef = take(6 * G * 8);
+  L.twiddle = take((size_t)c.Nz * 16);
+  for (int b = 0; b < 2; ++b) {
+    for (int k = 0; k < 7; ++k) L.part[b][k] = take(cap * 8);
+    L.pid[b] = take(cap * 4);
+  }
+  L.keys = take(cap * 4);
+  L.perm = take(cap * 4);
+  L.perm_tmp = take(cap * 4);
+  L.count = take((ncell + 1) * 4);
+  L.start = take((ncell + 1) * 4);
+  L.scan_blk = take(4 * 4096 * 4 + (ncell + 1) * 4);   // block totals, then the scatter cursor
+  L.big_list = take(ncell * 4);
+  L.big_count = take(256);
+  L.diag_acc = take(diag_acc_doubles() * 8);
+  L.err = take(256);
+  L.total = off;
+  return L;
+}
+
+struct BufView {
+  size_t off, bytes;
+};
+
+bool buffer_view(const Sim* s, int32_t id, BufView* v) {
+  const pic_config& c = s->cfg;
+  const size_t G = s->grid_elems(), cb = s->cplx_bytes, Nr2 = (size_t)c.Nr * c.Nr;
+  switch (id) {
+    case PIC_BUF_E: *v = {s->lay.E, 3 * G * cb}; return true;
+    case PIC_BUF_B: *v = {s->lay.B, 3 * G * cb}; return true;
+    case PIC_BUF_EH: *v = {s->lay.Eh, 3 * G * cb}; return true;
+    case PIC_BUF_BH: *v = {s->lay.Bh, 3 * G * cb}; return true;
+    case PIC_BUF_DEP: *v = {s->lay.dep, 4 * G * cb}; return true;
+    case PIC_BUF_SRC_H: *v = {s->lay.srch, 4 * G * cb}; return true;
+    case PIC_BUF_RHO_PREV_H: *v = {s->lay.rho_prev_h, G * cb}; return true;
+    case PIC_BUF_RHO_ION: *v = {s->lay.rho_ion, G * cb}; return true;
+    case PIC_BUF_KPERP: *v = {s->lay.kperp, (size_t)c.Nm * c.Nr * 8}; return true;
+    case PIC_BUF_HANKEL_INV: *v = {s->lay.binv, (size_t)c.Nm * 3 * Nr2 * 8}; return true;
+    case PIC_BUF_HANKEL_FWD: *v = {s->lay.mfwd, (size_t)c.Nm * 3 * Nr2 * 8}; return true;
+    case PIC_BUF_KZ_MOD: *v = {s->lay.kzmod, (size_t)c.Nz * 8}; return true;
+    case PIC_BUF_KEYS: *v = {s->lay.keys, (size_t)s->np * 4}; return true;
+    case PIC_BUF_PERM: *v = {s->lay.perm, (size_t)s->np * 4}; return true;
+    default: return false;
+  }
+}
+
+// forward z-FFT of the first n_comp components of dep into tmp, with
+// J_+- = (J_r -+ i J_theta)/2 formed on load.
+pic_status fft_forward(Sim* s, int n_comp) {
+  RowCombine rc{};
+  rc.n_out = n_comp;
+  for (int k = 0; k < 6; ++k) { rc.srcA[k] = k; rc.srcB[k] = -1; rc.caRe[k] = 1.0; }
+  if (n_comp == 4) {
+    // out: rho, J_+ = (J_r - i J_th)/2, J_- = (J_r + i J_th)/2, J_z
+    rc.srcA[1] = 1; rc.caRe[1] = 0.5; rc.srcB[1] = 2; rc.cbRe[1] = 0.0; rc.cbIm[1] = -0.5;
+    rc.srcA[2] = 1; rc.caRe[2] = 0.5; rc.srcB[2] = 2; rc.cbRe[2] = 0.0; rc.cbIm[2] = 0.5;
+    rc.srcA[3] = 3;
+  }
+  return launch_fft_rows(s, s->at<char>(s->lay.dep), s->at<char>(s->lay.tmp), rc, false);
+}
+
+// forward DHT of every (component, mode) of tmp into srch.
+pic_status dht_forward(Sim* s, int n_comp) {
+  const pic_config& c = s->cfg;
+  const size_t G = s->grid_elems();
+  DhtBatch b{};
+  const int slot_of[4] = {1, 2, 0, 1};   // rho: order m, J_+: m+1, J_-: m-1, J_z: m
+  const size_t Nr2 = (size_t)c.Nr * c.Nr;
+  for (int comp = 0; comp < n_comp; ++comp)
+    for (int m = 0; m < c.Nm; ++m) {
+      b.A[b.n] = s->at<double>(s->lay.mfwd) + ((size_t)m * 3 + slot_of[comp]) * Nr2;
+      b.X[b.n] = s->at<char>(s->lay.tmp) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
+      b.Y[b.n] = s->at<char>(s->lay.srch) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
+      ++b.n;
+    }
+  return launch_dht(s, b);
+}
+
+pic_status forward_transform(Sim* s, int n_comp) {
+  pic_status st = fft_forward(s, n_comp);
+  if (st != PIC_OK) return st;
+  return dht_forward(s, n_comp);
+}
+
+// inverse DHT of Eh, Bh (+, -, z) per mode into tmp.
+pic_status dht_inverse(Sim* s) {
+  const pic_config& c = s->cfg;
+  const size_t G = s->grid_elems();
+  const size_t Nr2 = (size_t)c.Nr * c.Nr;
+  const int slot_of[3] = {2, 0, 1};      // +: m+1, -: m-1, z: m
+  DhtBatch b{};
+  for (int comp = 0; comp < 6; ++comp)
+    for (int m = 0; m < c.Nm; ++m) {
+      b.A[b.n] = s->at<double>(s->lay.binv) + ((size_t)m * 3 + slot_of[comp % 3]) * Nr2;
+      b.X[b.n] = s->at<char>(s->lay.Eh) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
+      b.Y[b.n] = s->at<char>(s->lay.tmp) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
+      ++b.n;
+    }
+  return launch_dht(s, b);
+}
+
+// inverse z-FFT of tmp into E, B with E_r = E_+ + E_-, E_theta = i (E_+ - E_-) formed on load.
+pic_status fft_inverse(Sim* s) {
+  RowCombine rc{};
+  rc.n_out = 6;
+  for (int f = 0; f < 2; ++f) {
+    const int o = 3 * f;
+    rc.srcA[o + 0] = o; rc.caRe[o + 0] = 1.0; rc.srcB[o + 0] = o + 1; rc.cbRe[o + 0] = 1.0;
+    rc.srcA[o + 1] = o; rc.caIm[o + 1] = 1.0; rc.srcB[o + 1] = o + 1; rc.cbIm[o + 1] = -1.0;
+    rc.srcA[o + 2] = o + 2; rc.caRe[o + 2] = 1.0; rc.srcB[o + 2] = -1;
+  }
+  return launch_fft_rows(s, s->at<char>(s->lay.tmp), s->at<char>(s->lay.E), rc, true);
+}
+
+pic_status inverse_transform(Sim* s) {
+  pic_status st = dht_inverse(s);
+  if (st != PIC_OK) return st;
+  return fft_inverse(s);
+}
+
+pic_status deposit_rho_with_background(Sim* s) {
+  const size_t G = s->grid_elems();
+  PIC_CUDA(cudaMemcpyAsync(s->at<char>(s->lay.dep), s->at<char>(s->lay.rho_ion), G * s->cplx_bytes,
+                           cudaMemcpyDeviceToDevice, s->stream));
+  return launch_deposit(s, PIC_DEP_RHO, INT32_MIN, INT32_MAX, nullptr);
+}
+
+// Optional stage timing: when ev is non-null, ev[k] is recorded after stage k-1.
+struct Marks {
+  cudaEvent_t* ev = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaError_t mark(int k) { return ev ? cudaEventRecord(ev[k], stream) : cudaSuccess; }
+};
+
+pic_status field_step(Sim* s, int32_t order_p, Marks* mk = nullptr, int base = 0) {
+  Marks none;
+  Marks& m = mk ? *mk : none;
+  pic_status st;
+  if (order_p >= 0 && order_p != s->order_tables) {
+    if (order_p != 0 && (order_p < 2 || order_p > 512 || (order_p & 1))) {
+      set_error("order_p=%d must be 0 (infinite) or even in [2, 512]", order_p);
+      return PIC_ERR_ARG;
+    }
+    if ((st = launch_setup_tables(s, order_p)) != PIC_OK) return st;
+  }
+  if ((st = fft_forward(s, 4)) != PIC_OK) return st;
+  PIC_CUDA(m.mark(base + 1));
+  if ((st = dht_forward(s, 4)) != PIC_OK) return st;
+  PIC_CUDA(m.mark(base + 2));
+  if ((st = launch_psatd(s)) != PIC_OK) return st;
+  PIC_CUDA(m.mark(base + 3));
+  if ((st = dht_inverse(s)) != PIC_OK) return st;
+  PIC_CUDA(m.mark(base + 4));
+  if ((st = fft_inverse(s)) != PIC_OK) return st;
+  PIC_CUDA(m.mark(base + 5));
+  return PIC_OK;
+}
+
+// One PIC cycle; with marks, events 0..8 bracket the eight stages of pic_stage.
+pic_status step_once(Sim* s, Marks* mk) {
+  Marks none;
+  Marks& m = mk ? *mk : none;
+  pic_status st;
+  PIC_CUDA(m.mark(0));
+  if ((st = launch_gather_push(s, 1)) != PIC_OK) return st;
+  PIC_CUDA(m.mark(1));
+  if ((st = launch_sort(s)) != PIC_OK) return st;
+  PIC_CUDA(m.mark(2));
+  if ((st = deposit_rho_with_background(s)) != PIC_OK) return st;
+  return field_step(s, -1, mk, 2);
+}
+
+#define CHECK_SIM(s)                                              \
+  do {                                                            \
+    if (!(s)) { set_error("sim handle is NULL"); return PIC_ERR_ARG; } \
+  } while (0)
+
+}  // namespace
+}  // namespace pic
+
+using namespace pic;
+
+extern "C" {
+
+const char* pic_last_error(void) { return g_last_error.c_str(); }
+
+pic_status pic_required_bytes(const pic_config* cfg, size_t* bytes) {
+  int32_t radix[kMaxRadixPasses], np_;
+  pic_status st = validate(cfg, radix, &np_);
+  if (st != PIC_OK) return st;
+  if (!bytes) { set_error("bytes is NULL"); return PIC_ERR_ARG; }
+  *bytes = make_layout(*cfg).total;
+  return PIC_OK;
+}
+
+pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_bytes, void* stream,
+                    pic_sim** out) {
+  if (!out) { set_error("out is NULL"); return PIC_ERR_ARG; }
+  *out = nullptr;
+  Sim tmp{};
+  pic_status st = validate(cfg, tmp.radix, &tmp.n_radix);
+  if (st != PIC_OK) return st;
+  Layout L = make_layout(*cfg);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+    set_error("workspace must be a non-NULL 256-byte aligned device pointer");
+    return PIC_ERR_ARG;
+  }
+  if (workspace_bytes < L.total) {
+    set_error("workspace has %zu bytes, %zu required", workspace_bytes, L.total);
+    return PIC_ERR_OOM;
+  }
+  Sim* s = new (std::nothrow) Sim(tmp);
+  if (!s) { set_error("host allocation failed"); return PIC_ERR_OOM; }
+  s->cfg = *cfg;
+  s->lay = L;
+  s->stream = reinterpret_cast<cudaStream_t>(stream);
+  s->ws = reinterpret_cast<char*>(workspace);
+  s->ws_bytes = workspace_bytes;
+  s->order_tables = -1;
+  s->np = 0;
+  s->cur = 0;
+  s->cplx_bytes = 16;
+  const size_t G = s->grid_elems();
+  auto fail = [&](pic_status e) { delete s; return e; };
+  cudaError_t ce;
+  if ((ce = cudaMemsetAsync(s->ws + L.E, 0, 6 * G * 16, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if ((ce = cudaMemsetAsync(s->ws + L.Eh, 0, 6 * G * 16, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if ((ce = cudaMemsetAsync(s->ws + L.rho_prev_h, 0, G * 16, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if ((ce = cudaMemsetAsync(s->ws + L.rho_ion, 0, G * 16, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if ((ce = cudaMemsetAsync(s->ws + L.dep, 0, 4 * G * 16, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if ((ce = cudaMemsetAsync(s->ws + L.err, 0, 256, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if ((st = launch_setup_twiddles(s)) != PIC_OK) return fail(st);
+  if ((st = launch_setup_hankel(s)) != PIC_OK) return fail(st);
+  if ((st = launch_setup_tables(s, cfg->order_p)) != PIC_OK) return fail(st);
+  if ((st = pic_sync(reinterpret_cast<pic_sim*>(s))) != PIC_OK) return fail(st);
+  *out = reinterpret_cast<pic_sim*>(s);
+  return PIC_OK;
+}
+
+pic_status pic_destroy(pic_sim* sim) {
+  delete reinterpret_cast<Sim*>(sim);
+  return PIC_OK;
+}
+
+pic_status pic_sync(pic_sim* sim) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  PIC_CUDA(cudaStreamSynchronize(s->stream));
+  int32_t e = 0;
+  PIC_CUDA(cudaMemcpy(&e, s->ws + s->lay.err, sizeof(e), cudaMemcpyDeviceToHost));
+  if (e & kErrTimeout) { set_error("a device loop hit its iteration cap (error word %d)", e); return PIC_ERR_TIMEOUT; }
+  if (e) { set_error("non-finite or out-of-range values on the device (error word %d)", e); return PIC_ERR_NUMERIC; }
+  return PIC_OK;
+}
+
+pic_status pic_write_particles(pic_sim* sim, const double* const soa[7], const int32_t* id, int64_t n,
+                               int32_t on_host) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (n < 0 || n > s->cfg.np_capacity) {
+    set_error("n=%lld exceeds the capacity %lld", (long long)n, (long long)s->cfg.np_capacity);
+    return PIC_ERR_ARG;
+  }
+  if (n > 0 && (!soa || !id)) { set_error("particle pointers are NULL"); return PIC_ERR_ARG; }
+  const cudaMemcpyKind kind = on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  for (int k = 0; k < 7 && n > 0; ++k) {
+    if (!soa[k]) { set_error("particle array %d is NULL", k); return PIC_ERR_ARG; }
+    PIC_CUDA(cudaMemcpyAsync(s->ws + s->lay.part[s->cur][k], soa[k], n * 8, kind, s->stream));
+  }
+  if (n > 0) PIC_CUDA(cudaMemcpyAsync(s->ws + s->lay.pid[s->cur], id, n * 4, kind, s->stream));
+  if (on_host) PIC_CUDA(cudaStreamSynchronize(s->stream));
+  s->np = n;
+  return PIC_OK;
+}
+
+pic_status pic_read_particles(pic_sim* sim, double* const soa[7], int32_t* id, int64_t n,
+                              int32_t on_host) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (n < 0 || n > s->np) { set_error("n=%lld exceeds the %lld particles held", (long long)n, (long long)s->np); return PIC_ERR_ARG; }
+  const cudaMemcpyKind kind = on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+  for (int k = 0; k < 7 && n > 0; ++k)
+    if (soa && soa[k]) PIC_CUDA(cudaMemcpyAsync(soa[k], s->ws + s->lay.part[s->cur][k], n * 8, kind, s->stream));
+  if (id && n > 0) PIC_CUDA(cudaMemcpyAsync(id, s->ws + s->lay.pid[s->cur], n * 4, kind, s->stream));
+  return pic_sync(sim);
+}
+
+pic_status pic_num_particles(pic_sim* sim, int64_t* n) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (!n) { set_error("n is NULL"); return PIC_ERR_ARG; }
+  *n = s->np;
+  return PIC_OK;
+}
+
+pic_status pic_init_background(pic_sim* sim, int32_t n_neutral) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  const size_t G = s->grid_elems();
+  PIC_CUDA(cudaMemsetAsync(s->ws + s->lay.dep, 0, G * 16, s->stream));
+  pic_status st = launch_deposit(s, PIC_DEP_RHO, 0, n_neutral, nullptr);
+  if (st != PIC_OK) return st;
+  return launch_scale_copy(s, s->ws + s->lay.rho_ion, s->ws + s->lay.dep, -1.0, G);
+}
+
+pic_status pic_add_beam_fields(pic_sim* sim, int32_t id_lo, int32_t id_hi, double gamma) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (!(gamma >= 1.0)) { set_error("gamma=%g must be >= 1", gamma); return PIC_ERR_ARG; }
+  const size_t G = s->grid_elems();
+  PIC_CUDA(cudaMemsetAsync(s->ws + s->lay.dep, 0, G * 16, s->stream));
+  pic_status st = launch_deposit(s, PIC_DEP_RHO, id_lo, id_hi, nullptr);
+  if (st != PIC_OK) return st;
+  if ((st = forward_transform(s, 1)) != PIC_OK) return st;
+  return launch_beam_fields(s, s->ws + s->lay.srch, gamma);
+}
+
+pic_status pic_init_fields(pic_sim* sim) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  pic_status st = deposit_rho_with_background(s);
+  if (st != PIC_OK) return st;
+  if ((st = forward_transform(s, 1)) != PIC_OK) return st;
+  if ((st = launch_filter_copy(s, s->ws + s->lay.rho_prev_h, s->ws + s->lay.srch)) != PIC_OK) return st;
+  if ((st = inverse_transform(s)) != PIC_OK) return st;
+  s->fields_ready = 1;
+  return PIC_OK;
+}
+
+pic_status pic_sort(pic_sim* sim) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  return launch_sort(s);
+}
+
+pic_status pic_deposit(pic_sim* sim, int32_t what) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (what & ~(PIC_DEP_RHO | PIC_DEP_J)) { set_error("what=%d has unknown bits", what); return PIC_ERR_ARG; }
+  pic_status st;
+  if (what & PIC_DEP_RHO) {
+    const size_t G = s->grid_elems();
+    PIC_CUDA(cudaMemcpyAsync(s->ws + s->lay.dep, s->ws + s->lay.rho_ion, G * 16, cudaMemcpyDeviceToDevice,
+                             s->stream));
+  }
+  if ((st = launch_deposit(s, what, INT32_MIN, INT32_MAX, nullptr)) != PIC_OK) return st;
+  return PIC_OK;
+}
+
+pic_status pic_gather_push(pic_sim* sim, int32_t fuse_current) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  return launch_gather_push(s, fuse_current);
+}
+
+pic_status pic_field_step(pic_sim* sim, int32_t order_p) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  return field_step(s, order_p);
+}
+
+pic_status pic_forward_transform(pic_sim* sim) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  return forward_transform(s, 4);
+}
+
+pic_status pic_psatd(pic_sim* sim) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  return launch_psatd(s);
+}
+
+pic_status pic_inverse_transform(pic_sim* sim) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  return inverse_transform(s);
+}
+
+pic_status pic_step(pic_sim* sim, int32_t n_steps) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (n_steps < 0) { set_error("n_steps=%d < 0", n_steps); return PIC_ERR_ARG; }
+  if (!s->fields_ready) { set_error("pic_init_fields must run before stepping"); return PIC_ERR_STATE; }
+  for (int32_t k = 0; k < n_steps; ++k) {
+    pic_status st = step_once(s, nullptr);
+    if (st != PIC_OK) return st;
+  }
+  return PIC_OK;
+}
+
+pic_status pic_step_timed(pic_sim* sim, int32_t n_steps, double* stage_ms) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (n_steps < 1 || n_steps > 4096 || !stage_ms) { set_error("n_steps must be in [1, 4096] and stage_ms non-NULL"); return PIC_ERR_ARG; }
+  if (!s->fields_ready) { set_error("pic_init_fields must run before stepping"); return PIC_ERR_STATE; }
+  const int per = PIC_NSTAGES + 1;
+  const size_t nev = (size_t)n_steps * per;
+  cudaEvent_t* ev = new (std::nothrow) cudaEvent_t[nev];
+  if (!ev) { set_error("host allocation failed"); return PIC_ERR_OOM; }
+  size_t made = 0;
+  pic_status st = PIC_OK;
+  for (; made < nev; ++made) {
+    cudaError_t e = cudaEventCreate(&ev[made]);
+    if (e != cudaSuccess) { st = cuda_status(e, "cudaEventCreate"); break; }
+  }
+  for (int32_t k = 0; st == PIC_OK && k < n_steps; ++k) {
+    Marks mk;
+    mk.ev = ev + (size_t)k * per;
+    mk.stream = s->stream;
+    st = step_once(s, &mk);
+  }
+  if (st == PIC_OK) {
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) st = cuda_status(e, "cudaStreamSynchronize");
+  }
+  if (st == PIC_OK) {
+    for (int i = 0; i <= PIC_NSTAGES; ++i) stage_ms[i] = 0.0;
+    for (int32_t k = 0; k < n_steps && st == PIC_OK; ++k) {
+      for (int i = 0; i < PIC_NSTAGES; ++i) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, ev[(size_t)k * per + i], ev[(size_t)k * per + i + 1]);
+        if (e != cudaSuccess) { st = cuda_status(e, "cudaEventElapsedTime"); break; }
+        stage_ms[i] += ms;
+      }
+    }
+    float tot = 0.f;
+    if (st == PIC_OK) {
+      cudaError_t e = cudaEventElapsedTime(&tot, ev[0], ev[nev - 1]);
+      if (e != cudaSuccess) st = cuda_status(e, "cudaEventElapsedTime");
+      stage_ms[PIC_NSTAGES] = tot;
+    }
+  }
+  for (size_t i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+  delete[] ev;
+  if (st != PIC_OK) return st;
+  return pic_sync(sim);
+}
+
+pic_status pic_diagnostics(pic_sim* sim, int32_t id_lo, int32_t id_hi, pic_diag* out,
+                           double* slice_sigma, int32_t max_slices) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (!out) { set_error("out is NULL"); return PIC_ERR_ARG; }
+  pic_status st = launch_diag(s, id_lo, id_hi, out, slice_sigma, max_slices);
+  if (st != PIC_OK) return st;
+  return pic_sync(sim);
+}
+
+pic_status pic_buffer_bytes(pic_sim* sim, int32_t buffer_id, size_t* bytes) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  BufView v;
+  if (!bytes || !buffer_view(s, buffer_id, &v)) { set_error("unknown buffer %d", buffer_id); return PIC_ERR_ARG; }
+  *bytes = v.bytes;
+  return PIC_OK;
+}
+
+pic_status pic_copy_buffer(pic_sim* sim, int32_t buffer_id, void* dst, size_t bytes, int32_t dst_on_host) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  BufView v;
+  if (!buffer_view(s, buffer_id, &v)) { set_error("unknown buffer %d", buffer_id); return PIC_ERR_ARG; }
+  if (!dst || bytes != v.bytes) { set_error("buffer %d has %zu bytes, %zu given", buffer_id, v.bytes, bytes); return PIC_ERR_ARG; }
+  PIC_CUDA(cudaMemcpyAsync(dst, s->ws + v.off, bytes,
+                           dst_on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s->stream));
+  if (dst_on_host) return pic_sync(sim);
+  return PIC_OK;
+}
+
+pic_status pic_load_buffer(pic_sim* sim, int32_t buffer_id, const void* src, size_t bytes, int32_t src_on_host) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  BufView v;
+  if (!buffer_view(s, buffer_id, &v)) { set_error("unknown buffer %d", buffer_id); return PIC_ERR_ARG; }
+  if (buffer_id == PIC_BUF_KEYS || buffer_id == PIC_BUF_PERM) { set_error("buffer %d is read-only", buffer_id); return PIC_ERR_ARG; }
+  if (!src || bytes != v.bytes) { set_error("buffer %d has %zu bytes, %zu given", buffer_id, v.bytes, bytes); return PIC_ERR_ARG; }
+  PIC_CUDA(cudaMemcpyAsync(s->ws + v.off, src, bytes,
+                           src_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s->stream));
+  if (src_on_host) PIC_CUDA(cudaStreamSynchronize(s->stream));
+  if (buffer_id == PIC_BUF_E || buffer_id == PIC_BUF_B) s->fields_ready = 1;
+  return PIC_OK;
+}
+
+pic_status pic_launch_count(pic_sim* sim, int64_t* launches) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (!launches) { set_error("launches is NULL"); return PIC_ERR_ARG; }
+  *launches = s->launches;
+  return PIC_OK;
+}
+
+}  // extern "C"

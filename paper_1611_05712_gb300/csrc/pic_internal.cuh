@@ -1,0 +1,115 @@
+// Internal declarations shared by the translation units of libpsatd_rz.so.
+//
+// Paper: Jalas et al., arXiv:1611.05712 -- quasi-cylindrical arbitrary-order PSATD
+// PIC cycle (section "Finite order pseudo-spectral solvers").  The public contract is
+// include/psatd_rz.h; this header holds the device-side layout and the launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/psatd_rz.h"
+
+namespace pic {
+
+// SI constants, CODATA 2018; mu0 is tied to eps0 and c so that mu0 eps0 c^2 = 1.
+constexpr double kC = 299792458.0;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMu0 = 1.0 / (kEps0 * kC * kC);
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kPinvRcond = 1e-3;   // singular values <= rcond * sigma_max are dropped
+constexpr double kSmallX = 0.25;      // omega*dt below which the PSATD coefficients use series
+constexpr double kSliceLen = 0.5e-6;  // slice length of the slice energy spread [m]
+
+constexpr int kMaxModes = 4;
+constexpr int kMaxNr = 1024;
+constexpr int kMaxRadixPasses = 16;
+
+// Device error word bits.
+enum : int32_t { kErrNumeric = 1, kErrTimeout = 2, kErrRange = 4 };
+
+// Device workspace layout, all offsets in bytes from the workspace base.
+struct Layout {
+  size_t E, B, Eh, Bh, dep, srch, tmp, rho_prev_h, rho_ion;   // grids
+  size_t kperp, binv, mfwd, svd_w, svd_v, svd_d;                // DHT tables and scratch
+  size_t kzmod, tz, tr, coef, twiddle;                           // PSATD tables
+  size_t part[2][7], pid[2];                                     // particles (double buffer)
+  size_t keys, perm, perm_tmp, count, start, scan_blk, big_list, big_count;
+  size_t diag_acc, err;
+  size_t total;
+};
+
+struct Sim {
+  pic_config cfg;
+  Layout lay;
+  cudaStream_t stream;
+  char* ws;
+  size_t ws_bytes;
+  int32_t order_tables;    // order p the coefficient tables were built for
+  int64_t np;              // particles held
+  int cur;                 // which particle buffer is current
+  int fields_ready;
+  int64_t launches;        // kernels launched by this handle (host-side count)
+  int32_t n_radix;
+  int32_t radix[kMaxRadixPasses];
+  size_t cplx_bytes;       // 16 (FP64) or 8 (mixed)
+
+  template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+  size_t grid_elems() const { return (size_t)cfg.Nm * cfg.Nr * cfg.Nz; }
+};
+
+// Error reporting (thread-local text, see pic_last_error).
+void set_error(const char* fmt, ...);
+pic_status cuda_status(cudaError_t e, const char* what);
+
+#define PIC_CUDA(call)                                                     \
+  do {                                                                     \
+    cudaError_t e__ = (call);                                              \
+    if (e__ != cudaSuccess) return ::pic::cuda_status(e__, #call);         \
+  } while (0)
+
+#define PIC_LAUNCHED(sim)                                                  \
+  do {                                                                     \
+    (sim)->launches++;                                                     \
+    cudaError_t e__ = cudaGetLastError();                                  \
+    if (e__ != cudaSuccess) return ::pic::cuda_status(e__, "kernel launch"); \
+  } while (0)
+
+// ---- launchers (setup.cu) ----
+pic_status launch_setup_hankel(Sim* s);          // zeros, B_p, pinv(B_p)
+pic_status launch_setup_tables(Sim* s, int32_t order_p);   // [k_z]_p and PSATD coefficients
+pic_status launch_setup_twiddles(Sim* s);
+
+// ---- launchers (fft.cu) ----
+// Row transform descriptor: out[c] = FFT(ca*in[srcA] + cb*in[srcB]) (inverse: iFFT).
+struct RowCombine {
+  int32_t n_out;
+  int32_t srcA[6], srcB[6];   // srcB < 0: none
+  double caRe[6], caIm[6], cbRe[6], cbIm[6];
+};
+pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& rc, bool inverse);
+
+// ---- launchers (dht.cu) ----
+// out[b] = A[b] (Nr x Nr, row-major [out][red]) * in[b] (Nr x 2Nz reals)
+struct DhtBatch {
+  int32_t n;
+  const double* A[24];
+  const void* X[24];
+  void* Y[24];
+};
+pic_status launch_dht(Sim* s, const DhtBatch& b);
+
+// ---- launchers (psatd.cu) ----
+pic_status launch_psatd(Sim* s);
+pic_status launch_beam_fields(Sim* s, const void* rho_h, double gamma);  // adds to Eh, Bh
+pic_status launch_filter_copy(Sim* s, void* dst, const void* src);        // dst = T * src
+pic_status launch_scale_copy(Sim* s, void* dst, const void* src, double a, size_t n_cplx);
+
+// ---- launchers (particles.cu) ----
+pic_status launch_sort(Sim* s);
+pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, void* rho_out);
+pic_status launch_gather_push(Sim* s, int32_t fuse_current);
+pic_status launch_diag(Sim* s, int32_t id_lo, int32_t id_hi, pic_diag* out, double* slice_sigma,
+                       int32_t max_slices);
+
+}  // namespace pic
