@@ -71,8 +71,8 @@ __global__ void __launch_bounds__(256) k_dht_f64(DhtBatch bt, int Nr, int Nc) {
 
 }  // namespace
 
-pic_status launch_dht(Sim* s, const DhtBatch& b) {
-  const int Nr = s->cfg.Nr, Nc = 2 * s->cfg.Nz;
+pic_status launch_dht(Sim* s, const DhtBatch& b, int ncols) {
+  const int Nr = s->cfg.Nr, Nc = ncols > 0 ? ncols : 2 * s->cfg.Nz;
   dim3 grid((Nc + BN - 1) / BN, (Nr + BM - 1) / BM, b.n);
   k_dht_f64<<<grid, 256, 0, s->stream>>>(b, Nr, Nc);
   PIC_LAUNCHED(s);

@@ -366,18 +366,18 @@ __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __
     const double ig = 1.0 / sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
     const double vx = ux * ig, vy = uy * ig, vz = uz * ig;
     const double hdt = 0.5 * dt;
-    x = x + hdt * vx;
-    y = y + hdt * vy;
-    z = z + hdt * vz;
+    x = __dadd_rn(x, __dmul_rn(hdt, vx));   // no FMA: one ulp of z is ~L/dz ulps of a weight
+    y = __dadd_rn(y, __dmul_rn(hdt, vy));
+    z = __dadd_rn(z, __dmul_rn(hdt, vz));
     if (z >= g.L) z -= g.L;
     if (z < 0.0) z += g.L;
     if (fuse) deposit_one(g, dep, invV, x, y, z, w, vx, vy, vz, false, true);
-    x = x + hdt * vx;
-    y = y + hdt * vy;
-    z = z + hdt * vz;
+    x = __dadd_rn(x, __dmul_rn(hdt, vx));   // no FMA: one ulp of z is ~L/dz ulps of a weight
+    y = __dadd_rn(y, __dmul_rn(hdt, vy));
+    z = __dadd_rn(z, __dmul_rn(hdt, vz));
     if (z >= g.L) z -= g.L;
     if (z < 0.0) z += g.L;
-    const double r1 = sqrt(x * x + y * y);
+    const double r1 = sqrt(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
     if (r1 >= g.R) {
       const double cx = x / r1, cy = y / r1;
       const double fr = (2.0 * g.R - r1) / r1;

@@ -262,7 +262,8 @@ pic_status step_once(Sim* s, Marks* mk) {
   if ((st = launch_sort(s)) != PIC_OK) return st;
   PIC_CUDA(m.mark(2));
   if ((st = deposit_rho_with_background(s)) != PIC_OK) return st;
-  return field_step(s, -1, mk, 2);
+  PIC_CUDA(m.mark(3));
+  return field_step(s, -1, mk, 3);   // marks 4..8
 }
 
 #define CHECK_SIM(s)                                              \

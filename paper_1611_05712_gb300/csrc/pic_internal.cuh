@@ -97,7 +97,8 @@ struct DhtBatch {
   const void* X[24];
   void* Y[24];
 };
-pic_status launch_dht(Sim* s, const DhtBatch& b);
+// ncols > 0 overrides the column count 2*Nz (used for Nr x Nr products at setup).
+pic_status launch_dht(Sim* s, const DhtBatch& b, int ncols = -1);
 
 // ---- launchers (psatd.cu) ----
 pic_status launch_psatd(Sim* s);

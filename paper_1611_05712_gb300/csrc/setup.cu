@@ -255,6 +255,16 @@ __global__ void k_pinv_assemble(const double* wt_all, const double* vt_all, cons
   if (n < Nr && j < Nr) mfwd[((size_t)mat * Nr + n) * Nr + j] = acc;
 }
 
+// w[mat][i][j] = 2 delta_ij - w[mat][i][j]
+__global__ void k_two_minus(double* w, int nmat, int Nr) {
+  const size_t total = (size_t)nmat * Nr * Nr;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int j = idx % Nr, i = (idx / Nr) % Nr;
+    w[idx] = (i == j ? 2.0 : 0.0) - w[idx];
+  }
+}
+
 // [k_z]_p per FFT bin: k_z = 2 pi f/(Nz dz), f in FFT order (Nyquist negative);
 // [k_z] = sum_{j=1}^{n} alpha_{n,j} sin(k_z j dz)/(j dz), p = 2n; p = 0 -> k_z.
 // Filter factor Tz = cos^2(k_z dz/2) (exact k_z).
@@ -366,9 +376,27 @@ pic_status launch_setup_hankel(Sim* s) {
   double tol = 2e-15 * std::sqrt((double)Nr);
   k_jacobi_svd<<<Nm * 3, kSvdThreads, 0, s->stream>>>(binv, wt, vt, d, Nr, tol, err);
   PIC_LAUNCHED(s);
+  double* mfwd = s->at<double>(s->lay.mfwd);
   dim3 g(blocks_for(Nr, 32), blocks_for(Nr, 32), Nm * 3);
-  k_pinv_assemble<<<g, dim3(32, 32), 0, s->stream>>>(wt, vt, d, s->at<double>(s->lay.mfwd), Nr);
+  k_pinv_assemble<<<g, dim3(32, 32), 0, s->stream>>>(wt, vt, d, mfwd, Nr);
   PIC_LAUNCHED(s);
+  // One Newton-Schulz step M <- M (2I - B M): the Jacobi result is accurate to about
+  // tol * cond; the step squares the error on the kept subspace, while components along
+  // dropped directions (of size ~tol |M|) only double.  W and V are free again here.
+  const size_t Nr2 = (size_t)Nr * Nr;
+  DhtBatch bm{}, mt{};
+  for (int k = 0; k < Nm * 3; ++k) {
+    bm.A[k] = binv + k * Nr2; bm.X[k] = mfwd + k * Nr2; bm.Y[k] = wt + k * Nr2;
+    mt.A[k] = mfwd + k * Nr2; mt.X[k] = wt + k * Nr2; mt.Y[k] = vt + k * Nr2;
+  }
+  bm.n = mt.n = Nm * 3;
+  pic_status st = launch_dht(s, bm, Nr);               // W = B M
+  if (st != PIC_OK) return st;
+  k_two_minus<<<(int)std::min<size_t>(blocks_for(Nm * 3 * Nr2, 256), 152 * 16), 256, 0, s->stream>>>(
+      wt, Nm * 3, Nr);                                  // W = 2I - W
+  PIC_LAUNCHED(s);
+  if ((st = launch_dht(s, mt, Nr)) != PIC_OK) return st;   // V = M W
+  PIC_CUDA(cudaMemcpyAsync(mfwd, vt, Nm * 3 * Nr2 * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
   k_tr_table<<<blocks_for((size_t)Nm * Nr, 128), 128, 0, s->stream>>>(s->at<double>(s->lay.tr), kperp,
                                                                        Nm * Nr, c.dr);
   PIC_LAUNCHED(s);
