@@ -237,6 +237,30 @@ pic_status pic_sync(pic_sim* sim);
 /* Number of kernels this handle has launched so far (host-side count, for accounting). */
 pic_status pic_launch_count(pic_sim* sim, int64_t* launches);
 
+/* ---- allocation-free variant ----------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory when they need the sort: code inside another framework's step
+ * while that step is being captured into a CUDA graph (cudaMalloc is not allowed during
+ * capture), or applications that give this library a fixed memory budget at start-up
+ * and forbid allocation afterwards.  It computes exactly what pic_sort computes (cell
+ * keys iz*Nr+ir and the stable permutation), but takes the particle coordinates and the
+ * output arrays as plain device pointers and needs no pic_sim workspace.
+ *   x, y, z: device float64 [n]; keys, perm: device int32 [n] (outputs, caller-owned).
+ *   Limits: 0 <= n <= 262144 and Nz*Nr <= 65536; larger sizes return PIC_ERR_ARG with a
+ *   message.  dz, dr > 0.  stream: cudaStream_t (NULL = legacy default stream).
+ * Its scratch (2.1 MB) is a fixed __device__ array inside the library: every GPU that
+ * loads the library holds it until the process exits.  The call allocates nothing
+ * (no cudaMalloc/cudaFree, no allocating library routine).  All calls share that array
+ * and the counts are cleared at the start of each call, so calls whose kernels overlap
+ * on the GPU (different streams, or different host threads on one device) race and must
+ * be serialised by the caller.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Asynchronous on the stream; non-finite coordinates get
+ * key 0.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+pic_status pic_sort_keys_noalloc(const double* x, const double* y, const double* z, int64_t n,
+                                 int32_t Nz, int32_t Nr, double dz, double dr, int32_t* keys,
+                                 int32_t* perm, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
