@@ -5,7 +5,8 @@
 //
 // FP64 form: register-tiled SIMT GEMM (64 x 64 tile per CTA, 4 x 4 outputs per thread,
 // K staged through shared memory in steps of 16).  On GB300 the FP64 pipe, not HBM or
-// shared memory, bounds this kernel, so the tile only has to keep that pipe fed.
+// shared memory, bounds this kernel, so the tile only has to keep that pipe fed.  The same
+// kernel serves the FP64 setup products (Newton-Schulz refinement of the pseudo-inverse).
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -13,39 +14,46 @@ namespace {
 
 constexpr int BM = 64, BN = 64, BK = 16;
 
-__global__ void __launch_bounds__(256) k_dht_f64(DhtBatch bt, int Nr, int Nc) {
+template <typename R>
+__global__ void __launch_bounds__(256) k_gemm(DhtBatch bt, int Nr, int Nc) {
   const int b = blockIdx.z;
-  const double* __restrict__ A = bt.A[b];
-  const double* __restrict__ X = static_cast<const double*>(bt.X[b]);
-  double* __restrict__ Y = static_cast<double*>(bt.Y[b]);
+  const R* __restrict__ A = static_cast<const R*>(bt.A[b]);
+  const R* __restrict__ Alo = static_cast<const R*>(bt.Alo[b]);
+  const R* __restrict__ X = static_cast<const R*>(bt.X[b]);
+  R* __restrict__ Y = static_cast<R*>(bt.Y[b]);
   const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
-  __shared__ __align__(16) double As[BK][BM];
-  __shared__ __align__(16) double Xs[BK][BN];
+  __shared__ __align__(16) R As[BK][BM];
+  __shared__ __align__(16) R Xs[BK][BN];
   const int t = threadIdx.x;
   const int tx = t & 15, ty = t >> 4;
-  double acc[4][4];
+  R acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = (R)0;
 
   for (int k0 = 0; k0 < Nr; k0 += BK) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int r = t >> 2, kk = ((t & 3) << 2) + q;
       const int gr = row0 + r, gk = k0 + kk;
-      As[kk][r] = (gr < Nr && gk < Nr) ? A[(size_t)gr * Nr + gk] : 0.0;
+      R a = (R)0;
+      if (gr < Nr && gk < Nr) {
+        a = A[(size_t)gr * Nr + gk];
+        if (Alo) a += Alo[(size_t)gr * Nr + gk];
+      }
+      As[kk][r] = a;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int kk = t >> 4, cc = ((t & 15) << 2) + q;
       const int gk = k0 + kk, gc = col0 + cc;
-      Xs[kk][cc] = (gk < Nr && gc < Nc) ? X[(size_t)gk * Nc + gc] : 0.0;
+      Xs[kk][cc] = (gk < Nr && gc < Nc) ? X[(size_t)gk * Nc + gc] : (R)0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], x[4];
+      R a[4], x[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
 #pragma unroll
@@ -71,10 +79,19 @@ __global__ void __launch_bounds__(256) k_dht_f64(DhtBatch bt, int Nr, int Nc) {
 
 }  // namespace
 
-pic_status launch_dht(Sim* s, const DhtBatch& b, int ncols) {
-  const int Nr = s->cfg.Nr, Nc = ncols > 0 ? ncols : 2 * s->cfg.Nz;
+pic_status launch_gemm_f64(Sim* s, const DhtBatch& b, int ncols) {
+  const int Nr = s->cfg.Nr;
+  dim3 grid((ncols + BN - 1) / BN, (Nr + BM - 1) / BM, b.n);
+  k_gemm<double><<<grid, 256, 0, s->stream>>>(b, Nr, ncols);
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
+pic_status launch_dht(Sim* s, const DhtBatch& b) {
+  const int Nr = s->cfg.Nr, Nc = 2 * s->cfg.Nz;
+  if (s->cfg.precision == PIC_FP64) return launch_gemm_f64(s, b, Nc);
   dim3 grid((Nc + BN - 1) / BN, (Nr + BM - 1) / BM, b.n);
-  k_dht_f64<<<grid, 256, 0, s->stream>>>(b, Nr, Nc);
+  k_gemm<float><<<grid, 256, 0, s->stream>>>(b, Nr, Nc);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }

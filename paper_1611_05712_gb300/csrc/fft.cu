@@ -38,9 +38,9 @@ struct FftPlan {
 };
 
 template <typename R, bool INV>
-__device__ __forceinline__ typename Vec2<R>::T twiddle(const double2* tw, int idx) {
+__device__ __forceinline__ typename Vec2<R>::T twiddle(const typename Vec2<R>::T* tw, int idx) {
   typename Vec2<R>::T w;
-  double2 t = tw[idx];
+  const typename Vec2<R>::T t = tw[idx];
   w.x = (R)t.x;
   w.y = INV ? (R)(-t.y) : (R)t.y;
   return w;
@@ -49,7 +49,7 @@ __device__ __forceinline__ typename Vec2<R>::T twiddle(const double2* tw, int id
 template <typename R, bool INV>
 __global__ void __launch_bounds__(256) k_fft_rows(const typename Vec2<R>::T* __restrict__ in,
                                                   typename Vec2<R>::T* __restrict__ out,
-                                                  const double2* __restrict__ tw, RowCombine rc,
+                                                  const typename Vec2<R>::T* __restrict__ tw, RowCombine rc,
                                                   FftPlan plan, int rows_per_comp) {
   using C2 = typename Vec2<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -147,6 +147,7 @@ pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& 
   const int rows_per_comp = c.Nm * c.Nr;
   const int rows = rc.n_out * rows_per_comp;
   const double2* tw = s->at<double2>(s->lay.twiddle);
+  const float2* twf = s->at<float2>(s->lay.twiddle_f);
   const size_t smem = 2 * (size_t)c.Nz * s->cplx_bytes;
   if (c.precision == PIC_FP64) {
     if (inverse) {
@@ -161,11 +162,11 @@ pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& 
   } else {
     if (inverse) {
       cudaFuncSetAttribute(k_fft_rows<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_fft_rows<float, true><<<rows, 256, smem, s->stream>>>((const float2*)in, (float2*)out, tw, rc,
+      k_fft_rows<float, true><<<rows, 256, smem, s->stream>>>((const float2*)in, (float2*)out, twf, rc,
                                                               plan, rows_per_comp);
     } else {
       cudaFuncSetAttribute(k_fft_rows<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      k_fft_rows<float, false><<<rows, 256, smem, s->stream>>>((const float2*)in, (float2*)out, tw, rc,
+      k_fft_rows<float, false><<<rows, 256, smem, s->stream>>>((const float2*)in, (float2*)out, twf, rc,
                                                                plan, rows_per_comp);
     }
   }

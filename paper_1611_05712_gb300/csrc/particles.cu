@@ -401,16 +401,342 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// pass 1: sum w, w x, w y, w z, w ux, w uy, w gamma, count
-__global__ void k_diag_moments(const Parts p, int64_t np, int32_t lo, int32_t hi, double* acc) {
-  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+// ------------------------------------------------------------------ mixed form: FP32 particles
+// z is kept relative to its cell: z = (iz + fz) dz with iz an int32 cell and fz in [0, 1);
+// x, y are float metres (|x|, |y| < R), momenta are u/c (float), w is float.
+struct PartsF {
+  int32_t* iz; float* fz; float* x; float* y; float* ux; float* uy; float* uz; float* w; int32_t* id;
+};
+
+PartsF partsf_of(Sim* s, int which) {
+  PartsF p;
+  p.iz = s->at<int32_t>(s->lay.pf[which][kPfIz]);
+  p.fz = s->at<float>(s->lay.pf[which][kPfFz]);
+  p.x = s->at<float>(s->lay.pf[which][kPfX]);
+  p.y = s->at<float>(s->lay.pf[which][kPfY]);
+  p.ux = s->at<float>(s->lay.pf[which][kPfUx]);
+  p.uy = s->at<float>(s->lay.pf[which][kPfUy]);
+  p.uz = s->at<float>(s->lay.pf[which][kPfUz]);
+  p.w = s->at<float>(s->lay.pf[which][kPfW]);
+  p.id = s->at<int32_t>(s->lay.pf[which][kPfId]);
+  return p;
+}
+
+struct GeomF {
+  int Nz, Nr, Nm;
+  float inv_dr, R;
+  size_t G;
+};
+
+GeomF geomf_of(const Sim* s) {
+  const pic_config& c = s->cfg;
+  GeomF g{c.Nz, c.Nr, c.Nm, (float)(1.0 / c.dr), (float)(c.Nr * c.dr), s->grid_elems()};
+  return g;
+}
+
+struct StencilF {
+  int i0, i1, j0;
+  float wz0, wz1, wr0, wr1;
+};
+
+__device__ __forceinline__ StencilF stencil_f(const GeomF& g, int iz, float fz, float r) {
+  StencilF st;
+  st.i0 = iz;
+  st.i1 = iz + 1 == g.Nz ? 0 : iz + 1;
+  st.wz1 = fz;
+  st.wz0 = 1.f - fz;
+  const float v = r * g.inv_dr - 0.5f;
+  const float fj = floorf(v);
+  st.j0 = (int)fminf(fmaxf(fj, -1.f), (float)g.Nr);
+  st.wr1 = v - fj;
+  st.wr0 = 1.f - st.wr1;
+  return st;
+}
+
+__device__ __forceinline__ void polar_f(float x, float y, float& r, float& c, float& s) {
+  r = sqrtf(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)));
+  if (r > 0.f) { c = x / r; s = y / r; } else { c = 1.f; s = 0.f; }
+}
+
+__device__ __forceinline__ void dep_node_f(float2* grid, const GeomF& g, int j, int i, float wgt, float fold,
+                                           float vre, float vim, const float* invV) {
+  if (j < 0) { j = -1 - j; wgt *= fold; }
+  if (j >= g.Nr) return;
+  const float f = wgt * invV[j];
+  float* p = reinterpret_cast<float*>(grid + (size_t)j * g.Nz + i);
+  atomicAdd(p, vre * f);
+  atomicAdd(p + 1, vim * f);
+}
+
+__device__ __forceinline__ float2 interp_f(const float2* grid, const GeomF& g, const StencilF& st, float fold) {
+  float re = 0.f, im = 0.f;
+#pragma unroll
+  for (int dj = 0; dj < 2; ++dj) {
+    int j = st.j0 + dj;
+    float wr = dj ? st.wr1 : st.wr0;
+    if (j < 0) { j = -1 - j; wr *= fold; }
+    if (j >= g.Nr) continue;
+    const float2 a = grid[(size_t)j * g.Nz + st.i0];
+    const float2 b = grid[(size_t)j * g.Nz + st.i1];
+    re += wr * (st.wz0 * a.x + st.wz1 * b.x);
+    im += wr * (st.wz0 * a.y + st.wz1 * b.y);
+  }
+  return make_float2(re, im);
+}
+
+struct DepArgsF {
+  float2* rho;
+  float2* J;
+  float q;
+  int32_t id_lo, id_hi;
+};
+
+// deposit of one particle at (iz+fz, x, y) with velocity (vx, vy, vz) [m/s]
+__device__ void deposit_one_f(const GeomF& g, const DepArgsF& a, const float* invV, int iz, float fz, float x,
+                              float y, float w, float vx, float vy, float vz, bool do_rho, bool do_J) {
+  float r, c, s;
+  polar_f(x, y, r, c, s);
+  const StencilF st = stencil_f(g, iz, fz, r);
+  const float vr = c * vx + s * vy, vt = c * vy - s * vx;
+  float phr = 1.f, phi = 0.f;   // e^{+i m theta}
+  const size_t RZ = (size_t)g.Nr * g.Nz;
+  for (int m = 0; m < g.Nm; ++m) {
+    const float qre = a.q * w * phr, qim = a.q * w * phi;
+    const float fs = (m & 1) ? -1.f : 1.f, fv = -fs;
+#pragma unroll
+    for (int dz = 0; dz < 2; ++dz) {
+      const int i = dz ? st.i1 : st.i0;
+      const float wz = dz ? st.wz1 : st.wz0;
+#pragma unroll
+      for (int dj = 0; dj < 2; ++dj) {
+        const int j = st.j0 + dj;
+        const float wgt = wz * (dj ? st.wr1 : st.wr0);
+        if (do_rho) dep_node_f(a.rho + m * RZ, g, j, i, wgt, fs, qre, qim, invV);
+        if (do_J) {
+          dep_node_f(a.J + m * RZ, g, j, i, wgt, fv, qre * vr, qim * vr, invV);
+          dep_node_f(a.J + g.G + m * RZ, g, j, i, wgt, fv, qre * vt, qim * vt, invV);
+          dep_node_f(a.J + 2 * g.G + m * RZ, g, j, i, wgt, fs, qre * vz, qim * vz, invV);
+        }
+      }
+    }
+    const float nr = phr * c - phi * s, ni = phr * s + phi * c;
+    phr = nr; phi = ni;
+  }
+}
+
+__global__ void k_inv_volume_f(float* invV, int Nr, double dr, double dz) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < Nr) invV[j] = (float)(1.0 / (2.0 * kPi * ((j + 0.5) * dr) * dr * dz));
+}
+
+__global__ void k_keys_f32(const PartsF p, int64_t np, GeomF g, int32_t* keys, int32_t* count, int32_t* err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float x = p.x[i], y = p.y[i];
+    const float r = sqrtf(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)));
+    float fr = floorf(r * g.inv_dr);
+    int iz = p.iz[i];
+    if (!(fr == fr) || isinf(fr) || iz < 0 || iz >= g.Nz) {
+      atomicOr(err, kErrNumeric);
+      fr = 0.f;
+      iz = 0;
+    }
+    const int ir = (int)fminf(fmaxf(fr, 0.f), (float)(g.Nr - 1));
+    const int key = iz * g.Nr + ir;
+    keys[i] = key;
+    atomicAdd(count + key, 1);
+  }
+}
+
+__global__ void k_permute_f32(const PartsF src, PartsF dst, const int32_t* perm, int64_t np) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t k = perm[i];
+    dst.iz[i] = src.iz[k]; dst.fz[i] = src.fz[k]; dst.x[i] = src.x[k]; dst.y[i] = src.y[k];
+    dst.ux[i] = src.ux[k]; dst.uy[i] = src.uy[k]; dst.uz[i] = src.uz[k]; dst.w[i] = src.w[k];
+    dst.id[i] = src.id[k];
+  }
+}
+
+__global__ void k_deposit_f32(const PartsF p, int64_t np, GeomF g, DepArgsF a, const float* invV, int32_t* err) {
+  const bool do_rho = a.rho != nullptr, do_J = a.J != nullptr;
+  const float c = (float)kC;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t id = p.id[i];
+    if (id < a.id_lo || id >= a.id_hi) continue;
+    const float x = p.x[i], y = p.y[i], fz = p.fz[i];
+    const int iz = p.iz[i];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(fz) || iz < 0 || iz >= g.Nz) {
+      atomicOr(err, kErrNumeric);
+      continue;
+    }
+    float vx = 0.f, vy = 0.f, vz = 0.f;
+    if (do_J) {
+      const float ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
+      const float ig = c * rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
+      vx = ux * ig; vy = uy * ig; vz = uz * ig;
+    }
+    deposit_one_f(g, a, invV, iz, fz, x, y, p.w[i], vx, vy, vz, do_rho, do_J);
+  }
+}
+
+// Advance (iz, fz) by dfz cells, periodic in iz.
+__device__ __forceinline__ void advance_z(int& iz, float& fz, float dfz, int Nz) {
+  fz += dfz;
+  const float k = floorf(fz);
+  fz -= k;
+  if (fz >= 1.f) { fz -= 1.f; iz += 1; }   // rounding of fz - k up to 1
+  iz += (int)k;
+  iz %= Nz;
+  if (iz < 0) iz += Nz;
+}
+
+// a2 + a3 (+ a4 J at x^{n+1/2}) in float: gather with mode sum, Boris push of u/c, two half
+// moves (z in cell units), specular reflection at r >= R.
+__global__ void k_gather_push_f32(PartsF p, int64_t np, GeomF g, const float2* __restrict__ E,
+                                  const float2* __restrict__ B, float kq, float kqc, float chdt,
+                                  float chdt_dz, DepArgsF dep, const float* invV, int fuse, int32_t* err) {
+  const size_t RZ = (size_t)g.Nr * g.Nz;
+  const float c_light = (float)kC;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float x = p.x[i], y = p.y[i], fz = p.fz[i];
+    int iz = p.iz[i];
+    if (!isfinite(x) || !isfinite(y) || !isfinite(fz) || iz < 0 || iz >= g.Nz) {
+      atomicOr(err, kErrNumeric);
+      continue;
+    }
+    float ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
+    const float w = p.w[i];
+    float r, c, s;
+    polar_f(x, y, r, c, s);
+    const StencilF st = stencil_f(g, iz, fz, r);
+    float F[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float phr = 1.f, phi = 0.f;   // e^{-i m theta}
+    for (int m = 0; m < g.Nm; ++m) {
+      const float fs = (m & 1) ? -1.f : 1.f, fv = -fs;
+      const float mult = m == 0 ? 1.f : 2.f;
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        const float2* base = (k < 3 ? E : B) + (size_t)(k % 3) * g.G + m * RZ;
+        const float2 v = interp_f(base, g, st, (k % 3) == 2 ? fs : fv);
+        F[k] += mult * (v.x * phr - v.y * phi);
+      }
+      const float nr = phr * c + phi * s, ni = phi * c - phr * s;
+      phr = nr; phi = ni;
+    }
+    const float Ex = F[0] * c - F[1] * s, Ey = F[0] * s + F[1] * c, Ez = F[2];
+    const float Bx = F[3] * c - F[4] * s, By = F[3] * s + F[4] * c, Bz = F[5];
+    // Boris on u/c: u- = u + kq E, t = kqc B / gamma-, kq = q dt/(2 m c), kqc = q dt/(2 m)
+    const float umx = ux + kq * Ex, umy = uy + kq * Ey, umz = uz + kq * Ez;
+    const float igm = rsqrtf(1.f + umx * umx + umy * umy + umz * umz);
+    const float tx = kqc * Bx * igm, ty = kqc * By * igm, tz = kqc * Bz * igm;
+    const float upx = umx + (umy * tz - umz * ty);
+    const float upy = umy + (umz * tx - umx * tz);
+    const float upz = umz + (umx * ty - umy * tx);
+    const float f = 2.f / (1.f + tx * tx + ty * ty + tz * tz);
+    const float sx = f * tx, sy = f * ty, sz = f * tz;
+    ux = umx + (upy * sz - upz * sy) + kq * Ex;
+    uy = umy + (upz * sx - upx * sz) + kq * Ey;
+    uz = umz + (upx * sy - upy * sx) + kq * Ez;
+    const float ig = rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
+    const float bx = ux * ig, by = uy * ig, bz = uz * ig;   // v / c
+    x += bx * chdt;
+    y += by * chdt;
+    advance_z(iz, fz, bz * chdt_dz, g.Nz);
+    if (fuse) deposit_one_f(g, dep, invV, iz, fz, x, y, w, bx * c_light, by * c_light, bz * c_light, false, true);
+    x += bx * chdt;
+    y += by * chdt;
+    advance_z(iz, fz, bz * chdt_dz, g.Nz);
+    const float r1 = sqrtf(x * x + y * y);
+    if (r1 >= g.R) {
+      const float cx = x / r1, cy = y / r1;
+      const float fr = (2.f * g.R - r1) / r1;
+      const float ur = ux * cx + uy * cy;
+      ux -= 2.f * ur * cx;
+      uy -= 2.f * ur * cy;
+      x *= fr;
+      y *= fr;
+    }
+    p.x[i] = x; p.y[i] = y; p.fz[i] = fz; p.iz[i] = iz;
+    p.ux[i] = ux; p.uy[i] = uy; p.uz[i] = uz;
+  }
+}
+
+// float64 SoA (x y z ux uy uz w) <-> FP32 cell-relative particles
+__global__ void k_p64_to_p32(const double* __restrict__ st, int64_t cap, const int32_t* __restrict__ id_in,
+                             PartsF p, int64_t np, int Nz, double dz) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double z = st[2 * cap + i];
+    const double u = z / dz;
+    double fl = floor(u);
+    float fz = (float)(u - fl);
+    long long izl = (long long)fl;
+    if (fz >= 1.f) { fz = 0.f; izl += 1; }
+    izl %= Nz;
+    if (izl < 0) izl += Nz;
+    p.iz[i] = (int32_t)izl;
+    p.fz[i] = fz;
+    p.x[i] = (float)st[i];
+    p.y[i] = (float)st[cap + i];
+    p.ux[i] = (float)(st[3 * cap + i] / kC);
+    p.uy[i] = (float)(st[4 * cap + i] / kC);
+    p.uz[i] = (float)(st[5 * cap + i] / kC);
+    p.w[i] = (float)st[6 * cap + i];
+    p.id[i] = id_in[i];
+  }
+}
+
+__global__ void k_p32_to_p64(const PartsF p, int64_t np, double* __restrict__ st, int64_t cap,
+                             int32_t* __restrict__ id_out, double dz) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    st[i] = p.x[i];
+    st[cap + i] = p.y[i];
+    st[2 * cap + i] = ((double)p.iz[i] + (double)p.fz[i]) * dz;
+    st[3 * cap + i] = (double)p.ux[i] * kC;
+    st[4 * cap + i] = (double)p.uy[i] * kC;
+    st[5 * cap + i] = (double)p.uz[i] * kC;
+    st[6 * cap + i] = p.w[i];
+    if (id_out) id_out[i] = p.id[i];
+  }
+}
+
+// ------------------------------------------------------------------ a10: diagnostics
+// Particle accessors: float64 particles as stored, or FP32 particles widened to float64.
+struct Acc64 {
+  Parts p;
+  __device__ void get(int64_t i, double& x, double& y, double& z, double& ux, double& uy, double& uz,
+                      double& w) const {
+    x = p.x[i]; y = p.y[i]; z = p.z[i]; ux = p.ux[i]; uy = p.uy[i]; uz = p.uz[i]; w = p.w[i];
+  }
+  __device__ int32_t id(int64_t i) const { return p.id[i]; }
+};
+struct Acc32 {
+  PartsF p;
+  double dz;
+  __device__ void get(int64_t i, double& x, double& y, double& z, double& ux, double& uy, double& uz,
+                      double& w) const {
+    x = p.x[i]; y = p.y[i]; z = ((double)p.iz[i] + (double)p.fz[i]) * dz;
+    ux = (double)p.ux[i] * kC; uy = (double)p.uy[i] * kC; uz = (double)p.uz[i] * kC; w = p.w[i];
+  }
+  __device__ int32_t id(int64_t i) const { return p.id[i]; }
+};
+
+// pass 1: sum w, w x, w y, w z, w ux, w uy, w gamma, count
+template <class A>
+__global__ void k_diag_moments(const A a, int64_t np, int32_t lo, int32_t hi, double* acc) {
+  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t id = a.id(i);
     if (id < lo || id >= hi) continue;
-    const double w = p.w[i], ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
+    double x, y, z, ux, uy, uz, w;
+    a.get(i, x, y, z, ux, uy, uz, w);
     const double gam = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
-    v[0] += w; v[1] += w * p.x[i]; v[2] += w * p.y[i]; v[3] += w * p.z[i];
+    v[0] += w; v[1] += w * x; v[2] += w * y; v[3] += w * z;
     v[4] += w * ux; v[5] += w * uy; v[6] += w * gam; v[7] += 1.0;
   }
   for (int k = 0; k < 8; ++k) {
@@ -420,16 +746,17 @@ __global__ void k_diag_moments(const Parts p, int64_t np, int32_t lo, int32_t hi
 }
 
 // pass 2: centred second moments w dx^2, w dux^2, w dx dux, (y), w dz^2
-__global__ void k_diag_central(const Parts p, int64_t np, int32_t lo, int32_t hi, const double* mean,
-                               double* acc) {
+template <class A>
+__global__ void k_diag_central(const A a, int64_t np, int32_t lo, int32_t hi, const double* mean, double* acc) {
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t id = p.id[i];
+    const int32_t id = a.id(i);
     if (id < lo || id >= hi) continue;
-    const double w = p.w[i];
-    const double dx = p.x[i] - mean[0], dy = p.y[i] - mean[1], dz = p.z[i] - mean[2];
-    const double dux = p.ux[i] - mean[3], duy = p.uy[i] - mean[4];
+    double x, y, z, ux, uy, uz, w;
+    a.get(i, x, y, z, ux, uy, uz, w);
+    const double dx = x - mean[0], dy = y - mean[1], dz = z - mean[2];
+    const double dux = ux - mean[3], duy = uy - mean[4];
     v[0] += w * (dx * dx); v[1] += w * (dux * dux); v[2] += w * (dx * dux);
     v[3] += w * (dy * dy); v[4] += w * (duy * duy); v[5] += w * (dy * duy);
     v[6] += w * (dz * dz);
@@ -441,18 +768,19 @@ __global__ void k_diag_central(const Parts p, int64_t np, int32_t lo, int32_t hi
 }
 
 // pass 3 (stage 0): per-slice sum w and sum w gamma; (stage 1): sum w (gamma - gbar_s)^2
-__global__ void k_diag_slices(const Parts p, int64_t np, int32_t lo, int32_t hi, double zstart,
-                              double zspan, double slen, int ns, double* sw, double* sg, double* sv,
-                              int stage) {
+template <class A>
+__global__ void k_diag_slices(const A a, int64_t np, int32_t lo, int32_t hi, double zstart, double zspan,
+                              double slen, int ns, double* sw, double* sg, double* sv, int stage) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t id = p.id[i];
+    const int32_t id = a.id(i);
     if (id < lo || id >= hi) continue;
-    const double d = p.z[i] - zstart;
+    double x, y, z, ux, uy, uz, w;
+    a.get(i, x, y, z, ux, uy, uz, w);
+    const double d = z - zstart;
     if (!(d >= 0.0 && d < zspan)) continue;
     int k = (int)floor(d / slen);
     if (k > ns - 1) k = ns - 1;
-    const double w = p.w[i], ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
     const double gam = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
     if (stage == 0) {
       atomicAdd(sw + k, w);
@@ -470,107 +798,18 @@ inline int pgrid(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
-}  // namespace
-
-pic_status launch_sort(Sim* s) {
-  const GridGeom g = geom_of(s);
-  const int64_t np = s->np;
-  const int ncell = g.Nz * g.Nr;
-  int32_t* keys = s->at<int32_t>(s->lay.keys);
-  int32_t* count = s->at<int32_t>(s->lay.count);
-  int32_t* start = s->at<int32_t>(s->lay.start);
-  int32_t* blk = s->at<int32_t>(s->lay.scan_blk);
-  int32_t* tmp = s->at<int32_t>(s->lay.perm_tmp);
-  int32_t* perm = s->at<int32_t>(s->lay.perm);
-  int32_t* big_list = s->at<int32_t>(s->lay.big_list);
-  int32_t* big_count = s->at<int32_t>(s->lay.big_count);
-  int32_t* err = s->at<int32_t>(s->lay.err);
-  int32_t* cursor = reinterpret_cast<int32_t*>(s->at<char>(s->lay.scan_blk) + 4 * 4096 * sizeof(int32_t));
-  PIC_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * (ncell + 1), s->stream));
-  PIC_CUDA(cudaMemsetAsync(big_count, 0, sizeof(int32_t), s->stream));
-  if (np == 0) return PIC_OK;
-  Parts src = parts_of(s, s->cur), dst = parts_of(s, 1 - s->cur);
-  k_keys<<<pgrid(np), 256, 0, s->stream>>>(src, np, g, keys, count, err);
-  PIC_LAUNCHED(s);
-  const int nblk = (ncell + kScanBlock - 1) / kScanBlock;
-  k_scan_local<<<nblk, kScanThreads, 0, s->stream>>>(count, start, blk, ncell);
-  PIC_LAUNCHED(s);
-  k_scan_blocks<<<1, kScanThreads, 0, s->stream>>>(blk, nblk, start, ncell);
-  PIC_LAUNCHED(s);
-  k_scan_add<<<pgrid(ncell), 256, 0, s->stream>>>(start, blk, ncell, cursor);
-  PIC_LAUNCHED(s);
-  k_scatter<<<pgrid(np), 256, 0, s->stream>>>(keys, np, cursor, tmp);
-  PIC_LAUNCHED(s);
-  k_cell_sort_small<<<pgrid(ncell), 256, 0, s->stream>>>(start, tmp, perm, ncell, big_list, big_count);
-  PIC_LAUNCHED(s);
-  k_cell_sort_big<<<152 * 4, 256, 0, s->stream>>>(start, tmp, perm, big_list, big_count);
-  PIC_LAUNCHED(s);
-  k_permute<<<pgrid(np), 256, 0, s->stream>>>(src, dst, perm, np);
-  PIC_LAUNCHED(s);
-  s->cur = 1 - s->cur;
-  return PIC_OK;
-}
-
-static pic_status ensure_inv_volume(Sim* s, double** invV) {
-  // the inverse ring volumes live at the tail of the diagnostics accumulator block
-  *invV = s->at<double>(s->lay.diag_acc) + 64 + 3 * (size_t)kMaxSlices;
-  k_inv_volume<<<(s->cfg.Nr + 127) / 128, 128, 0, s->stream>>>(*invV, s->cfg.Nr, s->cfg.dr, s->cfg.dz);
-  PIC_LAUNCHED(s);
-  return PIC_OK;
-}
-
-pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, void* rho_out) {
-  const GridGeom g = geom_of(s);
-  double* invV;
-  pic_status st = ensure_inv_volume(s, &invV);
-  if (st != PIC_OK) return st;
-  DepArgs a;
-  a.q = s->cfg.q;
-  a.id_lo = id_lo;
-  a.id_hi = id_hi;
-  a.rho = (what & PIC_DEP_RHO) ? (rho_out ? (double2*)rho_out : s->at<double2>(s->lay.dep)) : nullptr;
-  a.J = (what & PIC_DEP_J) ? s->at<double2>(s->lay.dep) + g.G : nullptr;
-  if (a.J) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * g.G * sizeof(double2), s->stream));
-  if (s->np == 0) return PIC_OK;
-  k_deposit<<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, g, a, invV,
-                                                  s->at<int32_t>(s->lay.err));
-  PIC_LAUNCHED(s);
-  return PIC_OK;
-}
-
-pic_status launch_gather_push(Sim* s, int32_t fuse_current) {
-  const GridGeom g = geom_of(s);
-  double* invV;
-  pic_status st = ensure_inv_volume(s, &invV);
-  if (st != PIC_OK) return st;
-  DepArgs a;
-  a.q = s->cfg.q;
-  a.id_lo = INT32_MIN;
-  a.id_hi = INT32_MAX;
-  a.rho = nullptr;
-  a.J = s->at<double2>(s->lay.dep) + g.G;
-  if (fuse_current) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * g.G * sizeof(double2), s->stream));
-  if (s->np == 0) return PIC_OK;
-  k_gather_push<<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, g,
-                                                      s->at<double2>(s->lay.E), s->at<double2>(s->lay.B),
-                                                      s->cfg.q, s->cfg.mass, s->cfg.dt, a, invV,
-                                                      fuse_current, s->at<int32_t>(s->lay.err));
-  PIC_LAUNCHED(s);
-  return PIC_OK;
-}
-
-pic_status launch_diag(Sim* s, int32_t lo, int32_t hi, pic_diag* out, double* slice_sigma,
-                       int32_t max_slices) {
+template <class A>
+pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* out, double* slice_sigma,
+                    int32_t max_slices) {
   const int64_t np = s->np;
   double* acc = s->at<double>(s->lay.diag_acc);
   double* sw = acc + 64;
   double* sg = sw + kMaxSlices;
   double* sv = sg + kMaxSlices;
-  Parts p = parts_of(s, s->cur);
   PIC_CUDA(cudaMemsetAsync(acc, 0, 64 * sizeof(double), s->stream));
-  int grid = pgrid(np);
+  const int grid = pgrid(np);
   if (np > 0) {
-    k_diag_moments<<<grid, kDiagThreads, 0, s->stream>>>(p, np, lo, hi, acc);
+    k_diag_moments<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, acc);
     PIC_LAUNCHED(s);
   }
   double h[8];
@@ -585,7 +824,7 @@ pic_status launch_diag(Sim* s, int32_t lo, int32_t hi, pic_diag* out, double* sl
   out->gamma_mean = h[6] / h[0];
   double* dmean = acc + 16;
   PIC_CUDA(cudaMemcpyAsync(dmean, mean, sizeof(mean), cudaMemcpyHostToDevice, s->stream));
-  k_diag_central<<<grid, kDiagThreads, 0, s->stream>>>(p, np, lo, hi, dmean, acc + 32);
+  k_diag_central<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, dmean, acc + 32);
   PIC_LAUNCHED(s);
   double c2[7];
   PIC_CUDA(cudaMemcpyAsync(c2, acc + 32, sizeof(c2), cudaMemcpyDeviceToHost, s->stream));
@@ -607,11 +846,11 @@ pic_status launch_diag(Sim* s, int32_t lo, int32_t hi, pic_diag* out, double* sl
   const int ns = (int)ns_d;
   const double zstart = mean[2] - 3.0 * sz;
   PIC_CUDA(cudaMemsetAsync(sw, 0, 3 * sizeof(double) * kMaxSlices, s->stream));
-  k_diag_slices<<<grid, kDiagThreads, 0, s->stream>>>(p, np, lo, hi, zstart, span, kSliceLen, ns, sw, sg,
-                                                       sv, 0);
+  k_diag_slices<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, zstart, span, kSliceLen, ns, sw,
+                                                          sg, sv, 0);
   PIC_LAUNCHED(s);
-  k_diag_slices<<<grid, kDiagThreads, 0, s->stream>>>(p, np, lo, hi, zstart, span, kSliceLen, ns, sw, sg,
-                                                       sv, 1);
+  k_diag_slices<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, zstart, span, kSliceLen, ns, sw,
+                                                          sg, sv, 1);
   PIC_LAUNCHED(s);
   std::vector<double> hw(ns), hv(ns);
   PIC_CUDA(cudaMemcpyAsync(hw.data(), sw, ns * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -629,6 +868,160 @@ pic_status launch_diag(Sim* s, int32_t lo, int32_t hi, pic_diag* out, double* sl
   }
   out->n_slices = ne;
   out->sigma_gamma_mean = ne ? sum / ne : 0.0;
+  return PIC_OK;
+}
+
+}  // namespace
+
+bool is_mixed(const Sim* s) { return s->cfg.precision != PIC_FP64; }
+
+pic_status launch_sort(Sim* s) {
+  const int64_t np = s->np;
+  const int ncell = s->cfg.Nz * s->cfg.Nr;
+  int32_t* keys = s->at<int32_t>(s->lay.keys);
+  int32_t* count = s->at<int32_t>(s->lay.count);
+  int32_t* start = s->at<int32_t>(s->lay.start);
+  int32_t* blk = s->at<int32_t>(s->lay.scan_blk);
+  int32_t* tmp = s->at<int32_t>(s->lay.perm_tmp);
+  int32_t* perm = s->at<int32_t>(s->lay.perm);
+  int32_t* big_list = s->at<int32_t>(s->lay.big_list);
+  int32_t* big_count = s->at<int32_t>(s->lay.big_count);
+  int32_t* err = s->at<int32_t>(s->lay.err);
+  int32_t* cursor = reinterpret_cast<int32_t*>(s->at<char>(s->lay.scan_blk) + 4 * 4096 * sizeof(int32_t));
+  PIC_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * (ncell + 1), s->stream));
+  PIC_CUDA(cudaMemsetAsync(big_count, 0, sizeof(int32_t), s->stream));
+  if (np == 0) return PIC_OK;
+  if (is_mixed(s))
+    k_keys_f32<<<pgrid(np), 256, 0, s->stream>>>(partsf_of(s, s->cur), np, geomf_of(s), keys, count, err);
+  else
+    k_keys<<<pgrid(np), 256, 0, s->stream>>>(parts_of(s, s->cur), np, geom_of(s), keys, count, err);
+  PIC_LAUNCHED(s);
+  const int nblk = (ncell + kScanBlock - 1) / kScanBlock;
+  k_scan_local<<<nblk, kScanThreads, 0, s->stream>>>(count, start, blk, ncell);
+  PIC_LAUNCHED(s);
+  k_scan_blocks<<<1, kScanThreads, 0, s->stream>>>(blk, nblk, start, ncell);
+  PIC_LAUNCHED(s);
+  k_scan_add<<<pgrid(ncell), 256, 0, s->stream>>>(start, blk, ncell, cursor);
+  PIC_LAUNCHED(s);
+  k_scatter<<<pgrid(np), 256, 0, s->stream>>>(keys, np, cursor, tmp);
+  PIC_LAUNCHED(s);
+  k_cell_sort_small<<<pgrid(ncell), 256, 0, s->stream>>>(start, tmp, perm, ncell, big_list, big_count);
+  PIC_LAUNCHED(s);
+  k_cell_sort_big<<<152 * 4, 256, 0, s->stream>>>(start, tmp, perm, big_list, big_count);
+  PIC_LAUNCHED(s);
+  if (is_mixed(s))
+    k_permute_f32<<<pgrid(np), 256, 0, s->stream>>>(partsf_of(s, s->cur), partsf_of(s, 1 - s->cur), perm, np);
+  else
+    k_permute<<<pgrid(np), 256, 0, s->stream>>>(parts_of(s, s->cur), parts_of(s, 1 - s->cur), perm, np);
+  PIC_LAUNCHED(s);
+  s->cur = 1 - s->cur;
+  return PIC_OK;
+}
+
+// Inverse ring volumes 1/(2 pi r_j dr dz), at the tail of the diagnostics block, built once.
+pic_status build_inv_volume(Sim* s) {
+  double* base = s->at<double>(s->lay.diag_acc) + 64 + 3 * (size_t)kMaxSlices;
+  if (is_mixed(s))
+    k_inv_volume_f<<<(s->cfg.Nr + 127) / 128, 128, 0, s->stream>>>(reinterpret_cast<float*>(base), s->cfg.Nr,
+                                                                    s->cfg.dr, s->cfg.dz);
+  else
+    k_inv_volume<<<(s->cfg.Nr + 127) / 128, 128, 0, s->stream>>>(base, s->cfg.Nr, s->cfg.dr, s->cfg.dz);
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
+static double* inv_volume(Sim* s) { return s->at<double>(s->lay.diag_acc) + 64 + 3 * (size_t)kMaxSlices; }
+
+pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, void* rho_out) {
+  const size_t G = s->grid_elems();
+  int32_t* err = s->at<int32_t>(s->lay.err);
+  if (is_mixed(s)) {
+    DepArgsF a;
+    a.q = (float)s->cfg.q;
+    a.id_lo = id_lo;
+    a.id_hi = id_hi;
+    a.rho = (what & PIC_DEP_RHO) ? (rho_out ? (float2*)rho_out : s->at<float2>(s->lay.dep)) : nullptr;
+    a.J = (what & PIC_DEP_J) ? s->at<float2>(s->lay.dep) + G : nullptr;
+    if (a.J) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * G * sizeof(float2), s->stream));
+    if (s->np == 0) return PIC_OK;
+    k_deposit_f32<<<pgrid(s->np), 256, 0, s->stream>>>(partsf_of(s, s->cur), s->np, geomf_of(s), a,
+                                                       reinterpret_cast<const float*>(inv_volume(s)), err);
+  } else {
+    DepArgs a;
+    a.q = s->cfg.q;
+    a.id_lo = id_lo;
+    a.id_hi = id_hi;
+    a.rho = (what & PIC_DEP_RHO) ? (rho_out ? (double2*)rho_out : s->at<double2>(s->lay.dep)) : nullptr;
+    a.J = (what & PIC_DEP_J) ? s->at<double2>(s->lay.dep) + G : nullptr;
+    if (a.J) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * G * sizeof(double2), s->stream));
+    if (s->np == 0) return PIC_OK;
+    k_deposit<<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, geom_of(s), a, inv_volume(s), err);
+  }
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
+pic_status launch_gather_push(Sim* s, int32_t fuse_current) {
+  const size_t G = s->grid_elems();
+  int32_t* err = s->at<int32_t>(s->lay.err);
+  const pic_config& c = s->cfg;
+  if (is_mixed(s)) {
+    DepArgsF a;
+    a.q = (float)c.q;
+    a.id_lo = INT32_MIN;
+    a.id_hi = INT32_MAX;
+    a.rho = nullptr;
+    a.J = s->at<float2>(s->lay.dep) + G;
+    if (fuse_current) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * G * sizeof(float2), s->stream));
+    if (s->np == 0) return PIC_OK;
+    const float kq = (float)(c.q * c.dt / (2.0 * c.mass * kC));
+    const float kqc = (float)(c.q * c.dt / (2.0 * c.mass));
+    const float chdt = (float)(0.5 * kC * c.dt);
+    const float chdt_dz = (float)(0.5 * kC * c.dt / c.dz);
+    k_gather_push_f32<<<pgrid(s->np), 256, 0, s->stream>>>(
+        partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.E), s->at<float2>(s->lay.B), kq, kqc, chdt,
+        chdt_dz, a, reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err);
+  } else {
+    DepArgs a;
+    a.q = c.q;
+    a.id_lo = INT32_MIN;
+    a.id_hi = INT32_MAX;
+    a.rho = nullptr;
+    a.J = s->at<double2>(s->lay.dep) + G;
+    if (fuse_current) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * G * sizeof(double2), s->stream));
+    if (s->np == 0) return PIC_OK;
+    k_gather_push<<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, geom_of(s),
+                                                        s->at<double2>(s->lay.E), s->at<double2>(s->lay.B), c.q,
+                                                        c.mass, c.dt, a, inv_volume(s), fuse_current, err);
+  }
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
+pic_status launch_diag(Sim* s, int32_t lo, int32_t hi, pic_diag* out, double* slice_sigma, int32_t max_slices) {
+  if (is_mixed(s)) {
+    Acc32 a{partsf_of(s, s->cur), s->cfg.dz};
+    return run_diag(s, a, lo, hi, out, slice_sigma, max_slices);
+  }
+  Acc64 a{parts_of(s, s->cur)};
+  return run_diag(s, a, lo, hi, out, slice_sigma, max_slices);
+}
+
+// Mixed form: float64 SoA in the staging area -> FP32 particles of the current buffer.
+pic_status launch_particles_in(Sim* s, const int32_t* id_dev, int64_t n) {
+  if (n == 0) return PIC_OK;
+  k_p64_to_p32<<<pgrid(n), 256, 0, s->stream>>>(s->at<double>(s->lay.stage64), s->cfg.np_capacity, id_dev,
+                                                 partsf_of(s, s->cur), n, s->cfg.Nz, s->cfg.dz);
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
+// Mixed form: FP32 particles -> float64 SoA in the staging area (ids to id_dev if given).
+pic_status launch_particles_out(Sim* s, int32_t* id_dev, int64_t n) {
+  if (n == 0) return PIC_OK;
+  k_p32_to_p64<<<pgrid(n), 256, 0, s->stream>>>(partsf_of(s, s->cur), n, s->at<double>(s->lay.stage64),
+                                                 s->cfg.np_capacity, id_dev, s->cfg.dz);
+  PIC_LAUNCHED(s);
   return PIC_OK;
 }
 

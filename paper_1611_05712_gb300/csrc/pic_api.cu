@@ -38,11 +38,11 @@ namespace {
 
 pic_status validate(const pic_config* c, int32_t* radix, int32_t* n_pass) {
   if (!c) { set_error("config is NULL"); return PIC_ERR_ARG; }
-  if (c->precision != PIC_FP64) {
-    set_error("precision %d is not available in this build", c->precision);
+  if (c->precision != PIC_FP64 && c->precision != PIC_MIXED_TF32X3) {
+    set_error("precision %d is not a pic_precision", c->precision);
     return PIC_ERR_ARG;
   }
-  const int max_nz = 4096;
+  const int max_nz = c->precision == PIC_FP64 ? 4096 : 8192;   // two shared-memory rows per FFT CTA
   if (c->Nz < 8 || c->Nz > max_nz || !plan_radix(c->Nz, radix, n_pass)) {
     set_error("Nz=%d must be a 7-smooth integer in [8, %d]", c->Nz, max_nz);
     return PIC_ERR_ARG;
@@ -70,7 +70,8 @@ Layout make_layout(const pic_config& c) {
     off += (bytes + 255) & ~(size_t)255;
     return o;
   };
-  const size_t cb = 16;   // complex float64
+  const bool mixed = c.precision != PIC_FP64;
+  const size_t cb = mixed ? 8 : 16;   // complex float64 or complex float
   const size_t G = (size_t)c.Nm * c.Nr * c.Nz;
   const size_t Nr2 = (size_t)c.Nr * c.Nr;
   const size_t cap = (size_t)std::max<int64_t>(c.np_capacity, 1);
@@ -95,9 +96,25 @@ Layout make_layout(const pic_config& c) {
   L.tr = take((size_t)c.Nm * c.Nr * 8);
   L.coef = take(6 * G * 8);
   L.twiddle = take((size_t)c.Nz * 16);
-  for (int b = 0; b < 2; ++b) {
-    for (int k = 0; k < 7; ++k) L.part[b][k] = take(cap * 8);
-    L.pid[b] = take(cap * 4);
+  if (mixed) {
+    for (int b = 0; b < 2; ++b)
+      for (int k = 0; k < 9; ++k) L.pf[b][k] = take(cap * 4);
+    L.stage64 = take(7 * cap * 8);
+    L.coef_f = take(6 * G * 4);
+    L.kperp_f = take((size_t)c.Nm * c.Nr * 4);
+    L.kzmod_f = take((size_t)c.Nz * 4);
+    L.tz_f = take((size_t)c.Nz * 4);
+    L.tr_f = take((size_t)c.Nm * c.Nr * 4);
+    L.twiddle_f = take((size_t)c.Nz * 8);
+    L.mfwd_hi = take((size_t)c.Nm * 3 * Nr2 * 4);
+    L.mfwd_lo = take((size_t)c.Nm * 3 * Nr2 * 4);
+    L.binv_hi = take((size_t)c.Nm * 3 * Nr2 * 4);
+    L.binv_lo = take((size_t)c.Nm * 3 * Nr2 * 4);
+  } else {
+    for (int b = 0; b < 2; ++b) {
+      for (int k = 0; k < 7; ++k) L.part[b][k] = take(cap * 8);
+      L.pid[b] = take(cap * 4);
+    }
   }
   L.keys = take(cap * 4);
   L.perm = take(cap * 4);
@@ -163,7 +180,13 @@ pic_status dht_forward(Sim* s, int n_comp) {
   const size_t Nr2 = (size_t)c.Nr * c.Nr;
   for (int comp = 0; comp < n_comp; ++comp)
     for (int m = 0; m < c.Nm; ++m) {
-      b.A[b.n] = s->at<double>(s->lay.mfwd) + ((size_t)m * 3 + slot_of[comp]) * Nr2;
+      const size_t moff = ((size_t)m * 3 + slot_of[comp]) * Nr2;
+      if (s->cfg.precision == PIC_FP64) {
+        b.A[b.n] = s->at<double>(s->lay.mfwd) + moff;
+      } else {
+        b.A[b.n] = s->at<float>(s->lay.mfwd_hi) + moff;
+        b.Alo[b.n] = s->at<float>(s->lay.mfwd_lo) + moff;
+      }
       b.X[b.n] = s->at<char>(s->lay.tmp) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       b.Y[b.n] = s->at<char>(s->lay.srch) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       ++b.n;
@@ -186,7 +209,13 @@ pic_status dht_inverse(Sim* s) {
   DhtBatch b{};
   for (int comp = 0; comp < 6; ++comp)
     for (int m = 0; m < c.Nm; ++m) {
-      b.A[b.n] = s->at<double>(s->lay.binv) + ((size_t)m * 3 + slot_of[comp % 3]) * Nr2;
+      const size_t moff = ((size_t)m * 3 + slot_of[comp % 3]) * Nr2;
+      if (s->cfg.precision == PIC_FP64) {
+        b.A[b.n] = s->at<double>(s->lay.binv) + moff;
+      } else {
+        b.A[b.n] = s->at<float>(s->lay.binv_hi) + moff;
+        b.Alo[b.n] = s->at<float>(s->lay.binv_lo) + moff;
+      }
       b.X[b.n] = s->at<char>(s->lay.Eh) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       b.Y[b.n] = s->at<char>(s->lay.tmp) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       ++b.n;
@@ -315,19 +344,21 @@ pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_byt
   s->order_tables = -1;
   s->np = 0;
   s->cur = 0;
-  s->cplx_bytes = 16;
+  s->cplx_bytes = cfg->precision == PIC_FP64 ? 16 : 8;
   const size_t G = s->grid_elems();
+  const size_t cb = s->cplx_bytes;
   auto fail = [&](pic_status e) { delete s; return e; };
   cudaError_t ce;
-  if ((ce = cudaMemsetAsync(s->ws + L.E, 0, 6 * G * 16, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
-  if ((ce = cudaMemsetAsync(s->ws + L.Eh, 0, 6 * G * 16, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
-  if ((ce = cudaMemsetAsync(s->ws + L.rho_prev_h, 0, G * 16, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
-  if ((ce = cudaMemsetAsync(s->ws + L.rho_ion, 0, G * 16, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
-  if ((ce = cudaMemsetAsync(s->ws + L.dep, 0, 4 * G * 16, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if ((ce = cudaMemsetAsync(s->ws + L.E, 0, 6 * G * cb, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if ((ce = cudaMemsetAsync(s->ws + L.Eh, 0, 6 * G * cb, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if ((ce = cudaMemsetAsync(s->ws + L.rho_prev_h, 0, G * cb, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if ((ce = cudaMemsetAsync(s->ws + L.rho_ion, 0, G * cb, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if ((ce = cudaMemsetAsync(s->ws + L.dep, 0, 4 * G * cb, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
   if ((ce = cudaMemsetAsync(s->ws + L.err, 0, 256, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
   if ((st = launch_setup_twiddles(s)) != PIC_OK) return fail(st);
   if ((st = launch_setup_hankel(s)) != PIC_OK) return fail(st);
   if ((st = launch_setup_tables(s, cfg->order_p)) != PIC_OK) return fail(st);
+  if ((st = build_inv_volume(s)) != PIC_OK) return fail(st);
   if ((st = pic_sync(reinterpret_cast<pic_sim*>(s))) != PIC_OK) return fail(st);
   *out = reinterpret_cast<pic_sim*>(s);
   return PIC_OK;
@@ -359,13 +390,24 @@ pic_status pic_write_particles(pic_sim* sim, const double* const soa[7], const i
   }
   if (n > 0 && (!soa || !id)) { set_error("particle pointers are NULL"); return PIC_ERR_ARG; }
   const cudaMemcpyKind kind = on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  const bool mixed = s->cfg.precision != PIC_FP64;
+  const size_t cap = (size_t)s->cfg.np_capacity;
   for (int k = 0; k < 7 && n > 0; ++k) {
     if (!soa[k]) { set_error("particle array %d is NULL", k); return PIC_ERR_ARG; }
-    PIC_CUDA(cudaMemcpyAsync(s->ws + s->lay.part[s->cur][k], soa[k], n * 8, kind, s->stream));
+    char* dst = mixed ? s->ws + s->lay.stage64 + k * cap * 8 : s->ws + s->lay.part[s->cur][k];
+    PIC_CUDA(cudaMemcpyAsync(dst, soa[k], n * 8, kind, s->stream));
   }
-  if (n > 0) PIC_CUDA(cudaMemcpyAsync(s->ws + s->lay.pid[s->cur], id, n * 4, kind, s->stream));
-  if (on_host) PIC_CUDA(cudaStreamSynchronize(s->stream));
+  if (n > 0) {
+    // ids go straight to their final place (FP64 form) or to the perm scratch (mixed form)
+    char* dst = mixed ? s->ws + s->lay.perm_tmp : s->ws + s->lay.pid[s->cur];
+    PIC_CUDA(cudaMemcpyAsync(dst, id, n * 4, kind, s->stream));
+  }
   s->np = n;
+  if (mixed) {
+    pic_status st = launch_particles_in(s, s->at<int32_t>(s->lay.perm_tmp), n);
+    if (st != PIC_OK) return st;
+  }
+  if (on_host) PIC_CUDA(cudaStreamSynchronize(s->stream));
   return PIC_OK;
 }
 
@@ -375,9 +417,20 @@ pic_status pic_read_particles(pic_sim* sim, double* const soa[7], int32_t* id, i
   CHECK_SIM(s);
   if (n < 0 || n > s->np) { set_error("n=%lld exceeds the %lld particles held", (long long)n, (long long)s->np); return PIC_ERR_ARG; }
   const cudaMemcpyKind kind = on_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
-  for (int k = 0; k < 7 && n > 0; ++k)
-    if (soa && soa[k]) PIC_CUDA(cudaMemcpyAsync(soa[k], s->ws + s->lay.part[s->cur][k], n * 8, kind, s->stream));
-  if (id && n > 0) PIC_CUDA(cudaMemcpyAsync(id, s->ws + s->lay.pid[s->cur], n * 4, kind, s->stream));
+  const bool mixed = s->cfg.precision != PIC_FP64;
+  const size_t cap = (size_t)s->cfg.np_capacity;
+  if (mixed) {
+    pic_status st = launch_particles_out(s, s->at<int32_t>(s->lay.perm_tmp), n);
+    if (st != PIC_OK) return st;
+  }
+  for (int k = 0; k < 7 && n > 0; ++k) {
+    const char* src = mixed ? s->ws + s->lay.stage64 + k * cap * 8 : s->ws + s->lay.part[s->cur][k];
+    if (soa && soa[k]) PIC_CUDA(cudaMemcpyAsync(soa[k], src, n * 8, kind, s->stream));
+  }
+  if (id && n > 0) {
+    const char* src = mixed ? s->ws + s->lay.perm_tmp : s->ws + s->lay.pid[s->cur];
+    PIC_CUDA(cudaMemcpyAsync(id, src, n * 4, kind, s->stream));
+  }
   return pic_sync(sim);
 }
 
@@ -393,7 +446,7 @@ pic_status pic_init_background(pic_sim* sim, int32_t n_neutral) {
   Sim* s = reinterpret_cast<Sim*>(sim);
   CHECK_SIM(s);
   const size_t G = s->grid_elems();
-  PIC_CUDA(cudaMemsetAsync(s->ws + s->lay.dep, 0, G * 16, s->stream));
+  PIC_CUDA(cudaMemsetAsync(s->ws + s->lay.dep, 0, G * s->cplx_bytes, s->stream));
   pic_status st = launch_deposit(s, PIC_DEP_RHO, 0, n_neutral, nullptr);
   if (st != PIC_OK) return st;
   return launch_scale_copy(s, s->ws + s->lay.rho_ion, s->ws + s->lay.dep, -1.0, G);
@@ -404,7 +457,7 @@ pic_status pic_add_beam_fields(pic_sim* sim, int32_t id_lo, int32_t id_hi, doubl
   CHECK_SIM(s);
   if (!(gamma >= 1.0)) { set_error("gamma=%g must be >= 1", gamma); return PIC_ERR_ARG; }
   const size_t G = s->grid_elems();
-  PIC_CUDA(cudaMemsetAsync(s->ws + s->lay.dep, 0, G * 16, s->stream));
+  PIC_CUDA(cudaMemsetAsync(s->ws + s->lay.dep, 0, G * s->cplx_bytes, s->stream));
   pic_status st = launch_deposit(s, PIC_DEP_RHO, id_lo, id_hi, nullptr);
   if (st != PIC_OK) return st;
   if ((st = forward_transform(s, 1)) != PIC_OK) return st;
@@ -436,8 +489,8 @@ pic_status pic_deposit(pic_sim* sim, int32_t what) {
   pic_status st;
   if (what & PIC_DEP_RHO) {
     const size_t G = s->grid_elems();
-    PIC_CUDA(cudaMemcpyAsync(s->ws + s->lay.dep, s->ws + s->lay.rho_ion, G * 16, cudaMemcpyDeviceToDevice,
-                             s->stream));
+    PIC_CUDA(cudaMemcpyAsync(s->ws + s->lay.dep, s->ws + s->lay.rho_ion, G * s->cplx_bytes,
+                             cudaMemcpyDeviceToDevice, s->stream));
   }
   if ((st = launch_deposit(s, what, INT32_MIN, INT32_MAX, nullptr)) != PIC_OK) return st;
   return PIC_OK;

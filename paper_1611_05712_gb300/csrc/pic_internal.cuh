@@ -36,8 +36,17 @@ struct Layout {
   size_t part[2][7], pid[2];                                     // particles (double buffer)
   size_t keys, perm, perm_tmp, count, start, scan_blk, big_list, big_count;
   size_t diag_acc, err;
+  // mixed-precision form only (0 otherwise): float copies of the tables, the split DHT
+  // matrices, FP32 cell-relative particles and an FP64 staging area for particle IO
+  size_t coef_f, kperp_f, kzmod_f, tz_f, tr_f, twiddle_f;
+  size_t mfwd_hi, mfwd_lo, binv_hi, binv_lo;
+  size_t pf[2][9];   // iz (int32), fz, x, y, ux/c, uy/c, uz/c, w (float), id (int32)
+  size_t stage64;    // 7 x capacity float64
   size_t total;
 };
+
+// FP32 particle array indices of the mixed form.
+enum { kPfIz = 0, kPfFz = 1, kPfX = 2, kPfY = 3, kPfUx = 4, kPfUy = 5, kPfUz = 6, kPfW = 7, kPfId = 8 };
 
 struct Sim {
   pic_config cfg;
@@ -79,6 +88,8 @@ pic_status cuda_status(cudaError_t e, const char* what);
 pic_status launch_setup_hankel(Sim* s);          // zeros, B_p, pinv(B_p)
 pic_status launch_setup_tables(Sim* s, int32_t order_p);   // [k_z]_p and PSATD coefficients
 pic_status launch_setup_twiddles(Sim* s);
+pic_status convert_hankel_tables(Sim* s);                    // mixed form: float/split copies
+pic_status convert_psatd_tables(Sim* s);
 
 // ---- launchers (fft.cu) ----
 // Row transform descriptor: out[c] = FFT(ca*in[srcA] + cb*in[srcB]) (inverse: iFFT).
@@ -90,15 +101,19 @@ struct RowCombine {
 pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& rc, bool inverse);
 
 // ---- launchers (dht.cu) ----
-// out[b] = A[b] (Nr x Nr, row-major [out][red]) * in[b] (Nr x 2Nz reals)
+// out[b] = A[b] (Nr x Nr, row-major [out][red]) * in[b] (Nr x 2Nz reals).  Element type
+// float64 in the FP64 form; float in the mixed form, where A is split as A + Alo.
 struct DhtBatch {
   int32_t n;
-  const double* A[24];
+  const void* A[24];
+  const void* Alo[24];   // null: no low part
   const void* X[24];
   void* Y[24];
 };
-// ncols > 0 overrides the column count 2*Nz (used for Nr x Nr products at setup).
-pic_status launch_dht(Sim* s, const DhtBatch& b, int ncols = -1);
+// The DHT of the current precision form (FP64 SIMT, or 3-term TF32 on tcgen05).
+pic_status launch_dht(Sim* s, const DhtBatch& b);
+// FP64 Y = A X with A Nr x Nr and X Nr x ncols (setup products and the FP64 DHT).
+pic_status launch_gemm_f64(Sim* s, const DhtBatch& b, int ncols);
 
 // ---- launchers (psatd.cu) ----
 pic_status launch_psatd(Sim* s);
@@ -112,5 +127,8 @@ pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, vo
 pic_status launch_gather_push(Sim* s, int32_t fuse_current);
 pic_status launch_diag(Sim* s, int32_t id_lo, int32_t id_hi, pic_diag* out, double* slice_sigma,
                        int32_t max_slices);
+pic_status build_inv_volume(Sim* s);                        // once, at init
+pic_status launch_particles_in(Sim* s, const int32_t* id_dev, int64_t n);   // mixed: stage64 -> FP32
+pic_status launch_particles_out(Sim* s, int32_t* id_dev, int64_t n);        // mixed: FP32 -> stage64
 
 }  // namespace pic

@@ -9,84 +9,100 @@
 // grad X = (-K_perp X/2, K_perp X/2, i K_z X),
 // curl V = (K_z V+ - i K_perp Vz/2, -K_z V- - i K_perp Vz/2, i K_perp (V+ + V-)),
 // div V = K_perp (V+ - V-) + i K_z Vz.
-// One thread per spectral cell; every grid is read once and written once.
+// One thread per spectral cell; every grid is read once and written once.  R = double in
+// the FP64 form, float (with float coefficient tables) in the mixed form.
 #include "pic_internal.cuh"
 
 namespace pic {
 namespace {
 
-struct Z {
-  double re, im;
-};
-__device__ __forceinline__ Z zld(const double2* p, size_t i) { double2 v = p[i]; return {v.x, v.y}; }
-__device__ __forceinline__ void zst(double2* p, size_t i, Z v) { p[i] = make_double2(v.re, v.im); }
-__device__ __forceinline__ Z zadd(Z a, Z b) { return {a.re + b.re, a.im + b.im}; }
-__device__ __forceinline__ Z zsub(Z a, Z b) { return {a.re - b.re, a.im - b.im}; }
-__device__ __forceinline__ Z zscale(double s, Z a) { return {s * a.re, s * a.im}; }
-__device__ __forceinline__ Z zi(double s, Z a) { return {-s * a.im, s * a.re}; }   // i s a
+template <typename R> struct V2;
+template <> struct V2<double> { using T = double2; };
+template <> struct V2<float> { using T = float2; };
 
-__global__ void __launch_bounds__(256) k_psatd_f64(double2* __restrict__ Eh, double2* __restrict__ Bh,
-                                                   const double2* __restrict__ src,
-                                                   double2* __restrict__ rho_prev,
-                                                   const double* __restrict__ coef,
-                                                   const double* __restrict__ kperp,
-                                                   const double* __restrict__ kzmod,
-                                                   const double* __restrict__ tz,
-                                                   const double* __restrict__ tr, int Nz, size_t G,
-                                                   double dt, int filter) {
+template <typename R> struct Z {
+  R re, im;
+};
+template <typename R> __device__ __forceinline__ Z<R> zld(const typename V2<R>::T* p, size_t i) {
+  const typename V2<R>::T v = p[i];
+  return {v.x, v.y};
+}
+template <typename R> __device__ __forceinline__ void zst(typename V2<R>::T* p, size_t i, Z<R> v) {
+  typename V2<R>::T o;
+  o.x = v.re;
+  o.y = v.im;
+  p[i] = o;
+}
+template <typename R> __device__ __forceinline__ Z<R> zadd(Z<R> a, Z<R> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename R> __device__ __forceinline__ Z<R> zsub(Z<R> a, Z<R> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename R> __device__ __forceinline__ Z<R> zscale(R s, Z<R> a) { return {s * a.re, s * a.im}; }
+template <typename R> __device__ __forceinline__ Z<R> zi(R s, Z<R> a) { return {-s * a.im, s * a.re}; }  // i s a
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_psatd(typename V2<R>::T* __restrict__ Eh, typename V2<R>::T* __restrict__ Bh,
+                                               const typename V2<R>::T* __restrict__ src,
+                                               typename V2<R>::T* __restrict__ rho_prev,
+                                               const R* __restrict__ coef, const R* __restrict__ kperp,
+                                               const R* __restrict__ kzmod, const R* __restrict__ tz,
+                                               const R* __restrict__ tr, int Nz, size_t G, double dt,
+                                               int filter) {
+  const R kc = (R)kC, ieps0 = (R)(1.0 / kEps0), idt = (R)(1.0 / dt);
+  const R jS_f = (R)(1.0 / (kEps0 * kC)), bS_f = (R)(1.0 / kC), mu0 = (R)kMu0;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < G;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int kz = idx % Nz;
     const size_t mn = idx / Nz;
-    const double Kp = kperp[mn], Kz = kzmod[kz];
-    const double T = filter ? tz[kz] * tr[mn] : 1.0;
-    Z rn = zscale(T, zld(src, idx));
-    Z Jp = zscale(T, zld(src, G + idx));
-    Z Jm = zscale(T, zld(src, 2 * G + idx));
-    Z Jz = zscale(T, zld(src, 3 * G + idx));
-    const Z rp = zld(rho_prev, idx);
-    const double C = coef[idx], SK = coef[G + idx], omc = coef[2 * G + idx];
-    const double an = coef[3 * G + idx], ap = coef[4 * G + idx], iK2 = coef[5 * G + idx];
+    const R Kp = kperp[mn], Kz = kzmod[kz];
+    const R T = filter ? tz[kz] * tr[mn] : (R)1;
+    Z<R> rn = zscale(T, zld<R>(src, idx));
+    Z<R> Jp = zscale(T, zld<R>(src, G + idx));
+    Z<R> Jm = zscale(T, zld<R>(src, 2 * G + idx));
+    Z<R> Jz = zscale(T, zld<R>(src, 3 * G + idx));
+    const Z<R> rp = zld<R>(rho_prev, idx);
+    const R C = coef[idx], SK = coef[G + idx], omc = coef[2 * G + idx];
+    const R an = coef[3 * G + idx], ap = coef[4 * G + idx], iK2 = coef[5 * G + idx];
+    const R h = (R)0.5;
     // current correction
-    Z divJ = zadd(zscale(Kp, zsub(Jp, Jm)), zi(Kz, Jz));
-    Z Gc = zscale(iK2, zadd(zscale(1.0 / dt, zsub(rn, rp)), divJ));
-    Jp = zadd(Jp, zscale(-0.5 * Kp, Gc));
-    Jm = zadd(Jm, zscale(0.5 * Kp, Gc));
+    const Z<R> divJ = zadd(zscale(Kp, zsub(Jp, Jm)), zi(Kz, Jz));
+    const Z<R> Gc = zscale(iK2, zadd(zscale(idt, zsub(rn, rp)), divJ));
+    Jp = zadd(Jp, zscale(-h * Kp, Gc));
+    Jm = zadd(Jm, zscale(h * Kp, Gc));
     Jz = zadd(Jz, zi(Kz, Gc));
-    const Z Ep = zld(Eh, idx), Em = zld(Eh, G + idx), Ez = zld(Eh, 2 * G + idx);
-    const Z Bp = zld(Bh, idx), Bm = zld(Bh, G + idx), Bz = zld(Bh, 2 * G + idx);
+    const Z<R> Ep = zld<R>(Eh, idx), Em = zld<R>(Eh, G + idx), Ez = zld<R>(Eh, 2 * G + idx);
+    const Z<R> Bp = zld<R>(Bh, idx), Bm = zld<R>(Bh, G + idx), Bz = zld<R>(Bh, 2 * G + idx);
     // curls
-    const Z cBp = zsub(zscale(Kz, Bp), zi(0.5 * Kp, Bz));
-    const Z cBm = zsub(zscale(-Kz, Bm), zi(0.5 * Kp, Bz));
-    const Z cBz = zi(Kp, zadd(Bp, Bm));
-    const Z cEp = zsub(zscale(Kz, Ep), zi(0.5 * Kp, Ez));
-    const Z cEm = zsub(zscale(-Kz, Em), zi(0.5 * Kp, Ez));
-    const Z cEz = zi(Kp, zadd(Ep, Em));
-    const Z cJp = zsub(zscale(Kz, Jp), zi(0.5 * Kp, Jz));
-    const Z cJm = zsub(zscale(-Kz, Jm), zi(0.5 * Kp, Jz));
-    const Z cJz = zi(Kp, zadd(Jp, Jm));
-    const Z X = zscale(1.0 / kEps0, zadd(zscale(an, rn), zscale(ap, rp)));
-    const double cSK = kC * SK, jS = SK / (kEps0 * kC), bS = SK / kC, jB = kMu0 * omc;
-    Z nEp = zadd(zadd(zscale(C, Ep), zscale(cSK, cBp)), zadd(zscale(-jS, Jp), zscale(-0.5 * Kp, X)));
-    Z nEm = zadd(zadd(zscale(C, Em), zscale(cSK, cBm)), zadd(zscale(-jS, Jm), zscale(0.5 * Kp, X)));
-    Z nEz = zadd(zadd(zscale(C, Ez), zscale(cSK, cBz)), zadd(zscale(-jS, Jz), zi(Kz, X)));
-    Z nBp = zadd(zadd(zscale(C, Bp), zscale(-bS, cEp)), zscale(jB, cJp));
-    Z nBm = zadd(zadd(zscale(C, Bm), zscale(-bS, cEm)), zscale(jB, cJm));
-    Z nBz = zadd(zadd(zscale(C, Bz), zscale(-bS, cEz)), zscale(jB, cJz));
-    zst(Eh, idx, nEp); zst(Eh, G + idx, nEm); zst(Eh, 2 * G + idx, nEz);
-    zst(Bh, idx, nBp); zst(Bh, G + idx, nBm); zst(Bh, 2 * G + idx, nBz);
-    zst(rho_prev, idx, rn);
+    const Z<R> cBp = zsub(zscale(Kz, Bp), zi(h * Kp, Bz));
+    const Z<R> cBm = zsub(zscale(-Kz, Bm), zi(h * Kp, Bz));
+    const Z<R> cBz = zi(Kp, zadd(Bp, Bm));
+    const Z<R> cEp = zsub(zscale(Kz, Ep), zi(h * Kp, Ez));
+    const Z<R> cEm = zsub(zscale(-Kz, Em), zi(h * Kp, Ez));
+    const Z<R> cEz = zi(Kp, zadd(Ep, Em));
+    const Z<R> cJp = zsub(zscale(Kz, Jp), zi(h * Kp, Jz));
+    const Z<R> cJm = zsub(zscale(-Kz, Jm), zi(h * Kp, Jz));
+    const Z<R> cJz = zi(Kp, zadd(Jp, Jm));
+    const Z<R> X = zscale(ieps0, zadd(zscale(an, rn), zscale(ap, rp)));
+    const R cSK = kc * SK, jS = SK * jS_f, bS = SK * bS_f, jB = mu0 * omc;
+    const Z<R> nEp = zadd(zadd(zscale(C, Ep), zscale(cSK, cBp)), zadd(zscale(-jS, Jp), zscale(-h * Kp, X)));
+    const Z<R> nEm = zadd(zadd(zscale(C, Em), zscale(cSK, cBm)), zadd(zscale(-jS, Jm), zscale(h * Kp, X)));
+    const Z<R> nEz = zadd(zadd(zscale(C, Ez), zscale(cSK, cBz)), zadd(zscale(-jS, Jz), zi(Kz, X)));
+    const Z<R> nBp = zadd(zadd(zscale(C, Bp), zscale(-bS, cEp)), zscale(jB, cJp));
+    const Z<R> nBm = zadd(zadd(zscale(C, Bm), zscale(-bS, cEm)), zscale(jB, cJm));
+    const Z<R> nBz = zadd(zadd(zscale(C, Bz), zscale(-bS, cEz)), zscale(jB, cJz));
+    zst<R>(Eh, idx, nEp); zst<R>(Eh, G + idx, nEm); zst<R>(Eh, 2 * G + idx, nEz);
+    zst<R>(Bh, idx, nBp); zst<R>(Bh, G + idx, nBm); zst<R>(Bh, 2 * G + idx, nBz);
+    zst<R>(rho_prev, idx, rn);
   }
 }
 
 // Space-charge field of a beam moving along +z (initial condition): relativistic
 // Poisson solve phi = rho/(eps0 (K_perp^2 + K_z^2/gamma^2)),
 // E += (K_perp phi/2, -K_perp phi/2, -i K_z phi/gamma^2), B += curl(0, 0, beta phi/c).
-__global__ void k_beam_fields(double2* __restrict__ Eh, double2* __restrict__ Bh,
-                              const double2* __restrict__ rho, const double* __restrict__ kperp,
+// Always evaluated in float64; the mixed form reads and writes float grids.
+template <typename R>
+__global__ void k_beam_fields(typename V2<R>::T* __restrict__ Eh, typename V2<R>::T* __restrict__ Bh,
+                              const typename V2<R>::T* __restrict__ rho, const double* __restrict__ kperp,
                               const double* __restrict__ kzmod, const double* __restrict__ tz,
-                              const double* __restrict__ tr, int Nz, size_t G, double gamma,
-                              int filter) {
+                              const double* __restrict__ tr, int Nz, size_t G, double gamma, int filter) {
   const double ig2 = 1.0 / (gamma * gamma);
   const double beta = sqrt(1.0 - ig2);
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < G;
@@ -95,35 +111,41 @@ __global__ void k_beam_fields(double2* __restrict__ Eh, double2* __restrict__ Bh
     const size_t mn = idx / Nz;
     const double Kp = kperp[mn], Kz = kzmod[kz];
     const double T = filter ? tz[kz] * tr[mn] : 1.0;
-    const Z r = zscale(T, zld(rho, idx));
-    const Z phi = zscale(1.0 / (kEps0 * (Kp * Kp + Kz * Kz * ig2)), r);
-    const Z A = zscale(beta / kC, phi);
-    zst(Eh, idx, zadd(zld(Eh, idx), zscale(0.5 * Kp, phi)));
-    zst(Eh, G + idx, zadd(zld(Eh, G + idx), zscale(-0.5 * Kp, phi)));
-    zst(Eh, 2 * G + idx, zadd(zld(Eh, 2 * G + idx), zi(-Kz * ig2, phi)));
-    zst(Bh, idx, zadd(zld(Bh, idx), zi(-0.5 * Kp, A)));
-    zst(Bh, G + idx, zadd(zld(Bh, G + idx), zi(-0.5 * Kp, A)));
+    const Z<R> r0 = zld<R>(rho, idx);
+    const Z<double> r = {T * (double)r0.re, T * (double)r0.im};
+    const Z<double> phi = zscale(1.0 / (kEps0 * (Kp * Kp + Kz * Kz * ig2)), r);
+    const Z<double> A = zscale(beta / kC, phi);
+    const Z<double> add[5] = {zscale(0.5 * Kp, phi), zscale(-0.5 * Kp, phi), zi(-Kz * ig2, phi),
+                              zi(-0.5 * Kp, A), zi(-0.5 * Kp, A)};
+    typename V2<R>::T* dst[5] = {Eh, Eh, Eh, Bh, Bh};
+    const size_t off[5] = {idx, G + idx, 2 * G + idx, idx, G + idx};
+    for (int k = 0; k < 5; ++k) {
+      const Z<R> v = zld<R>(dst[k], off[k]);
+      zst<R>(dst[k], off[k], Z<R>{(R)((double)v.re + add[k].re), (R)((double)v.im + add[k].im)});
+    }
   }
 }
 
 // dst[idx] = T * src[idx] (T = filter factor, or 1 when the filter is off)
-__global__ void k_filter_copy(double2* __restrict__ dst, const double2* __restrict__ src,
+template <typename R>
+__global__ void k_filter_copy(typename V2<R>::T* __restrict__ dst, const typename V2<R>::T* __restrict__ src,
                               const double* __restrict__ tz, const double* __restrict__ tr, int Nz,
                               size_t G, int filter) {
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < G;
        idx += (size_t)gridDim.x * blockDim.x) {
     const double T = filter ? tz[idx % Nz] * tr[idx / Nz] : 1.0;
-    double2 v = src[idx];
-    dst[idx] = make_double2(T * v.x, T * v.y);
+    const Z<R> v = zld<R>(src, idx);
+    zst<R>(dst, idx, Z<R>{(R)(T * v.re), (R)(T * v.im)});
   }
 }
 
-__global__ void k_scale_copy(double2* __restrict__ dst, const double2* __restrict__ src, double a,
-                             size_t n) {
+template <typename R>
+__global__ void k_scale_copy(typename V2<R>::T* __restrict__ dst, const typename V2<R>::T* __restrict__ src,
+                             double a, size_t n) {
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < n;
        idx += (size_t)gridDim.x * blockDim.x) {
-    double2 v = src[idx];
-    dst[idx] = make_double2(a * v.x, a * v.y);
+    const Z<R> v = zld<R>(src, idx);
+    zst<R>(dst, idx, Z<R>{(R)(a * v.re), (R)(a * v.im)});
   }
 }
 
@@ -137,11 +159,19 @@ inline int grid_for(size_t n) {
 pic_status launch_psatd(Sim* s) {
   const pic_config& c = s->cfg;
   const size_t G = s->grid_elems();
-  k_psatd_f64<<<grid_for(G), 256, 0, s->stream>>>(
-      s->at<double2>(s->lay.Eh), s->at<double2>(s->lay.Bh), s->at<double2>(s->lay.srch),
-      s->at<double2>(s->lay.rho_prev_h), s->at<double>(s->lay.coef), s->at<double>(s->lay.kperp),
-      s->at<double>(s->lay.kzmod), s->at<double>(s->lay.tz), s->at<double>(s->lay.tr), c.Nz, G, c.dt,
-      c.filter);
+  if (c.precision == PIC_FP64) {
+    k_psatd<double><<<grid_for(G), 256, 0, s->stream>>>(
+        s->at<double2>(s->lay.Eh), s->at<double2>(s->lay.Bh), s->at<double2>(s->lay.srch),
+        s->at<double2>(s->lay.rho_prev_h), s->at<double>(s->lay.coef), s->at<double>(s->lay.kperp),
+        s->at<double>(s->lay.kzmod), s->at<double>(s->lay.tz), s->at<double>(s->lay.tr), c.Nz, G, c.dt,
+        c.filter);
+  } else {
+    k_psatd<float><<<grid_for(G), 256, 0, s->stream>>>(
+        s->at<float2>(s->lay.Eh), s->at<float2>(s->lay.Bh), s->at<float2>(s->lay.srch),
+        s->at<float2>(s->lay.rho_prev_h), s->at<float>(s->lay.coef_f), s->at<float>(s->lay.kperp_f),
+        s->at<float>(s->lay.kzmod_f), s->at<float>(s->lay.tz_f), s->at<float>(s->lay.tr_f), c.Nz, G, c.dt,
+        c.filter);
+  }
   PIC_LAUNCHED(s);
   return PIC_OK;
 }
@@ -149,16 +179,23 @@ pic_status launch_psatd(Sim* s) {
 pic_status launch_beam_fields(Sim* s, const void* rho_h, double gamma) {
   const pic_config& c = s->cfg;
   const size_t G = s->grid_elems();
-  k_beam_fields<<<grid_for(G), 256, 0, s->stream>>>(
-      s->at<double2>(s->lay.Eh), s->at<double2>(s->lay.Bh), (const double2*)rho_h,
-      s->at<double>(s->lay.kperp), s->at<double>(s->lay.kzmod), s->at<double>(s->lay.tz),
-      s->at<double>(s->lay.tr), c.Nz, G, gamma, c.filter);
+  if (c.precision == PIC_FP64)
+    k_beam_fields<double><<<grid_for(G), 256, 0, s->stream>>>(
+        s->at<double2>(s->lay.Eh), s->at<double2>(s->lay.Bh), (const double2*)rho_h, s->at<double>(s->lay.kperp),
+        s->at<double>(s->lay.kzmod), s->at<double>(s->lay.tz), s->at<double>(s->lay.tr), c.Nz, G, gamma, c.filter);
+  else
+    k_beam_fields<float><<<grid_for(G), 256, 0, s->stream>>>(
+        s->at<float2>(s->lay.Eh), s->at<float2>(s->lay.Bh), (const float2*)rho_h, s->at<double>(s->lay.kperp),
+        s->at<double>(s->lay.kzmod), s->at<double>(s->lay.tz), s->at<double>(s->lay.tr), c.Nz, G, gamma, c.filter);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }
 
 pic_status launch_scale_copy(Sim* s, void* dst, const void* src, double a, size_t n_cplx) {
-  k_scale_copy<<<grid_for(n_cplx), 256, 0, s->stream>>>((double2*)dst, (const double2*)src, a, n_cplx);
+  if (s->cfg.precision == PIC_FP64)
+    k_scale_copy<double><<<grid_for(n_cplx), 256, 0, s->stream>>>((double2*)dst, (const double2*)src, a, n_cplx);
+  else
+    k_scale_copy<float><<<grid_for(n_cplx), 256, 0, s->stream>>>((float2*)dst, (const float2*)src, a, n_cplx);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }
@@ -166,9 +203,14 @@ pic_status launch_scale_copy(Sim* s, void* dst, const void* src, double a, size_
 pic_status launch_filter_copy(Sim* s, void* dst, const void* src) {
   const pic_config& c = s->cfg;
   const size_t G = s->grid_elems();
-  k_filter_copy<<<grid_for(G), 256, 0, s->stream>>>((double2*)dst, (const double2*)src,
-                                                    s->at<double>(s->lay.tz),
-                                                    s->at<double>(s->lay.tr), c.Nz, G, c.filter);
+  if (c.precision == PIC_FP64)
+    k_filter_copy<double><<<grid_for(G), 256, 0, s->stream>>>((double2*)dst, (const double2*)src,
+                                                              s->at<double>(s->lay.tz), s->at<double>(s->lay.tr),
+                                                              c.Nz, G, c.filter);
+  else
+    k_filter_copy<float><<<grid_for(G), 256, 0, s->stream>>>((float2*)dst, (const float2*)src,
+                                                             s->at<double>(s->lay.tz), s->at<double>(s->lay.tr),
+                                                             c.Nz, G, c.filter);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }

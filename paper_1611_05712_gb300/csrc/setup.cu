@@ -354,7 +354,61 @@ __global__ void k_twiddles(double2* tw, int N) {
 
 inline int blocks_for(size_t n, int t) { return (int)((n + t - 1) / t); }
 
+// float copies of FP64 tables (round to nearest)
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// Split of an FP64 matrix for 3-term TF32 products: hi = the value rounded to TF32
+// (10 explicit mantissa bits, low 13 bits of the float zero), lo = float(value - hi).
+__global__ void k_split_tf32(const double* __restrict__ in, float* __restrict__ hi, float* __restrict__ lo,
+                             size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double v = in[i];
+    const float f = (float)v;
+    // round-to-nearest-even at bit 13 of the float's bit pattern (finite values)
+    uint32_t b = __float_as_uint(f);
+    b = (b + 0x0fffu + ((b >> 13) & 1u)) & 0xffffe000u;
+    const float h = __uint_as_float(b);
+    hi[i] = h;
+    lo[i] = (float)(v - (double)h);
+  }
+}
+
+inline int conv_grid(size_t n) { return (int)std::min<size_t>(blocks_for(n, 256), 152 * 16); }
+
 }  // namespace
+
+// Mixed form: float copies of k_perp, the filter factor in r and the split DHT matrices.
+pic_status convert_hankel_tables(Sim* s) {
+  const pic_config& c = s->cfg;
+  const size_t nmn = (size_t)c.Nm * c.Nr, nmat = (size_t)c.Nm * 3 * c.Nr * c.Nr;
+  k_to_float<<<conv_grid(nmn), 256, 0, s->stream>>>(s->at<double>(s->lay.kperp), s->at<float>(s->lay.kperp_f), nmn);
+  PIC_LAUNCHED(s);
+  k_to_float<<<conv_grid(nmn), 256, 0, s->stream>>>(s->at<double>(s->lay.tr), s->at<float>(s->lay.tr_f), nmn);
+  PIC_LAUNCHED(s);
+  k_split_tf32<<<conv_grid(nmat), 256, 0, s->stream>>>(s->at<double>(s->lay.mfwd), s->at<float>(s->lay.mfwd_hi),
+                                                         s->at<float>(s->lay.mfwd_lo), nmat);
+  PIC_LAUNCHED(s);
+  k_split_tf32<<<conv_grid(nmat), 256, 0, s->stream>>>(s->at<double>(s->lay.binv), s->at<float>(s->lay.binv_hi),
+                                                         s->at<float>(s->lay.binv_lo), nmat);
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
+// Mixed form: float copies of the PSATD coefficient tables, [k_z]_p and the z filter.
+pic_status convert_psatd_tables(Sim* s) {
+  const pic_config& c = s->cfg;
+  const size_t G6 = 6 * s->grid_elems();
+  k_to_float<<<conv_grid(G6), 256, 0, s->stream>>>(s->at<double>(s->lay.coef), s->at<float>(s->lay.coef_f), G6);
+  PIC_LAUNCHED(s);
+  k_to_float<<<conv_grid(c.Nz), 256, 0, s->stream>>>(s->at<double>(s->lay.kzmod), s->at<float>(s->lay.kzmod_f), c.Nz);
+  PIC_LAUNCHED(s);
+  k_to_float<<<conv_grid(c.Nz), 256, 0, s->stream>>>(s->at<double>(s->lay.tz), s->at<float>(s->lay.tz_f), c.Nz);
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
 
 pic_status launch_setup_hankel(Sim* s) {
   const pic_config& c = s->cfg;
@@ -390,16 +444,17 @@ pic_status launch_setup_hankel(Sim* s) {
     mt.A[k] = mfwd + k * Nr2; mt.X[k] = wt + k * Nr2; mt.Y[k] = vt + k * Nr2;
   }
   bm.n = mt.n = Nm * 3;
-  pic_status st = launch_dht(s, bm, Nr);               // W = B M
+  pic_status st = launch_gemm_f64(s, bm, Nr);          // W = B M
   if (st != PIC_OK) return st;
   k_two_minus<<<(int)std::min<size_t>(blocks_for(Nm * 3 * Nr2, 256), 152 * 16), 256, 0, s->stream>>>(
       wt, Nm * 3, Nr);                                  // W = 2I - W
   PIC_LAUNCHED(s);
-  if ((st = launch_dht(s, mt, Nr)) != PIC_OK) return st;   // V = M W
+  if ((st = launch_gemm_f64(s, mt, Nr)) != PIC_OK) return st;   // V = M W
   PIC_CUDA(cudaMemcpyAsync(mfwd, vt, Nm * 3 * Nr2 * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
   k_tr_table<<<blocks_for((size_t)Nm * Nr, 128), 128, 0, s->stream>>>(s->at<double>(s->lay.tr), kperp,
                                                                        Nm * Nr, c.dr);
   PIC_LAUNCHED(s);
+  if (c.precision != PIC_FP64) return convert_hankel_tables(s);
   return PIC_OK;
 }
 
@@ -415,6 +470,7 @@ pic_status launch_setup_tables(Sim* s, int32_t order_p) {
       c.Nr, c.Nz, c.dt);
   PIC_LAUNCHED(s);
   s->order_tables = order_p;
+  if (c.precision != PIC_FP64) return convert_psatd_tables(s);
   return PIC_OK;
 }
 
@@ -422,6 +478,11 @@ pic_status launch_setup_twiddles(Sim* s) {
   k_twiddles<<<blocks_for(s->cfg.Nz, 128), 128, 0, s->stream>>>(s->at<double2>(s->lay.twiddle),
                                                                 s->cfg.Nz);
   PIC_LAUNCHED(s);
+  if (s->cfg.precision != PIC_FP64) {
+    const size_t n2 = 2 * (size_t)s->cfg.Nz;
+    k_to_float<<<conv_grid(n2), 256, 0, s->stream>>>(s->at<double>(s->lay.twiddle), s->at<float>(s->lay.twiddle_f), n2);
+    PIC_LAUNCHED(s);
+  }
   return PIC_OK;
 }
 
