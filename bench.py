@@ -26,6 +26,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2070 MHz (nominal 1.25)
+BF16_TFLOPS = 1884.9                           # MEASURED_PEAKS.json bf16 burst
 FP64_PROBE_TFLOPS = 1.1947                     # FMA-loop probe on this machine's GB300 at 1987 MHz
 # DRAM bytes per k_dht_f64 launch on this workload, from one ncu capture of the current kernel
 # (forward 71.29 + 28.10 MB, inverse 107.18 + 61.11 MB, mean of the two launches)
@@ -39,6 +40,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--order", type=int, default=32)
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+                    help="fp64: every stage in float64; mixed: float grids and particles, "
+                         "3-term TF32 DHT on tcgen05")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -49,9 +53,9 @@ def workload(order, rank=0):
     return W.wake_2048x256(order_p=order, seed=2 + rank)
 
 
-def config_of(w, n):
+def config_of(w, n, precision="fp64"):
     return {"workload": w.name, "Nz": w.Nz, "Nr": w.Nr, "Nm": w.Nm, "order_p": w.order_p,
-            "particles": n, "dz_m": w.dz, "dt_s": w.dt, "precision": "fp64",
+            "particles": n, "dz_m": w.dz, "dt_s": w.dt, "precision": precision,
             "l2": "no flush: working set (fields + particles, ~0.8 GB) exceeds the 129 MB L2"}
 
 
@@ -175,7 +179,9 @@ def run_ours(args):
     w = workload(args.order, rank)
     P, npl, beams = W.particles(w)
     n = len(P["x"])
-    sim = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}")
+    mixed = args.precision == "mixed"
+    sim = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}",
+                               precision=bd.PIC_MIXED_TF32X3 if mixed else bd.PIC_FP64)
     wit_lo, wit_hi = beams[-1][0], beams[-1][1]
     sim.step(args.warmup)
     sim.sync()
@@ -227,20 +233,31 @@ def run_ours(args):
     dht_ms = stage_ms["dht_fwd"] + stage_ms["dht_inv"]
     launches_dht = 2 * args.steps
     achieved = (dht_flops_per_step * args.steps / launches_dht) / (dht_ms * 1e-3 / launches_dht) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": DHT_F64_TRAFFIC_BYTES,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the "
-                                  "forward and inverse launch (profiles/k_dht_f64__wake_2048x256_m2_fp64.md)",
-                "kernel": "k_dht_f64 (forward and inverse DHT, FP64 SIMT)",
-                "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe nominal "
-                               "1.25 TFLOP/s); FMA probe measured 1.195 TFLOP/s",
-                "share_of_step": dht_ms / sum(stage_ms.values())}
+    if mixed:
+        # 3 TF32 products per algorithmic multiply-add; peak for TF32 = measured BF16 burst
+        # x the recipe's nominal TF32/BF16 ratio (1.1 / 2.25)
+        tf32_peak = BF16_TFLOPS * 1.1 / 2.25
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / tf32_peak, "traffic": None,
+                    "executed_tflops": 3 * achieved, "executed_frac": 3 * achieved / tf32_peak,
+                    "kernel": "k_dht_tc (3-term TF32 on tcgen05)",
+                    "peak_source": "measured bf16 burst 1884.9 TFLOP/s x nominal tf32/bf16 1.1/2.25",
+                    "share_of_step": dht_ms / sum(stage_ms.values())}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": DHT_F64_TRAFFIC_BYTES,
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the "
+                                      "forward and inverse launch (profiles/k_dht_f64__wake_2048x256_m2_fp64.md)",
+                    "kernel": "k_dht_f64 (forward and inverse DHT, FP64 SIMT)",
+                    "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe nominal "
+                                   "1.25 TFLOP/s); FMA probe measured 1.195 TFLOP/s",
+                    "share_of_step": dht_ms / sum(stage_ms.values())}
 
     line = {
         "metric": "pic_steps_per_s", "value": steps_per_s, "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config_of(w, n),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+tf32x3" if mixed else "f64", "data": "synthetic", "config": config_of(w, n, args.precision),
         "particle_updates_per_s": steps_per_s * n,
         "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),

@@ -88,12 +88,8 @@ pic_status launch_gemm_f64(Sim* s, const DhtBatch& b, int ncols) {
 }
 
 pic_status launch_dht(Sim* s, const DhtBatch& b) {
-  const int Nr = s->cfg.Nr, Nc = 2 * s->cfg.Nz;
-  if (s->cfg.precision == PIC_FP64) return launch_gemm_f64(s, b, Nc);
-  dim3 grid((Nc + BN - 1) / BN, (Nr + BM - 1) / BM, b.n);
-  k_gemm<float><<<grid, 256, 0, s->stream>>>(b, Nr, Nc);
-  PIC_LAUNCHED(s);
-  return PIC_OK;
+  if (s->cfg.precision == PIC_FP64) return launch_gemm_f64(s, b, 2 * s->cfg.Nz);
+  return launch_dht_tc(s, b);   // mixed form: 3-term TF32 on tcgen05 (dht_tc.cu)
 }
 
 }  // namespace pic

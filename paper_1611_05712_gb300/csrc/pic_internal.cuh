@@ -114,6 +114,8 @@ struct DhtBatch {
 pic_status launch_dht(Sim* s, const DhtBatch& b);
 // FP64 Y = A X with A Nr x Nr and X Nr x ncols (setup products and the FP64 DHT).
 pic_status launch_gemm_f64(Sim* s, const DhtBatch& b, int ncols);
+// Mixed form: Y = (Ahi + Alo) X with 3-term TF32 products on tcgen05 (dht_tc.cu).
+pic_status launch_dht_tc(Sim* s, const DhtBatch& b);
 
 // ---- launchers (psatd.cu) ----
 pic_status launch_psatd(Sim* s);
