@@ -45,6 +45,7 @@ def parse():
                          "3-term TF32 DHT on tcgen05")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-form comparison")
     return ap.parse_args()
 
 
@@ -110,6 +111,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------------------- multi-rank
+def reduce_max(x, dist=None, device=None):
+    """Max of a per-rank time over all ranks (a timing reduction, not a data-path exchange)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_throughput(steps, world, max_ms):
+    """Whole-job cycles/s: every rank advances its own simulation `steps` cycles."""
+    return world * steps / (max_ms * 1e-3)
+
+
 # ------------------------------------------------------------------------- CPU oracle
 def oracle_steps_per_s(w, P, npl, beams, n_steps):
     """Time the FP64 oracle as it stands on the host cores: n_steps full cycles."""
@@ -153,6 +170,92 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------- GPU
+
+def measure(args, w, P, npl, beams, mixed, dist, dev, world, local):
+    """Set one simulation up (untimed), warm up, time args.steps cycles with CUDA events
+    between the stages, then time args.e2e_steps cycles end to end through the C ABI."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    from paper_1611_05712_gb300 import binding as bd
+    n = len(P["x"])
+    sim = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}",
+                               precision=bd.PIC_MIXED_TF32X3 if mixed else bd.PIC_FP64)
+    wit_lo, wit_hi = beams[-1][0], beams[-1][1]
+    sim.step(args.warmup)
+    sim.sync()
+    torch.cuda.synchronize(dev)
+
+    # timed region: K cycles, CUDA events between stages on the library's stream
+    l0 = sim.launch_count()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        stage_ms, total_ms = sim.step_timed(args.steps)
+    torch.cuda.synchronize(dev)
+    launches = sim.launch_count() - l0
+    el_ms = reduce_max(total_ms, dist, dev)
+    steps_per_s = weak_throughput(args.steps, world, el_ms)
+
+    # end to end through the C ABI with host buffers: H2D of the step's particles from
+    # pinned memory, one cycle, D2H of the witness-beam diagnostics
+    pinned = {k: torch.from_numpy(np.ascontiguousarray(P[k])).pin_memory() for k in bd.SOA}
+    pinned_id = torch.from_numpy(P["id"]).pin_memory()
+    ptrs = (ctypes.c_void_p * 7)(*[pinned[k].data_ptr() for k in bd.SOA])
+    n_slices = 0
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        bd._check(sim.lib.pic_write_particles(sim.h, ptrs, ctypes.c_void_p(pinned_id.data_ptr()), n, 1),
+                  "pic_write_particles")
+        sim.step(1)
+        d = sim.diagnostics(wit_lo, wit_hi)
+        n_slices = d["n_slices"]
+    e2e_s = time.perf_counter() - t0
+    e2e_s = reduce_max(e2e_s, dist, dev)
+    e2e = {"value": weak_throughput(args.e2e_steps, world, 1e3 * max(e2e_s, 1e-12)), "unit": "steps/s",
+           "h2d_bytes_per_step": n * (7 * 8 + 4) + 5 * 8,
+           "d2h_bytes_per_step": 8 * (8 + 7 + 2 * max(n_slices, 1)) + 4,
+           "steps": args.e2e_steps}
+
+    # roofline of the dominant kernel: the DHT (two launches per cycle)
+    dht_flops_per_step = 10 * w.Nm * 4.0 * w.Nz * w.Nr ** 2
+    dht_ms = stage_ms["dht_fwd"] + stage_ms["dht_inv"]
+    launches_dht = 2 * args.steps
+    achieved = (dht_flops_per_step * args.steps / launches_dht) / (dht_ms * 1e-3 / launches_dht) / 1e12
+    share = dht_ms / sum(stage_ms.values())
+    if mixed:
+        # 3 TF32 products per algorithmic multiply-add; the TF32 peak is the measured BF16
+        # burst x the recipe's nominal TF32/BF16 ratio (1.1 / 2.25)
+        tf32_peak = BF16_TFLOPS * 1.1 / 2.25
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / tf32_peak, "traffic": None,
+                    "executed_tflops": 3 * achieved, "executed_frac": 3 * achieved / tf32_peak,
+                    "kernel": "k_dht_tc (3-term TF32 on tcgen05)",
+                    "peak_source": "of measured: bf16 burst 1884.9 TFLOP/s x nominal tf32/bf16 1.1/2.25",
+                    "share_of_step": share}
+    else:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": DHT_F64_TRAFFIC_BYTES,
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the "
+                                      "forward and inverse launch (profiles/k_dht_f64__wake_2048x256_m2_fp64.md)",
+                    "kernel": "k_dht_f64 (forward and inverse DHT, FP64 SIMT)",
+                    "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe nominal "
+                                   "1.25 TFLOP/s); FMA probe measured 1.195 TFLOP/s",
+                    "share_of_step": share}
+    out = {"steps_per_s": steps_per_s, "ms_per_step": el_ms / args.steps,
+           "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+           "dtype": "f32+tf32x3" if mixed else "f64"}
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -179,89 +282,27 @@ def run_ours(args):
     w = workload(args.order, rank)
     P, npl, beams = W.particles(w)
     n = len(P["x"])
-    mixed = args.precision == "mixed"
-    sim = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}",
-                               precision=bd.PIC_MIXED_TF32X3 if mixed else bd.PIC_FP64)
-    wit_lo, wit_hi = beams[-1][0], beams[-1][1]
-    sim.step(args.warmup)
-    sim.sync()
-    torch.cuda.synchronize(dev)
-
-    # timed region: K cycles, CUDA events between stages on the library's stream
-    l0 = sim.launch_count()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    with ClockSampler(local) as clk:
-        stage_ms, total_ms = sim.step_timed(args.steps)
-    torch.cuda.synchronize(dev)
-    launches = sim.launch_count() - l0
-    el_ms = total_ms
-    if dist:
-        t = torch.tensor([el_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el_ms = float(t.item())
-    steps_per_s = world * args.steps / (el_ms * 1e-3)
-
-    # end-to-end through the C ABI with host buffers: H2D of the step's particles from
-    # pinned memory, one cycle, D2H of the witness-beam diagnostics
-    pinned = {k: torch.from_numpy(np.ascontiguousarray(P[k])).pin_memory() for k in bd.SOA}
-    pinned_id = torch.from_numpy(P["id"]).pin_memory()
-    import ctypes
-    ptrs = (ctypes.c_void_p * 7)(*[pinned[k].data_ptr() for k in bd.SOA])
-    n_slices = 0
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        bd._check(sim.lib.pic_write_particles(sim.h, ptrs, ctypes.c_void_p(pinned_id.data_ptr()), n, 1),
-                  "pic_write_particles")
-        sim.step(1)
-        d = sim.diagnostics(wit_lo, wit_hi)
-        n_slices = d["n_slices"]
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * args.e2e_steps / max(e2e_s, 1e-12), "unit": "steps/s",
-           "h2d_bytes_per_step": n * (7 * 8 + 4) + 5 * 8,
-           "d2h_bytes_per_step": 8 * (8 + 7 + 2 * max(n_slices, 1)) + 4,
-           "steps": args.e2e_steps}
-    if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e["value"] = world * args.e2e_steps / float(t.item())
-
-    # roofline of the dominant kernel: the FP64 DHT (two launches per cycle)
-    dht_flops_per_step = 10 * w.Nm * 4.0 * w.Nz * w.Nr ** 2
-    dht_ms = stage_ms["dht_fwd"] + stage_ms["dht_inv"]
-    launches_dht = 2 * args.steps
-    achieved = (dht_flops_per_step * args.steps / launches_dht) / (dht_ms * 1e-3 / launches_dht) / 1e12
-    if mixed:
-        # 3 TF32 products per algorithmic multiply-add; peak for TF32 = measured BF16 burst
-        # x the recipe's nominal TF32/BF16 ratio (1.1 / 2.25)
-        tf32_peak = BF16_TFLOPS * 1.1 / 2.25
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                    "frac": achieved / tf32_peak, "traffic": None,
-                    "executed_tflops": 3 * achieved, "executed_frac": 3 * achieved / tf32_peak,
-                    "kernel": "k_dht_tc (3-term TF32 on tcgen05)",
-                    "peak_source": "measured bf16 burst 1884.9 TFLOP/s x nominal tf32/bf16 1.1/2.25",
-                    "share_of_step": dht_ms / sum(stage_ms.values())}
-    else:
-        roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / FP64_PEAK_TFLOPS, "traffic": DHT_F64_TRAFFIC_BYTES,
-                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the "
-                                      "forward and inverse launch (profiles/k_dht_f64__wake_2048x256_m2_fp64.md)",
-                    "kernel": "k_dht_f64 (forward and inverse DHT, FP64 SIMT)",
-                    "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe nominal "
-                                   "1.25 TFLOP/s); FMA probe measured 1.195 TFLOP/s",
-                    "share_of_step": dht_ms / sum(stage_ms.values())}
-
+    head = measure(args, w, P, npl, beams, args.precision == "mixed", dist, dev, world, local)
     line = {
-        "metric": "pic_steps_per_s", "value": steps_per_s, "unit": "steps/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
+        "metric": "pic_steps_per_s", "value": head["steps_per_s"], "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+tf32x3" if mixed else "f64", "data": "synthetic", "config": config_of(w, n, args.precision),
-        "particle_updates_per_s": steps_per_s * n,
-        "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
-        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+        "dtype": head["dtype"], "data": "synthetic", "config": config_of(w, n, args.precision),
+        "particle_updates_per_s": head["steps_per_s"] * n,
+        "stage_ms_per_step": head["stage_ms_per_step"],
+        "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"],
     }
+    if args.precision == "fp64" and not args.no_mixed:
+        # the chosen mixed-precision form on the same workload (beam emittance and slice
+        # energy spread within 1e-4 of FP64: tests/test_gpu_mixed.py)
+        mx = measure(args, w, P, npl, beams, True, dist, dev, world, local)
+        line["mixed_form"] = {
+            "value": mx["steps_per_s"], "unit": "steps/s", "dtype": mx["dtype"],
+            "ms_per_step": mx["ms_per_step"], "particle_updates_per_s": mx["steps_per_s"] * n,
+            "speedup_vs_fp64": mx["steps_per_s"] / head["steps_per_s"],
+            "stage_ms_per_step": mx["stage_ms_per_step"], "roofline": mx["roofline"], "e2e": mx["e2e"],
+            "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, secs = oracle_steps_per_s(w, P, npl, beams, 1)
         line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": os.cpu_count(),
