@@ -218,6 +218,24 @@ typedef enum {
  * 1 <= n_steps <= 4096.  Synchronises. */
 pic_status pic_step_timed(pic_sim* sim, int32_t n_steps, double* stage_ms);
 
+/* ---- batched scan (many independent simulations) ---------------------------------
+ * The paper's results come from scans over stencil order, resolution, charge and
+ * propagation length (section "Accurate modeling of plasma accelerators in finite order
+ * PSATD").  pic_batch_create captures cycles_per_launch full cycles of every simulation
+ * into ONE CUDA graph: each simulation runs on its own stream (given at its pic_init; must
+ * not be the default stream), forked from and joined back to origin_stream (a created
+ * stream), so uneven simulations run concurrently.  cycles_per_launch must be even (the
+ * particle double buffers return to their starting parity).  The handles must have been
+ * brought to their initial state (pic_init_fields) and must not be stepped through other
+ * calls while the batch exists.  pic_batch_launch enqueues n graph launches on
+ * origin_stream (asynchronous).  Errors: PIC_ERR_ARG, PIC_ERR_CUDA, PIC_ERR_OOM. */
+typedef struct pic_batch pic_batch;
+pic_status pic_batch_create(pic_sim* const* sims, int32_t n_sims, int32_t cycles_per_launch,
+                            void* origin_stream, pic_batch** out);
+pic_status pic_batch_launch(pic_batch* batch, int32_t n_launches);
+pic_status pic_batch_info(pic_batch* batch, int32_t* cycles_per_launch, int64_t* kernels_per_launch);
+pic_status pic_batch_destroy(pic_batch* batch);
+
 /* a10: FP64 diagnostics of the particles with id in [id_lo, id_hi).  slice_sigma (host,
  * may be NULL) receives up to max_slices per-slice std of gamma.  Synchronises. */
 pic_status pic_diagnostics(pic_sim* sim, int32_t id_lo, int32_t id_hi, pic_diag* out,

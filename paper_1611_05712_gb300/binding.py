@@ -92,6 +92,10 @@ def load():
         "pic_load_buffer": [P, I32, P, SZ, I32],
         "pic_sync": [P],
         "pic_launch_count": [P, ctypes.POINTER(I64)],
+        "pic_batch_create": [PP, I32, I32, P, ctypes.POINTER(P)],
+        "pic_batch_launch": [P, I32],
+        "pic_batch_info": [P, ctypes.POINTER(I32), ctypes.POINTER(I64)],
+        "pic_batch_destroy": [P],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -285,17 +289,54 @@ class Sim:
     # -- convenience ------------------------------------------------------------------
     @classmethod
     def from_workload(cls, w, particles, n_plasma, beams, precision=PIC_FP64, filter=True,
-                      order_p=None, capacity=None, device="cuda:0"):
+                      order_p=None, capacity=None, device="cuda:0", stream=None):
         """Create a handle for a workload and bring it to its initial state: particles,
         neutralising ions for the plasma, beam space-charge fields, rho^0 and E^0, B^0."""
         n = len(particles["x"])
         cfg = make_config(w.Nz, w.Nr, w.Nm, w.dz, w.dr, w.dt,
                           w.order_p if order_p is None else order_p, filter, precision,
                           capacity if capacity is not None else n)
-        s = cls(cfg, device=device)
+        s = cls(cfg, device=device, stream=stream)
         s.write_particles(particles)
         s.init_background(n_plasma)
         for lo, hi, gam in beams:
             s.add_beam_fields(lo, hi, gam)
         s.init_fields()
         return s
+
+
+class Batch:
+    """Many simulations advanced together by one captured CUDA graph per launch.
+
+    Each simulation must have been created on its own (non-default) torch stream and brought
+    to its initial state; ``cycles`` (even) full cycles of every simulation run per launch.
+    """
+
+    def __init__(self, sims, cycles=2, origin=None):
+        import torch
+        self.lib = load()
+        self.sims = list(sims)
+        self.origin = origin if origin is not None else torch.cuda.Stream(self.sims[0].device)
+        arr = (ctypes.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
+        h = ctypes.c_void_p()
+        _check(self.lib.pic_batch_create(arr, len(self.sims), int(cycles),
+                                         ctypes.c_void_p(self.origin.cuda_stream), ctypes.byref(h)),
+               "pic_batch_create")
+        self.h = h
+        c, k = ctypes.c_int32(), ctypes.c_int64()
+        _check(self.lib.pic_batch_info(self.h, ctypes.byref(c), ctypes.byref(k)), "pic_batch_info")
+        self.cycles, self.kernels_per_launch = c.value, k.value
+
+    def launch(self, n=1):
+        _check(self.lib.pic_batch_launch(self.h, int(n)), "pic_batch_launch")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pic_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

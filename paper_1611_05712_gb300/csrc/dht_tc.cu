@@ -21,6 +21,8 @@
 // 32*(w%4)..+31) and writes Yf[n][c] so that the 32 lanes of a warp store 32 consecutive c.
 #include <stdint.h>
 
+#include <mutex>
+
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -259,6 +261,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams 
 
 size_t dht_tc_smem_bytes(int NT) { return 1024 + 2 * (2 * kTcM * 128 + 2 * (size_t)NT * 128) + 64; }
 
+// Raised once per device to the largest tile (N_T = 256); per-launch changes of this
+// per-function attribute would race between host threads.
+pic_status dht_tc_configure_device() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  PIC_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && done[dev]) return PIC_OK;
+  PIC_CUDA(cudaFuncSetAttribute(k_dht_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dht_tc_smem_bytes(kTcMaxN)));
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return PIC_OK;
+}
+
 pic_status launch_dht_tc(Sim* s, const DhtBatch& b) {
   const int Nr = s->cfg.Nr, Nc = 2 * s->cfg.Nz;
   TcParams P;
@@ -272,7 +289,6 @@ pic_status launch_dht_tc(Sim* s, const DhtBatch& b) {
   P.tmem_cols = tc;
   P.m_tiles = (Nc + kTcM - 1) / kTcM;
   const size_t smem = dht_tc_smem_bytes(P.NT);
-  PIC_CUDA(cudaFuncSetAttribute(k_dht_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   dim3 grid(P.m_tiles, P.n_tiles, b.n);
   k_dht_tc<<<grid, kTcThreads, smem, s->stream>>>(b, P, s->at<int32_t>(s->lay.err));
   PIC_LAUNCHED(s);

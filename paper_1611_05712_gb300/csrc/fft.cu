@@ -7,6 +7,8 @@
 // The component combination of the quasi-cylindrical scheme is fused into the row load:
 // out = ca * inA + cb * inB, which forms J_+- = (J_r -+ i J_theta)/2 before the forward
 // transform and E_r = E_+ + E_-, E_theta = i (E_+ - E_-) before the inverse one.
+#include <mutex>
+
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -138,6 +140,27 @@ bool plan_radix(int N, int32_t* radix, int32_t* n_pass) {
   return n == 1;
 }
 
+// The shared-memory limit of the FFT kernels is raised once per device to the largest row
+// pair any configuration uses (2 x 4096 complex double = 2 x 8192 complex float = 128 KB):
+// the attribute is per function, so changing it per launch would race between host
+// threads that launch for simulations of different Nz.
+constexpr int kFftSmemMax = 2 * 4096 * 16;
+
+pic_status fft_configure_device() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  PIC_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && done[dev]) return PIC_OK;
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return PIC_OK;
+}
+
 pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& rc, bool inverse) {
   const pic_config& c = s->cfg;
   FftPlan plan;
@@ -151,21 +174,17 @@ pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& 
   const size_t smem = 2 * (size_t)c.Nz * s->cplx_bytes;
   if (c.precision == PIC_FP64) {
     if (inverse) {
-      cudaFuncSetAttribute(k_fft_rows<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_fft_rows<double, true><<<rows, 256, smem, s->stream>>>((const double2*)in, (double2*)out, tw, rc,
                                                                plan, rows_per_comp);
     } else {
-      cudaFuncSetAttribute(k_fft_rows<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_fft_rows<double, false><<<rows, 256, smem, s->stream>>>((const double2*)in, (double2*)out, tw, rc,
                                                                 plan, rows_per_comp);
     }
   } else {
     if (inverse) {
-      cudaFuncSetAttribute(k_fft_rows<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_fft_rows<float, true><<<rows, 256, smem, s->stream>>>((const float2*)in, (float2*)out, twf, rc,
                                                               plan, rows_per_comp);
     } else {
-      cudaFuncSetAttribute(k_fft_rows<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       k_fft_rows<float, false><<<rows, 256, smem, s->stream>>>((const float2*)in, (float2*)out, twf, rc,
                                                                plan, rows_per_comp);
     }

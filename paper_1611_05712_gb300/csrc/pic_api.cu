@@ -301,6 +301,9 @@ pic_status step_once(Sim* s, Marks* mk) {
   } while (0)
 
 }  // namespace
+
+pic_status step_cycle(Sim* s) { return step_once(s, nullptr); }
+
 }  // namespace pic
 
 using namespace pic;
@@ -355,6 +358,8 @@ pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_byt
   if ((ce = cudaMemsetAsync(s->ws + L.rho_ion, 0, G * cb, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
   if ((ce = cudaMemsetAsync(s->ws + L.dep, 0, 4 * G * cb, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
   if ((ce = cudaMemsetAsync(s->ws + L.err, 0, 256, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if ((st = fft_configure_device()) != PIC_OK) return fail(st);
+  if ((st = dht_tc_configure_device()) != PIC_OK) return fail(st);
   if ((st = launch_setup_twiddles(s)) != PIC_OK) return fail(st);
   if ((st = launch_setup_hankel(s)) != PIC_OK) return fail(st);
   if ((st = launch_setup_tables(s, cfg->order_p)) != PIC_OK) return fail(st);
@@ -372,9 +377,9 @@ pic_status pic_destroy(pic_sim* sim) {
 pic_status pic_sync(pic_sim* sim) {
   Sim* s = reinterpret_cast<Sim*>(sim);
   CHECK_SIM(s);
-  PIC_CUDA(cudaStreamSynchronize(s->stream));
   int32_t e = 0;
-  PIC_CUDA(cudaMemcpy(&e, s->ws + s->lay.err, sizeof(e), cudaMemcpyDeviceToHost));
+  PIC_CUDA(cudaMemcpyAsync(&e, s->ws + s->lay.err, sizeof(e), cudaMemcpyDeviceToHost, s->stream));
+  PIC_CUDA(cudaStreamSynchronize(s->stream));
   if (e & kErrTimeout) { set_error("a device loop hit its iteration cap (error word %d)", e); return PIC_ERR_TIMEOUT; }
   if (e) { set_error("non-finite or out-of-range values on the device (error word %d)", e); return PIC_ERR_NUMERIC; }
   return PIC_OK;

@@ -99,6 +99,7 @@ struct RowCombine {
   double caRe[6], caIm[6], cbRe[6], cbIm[6];
 };
 pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& rc, bool inverse);
+pic_status fft_configure_device();      // once per device, before any FFT launch
 
 // ---- launchers (dht.cu) ----
 // out[b] = A[b] (Nr x Nr, row-major [out][red]) * in[b] (Nr x 2Nz reals).  Element type
@@ -116,6 +117,7 @@ pic_status launch_dht(Sim* s, const DhtBatch& b);
 pic_status launch_gemm_f64(Sim* s, const DhtBatch& b, int ncols);
 // Mixed form: Y = (Ahi + Alo) X with 3-term TF32 products on tcgen05 (dht_tc.cu).
 pic_status launch_dht_tc(Sim* s, const DhtBatch& b);
+pic_status dht_tc_configure_device();   // once per device, before any tcgen05 DHT launch
 
 // ---- launchers (psatd.cu) ----
 pic_status launch_psatd(Sim* s);
