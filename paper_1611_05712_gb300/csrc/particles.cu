@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "pic_internal.cuh"
@@ -491,9 +492,83 @@ struct DepArgsF {
   int32_t id_lo, id_hi;
 };
 
+// A CTA's band of TZ z-rows (all r nodes, modes and ncomp components) in shared memory,
+// starting at row iz_lo.  Deposits to nodes in the band go to shared memory; nodes outside
+// it go straight to the global grid, so the result does not depend on how particles move.
+struct BandF {
+  float2* tile;   // [TZ][ncomp][Nm][Nr] or null (no band)
+  int iz_lo, TZ, ncomp;
+};
+
+__device__ __forceinline__ void dep_node_fb(float2* grid_cm, const GeomF& g, const BandF& bd, int comp, int m,
+                                            int j, int i, float wgt, float fold, float vre, float vim,
+                                            const float* invV) {
+  if (j < 0) { j = -1 - j; wgt *= fold; }
+  if (j >= g.Nr) return;
+  const float f = wgt * invV[j];
+  if (bd.tile) {
+    int row = i - bd.iz_lo;
+    if (row < 0) row += g.Nz;
+    if (row < bd.TZ) {
+      float* t = reinterpret_cast<float*>(bd.tile + (((size_t)row * bd.ncomp + comp) * g.Nm + m) * g.Nr + j);
+      atomicAdd(t, vre * f);
+      atomicAdd(t + 1, vim * f);
+      return;
+    }
+  }
+  float* q = reinterpret_cast<float*>(grid_cm + (size_t)j * g.Nz + i);
+  atomicAdd(q, vre * f);
+  atomicAdd(q + 1, vim * f);
+}
+
+// Band of a chunk of cell-sorted particles whose first and last cells are iz_first, iz_last:
+// rows from iz_first - 1 to iz_last + 2 (moves of up to half a cell per half step, and the
+// +1 node), at most tz_max rows; rows beyond it are simply not banded.
+__device__ __forceinline__ BandF make_band(float2* smem, int iz_first, int iz_last, const GeomF& g, int tz_max,
+                                           int ncomp) {
+  if (iz_first < 0 || iz_first >= g.Nz) iz_first = 0;
+  if (iz_last < 0 || iz_last >= g.Nz) iz_last = iz_first;
+  int span = iz_last - iz_first;
+  if (span < 0) span += g.Nz;
+  int rows = span + 4;
+  if (rows > tz_max) rows = tz_max;
+  return BandF{smem, iz_first == 0 ? g.Nz - 1 : iz_first - 1, rows, ncomp};
+}
+
+// Zero a band (all threads of the CTA).
+__device__ __forceinline__ void band_zero(const BandF& bd, const GeomF& g) {
+  if (!bd.tile) return;
+  const int n = bd.TZ * bd.ncomp * g.Nm * g.Nr;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) bd.tile[k] = make_float2(0.f, 0.f);
+}
+
+// Add a band's non-zero entries to the global grids (all threads of the CTA).  grid0 is
+// component 0 of the band; component c lives c * G further.  Consecutive threads take
+// consecutive rows of one (component, mode, r) column, which are adjacent in global memory.
+__device__ void band_flush(const BandF& bd, const GeomF& g, float2* grid0) {
+  if (!bd.tile) return;
+  const int n = bd.TZ * bd.ncomp * g.Nm * g.Nr;
+  const size_t RZ = (size_t)g.Nr * g.Nz;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const int row = k % bd.TZ;
+    const int col = k / bd.TZ;            // (comp, m, j)
+    const int j = col % g.Nr;
+    const int m = (col / g.Nr) % g.Nm;
+    const int comp = col / (g.Nr * g.Nm);
+    const float2 v = bd.tile[(((size_t)row * bd.ncomp + comp) * g.Nm + m) * g.Nr + j];
+    if (v.x == 0.f && v.y == 0.f) continue;
+    int i = bd.iz_lo + row;
+    if (i >= g.Nz) i -= g.Nz;
+    float* q = reinterpret_cast<float*>(grid0 + comp * g.G + m * RZ + (size_t)j * g.Nz + i);
+    atomicAdd(q, v.x);
+    atomicAdd(q + 1, v.y);
+  }
+}
+
 // deposit of one particle at (iz+fz, x, y) with velocity (vx, vy, vz) [m/s]
-__device__ void deposit_one_f(const GeomF& g, const DepArgsF& a, const float* invV, int iz, float fz, float x,
-                              float y, float w, float vx, float vy, float vz, bool do_rho, bool do_J) {
+__device__ void deposit_one_f(const GeomF& g, const DepArgsF& a, const float* invV, const BandF& bR,
+                              const BandF& bJ, int iz, float fz, float x, float y, float w, float vx, float vy,
+                              float vz, bool do_rho, bool do_J) {
   float r, c, s;
   polar_f(x, y, r, c, s);
   const StencilF st = stencil_f(g, iz, fz, r);
@@ -511,11 +586,11 @@ __device__ void deposit_one_f(const GeomF& g, const DepArgsF& a, const float* in
       for (int dj = 0; dj < 2; ++dj) {
         const int j = st.j0 + dj;
         const float wgt = wz * (dj ? st.wr1 : st.wr0);
-        if (do_rho) dep_node_f(a.rho + m * RZ, g, j, i, wgt, fs, qre, qim, invV);
+        if (do_rho) dep_node_fb(a.rho + m * RZ, g, bR, 0, m, j, i, wgt, fs, qre, qim, invV);
         if (do_J) {
-          dep_node_f(a.J + m * RZ, g, j, i, wgt, fv, qre * vr, qim * vr, invV);
-          dep_node_f(a.J + g.G + m * RZ, g, j, i, wgt, fv, qre * vt, qim * vt, invV);
-          dep_node_f(a.J + 2 * g.G + m * RZ, g, j, i, wgt, fs, qre * vz, qim * vz, invV);
+          dep_node_fb(a.J + m * RZ, g, bJ, 0, m, j, i, wgt, fv, qre * vr, qim * vr, invV);
+          dep_node_fb(a.J + g.G + m * RZ, g, bJ, 1, m, j, i, wgt, fv, qre * vt, qim * vt, invV);
+          dep_node_fb(a.J + 2 * g.G + m * RZ, g, bJ, 2, m, j, i, wgt, fs, qre * vz, qim * vz, invV);
         }
       }
     }
@@ -558,11 +633,23 @@ __global__ void k_permute_f32(const PartsF src, PartsF dst, const int32_t* perm,
   }
 }
 
-__global__ void k_deposit_f32(const PartsF p, int64_t np, GeomF g, DepArgsF a, const float* invV, int32_t* err) {
+// One CTA per chunk of `chunk` consecutive (cell-sorted) particles; with tz > 0 and a single
+// deposit kind the CTA accumulates into a band of tz z-rows starting one row below its
+// first particle's cell.
+__global__ void k_deposit_f32(const PartsF p, int64_t np, GeomF g, DepArgsF a, const float* invV, int32_t* err,
+                              int64_t chunk, int tz) {
+  extern __shared__ __align__(16) float2 band_smem[];
   const bool do_rho = a.rho != nullptr, do_J = a.J != nullptr;
   const float c = (float)kC;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t b0 = blockIdx.x * chunk;
+  if (b0 >= np) return;
+  const int64_t b1 = b0 + chunk < np ? b0 + chunk : np;
+  BandF none{nullptr, 0, 0, 0};
+  BandF band{nullptr, 0, 0, 0};
+  if (tz > 0 && do_rho != do_J) band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, tz, do_rho ? 1 : 3);
+  band_zero(band, g);
+  __syncthreads();
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
     const int32_t id = p.id[i];
     if (id < a.id_lo || id >= a.id_hi) continue;
     const float x = p.x[i], y = p.y[i], fz = p.fz[i];
@@ -577,8 +664,11 @@ __global__ void k_deposit_f32(const PartsF p, int64_t np, GeomF g, DepArgsF a, c
       const float ig = c * rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
       vx = ux * ig; vy = uy * ig; vz = uz * ig;
     }
-    deposit_one_f(g, a, invV, iz, fz, x, y, p.w[i], vx, vy, vz, do_rho, do_J);
+    deposit_one_f(g, a, invV, do_rho ? band : none, do_J ? band : none, iz, fz, x, y, p.w[i], vx, vy, vz,
+                  do_rho, do_J);
   }
+  __syncthreads();
+  band_flush(band, g, do_rho ? a.rho : a.J);
 }
 
 // Advance (iz, fz) by dfz cells, periodic in iz.
@@ -594,13 +684,25 @@ __device__ __forceinline__ void advance_z(int& iz, float& fz, float dfz, int Nz)
 
 // a2 + a3 (+ a4 J at x^{n+1/2}) in float: gather with mode sum, Boris push of u/c, two half
 // moves (z in cell units), specular reflection at r >= R.
+// One CTA per chunk of `chunk` consecutive (cell-sorted) particles; with tz > 0 the fused J
+// deposit accumulates into a band of tz z-rows from one row below the chunk's first cell
+// (a half step moves a particle by at most half a cell at c dt <= dz).
 __global__ void k_gather_push_f32(PartsF p, int64_t np, GeomF g, const float2* __restrict__ E,
                                   const float2* __restrict__ B, float kq, float kqc, float chdt,
-                                  float chdt_dz, DepArgsF dep, const float* invV, int fuse, int32_t* err) {
+                                  float chdt_dz, DepArgsF dep, const float* invV, int fuse, int32_t* err,
+                                  int64_t chunk, int tz) {
+  extern __shared__ __align__(16) float2 band_smem[];
   const size_t RZ = (size_t)g.Nr * g.Nz;
   const float c_light = (float)kC;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-       i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t b0 = blockIdx.x * chunk;
+  if (b0 >= np) return;
+  const int64_t b1 = b0 + chunk < np ? b0 + chunk : np;
+  const BandF none{nullptr, 0, 0, 0};
+  BandF band{nullptr, 0, 0, 0};
+  if (fuse && tz > 0) band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, tz, 3);
+  band_zero(band, g);
+  __syncthreads();
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
     float x = p.x[i], y = p.y[i], fz = p.fz[i];
     int iz = p.iz[i];
     if (!isfinite(x) || !isfinite(y) || !isfinite(fz) || iz < 0 || iz >= g.Nz) {
@@ -645,7 +747,9 @@ __global__ void k_gather_push_f32(PartsF p, int64_t np, GeomF g, const float2* _
     x += bx * chdt;
     y += by * chdt;
     advance_z(iz, fz, bz * chdt_dz, g.Nz);
-    if (fuse) deposit_one_f(g, dep, invV, iz, fz, x, y, w, bx * c_light, by * c_light, bz * c_light, false, true);
+    if (fuse)
+      deposit_one_f(g, dep, invV, none, band, iz, fz, x, y, w, bx * c_light, by * c_light, bz * c_light, false,
+                    true);
     x += bx * chdt;
     y += by * chdt;
     advance_z(iz, fz, bz * chdt_dz, g.Nz);
@@ -662,6 +766,8 @@ __global__ void k_gather_push_f32(PartsF p, int64_t np, GeomF g, const float2* _
     p.x[i] = x; p.y[i] = y; p.fz[i] = fz; p.iz[i] = iz;
     p.ux[i] = ux; p.uy[i] = uy; p.uz[i] = uz;
   }
+  __syncthreads();
+  band_flush(band, g, dep.J);
 }
 
 // float64 SoA (x y z ux uy uz w) <-> FP32 cell-relative particles
@@ -875,6 +981,28 @@ pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* ou
 
 bool is_mixed(const Sim* s) { return s->cfg.precision != PIC_FP64; }
 
+// Shared-memory bands for the deposits: chunks of 1024 cell-sorted particles per CTA, and a
+// band of at most tz z-rows of ncomp components (all modes and r nodes) within half of a
+// 96 KB budget, so that two CTAs fit on an SM.
+constexpr size_t kBandBudget = 96 * 1024;
+struct BandPlan {
+  int64_t chunk;
+  int tz;
+  size_t smem;
+};
+BandPlan band_plan(const Sim* s, int ncomp) {
+  const pic_config& c = s->cfg;
+  BandPlan bp{1024, 0, 0};
+  if (ncomp <= 0) return bp;
+  const size_t row_bytes = (size_t)ncomp * c.Nm * c.Nr * sizeof(float2);
+  // at most half the budget per CTA so that two CTAs share an SM
+  int tz = (int)std::min<size_t>(std::min<size_t>(kBandBudget / 2 / row_bytes, 8), (size_t)c.Nz);
+  if (tz < 4) return bp;   // a band must hold at least a 2-row footprint plus slack
+  bp.tz = tz;
+  bp.smem = (size_t)tz * row_bytes;
+  return bp;
+}
+
 pic_status launch_sort(Sim* s) {
   const int64_t np = s->np;
   const int ncell = s->cfg.Nz * s->cfg.Nr;
@@ -944,8 +1072,11 @@ pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, vo
     a.J = (what & PIC_DEP_J) ? s->at<float2>(s->lay.dep) + G : nullptr;
     if (a.J) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * G * sizeof(float2), s->stream));
     if (s->np == 0) return PIC_OK;
-    k_deposit_f32<<<pgrid(s->np), 256, 0, s->stream>>>(partsf_of(s, s->cur), s->np, geomf_of(s), a,
-                                                       reinterpret_cast<const float*>(inv_volume(s)), err);
+    const bool single = (a.rho != nullptr) != (a.J != nullptr);
+    const BandPlan bp = band_plan(s, single ? (a.rho ? 1 : 3) : 0);
+    k_deposit_f32<<<(int)((s->np + bp.chunk - 1) / bp.chunk), 256, bp.smem, s->stream>>>(
+        partsf_of(s, s->cur), s->np, geomf_of(s), a, reinterpret_cast<const float*>(inv_volume(s)), err, bp.chunk,
+        bp.tz);
   } else {
     DepArgs a;
     a.q = s->cfg.q;
@@ -978,9 +1109,10 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current) {
     const float kqc = (float)(c.q * c.dt / (2.0 * c.mass));
     const float chdt = (float)(0.5 * kC * c.dt);
     const float chdt_dz = (float)(0.5 * kC * c.dt / c.dz);
-    k_gather_push_f32<<<pgrid(s->np), 256, 0, s->stream>>>(
+    const BandPlan bp = band_plan(s, fuse_current ? 3 : 0);
+    k_gather_push_f32<<<(int)((s->np + bp.chunk - 1) / bp.chunk), 256, bp.smem, s->stream>>>(
         partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.E), s->at<float2>(s->lay.B), kq, kqc, chdt,
-        chdt_dz, a, reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err);
+        chdt_dz, a, reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.chunk, bp.tz);
   } else {
     DepArgs a;
     a.q = c.q;
@@ -1026,5 +1158,20 @@ pic_status launch_particles_out(Sim* s, int32_t* id_dev, int64_t n) {
 }
 
 size_t diag_acc_doubles() { return 64 + 3 * (size_t)kMaxSlices + kMaxNr; }
+
+// The band kernels may use up to kBandBudget bytes of dynamic shared memory; the limit is
+// raised once per device (a per-launch change would race between host threads).
+pic_status particles_configure_device() {
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  PIC_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && done[dev]) return PIC_OK;
+  PIC_CUDA(cudaFuncSetAttribute(k_deposit_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandBudget));
+  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandBudget));
+  if (dev >= 0 && dev < 64) done[dev] = true;
+  return PIC_OK;
+}
 
 }  // namespace pic

@@ -360,6 +360,7 @@ pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_byt
   if ((ce = cudaMemsetAsync(s->ws + L.err, 0, 256, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
   if ((st = fft_configure_device()) != PIC_OK) return fail(st);
   if ((st = dht_tc_configure_device()) != PIC_OK) return fail(st);
+  if ((st = particles_configure_device()) != PIC_OK) return fail(st);
   if ((st = launch_setup_twiddles(s)) != PIC_OK) return fail(st);
   if ((st = launch_setup_hankel(s)) != PIC_OK) return fail(st);
   if ((st = launch_setup_tables(s, cfg->order_p)) != PIC_OK) return fail(st);

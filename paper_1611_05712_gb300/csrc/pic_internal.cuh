@@ -132,6 +132,7 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current);
 pic_status launch_diag(Sim* s, int32_t id_lo, int32_t id_hi, pic_diag* out, double* slice_sigma,
                        int32_t max_slices);
 pic_status build_inv_volume(Sim* s);                        // once, at init
+pic_status particles_configure_device();                    // once per device
 pic_status launch_particles_in(Sim* s, const int32_t* id_dev, int64_t n);   // mixed: stage64 -> FP32
 pic_status launch_particles_out(Sim* s, int32_t* id_dev, int64_t n);        // mixed: FP32 -> stage64
 
