@@ -6,8 +6,10 @@
 // interleaved).  Here it is computed transposed,
 //     D[c][n] = sum_j Xf[j][c] A[n][j]      (D = Yf^T, M = columns c, N = rows n, K = j),
 // so both tensor-core operands are K-major: the A-operand tile (128 columns c x 32 j) is
-// transposed while it is staged into shared memory, and the B operand (rows of A) is
-// K-major as stored.  Both use the 128-byte swizzled canonical layout.
+// transposed while it is staged into shared memory by the CTA's threads, and the B operand
+// (rows of A, K-major as stored, row pitch a multiple of 16 bytes) is copied by the tensor
+// memory accelerator (2-D tiled copies, completion counted in mbarrier transaction bytes;
+// coordinates past Nr read zero).  Both use the 128-byte swizzled canonical layout.
 //
 // Precision: 3-term TF32 products.  Every float operand x is split as hi = x rounded to
 // TF32 and lo = x - hi (exact in float); D accumulates Xhi*Ahi + Xhi*Alo + Xlo*Ahi in FP32
@@ -15,12 +17,15 @@
 //
 // One CTA owns a 128-column x N_T tile of D (N_T <= 256 TMEM columns) for one batch; K is
 // consumed in chunks of 32 through two shared-memory stages: all 256 threads stage chunk
-// k+1 while the tensor core runs chunk k.  One thread issues the MMAs and commits them to
+// k+1 while the tensor core runs chunk k, and the data-panel loads of chunk k+2 are issued
+// before the wait for chunk k+1's stage.  One thread issues the MMAs and commits them to
 // an mbarrier per stage; every wait on an mbarrier is bounded and sets the device error
 // word on timeout.  The epilogue reads TMEM with tcgen05.ld (warp w owns TMEM lanes
 // 32*(w%4)..+31) and writes Yf[n][c] so that the 32 lanes of a warp store 32 consecutive c.
+#include <cuda.h>
 #include <stdint.h>
 
+#include <cstring>
 #include <mutex>
 
 #include "pic_internal.cuh"
@@ -107,7 +112,30 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams P, int32_t* err) {
+// One arrival on `bar` that also expects `bytes` of asynchronous-copy transactions.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// 2-D tiled tensor copy global -> shared (box at inner coordinate x, row y), completing
+// its bytes on `bar`.  x is a multiple of 32 floats, so the start is 128-byte aligned.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Tensor maps of the batch's split matrices (hi, lo), passed by value as a grid constant.
+struct TcMaps {
+  Sim::TensorMapBytes hi[24];
+  Sim::TensorMapBytes lo[24];
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams P, const __grid_constant__ TcMaps maps,
+                                                           int32_t* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   // 1024-byte aligned carve-up: [stage][A_hi | A_lo | B_hi | B_lo], then barriers
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -115,8 +143,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams 
   const uint32_t a_bytes = kTcM * 128;            // 16 KB
   const uint32_t b_bytes = (uint32_t)P.NT * 128;  // up to 32 KB
   const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * stage_bytes);   // [2] per-stage MMA done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  // bars[0..1]: per-stage "MMAs that read this stage are done"; bars[2..3]: per-stage
+  // "matrix tiles have landed" (transaction counted)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * stage_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int b = blockIdx.z;
@@ -124,8 +154,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams 
   const int m_tile = blockIdx.x;
   const int c0 = m_tile * kTcM, n0 = n_tile * P.NT;
   const float* __restrict__ X = static_cast<const float*>(bt.X[b]);
-  const float* __restrict__ Ahi = static_cast<const float*>(bt.A[b]);
-  const float* __restrict__ Alo = static_cast<const float*>(bt.Alo[b]);
   float* __restrict__ Y = static_cast<float*>(bt.Y[b]);
 
   if (warp == 0) {
@@ -137,7 +165,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams 
   if (tid == 0) {
     mbar_init(&bars[0], 1);
     mbar_init(&bars[1], 1);
+    mbar_init(&bars[2], 1);
+    mbar_init(&bars[3], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.hi[b])) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.lo[b])) : "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -146,6 +178,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams 
   const uint32_t idesc = make_idesc(kTcM, P.NT);
   const int nK = (P.Nr + kTcK - 1) / kTcK;
   bool ok = true;
+  int issued = -1, committed = -1;   // last chunk whose matrix copies / MMAs were issued (block-uniform)
+
+  // data-panel values of the next chunk, loaded ahead of the wait for a free stage:
+  // item it = tid + q*256 covers row c0 + (it % 128), 16-byte chunk it / 128 (4 values of j)
+  float pv[4][4];
+  auto load_chunk = [&](int kc) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int it = tid + q * kTcThreads;
+      const int c = c0 + (it & (kTcM - 1)), ch = it >> 7;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = kc * kTcK + ch * 4 + e;
+        pv[q][e] = (c < P.Nc && j < P.Nr) ? X[(size_t)j * P.Nc + c] : 0.f;
+      }
+    }
+  };
+  if (nK > 0) load_chunk(0);
 
   for (int kc = 0; kc < nK && ok; ++kc) {
     const int st = kc & 1;
@@ -158,51 +208,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams 
     unsigned char* sB = sAlo + a_bytes;
     unsigned char* sBlo = sB + b_bytes;
     const int k0 = kc * kTcK;
-    // A operand (transposed X): item = (row c, 16-byte chunk of 4 consecutive j)
-    for (int it = tid; it < kTcM * 8; it += kTcThreads) {
+    if (tid == 0) {   // matrix tiles (rows n0.., columns k0..k0+31; zero fill beyond Nr)
+      mbar_arrive_expect_tx(&bars[2 + st], 2 * b_bytes);
+      tma_load_2d(sB, &maps.hi[b], k0, n0, &bars[2 + st]);
+      tma_load_2d(sBlo, &maps.lo[b], k0, n0, &bars[2 + st]);
+    }
+    issued = kc;
+    // A operand (transposed X): split the prefetched values and store them swizzled
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int it = tid + q * kTcThreads;
       const int row = it & (kTcM - 1), ch = it >> 7;
-      const int c = c0 + row;
-      float v[4], lo[4];
+      float hv[4], lv[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const int j = k0 + ch * 4 + e;
-        v[e] = (c < P.Nc && j < P.Nr) ? X[(size_t)j * P.Nc + c] : 0.f;
-        const float h = tf32_hi(v[e]);
-        lo[e] = v[e] - h;
-        v[e] = h;
+        hv[e] = tf32_hi(pv[q][e]);
+        lv[e] = pv[q][e] - hv[e];
       }
       const uint32_t off = sw128_off(row, ch);
-      *reinterpret_cast<float4*>(sA + off) = make_float4(v[0], v[1], v[2], v[3]);
-      *reinterpret_cast<float4*>(sAlo + off) = make_float4(lo[0], lo[1], lo[2], lo[3]);
+      *reinterpret_cast<float4*>(sA + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+      *reinterpret_cast<float4*>(sAlo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
     }
-    // B operand (rows n of the split matrix): item = (row n, 16-byte chunk)
-    for (int it = tid; it < P.NT * 8; it += kTcThreads) {
-      const int row = it >> 3, ch = it & 7;
-      const int n = n0 + row, j = k0 + ch * 4;
-      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-      if (n < P.Nr) {
-        const float* ph = Ahi + (size_t)n * P.Nr + j;
-        const float* pl = Alo + (size_t)n * P.Nr + j;
-        if (j + 3 < P.Nr && ((P.Nr & 3) == 0)) {
-          h = *reinterpret_cast<const float4*>(ph);
-          l = *reinterpret_cast<const float4*>(pl);
-        } else {
-          float hv[4], lv[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            hv[e] = (j + e < P.Nr) ? ph[e] : 0.f;
-            lv[e] = (j + e < P.Nr) ? pl[e] : 0.f;
-          }
-          h = make_float4(hv[0], hv[1], hv[2], hv[3]);
-          l = make_float4(lv[0], lv[1], lv[2], lv[3]);
-        }
-      }
-      const uint32_t off = sw128_off(row, ch);
-      *reinterpret_cast<float4*>(sB + off) = h;
-      *reinterpret_cast<float4*>(sBlo + off) = l;
-    }
+    if (kc + 1 < nK) load_chunk(kc + 1);   // in flight while this chunk is multiplied
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
+    const bool landed = (tid == 0) ? mbar_wait(&bars[2 + st], (uint32_t)((kc >> 1) & 1)) : true;
+    if (!__syncthreads_and(landed)) { ok = false; break; }
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a_hi = smem_u32(sA), a_lo = smem_u32(sAlo), b_hi = smem_u32(sB), b_lo = smem_u32(sBlo);
@@ -216,14 +246,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams 
       }
       mma_commit(&bars[st]);
     }
+    committed = kc;
   }
   // wait for the last chunk's commit (it covers every MMA issued before it)
   if (ok && nK > 0) ok = mbar_wait(&bars[(nK - 1) & 1], (uint32_t)(((nK - 1) >> 1) & 1));
   ok = __syncthreads_and(ok);
   if (!ok) {
-    if (tid == 0) atomicOr(err, kErrTimeout);
-    // wait (bounded) for anything still in flight before releasing tensor memory
-    if (nK > 0) mbar_wait(&bars[(nK - 1) & 1], (uint32_t)(((nK - 1) >> 1) & 1));
+    if (tid == 0) {
+      atomicOr(err, kErrTimeout);
+      // wait (bounded) for the copies and MMAs still in flight before the shared and
+      // tensor memory are released
+      if (issued > committed) mbar_wait(&bars[2 + (issued & 1)], (uint32_t)((issued >> 1) & 1));
+      if (committed >= 0) mbar_wait(&bars[committed & 1], (uint32_t)((committed >> 1) & 1));
+    }
+    __syncthreads();
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
@@ -276,21 +312,94 @@ pic_status dht_tc_configure_device() {
   return PIC_OK;
 }
 
+namespace {
+
+// N tiling shared by the tensor maps and the launches: n_tiles tiles of NT rows of A.
+void tc_tiles(int Nr, int* n_tiles, int* NT) {
+  *n_tiles = (Nr + kTcMaxN - 1) / kTcMaxN;
+  const int per = (Nr + *n_tiles - 1) / *n_tiles;
+  *NT = (per + 15) / 16 * 16;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+}  // namespace
+
+// Tensor maps of the split matrices: 2-D float32 views (Nr columns j, Nr rows n, row
+// pitch split_pitch(Nr)), box 32 j x NT rows, 128-byte swizzle; coordinates past Nr read 0.
+pic_status dht_tc_make_maps(Sim* s) {
+  std::memset(s->tmaps, 0, sizeof(s->tmaps));
+  if (s->cfg.precision == PIC_FP64) return PIC_OK;
+  EncodeTiledFn encode = encode_fn();
+  if (!encode) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return PIC_ERR_CUDA;
+  }
+  const int Nr = s->cfg.Nr, pitch = split_pitch(Nr);
+  int n_tiles = 0, NT = 0;
+  tc_tiles(Nr, &n_tiles, &NT);
+  const size_t mat_floats = (size_t)Nr * pitch;
+  for (int dir = 0; dir < 2; ++dir) {
+    for (int mi = 0; mi < s->cfg.Nm * 3; ++mi) {
+      for (int part = 0; part < 2; ++part) {
+        const size_t off = dir == 0 ? (part == 0 ? s->lay.mfwd_hi : s->lay.mfwd_lo)
+                                    : (part == 0 ? s->lay.binv_hi : s->lay.binv_lo);
+        float* g = s->at<float>(off) + (size_t)mi * mat_floats;
+        const cuuint64_t dims[2] = {(cuuint64_t)Nr, (cuuint64_t)Nr};
+        const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)NT};
+        const cuuint32_t estr[2] = {1, 1};
+        CUtensorMap* map = reinterpret_cast<CUtensorMap*>(s->tmaps[dir * kMaxModes * 3 + mi][part].b);
+        const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, g, dims, strides, box, estr,
+                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+          set_error("cuTensorMapEncodeTiled failed (%d) for split matrix %d", (int)r, dir * kMaxModes * 3 + mi);
+          return PIC_ERR_CUDA;
+        }
+      }
+    }
+  }
+  return PIC_OK;
+}
+
 pic_status launch_dht_tc(Sim* s, const DhtBatch& b) {
   const int Nr = s->cfg.Nr, Nc = 2 * s->cfg.Nz;
   TcParams P;
   P.Nr = Nr;
   P.Nc = Nc;
-  P.n_tiles = (Nr + kTcMaxN - 1) / kTcMaxN;
-  const int per = (Nr + P.n_tiles - 1) / P.n_tiles;
-  P.NT = (per + 15) / 16 * 16;
+  tc_tiles(Nr, &P.n_tiles, &P.NT);
   int tc = 32;
   while (tc < P.NT) tc <<= 1;
   P.tmem_cols = tc;
   P.m_tiles = (Nc + kTcM - 1) / kTcM;
+  TcMaps maps;
+  for (int i = 0; i < b.n; ++i) {
+    if (b.mat[i] < 0 || b.mat[i] >= 2 * kMaxModes * 3) {
+      set_error("DHT batch entry %d has no split matrix", i);
+      return PIC_ERR_ARG;
+    }
+    maps.hi[i] = s->tmaps[b.mat[i]][0];
+    maps.lo[i] = s->tmaps[b.mat[i]][1];
+  }
   const size_t smem = dht_tc_smem_bytes(P.NT);
   dim3 grid(P.m_tiles, P.n_tiles, b.n);
-  k_dht_tc<<<grid, kTcThreads, smem, s->stream>>>(b, P, s->at<int32_t>(s->lay.err));
+  k_dht_tc<<<grid, kTcThreads, smem, s->stream>>>(b, P, maps, s->at<int32_t>(s->lay.err));
   PIC_LAUNCHED(s);
   return PIC_OK;
 }

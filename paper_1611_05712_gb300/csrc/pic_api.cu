@@ -106,10 +106,10 @@ Layout make_layout(const pic_config& c) {
     L.tz_f = take((size_t)c.Nz * 4);
     L.tr_f = take((size_t)c.Nm * c.Nr * 4);
     L.twiddle_f = take((size_t)c.Nz * 8);
-    L.mfwd_hi = take((size_t)c.Nm * 3 * Nr2 * 4);
-    L.mfwd_lo = take((size_t)c.Nm * 3 * Nr2 * 4);
-    L.binv_hi = take((size_t)c.Nm * 3 * Nr2 * 4);
-    L.binv_lo = take((size_t)c.Nm * 3 * Nr2 * 4);
+    L.mfwd_hi = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
+    L.mfwd_lo = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
+    L.binv_hi = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
+    L.binv_lo = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
   } else {
     for (int b = 0; b < 2; ++b) {
       for (int k = 0; k < 7; ++k) L.part[b][k] = take(cap * 8);
@@ -184,8 +184,10 @@ pic_status dht_forward(Sim* s, int n_comp) {
       if (s->cfg.precision == PIC_FP64) {
         b.A[b.n] = s->at<double>(s->lay.mfwd) + moff;
       } else {
-        b.A[b.n] = s->at<float>(s->lay.mfwd_hi) + moff;
-        b.Alo[b.n] = s->at<float>(s->lay.mfwd_lo) + moff;
+        const size_t foff = ((size_t)m * 3 + slot_of[comp]) * c.Nr * split_pitch(c.Nr);
+        b.A[b.n] = s->at<float>(s->lay.mfwd_hi) + foff;
+        b.Alo[b.n] = s->at<float>(s->lay.mfwd_lo) + foff;
+        b.mat[b.n] = (int16_t)(m * 3 + slot_of[comp]);
       }
       b.X[b.n] = s->at<char>(s->lay.tmp) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       b.Y[b.n] = s->at<char>(s->lay.srch) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
@@ -213,8 +215,10 @@ pic_status dht_inverse(Sim* s) {
       if (s->cfg.precision == PIC_FP64) {
         b.A[b.n] = s->at<double>(s->lay.binv) + moff;
       } else {
-        b.A[b.n] = s->at<float>(s->lay.binv_hi) + moff;
-        b.Alo[b.n] = s->at<float>(s->lay.binv_lo) + moff;
+        const size_t foff = ((size_t)m * 3 + slot_of[comp % 3]) * c.Nr * split_pitch(c.Nr);
+        b.A[b.n] = s->at<float>(s->lay.binv_hi) + foff;
+        b.Alo[b.n] = s->at<float>(s->lay.binv_lo) + foff;
+        b.mat[b.n] = (int16_t)(kMaxModes * 3 + m * 3 + slot_of[comp % 3]);
       }
       b.X[b.n] = s->at<char>(s->lay.Eh) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       b.Y[b.n] = s->at<char>(s->lay.tmp) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
@@ -360,6 +364,7 @@ pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_byt
   if ((ce = cudaMemsetAsync(s->ws + L.err, 0, 256, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
   if ((st = fft_configure_device()) != PIC_OK) return fail(st);
   if ((st = dht_tc_configure_device()) != PIC_OK) return fail(st);
+  if ((st = dht_tc_make_maps(s)) != PIC_OK) return fail(st);
   if ((st = particles_configure_device()) != PIC_OK) return fail(st);
   if ((st = launch_setup_twiddles(s)) != PIC_OK) return fail(st);
   if ((st = launch_setup_hankel(s)) != PIC_OK) return fail(st);

@@ -45,6 +45,10 @@ struct Layout {
   size_t total;
 };
 
+// Row pitch (floats) of the split DHT matrices of the mixed form: Nr rounded up to a
+// multiple of 4 so that rows start on 16-byte boundaries (tensor-memory-access copies).
+inline int split_pitch(int Nr) { return (Nr + 3) / 4 * 4; }
+
 // FP32 particle array indices of the mixed form.
 enum { kPfIz = 0, kPfFz = 1, kPfX = 2, kPfY = 3, kPfUx = 4, kPfUy = 5, kPfUz = 6, kPfW = 7, kPfId = 8 };
 
@@ -62,6 +66,11 @@ struct Sim {
   int32_t n_radix;
   int32_t radix[kMaxRadixPasses];
   size_t cplx_bytes;       // 16 (FP64) or 8 (mixed)
+  // mixed form: encoded 2-D tensor maps (CUtensorMap, 128 B each) of the split DHT
+  // matrices, [matrix id][hi, lo], built once at init
+  struct alignas(64) TensorMapBytes {
+    unsigned char b[128];
+  } tmaps[2 * kMaxModes * 3][2];
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   size_t grid_elems() const { return (size_t)cfg.Nm * cfg.Nr * cfg.Nz; }
@@ -110,6 +119,7 @@ struct DhtBatch {
   const void* Alo[24];   // null: no low part
   const void* X[24];
   void* Y[24];
+  int16_t mat[24];       // mixed form: matrix id (fwd: m*3+slot, inv: kMaxModes*3 + m*3+slot)
 };
 // The DHT of the current precision form (FP64 SIMT, or 3-term TF32 on tcgen05).
 pic_status launch_dht(Sim* s, const DhtBatch& b);
@@ -118,6 +128,7 @@ pic_status launch_gemm_f64(Sim* s, const DhtBatch& b, int ncols);
 // Mixed form: Y = (Ahi + Alo) X with 3-term TF32 products on tcgen05 (dht_tc.cu).
 pic_status launch_dht_tc(Sim* s, const DhtBatch& b);
 pic_status dht_tc_configure_device();   // once per device, before any tcgen05 DHT launch
+pic_status dht_tc_make_maps(Sim* s);     // once per handle: tensor maps of the split matrices
 
 // ---- launchers (psatd.cu) ----
 pic_status launch_psatd(Sim* s);

@@ -360,19 +360,24 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
     out[i] = (float)in[i];
 }
 
-// Split of an FP64 matrix for 3-term TF32 products: hi = the value rounded to TF32
-// (10 explicit mantissa bits, low 13 bits of the float zero), lo = float(value - hi).
+// Split of FP64 matrices (rows of Nr) for 3-term TF32 products: hi = the value rounded to
+// TF32 (10 explicit mantissa bits, low 13 bits of the float zero), lo = float(value - hi).
+// Output rows have a pitch of `pitch` >= Nr floats (16-byte multiple for the tensor-memory
+// copies); the padding is zero.
 __global__ void k_split_tf32(const double* __restrict__ in, float* __restrict__ hi, float* __restrict__ lo,
-                             size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const double v = in[i];
+                             size_t rows, int Nr, int pitch) {
+  const size_t n = rows * (size_t)pitch;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const int col = (int)(o % pitch);
+    if (col >= Nr) { hi[o] = 0.f; lo[o] = 0.f; continue; }
+    const double v = in[(o / pitch) * Nr + col];
     const float f = (float)v;
     // round-to-nearest-even at bit 13 of the float's bit pattern (finite values)
     uint32_t b = __float_as_uint(f);
     b = (b + 0x0fffu + ((b >> 13) & 1u)) & 0xffffe000u;
     const float h = __uint_as_float(b);
-    hi[i] = h;
-    lo[i] = (float)(v - (double)h);
+    hi[o] = h;
+    lo[o] = (float)(v - (double)h);
   }
 }
 
@@ -383,16 +388,18 @@ inline int conv_grid(size_t n) { return (int)std::min<size_t>(blocks_for(n, 256)
 // Mixed form: float copies of k_perp, the filter factor in r and the split DHT matrices.
 pic_status convert_hankel_tables(Sim* s) {
   const pic_config& c = s->cfg;
-  const size_t nmn = (size_t)c.Nm * c.Nr, nmat = (size_t)c.Nm * 3 * c.Nr * c.Nr;
+  const size_t nmn = (size_t)c.Nm * c.Nr, rows = (size_t)c.Nm * 3 * c.Nr;
+  const int pitch = split_pitch(c.Nr);
+  const size_t nmat = rows * pitch;
   k_to_float<<<conv_grid(nmn), 256, 0, s->stream>>>(s->at<double>(s->lay.kperp), s->at<float>(s->lay.kperp_f), nmn);
   PIC_LAUNCHED(s);
   k_to_float<<<conv_grid(nmn), 256, 0, s->stream>>>(s->at<double>(s->lay.tr), s->at<float>(s->lay.tr_f), nmn);
   PIC_LAUNCHED(s);
   k_split_tf32<<<conv_grid(nmat), 256, 0, s->stream>>>(s->at<double>(s->lay.mfwd), s->at<float>(s->lay.mfwd_hi),
-                                                         s->at<float>(s->lay.mfwd_lo), nmat);
+                                                         s->at<float>(s->lay.mfwd_lo), rows, c.Nr, pitch);
   PIC_LAUNCHED(s);
   k_split_tf32<<<conv_grid(nmat), 256, 0, s->stream>>>(s->at<double>(s->lay.binv), s->at<float>(s->lay.binv_hi),
-                                                         s->at<float>(s->lay.binv_lo), nmat);
+                                                         s->at<float>(s->lay.binv_lo), rows, c.Nr, pitch);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }
