@@ -123,6 +123,214 @@ __global__ void __launch_bounds__(256) k_fft_rows(const typename Vec2<R>::T* __r
   }
 }
 
+// ---- power-of-two rows ----
+// Self-sorting Stockham passes of radix 8 (then one radix-2 or radix-4 pass when log2 N is
+// not a multiple of 3).  Pass p (radix R, L = product of the earlier radices) maps
+//   y_s = sum_r v_r w_R^{rs},  v_r = x[t + r N/R] w_{LR}^{r k},  k = t mod L, j = t / L,
+//   out[j L R + s L + k] = y_s,
+// so the first pass reads a row in natural order and the last pass (L = N/R, j = 0)
+// writes it in natural order: both go straight between global memory and registers.
+// Each thread holds E values of its row; the intermediate passes exchange them through one
+// row buffer in shared memory, padded by one element per 128 bytes against bank conflicts.
+// The twiddles w_{LR}^{rk} of pass (R, L) sit at table entry L-1 + (r-1) L + k (the
+// tables of all passes tile entries 0..N-2), so a warp reads consecutive entries.
+constexpr int kFftThreads = 256;
+
+template <typename C2, bool INV> __device__ __forceinline__ C2 conj_if(C2 w) {
+  if (INV) w.y = -w.y;
+  return w;
+}
+
+template <typename C2, bool INV> __device__ __forceinline__ void dft2(C2* v) {
+  const C2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <typename C2, bool INV> __device__ __forceinline__ void dft4(C2* v) {
+  const C2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+  const C2 s13 = cadd(v[1], v[3]), d13 = mul_mi<C2, INV>(csub(v[1], v[3]));
+  v[0] = cadd(s02, s13);
+  v[1] = cadd(d02, d13);
+  v[2] = csub(s02, s13);
+  v[3] = csub(d02, d13);
+}
+
+// 8-point DFT as two 4-point DFTs: even outputs from a_r = v_r + v_{r+4}, odd outputs from
+// b_r = (v_r - v_{r+4}) w_8^r.
+template <typename C2, bool INV> __device__ __forceinline__ void dft8(C2* v) {
+  using R = decltype(v[0].x);
+  const R h = (R)0.70710678118654752440;   // 1/sqrt(2)
+  C2 a[4], b[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    a[r] = cadd(v[r], v[r + 4]);
+    b[r] = csub(v[r], v[r + 4]);
+  }
+  {   // w_8^1 = (1 -+ i)/sqrt(2)
+    const C2 x = b[1];
+    if (INV) { b[1].x = h * (x.x - x.y); b[1].y = h * (x.x + x.y); }
+    else     { b[1].x = h * (x.x + x.y); b[1].y = h * (x.y - x.x); }
+  }
+  b[2] = mul_mi<C2, INV>(b[2]);   // w_8^2 = -+ i
+  {   // w_8^3 = (-1 -+ i)/sqrt(2)
+    const C2 x = b[3];
+    if (INV) { b[3].x = -h * (x.x + x.y); b[3].y = h * (x.x - x.y); }
+    else     { b[3].x = h * (x.y - x.x); b[3].y = -h * (x.x + x.y); }
+  }
+  dft4<C2, INV>(a);
+  dft4<C2, INV>(b);
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    v[2 * r] = a[r];
+    v[2 * r + 1] = b[r];
+  }
+}
+
+// Per-row context of the power-of-two kernel.
+template <typename C2> struct RowCtx {
+  const C2* a;    // source rows of the combination (b may be null)
+  const C2* b;
+  C2 ca, cb;
+  C2* o;          // destination row
+  C2* buf;        // padded shared row buffer
+  int N, tr, TR;
+  bool active;    // false for the idle row slots of the last CTA
+};
+
+template <int PS> __device__ __forceinline__ int padded(int i) { return i + (i >> PS); }
+
+// Inputs of the first pass (radix 8): v[8q + r] = (ca a + cb b)[t + r N/8], t = tr + q TR.
+template <typename C2, int E>
+__device__ __forceinline__ void pow2_load_global(C2 (&v)[E], const RowCtx<C2>& c) {
+  using Re = decltype(v[0].x);
+  const int N8 = c.N >> 3;
+#pragma unroll
+  for (int q = 0; q < E / 8; ++q) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int idx = c.tr + q * c.TR + r * N8;
+      C2 x;
+      x.x = (Re)0; x.y = (Re)0;
+      if (c.active) {
+        x = cmul(c.ca, c.a[idx]);
+        if (c.b) x = cadd(x, cmul(c.cb, c.b[idx]));
+      }
+      v[q * 8 + r] = x;
+    }
+  }
+}
+
+// Inputs of a later pass of radix R from the shared row buffer.
+template <typename C2, int E, int R, int PS>
+__device__ __forceinline__ void pow2_load_shared(C2 (&v)[E], const RowCtx<C2>& c) {
+  const int NR = c.N / R;
+#pragma unroll
+  for (int q = 0; q < E / R; ++q) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[q * R + r] = c.buf[padded<PS>(c.tr + q * c.TR + r * NR)];
+  }
+}
+
+// Twiddles w_{LR}^{rk} and the R-point DFTs of a pass.
+template <typename C2, bool INV, int E, int R>
+__device__ __forceinline__ void pow2_butterflies(C2 (&v)[E], const RowCtx<C2>& c, const C2* __restrict__ twp,
+                                                 int L) {
+#pragma unroll
+  for (int q = 0; q < E / R; ++q) {
+    if (L > 1) {
+      const int k = (c.tr + q * c.TR) & (L - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], conj_if<C2, INV>(twp[L - 1 + (r - 1) * L + k]));
+    }
+    if (R == 8) dft8<C2, INV>(&v[q * R]);
+    else if (R == 4) dft4<C2, INV>(&v[q * R]);
+    else dft2<C2, INV>(&v[q * R]);
+  }
+}
+
+// Outputs of a pass: out[j L R + s L + k] = y_s, to the shared buffer or (last pass, L =
+// N/R) to the destination row, scaled by 1/N for the inverse transform.
+template <typename C2, bool INV, int E, int R, int PS>
+__device__ __forceinline__ void pow2_store(C2 (&v)[E], const RowCtx<C2>& c, int L, int lgL, bool last) {
+  using Re = decltype(v[0].x);
+  const Re scale = INV ? (Re)1 / (Re)c.N : (Re)1;
+#pragma unroll
+  for (int q = 0; q < E / R; ++q) {
+    const int t = c.tr + q * c.TR;
+    const int base = ((t >> lgL) * R) * L + (t & (L - 1));
+#pragma unroll
+    for (int s2 = 0; s2 < R; ++s2) {
+      const int idx = base + s2 * L;
+      if (last) {
+        if (c.active) {
+          C2 y = v[q * R + s2];
+          y.x *= scale;
+          y.y *= scale;
+          c.o[idx] = y;
+        }
+      } else {
+        c.buf[padded<PS>(idx)] = v[q * R + s2];
+      }
+    }
+  }
+}
+
+template <typename C2, bool INV, int E, int R, int PS>
+__device__ __forceinline__ void pow2_pass(C2 (&v)[E], const RowCtx<C2>& c, const C2* __restrict__ twp, int L,
+                                          int lgL, bool last) {
+  pow2_butterflies<C2, INV, E, R>(v, c, twp, L);
+  pow2_store<C2, INV, E, R, PS>(v, c, L, lgL, last);
+}
+
+// One CTA of 256 threads transforms 256 E / N rows (N <= 2048: E = 8; N = 4096, 8192: one
+// row with E = 16, 32).
+template <typename R, bool INV, int E>
+__global__ void __launch_bounds__(kFftThreads, E == 8 ? 4 : (E == 16 ? 2 : 1)) k_fft_pow2(const typename Vec2<R>::T* __restrict__ in,
+                                                          typename Vec2<R>::T* __restrict__ out,
+                                                          const typename Vec2<R>::T* __restrict__ twp,
+                                                          RowCombine rc, int N, int lgN, int rows,
+                                                          int rows_per_comp) {
+  using C2 = typename Vec2<R>::T;
+  constexpr int PS = sizeof(R) == 4 ? 4 : 3;   // one pad element per 128 bytes
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RowCtx<C2> c;
+  c.N = N;
+  c.TR = N / E;
+  const int lr = threadIdx.x / c.TR;
+  c.tr = threadIdx.x - lr * c.TR;
+  const int row = blockIdx.x * (kFftThreads / c.TR) + lr;
+  c.active = row < rows;
+  c.buf = reinterpret_cast<C2*>(smem_raw) + (size_t)lr * (N + (N >> PS));
+  const int rrow = c.active ? row : 0;
+  const int comp = rrow / rows_per_comp;
+  const int rr = rrow - comp * rows_per_comp;
+  c.a = in + ((size_t)rc.srcA[comp] * rows_per_comp + rr) * N;
+  const int sb = rc.srcB[comp];
+  c.b = sb >= 0 ? in + ((size_t)sb * rows_per_comp + rr) * N : nullptr;
+  c.ca.x = (R)rc.caRe[comp]; c.ca.y = (R)rc.caIm[comp];
+  c.cb.x = (R)rc.cbRe[comp]; c.cb.y = (R)rc.cbIm[comp];
+  c.o = out + (size_t)rrow * N;
+  C2 v[E];
+  const int n8 = lgN / 3, rem = lgN - 3 * n8;   // n8 >= 1 radix-8 passes, then radix 2^rem
+  pow2_load_global<C2, E>(v, c);
+  int L = 1, lgL = 0;
+  for (int p = 0; p < n8; ++p) {
+    const bool last = p == n8 - 1 && rem == 0;
+    pow2_pass<C2, INV, E, 8, PS>(v, c, twp, L, lgL, last);
+    if (last) return;
+    L <<= 3;
+    lgL += 3;
+    __syncthreads();   // the pass's outputs are in the buffer
+    if (p + 1 < n8) pow2_load_shared<C2, E, 8, PS>(v, c);
+    else if (rem == 2) pow2_load_shared<C2, E, 4, PS>(v, c);
+    else pow2_load_shared<C2, E, 2, PS>(v, c);
+    __syncthreads();   // the buffer is read in full before it is rewritten
+  }
+  if (rem == 2) pow2_pass<C2, INV, E, 4, PS>(v, c, twp, L, lgL, true);
+  else pow2_pass<C2, INV, E, 2, PS>(v, c, twp, L, lgL, true);
+}
+
 }  // namespace
 
 // Factor Nz into passes of radix 4, 2, 3, 5, 7 (the Stockham order is free).
@@ -157,18 +365,66 @@ pic_status fft_configure_device() {
   PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
+  // power-of-two rows: one padded row buffer, largest for Nz = 8192 float / 4096 double
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<float, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<float, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
   if (dev >= 0 && dev < 64) done[dev] = true;
   return PIC_OK;
 }
 
+namespace {
+
+template <typename R, bool INV, int E>
+void launch_pow2(Sim* s, const void* in, void* out, const void* twp, const RowCombine& rc, int rows,
+                 int rows_per_comp) {
+  using C2 = typename Vec2<R>::T;
+  const int N = s->cfg.Nz;
+  int lgN = 0;
+  while ((1 << lgN) < N) ++lgN;
+  constexpr int PS = sizeof(R) == 4 ? 4 : 3;
+  const int rpc = kFftThreads / (N / E);
+  const size_t smem = (size_t)rpc * (N + (N >> PS)) * sizeof(C2);
+  const int grid = (rows + rpc - 1) / rpc;
+  k_fft_pow2<R, INV, E><<<grid, kFftThreads, smem, s->stream>>>((const C2*)in, (C2*)out, (const C2*)twp, rc, N,
+                                                                lgN, rows, rows_per_comp);
+}
+
+template <typename R, bool INV>
+void launch_pow2_e(Sim* s, const void* in, void* out, const void* twp, const RowCombine& rc, int rows,
+                   int rows_per_comp) {
+  const int N = s->cfg.Nz;
+  if (N <= 2048) launch_pow2<R, INV, 8>(s, in, out, twp, rc, rows, rows_per_comp);
+  else if (N == 4096 || sizeof(R) == 8) launch_pow2<R, INV, 16>(s, in, out, twp, rc, rows, rows_per_comp);
+  else launch_pow2<R, INV, sizeof(R) == 8 ? 16 : 32>(s, in, out, twp, rc, rows, rows_per_comp);
+}
+
+}  // namespace
+
+bool fft_is_pow2(int N) { return N >= 8 && (N & (N - 1)) == 0; }
+
 pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& rc, bool inverse) {
   const pic_config& c = s->cfg;
+  const int rows_per_comp = c.Nm * c.Nr;
+  const int rows = rc.n_out * rows_per_comp;
+  if (fft_is_pow2(c.Nz)) {
+    if (c.precision == PIC_FP64) {
+      const void* twp = s->at<double2>(s->lay.twp);
+      if (inverse) launch_pow2_e<double, true>(s, in, out, twp, rc, rows, rows_per_comp);
+      else launch_pow2_e<double, false>(s, in, out, twp, rc, rows, rows_per_comp);
+    } else {
+      const void* twp = s->at<float2>(s->lay.twp_f);
+      if (inverse) launch_pow2_e<float, true>(s, in, out, twp, rc, rows, rows_per_comp);
+      else launch_pow2_e<float, false>(s, in, out, twp, rc, rows, rows_per_comp);
+    }
+    PIC_LAUNCHED(s);
+    return PIC_OK;
+  }
   FftPlan plan;
   plan.N = c.Nz;
   plan.n_pass = s->n_radix;
   for (int i = 0; i < kMaxRadixPasses; ++i) plan.radix[i] = s->radix[i];
-  const int rows_per_comp = c.Nm * c.Nr;
-  const int rows = rc.n_out * rows_per_comp;
   const double2* tw = s->at<double2>(s->lay.twiddle);
   const float2* twf = s->at<float2>(s->lay.twiddle_f);
   const size_t smem = 2 * (size_t)c.Nz * s->cplx_bytes;

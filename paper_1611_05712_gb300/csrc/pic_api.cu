@@ -96,6 +96,7 @@ Layout make_layout(const pic_config& c) {
   L.tr = take((size_t)c.Nm * c.Nr * 8);
   L.coef = take(6 * G * 8);
   L.twiddle = take((size_t)c.Nz * 16);
+  L.twp = take((size_t)c.Nz * 16);
   if (mixed) {
     for (int b = 0; b < 2; ++b)
       for (int k = 0; k < 9; ++k) L.pf[b][k] = take(cap * 4);
@@ -106,6 +107,7 @@ Layout make_layout(const pic_config& c) {
     L.tz_f = take((size_t)c.Nz * 4);
     L.tr_f = take((size_t)c.Nm * c.Nr * 4);
     L.twiddle_f = take((size_t)c.Nz * 8);
+    L.twp_f = take((size_t)c.Nz * 8);
     L.mfwd_hi = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
     L.mfwd_lo = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
     L.binv_hi = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);

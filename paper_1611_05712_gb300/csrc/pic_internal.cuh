@@ -33,12 +33,13 @@ struct Layout {
   size_t E, B, Eh, Bh, dep, srch, tmp, rho_prev_h, rho_ion;   // grids
   size_t kperp, binv, mfwd, svd_w, svd_v, svd_d;                // DHT tables and scratch
   size_t kzmod, tz, tr, coef, twiddle;                           // PSATD tables
+  size_t twp;        // power-of-two Nz: per-pass twiddle tables of the radix-8 FFT
   size_t part[2][7], pid[2];                                     // particles (double buffer)
   size_t keys, perm, perm_tmp, count, start, scan_blk, big_list, big_count;
   size_t diag_acc, err;
   // mixed-precision form only (0 otherwise): float copies of the tables, the split DHT
   // matrices, FP32 cell-relative particles and an FP64 staging area for particle IO
-  size_t coef_f, kperp_f, kzmod_f, tz_f, tr_f, twiddle_f;
+  size_t coef_f, kperp_f, kzmod_f, tz_f, tr_f, twiddle_f, twp_f;
   size_t mfwd_hi, mfwd_lo, binv_hi, binv_lo;
   size_t pf[2][9];   // iz (int32), fz, x, y, ux/c, uy/c, uz/c, w (float), id (int32)
   size_t stage64;    // 7 x capacity float64
@@ -109,6 +110,7 @@ struct RowCombine {
 };
 pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& rc, bool inverse);
 pic_status fft_configure_device();      // once per device, before any FFT launch
+bool fft_is_pow2(int N);                // rows of power-of-two length use the radix-8 kernel
 
 // ---- launchers (dht.cu) ----
 // out[b] = A[b] (Nr x Nr, row-major [out][red]) * in[b] (Nr x 2Nz reals).  Element type

@@ -38,7 +38,8 @@ def crand(rng, shape, scale=1.0):
     return scale * (rng.normal(size=shape) + 1j * rng.normal(size=shape))
 
 
-SHAPES = [(16, 8, 2), (60, 33, 3), (256, 64, 2), (2048, 256, 2)]
+SHAPES = [(16, 8, 2), (60, 33, 3), (256, 64, 2), (2048, 256, 2), (32, 4, 1), (128, 8, 1), (1024, 8, 1),
+          (4096, 8, 1), (8192, 8, 2)]
 
 
 @pytest.mark.parametrize("Nz,Nr,Nm", SHAPES)
