@@ -495,78 +495,127 @@ struct DepArgsF {
 // A CTA's band of TZ z-rows (all r nodes, modes and ncomp components) in shared memory,
 // starting at row iz_lo.  Deposits to nodes in the band go to shared memory; nodes outside
 // it go straight to the global grid, so the result does not depend on how particles move.
+//
+// The band holds fixed-point sums: a contribution x (charge times weights, before the
+// 1/V_j factor) is y = x 2^S rounded to an integer and split as y = 2^16 hi + lo with
+// 0 <= lo <= 2^16, and hi and lo are added to two int32 planes.  Integer shared-memory
+// atomics are native and are not slowed by lanes that hit the same node (particles of one
+// cell do), unlike float ones; integer sums are also independent of the order of the adds.
+// S is chosen per CTA so that |y| <= 2^36 for every contribution of its chunk of at most
+// 1024 particles: |sum of hi| < 2^30 and sum of lo <= 2^26 cannot overflow, and the
+// resolution is 2^-36 of the largest possible contribution.
 struct BandF {
-  float2* tile;   // [TZ][ncomp][Nm][Nr] or null (no band)
-  int iz_lo, TZ, ncomp;
+  int32_t* tile;   // 4 planes (re hi, re lo, im hi, im lo) of P = TZ*ncomp*Nm*Nr words, or null
+  int iz_lo, TZ, ncomp, P;
+  float scale;     // 2^S
 };
+
+__device__ __forceinline__ void fixed_split(float y, int& hi, int& lo) {
+  const float f = floorf(y * (1.f / 65536.f));   // exact: power-of-two scaling of an integer-valued float
+  hi = (int)f;
+  lo = __float2int_rn(fmaf(-f, 65536.f, y));      // y - 65536 f, exact, in [0, 65536)
+}
 
 __device__ __forceinline__ void dep_node_fb(float2* grid_cm, const GeomF& g, const BandF& bd, int comp, int m,
                                             int j, int i, float wgt, float fold, float vre, float vim,
                                             const float* invV) {
   if (j < 0) { j = -1 - j; wgt *= fold; }
   if (j >= g.Nr) return;
-  const float f = wgt * invV[j];
   if (bd.tile) {
     int row = i - bd.iz_lo;
     if (row < 0) row += g.Nz;
     if (row < bd.TZ) {
-      float* t = reinterpret_cast<float*>(bd.tile + (((size_t)row * bd.ncomp + comp) * g.Nm + m) * g.Nr + j);
-      atomicAdd(t, vre * f);
-      atomicAdd(t + 1, vim * f);
+      const int e = ((row * bd.ncomp + comp) * g.Nm + m) * g.Nr + j;
+      int hr, lr, hi, li;
+      fixed_split(vre * wgt * bd.scale, hr, lr);
+      fixed_split(vim * wgt * bd.scale, hi, li);
+      atomicAdd(bd.tile + e, hr);
+      atomicAdd(bd.tile + bd.P + e, lr);
+      atomicAdd(bd.tile + 2 * bd.P + e, hi);
+      atomicAdd(bd.tile + 3 * bd.P + e, li);
       return;
     }
   }
+  const float f = wgt * invV[j];
   float* q = reinterpret_cast<float*>(grid_cm + (size_t)j * g.Nz + i);
   atomicAdd(q, vre * f);
   atomicAdd(q + 1, vim * f);
 }
 
+// Largest |w| over particles [b0, b1) (all threads of the CTA; non-finite weights raise the
+// numeric error bit and count as 0).
+__device__ __forceinline__ float chunk_max_weight(const float* w, int64_t b0, int64_t b1, uint32_t* slot,
+                                                  int32_t* err) {
+  if (threadIdx.x == 0) *slot = 0u;
+  __syncthreads();
+  float mx = 0.f;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    float a = fabsf(w[i]);
+    if (!(a <= 3.0e38f)) { atomicOr(err, kErrNumeric); a = 0.f; }
+    mx = fmaxf(mx, a);
+  }
+  // non-negative floats order like their bit patterns
+  const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
+  if ((threadIdx.x & 31) == 0) atomicMax(slot, m);
+  __syncthreads();
+  return __uint_as_float(*slot);
+}
+
 // Band of a chunk of cell-sorted particles whose first and last cells are iz_first, iz_last:
 // rows from iz_first - 1 to iz_last + 2 (moves of up to half a cell per half step, and the
-// +1 node), at most tz_max rows; rows beyond it are simply not banded.
-__device__ __forceinline__ BandF make_band(float2* smem, int iz_first, int iz_last, const GeomF& g, int tz_max,
-                                           int ncomp) {
+// +1 node), at most tz_max rows; rows beyond it are simply not banded.  bound is an upper
+// bound of |x| over the chunk's contributions.
+__device__ __forceinline__ BandF make_band(int32_t* smem, int iz_first, int iz_last, const GeomF& g, int tz_max,
+                                           int ncomp, float bound) {
   if (iz_first < 0 || iz_first >= g.Nz) iz_first = 0;
   if (iz_last < 0 || iz_last >= g.Nz) iz_last = iz_first;
   int span = iz_last - iz_first;
   if (span < 0) span += g.Nz;
   int rows = span + 4;
   if (rows > tz_max) rows = tz_max;
-  return BandF{smem, iz_first == 0 ? g.Nz - 1 : iz_first - 1, rows, ncomp};
+  int e = 0;
+  frexpf(bound, &e);   // bound <= 2^e
+  const int S = min(max(36 - e, -126), 126);
+  return BandF{smem, iz_first == 0 ? g.Nz - 1 : iz_first - 1, rows, ncomp, rows * ncomp * g.Nm * g.Nr,
+               ldexpf(1.f, S)};
 }
 
 // Zero a band (all threads of the CTA).
-__device__ __forceinline__ void band_zero(const BandF& bd, const GeomF& g) {
+__device__ __forceinline__ void band_zero(const BandF& bd) {
   if (!bd.tile) return;
-  const int n = bd.TZ * bd.ncomp * g.Nm * g.Nr;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) bd.tile[k] = make_float2(0.f, 0.f);
+  for (int k = threadIdx.x; k < 4 * bd.P; k += blockDim.x) bd.tile[k] = 0;
 }
 
-// Add a band's non-zero entries to the global grids (all threads of the CTA).  grid0 is
-// component 0 of the band; component c lives c * G further.  Consecutive threads take
-// consecutive rows of one (component, mode, r) column, which are adjacent in global memory.
-__device__ void band_flush(const BandF& bd, const GeomF& g, float2* grid0) {
+// Add a band's non-zero entries, times 2^-S / V_j, to the global grids (all threads of the
+// CTA).  grid0 is component 0 of the band; component c lives c * G further.  Consecutive
+// threads take consecutive rows of one (component, mode, r) column, which are adjacent in
+// global memory.
+__device__ void band_flush(const BandF& bd, const GeomF& g, float2* grid0, const float* invV) {
   if (!bd.tile) return;
-  const int n = bd.TZ * bd.ncomp * g.Nm * g.Nr;
   const size_t RZ = (size_t)g.Nr * g.Nz;
-  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+  const float inv_scale = 1.f / bd.scale;   // power of two: exact
+  for (int k = threadIdx.x; k < bd.P; k += blockDim.x) {
     const int row = k % bd.TZ;
     const int col = k / bd.TZ;            // (comp, m, j)
     const int j = col % g.Nr;
     const int m = (col / g.Nr) % g.Nm;
     const int comp = col / (g.Nr * g.Nm);
-    const float2 v = bd.tile[(((size_t)row * bd.ncomp + comp) * g.Nm + m) * g.Nr + j];
-    if (v.x == 0.f && v.y == 0.f) continue;
+    const int e = ((row * bd.ncomp + comp) * g.Nm + m) * g.Nr + j;
+    const int hr = bd.tile[e], lr = bd.tile[bd.P + e], hi = bd.tile[2 * bd.P + e], li = bd.tile[3 * bd.P + e];
+    if ((hr | lr | hi | li) == 0) continue;
+    const float f = inv_scale * invV[j];
+    const float vr = __ll2float_rn((long long)hr * 65536 + lr) * f;
+    const float vi = __ll2float_rn((long long)hi * 65536 + li) * f;
     int i = bd.iz_lo + row;
     if (i >= g.Nz) i -= g.Nz;
     float* q = reinterpret_cast<float*>(grid0 + comp * g.G + m * RZ + (size_t)j * g.Nz + i);
-    atomicAdd(q, v.x);
-    atomicAdd(q + 1, v.y);
+    atomicAdd(q, vr);
+    atomicAdd(q + 1, vi);
   }
 }
 
 // deposit of one particle at (iz+fz, x, y) with velocity (vx, vy, vz) [m/s]
-__device__ void deposit_one_f(const GeomF& g, const DepArgsF& a, const float* invV, const BandF& bR,
+__device__ __forceinline__ void deposit_one_f(const GeomF& g, const DepArgsF& a, const float* invV, const BandF& bR,
                               const BandF& bJ, int iz, float fz, float x, float y, float w, float vx, float vy,
                               float vz, bool do_rho, bool do_J) {
   float r, c, s;
@@ -638,16 +687,22 @@ __global__ void k_permute_f32(const PartsF src, PartsF dst, const int32_t* perm,
 // first particle's cell.
 __global__ void k_deposit_f32(const PartsF p, int64_t np, GeomF g, DepArgsF a, const float* invV, int32_t* err,
                               int64_t chunk, int tz) {
-  extern __shared__ __align__(16) float2 band_smem[];
+  extern __shared__ __align__(16) int32_t band_smem[];
+  __shared__ uint32_t wmax_slot;
   const bool do_rho = a.rho != nullptr, do_J = a.J != nullptr;
   const float c = (float)kC;
   const int64_t b0 = blockIdx.x * chunk;
   if (b0 >= np) return;
   const int64_t b1 = b0 + chunk < np ? b0 + chunk : np;
-  BandF none{nullptr, 0, 0, 0};
-  BandF band{nullptr, 0, 0, 0};
-  if (tz > 0 && do_rho != do_J) band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, tz, do_rho ? 1 : 3);
-  band_zero(band, g);
+  BandF none{nullptr, 0, 0, 0, 0, 1.f};
+  BandF band{nullptr, 0, 0, 0, 0, 1.f};
+  if (tz > 0 && do_rho != do_J) {
+    const float wmax = chunk_max_weight(p.w, b0, b1, &wmax_slot, err);
+    band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, tz, do_rho ? 1 : 3,
+                     fabsf(a.q) * wmax * (do_J ? c : 1.f));
+  }
+  band_zero(band);
+  const BandF bR = do_rho ? band : none, bJ = do_J ? band : none;   // copies: no address taken
   __syncthreads();
   for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
     const int32_t id = p.id[i];
@@ -664,11 +719,10 @@ __global__ void k_deposit_f32(const PartsF p, int64_t np, GeomF g, DepArgsF a, c
       const float ig = c * rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
       vx = ux * ig; vy = uy * ig; vz = uz * ig;
     }
-    deposit_one_f(g, a, invV, do_rho ? band : none, do_J ? band : none, iz, fz, x, y, p.w[i], vx, vy, vz,
-                  do_rho, do_J);
+    deposit_one_f(g, a, invV, bR, bJ, iz, fz, x, y, p.w[i], vx, vy, vz, do_rho, do_J);
   }
   __syncthreads();
-  band_flush(band, g, do_rho ? a.rho : a.J);
+  band_flush(band, g, do_rho ? a.rho : a.J, invV);
 }
 
 // Advance (iz, fz) by dfz cells, periodic in iz.
@@ -691,16 +745,20 @@ __global__ void k_gather_push_f32(PartsF p, int64_t np, GeomF g, const float2* _
                                   const float2* __restrict__ B, float kq, float kqc, float chdt,
                                   float chdt_dz, DepArgsF dep, const float* invV, int fuse, int32_t* err,
                                   int64_t chunk, int tz) {
-  extern __shared__ __align__(16) float2 band_smem[];
+  extern __shared__ __align__(16) int32_t band_smem[];
+  __shared__ uint32_t wmax_slot;
   const size_t RZ = (size_t)g.Nr * g.Nz;
   const float c_light = (float)kC;
   const int64_t b0 = blockIdx.x * chunk;
   if (b0 >= np) return;
   const int64_t b1 = b0 + chunk < np ? b0 + chunk : np;
-  const BandF none{nullptr, 0, 0, 0};
-  BandF band{nullptr, 0, 0, 0};
-  if (fuse && tz > 0) band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, tz, 3);
-  band_zero(band, g);
+  const BandF none{nullptr, 0, 0, 0, 0, 1.f};
+  BandF band{nullptr, 0, 0, 0, 0, 1.f};
+  if (fuse && tz > 0) {
+    const float wmax = chunk_max_weight(p.w, b0, b1, &wmax_slot, err);
+    band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, tz, 3, fabsf(dep.q) * wmax * c_light);
+  }
+  band_zero(band);
   __syncthreads();
   for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
     float x = p.x[i], y = p.y[i], fz = p.fz[i];
@@ -767,7 +825,7 @@ __global__ void k_gather_push_f32(PartsF p, int64_t np, GeomF g, const float2* _
     p.ux[i] = ux; p.uy[i] = uy; p.uz[i] = uz;
   }
   __syncthreads();
-  band_flush(band, g, dep.J);
+  band_flush(band, g, dep.J, invV);
 }
 
 // float64 SoA (x y z ux uy uz w) <-> FP32 cell-relative particles
@@ -982,9 +1040,9 @@ pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* ou
 bool is_mixed(const Sim* s) { return s->cfg.precision != PIC_FP64; }
 
 // Shared-memory bands for the deposits: chunks of 1024 cell-sorted particles per CTA, and a
-// band of at most tz z-rows of ncomp components (all modes and r nodes) within half of a
-// 96 KB budget, so that two CTAs fit on an SM.
-constexpr size_t kBandBudget = 96 * 1024;
+// band of 4 to 8 z-rows of ncomp components (all modes and r nodes, 16 bytes per complex
+// node) within kBandBudget, so that two CTAs fit on an SM.
+constexpr size_t kBandBudget = 100 * 1024;
 struct BandPlan {
   int64_t chunk;
   int tz;
@@ -994,9 +1052,8 @@ BandPlan band_plan(const Sim* s, int ncomp) {
   const pic_config& c = s->cfg;
   BandPlan bp{1024, 0, 0};
   if (ncomp <= 0) return bp;
-  const size_t row_bytes = (size_t)ncomp * c.Nm * c.Nr * sizeof(float2);
-  // at most half the budget per CTA so that two CTAs share an SM
-  int tz = (int)std::min<size_t>(std::min<size_t>(kBandBudget / 2 / row_bytes, 8), (size_t)c.Nz);
+  const size_t row_bytes = (size_t)ncomp * c.Nm * c.Nr * 4 * sizeof(int32_t);
+  int tz = (int)std::min<size_t>(std::min<size_t>(kBandBudget / row_bytes, 8), (size_t)c.Nz);
   if (tz < 4) return bp;   // a band must hold at least a 2-row footprint plus slack
   bp.tz = tz;
   bp.smem = (size_t)tz * row_bytes;
