@@ -459,16 +459,6 @@ __device__ __forceinline__ void polar_f(float x, float y, float& r, float& c, fl
   if (r > 0.f) { c = x / r; s = y / r; } else { c = 1.f; s = 0.f; }
 }
 
-__device__ __forceinline__ void dep_node_f(float2* grid, const GeomF& g, int j, int i, float wgt, float fold,
-                                           float vre, float vim, const float* invV) {
-  if (j < 0) { j = -1 - j; wgt *= fold; }
-  if (j >= g.Nr) return;
-  const float f = wgt * invV[j];
-  float* p = reinterpret_cast<float*>(grid + (size_t)j * g.Nz + i);
-  atomicAdd(p, vre * f);
-  atomicAdd(p + 1, vim * f);
-}
-
 __device__ __forceinline__ float2 interp_f(const float2* grid, const GeomF& g, const StencilF& st, float fold) {
   float re = 0.f, im = 0.f;
 #pragma unroll
@@ -506,8 +496,9 @@ struct DepArgsF {
 // resolution is 2^-36 of the largest possible contribution.
 struct BandF {
   int32_t* tile;   // 4 planes (re hi, re lo, im hi, im lo) of P = TZ*ncomp*Nm*Nr words, or null
-  int iz_lo, TZ, ncomp, P;
+  int iz_lo, TZ, ncomp, P;   // TZ is a power of two
   float scale;     // 2^S
+  int lgTZ;
 };
 
 __device__ __forceinline__ void fixed_split(float y, int& hi, int& lo) {
@@ -537,9 +528,7 @@ __device__ __forceinline__ void dep_node_fb(float2* grid_cm, const GeomF& g, con
     }
   }
   const float f = wgt * invV[j];
-  float* q = reinterpret_cast<float*>(grid_cm + (size_t)j * g.Nz + i);
-  atomicAdd(q, vre * f);
-  atomicAdd(q + 1, vim * f);
+  atomicAdd(grid_cm + (size_t)j * g.Nz + i, make_float2(vre * f, vim * f));
 }
 
 // Largest |w| over particles [b0, b1) (all threads of the CTA; non-finite weights raise the
@@ -571,13 +560,14 @@ __device__ __forceinline__ BandF make_band(int32_t* smem, int iz_first, int iz_l
   if (iz_last < 0 || iz_last >= g.Nz) iz_last = iz_first;
   int span = iz_last - iz_first;
   if (span < 0) span += g.Nz;
-  int rows = span + 4;
-  if (rows > tz_max) rows = tz_max;
+  int lg = 2;   // rows: the smallest power of two >= span + 4, at most tz_max (a power of two)
+  while ((1 << lg) < span + 4 && (2 << lg) <= tz_max) ++lg;
+  const int rows = 1 << lg;
   int e = 0;
   frexpf(bound, &e);   // bound <= 2^e
   const int S = min(max(36 - e, -126), 126);
   return BandF{smem, iz_first == 0 ? g.Nz - 1 : iz_first - 1, rows, ncomp, rows * ncomp * g.Nm * g.Nr,
-               ldexpf(1.f, S)};
+               ldexpf(1.f, S), lg};
 }
 
 // Zero a band (all threads of the CTA).
@@ -594,13 +584,18 @@ __device__ void band_flush(const BandF& bd, const GeomF& g, float2* grid0, const
   if (!bd.tile) return;
   const size_t RZ = (size_t)g.Nr * g.Nz;
   const float inv_scale = 1.f / bd.scale;   // power of two: exact
+  const int NC = bd.ncomp * g.Nm * g.Nr;    // columns (comp, m, j); entry e = row * NC + col
+  const float inv_nr = 1.f / (float)g.Nr, inv_nm = 1.f / (float)g.Nm;
   for (int k = threadIdx.x; k < bd.P; k += blockDim.x) {
-    const int row = k % bd.TZ;
-    const int col = k / bd.TZ;            // (comp, m, j)
-    const int j = col % g.Nr;
-    const int m = (col / g.Nr) % g.Nm;
-    const int comp = col / (g.Nr * g.Nm);
-    const int e = ((row * bd.ncomp + comp) * g.Nm + m) * g.Nr + j;
+    const int row = k & (bd.TZ - 1);
+    const int col = k >> bd.lgTZ;
+    // col / Nr and cm / Nm from float reciprocals: (n + 1/2)/d is at least 1/(2d) away from
+    // an integer and the product errs by < (n + 1/2) 2^-23 / d, exact for n < 2^22
+    const int cm = (int)(((float)col + 0.5f) * inv_nr);
+    const int j = col - cm * g.Nr;
+    const int comp = (int)(((float)cm + 0.5f) * inv_nm);
+    const int m = cm - comp * g.Nm;
+    const int e = row * NC + col;
     const int hr = bd.tile[e], lr = bd.tile[bd.P + e], hi = bd.tile[2 * bd.P + e], li = bd.tile[3 * bd.P + e];
     if ((hr | lr | hi | li) == 0) continue;
     const float f = inv_scale * invV[j];
@@ -608,9 +603,7 @@ __device__ void band_flush(const BandF& bd, const GeomF& g, float2* grid0, const
     const float vi = __ll2float_rn((long long)hi * 65536 + li) * f;
     int i = bd.iz_lo + row;
     if (i >= g.Nz) i -= g.Nz;
-    float* q = reinterpret_cast<float*>(grid0 + comp * g.G + m * RZ + (size_t)j * g.Nz + i);
-    atomicAdd(q, vr);
-    atomicAdd(q + 1, vi);
+    atomicAdd(grid0 + comp * g.G + m * RZ + (size_t)j * g.Nz + i, make_float2(vr, vi));
   }
 }
 
@@ -685,7 +678,11 @@ __global__ void k_permute_f32(const PartsF src, PartsF dst, const int32_t* perm,
 // One CTA per chunk of `chunk` consecutive (cell-sorted) particles; with tz > 0 and a single
 // deposit kind the CTA accumulates into a band of tz z-rows starting one row below its
 // first particle's cell.
-__global__ void k_deposit_f32(const PartsF p, int64_t np, GeomF g, DepArgsF a, const float* invV, int32_t* err,
+// Threads per CTA of the band kernels: one band (up to kBandBudget bytes) per CTA, two CTAs
+// per SM; 512 threads x 64 registers x 2 CTAs fill the register file.
+constexpr int kBandThreads = 512;
+
+__global__ void __launch_bounds__(kBandThreads, 2) k_deposit_f32(const PartsF p, int64_t np, GeomF g, DepArgsF a, const float* invV, int32_t* err,
                               int64_t chunk, int tz) {
   extern __shared__ __align__(16) int32_t band_smem[];
   __shared__ uint32_t wmax_slot;
@@ -694,8 +691,8 @@ __global__ void k_deposit_f32(const PartsF p, int64_t np, GeomF g, DepArgsF a, c
   const int64_t b0 = blockIdx.x * chunk;
   if (b0 >= np) return;
   const int64_t b1 = b0 + chunk < np ? b0 + chunk : np;
-  BandF none{nullptr, 0, 0, 0, 0, 1.f};
-  BandF band{nullptr, 0, 0, 0, 0, 1.f};
+  BandF none{nullptr, 0, 0, 0, 0, 1.f, 0};
+  BandF band{nullptr, 0, 0, 0, 0, 1.f, 0};
   if (tz > 0 && do_rho != do_J) {
     const float wmax = chunk_max_weight(p.w, b0, b1, &wmax_slot, err);
     band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, tz, do_rho ? 1 : 3,
@@ -741,7 +738,7 @@ __device__ __forceinline__ void advance_z(int& iz, float& fz, float dfz, int Nz)
 // One CTA per chunk of `chunk` consecutive (cell-sorted) particles; with tz > 0 the fused J
 // deposit accumulates into a band of tz z-rows from one row below the chunk's first cell
 // (a half step moves a particle by at most half a cell at c dt <= dz).
-__global__ void k_gather_push_f32(PartsF p, int64_t np, GeomF g, const float2* __restrict__ E,
+__global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, int64_t np, GeomF g, const float2* __restrict__ E,
                                   const float2* __restrict__ B, float kq, float kqc, float chdt,
                                   float chdt_dz, DepArgsF dep, const float* invV, int fuse, int32_t* err,
                                   int64_t chunk, int tz) {
@@ -752,8 +749,8 @@ __global__ void k_gather_push_f32(PartsF p, int64_t np, GeomF g, const float2* _
   const int64_t b0 = blockIdx.x * chunk;
   if (b0 >= np) return;
   const int64_t b1 = b0 + chunk < np ? b0 + chunk : np;
-  const BandF none{nullptr, 0, 0, 0, 0, 1.f};
-  BandF band{nullptr, 0, 0, 0, 0, 1.f};
+  const BandF none{nullptr, 0, 0, 0, 0, 1.f, 0};
+  BandF band{nullptr, 0, 0, 0, 0, 1.f, 0};
   if (fuse && tz > 0) {
     const float wmax = chunk_max_weight(p.w, b0, b1, &wmax_slot, err);
     band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, tz, 3, fabsf(dep.q) * wmax * c_light);
@@ -1053,8 +1050,9 @@ BandPlan band_plan(const Sim* s, int ncomp) {
   BandPlan bp{1024, 0, 0};
   if (ncomp <= 0) return bp;
   const size_t row_bytes = (size_t)ncomp * c.Nm * c.Nr * 4 * sizeof(int32_t);
-  int tz = (int)std::min<size_t>(std::min<size_t>(kBandBudget / row_bytes, 8), (size_t)c.Nz);
-  if (tz < 4) return bp;   // a band must hold at least a 2-row footprint plus slack
+  const size_t fit = kBandBudget / row_bytes;
+  if (fit < 4) return bp;   // a band must hold at least a 2-row footprint plus slack
+  const int tz = fit >= 8 ? 8 : 4;   // a power of two (Nz >= 8)
   bp.tz = tz;
   bp.smem = (size_t)tz * row_bytes;
   return bp;
@@ -1131,7 +1129,7 @@ pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, vo
     if (s->np == 0) return PIC_OK;
     const bool single = (a.rho != nullptr) != (a.J != nullptr);
     const BandPlan bp = band_plan(s, single ? (a.rho ? 1 : 3) : 0);
-    k_deposit_f32<<<(int)((s->np + bp.chunk - 1) / bp.chunk), 256, bp.smem, s->stream>>>(
+    k_deposit_f32<<<(int)((s->np + bp.chunk - 1) / bp.chunk), kBandThreads, bp.smem, s->stream>>>(
         partsf_of(s, s->cur), s->np, geomf_of(s), a, reinterpret_cast<const float*>(inv_volume(s)), err, bp.chunk,
         bp.tz);
   } else {
@@ -1167,7 +1165,7 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current) {
     const float chdt = (float)(0.5 * kC * c.dt);
     const float chdt_dz = (float)(0.5 * kC * c.dt / c.dz);
     const BandPlan bp = band_plan(s, fuse_current ? 3 : 0);
-    k_gather_push_f32<<<(int)((s->np + bp.chunk - 1) / bp.chunk), 256, bp.smem, s->stream>>>(
+    k_gather_push_f32<<<(int)((s->np + bp.chunk - 1) / bp.chunk), kBandThreads, bp.smem, s->stream>>>(
         partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.E), s->at<float2>(s->lay.B), kq, kqc, chdt,
         chdt_dz, a, reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.chunk, bp.tz);
   } else {
