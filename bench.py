@@ -46,9 +46,13 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-form comparison")
-    ap.add_argument("--workload", choices=["wake", "scan"], default="wake",
+    ap.add_argument("--accuracy-cycles", type=int, default=100,
+                    help="cycles after which the mixed form's fields and beam quality are "
+                         "compared with the FP64 form (0: skip)")
+    ap.add_argument("--workload", choices=["wake", "scan", "large"], default="wake",
                     help="wake: the 2048x256 wakefield run; scan: many uneven simulations "
-                         "(order / resolution scan) advanced by one CUDA graph per launch")
+                         "(order / resolution scan) advanced by one CUDA graph per launch; "
+                         "large: the 8192x1024 3-mode run with ~103M particles, mixed form")
     ap.add_argument("--sims", type=int, default=64, help="simulations in the scan workload")
     return ap.parse_args()
 
@@ -260,6 +264,42 @@ def measure(args, w, P, npl, beams, mixed, dist, dev, world, local):
     return out
 
 
+def accuracy_vs_fp64(w, P, npl, beams, n_cycles, local):
+    """Error of the mixed form against the FP64 form after n_cycles from the same initial
+    state: per field max |mixed - fp64| / max |fp64| over all components and modes, and the
+    relative differences of each beam's normalised emittances and slice energy spread."""
+    import numpy as np
+    import torch
+
+    from paper_1611_05712_gb300 import binding as bd
+    sims = {}
+    for name, prec in (("fp64", bd.PIC_FP64), ("mixed", bd.PIC_MIXED_TF32X3)):
+        s = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}", precision=prec)
+        s.step(n_cycles)
+        s.sync()
+        sims[name] = s
+    a, b = sims["fp64"], sims["mixed"]
+
+    def rel(x, y):
+        return float(np.abs(y - x).max() / max(np.abs(x).max(), 1e-300))
+
+    dep_a, dep_b = a.get("DEP"), b.get("DEP")
+    out = {"cycles": n_cycles,
+           "E": rel(a.get("E"), b.get("E")), "B": rel(a.get("B"), b.get("B")),
+           "J": rel(dep_a[1:], dep_b[1:]), "rho": rel(dep_a[:1], dep_b[:1])}
+    for bi, bm in enumerate(beams):
+        lo, hi = bm[0], bm[1]
+        name = "drive" if bi == 0 and len(beams) > 1 else ("witness" if bi == len(beams) - 1 else f"beam{bi}")
+        da, db = a.diagnostics(lo, hi), b.diagnostics(lo, hi)
+        out[name] = {k: abs(db[k] - da[k]) / max(abs(da[k]), 1e-300)
+                     for k in ("emit_nx", "emit_ny", "sigma_gamma_mean", "gamma_mean")}
+    for s in sims.values():
+        s.close()
+    del sims, a, b
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -307,6 +347,9 @@ def run_ours(args):
             "speedup_vs_fp64": mx["steps_per_s"] / head["steps_per_s"],
             "stage_ms_per_step": mx["stage_ms_per_step"], "roofline": mx["roofline"], "e2e": mx["e2e"],
             "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"]}
+        if args.accuracy_cycles > 0:
+            line["mixed_form"]["accuracy_vs_fp64"] = accuracy_vs_fp64(w, P, npl, beams, args.accuracy_cycles,
+                                                                      local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, secs = oracle_steps_per_s(w, P, npl, beams, 1)
         line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": os.cpu_count(),
@@ -397,12 +440,59 @@ def run_scan(args):
     return 0
 
 
+def run_large(args):
+    """The large single run: 8192 x 1024, 3 modes, p = 32, 12 plasma macroparticles per cell
+    plus 1M-particle drive and witness beams (~102.7M particles), mixed form only."""
+    import torch
+
+    from paper_1611_05712_gb300 import workloads as W
+    from paper_1611_05712_gb300.build import build
+    build()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = W.large_8192x1024(order_p=args.order)
+    t0 = time.perf_counter()
+    P, npl, beams = W.particles(w)
+    gen_s = time.perf_counter() - t0
+    n = len(P["x"])
+    args.e2e_steps = min(args.e2e_steps, 2)   # each end-to-end cycle uploads 5.8 GB of particles
+    t0 = time.perf_counter()
+    mx = measure(args, w, P, npl, beams, True, dist, dev, world, local)
+    run_s = time.perf_counter() - t0
+    cfg = config_of(w, n, "mixed")
+    cfg["l2"] = "no flush: working set (fields + particles, ~21 GB) exceeds the 129 MB L2"
+    cfg["host_generation_s"] = gen_s
+    cfg["setup_and_run_s"] = run_s
+    line = {
+        "metric": "pic_steps_per_s", "value": mx["steps_per_s"], "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mx["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": mx["dtype"],
+        "data": "synthetic", "config": cfg, "particle_updates_per_s": mx["steps_per_s"] * n,
+        "stage_ms_per_step": mx["stage_ms_per_step"], "roofline": mx["roofline"], "e2e": mx["e2e"],
+        "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"],
+    }
+    if int(os.environ.get("RANK", "0")) == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "scan":
         return run_scan(args)
+    if args.workload == "large":
+        return run_large(args)
     return run_ours(args)
 
 

@@ -482,9 +482,10 @@ struct DepArgsF {
   int32_t id_lo, id_hi;
 };
 
-// A CTA's band of TZ z-rows (all r nodes, modes and ncomp components) in shared memory,
-// starting at row iz_lo.  Deposits to nodes in the band go to shared memory; nodes outside
-// it go straight to the global grid, so the result does not depend on how particles move.
+// A CTA's band of TZ z-rows x JW r nodes (all modes and ncomp components) in shared memory,
+// starting at row iz_lo and node j_lo.  Deposits to nodes in the band go to shared memory;
+// nodes outside it go straight to the global grid, so the result does not depend on how
+// particles move.
 //
 // The band holds fixed-point sums: a contribution x (charge times weights, before the
 // 1/V_j factor) is y = x 2^S rounded to an integer and split as y = 2^16 hi + lo with
@@ -495,10 +496,24 @@ struct DepArgsF {
 // 1024 particles: |sum of hi| < 2^30 and sum of lo <= 2^26 cannot overflow, and the
 // resolution is 2^-36 of the largest possible contribution.
 struct BandF {
-  int32_t* tile;   // 4 planes (re hi, re lo, im hi, im lo) of P = TZ*ncomp*Nm*Nr words, or null
+  int32_t* tile;   // 4 planes (re hi, re lo, im hi, im lo) of P = TZ*ncomp*Nm*JW words, or null
   int iz_lo, TZ, ncomp, P;   // TZ is a power of two
   float scale;     // 2^S
   int lgTZ;
+  int j_lo, JW;    // r nodes j_lo .. j_lo + JW - 1
+};
+
+// Launch-wide band parameters: chunk of particles per CTA, at most tz rows (a power of two,
+// 0: no band) and jw_max r nodes; jmargin = r nodes a particle can move before it deposits.
+struct BandArgs {
+  int64_t chunk;
+  int tz, jw_max, jmargin;
+};
+
+// Per-chunk statistics gathered before a band is laid out.
+struct ChunkStats {
+  uint32_t wmax_bits;   // largest |w| (non-negative float bits)
+  int jmin, jmax;       // range of the particles' lower radial stencil node floor(r/dr - 1/2)
 };
 
 __device__ __forceinline__ void fixed_split(float y, int& hi, int& lo) {
@@ -515,8 +530,9 @@ __device__ __forceinline__ void dep_node_fb(float2* grid_cm, const GeomF& g, con
   if (bd.tile) {
     int row = i - bd.iz_lo;
     if (row < 0) row += g.Nz;
-    if (row < bd.TZ) {
-      const int e = ((row * bd.ncomp + comp) * g.Nm + m) * g.Nr + j;
+    const int jj = j - bd.j_lo;
+    if (row < bd.TZ && (unsigned)jj < (unsigned)bd.JW) {
+      const int e = ((row * bd.ncomp + comp) * g.Nm + m) * bd.JW + jj;
       int hr, lr, hi, li;
       fixed_split(vre * wgt * bd.scale, hr, lr);
       fixed_split(vim * wgt * bd.scale, hi, li);
@@ -531,31 +547,47 @@ __device__ __forceinline__ void dep_node_fb(float2* grid_cm, const GeomF& g, con
   atomicAdd(grid_cm + (size_t)j * g.Nz + i, make_float2(vre * f, vim * f));
 }
 
-// Largest |w| over particles [b0, b1) (all threads of the CTA; non-finite weights raise the
-// numeric error bit and count as 0).
-__device__ __forceinline__ float chunk_max_weight(const float* w, int64_t b0, int64_t b1, uint32_t* slot,
-                                                  int32_t* err) {
-  if (threadIdx.x == 0) *slot = 0u;
+// Largest |w| and radial stencil range over particles [b0, b1) (all threads of the CTA;
+// non-finite weights raise the numeric error bit and count as 0).
+__device__ __forceinline__ ChunkStats chunk_stats(const PartsF& p, const GeomF& g, int64_t b0, int64_t b1,
+                                                  ChunkStats* slot, int32_t* err) {
+  if (threadIdx.x == 0) *slot = ChunkStats{0u, g.Nr, -1};
   __syncthreads();
   float mx = 0.f;
+  int jmin = g.Nr, jmax = -1;
   for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-    float a = fabsf(w[i]);
+    float a = fabsf(p.w[i]);
     if (!(a <= 3.0e38f)) { atomicOr(err, kErrNumeric); a = 0.f; }
     mx = fmaxf(mx, a);
+    const float x = p.x[i], y = p.y[i];
+    const float v = sqrtf(x * x + y * y) * g.inv_dr - 0.5f;
+    const int j = (int)fminf(fmaxf(floorf(v), -1.f), (float)g.Nr);   // NaN -> -1 after fmaxf
+    jmin = min(jmin, j);
+    jmax = max(jmax, j);
   }
   // non-negative floats order like their bit patterns
   const uint32_t m = __reduce_max_sync(0xffffffffu, __float_as_uint(mx));
-  if ((threadIdx.x & 31) == 0) atomicMax(slot, m);
+  jmin = __reduce_min_sync(0xffffffffu, jmin);
+  jmax = __reduce_max_sync(0xffffffffu, jmax);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&slot->wmax_bits, m);
+    atomicMin(&slot->jmin, jmin);
+    atomicMax(&slot->jmax, jmax);
+  }
   __syncthreads();
-  return __uint_as_float(*slot);
+  return *slot;
 }
 
 // Band of a chunk of cell-sorted particles whose first and last cells are iz_first, iz_last:
 // rows from iz_first - 1 to iz_last + 2 (moves of up to half a cell per half step, and the
-// +1 node), at most tz_max rows; rows beyond it are simply not banded.  bound is an upper
-// bound of |x| over the chunk's contributions.
+// +1 node), at most tz_max rows; r nodes from the chunk's lowest stencil node - jmargin to
+// its highest + 1 + jmargin, at most jw_max of them; nodes beyond are simply not banded.
+// bound is an upper bound of |x| over the chunk's contributions.
 __device__ __forceinline__ BandF make_band(int32_t* smem, int iz_first, int iz_last, const GeomF& g, int tz_max,
-                                           int ncomp, float bound) {
+                                           int ncomp, float bound, const ChunkStats& cs, int jw_max, int jmargin) {
+  const int j_lo = max(0, cs.jmin - jmargin);
+  const int j_hi = min(g.Nr - 1, cs.jmax + 1 + jmargin);
+  const int JW = max(1, min(jw_max, j_hi - j_lo + 1));
   if (iz_first < 0 || iz_first >= g.Nz) iz_first = 0;
   if (iz_last < 0 || iz_last >= g.Nz) iz_last = iz_first;
   int span = iz_last - iz_first;
@@ -566,8 +598,8 @@ __device__ __forceinline__ BandF make_band(int32_t* smem, int iz_first, int iz_l
   int e = 0;
   frexpf(bound, &e);   // bound <= 2^e
   const int S = min(max(36 - e, -126), 126);
-  return BandF{smem, iz_first == 0 ? g.Nz - 1 : iz_first - 1, rows, ncomp, rows * ncomp * g.Nm * g.Nr,
-               ldexpf(1.f, S), lg};
+  return BandF{smem, iz_first == 0 ? g.Nz - 1 : iz_first - 1, rows, ncomp, rows * ncomp * g.Nm * JW,
+               ldexpf(1.f, S), lg, j_lo, JW};
 }
 
 // Zero a band (all threads of the CTA).
@@ -584,15 +616,15 @@ __device__ void band_flush(const BandF& bd, const GeomF& g, float2* grid0, const
   if (!bd.tile) return;
   const size_t RZ = (size_t)g.Nr * g.Nz;
   const float inv_scale = 1.f / bd.scale;   // power of two: exact
-  const int NC = bd.ncomp * g.Nm * g.Nr;    // columns (comp, m, j); entry e = row * NC + col
-  const float inv_nr = 1.f / (float)g.Nr, inv_nm = 1.f / (float)g.Nm;
+  const int NC = bd.ncomp * g.Nm * bd.JW;   // columns (comp, m, j); entry e = row * NC + col
+  const float inv_jw = 1.f / (float)bd.JW, inv_nm = 1.f / (float)g.Nm;
   for (int k = threadIdx.x; k < bd.P; k += blockDim.x) {
     const int row = k & (bd.TZ - 1);
     const int col = k >> bd.lgTZ;
-    // col / Nr and cm / Nm from float reciprocals: (n + 1/2)/d is at least 1/(2d) away from
+    // col / JW and cm / Nm from float reciprocals: (n + 1/2)/d is at least 1/(2d) away from
     // an integer and the product errs by < (n + 1/2) 2^-23 / d, exact for n < 2^22
-    const int cm = (int)(((float)col + 0.5f) * inv_nr);
-    const int j = col - cm * g.Nr;
+    const int cm = (int)(((float)col + 0.5f) * inv_jw);
+    const int j = bd.j_lo + col - cm * bd.JW;
     const int comp = (int)(((float)cm + 0.5f) * inv_nm);
     const int m = cm - comp * g.Nm;
     const int e = row * NC + col;
@@ -682,21 +714,22 @@ __global__ void k_permute_f32(const PartsF src, PartsF dst, const int32_t* perm,
 // per SM; 512 threads x 64 registers x 2 CTAs fill the register file.
 constexpr int kBandThreads = 512;
 
-__global__ void __launch_bounds__(kBandThreads, 2) k_deposit_f32(const PartsF p, int64_t np, GeomF g, DepArgsF a, const float* invV, int32_t* err,
-                              int64_t chunk, int tz) {
+__global__ void __launch_bounds__(kBandThreads, 2) k_deposit_f32(const PartsF p, int64_t np, GeomF g, DepArgsF a,
+                                                                   const float* invV, int32_t* err, BandArgs ba) {
   extern __shared__ __align__(16) int32_t band_smem[];
-  __shared__ uint32_t wmax_slot;
+  __shared__ ChunkStats stats_slot;
+  const int64_t chunk = ba.chunk;
   const bool do_rho = a.rho != nullptr, do_J = a.J != nullptr;
   const float c = (float)kC;
   const int64_t b0 = blockIdx.x * chunk;
   if (b0 >= np) return;
   const int64_t b1 = b0 + chunk < np ? b0 + chunk : np;
-  BandF none{nullptr, 0, 0, 0, 0, 1.f, 0};
-  BandF band{nullptr, 0, 0, 0, 0, 1.f, 0};
-  if (tz > 0 && do_rho != do_J) {
-    const float wmax = chunk_max_weight(p.w, b0, b1, &wmax_slot, err);
-    band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, tz, do_rho ? 1 : 3,
-                     fabsf(a.q) * wmax * (do_J ? c : 1.f));
+  BandF none{nullptr, 0, 0, 0, 0, 1.f, 0, 0, 1};
+  BandF band{nullptr, 0, 0, 0, 0, 1.f, 0, 0, 1};
+  if (ba.tz > 0 && do_rho != do_J) {
+    const ChunkStats cs = chunk_stats(p, g, b0, b1, &stats_slot, err);
+    band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, do_rho ? 1 : 3,
+                     fabsf(a.q) * __uint_as_float(cs.wmax_bits) * (do_J ? c : 1.f), cs, ba.jw_max, ba.jmargin);
   }
   band_zero(band);
   const BandF bR = do_rho ? band : none, bJ = do_J ? band : none;   // copies: no address taken
@@ -741,19 +774,21 @@ __device__ __forceinline__ void advance_z(int& iz, float& fz, float dfz, int Nz)
 __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, int64_t np, GeomF g, const float2* __restrict__ E,
                                   const float2* __restrict__ B, float kq, float kqc, float chdt,
                                   float chdt_dz, DepArgsF dep, const float* invV, int fuse, int32_t* err,
-                                  int64_t chunk, int tz) {
+                                  BandArgs ba) {
   extern __shared__ __align__(16) int32_t band_smem[];
-  __shared__ uint32_t wmax_slot;
+  __shared__ ChunkStats stats_slot;
+  const int64_t chunk = ba.chunk;
   const size_t RZ = (size_t)g.Nr * g.Nz;
   const float c_light = (float)kC;
   const int64_t b0 = blockIdx.x * chunk;
   if (b0 >= np) return;
   const int64_t b1 = b0 + chunk < np ? b0 + chunk : np;
-  const BandF none{nullptr, 0, 0, 0, 0, 1.f, 0};
-  BandF band{nullptr, 0, 0, 0, 0, 1.f, 0};
-  if (fuse && tz > 0) {
-    const float wmax = chunk_max_weight(p.w, b0, b1, &wmax_slot, err);
-    band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, tz, 3, fabsf(dep.q) * wmax * c_light);
+  const BandF none{nullptr, 0, 0, 0, 0, 1.f, 0, 0, 1};
+  BandF band{nullptr, 0, 0, 0, 0, 1.f, 0, 0, 1};
+  if (fuse && ba.tz > 0) {
+    const ChunkStats cs = chunk_stats(p, g, b0, b1, &stats_slot, err);
+    band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, 3,
+                     fabsf(dep.q) * __uint_as_float(cs.wmax_bits) * c_light, cs, ba.jw_max, ba.jmargin);
   }
   band_zero(band);
   __syncthreads();
@@ -1036,25 +1071,33 @@ pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* ou
 
 bool is_mixed(const Sim* s) { return s->cfg.precision != PIC_FP64; }
 
-// Shared-memory bands for the deposits: chunks of 1024 cell-sorted particles per CTA, and a
-// band of 4 to 8 z-rows of ncomp components (all modes and r nodes, 16 bytes per complex
-// node) within kBandBudget, so that two CTAs fit on an SM.
+// Shared-memory bands for the deposits: chunks of 1024 cell-sorted particles per CTA and a
+// band of ncomp components (all modes, 16 bytes per complex node) within kBandBudget, so
+// that two CTAs fit on an SM: 8 or 4 full z-rows when they fit, else 4 rows of as many r
+// nodes as fit (at least 16).  jmargin: r nodes a particle can move before it deposits.
 constexpr size_t kBandBudget = 100 * 1024;
 struct BandPlan {
-  int64_t chunk;
-  int tz;
+  BandArgs args;
   size_t smem;
 };
-BandPlan band_plan(const Sim* s, int ncomp) {
+BandPlan band_plan(const Sim* s, int ncomp, int jmargin) {
   const pic_config& c = s->cfg;
-  BandPlan bp{1024, 0, 0};
+  BandPlan bp{BandArgs{1024, 0, 0, jmargin}, 0};
   if (ncomp <= 0) return bp;
-  const size_t row_bytes = (size_t)ncomp * c.Nm * c.Nr * 4 * sizeof(int32_t);
-  const size_t fit = kBandBudget / row_bytes;
-  if (fit < 4) return bp;   // a band must hold at least a 2-row footprint plus slack
-  const int tz = fit >= 8 ? 8 : 4;   // a power of two (Nz >= 8)
-  bp.tz = tz;
-  bp.smem = (size_t)tz * row_bytes;
+  const size_t node_bytes = (size_t)ncomp * c.Nm * 4 * sizeof(int32_t);   // one r node of one row
+  const size_t row_bytes = node_bytes * c.Nr;
+  int tz = 0, jw = 0;
+  if (kBandBudget / row_bytes >= 4) {
+    tz = kBandBudget / row_bytes >= 8 ? 8 : 4;   // a power of two (Nz >= 8)
+    jw = c.Nr;
+  } else {
+    tz = 4;
+    jw = (int)(kBandBudget / (4 * node_bytes));
+    if (jw < 16) return bp;
+  }
+  bp.args.tz = tz;
+  bp.args.jw_max = jw;
+  bp.smem = (size_t)tz * jw * node_bytes;
   return bp;
 }
 
@@ -1128,10 +1171,9 @@ pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, vo
     if (a.J) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * G * sizeof(float2), s->stream));
     if (s->np == 0) return PIC_OK;
     const bool single = (a.rho != nullptr) != (a.J != nullptr);
-    const BandPlan bp = band_plan(s, single ? (a.rho ? 1 : 3) : 0);
-    k_deposit_f32<<<(int)((s->np + bp.chunk - 1) / bp.chunk), kBandThreads, bp.smem, s->stream>>>(
-        partsf_of(s, s->cur), s->np, geomf_of(s), a, reinterpret_cast<const float*>(inv_volume(s)), err, bp.chunk,
-        bp.tz);
+    const BandPlan bp = band_plan(s, single ? (a.rho ? 1 : 3) : 0, 1);
+    k_deposit_f32<<<(int)((s->np + bp.args.chunk - 1) / bp.args.chunk), kBandThreads, bp.smem, s->stream>>>(
+        partsf_of(s, s->cur), s->np, geomf_of(s), a, reinterpret_cast<const float*>(inv_volume(s)), err, bp.args);
   } else {
     DepArgs a;
     a.q = s->cfg.q;
@@ -1164,10 +1206,11 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current) {
     const float kqc = (float)(c.q * c.dt / (2.0 * c.mass));
     const float chdt = (float)(0.5 * kC * c.dt);
     const float chdt_dz = (float)(0.5 * kC * c.dt / c.dz);
-    const BandPlan bp = band_plan(s, fuse_current ? 3 : 0);
-    k_gather_push_f32<<<(int)((s->np + bp.chunk - 1) / bp.chunk), kBandThreads, bp.smem, s->stream>>>(
+    // a half step moves a particle by at most c dt / 2 in r
+    const BandPlan bp = band_plan(s, fuse_current ? 3 : 0, 1 + (int)std::ceil(0.5 * kC * c.dt / c.dr));
+    k_gather_push_f32<<<(int)((s->np + bp.args.chunk - 1) / bp.args.chunk), kBandThreads, bp.smem, s->stream>>>(
         partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.E), s->at<float2>(s->lay.B), kq, kqc, chdt,
-        chdt_dz, a, reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.chunk, bp.tz);
+        chdt_dz, a, reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args);
   } else {
     DepArgs a;
     a.q = c.q;
