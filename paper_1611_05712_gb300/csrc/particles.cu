@@ -403,35 +403,77 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // ------------------------------------------------------------------ mixed form: FP32 particles
-// z is kept relative to its cell: z = (iz + fz) dz with iz an int32 cell and fz in [0, 1);
-// x, y are float metres (|x|, |y| < R), momenta are u/c (float), w is float.
+// Positions are kept relative to their cell: z = (iz + fz) dz with iz an int32 cell and
+// x = (ix + fx) dr, y = (iy + fy) dr with (ix, iy) two int16 packed in one int32, and the
+// fractions fz, fx, fy in [0, 1): a float fraction resolves 2^-24 of a cell anywhere in the
+// box, where a float coordinate in metres loses precision away from the origin.  Momenta
+// are u/c as float pairs hi + lo (|lo| <= ulp(hi)/2, 48 significant bits): a per-step kick
+// of a gamma = 2000 beam is about one ulp of a float u/c, so a single float would round the
+// beam's energy changes away.  w is float.
 struct PartsF {
-  int32_t* iz; float* fz; float* x; float* y; float* ux; float* uy; float* uz; float* w; int32_t* id;
+  int32_t* iz; float* fz; int32_t* ixy; float* fx; float* fy;
+  float* ux; float* uy; float* uz; float* uxl; float* uyl; float* uzl; float* w; int32_t* id;
 };
 
 PartsF partsf_of(Sim* s, int which) {
   PartsF p;
   p.iz = s->at<int32_t>(s->lay.pf[which][kPfIz]);
   p.fz = s->at<float>(s->lay.pf[which][kPfFz]);
-  p.x = s->at<float>(s->lay.pf[which][kPfX]);
-  p.y = s->at<float>(s->lay.pf[which][kPfY]);
+  p.ixy = s->at<int32_t>(s->lay.pf[which][kPfIxy]);
+  p.fx = s->at<float>(s->lay.pf[which][kPfFx]);
+  p.fy = s->at<float>(s->lay.pf[which][kPfFy]);
   p.ux = s->at<float>(s->lay.pf[which][kPfUx]);
   p.uy = s->at<float>(s->lay.pf[which][kPfUy]);
   p.uz = s->at<float>(s->lay.pf[which][kPfUz]);
+  p.uxl = s->at<float>(s->lay.pf[which][kPfUxLo]);
+  p.uyl = s->at<float>(s->lay.pf[which][kPfUyLo]);
+  p.uzl = s->at<float>(s->lay.pf[which][kPfUzLo]);
   p.w = s->at<float>(s->lay.pf[which][kPfW]);
   p.id = s->at<int32_t>(s->lay.pf[which][kPfId]);
   return p;
 }
 
+__host__ __device__ __forceinline__ int32_t pack_cells(int ix, int iy) {
+  return (int32_t)(((uint32_t)ix & 0xffffu) | ((uint32_t)iy << 16));
+}
+__device__ __forceinline__ int cell_x(int32_t v) { return (int)(int16_t)(v & 0xffff); }
+__device__ __forceinline__ int cell_y(int32_t v) { return v >> 16; }
+
+// (hi, lo) += b for a float pair (two-sum, then renormalisation)
+__device__ __forceinline__ void ff_add(float& h, float& l, float b) {
+  const float s = h + b;
+  const float bb = s - h;
+  const float e = (h - (s - bb)) + (b - bb);
+  const float t = l + e;
+  h = s + t;
+  l = t - (h - s);
+}
+
+// Advance a cell-relative coordinate (cell, fraction in [0, 1)) by d cells.
+__device__ __forceinline__ void advance_cell(int& cell, float& f, float d) {
+  f += d;
+  const float k = floorf(f);
+  f -= k;
+  if (f >= 1.f) { f -= 1.f; cell += 1; }   // rounding of f - k up to 1
+  cell += (int)k;
+}
+
+// x / dr and y / dr of particle i
+__device__ __forceinline__ void pos_cells(const PartsF& p, int64_t i, float& x, float& y) {
+  const int32_t c = p.ixy[i];
+  x = (float)cell_x(c) + p.fx[i];
+  y = (float)cell_y(c) + p.fy[i];
+}
+
+// Positions are handled in cell units (x / dr, y / dr) on the device.
 struct GeomF {
   int Nz, Nr, Nm;
-  float inv_dr, R;
   size_t G;
 };
 
 GeomF geomf_of(const Sim* s) {
   const pic_config& c = s->cfg;
-  GeomF g{c.Nz, c.Nr, c.Nm, (float)(1.0 / c.dr), (float)(c.Nr * c.dr), s->grid_elems()};
+  GeomF g{c.Nz, c.Nr, c.Nm, s->grid_elems()};
   return g;
 }
 
@@ -440,13 +482,14 @@ struct StencilF {
   float wz0, wz1, wr0, wr1;
 };
 
+// r in cells (r / dr)
 __device__ __forceinline__ StencilF stencil_f(const GeomF& g, int iz, float fz, float r) {
   StencilF st;
   st.i0 = iz;
   st.i1 = iz + 1 == g.Nz ? 0 : iz + 1;
   st.wz1 = fz;
   st.wz0 = 1.f - fz;
-  const float v = r * g.inv_dr - 0.5f;
+  const float v = r - 0.5f;
   const float fj = floorf(v);
   st.j0 = (int)fminf(fmaxf(fj, -1.f), (float)g.Nr);
   st.wr1 = v - fj;
@@ -559,8 +602,9 @@ __device__ __forceinline__ ChunkStats chunk_stats(const PartsF& p, const GeomF& 
     float a = fabsf(p.w[i]);
     if (!(a <= 3.0e38f)) { atomicOr(err, kErrNumeric); a = 0.f; }
     mx = fmaxf(mx, a);
-    const float x = p.x[i], y = p.y[i];
-    const float v = sqrtf(x * x + y * y) * g.inv_dr - 0.5f;
+    float x, y;
+    pos_cells(p, i, x, y);
+    const float v = sqrtf(x * x + y * y) - 0.5f;
     const int j = (int)fminf(fmaxf(floorf(v), -1.f), (float)g.Nr);   // NaN -> -1 after fmaxf
     jmin = min(jmin, j);
     jmax = max(jmax, j);
@@ -681,9 +725,10 @@ __global__ void k_inv_volume_f(float* invV, int Nr, double dr, double dz) {
 __global__ void k_keys_f32(const PartsF p, int64_t np, GeomF g, int32_t* keys, int32_t* count, int32_t* err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const float x = p.x[i], y = p.y[i];
+    float x, y;
+    pos_cells(p, i, x, y);
     const float r = sqrtf(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)));
-    float fr = floorf(r * g.inv_dr);
+    float fr = floorf(r);
     int iz = p.iz[i];
     if (!(fr == fr) || isinf(fr) || iz < 0 || iz >= g.Nz) {
       atomicOr(err, kErrNumeric);
@@ -701,9 +746,11 @@ __global__ void k_permute_f32(const PartsF src, PartsF dst, const int32_t* perm,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t k = perm[i];
-    dst.iz[i] = src.iz[k]; dst.fz[i] = src.fz[k]; dst.x[i] = src.x[k]; dst.y[i] = src.y[k];
-    dst.ux[i] = src.ux[k]; dst.uy[i] = src.uy[k]; dst.uz[i] = src.uz[k]; dst.w[i] = src.w[k];
-    dst.id[i] = src.id[k];
+    dst.iz[i] = src.iz[k]; dst.fz[i] = src.fz[k]; dst.ixy[i] = src.ixy[k]; dst.fx[i] = src.fx[k];
+    dst.fy[i] = src.fy[k];
+    dst.ux[i] = src.ux[k]; dst.uy[i] = src.uy[k]; dst.uz[i] = src.uz[k];
+    dst.uxl[i] = src.uxl[k]; dst.uyl[i] = src.uyl[k]; dst.uzl[i] = src.uzl[k];
+    dst.w[i] = src.w[k]; dst.id[i] = src.id[k];
   }
 }
 
@@ -737,7 +784,9 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_deposit_f32(const PartsF p,
   for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
     const int32_t id = p.id[i];
     if (id < a.id_lo || id >= a.id_hi) continue;
-    const float x = p.x[i], y = p.y[i], fz = p.fz[i];
+    float x, y;
+    pos_cells(p, i, x, y);
+    const float fz = p.fz[i];
     const int iz = p.iz[i];
     if (!isfinite(x) || !isfinite(y) || !isfinite(fz) || iz < 0 || iz >= g.Nz) {
       atomicOr(err, kErrNumeric);
@@ -745,7 +794,7 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_deposit_f32(const PartsF p,
     }
     float vx = 0.f, vy = 0.f, vz = 0.f;
     if (do_J) {
-      const float ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
+      const float ux = p.ux[i] + p.uxl[i], uy = p.uy[i] + p.uyl[i], uz = p.uz[i] + p.uzl[i];
       const float ig = c * rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
       vx = ux * ig; vy = uy * ig; vz = uz * ig;
     }
@@ -772,7 +821,7 @@ __device__ __forceinline__ void advance_z(int& iz, float& fz, float dfz, int Nz)
 // deposit accumulates into a band of tz z-rows from one row below the chunk's first cell
 // (a half step moves a particle by at most half a cell at c dt <= dz).
 __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, int64_t np, GeomF g, const float2* __restrict__ E,
-                                  const float2* __restrict__ B, float kq, float kqc, float chdt,
+                                  const float2* __restrict__ B, float kq, float kqc, float chdt_dr,
                                   float chdt_dz, DepArgsF dep, const float* invV, int fuse, int32_t* err,
                                   BandArgs ba) {
   extern __shared__ __align__(16) int32_t band_smem[];
@@ -793,13 +842,17 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
   band_zero(band);
   __syncthreads();
   for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
-    float x = p.x[i], y = p.y[i], fz = p.fz[i];
+    const int32_t cells = p.ixy[i];
+    int ix = cell_x(cells), iy = cell_y(cells);
+    float fx = p.fx[i], fy = p.fy[i], fz = p.fz[i];
     int iz = p.iz[i];
+    float x = (float)ix + fx, y = (float)iy + fy;   // cells
     if (!isfinite(x) || !isfinite(y) || !isfinite(fz) || iz < 0 || iz >= g.Nz) {
       atomicOr(err, kErrNumeric);
       continue;
     }
-    float ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
+    float uxh = p.ux[i], uyh = p.uy[i], uzh = p.uz[i];
+    float uxl = p.uxl[i], uyl = p.uyl[i], uzl = p.uzl[i];
     const float w = p.w[i];
     float r, c, s;
     polar_f(x, y, r, c, s);
@@ -820,8 +873,11 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
     }
     const float Ex = F[0] * c - F[1] * s, Ey = F[0] * s + F[1] * c, Ez = F[2];
     const float Bx = F[3] * c - F[4] * s, By = F[3] * s + F[4] * c, Bz = F[5];
-    // Boris on u/c: u- = u + kq E, t = kqc B / gamma-, kq = q dt/(2 m c), kqc = q dt/(2 m)
-    const float umx = ux + kq * Ex, umy = uy + kq * Ey, umz = uz + kq * Ez;
+    // Boris on u/c: u- = u + kq E, t = kqc B / gamma-, kq = q dt/(2 m c), kqc = q dt/(2 m).
+    // The increments are formed in float from float values of u; the sums are kept as pairs.
+    const float ex = kq * Ex, ey = kq * Ey, ez = kq * Ez;
+    ff_add(uxh, uxl, ex); ff_add(uyh, uyl, ey); ff_add(uzh, uzl, ez);   // u-
+    const float umx = uxh + uxl, umy = uyh + uyl, umz = uzh + uzl;
     const float igm = rsqrtf(1.f + umx * umx + umy * umy + umz * umz);
     const float tx = kqc * Bx * igm, ty = kqc * By * igm, tz = kqc * Bz * igm;
     const float upx = umx + (umy * tz - umz * ty);
@@ -829,72 +885,96 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
     const float upz = umz + (umx * ty - umy * tx);
     const float f = 2.f / (1.f + tx * tx + ty * ty + tz * tz);
     const float sx = f * tx, sy = f * ty, sz = f * tz;
-    ux = umx + (upy * sz - upz * sy) + kq * Ex;
-    uy = umy + (upz * sx - upx * sz) + kq * Ey;
-    uz = umz + (upx * sy - upy * sx) + kq * Ez;
+    ff_add(uxh, uxl, upy * sz - upz * sy);   // u+ = u- + u' x s
+    ff_add(uyh, uyl, upz * sx - upx * sz);
+    ff_add(uzh, uzl, upx * sy - upy * sx);
+    ff_add(uxh, uxl, ex); ff_add(uyh, uyl, ey); ff_add(uzh, uzl, ez);   // u^{n+1/2}
+    const float ux = uxh + uxl, uy = uyh + uyl, uz = uzh + uzl;
     const float ig = rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
     const float bx = ux * ig, by = uy * ig, bz = uz * ig;   // v / c
-    x += bx * chdt;
-    y += by * chdt;
+    advance_cell(ix, fx, bx * chdt_dr);
+    advance_cell(iy, fy, by * chdt_dr);
     advance_z(iz, fz, bz * chdt_dz, g.Nz);
     if (fuse)
-      deposit_one_f(g, dep, invV, none, band, iz, fz, x, y, w, bx * c_light, by * c_light, bz * c_light, false,
-                    true);
-    x += bx * chdt;
-    y += by * chdt;
+      deposit_one_f(g, dep, invV, none, band, iz, fz, (float)ix + fx, (float)iy + fy, w, bx * c_light,
+                    by * c_light, bz * c_light, false, true);
+    advance_cell(ix, fx, bx * chdt_dr);
+    advance_cell(iy, fy, by * chdt_dr);
     advance_z(iz, fz, bz * chdt_dz, g.Nz);
+    x = (float)ix + fx;
+    y = (float)iy + fy;
     const float r1 = sqrtf(x * x + y * y);
-    if (r1 >= g.R) {
+    if (r1 >= (float)g.Nr) {   // specular reflection at r = R
       const float cx = x / r1, cy = y / r1;
-      const float fr = (2.f * g.R - r1) / r1;
+      const float fr = (2.f * (float)g.Nr - r1) / r1;
       const float ur = ux * cx + uy * cy;
-      ux -= 2.f * ur * cx;
-      uy -= 2.f * ur * cy;
+      ff_add(uxh, uxl, -2.f * ur * cx);
+      ff_add(uyh, uyl, -2.f * ur * cy);
       x *= fr;
       y *= fr;
+      const float kx = floorf(x), ky = floorf(y);
+      ix = (int)kx; fx = x - kx;
+      iy = (int)ky; fy = y - ky;
+      if (fx >= 1.f) { fx = 0.f; ix += 1; }
+      if (fy >= 1.f) { fy = 0.f; iy += 1; }
     }
-    p.x[i] = x; p.y[i] = y; p.fz[i] = fz; p.iz[i] = iz;
-    p.ux[i] = ux; p.uy[i] = uy; p.uz[i] = uz;
+    p.ixy[i] = pack_cells(ix, iy); p.fx[i] = fx; p.fy[i] = fy; p.fz[i] = fz; p.iz[i] = iz;
+    p.ux[i] = uxh; p.uy[i] = uyh; p.uz[i] = uzh;
+    p.uxl[i] = uxl; p.uyl[i] = uyl; p.uzl[i] = uzl;
   }
   __syncthreads();
   band_flush(band, g, dep.J, invV);
 }
 
 // float64 SoA (x y z ux uy uz w) <-> FP32 cell-relative particles
+__device__ __forceinline__ void split_cell(double u, int& cell, float& f) {
+  const double fl = floor(u);
+  f = (float)(u - fl);
+  long long c = (long long)fl;
+  if (f >= 1.f) { f = 0.f; c += 1; }
+  cell = (int)c;
+}
+
+__device__ __forceinline__ void split_pair(double u, float& h, float& l) {
+  h = (float)u;
+  l = (float)(u - (double)h);
+}
+
 __global__ void k_p64_to_p32(const double* __restrict__ st, int64_t cap, const int32_t* __restrict__ id_in,
-                             PartsF p, int64_t np, int Nz, double dz) {
+                             PartsF p, int64_t np, int Nz, double dz, double dr) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const double z = st[2 * cap + i];
-    const double u = z / dz;
-    double fl = floor(u);
-    float fz = (float)(u - fl);
-    long long izl = (long long)fl;
-    if (fz >= 1.f) { fz = 0.f; izl += 1; }
-    izl %= Nz;
-    if (izl < 0) izl += Nz;
-    p.iz[i] = (int32_t)izl;
+    int iz, ix, iy;
+    float fz, fx, fy;
+    split_cell(st[2 * cap + i] / dz, iz, fz);
+    iz %= Nz;
+    if (iz < 0) iz += Nz;
+    split_cell(st[i] / dr, ix, fx);
+    split_cell(st[cap + i] / dr, iy, fy);
+    p.iz[i] = iz;
     p.fz[i] = fz;
-    p.x[i] = (float)st[i];
-    p.y[i] = (float)st[cap + i];
-    p.ux[i] = (float)(st[3 * cap + i] / kC);
-    p.uy[i] = (float)(st[4 * cap + i] / kC);
-    p.uz[i] = (float)(st[5 * cap + i] / kC);
+    p.ixy[i] = pack_cells(ix, iy);
+    p.fx[i] = fx;
+    p.fy[i] = fy;
+    split_pair(st[3 * cap + i] / kC, p.ux[i], p.uxl[i]);
+    split_pair(st[4 * cap + i] / kC, p.uy[i], p.uyl[i]);
+    split_pair(st[5 * cap + i] / kC, p.uz[i], p.uzl[i]);
     p.w[i] = (float)st[6 * cap + i];
     p.id[i] = id_in[i];
   }
 }
 
 __global__ void k_p32_to_p64(const PartsF p, int64_t np, double* __restrict__ st, int64_t cap,
-                             int32_t* __restrict__ id_out, double dz) {
+                             int32_t* __restrict__ id_out, double dz, double dr) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
-    st[i] = p.x[i];
-    st[cap + i] = p.y[i];
+    const int32_t c = p.ixy[i];
+    st[i] = ((double)cell_x(c) + (double)p.fx[i]) * dr;
+    st[cap + i] = ((double)cell_y(c) + (double)p.fy[i]) * dr;
     st[2 * cap + i] = ((double)p.iz[i] + (double)p.fz[i]) * dz;
-    st[3 * cap + i] = (double)p.ux[i] * kC;
-    st[4 * cap + i] = (double)p.uy[i] * kC;
-    st[5 * cap + i] = (double)p.uz[i] * kC;
+    st[3 * cap + i] = ((double)p.ux[i] + (double)p.uxl[i]) * kC;
+    st[4 * cap + i] = ((double)p.uy[i] + (double)p.uyl[i]) * kC;
+    st[5 * cap + i] = ((double)p.uz[i] + (double)p.uzl[i]) * kC;
     st[6 * cap + i] = p.w[i];
     if (id_out) id_out[i] = p.id[i];
   }
@@ -912,11 +992,17 @@ struct Acc64 {
 };
 struct Acc32 {
   PartsF p;
-  double dz;
+  double dz, dr;
   __device__ void get(int64_t i, double& x, double& y, double& z, double& ux, double& uy, double& uz,
                       double& w) const {
-    x = p.x[i]; y = p.y[i]; z = ((double)p.iz[i] + (double)p.fz[i]) * dz;
-    ux = (double)p.ux[i] * kC; uy = (double)p.uy[i] * kC; uz = (double)p.uz[i] * kC; w = p.w[i];
+    const int32_t c = p.ixy[i];
+    x = ((double)cell_x(c) + (double)p.fx[i]) * dr;
+    y = ((double)cell_y(c) + (double)p.fy[i]) * dr;
+    z = ((double)p.iz[i] + (double)p.fz[i]) * dz;
+    ux = ((double)p.ux[i] + (double)p.uxl[i]) * kC;
+    uy = ((double)p.uy[i] + (double)p.uyl[i]) * kC;
+    uz = ((double)p.uz[i] + (double)p.uzl[i]) * kC;
+    w = p.w[i];
   }
   __device__ int32_t id(int64_t i) const { return p.id[i]; }
 };
@@ -1204,13 +1290,13 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current) {
     if (s->np == 0) return PIC_OK;
     const float kq = (float)(c.q * c.dt / (2.0 * c.mass * kC));
     const float kqc = (float)(c.q * c.dt / (2.0 * c.mass));
-    const float chdt = (float)(0.5 * kC * c.dt);
+    const float chdt_dr = (float)(0.5 * kC * c.dt / c.dr);
     const float chdt_dz = (float)(0.5 * kC * c.dt / c.dz);
     // a half step moves a particle by at most c dt / 2 in r
     const BandPlan bp = band_plan(s, fuse_current ? 3 : 0, 1 + (int)std::ceil(0.5 * kC * c.dt / c.dr));
     k_gather_push_f32<<<(int)((s->np + bp.args.chunk - 1) / bp.args.chunk), kBandThreads, bp.smem, s->stream>>>(
-        partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.E), s->at<float2>(s->lay.B), kq, kqc, chdt,
-        chdt_dz, a, reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args);
+        partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.E), s->at<float2>(s->lay.B), kq, kqc,
+        chdt_dr, chdt_dz, a, reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args);
   } else {
     DepArgs a;
     a.q = c.q;
@@ -1230,7 +1316,7 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current) {
 
 pic_status launch_diag(Sim* s, int32_t lo, int32_t hi, pic_diag* out, double* slice_sigma, int32_t max_slices) {
   if (is_mixed(s)) {
-    Acc32 a{partsf_of(s, s->cur), s->cfg.dz};
+    Acc32 a{partsf_of(s, s->cur), s->cfg.dz, s->cfg.dr};
     return run_diag(s, a, lo, hi, out, slice_sigma, max_slices);
   }
   Acc64 a{parts_of(s, s->cur)};
@@ -1241,7 +1327,7 @@ pic_status launch_diag(Sim* s, int32_t lo, int32_t hi, pic_diag* out, double* sl
 pic_status launch_particles_in(Sim* s, const int32_t* id_dev, int64_t n) {
   if (n == 0) return PIC_OK;
   k_p64_to_p32<<<pgrid(n), 256, 0, s->stream>>>(s->at<double>(s->lay.stage64), s->cfg.np_capacity, id_dev,
-                                                 partsf_of(s, s->cur), n, s->cfg.Nz, s->cfg.dz);
+                                                 partsf_of(s, s->cur), n, s->cfg.Nz, s->cfg.dz, s->cfg.dr);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }
@@ -1250,7 +1336,7 @@ pic_status launch_particles_in(Sim* s, const int32_t* id_dev, int64_t n) {
 pic_status launch_particles_out(Sim* s, int32_t* id_dev, int64_t n) {
   if (n == 0) return PIC_OK;
   k_p32_to_p64<<<pgrid(n), 256, 0, s->stream>>>(partsf_of(s, s->cur), n, s->at<double>(s->lay.stage64),
-                                                 s->cfg.np_capacity, id_dev, s->cfg.dz);
+                                                 s->cfg.np_capacity, id_dev, s->cfg.dz, s->cfg.dr);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }

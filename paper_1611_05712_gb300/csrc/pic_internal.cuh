@@ -41,7 +41,7 @@ struct Layout {
   // matrices, FP32 cell-relative particles and an FP64 staging area for particle IO
   size_t coef_f, kperp_f, kzmod_f, tz_f, tr_f, twiddle_f, twp_f;
   size_t mfwd_hi, mfwd_lo, binv_hi, binv_lo;
-  size_t pf[2][9];   // iz (int32), fz, x, y, ux/c, uy/c, uz/c, w (float), id (int32)
+  size_t pf[2][13];  // iz, fz, ixy (packed int16 x, y cells), fx, fy, u/c hi (3), u/c lo (3), w, id
   size_t stage64;    // 7 x capacity float64
   size_t total;
 };
@@ -50,8 +50,13 @@ struct Layout {
 // multiple of 4 so that rows start on 16-byte boundaries (tensor-memory-access copies).
 inline int split_pitch(int Nr) { return (Nr + 3) / 4 * 4; }
 
-// FP32 particle array indices of the mixed form.
-enum { kPfIz = 0, kPfFz = 1, kPfX = 2, kPfY = 3, kPfUx = 4, kPfUy = 5, kPfUz = 6, kPfW = 7, kPfId = 8 };
+// FP32 particle array indices of the mixed form: z = (iz + fz) dz, x = (ix + fx) dr,
+// y = (iy + fy) dr with fz, fx, fy in [0, 1) and (ix, iy) two int16 packed in one int32;
+// u/c = hi + lo per component (float pairs, |lo| <= ulp(hi)/2).
+enum {
+  kPfIz = 0, kPfFz, kPfIxy, kPfFx, kPfFy, kPfUx, kPfUy, kPfUz, kPfUxLo, kPfUyLo, kPfUzLo, kPfW, kPfId,
+  kPfCount
+};
 
 struct Sim {
   pic_config cfg;
