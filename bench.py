@@ -192,6 +192,7 @@ def measure(args, w, P, npl, beams, mixed, dist, dev, world, local):
     sim = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}",
                                precision=bd.PIC_MIXED_TF32X3 if mixed else bd.PIC_FP64)
     wit_lo, wit_hi = beams[-1][0], beams[-1][1]
+    tuning = sim.autotune() if mixed else None   # untimed: tile sizes for this workload
     sim.step(args.warmup)
     sim.sync()
     torch.cuda.synchronize(dev)
@@ -258,6 +259,8 @@ def measure(args, w, P, npl, beams, mixed, dist, dev, world, local):
            "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
            "dtype": "f32+tf32x3" if mixed else "f64"}
+    if tuning is not None:
+        out["tuning"] = tuning
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -346,7 +349,7 @@ def run_ours(args):
             "ms_per_step": mx["ms_per_step"], "particle_updates_per_s": mx["steps_per_s"] * n,
             "speedup_vs_fp64": mx["steps_per_s"] / head["steps_per_s"],
             "stage_ms_per_step": mx["stage_ms_per_step"], "roofline": mx["roofline"], "e2e": mx["e2e"],
-            "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"]}
+            "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"], "tuning": mx.get("tuning")}
         if args.accuracy_cycles > 0:
             line["mixed_form"]["accuracy_vs_fp64"] = accuracy_vs_fp64(w, P, npl, beams, args.accuracy_cycles,
                                                                       local)
@@ -398,6 +401,8 @@ def run_scan(args):
 
     with cf.ThreadPoolExecutor(max_workers=16) as ex:
         sims = list(ex.map(init, range(len(members))))
+    # tile sizes per member, one at a time so that the timings do not overlap
+    tunings = [s.autotune() for s in sims]
     setup_s = time.perf_counter() - t0
     batch = bd.Batch(sims, cycles=2)
     batch.launch(max(1, args.warmup // 2 + 1))
@@ -426,7 +431,9 @@ def run_scan(args):
                    "Nz": [w.Nz for w in members], "Nr": [w.Nr for w in members],
                    "Nm": [w.Nm for w in members], "order_p": [w.order_p for w in members],
                    "cdt_over_dz": [round(299792458.0 * w.dt / w.dz, 3) for w in members],
-                   "cycles_per_graph_launch": 2, "setup_s": setup_s},
+                   "cycles_per_graph_launch": 2, "setup_s": setup_s,
+                   "dht_n_tile": [t["dht_n_tile"] for t in tunings],
+                   "band_chunk": [t["band_chunk"] for t in tunings]},
         "particle_updates_per_s": world * cycles * n_tot / (ms * 1e-3),
         "gpu_launches": batch.kernels_per_launch * launches, "graph_launches": launches,
         "clocks": clk.summary(),
@@ -475,7 +482,7 @@ def run_large(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": mx["dtype"],
         "data": "synthetic", "config": cfg, "particle_updates_per_s": mx["steps_per_s"] * n,
         "stage_ms_per_step": mx["stage_ms_per_step"], "roofline": mx["roofline"], "e2e": mx["e2e"],
-        "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"],
+        "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"], "tuning": mx.get("tuning"),
     }
     if int(os.environ.get("RANK", "0")) == 0:
         print(json.dumps(line), flush=True)

@@ -236,6 +236,35 @@ pic_status pic_batch_launch(pic_batch* batch, int32_t n_launches);
 pic_status pic_batch_info(pic_batch* batch, int32_t* cycles_per_launch, int64_t* kernels_per_launch);
 pic_status pic_batch_destroy(pic_batch* batch);
 
+/* ---- tile tuning -----------------------------------------------------------------
+ * The paper gives no kernel tiling; these choices belong to this library.  Two tile sizes
+ * of the mixed form (PIC_MIXED_TF32X3) are tunable:
+ *   dht_n_tile: rows of the Hankel matrix per tensor-core tile of the DHT (16..256, a
+ *               multiple of 16; 0 = the built-in rule: Nr split into tiles of <= 256);
+ *   band_chunk: cell-sorted particles per CTA of the deposit kernels (512, 1024 or 2048),
+ *               which also sets how many grid rows a CTA's shared-memory band covers.
+ * Neither changes the arithmetic of a DHT output (same K order, bit-identical results);
+ * band_chunk changes the order of the float additions to the global grid only.
+ * pic_autotune times the candidates (n tiles of 256, 128, 64 rows; chunks of 512, 1024,
+ * 2048) on the handle's own data: the forward and inverse DHT of the current spectral
+ * state and the current deposit of the current particles, each after one warm-up launch,
+ * best of 3, and keeps the fastest.  It overwrites only buffers that every cycle rewrites
+ * before reading (the transform scratch, the spectral sources and the deposit grid), so it
+ * may be called between cycles; call it before pic_batch_create.  Synchronises.  In the
+ * FP64 form it leaves the (untuned) defaults.  out (host, may be NULL) receives the
+ * choice.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA, PIC_ERR_TIMEOUT. */
+typedef struct pic_tuning {
+  int32_t dht_n_tile;
+  int32_t band_chunk;
+  double dht_ms;       /* pic_autotune: forward + inverse DHT time of the choice [ms] */
+  double deposit_ms;   /* pic_autotune: J deposit time of the choice [ms]             */
+} pic_tuning;
+pic_status pic_autotune(pic_sim* sim, pic_tuning* out);
+/* Set the tile sizes (dht_n_tile, band_chunk; the time fields are ignored).  Errors:
+ * PIC_ERR_ARG (a value outside the ranges above), PIC_ERR_CUDA. */
+pic_status pic_set_tuning(pic_sim* sim, const pic_tuning* tuning);
+pic_status pic_get_tuning(pic_sim* sim, pic_tuning* out);
+
 /* a10: FP64 diagnostics of the particles with id in [id_lo, id_hi).  slice_sigma (host,
  * may be NULL) receives up to max_slices per-slice std of gamma.  Synchronises. */
 pic_status pic_diagnostics(pic_sim* sim, int32_t id_lo, int32_t id_hi, pic_diag* out,

@@ -41,6 +41,11 @@ class PicDiag(ctypes.Structure):
                 ("n_slices", ctypes.c_int32), ("n_particles", ctypes.c_int32)]
 
 
+class PicTuning(ctypes.Structure):
+    _fields_ = [("dht_n_tile", ctypes.c_int32), ("band_chunk", ctypes.c_int32),
+                ("dht_ms", ctypes.c_double), ("deposit_ms", ctypes.c_double)]
+
+
 class PicError(RuntimeError):
     def __init__(self, status, where, text):
         super().__init__(f"{where}: {STATUS.get(status, status)}: {text}")
@@ -96,6 +101,9 @@ def load():
         "pic_batch_launch": [P, I32],
         "pic_batch_info": [P, ctypes.POINTER(I32), ctypes.POINTER(I64)],
         "pic_batch_destroy": [P],
+        "pic_autotune": [P, ctypes.POINTER(PicTuning)],
+        "pic_set_tuning": [P, ctypes.POINTER(PicTuning)],
+        "pic_get_tuning": [P, ctypes.POINTER(PicTuning)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -237,6 +245,21 @@ class Sim:
         n = ctypes.c_int64()
         _check(self.lib.pic_launch_count(self.h, ctypes.byref(n)), "pic_launch_count")
         return n.value
+
+    def autotune(self):
+        """Time the tile candidates on this simulation's data and keep the fastest."""
+        t = PicTuning()
+        _check(self.lib.pic_autotune(self.h, ctypes.byref(t)), "pic_autotune")
+        return {f: getattr(t, f) for f, _ in PicTuning._fields_}
+
+    def set_tuning(self, dht_n_tile=0, band_chunk=1024):
+        t = PicTuning(dht_n_tile, band_chunk, 0.0, 0.0)
+        _check(self.lib.pic_set_tuning(self.h, ctypes.byref(t)), "pic_set_tuning")
+
+    def get_tuning(self):
+        t = PicTuning()
+        _check(self.lib.pic_get_tuning(self.h, ctypes.byref(t)), "pic_get_tuning")
+        return {"dht_n_tile": t.dht_n_tile, "band_chunk": t.band_chunk}
 
     def diagnostics(self, id_lo, id_hi, max_slices=4096):
         d = PicDiag()

@@ -25,6 +25,7 @@
 #include <cuda.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -314,8 +315,15 @@ pic_status dht_tc_configure_device() {
 
 namespace {
 
-// N tiling shared by the tensor maps and the launches: n_tiles tiles of NT rows of A.
-void tc_tiles(int Nr, int* n_tiles, int* NT) {
+// N tiling shared by the tensor maps and the launches: n_tiles tiles of NT rows of A
+// (the tuned tile if set, else Nr split into the fewest tiles of <= 256 rows).
+void tc_tiles(const Sim* s, int* n_tiles, int* NT) {
+  const int Nr = s->cfg.Nr;
+  if (s->tune_nt > 0) {
+    *NT = std::min(s->tune_nt, (Nr + 15) / 16 * 16);
+    *n_tiles = (Nr + *NT - 1) / *NT;
+    return;
+  }
   *n_tiles = (Nr + kTcMaxN - 1) / kTcMaxN;
   const int per = (Nr + *n_tiles - 1) / *n_tiles;
   *NT = (per + 15) / 16 * 16;
@@ -352,7 +360,7 @@ pic_status dht_tc_make_maps(Sim* s) {
   }
   const int Nr = s->cfg.Nr, pitch = split_pitch(Nr);
   int n_tiles = 0, NT = 0;
-  tc_tiles(Nr, &n_tiles, &NT);
+  tc_tiles(s, &n_tiles, &NT);
   const size_t mat_floats = (size_t)Nr * pitch;
   for (int dir = 0; dir < 2; ++dir) {
     for (int mi = 0; mi < s->cfg.Nm * 3; ++mi) {
@@ -383,7 +391,7 @@ pic_status launch_dht_tc(Sim* s, const DhtBatch& b) {
   TcParams P;
   P.Nr = Nr;
   P.Nc = Nc;
-  tc_tiles(Nr, &P.n_tiles, &P.NT);
+  tc_tiles(s, &P.n_tiles, &P.NT);
   int tc = 32;
   while (tc < P.NT) tc <<= 1;
   P.tmem_cols = tc;

@@ -535,9 +535,10 @@ struct DepArgsF {
 // 0 <= lo <= 2^16, and hi and lo are added to two int32 planes.  Integer shared-memory
 // atomics are native and are not slowed by lanes that hit the same node (particles of one
 // cell do), unlike float ones; integer sums are also independent of the order of the adds.
-// S is chosen per CTA so that |y| <= 2^36 for every contribution of its chunk of at most
-// 1024 particles: |sum of hi| < 2^30 and sum of lo <= 2^26 cannot overflow, and the
-// resolution is 2^-36 of the largest possible contribution.
+// S is chosen per CTA so that |y| <= 2^(46 - log2 chunk) for every contribution of its
+// chunk (2^36 for 1024 particles): |sum of hi| < 2^30 and sum of lo <= 2^(16 + log2 chunk)
+// cannot overflow, and the resolution is 2^-36 (chunk 1024) of the largest possible
+// contribution.
 struct BandF {
   int32_t* tile;   // 4 planes (re hi, re lo, im hi, im lo) of P = TZ*ncomp*Nm*JW words, or null
   int iz_lo, TZ, ncomp, P;   // TZ is a power of two
@@ -551,6 +552,7 @@ struct BandF {
 struct BandArgs {
   int64_t chunk;
   int tz, jw_max, jmargin;
+  int lg_chunk;   // log2 chunk: sets the fixed-point headroom
 };
 
 // Per-chunk statistics gathered before a band is laid out.
@@ -628,7 +630,8 @@ __device__ __forceinline__ ChunkStats chunk_stats(const PartsF& p, const GeomF& 
 // its highest + 1 + jmargin, at most jw_max of them; nodes beyond are simply not banded.
 // bound is an upper bound of |x| over the chunk's contributions.
 __device__ __forceinline__ BandF make_band(int32_t* smem, int iz_first, int iz_last, const GeomF& g, int tz_max,
-                                           int ncomp, float bound, const ChunkStats& cs, int jw_max, int jmargin) {
+                                           int ncomp, float bound, const ChunkStats& cs, int jw_max, int jmargin,
+                                           int lg_chunk) {
   const int j_lo = max(0, cs.jmin - jmargin);
   const int j_hi = min(g.Nr - 1, cs.jmax + 1 + jmargin);
   const int JW = max(1, min(jw_max, j_hi - j_lo + 1));
@@ -641,7 +644,7 @@ __device__ __forceinline__ BandF make_band(int32_t* smem, int iz_first, int iz_l
   const int rows = 1 << lg;
   int e = 0;
   frexpf(bound, &e);   // bound <= 2^e
-  const int S = min(max(36 - e, -126), 126);
+  const int S = min(max(46 - lg_chunk - e, -126), 126);
   return BandF{smem, iz_first == 0 ? g.Nz - 1 : iz_first - 1, rows, ncomp, rows * ncomp * g.Nm * JW,
                ldexpf(1.f, S), lg, j_lo, JW};
 }
@@ -776,7 +779,7 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_deposit_f32(const PartsF p,
   if (ba.tz > 0 && do_rho != do_J) {
     const ChunkStats cs = chunk_stats(p, g, b0, b1, &stats_slot, err);
     band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, do_rho ? 1 : 3,
-                     fabsf(a.q) * __uint_as_float(cs.wmax_bits) * (do_J ? c : 1.f), cs, ba.jw_max, ba.jmargin);
+                     fabsf(a.q) * __uint_as_float(cs.wmax_bits) * (do_J ? c : 1.f), cs, ba.jw_max, ba.jmargin, ba.lg_chunk);
   }
   band_zero(band);
   const BandF bR = do_rho ? band : none, bJ = do_J ? band : none;   // copies: no address taken
@@ -837,7 +840,7 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
   if (fuse && ba.tz > 0) {
     const ChunkStats cs = chunk_stats(p, g, b0, b1, &stats_slot, err);
     band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, 3,
-                     fabsf(dep.q) * __uint_as_float(cs.wmax_bits) * c_light, cs, ba.jw_max, ba.jmargin);
+                     fabsf(dep.q) * __uint_as_float(cs.wmax_bits) * c_light, cs, ba.jw_max, ba.jmargin, ba.lg_chunk);
   }
   band_zero(band);
   __syncthreads();
@@ -1157,7 +1160,8 @@ pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* ou
 
 bool is_mixed(const Sim* s) { return s->cfg.precision != PIC_FP64; }
 
-// Shared-memory bands for the deposits: chunks of 1024 cell-sorted particles per CTA and a
+// Shared-memory bands for the deposits: chunks of cell-sorted particles per CTA (1024, or
+// the tuned size: a power of two) and a
 // band of ncomp components (all modes, 16 bytes per complex node) within kBandBudget, so
 // that two CTAs fit on an SM: 8 or 4 full z-rows when they fit, else 4 rows of as many r
 // nodes as fit (at least 16).  jmargin: r nodes a particle can move before it deposits.
@@ -1168,7 +1172,10 @@ struct BandPlan {
 };
 BandPlan band_plan(const Sim* s, int ncomp, int jmargin) {
   const pic_config& c = s->cfg;
-  BandPlan bp{BandArgs{1024, 0, 0, jmargin}, 0};
+  const int64_t chunk = s->tune_chunk > 0 ? s->tune_chunk : 1024;
+  int lg = 0;
+  while ((int64_t(1) << lg) < chunk) ++lg;
+  BandPlan bp{BandArgs{chunk, 0, 0, jmargin, lg}, 0};
   if (ncomp <= 0) return bp;
   const size_t node_bytes = (size_t)ncomp * c.Nm * 4 * sizeof(int32_t);   // one r node of one row
   const size_t row_bytes = node_bytes * c.Nr;

@@ -306,6 +306,37 @@ pic_status step_once(Sim* s, Marks* mk) {
     if (!(s)) { set_error("sim handle is NULL"); return PIC_ERR_ARG; } \
   } while (0)
 
+bool valid_tuning(const pic_tuning* t) {
+  const bool nt_ok = t->dht_n_tile == 0 || (t->dht_n_tile >= 16 && t->dht_n_tile <= 256 && t->dht_n_tile % 16 == 0);
+  const bool ch_ok = t->band_chunk == 512 || t->band_chunk == 1024 || t->band_chunk == 2048;
+  return nt_ok && ch_ok;
+}
+
+pic_status apply_tuning(Sim* s, int32_t nt, int32_t chunk) {
+  s->tune_nt = nt;
+  s->tune_chunk = chunk;
+  return s->cfg.precision == PIC_FP64 ? PIC_OK : dht_tc_make_maps(s);
+}
+
+// Device time of fn() on the handle's stream: one warm-up call, then the best of 3.
+template <class F>
+pic_status best_of_3(Sim* s, cudaEvent_t e0, cudaEvent_t e1, F&& fn, double* ms) {
+  pic_status st = fn();
+  if (st != PIC_OK) return st;
+  float best = 3.0e38f;
+  for (int r = 0; r < 3; ++r) {
+    PIC_CUDA(cudaEventRecord(e0, s->stream));
+    if ((st = fn()) != PIC_OK) return st;
+    PIC_CUDA(cudaEventRecord(e1, s->stream));
+    PIC_CUDA(cudaEventSynchronize(e1));
+    float t = 0.f;
+    PIC_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    best = std::min(best, t);
+  }
+  *ms = best;
+  return PIC_OK;
+}
+
 }  // namespace
 
 pic_status step_cycle(Sim* s) { return step_once(s, nullptr); }
@@ -354,6 +385,8 @@ pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_byt
   s->np = 0;
   s->cur = 0;
   s->cplx_bytes = cfg->precision == PIC_FP64 ? 16 : 8;
+  s->tune_nt = 0;
+  s->tune_chunk = 1024;
   const size_t G = s->grid_elems();
   const size_t cb = s->cplx_bytes;
   auto fail = [&](pic_status e) { delete s; return e; };
@@ -374,6 +407,73 @@ pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_byt
   if ((st = build_inv_volume(s)) != PIC_OK) return fail(st);
   if ((st = pic_sync(reinterpret_cast<pic_sim*>(s))) != PIC_OK) return fail(st);
   *out = reinterpret_cast<pic_sim*>(s);
+  return PIC_OK;
+}
+
+pic_status pic_autotune(pic_sim* sim, pic_tuning* out) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  pic_tuning res{s->tune_nt, s->tune_chunk, 0.0, 0.0};
+  if (s->cfg.precision != PIC_FP64) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    PIC_CUDA(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) { cudaEventDestroy(e0); return cuda_status(ce, "cudaEventCreate"); }
+    pic_status st = PIC_OK;
+    // DHT: forward (4 source components) + inverse (6 field components) per N tile
+    const int nr16 = (s->cfg.Nr + 15) / 16 * 16;
+    int last_tiles = -1;
+    double best = 3.0e38;
+    for (int cand : {256, 128, 64}) {
+      const int NT = std::min(cand, nr16);
+      const int tiles = (s->cfg.Nr + NT - 1) / NT;
+      if (tiles == last_tiles) continue;
+      last_tiles = tiles;
+      if ((st = apply_tuning(s, cand, s->tune_chunk)) != PIC_OK) break;
+      double ms = 0.0;
+      st = best_of_3(s, e0, e1, [&]() {
+        pic_status q = dht_forward(s, 4);
+        return q != PIC_OK ? q : dht_inverse(s);
+      }, &ms);
+      if (st != PIC_OK) break;
+      if (ms < best) { best = ms; res.dht_n_tile = cand; res.dht_ms = ms; }
+    }
+    // deposit band chunk (the fused J deposit of gather/push uses the same bands)
+    if (st == PIC_OK && s->np > 0) {
+      best = 3.0e38;
+      for (int cand : {512, 1024, 2048}) {
+        s->tune_chunk = cand;
+        double ms = 0.0;
+        st = best_of_3(s, e0, e1, [&]() { return launch_deposit(s, PIC_DEP_J, INT32_MIN, INT32_MAX, nullptr); }, &ms);
+        if (st != PIC_OK) break;
+        if (ms < best) { best = ms; res.band_chunk = cand; res.deposit_ms = ms; }
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PIC_OK) return st;
+    if ((st = apply_tuning(s, res.dht_n_tile, res.band_chunk)) != PIC_OK) return st;
+    if ((st = pic_sync(sim)) != PIC_OK) return st;
+  }
+  if (out) *out = res;
+  return PIC_OK;
+}
+
+pic_status pic_set_tuning(pic_sim* sim, const pic_tuning* t) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (!t || !valid_tuning(t)) {
+    set_error("tuning must have dht_n_tile 0 or a multiple of 16 in [16, 256] and band_chunk 512, 1024 or 2048");
+    return PIC_ERR_ARG;
+  }
+  return apply_tuning(s, t->dht_n_tile, t->band_chunk);
+}
+
+pic_status pic_get_tuning(pic_sim* sim, pic_tuning* out) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (!out) { set_error("out is NULL"); return PIC_ERR_ARG; }
+  *out = pic_tuning{s->tune_nt, s->tune_chunk, 0.0, 0.0};
   return PIC_OK;
 }
 

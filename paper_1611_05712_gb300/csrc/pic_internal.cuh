@@ -72,6 +72,8 @@ struct Sim {
   int32_t n_radix;
   int32_t radix[kMaxRadixPasses];
   size_t cplx_bytes;       // 16 (FP64) or 8 (mixed)
+  int32_t tune_nt;         // mixed-form DHT N tile (0: built-in rule), see pic_set_tuning
+  int32_t tune_chunk;      // particles per CTA of the band kernels
   // mixed form: encoded 2-D tensor maps (CUtensorMap, 128 B each) of the split DHT
   // matrices, [matrix id][hi, lo], built once at init
   struct alignas(64) TensorMapBytes {
