@@ -40,9 +40,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--order", type=int, default=32)
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64",
+    ap.add_argument("--precision", choices=["fp64", "mixed", "bf16"], default="fp64",
                     help="fp64: every stage in float64; mixed: float grids and particles, "
-                         "3-term TF32 DHT on tcgen05")
+                         "3-term TF32 DHT on tcgen05; bf16: the same with the 6-product BF16 DHT")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-form comparison")
@@ -179,7 +179,7 @@ def run_reference(args):
 
 # ------------------------------------------------------------------------- GPU
 
-def measure(args, w, P, npl, beams, mixed, dist, dev, world, local):
+def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
     """Set one simulation up (untimed), warm up, time args.steps cycles with CUDA events
     between the stages, then time args.e2e_steps cycles end to end through the C ABI."""
     import ctypes
@@ -189,8 +189,8 @@ def measure(args, w, P, npl, beams, mixed, dist, dev, world, local):
 
     from paper_1611_05712_gb300 import binding as bd
     n = len(P["x"])
-    sim = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}",
-                               precision=bd.PIC_MIXED_TF32X3 if mixed else bd.PIC_FP64)
+    mixed = prec != bd.PIC_FP64
+    sim = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}", precision=prec)
     wit_lo, wit_hi = beams[-1][0], beams[-1][1]
     tuning = sim.autotune() if mixed else None   # untimed: tile sizes for this workload
     sim.step(args.warmup)
@@ -236,15 +236,23 @@ def measure(args, w, P, npl, beams, mixed, dist, dev, world, local):
     launches_dht = 2 * args.steps
     achieved = (dht_flops_per_step * args.steps / launches_dht) / (dht_ms * 1e-3 / launches_dht) / 1e12
     share = dht_ms / sum(stage_ms.values())
-    if mixed:
+    if prec == bd.PIC_MIXED_TF32X3:
         # 3 TF32 products per algorithmic multiply-add; the TF32 peak is the measured BF16
         # burst x the recipe's nominal TF32/BF16 ratio (1.1 / 2.25)
         tf32_peak = BF16_TFLOPS * 1.1 / 2.25
         roofline = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
                     "frac": achieved / tf32_peak, "traffic": None,
                     "executed_tflops": 3 * achieved, "executed_frac": 3 * achieved / tf32_peak,
-                    "kernel": "k_dht_tc (3-term TF32 on tcgen05)",
+                    "kernel": "k_dht_tc<TF32x3> (3-term TF32 on tcgen05)",
                     "peak_source": "of measured: bf16 burst 1884.9 TFLOP/s x nominal tf32/bf16 1.1/2.25",
+                    "share_of_step": share}
+    elif prec == bd.PIC_MIXED_BF16X6:
+        # 6 BF16 products per algorithmic multiply-add against the measured BF16 burst peak
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": BF16_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / BF16_TFLOPS, "traffic": None,
+                    "executed_tflops": 6 * achieved, "executed_frac": 6 * achieved / BF16_TFLOPS,
+                    "kernel": "k_dht_tc<BF16x6> (6 BF16 split products on tcgen05)",
+                    "peak_source": "of measured: bf16 burst 1884.9 TFLOP/s",
                     "share_of_step": share}
     else:
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -258,7 +266,8 @@ def measure(args, w, P, npl, beams, mixed, dist, dev, world, local):
     out = {"steps_per_s": steps_per_s, "ms_per_step": el_ms / args.steps,
            "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
-           "dtype": "f32+tf32x3" if mixed else "f64"}
+           "dtype": {bd.PIC_FP64: "f64", bd.PIC_MIXED_TF32X3: "f32+tf32x3",
+                     bd.PIC_MIXED_BF16X6: "f32+bf16x6"}[prec]}
     if tuning is not None:
         out["tuning"] = tuning
     sim.close()
@@ -267,7 +276,7 @@ def measure(args, w, P, npl, beams, mixed, dist, dev, world, local):
     return out
 
 
-def accuracy_vs_fp64(w, P, npl, beams, n_cycles, local):
+def accuracy_vs_fp64(w, P, npl, beams, n_cycles, local, prec):
     """Error of the mixed form against the FP64 form after n_cycles from the same initial
     state: per field max |mixed - fp64| / max |fp64| over all components and modes, and the
     relative differences of each beam's normalised emittances and slice energy spread."""
@@ -276,8 +285,8 @@ def accuracy_vs_fp64(w, P, npl, beams, n_cycles, local):
 
     from paper_1611_05712_gb300 import binding as bd
     sims = {}
-    for name, prec in (("fp64", bd.PIC_FP64), ("mixed", bd.PIC_MIXED_TF32X3)):
-        s = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}", precision=prec)
+    for name, pr in (("fp64", bd.PIC_FP64), ("mixed", prec)):
+        s = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}", precision=pr)
         s.step(n_cycles)
         s.sync()
         sims[name] = s
@@ -329,7 +338,8 @@ def run_ours(args):
     w = workload(args.order, rank)
     P, npl, beams = W.particles(w)
     n = len(P["x"])
-    head = measure(args, w, P, npl, beams, args.precision == "mixed", dist, dev, world, local)
+    head_prec = {"fp64": bd.PIC_FP64, "mixed": bd.PIC_MIXED_TF32X3, "bf16": bd.PIC_MIXED_BF16X6}[args.precision]
+    head = measure(args, w, P, npl, beams, head_prec, dist, dev, world, local)
     line = {
         "metric": "pic_steps_per_s", "value": head["steps_per_s"], "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
@@ -341,18 +351,19 @@ def run_ours(args):
         "clocks": head["clocks"],
     }
     if args.precision == "fp64" and not args.no_mixed:
-        # the chosen mixed-precision form on the same workload (beam emittance and slice
-        # energy spread within 1e-4 of FP64: tests/test_gpu_mixed.py)
-        mx = measure(args, w, P, npl, beams, True, dist, dev, world, local)
-        line["mixed_form"] = {
-            "value": mx["steps_per_s"], "unit": "steps/s", "dtype": mx["dtype"],
-            "ms_per_step": mx["ms_per_step"], "particle_updates_per_s": mx["steps_per_s"] * n,
-            "speedup_vs_fp64": mx["steps_per_s"] / head["steps_per_s"],
-            "stage_ms_per_step": mx["stage_ms_per_step"], "roofline": mx["roofline"], "e2e": mx["e2e"],
-            "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"], "tuning": mx.get("tuning")}
-        if args.accuracy_cycles > 0:
-            line["mixed_form"]["accuracy_vs_fp64"] = accuracy_vs_fp64(w, P, npl, beams, args.accuracy_cycles,
-                                                                      local)
+        # the chosen mixed-precision form on the same workload (3-term TF32 DHT), and the
+        # BF16-split variant of it
+        for key, prec in (("mixed_form", bd.PIC_MIXED_TF32X3), ("mixed_form_bf16", bd.PIC_MIXED_BF16X6)):
+            mx = measure(args, w, P, npl, beams, prec, dist, dev, world, local)
+            line[key] = {
+                "value": mx["steps_per_s"], "unit": "steps/s", "dtype": mx["dtype"],
+                "ms_per_step": mx["ms_per_step"], "particle_updates_per_s": mx["steps_per_s"] * n,
+                "speedup_vs_fp64": mx["steps_per_s"] / head["steps_per_s"],
+                "stage_ms_per_step": mx["stage_ms_per_step"], "roofline": mx["roofline"], "e2e": mx["e2e"],
+                "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"], "tuning": mx.get("tuning")}
+            if args.accuracy_cycles > 0:
+                line[key]["accuracy_vs_fp64"] = accuracy_vs_fp64(w, P, npl, beams, args.accuracy_cycles, local,
+                                                                 prec)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, secs = oracle_steps_per_s(w, P, npl, beams, 1)
         line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": os.cpu_count(),
@@ -470,7 +481,8 @@ def run_large(args):
     n = len(P["x"])
     args.e2e_steps = min(args.e2e_steps, 2)   # each end-to-end cycle uploads 5.8 GB of particles
     t0 = time.perf_counter()
-    mx = measure(args, w, P, npl, beams, True, dist, dev, world, local)
+    from paper_1611_05712_gb300 import binding as bd
+    mx = measure(args, w, P, npl, beams, bd.PIC_MIXED_TF32X3, dist, dev, world, local)
     run_s = time.perf_counter() - t0
     cfg = config_of(w, n, "mixed")
     cfg["l2"] = "no flush: working set (fields + particles, ~21 GB) exceeds the 129 MB L2"

@@ -59,9 +59,13 @@ typedef enum {
 } pic_status;
 
 typedef enum {
-  PIC_FP64 = 0,         /* every stage in float64                                            */
-  PIC_MIXED_TF32X3 = 1  /* float32 grids and particles (cell-relative), DHT as 3-term TF32
-                           tcgen05 products with float32 accumulation; FP64 setup and diags  */
+  PIC_FP64 = 0,          /* every stage in float64                                           */
+  PIC_MIXED_TF32X3 = 1,  /* float32 grids, FP32 particles relative to their cell (momenta as
+                            float pairs), DHT as 3-term TF32 tcgen05 products with float32
+                            accumulation; FP64 setup and diagnostics                         */
+  PIC_MIXED_BF16X6 = 2   /* as PIC_MIXED_TF32X3 but the DHT splits each float into three
+                            BF16 pieces and sums the six products of order <= 2 on tcgen05
+                            (float32 accumulation); DHT row tiles of at most 128             */
 } pic_precision;
 
 typedef struct pic_config {
@@ -238,9 +242,10 @@ pic_status pic_batch_destroy(pic_batch* batch);
 
 /* ---- tile tuning -----------------------------------------------------------------
  * The paper gives no kernel tiling; these choices belong to this library.  Two tile sizes
- * of the mixed form (PIC_MIXED_TF32X3) are tunable:
+ * of the mixed forms (PIC_MIXED_TF32X3, PIC_MIXED_BF16X6) are tunable:
  *   dht_n_tile: rows of the Hankel matrix per tensor-core tile of the DHT (16..256, a
- *               multiple of 16; 0 = the built-in rule: Nr split into tiles of <= 256);
+ *               multiple of 16, capped at 128 in the BF16 form; 0 = the built-in rule: Nr
+ *               split into the fewest tiles of <= 256 (TF32) or <= 128 (BF16) rows);
  *   band_chunk: cell-sorted particles per CTA of the deposit kernels (512, 1024 or 2048),
  *               which also sets how many grid rows a CTA's shared-memory band covers.
  * Neither changes the arithmetic of a DHT output (same K order, bit-identical results);

@@ -16,7 +16,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "lib", "libpsatd_rz.so")
 HEADER = os.path.join(os.path.dirname(PKG), "include", "psatd_rz.h")
 
-PIC_FP64, PIC_MIXED_TF32X3 = 0, 1
+PIC_FP64, PIC_MIXED_TF32X3, PIC_MIXED_BF16X6 = 0, 1, 2
 PIC_DEP_RHO, PIC_DEP_J = 1, 2
 BUF = dict(E=0, B=1, EH=2, BH=3, DEP=4, SRC_H=5, RHO_PREV_H=6, RHO_ION=7, KPERP=8,
            HANKEL_INV=9, HANKEL_FWD=10, KZ_MOD=11, KEYS=12, PERM=13)

@@ -23,6 +23,7 @@
 // word on timeout.  The epilogue reads TMEM with tcgen05.ld (warp w owns TMEM lanes
 // 32*(w%4)..+31) and writes Yf[n][c] so that the 32 lanes of a warp store 32 consecutive c.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -36,8 +37,8 @@ namespace {
 
 constexpr int kTcThreads = 256;
 constexpr int kTcM = 128;          // rows of D (columns c of Xf) per CTA
-constexpr int kTcK = 32;           // floats of K per stage (128 bytes = one swizzle row)
-constexpr int kTcMaxN = 256;
+constexpr int kTcMaxN = 256;       // largest N tile, TF32 form
+constexpr int kTcMaxNBf16 = 128;   // largest N tile, BF16 form (three planes per operand)
 constexpr uint32_t kTcWaitCap = 1u << 26;   // mbarrier polls before giving up
 
 struct TcParams {
@@ -67,11 +68,6 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
   d |= (uint64_t)1u << 46;                          // descriptor version (SM100)
   d |= (uint64_t)2u << 61;                          // layout: SWIZZLE_128B
   return d;
-}
-
-// Instruction descriptor, kind::tf32: D f32, A/B tf32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t make_idesc(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 __device__ __forceinline__ float tf32_hi(float x) {
@@ -108,6 +104,53 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64
       : "memory");
 }
 
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                        uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// The two product kinds.  Planes are the pieces an operand is split into; product p
+// multiplies A plane a_plane[p] by B plane b_plane[p].
+//   TF32x3: x = hi + lo (hi = x rounded to TF32), products hi.hi, hi.lo, lo.hi;
+//   BF16x6: x = b0 + b1 + b2 (each the BF16 rounding of what is left), products of order
+//           <= 2: b0.b0, b0.b1, b1.b0, b0.b2, b1.b1, b2.b0.
+// A 128-byte swizzle row holds kChunkK elements; one MMA consumes 32 bytes of K.
+template <int KIND> struct TcKind;
+template <> struct TcKind<0> {
+  static constexpr int kPlanes = 2, kElemBytes = 4, kChunkK = 32, kProducts = 3;
+  static constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10);   // D f32, A/B tf32
+  __device__ static int a_plane(int p) { return p == 2 ? 1 : 0; }
+  __device__ static int b_plane(int p) { return p == 1 ? 1 : 0; }
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    mma_tf32(d, a, b, idesc, acc);
+  }
+};
+template <> struct TcKind<1> {
+  static constexpr int kPlanes = 3, kElemBytes = 2, kChunkK = 64, kProducts = 6;
+  static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10);   // D f32, A/B bf16
+  __device__ static int a_plane(int p) { return (p == 2 || p == 4) ? 1 : (p == 5 ? 2 : 0); }
+  __device__ static int b_plane(int p) { return (p == 1 || p == 4) ? 1 : (p == 3 ? 2 : 0); }
+  __device__ static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    mma_f16(d, a, b, idesc, acc);
+  }
+};
+
+// x = b0 + b1 + b2 with each piece the BF16 rounding of what is left (differences exact in
+// float); returns the three 16-bit patterns.
+__device__ __forceinline__ void split_bf16x3(float x, uint32_t& b0, uint32_t& b1, uint32_t& b2) {
+  const __nv_bfloat16 h0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h0);
+  const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+  const float r2 = r1 - __bfloat162float(h1);
+  b0 = __bfloat16_as_ushort(h0);
+  b1 = __bfloat16_as_ushort(h1);
+  b2 = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
@@ -129,21 +172,25 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, 
       : "memory");
 }
 
-// Tensor maps of the batch's split matrices (hi, lo), passed by value as a grid constant.
+// Tensor maps of the batch's split matrices (one per plane), passed by value as a grid
+// constant.
 struct TcMaps {
-  Sim::TensorMapBytes hi[24];
-  Sim::TensorMapBytes lo[24];
+  Sim::TensorMapBytes m[3][24];
 };
 
+template <int KIND>
 __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams P, const __grid_constant__ TcMaps maps,
                                                            int32_t* err) {
+  using K = TcKind<KIND>;
+  constexpr int NP = K::kPlanes;
+  constexpr int EPC = 16 / K::kElemBytes;   // K elements per 16-byte chunk of a swizzle row
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned carve-up: [stage][A_hi | A_lo | B_hi | B_lo], then barriers
+  // 1024-byte aligned carve-up: [stage][A planes | B planes], then barriers
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const uint32_t a_bytes = kTcM * 128;            // 16 KB
-  const uint32_t b_bytes = (uint32_t)P.NT * 128;  // up to 32 KB
-  const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  const uint32_t a_bytes = kTcM * 128;            // 16 KB per plane
+  const uint32_t b_bytes = (uint32_t)P.NT * 128;  // up to 32 KB per plane
+  const uint32_t stage_bytes = NP * (a_bytes + b_bytes);
   // bars[0..1]: per-stage "MMAs that read this stage are done"; bars[2..3]: per-stage
   // "matrix tiles have landed" (transaction counted)
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * stage_bytes);
@@ -169,29 +216,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams 
     mbar_init(&bars[2], 1);
     mbar_init(&bars[3], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.hi[b])) : "memory");
-    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.lo[b])) : "memory");
+#pragma unroll
+    for (int pl = 0; pl < NP; ++pl)
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.m[pl][b])) : "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = make_idesc(kTcM, P.NT);
-  const int nK = (P.Nr + kTcK - 1) / kTcK;
+  const uint32_t idesc = K::kIdesc | ((uint32_t)(P.NT >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+  const int nK = (P.Nr + K::kChunkK - 1) / K::kChunkK;
   bool ok = true;
   int issued = -1, committed = -1;   // last chunk whose matrix copies / MMAs were issued (block-uniform)
 
   // data-panel values of the next chunk, loaded ahead of the wait for a free stage:
-  // item it = tid + q*256 covers row c0 + (it % 128), 16-byte chunk it / 128 (4 values of j)
-  float pv[4][4];
+  // item it = tid + q*256 covers row c0 + (it % 128), 16-byte chunk it / 128 (EPC values of j)
+  float pv[4][EPC];
   auto load_chunk = [&](int kc) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int it = tid + q * kTcThreads;
       const int c = c0 + (it & (kTcM - 1)), ch = it >> 7;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int j = kc * kTcK + ch * 4 + e;
+      for (int e = 0; e < EPC; ++e) {
+        const int j = kc * K::kChunkK + ch * EPC + e;
         pv[q][e] = (c < P.Nc && j < P.Nr) ? X[(size_t)j * P.Nc + c] : 0.f;
       }
     }
@@ -204,15 +252,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams 
       const bool w = mbar_wait(&bars[st], (uint32_t)(((kc - 2) >> 1) & 1));
       if (!__syncthreads_and(w)) { ok = false; break; }   // one decision for the whole block
     }
-    unsigned char* sA = base + st * stage_bytes;
-    unsigned char* sAlo = sA + a_bytes;
-    unsigned char* sB = sAlo + a_bytes;
-    unsigned char* sBlo = sB + b_bytes;
-    const int k0 = kc * kTcK;
-    if (tid == 0) {   // matrix tiles (rows n0.., columns k0..k0+31; zero fill beyond Nr)
-      mbar_arrive_expect_tx(&bars[2 + st], 2 * b_bytes);
-      tma_load_2d(sB, &maps.hi[b], k0, n0, &bars[2 + st]);
-      tma_load_2d(sBlo, &maps.lo[b], k0, n0, &bars[2 + st]);
+    unsigned char* sA = base + st * stage_bytes;      // NP planes of a_bytes
+    unsigned char* sB = sA + NP * a_bytes;            // NP planes of b_bytes
+    const int k0 = kc * K::kChunkK;
+    if (tid == 0) {   // matrix tiles (rows n0.., columns k0..; zero fill beyond Nr)
+      mbar_arrive_expect_tx(&bars[2 + st], NP * b_bytes);
+#pragma unroll
+      for (int pl = 0; pl < NP; ++pl) tma_load_2d(sB + pl * b_bytes, &maps.m[pl][b], k0, n0, &bars[2 + st]);
     }
     issued = kc;
     // A operand (transposed X): split the prefetched values and store them swizzled
@@ -220,15 +266,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams 
     for (int q = 0; q < 4; ++q) {
       const int it = tid + q * kTcThreads;
       const int row = it & (kTcM - 1), ch = it >> 7;
-      float hv[4], lv[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        hv[e] = tf32_hi(pv[q][e]);
-        lv[e] = pv[q][e] - hv[e];
-      }
       const uint32_t off = sw128_off(row, ch);
-      *reinterpret_cast<float4*>(sA + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-      *reinterpret_cast<float4*>(sAlo + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+      if (KIND == 0) {
+        float hv[4], lv[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          hv[e] = tf32_hi(pv[q][e]);
+          lv[e] = pv[q][e] - hv[e];
+        }
+        *reinterpret_cast<float4*>(sA + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+        *reinterpret_cast<float4*>(sA + a_bytes + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+      } else {
+        uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+        for (int e = 0; e < EPC; e += 2) {
+          uint32_t a0, a1, a2, b0, b1, b2;
+          split_bf16x3(pv[q][e], a0, a1, a2);
+          split_bf16x3(pv[q][e + 1], b0, b1, b2);
+          w0[e / 2] = a0 | (b0 << 16);
+          w1[e / 2] = a1 | (b1 << 16);
+          w2[e / 2] = a2 | (b2 << 16);
+        }
+        *reinterpret_cast<uint4*>(sA + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        *reinterpret_cast<uint4*>(sA + a_bytes + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        *reinterpret_cast<uint4*>(sA + 2 * a_bytes + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+      }
     }
     if (kc + 1 < nK) load_chunk(kc + 1);   // in flight while this chunk is multiplied
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -236,14 +298,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams 
     if (!__syncthreads_and(landed)) { ok = false; break; }
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a_hi = smem_u32(sA), a_lo = smem_u32(sAlo), b_hi = smem_u32(sB), b_lo = smem_u32(sBlo);
+      const uint32_t sa = smem_u32(sA), sb = smem_u32(sB);
 #pragma unroll
-      for (int ks = 0; ks < kTcK / 8; ++ks) {
-        const uint32_t koff = ks * 32;   // 8 tf32 = 32 bytes along K inside the swizzle row
-        const uint32_t acc0 = (kc > 0 || ks > 0) ? 1u : 0u;
-        mma_tf32(tmem, make_desc(a_hi + koff), make_desc(b_hi + koff), idesc, acc0);
-        mma_tf32(tmem, make_desc(a_hi + koff), make_desc(b_lo + koff), idesc, 1u);
-        mma_tf32(tmem, make_desc(a_lo + koff), make_desc(b_hi + koff), idesc, 1u);
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint32_t koff = ks * 32;   // 32 bytes of K per MMA inside the swizzle row
+#pragma unroll
+        for (int pr = 0; pr < K::kProducts; ++pr) {
+          const uint32_t acc = (kc > 0 || ks > 0 || pr > 0) ? 1u : 0u;
+          K::mma(tmem, make_desc(sa + K::a_plane(pr) * a_bytes + koff), make_desc(sb + K::b_plane(pr) * b_bytes + koff),
+                 idesc, acc);
+        }
       }
       mma_commit(&bars[st]);
     }
@@ -296,10 +360,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams 
 
 }  // namespace
 
-size_t dht_tc_smem_bytes(int NT) { return 1024 + 2 * (2 * kTcM * 128 + 2 * (size_t)NT * 128) + 64; }
+// Dynamic shared memory of one launch: two stages of planes x (A tile + B tile), barriers.
+size_t dht_tc_smem_bytes(int planes, int NT) {
+  return 1024 + 2 * (size_t)planes * (kTcM * 128 + (size_t)NT * 128) + 64;
+}
 
-// Raised once per device to the largest tile (N_T = 256); per-launch changes of this
-// per-function attribute would race between host threads.
+// Raised once per device to the largest tile of each kind (TF32: N_T = 256, BF16: 128);
+// per-launch changes of this per-function attribute would race between host threads.
 pic_status dht_tc_configure_device() {
   static std::mutex mu;
   static bool done[64] = {};
@@ -307,24 +374,30 @@ pic_status dht_tc_configure_device() {
   PIC_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(mu);
   if (dev >= 0 && dev < 64 && done[dev]) return PIC_OK;
-  PIC_CUDA(cudaFuncSetAttribute(k_dht_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dht_tc_smem_bytes(kTcMaxN)));
+  PIC_CUDA(cudaFuncSetAttribute(k_dht_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dht_tc_smem_bytes(2, kTcMaxN)));
+  PIC_CUDA(cudaFuncSetAttribute(k_dht_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)dht_tc_smem_bytes(3, kTcMaxNBf16)));
   if (dev >= 0 && dev < 64) done[dev] = true;
   return PIC_OK;
 }
 
 namespace {
 
+bool is_bf16(const Sim* s) { return s->cfg.precision == PIC_MIXED_BF16X6; }
+
 // N tiling shared by the tensor maps and the launches: n_tiles tiles of NT rows of A
-// (the tuned tile if set, else Nr split into the fewest tiles of <= 256 rows).
+// (the tuned tile if set, else Nr split into the fewest tiles of <= 256 rows, or <= 128
+// in the BF16 form, whose three planes per operand fill shared memory at 128).
 void tc_tiles(const Sim* s, int* n_tiles, int* NT) {
   const int Nr = s->cfg.Nr;
+  const int cap = is_bf16(s) ? kTcMaxNBf16 : kTcMaxN;
   if (s->tune_nt > 0) {
-    *NT = std::min(s->tune_nt, (Nr + 15) / 16 * 16);
+    *NT = std::min(std::min(s->tune_nt, cap), (Nr + 15) / 16 * 16);
     *n_tiles = (Nr + *NT - 1) / *NT;
     return;
   }
-  *n_tiles = (Nr + kTcMaxN - 1) / kTcMaxN;
+  *n_tiles = (Nr + cap - 1) / cap;
   const int per = (Nr + *n_tiles - 1) / *n_tiles;
   *NT = (per + 15) / 16 * 16;
 }
@@ -348,8 +421,9 @@ EncodeTiledFn encode_fn() {
 
 }  // namespace
 
-// Tensor maps of the split matrices: 2-D float32 views (Nr columns j, Nr rows n, row
-// pitch split_pitch(Nr)), box 32 j x NT rows, 128-byte swizzle; coordinates past Nr read 0.
+// Tensor maps of the split matrices: 2-D views of each plane (Nr columns j, Nr rows n,
+// rows padded to 16 bytes), box of one 128-byte swizzle row of j (32 float or 64 BF16
+// elements) x NT rows, 128-byte swizzle; coordinates past Nr read 0.
 pic_status dht_tc_make_maps(Sim* s) {
   std::memset(s->tmaps, 0, sizeof(s->tmaps));
   if (s->cfg.precision == PIC_FP64) return PIC_OK;
@@ -358,24 +432,35 @@ pic_status dht_tc_make_maps(Sim* s) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return PIC_ERR_CUDA;
   }
-  const int Nr = s->cfg.Nr, pitch = split_pitch(Nr);
+  const bool bf = is_bf16(s);
+  const int Nr = s->cfg.Nr;
+  const int pitch = bf ? split_pitch_b16(Nr) : split_pitch(Nr);
+  const size_t esz = bf ? 2 : 4;
+  const int planes = bf ? 3 : 2;
   int n_tiles = 0, NT = 0;
   tc_tiles(s, &n_tiles, &NT);
-  const size_t mat_floats = (size_t)Nr * pitch;
+  const size_t mat_bytes = (size_t)Nr * pitch * esz;
+  const size_t plane_bytes = (size_t)s->cfg.Nm * 3 * mat_bytes;   // BF16: planes follow each other
   for (int dir = 0; dir < 2; ++dir) {
     for (int mi = 0; mi < s->cfg.Nm * 3; ++mi) {
-      for (int part = 0; part < 2; ++part) {
-        const size_t off = dir == 0 ? (part == 0 ? s->lay.mfwd_hi : s->lay.mfwd_lo)
-                                    : (part == 0 ? s->lay.binv_hi : s->lay.binv_lo);
-        float* g = s->at<float>(off) + (size_t)mi * mat_floats;
+      for (int part = 0; part < planes; ++part) {
+        char* g;
+        if (bf) {
+          g = s->at<char>(dir == 0 ? s->lay.mfwd_hi : s->lay.binv_hi) + part * plane_bytes + mi * mat_bytes;
+        } else {
+          const size_t off = dir == 0 ? (part == 0 ? s->lay.mfwd_hi : s->lay.mfwd_lo)
+                                      : (part == 0 ? s->lay.binv_hi : s->lay.binv_lo);
+          g = s->at<char>(off) + mi * mat_bytes;
+        }
         const cuuint64_t dims[2] = {(cuuint64_t)Nr, (cuuint64_t)Nr};
-        const cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
-        const cuuint32_t box[2] = {(cuuint32_t)kTcK, (cuuint32_t)NT};
+        const cuuint64_t strides[1] = {(cuuint64_t)pitch * esz};
+        const cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)NT};
         const cuuint32_t estr[2] = {1, 1};
         CUtensorMap* map = reinterpret_cast<CUtensorMap*>(s->tmaps[dir * kMaxModes * 3 + mi][part].b);
-        const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, g, dims, strides, box, estr,
-                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        const CUresult r = encode(map, bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                                  g, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
           set_error("cuTensorMapEncodeTiled failed (%d) for split matrix %d", (int)r, dir * kMaxModes * 3 + mi);
           return PIC_ERR_CUDA;
@@ -388,6 +473,7 @@ pic_status dht_tc_make_maps(Sim* s) {
 
 pic_status launch_dht_tc(Sim* s, const DhtBatch& b) {
   const int Nr = s->cfg.Nr, Nc = 2 * s->cfg.Nz;
+  const bool bf = is_bf16(s);
   TcParams P;
   P.Nr = Nr;
   P.Nc = Nc;
@@ -402,12 +488,13 @@ pic_status launch_dht_tc(Sim* s, const DhtBatch& b) {
       set_error("DHT batch entry %d has no split matrix", i);
       return PIC_ERR_ARG;
     }
-    maps.hi[i] = s->tmaps[b.mat[i]][0];
-    maps.lo[i] = s->tmaps[b.mat[i]][1];
+    for (int pl = 0; pl < 3; ++pl) maps.m[pl][i] = s->tmaps[b.mat[i]][pl];
   }
-  const size_t smem = dht_tc_smem_bytes(P.NT);
   dim3 grid(P.m_tiles, P.n_tiles, b.n);
-  k_dht_tc<<<grid, kTcThreads, smem, s->stream>>>(b, P, maps, s->at<int32_t>(s->lay.err));
+  if (bf)
+    k_dht_tc<1><<<grid, kTcThreads, dht_tc_smem_bytes(3, P.NT), s->stream>>>(b, P, maps, s->at<int32_t>(s->lay.err));
+  else
+    k_dht_tc<0><<<grid, kTcThreads, dht_tc_smem_bytes(2, P.NT), s->stream>>>(b, P, maps, s->at<int32_t>(s->lay.err));
   PIC_LAUNCHED(s);
   return PIC_OK;
 }

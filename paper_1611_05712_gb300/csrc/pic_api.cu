@@ -38,7 +38,7 @@ namespace {
 
 pic_status validate(const pic_config* c, int32_t* radix, int32_t* n_pass) {
   if (!c) { set_error("config is NULL"); return PIC_ERR_ARG; }
-  if (c->precision != PIC_FP64 && c->precision != PIC_MIXED_TF32X3) {
+  if (c->precision != PIC_FP64 && c->precision != PIC_MIXED_TF32X3 && c->precision != PIC_MIXED_BF16X6) {
     set_error("precision %d is not a pic_precision", c->precision);
     return PIC_ERR_ARG;
   }
@@ -108,10 +108,17 @@ Layout make_layout(const pic_config& c) {
     L.tr_f = take((size_t)c.Nm * c.Nr * 4);
     L.twiddle_f = take((size_t)c.Nz * 8);
     L.twp_f = take((size_t)c.Nz * 8);
-    L.mfwd_hi = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
-    L.mfwd_lo = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
-    L.binv_hi = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
-    L.binv_lo = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
+    if (c.precision == PIC_MIXED_BF16X6) {
+      // three BF16 planes per matrix, rows padded to 16 bytes
+      const size_t plane = (size_t)c.Nm * 3 * c.Nr * split_pitch_b16(c.Nr) * 2;
+      L.mfwd_hi = take(3 * plane);
+      L.binv_hi = take(3 * plane);
+    } else {
+      L.mfwd_hi = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
+      L.mfwd_lo = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
+      L.binv_hi = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
+      L.binv_lo = take((size_t)c.Nm * 3 * c.Nr * split_pitch(c.Nr) * 4);
+    }
   } else {
     for (int b = 0; b < 2; ++b) {
       for (int k = 0; k < 7; ++k) L.part[b][k] = take(cap * 8);

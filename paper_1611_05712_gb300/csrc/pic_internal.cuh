@@ -40,7 +40,7 @@ struct Layout {
   // mixed-precision form only (0 otherwise): float copies of the tables, the split DHT
   // matrices, FP32 cell-relative particles and an FP64 staging area for particle IO
   size_t coef_f, kperp_f, kzmod_f, tz_f, tr_f, twiddle_f, twp_f;
-  size_t mfwd_hi, mfwd_lo, binv_hi, binv_lo;
+  size_t mfwd_hi, mfwd_lo, binv_hi, binv_lo;   // TF32 form: hi/lo planes; BF16 form: *_hi = 3 planes
   size_t pf[2][13];  // iz, fz, ixy (packed int16 x, y cells), fx, fy, u/c hi (3), u/c lo (3), w, id
   size_t stage64;    // 7 x capacity float64
   size_t total;
@@ -49,6 +49,8 @@ struct Layout {
 // Row pitch (floats) of the split DHT matrices of the mixed form: Nr rounded up to a
 // multiple of 4 so that rows start on 16-byte boundaries (tensor-memory-access copies).
 inline int split_pitch(int Nr) { return (Nr + 3) / 4 * 4; }
+// Row pitch (elements) of the BF16 planes of the BF16 form: Nr rounded up to a multiple of 8.
+inline int split_pitch_b16(int Nr) { return (Nr + 7) / 8 * 8; }
 
 // FP32 particle array indices of the mixed form: z = (iz + fz) dz, x = (ix + fx) dr,
 // y = (iy + fy) dr with fz, fx, fy in [0, 1) and (ix, iy) two int16 packed in one int32;
@@ -74,11 +76,11 @@ struct Sim {
   size_t cplx_bytes;       // 16 (FP64) or 8 (mixed)
   int32_t tune_nt;         // mixed-form DHT N tile (0: built-in rule), see pic_set_tuning
   int32_t tune_chunk;      // particles per CTA of the band kernels
-  // mixed form: encoded 2-D tensor maps (CUtensorMap, 128 B each) of the split DHT
-  // matrices, [matrix id][hi, lo], built once at init
+  // mixed forms: encoded 2-D tensor maps (CUtensorMap, 128 B each) of the split DHT
+  // matrices, [matrix id][plane] (TF32: hi, lo; BF16: three pieces), built at init
   struct alignas(64) TensorMapBytes {
     unsigned char b[128];
-  } tmaps[2 * kMaxModes * 3][2];
+  } tmaps[2 * kMaxModes * 3][3];
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   size_t grid_elems() const { return (size_t)cfg.Nm * cfg.Nr * cfg.Nz; }

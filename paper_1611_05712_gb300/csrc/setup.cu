@@ -11,6 +11,8 @@
 
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -406,6 +408,27 @@ __global__ void k_split_tf32(const double* __restrict__ in, float* __restrict__ 
   }
 }
 
+// Split of FP64 matrices (rows of Nr) into three BF16 pieces for the BF16 form:
+// b0 = bf16(a), b1 = bf16(a - b0), b2 = bf16(a - b0 - b1) (differences in FP64), stored as
+// three planes of rows with a pitch of `pitch` >= Nr elements (16-byte multiple); the
+// padding is zero.
+__global__ void k_split_bf16x3(const double* __restrict__ in, __nv_bfloat16* __restrict__ p0,
+                               __nv_bfloat16* __restrict__ p1, __nv_bfloat16* __restrict__ p2, size_t rows,
+                               int Nr, int pitch) {
+  const size_t n = rows * (size_t)pitch;
+  for (size_t o = blockIdx.x * (size_t)blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const int col = (int)(o % pitch);
+    double v = col < Nr ? in[(o / pitch) * Nr + col] : 0.0;
+    const __nv_bfloat16 b0 = __double2bfloat16(v);
+    v -= (double)__bfloat162float(b0);
+    const __nv_bfloat16 b1 = __double2bfloat16(v);
+    v -= (double)__bfloat162float(b1);
+    p0[o] = b0;
+    p1[o] = b1;
+    p2[o] = __double2bfloat16(v);
+  }
+}
+
 inline int conv_grid(size_t n) { return (int)std::min<size_t>(blocks_for(n, 256), 152 * 16); }
 
 }  // namespace
@@ -420,6 +443,17 @@ pic_status convert_hankel_tables(Sim* s) {
   PIC_LAUNCHED(s);
   k_to_float<<<conv_grid(nmn), 256, 0, s->stream>>>(s->at<double>(s->lay.tr), s->at<float>(s->lay.tr_f), nmn);
   PIC_LAUNCHED(s);
+  if (c.precision == PIC_MIXED_BF16X6) {
+    const int pb = split_pitch_b16(c.Nr);
+    const size_t plane = rows * pb;
+    for (int dir = 0; dir < 2; ++dir) {
+      __nv_bfloat16* base = s->at<__nv_bfloat16>(dir == 0 ? s->lay.mfwd_hi : s->lay.binv_hi);
+      k_split_bf16x3<<<conv_grid(plane), 256, 0, s->stream>>>(s->at<double>(dir == 0 ? s->lay.mfwd : s->lay.binv),
+                                                               base, base + plane, base + 2 * plane, rows, c.Nr, pb);
+      PIC_LAUNCHED(s);
+    }
+    return PIC_OK;
+  }
   k_split_tf32<<<conv_grid(nmat), 256, 0, s->stream>>>(s->at<double>(s->lay.mfwd), s->at<float>(s->lay.mfwd_hi),
                                                          s->at<float>(s->lay.mfwd_lo), rows, c.Nr, pitch);
   PIC_LAUNCHED(s);
