@@ -54,6 +54,9 @@ def parse():
                          "(order / resolution scan) advanced by one CUDA graph per launch; "
                          "large: the 8192x1024 3-mode run with ~103M particles, mixed form")
     ap.add_argument("--sims", type=int, default=64, help="simulations in the scan workload")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket each timed region with cudaProfilerStart/Stop (for "
+                         "ncu --profile-from-start off); no work is skipped")
     return ap.parse_args()
 
 
@@ -203,7 +206,12 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
+        if args.profile_range:
+            torch.cuda.profiler.start()
         stage_ms, total_ms = sim.step_timed(args.steps)
+        if args.profile_range:
+            torch.cuda.synchronize(dev)
+            torch.cuda.profiler.stop()
     torch.cuda.synchronize(dev)
     launches = sim.launch_count() - l0
     el_ms = reduce_max(total_ms, dist, dev)
