@@ -502,7 +502,27 @@ __device__ __forceinline__ void polar_f(float x, float y, float& r, float& c, fl
   if (r > 0.f) { c = x / r; s = y / r; } else { c = 1.f; s = 0.f; }
 }
 
-__device__ __forceinline__ float2 interp_f(const float2* grid, const GeomF& g, const StencilF& st, float fold) {
+// Transpose of [plane][Nr][Nz] complex planes into [plane][Nz][Nr] (32 x 32 tiles staged in
+// shared memory, both sides coalesced): the gather reads the 4 nodes of a warp's
+// particles, which sit in consecutive r cells of one z row, from consecutive addresses.
+__global__ void k_transpose_rz(const float2* __restrict__ src, float2* __restrict__ dst, int Nr, int Nz) {
+  __shared__ float2 tile[32][33];
+  const size_t plane = (size_t)blockIdx.z * Nr * Nz;
+  const int z0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int r = r0 + k, z = z0 + threadIdx.x;
+    if (r < Nr && z < Nz) tile[k][threadIdx.x] = src[plane + (size_t)r * Nz + z];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int z = z0 + k, r = r0 + threadIdx.x;
+    if (r < Nr && z < Nz) dst[plane + (size_t)z * Nr + r] = tile[threadIdx.x][k];
+  }
+}
+
+// Linear interpolation of one complex mode component from the r-fastest copy
+// ([Nz][Nr] plane), with the axis fold of node -1.
+__device__ __forceinline__ float2 interp_t(const float2* grid, const GeomF& g, const StencilF& st, float fold) {
   float re = 0.f, im = 0.f;
 #pragma unroll
   for (int dj = 0; dj < 2; ++dj) {
@@ -510,8 +530,8 @@ __device__ __forceinline__ float2 interp_f(const float2* grid, const GeomF& g, c
     float wr = dj ? st.wr1 : st.wr0;
     if (j < 0) { j = -1 - j; wr *= fold; }
     if (j >= g.Nr) continue;
-    const float2 a = grid[(size_t)j * g.Nz + st.i0];
-    const float2 b = grid[(size_t)j * g.Nz + st.i1];
+    const float2 a = grid[(size_t)st.i0 * g.Nr + j];
+    const float2 b = grid[(size_t)st.i1 * g.Nr + j];
     re += wr * (st.wz0 * a.x + st.wz1 * b.x);
     im += wr * (st.wz0 * a.y + st.wz1 * b.y);
   }
@@ -533,8 +553,8 @@ struct DepArgsF {
 // The band holds fixed-point sums: a contribution x (charge times weights, before the
 // 1/V_j factor) is y = x 2^S rounded to an integer and split as y = 2^16 hi + lo with
 // 0 <= lo <= 2^16, and hi and lo are added to two int32 planes.  Integer shared-memory
-// atomics are native and are not slowed by lanes that hit the same node (particles of one
-// cell do), unlike float ones; integer sums are also independent of the order of the adds.
+// atomics are native (float ones are compare-and-swap loops), and integer sums do not
+// depend on the order of the adds.
 // S is chosen per CTA so that |y| <= 2^(46 - log2 chunk) for every contribution of its
 // chunk (2^36 for 1024 particles): |sum of hi| < 2^30 and sum of lo <= 2^(16 + log2 chunk)
 // cannot overflow, and the resolution is 2^-36 (chunk 1024) of the largest possible
@@ -745,15 +765,40 @@ __global__ void k_keys_f32(const PartsF p, int64_t np, GeomF g, int32_t* keys, i
   }
 }
 
-__global__ void k_permute_f32(const PartsF src, PartsF dst, const int32_t* perm, int64_t np) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t k = perm[i];
-    dst.iz[i] = src.iz[k]; dst.fz[i] = src.fz[k]; dst.ixy[i] = src.ixy[k]; dst.fx[i] = src.fx[k];
-    dst.fy[i] = src.fy[k];
-    dst.ux[i] = src.ux[k]; dst.uy[i] = src.uy[k]; dst.uz[i] = src.uz[k];
-    dst.uxl[i] = src.uxl[k]; dst.uyl[i] = src.uyl[k]; dst.uzl[i] = src.uzl[k];
-    dst.w[i] = src.w[k]; dst.id[i] = src.id[k];
+// dst[i] = src[perm[i]] for the 13 arrays; four particles per thread, all loads issued
+// before the stores (the gathered reads are latency-bound).
+__global__ void k_permute_f32(const PartsF src, PartsF dst, const int32_t* __restrict__ perm, int64_t np) {
+  constexpr int U = 4;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < np; i0 += U * stride) {
+    int32_t k[U];
+    bool ok[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t i = i0 + u * stride;
+      ok[u] = i < np;
+      k[u] = ok[u] ? perm[i] : 0;
+    }
+    int32_t iz[U], ixy[U], id[U];
+    float fz[U], fx[U], fy[U], ux[U], uy[U], uz[U], uxl[U], uyl[U], uzl[U], w[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!ok[u]) continue;
+      const int32_t j = k[u];
+      iz[u] = src.iz[j]; fz[u] = src.fz[j]; ixy[u] = src.ixy[j]; fx[u] = src.fx[j]; fy[u] = src.fy[j];
+      ux[u] = src.ux[j]; uy[u] = src.uy[j]; uz[u] = src.uz[j];
+      uxl[u] = src.uxl[j]; uyl[u] = src.uyl[j]; uzl[u] = src.uzl[j];
+      w[u] = src.w[j]; id[u] = src.id[j];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!ok[u]) continue;
+      const int64_t i = i0 + u * stride;
+      dst.iz[i] = iz[u]; dst.fz[i] = fz[u]; dst.ixy[i] = ixy[u]; dst.fx[i] = fx[u]; dst.fy[i] = fy[u];
+      dst.ux[i] = ux[u]; dst.uy[i] = uy[u]; dst.uz[i] = uz[u];
+      dst.uxl[i] = uxl[u]; dst.uyl[i] = uyl[u]; dst.uzl[i] = uzl[u];
+      dst.w[i] = w[u]; dst.id[i] = id[u];
+    }
   }
 }
 
@@ -823,8 +868,8 @@ __device__ __forceinline__ void advance_z(int& iz, float& fz, float dfz, int Nz)
 // One CTA per chunk of `chunk` consecutive (cell-sorted) particles; with tz > 0 the fused J
 // deposit accumulates into a band of tz z-rows from one row below the chunk's first cell
 // (a half step moves a particle by at most half a cell at c dt <= dz).
-__global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, int64_t np, GeomF g, const float2* __restrict__ E,
-                                  const float2* __restrict__ B, float kq, float kqc, float chdt_dr,
+__global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, int64_t np, GeomF g,
+                                  const float2* __restrict__ EBt, float kq, float kqc, float chdt_dr,
                                   float chdt_dz, DepArgsF dep, const float* invV, int fuse, int32_t* err,
                                   BandArgs ba) {
   extern __shared__ __align__(16) int32_t band_smem[];
@@ -867,8 +912,8 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
       const float mult = m == 0 ? 1.f : 2.f;
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
-        const float2* base = (k < 3 ? E : B) + (size_t)(k % 3) * g.G + m * RZ;
-        const float2 v = interp_f(base, g, st, (k % 3) == 2 ? fs : fv);
+        const float2* base = EBt + (size_t)k * g.G + m * RZ;   // E r, th, z, then B r, th, z
+        const float2 v = interp_t(base, g, st, (k % 3) == 2 ? fs : fv);
         F[k] += mult * (v.x * phr - v.y * phi);
       }
       const float nr = phr * c + phi * s, ni = phi * c - phr * s;
@@ -1301,8 +1346,13 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current) {
     const float chdt_dz = (float)(0.5 * kC * c.dt / c.dz);
     // a half step moves a particle by at most c dt / 2 in r
     const BandPlan bp = band_plan(s, fuse_current ? 3 : 0, 1 + (int)std::ceil(0.5 * kC * c.dt / c.dr));
+    // E and B (adjacent, 6 x Nm planes) into the r-fastest gather layout
+    dim3 tgrid((c.Nz + 31) / 32, (c.Nr + 31) / 32, 6 * c.Nm);
+    k_transpose_rz<<<tgrid, dim3(32, 8), 0, s->stream>>>(s->at<float2>(s->lay.E), s->at<float2>(s->lay.ebt), c.Nr,
+                                                          c.Nz);
+    PIC_LAUNCHED(s);
     k_gather_push_f32<<<(int)((s->np + bp.args.chunk - 1) / bp.args.chunk), kBandThreads, bp.smem, s->stream>>>(
-        partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.E), s->at<float2>(s->lay.B), kq, kqc,
+        partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.ebt), kq, kqc,
         chdt_dr, chdt_dz, a, reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args);
   } else {
     DepArgs a;

@@ -101,6 +101,7 @@ Layout make_layout(const pic_config& c) {
     for (int b = 0; b < 2; ++b)
       for (int k = 0; k < kPfCount; ++k) L.pf[b][k] = take(cap * 4);
     L.stage64 = take(7 * cap * 8);
+    L.ebt = take(6 * G * 8);
     L.coef_f = take(6 * G * 4);
     L.kperp_f = take((size_t)c.Nm * c.Nr * 4);
     L.kzmod_f = take((size_t)c.Nz * 4);

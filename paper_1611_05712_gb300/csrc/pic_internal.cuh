@@ -43,6 +43,7 @@ struct Layout {
   size_t mfwd_hi, mfwd_lo, binv_hi, binv_lo;   // TF32 form: hi/lo planes; BF16 form: *_hi = 3 planes
   size_t pf[2][13];  // iz, fz, ixy (packed int16 x, y cells), fx, fy, u/c hi (3), u/c lo (3), w, id
   size_t stage64;    // 7 x capacity float64
+  size_t ebt;        // E, B with r fastest: [6][Nm][Nz][Nr] complex float (gather layout)
   size_t total;
 };
 
