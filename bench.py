@@ -28,9 +28,9 @@ sys.path.insert(0, ROOT)
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2070 MHz (nominal 1.25)
 BF16_TFLOPS = 1884.9                           # MEASURED_PEAKS.json bf16 burst
 FP64_PROBE_TFLOPS = 1.1947                     # FMA-loop probe on this machine's GB300 at 1987 MHz
-# DRAM bytes per k_dht_f64 launch on this workload, from one ncu capture of the current kernel
-# (forward 71.29 + 28.10 MB, inverse 107.18 + 61.11 MB, mean of the two launches)
-DHT_F64_TRAFFIC_BYTES = (71.288064 + 28.1024 + 107.177728 + 61.111552) / 2 * 1e6
+# DRAM bytes per FP64 DHT launch (k_gemm<double>) on this workload, from one ncu capture of
+# the current kernel (forward 71.51 + 27.33 MB, inverse 107.24 + 61.24 MB, mean of the two)
+DHT_F64_TRAFFIC_BYTES = (71.50592 + 27.328 + 107.238912 + 61.2352) / 2 * 1e6
 
 
 def parse():
@@ -266,8 +266,8 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
         roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": DHT_F64_TRAFFIC_BYTES,
                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the "
-                                      "forward and inverse launch (profiles/k_dht_f64__wake_2048x256_m2_fp64.md)",
-                    "kernel": "k_dht_f64 (forward and inverse DHT, FP64 SIMT)",
+                                      "forward and inverse launch (profiles/k_gemm_f64__wake_2048x256_m2_fp64.md)",
+                    "kernel": "k_gemm<double> (forward and inverse DHT, FP64 SIMT)",
                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe nominal "
                                    "1.25 TFLOP/s); FMA probe measured 1.195 TFLOP/s",
                     "share_of_step": share}
