@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--accuracy-cycles", type=int, default=100,
                     help="cycles after which the mixed form's fields and beam quality are "
                          "compared with the FP64 form (0: skip)")
-    ap.add_argument("--workload", choices=["wake", "scan", "large"], default="wake",
+    ap.add_argument("--workload", choices=["wake", "scan", "large", "guard"], default="wake",
                     help="wake: the 2048x256 wakefield run; scan: many uneven simulations "
                          "(order / resolution scan) advanced by one CUDA graph per launch; "
                          "large: the 8192x1024 3-mode run with ~103M particles, mixed form")
@@ -512,6 +512,50 @@ def run_large(args):
     return 0
 
 
+def run_guard(args):
+    """Guard-cell domain decomposition along z (FP64, no sources): max relative difference
+    between four subdomains advanced with their own FFT over interior + g guard cells and
+    the global field step, for stencil orders p and guard widths g."""
+    import numpy as np
+
+    from oracle import psatd_rz as O
+    from paper_1611_05712_gb300 import binding as bd
+    from paper_1611_05712_gb300.build import build
+    from paper_1611_05712_gb300.domains import GuardedDomains
+    build()
+    Nz, Nr, Nm, dz = 512, 32, 2, 0.05e-6
+    table = {}
+    for p in (8, 16, 32, 64, 0):
+        row = {}
+        for g in (0, 8, 16, 32, 48, 64, 96, 128):
+            cfg = bd.make_config(Nz, Nr, Nm, dz, dz, dz / O.C_LIGHT, p, True, bd.PIC_FP64, 0)
+            glob, out = bd.Sim(cfg), bd.Sim(cfg)
+            rng = np.random.default_rng(7)
+            shape = (3, Nm, Nr, Nz)
+            glob.set("E", rng.normal(size=shape) + 1j * rng.normal(size=shape))
+            glob.set("B", (rng.normal(size=shape) + 1j * rng.normal(size=shape)) / O.C_LIGHT)
+            for h in (glob, out):
+                h.set("DEP", h.zeros("DEP"))
+                h.set("RHO_PREV_H", h.zeros("RHO_PREV_H"))
+            dom = GuardedDomains(cfg, 4, g)
+            dom.field_step(glob, out)
+            glob.fields_to_spectral()
+            glob.field_step()
+            err = 0.0
+            for name in ("E", "B"):
+                a, b = out.get(name), glob.get(name)
+                err = max(err, float(np.abs(a - b).max() / np.abs(b).max()))
+            row[g] = err
+            for h in (dom, glob, out):
+                h.close()
+        table["inf" if p == 0 else str(p)] = row
+    print(json.dumps({"metric": "guard_cell_decomposition_error", "unit": "max relative difference",
+                      "config": {"Nz": Nz, "Nr": Nr, "Nm": Nm, "subdomains": 4, "precision": "fp64",
+                                 "fields": "random E, B, no sources", "steps": 1},
+                      "error_by_order_and_guard": table}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -520,6 +564,8 @@ def main():
         return run_scan(args)
     if args.workload == "large":
         return run_large(args)
+    if args.workload == "guard":
+        return run_guard(args)
     return run_ours(args)
 
 

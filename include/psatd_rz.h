@@ -240,6 +240,30 @@ pic_status pic_batch_launch(pic_batch* batch, int32_t n_launches);
 pic_status pic_batch_info(pic_batch* batch, int32_t* cycles_per_launch, int64_t* kernels_per_launch);
 pic_status pic_batch_destroy(pic_batch* batch);
 
+/* ---- domain decomposition along z ---------------------------------------------------
+ * A stencil of finite order p reaches only a finite number of cells (section "Finite order
+ * pseudo-spectral solvers", unit-pulse figure; "Conclusion": about 60 guard cells at
+ * p = 32), so a z subdomain extended by that many guard cells on each side can be advanced
+ * with its own Fourier transform and reproduce the global update in its interior.  These
+ * two calls let a caller build that scheme from several handles of equal Nr, Nm and
+ * precision (one per subdomain, Nz = interior + 2 guards).
+ *
+ * pic_fields_to_spectral: Eh, Bh <- forward transforms (z-FFT, then the DHT of orders m+1,
+ * m-1, m per mode) of the real-space E, B buffers, with F_+- = (F_r -/+ i F_theta)/2.  The
+ * counterpart of pic_inverse_transform; it sets the spectral field state from real-space
+ * fields loaded with pic_load_buffer or pic_copy_window.  Asynchronous.
+ *
+ * pic_copy_window: for every (component, mode, r) row of a real-space grid buffer
+ * (PIC_BUF_E, PIC_BUF_B, PIC_BUF_DEP or PIC_BUF_RHO_ION),
+ *     dst[row][(dst_z0 + t) mod dst.Nz] = src[row][(src_z0 + t) mod src.Nz],  0 <= t < nz,
+ * i.e. a periodic window of the source written, periodically, into the destination.
+ * 0 <= nz <= both Nz.  The copy runs on the destination's stream: order it after work on
+ * the source's stream (same stream, or synchronise first).  Errors: PIC_ERR_ARG
+ * (another buffer, unequal Nr / Nm / precision, nz out of range), PIC_ERR_CUDA. */
+pic_status pic_fields_to_spectral(pic_sim* sim);
+pic_status pic_copy_window(pic_sim* src, int32_t buffer_id, int32_t src_z0, int32_t nz, pic_sim* dst,
+                           int32_t dst_z0);
+
 /* ---- tile tuning -----------------------------------------------------------------
  * The paper gives no kernel tiling; these choices belong to this library.  Two tile sizes
  * of the mixed forms (PIC_MIXED_TF32X3, PIC_MIXED_BF16X6) are tunable:

@@ -104,6 +104,8 @@ def load():
         "pic_autotune": [P, ctypes.POINTER(PicTuning)],
         "pic_set_tuning": [P, ctypes.POINTER(PicTuning)],
         "pic_get_tuning": [P, ctypes.POINTER(PicTuning)],
+        "pic_fields_to_spectral": [P],
+        "pic_copy_window": [P, I32, I32, I32, P, I32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -219,6 +221,14 @@ class Sim:
     def field_step(self, order_p=-1):
         _check(self.lib.pic_field_step(self.h, int(order_p)), "pic_field_step")
 
+    def fields_to_spectral(self):
+        _check(self.lib.pic_fields_to_spectral(self.h), "pic_fields_to_spectral")
+
+    def copy_window_to(self, dst, name, src_z0, nz, dst_z0):
+        """Periodic z window of buffer ``name`` of this handle into handle ``dst``."""
+        _check(self.lib.pic_copy_window(self.h, BUF[name], int(src_z0), int(nz), dst.h, int(dst_z0)),
+               "pic_copy_window")
+
     def forward_transform(self):
         _check(self.lib.pic_forward_transform(self.h), "pic_forward_transform")
 
@@ -299,6 +309,11 @@ class Sim:
         _check(self.lib.pic_copy_buffer(self.h, BUF[name], ctypes.c_void_p(out.ctypes.data), nb, 1),
                "pic_copy_buffer")
         return out.reshape(self._shape(name))
+
+    def zeros(self, name):
+        """A host array of zeros with the shape and element type of buffer ``name``."""
+        nb = self.buffer_bytes(name)
+        return np.zeros(nb // np.dtype(self._dtype(name)).itemsize, self._dtype(name)).reshape(self._shape(name))
 
     def set(self, name, arr):
         """Copy a host numpy array into an internal buffer."""

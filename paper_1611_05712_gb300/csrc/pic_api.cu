@@ -206,6 +206,39 @@ pic_status dht_forward(Sim* s, int n_comp) {
   return launch_dht(s, b);
 }
 
+// Forward transforms of the real-space fields into the spectral state: z-FFT of E, B with
+// F_+- = (F_r -+ i F_theta)/2 formed on load, then the DHT of orders m+1, m-1, m into Eh, Bh.
+pic_status fields_forward(Sim* s) {
+  const pic_config& c = s->cfg;
+  RowCombine rc{};
+  rc.n_out = 6;
+  for (int f = 0; f < 2; ++f) {
+    const int o = 3 * f;
+    rc.srcA[o + 0] = o; rc.caRe[o + 0] = 0.5; rc.srcB[o + 0] = o + 1; rc.cbIm[o + 0] = -0.5;
+    rc.srcA[o + 1] = o; rc.caRe[o + 1] = 0.5; rc.srcB[o + 1] = o + 1; rc.cbIm[o + 1] = 0.5;
+    rc.srcA[o + 2] = o + 2; rc.caRe[o + 2] = 1.0; rc.srcB[o + 2] = -1;
+  }
+  pic_status st = launch_fft_rows(s, s->at<char>(s->lay.E), s->at<char>(s->lay.tmp), rc, false);
+  if (st != PIC_OK) return st;
+  const size_t G = s->grid_elems();
+  const size_t Nr2 = (size_t)c.Nr * c.Nr;
+  const int slot_of[3] = {2, 0, 1};      // +: m+1, -: m-1, z: m
+  DhtBatch b{};
+  for (int comp = 0; comp < 6; ++comp)
+    for (int m = 0; m < c.Nm; ++m) {
+      const int slot = slot_of[comp % 3];
+      if (c.precision == PIC_FP64) {
+        b.A[b.n] = s->at<double>(s->lay.mfwd) + ((size_t)m * 3 + slot) * Nr2;
+      } else {
+        b.mat[b.n] = (int16_t)(m * 3 + slot);
+      }
+      b.X[b.n] = s->at<char>(s->lay.tmp) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
+      b.Y[b.n] = s->at<char>(s->lay.Eh) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
+      ++b.n;
+    }
+  return launch_dht(s, b);
+}
+
 pic_status forward_transform(Sim* s, int n_comp) {
   pic_status st = fft_forward(s, n_comp);
   if (st != PIC_OK) return st;
@@ -483,6 +516,43 @@ pic_status pic_get_tuning(pic_sim* sim, pic_tuning* out) {
   if (!out) { set_error("out is NULL"); return PIC_ERR_ARG; }
   *out = pic_tuning{s->tune_nt, s->tune_chunk, 0.0, 0.0};
   return PIC_OK;
+}
+
+pic_status pic_fields_to_spectral(pic_sim* sim) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  return fields_forward(s);
+}
+
+pic_status pic_copy_window(pic_sim* src_sim, int32_t buffer_id, int32_t src_z0, int32_t nz, pic_sim* dst_sim,
+                           int32_t dst_z0) {
+  Sim* a = reinterpret_cast<Sim*>(src_sim);
+  Sim* b = reinterpret_cast<Sim*>(dst_sim);
+  CHECK_SIM(a);
+  CHECK_SIM(b);
+  int ncomp = 0;
+  switch (buffer_id) {
+    case PIC_BUF_E: case PIC_BUF_B: ncomp = 3; break;
+    case PIC_BUF_DEP: ncomp = 4; break;
+    case PIC_BUF_RHO_ION: ncomp = 1; break;
+    default:
+      set_error("buffer %d is not a real-space grid (E, B, DEP or RHO_ION)", buffer_id);
+      return PIC_ERR_ARG;
+  }
+  if (a->cfg.Nr != b->cfg.Nr || a->cfg.Nm != b->cfg.Nm || a->cplx_bytes != b->cplx_bytes) {
+    set_error("windows copy between handles of equal Nr, Nm and precision only");
+    return PIC_ERR_ARG;
+  }
+  if (nz < 0 || nz > a->cfg.Nz || nz > b->cfg.Nz) {
+    set_error("nz=%d exceeds a grid (source Nz=%d, destination Nz=%d)", nz, a->cfg.Nz, b->cfg.Nz);
+    return PIC_ERR_ARG;
+  }
+  if (nz == 0) return PIC_OK;
+  BufView va, vb;
+  buffer_view(a, buffer_id, &va);
+  buffer_view(b, buffer_id, &vb);
+  return launch_copy_window(b, a->ws + va.off, a->cfg.Nz, src_z0, b->ws + vb.off, b->cfg.Nz, dst_z0, nz,
+                            ncomp * a->cfg.Nm * a->cfg.Nr);
 }
 
 pic_status pic_destroy(pic_sim* sim) {

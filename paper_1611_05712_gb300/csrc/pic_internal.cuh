@@ -148,6 +148,12 @@ pic_status launch_beam_fields(Sim* s, const void* rho_h, double gamma);  // adds
 pic_status launch_filter_copy(Sim* s, void* dst, const void* src);        // dst = T * src
 pic_status launch_scale_copy(Sim* s, void* dst, const void* src, double a, size_t n_cplx);
 
+// ---- launchers (domain.cu) ----
+// dst rows [row][dst_z0 + t mod dst_nz] = src rows [row][src_z0 + t mod src_nz], t < nz, for
+// `rows` complex rows of either element size (cplx_bytes of dst), on dst's stream.
+pic_status launch_copy_window(Sim* dst_sim, const char* src, int src_nz, int src_z0, char* dst, int dst_nz,
+                              int dst_z0, int nz, int rows);
+
 // ---- launchers (particles.cu) ----
 pic_status launch_sort(Sim* s);
 pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, void* rho_out);
