@@ -518,22 +518,22 @@ def run_guard(args):
     the global field step, for stencil orders p and guard widths g."""
     import numpy as np
 
-    from oracle import psatd_rz as O
     from paper_1611_05712_gb300 import binding as bd
     from paper_1611_05712_gb300.build import build
     from paper_1611_05712_gb300.domains import GuardedDomains
     build()
+    c_light = 299792458.0
     Nz, Nr, Nm, dz = 512, 32, 2, 0.05e-6
     table = {}
     for p in (8, 16, 32, 64, 0):
         row = {}
         for g in (0, 8, 16, 32, 48, 64, 96, 128):
-            cfg = bd.make_config(Nz, Nr, Nm, dz, dz, dz / O.C_LIGHT, p, True, bd.PIC_FP64, 0)
+            cfg = bd.make_config(Nz, Nr, Nm, dz, dz, dz / c_light, p, True, bd.PIC_FP64, 0)
             glob, out = bd.Sim(cfg), bd.Sim(cfg)
             rng = np.random.default_rng(7)
             shape = (3, Nm, Nr, Nz)
             glob.set("E", rng.normal(size=shape) + 1j * rng.normal(size=shape))
-            glob.set("B", (rng.normal(size=shape) + 1j * rng.normal(size=shape)) / O.C_LIGHT)
+            glob.set("B", (rng.normal(size=shape) + 1j * rng.normal(size=shape)) / c_light)
             for h in (glob, out):
                 h.set("DEP", h.zeros("DEP"))
                 h.set("RHO_PREV_H", h.zeros("RHO_PREV_H"))
