@@ -49,11 +49,12 @@ def parse():
     ap.add_argument("--accuracy-cycles", type=int, default=100,
                     help="cycles after which the mixed form's fields and beam quality are "
                          "compared with the FP64 form (0: skip)")
-    ap.add_argument("--workload", choices=["wake", "scan", "large", "guard"], default="wake",
+    ap.add_argument("--workload", choices=["wake", "scan", "large", "guard", "order_sweep"], default="wake",
                     help="wake: the 2048x256 wakefield run; scan: many uneven simulations "
                          "(order / resolution scan) advanced by one CUDA graph per launch; "
                          "large: the 8192x1024 3-mode run with ~103M particles, mixed form")
     ap.add_argument("--sims", type=int, default=64, help="simulations in the scan workload")
+    ap.add_argument("--sweep-steps", type=int, default=2000, help="cycles per order in the order sweep")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket each timed region with cudaProfilerStart/Stop (for "
                          "ncu --profile-from-start off); no work is skipped")
@@ -556,6 +557,46 @@ def run_guard(args):
     return 0
 
 
+def run_order_sweep(args):
+    """Order study of the beam-driven wakefield (2048 x 256, 2 modes): the same initial
+    state advanced args.sweep_steps cycles at each stencil order p and at infinite order;
+    Err_eps, Err_sigma_gamma (witness beam) and Err_Ez of each finite order against the
+    infinite-order run (numerical Cherenkov radiation measures of the paper)."""
+    from paper_1611_05712_gb300 import binding as bd
+    from paper_1611_05712_gb300 import ncr
+    from paper_1611_05712_gb300 import workloads as W
+    from paper_1611_05712_gb300.build import build
+    build()
+    prec = {"fp64": bd.PIC_FP64, "mixed": bd.PIC_MIXED_TF32X3, "bf16": bd.PIC_MIXED_BF16X6}[args.precision]
+    w = W.wake_2048x256(order_p=0)
+    P, npl, beams = W.particles(w)
+    lo, hi = beams[-1][0], beams[-1][1]
+    runs = {}
+    t0 = time.perf_counter()
+    for p in (0, 4, 8, 16, 32, 64, 128, 256):
+        s = bd.Sim.from_workload(w, P, npl, beams, precision=prec, order_p=p)
+        if prec != bd.PIC_FP64:
+            s.autotune()
+        s.step(args.sweep_steps)
+        d = s.diagnostics(lo, hi)
+        runs[p] = (d, ncr.ez_plane(s.get("E")))
+        s.close()
+    ref_d, ref_ez = runs[0]
+    res = {}
+    for p in (4, 8, 16, 32, 64, 128, 256):
+        d, ez = runs[p]
+        res[str(p)] = {"err_eps_x": ncr.err_emittance(d["emit_nx"], ref_d["emit_nx"]),
+                       "err_eps_y": ncr.err_emittance(d["emit_ny"], ref_d["emit_ny"]),
+                       "err_sigma_gamma": ncr.err_sigma_gamma(d["slice_sigma_gamma"], ref_d["slice_sigma_gamma"]),
+                       "err_ez": ncr.err_ez(ez, ref_ez), "err_ez_l2": ncr.err_ez_l2(ez, ref_ez)}
+    print(json.dumps({"metric": "ncr_order_sweep", "unit": "relative error vs infinite order",
+                      "config": {"workload": w.name, "cycles": args.sweep_steps, "precision": args.precision,
+                                 "beam": "witness", "reference": "p = inf, same initial state",
+                                 "wall_s": time.perf_counter() - t0},
+                      "errors_by_order": res}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -566,6 +607,8 @@ def main():
         return run_large(args)
     if args.workload == "guard":
         return run_guard(args)
+    if args.workload == "order_sweep":
+        return run_order_sweep(args)
     return run_ours(args)
 
 

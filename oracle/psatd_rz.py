@@ -735,3 +735,20 @@ def err_sigma_gamma(sig_f, sig_inf):
 def err_emittance(eps_f, eps_inf):
     """Err_eps of AMPA Eq. err-metrics."""
     return (eps_f - eps_inf) / eps_inf
+
+
+def field_on_plane(F_modes, theta=0.0):
+    """F(r, z) at azimuth theta from mode grids F_m[r][z] (R-modes):
+    Re[F_0 + 2 sum_{m>=1} F_m e^{-i m theta}]."""
+    out = np.real(np.asarray(F_modes[0], dtype=np.complex128)).copy()
+    for m in range(1, len(F_modes)):
+        out = out + 2.0 * np.real(np.asarray(F_modes[m], dtype=np.complex128) * np.exp(-1j * m * theta))
+    return out
+
+
+def err_ez(ez_f, ez_inf):
+    """Err_Ez of AMPA Eq. err-metrics: root mean square over all cells of the spatial
+    (z, r) discrete Fourier transform of the relative difference of FFT_2(E_z)."""
+    Ff = np.fft.fft2(np.asarray(ez_f, dtype=np.float64))
+    Fi = np.fft.fft2(np.asarray(ez_inf, dtype=np.float64))
+    return float(np.sqrt(np.mean(np.abs((Ff - Fi) / Fi) ** 2)))
