@@ -11,17 +11,18 @@
 // memory accelerator (2-D tiled copies, completion counted in mbarrier transaction bytes;
 // coordinates past Nr read zero).  Both use the 128-byte swizzled canonical layout.
 //
-// Precision: 3-term TF32 products.  Every float operand x is split as hi = x rounded to
-// TF32 and lo = x - hi (exact in float); D accumulates Xhi*Ahi + Xhi*Alo + Xlo*Ahi in FP32
-// in tensor memory (the A split is precomputed from the FP64 matrix at setup).
+// Precision (two kinds): 3-term TF32 products (every float x split as hi = x rounded to
+// TF32 and lo = x - hi, D accumulates Xhi*Ahi + Xhi*Alo + Xlo*Ahi) or 6-term BF16 products
+// (x split into three BF16 pieces, the six products of order <= 2); FP32 accumulation in
+// tensor memory; the matrices' pieces are precomputed from their FP64 values at setup.
 //
-// One CTA owns a 128-column x N_T tile of D (N_T <= 256 TMEM columns) for one batch; K is
-// consumed in chunks of 32 through two shared-memory stages: all 256 threads stage chunk
-// k+1 while the tensor core runs chunk k, and the data-panel loads of chunk k+2 are issued
-// before the wait for chunk k+1's stage.  One thread issues the MMAs and commits them to
-// an mbarrier per stage; every wait on an mbarrier is bounded and sets the device error
-// word on timeout.  The epilogue reads TMEM with tcgen05.ld (warp w owns TMEM lanes
-// 32*(w%4)..+31) and writes Yf[n][c] so that the 32 lanes of a warp store 32 consecutive c.
+// Kernel: persistent and warp-specialised (k_dht_tc_ws): one CTA per SM walks the
+// (M tile, N tile, batch) tiles; producer warps stage the panel and issue the matrix
+// copies into a ring of shared-memory stages, one thread issues the MMAs into one of two
+// TMEM accumulators, and epilogue warps drain the other accumulator (tcgen05.ld, warp w
+// owns TMEM lanes 32*(w%4)..+31, stores of 32 consecutive c per warp), so a tile's
+// epilogue runs under the next tile's main loop.  Every mbarrier wait is bounded and sets
+// the device error word on timeout.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -35,7 +36,6 @@
 namespace pic {
 namespace {
 
-constexpr int kTcThreads = 256;
 constexpr int kTcM = 128;          // rows of D (columns c of Xf) per CTA
 constexpr int kTcMaxN = 256;       // largest N tile, TF32 form
 constexpr int kTcMaxNBf16 = 128;   // largest N tile, BF16 form (three planes per operand)
@@ -118,10 +118,10 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_
 //   TF32x3: x = hi + lo (hi = x rounded to TF32), products hi.hi, hi.lo, lo.hi;
 //   BF16x6: x = b0 + b1 + b2 (each the BF16 rounding of what is left), products of order
 //           <= 2: b0.b0, b0.b1, b1.b0, b0.b2, b1.b1, b2.b0.
-// A 128-byte swizzle row holds kChunkK elements; one MMA consumes 32 bytes of K.
+// A 128-byte swizzle row holds 128 / kElemBytes elements; one MMA consumes 32 bytes of K.
 template <int KIND> struct TcKind;
 template <> struct TcKind<0> {
-  static constexpr int kPlanes = 2, kElemBytes = 4, kChunkK = 32, kProducts = 3;
+  static constexpr int kPlanes = 2, kElemBytes = 4, kProducts = 3;
   static constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10);   // D f32, A/B tf32
   __device__ static int a_plane(int p) { return p == 2 ? 1 : 0; }
   __device__ static int b_plane(int p) { return p == 1 ? 1 : 0; }
@@ -130,7 +130,7 @@ template <> struct TcKind<0> {
   }
 };
 template <> struct TcKind<1> {
-  static constexpr int kPlanes = 3, kElemBytes = 2, kChunkK = 64, kProducts = 6;
+  static constexpr int kPlanes = 3, kElemBytes = 2, kProducts = 6;
   static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10);   // D f32, A/B bf16
   __device__ static int a_plane(int p) { return (p == 2 || p == 4) ? 1 : (p == 5 ? 2 : 0); }
   __device__ static int b_plane(int p) { return (p == 1 || p == 4) ? 1 : (p == 3 ? 2 : 0); }
@@ -178,191 +178,257 @@ struct TcMaps {
   Sim::TensorMapBytes m[3][24];
 };
 
+// ---- persistent, warp-specialised form ------------------------------------------------
+// One CTA per SM walks the tiles (m fastest, then n, then batch) with a stride of the grid.
+//   warps 0-3 (producers): each thread owns one row c of the 128-row M tile; per K chunk it
+//     splits its prefetched panel values and writes them swizzled into the stage, then the
+//     warp arrives on full[stage]; thread 0 first arms full[stage] with the matrix tiles'
+//     transaction bytes and issues their TMA copies.  The next chunk's loads (of this or the
+//     next tile) are issued before the wait for a free stage.
+//   warp 8 (MMA): one thread waits full[stage], issues the products into the tile's
+//     accumulator (two TMEM accumulators of N_T columns, alternating by tile), commits to
+//     empty[stage], and after a tile's last chunk commits to tmem_full[acc].
+//   warps 4-7 (epilogue): wait tmem_full[acc], read their 32 TMEM lanes (rows c) with
+//     tcgen05.ld and store Y, then arrive on tmem_empty[acc]; the MMA thread waits on it
+//     before it reuses that accumulator two tiles later.
+// So a tile's epilogue runs under the next tile's main loop.  Every wait is bounded; a
+// timeout sets the device error word and a shared abort flag that every loop checks, and
+// before tensor memory is released the CTA waits (bounded) for its copies and MMAs.
+constexpr int kWsThreads = 288;
+constexpr int kWsMaxStages = 4;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+struct WsTile {
+  int b, n0, c0;
+};
+
+__device__ __forceinline__ WsTile ws_tile(int t, const TcParams& P) {
+  const int m = t % P.m_tiles;
+  const int rest = t / P.m_tiles;
+  return WsTile{rest / P.n_tiles, (rest % P.n_tiles) * P.NT, m * kTcM};
+}
+
 template <int KIND>
-__global__ void __launch_bounds__(kTcThreads, 1) k_dht_tc(DhtBatch bt, TcParams P, const __grid_constant__ TcMaps maps,
-                                                           int32_t* err) {
+__global__ void __launch_bounds__(kWsThreads, 1) k_dht_tc_ws(DhtBatch bt, TcParams P,
+                                                              const __grid_constant__ TcMaps maps, int32_t* err,
+                                                              int n_stages, int n_tiles_total) {
   using K = TcKind<KIND>;
   constexpr int NP = K::kPlanes;
-  constexpr int EPC = 16 / K::kElemBytes;   // K elements per 16-byte chunk of a swizzle row
+  constexpr int EPC = 16 / K::kElemBytes;    // K elements per 16-byte chunk of a swizzle row
+  constexpr int KPR = 8 * EPC;              // K elements per 128-byte row (= kChunkK)
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned carve-up: [stage][A planes | B planes], then barriers
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  const uint32_t a_bytes = kTcM * 128;            // 16 KB per plane
-  const uint32_t b_bytes = (uint32_t)P.NT * 128;  // up to 32 KB per plane
+  const uint32_t a_bytes = kTcM * 128;
+  const uint32_t b_bytes = (uint32_t)P.NT * 128;
   const uint32_t stage_bytes = NP * (a_bytes + b_bytes);
-  // bars[0..1]: per-stage "MMAs that read this stage are done"; bars[2..3]: per-stage
-  // "matrix tiles have landed" (transaction counted)
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * stage_bytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 4);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + n_stages * stage_bytes);
+  uint64_t* empty = full + kWsMaxStages;
+  uint64_t* tfull = empty + kWsMaxStages;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int b = blockIdx.z;
-  const int n_tile = blockIdx.y;
-  const int m_tile = blockIdx.x;
-  const int c0 = m_tile * kTcM, n0 = n_tile * P.NT;
-  const float* __restrict__ X = static_cast<const float*>(bt.X[b]);
-  float* __restrict__ Y = static_cast<float*>(bt.Y[b]);
+  const int nK = (P.Nr + KPR - 1) / KPR;
+  const uint32_t tmem_cols = (uint32_t)P.tmem_cols;
 
-  if (warp == 0) {
+  if (warp == 8) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)P.tmem_cols)
+                 "r"(tmem_cols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    mbar_init(&bars[2], 1);
-    mbar_init(&bars[3], 1);
+    for (int i = 0; i < n_stages; ++i) {
+      mbar_init(&full[i], 5);    // TMA issuer's arrive.expect_tx + one arrival per producer warp
+      mbar_init(&empty[i], 1);   // MMA commit
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&tfull[i], 1);   // MMA commit after a tile's last chunk
+      mbar_init(&tempty[i], 4);  // one arrival per epilogue warp
+    }
+    *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-#pragma unroll
-    for (int pl = 0; pl < NP; ++pl)
-      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&maps.m[pl][b])) : "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = K::kIdesc | ((uint32_t)(P.NT >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
-  const int nK = (P.Nr + K::kChunkK - 1) / K::kChunkK;
-  bool ok = true;
-  int issued = -1, committed = -1;   // last chunk whose matrix copies / MMAs were issued (block-uniform)
 
-  // data-panel values of the next chunk, loaded ahead of the wait for a free stage:
-  // item it = tid + q*256 covers row c0 + (it % 128), 16-byte chunk it / 128 (EPC values of j)
-  float pv[4][EPC];
-  auto load_chunk = [&](int kc) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int it = tid + q * kTcThreads;
-      const int c = c0 + (it & (kTcM - 1)), ch = it >> 7;
-#pragma unroll
-      for (int e = 0; e < EPC; ++e) {
-        const int j = kc * K::kChunkK + ch * EPC + e;
-        pv[q][e] = (c < P.Nc && j < P.Nr) ? X[(size_t)j * P.Nc + c] : 0.f;
-      }
-    }
+  auto fail = [&]() {
+    *abort_flag = 1;
+    atomicOr(err, kErrTimeout);
   };
-  if (nK > 0) load_chunk(0);
 
-  for (int kc = 0; kc < nK && ok; ++kc) {
-    const int st = kc & 1;
-    if (kc >= 2) {   // the MMAs that last read this stage (chunk kc-2) must be done
-      const bool w = mbar_wait(&bars[st], (uint32_t)(((kc - 2) >> 1) & 1));
-      if (!__syncthreads_and(w)) { ok = false; break; }   // one decision for the whole block
-    }
-    unsigned char* sA = base + st * stage_bytes;      // NP planes of a_bytes
-    unsigned char* sB = sA + NP * a_bytes;            // NP planes of b_bytes
-    const int k0 = kc * K::kChunkK;
-    if (tid == 0) {   // matrix tiles (rows n0.., columns k0..; zero fill beyond Nr)
-      mbar_arrive_expect_tx(&bars[2 + st], NP * b_bytes);
+  if (warp < 4) {
+    // ---------------------------------------------------------------- producers
+    const int row = tid;   // 0..127
+    float pv[KPR];
+    auto load = [&](int t, int kc) {
+      const WsTile w = ws_tile(t, P);
+      const float* __restrict__ X = static_cast<const float*>(bt.X[w.b]);
+      const int c = w.c0 + row;
 #pragma unroll
-      for (int pl = 0; pl < NP; ++pl) tma_load_2d(sB + pl * b_bytes, &maps.m[pl][b], k0, n0, &bars[2 + st]);
-    }
-    issued = kc;
-    // A operand (transposed X): split the prefetched values and store them swizzled
+      for (int e = 0; e < KPR; ++e) {
+        const int j = kc * KPR + e;
+        pv[e] = (c < P.Nc && j < P.Nr) ? X[(size_t)j * P.Nc + c] : 0.f;
+      }
+    };
+    uint32_t g = 0;
+    int last_armed = -1;   // stage armed by thread 0 whose bytes may still be in flight
+    bool have = blockIdx.x < n_tiles_total && nK > 0;
+    if (have) load(blockIdx.x, 0);
+    for (int t = blockIdx.x; t < n_tiles_total && !*abort_flag; t += gridDim.x) {
+      const WsTile w = ws_tile(t, P);
+      for (int kc = 0; kc < nK; ++kc, ++g) {
+        const int st = (int)(g % (uint32_t)n_stages);
+        const uint32_t use = g / (uint32_t)n_stages;
+        if (use > 0 && !mbar_wait(&empty[st], (use - 1) & 1)) { fail(); break; }
+        if (*abort_flag) break;
+        unsigned char* sA = base + st * stage_bytes;
+        unsigned char* sB = sA + NP * a_bytes;
+        if (tid == 0) {
+          mbar_arrive_expect_tx(&full[st], NP * b_bytes);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int it = tid + q * kTcThreads;
-      const int row = it & (kTcM - 1), ch = it >> 7;
-      const uint32_t off = sw128_off(row, ch);
-      if (KIND == 0) {
-        float hv[4], lv[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          hv[e] = tf32_hi(pv[q][e]);
-          lv[e] = pv[q][e] - hv[e];
+          for (int pl = 0; pl < NP; ++pl) tma_load_2d(sB + pl * b_bytes, &maps.m[pl][w.b], kc * KPR, w.n0, &full[st]);
+          last_armed = st;
         }
-        *reinterpret_cast<float4*>(sA + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
-        *reinterpret_cast<float4*>(sA + a_bytes + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
-      } else {
-        uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
-        for (int e = 0; e < EPC; e += 2) {
-          uint32_t a0, a1, a2, b0, b1, b2;
-          split_bf16x3(pv[q][e], a0, a1, a2);
-          split_bf16x3(pv[q][e + 1], b0, b1, b2);
-          w0[e / 2] = a0 | (b0 << 16);
-          w1[e / 2] = a1 | (b1 << 16);
-          w2[e / 2] = a2 | (b2 << 16);
+        for (int ch = 0; ch < 8; ++ch) {
+          const uint32_t off = sw128_off(row, ch);
+          if (KIND == 0) {
+            float hv[4], lv[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              hv[e] = tf32_hi(pv[ch * 4 + e]);
+              lv[e] = pv[ch * 4 + e] - hv[e];
+            }
+            *reinterpret_cast<float4*>(sA + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+            *reinterpret_cast<float4*>(sA + a_bytes + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
+          } else {
+            uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+              uint32_t a0, a1, a2, b0, b1, b2;
+              split_bf16x3(pv[ch * 8 + e], a0, a1, a2);
+              split_bf16x3(pv[ch * 8 + e + 1], b0, b1, b2);
+              w0[e / 2] = a0 | (b0 << 16);
+              w1[e / 2] = a1 | (b1 << 16);
+              w2[e / 2] = a2 | (b2 << 16);
+            }
+            *reinterpret_cast<uint4*>(sA + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+            *reinterpret_cast<uint4*>(sA + a_bytes + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+            *reinterpret_cast<uint4*>(sA + 2 * a_bytes + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+          }
         }
-        *reinterpret_cast<uint4*>(sA + off) = make_uint4(w0[0], w0[1], w0[2], w0[3]);
-        *reinterpret_cast<uint4*>(sA + a_bytes + off) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-        *reinterpret_cast<uint4*>(sA + 2 * a_bytes + off) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        // the next chunk's panel values: of this tile, or the first of the next tile
+        if (kc + 1 < nK) load(t, kc + 1);
+        else if (t + (int)gridDim.x < n_tiles_total) load(t + gridDim.x, 0);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&full[st]);
       }
     }
-    if (kc + 1 < nK) load_chunk(kc + 1);   // in flight while this chunk is multiplied
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    const bool landed = (tid == 0) ? mbar_wait(&bars[2 + st], (uint32_t)((kc >> 1) & 1)) : true;
-    if (!__syncthreads_and(landed)) { ok = false; break; }
-    if (tid == 0) {
+    // before shared memory is released: the last armed stage's copies must have landed
+    if (tid == 0 && last_armed >= 0 && *abort_flag) {
+      const uint32_t gl = g == 0 ? 0 : g - 1;
+      mbar_wait(&full[last_armed], (gl / (uint32_t)n_stages) & 1);
+    }
+  } else if (warp == 8) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      uint32_t g = 0, i = 0;
+      uint64_t* last_bar = nullptr;   // barrier and phase of the last commit issued
+      uint32_t last_parity = 0;
+      for (int t = blockIdx.x; t < n_tiles_total && !*abort_flag; t += gridDim.x, ++i) {
+        const uint32_t acc = i & 1, acc_use = i >> 1;
+        if (acc_use > 0 && !mbar_wait(&tempty[acc], (acc_use - 1) & 1)) { fail(); break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + acc * (uint32_t)P.NT;
+        bool ok = true;
+        for (int kc = 0; kc < nK; ++kc, ++g) {
+          const int st = (int)(g % (uint32_t)n_stages);
+          if (!mbar_wait(&full[st], (g / (uint32_t)n_stages) & 1)) { fail(); ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sa = smem_u32(base + st * stage_bytes), sb = sa + NP * a_bytes;
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t koff = ks * 32;
+#pragma unroll
+            for (int pr = 0; pr < K::kProducts; ++pr) {
+              const uint32_t accf = (kc > 0 || ks > 0 || pr > 0) ? 1u : 0u;
+              K::mma(d, make_desc(sa + K::a_plane(pr) * a_bytes + koff), make_desc(sb + K::b_plane(pr) * b_bytes + koff),
+                     idesc, accf);
+            }
+          }
+          mma_commit(&empty[st]);
+          last_bar = &empty[st];
+          last_parity = (g / (uint32_t)n_stages) & 1;
+        }
+        if (!ok) break;
+        mma_commit(&tfull[acc]);
+        last_bar = &tfull[acc];
+        last_parity = (i >> 1) & 1;
+      }
+      // on abort: let the MMAs already issued finish before tensor memory is released
+      if (*abort_flag && last_bar) mbar_wait(last_bar, last_parity);
+    }
+    __syncwarp();
+  } else {
+    // ---------------------------------------------------------------- epilogue (warps 4-7)
+    const int q = warp - 4;   // TMEM lanes 32q..32q+31 = rows c
+    uint32_t i = 0;
+    for (int t = blockIdx.x; t < n_tiles_total && !*abort_flag; t += gridDim.x, ++i) {
+      const uint32_t acc = i & 1;
+      if (!mbar_wait(&tfull[acc], (i >> 1) & 1)) { fail(); break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t sa = smem_u32(sA), sb = smem_u32(sB);
+      const WsTile w = ws_tile(t, P);
+      float* __restrict__ Y = static_cast<float*>(bt.Y[w.b]);
+      const int c = w.c0 + q * 32 + lane;
+      for (int j0 = 0; j0 < P.NT; j0 += 8) {
+        uint32_t r[8];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + acc * (uint32_t)P.NT + (uint32_t)j0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+            : "r"(taddr)
+            : "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (c < P.Nc) {
 #pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {
-        const uint32_t koff = ks * 32;   // 32 bytes of K per MMA inside the swizzle row
-#pragma unroll
-        for (int pr = 0; pr < K::kProducts; ++pr) {
-          const uint32_t acc = (kc > 0 || ks > 0 || pr > 0) ? 1u : 0u;
-          K::mma(tmem, make_desc(sa + K::a_plane(pr) * a_bytes + koff), make_desc(sb + K::b_plane(pr) * b_bytes + koff),
-                 idesc, acc);
+          for (int e = 0; e < 8; ++e) {
+            const int n = w.n0 + j0 + e;
+            if (n < P.Nr) Y[(size_t)n * P.Nc + c] = __uint_as_float(r[e]);
+          }
         }
       }
-      mma_commit(&bars[st]);
-    }
-    committed = kc;
-  }
-  // wait for the last chunk's commit (it covers every MMA issued before it)
-  if (ok && nK > 0) ok = mbar_wait(&bars[(nK - 1) & 1], (uint32_t)(((nK - 1) >> 1) & 1));
-  ok = __syncthreads_and(ok);
-  if (!ok) {
-    if (tid == 0) {
-      atomicOr(err, kErrTimeout);
-      // wait (bounded) for the copies and MMAs still in flight before the shared and
-      // tensor memory are released
-      if (issued > committed) mbar_wait(&bars[2 + (issued & 1)], (uint32_t)((issued >> 1) & 1));
-      if (committed >= 0) mbar_wait(&bars[committed & 1], (uint32_t)((committed >> 1) & 1));
-    }
-    __syncthreads();
-  }
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-  if (ok) {
-    // epilogue: warp w reads TMEM lanes 32*(w%4).. (rows c) and half (w/4) of the N columns
-    const int quarter = warp & 3, half = warp >> 2;
-    const int c = c0 + quarter * 32 + lane;
-    const int ncol_half = P.NT / 2;
-    for (int j0 = half * ncol_half; j0 < (half + 1) * ncol_half; j0 += 8) {
-      uint32_t r[8];
-      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)j0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-          : "r"(taddr)
-          : "memory");
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (c < P.Nc) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int n = n0 + j0 + e;
-          if (n < P.Nr) Y[(size_t)n * P.Nc + c] = __uint_as_float(r[e]);
-        }
-      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[acc]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)P.tmem_cols)
-                 : "memory");
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 8)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
 }  // namespace
 
-// Dynamic shared memory of one launch: two stages of planes x (A tile + B tile), barriers.
-size_t dht_tc_smem_bytes(int planes, int NT) {
-  return 1024 + 2 * (size_t)planes * (kTcM * 128 + (size_t)NT * 128) + 64;
+constexpr size_t kWsSmemMax = 227 * 1024;   // dynamic shared memory of the persistent kernel
+int sm_count_of[64] = {};
+
+// SMs of the current device (recorded by dht_tc_configure_device).
+int dht_tc_sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || sm_count_of[dev] <= 0) return 152;
+  return sm_count_of[dev];
 }
 
 // Raised once per device to the largest tile of each kind (TF32: N_T = 256, BF16: 128);
@@ -374,10 +440,11 @@ pic_status dht_tc_configure_device() {
   PIC_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(mu);
   if (dev >= 0 && dev < 64 && done[dev]) return PIC_OK;
-  PIC_CUDA(cudaFuncSetAttribute(k_dht_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dht_tc_smem_bytes(2, kTcMaxN)));
-  PIC_CUDA(cudaFuncSetAttribute(k_dht_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)dht_tc_smem_bytes(3, kTcMaxNBf16)));
+  PIC_CUDA(cudaFuncSetAttribute(k_dht_tc_ws<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemMax));
+  PIC_CUDA(cudaFuncSetAttribute(k_dht_tc_ws<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWsSmemMax));
+  int sms = 0;
+  PIC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (dev >= 0 && dev < 64) sm_count_of[dev] = sms;
   if (dev >= 0 && dev < 64) done[dev] = true;
   return PIC_OK;
 }
@@ -490,11 +557,27 @@ pic_status launch_dht_tc(Sim* s, const DhtBatch& b) {
     }
     for (int pl = 0; pl < 3; ++pl) maps.m[pl][i] = s->tmaps[b.mat[i]][pl];
   }
-  dim3 grid(P.m_tiles, P.n_tiles, b.n);
+  // persistent, warp-specialised launch: one CTA per SM, as many stages as shared memory
+  // holds (2..4), two TMEM accumulators of N_T columns
+  const int planes = bf ? 3 : 2;
+  const size_t stage_bytes = (size_t)planes * (kTcM * 128 + (size_t)P.NT * 128);
+  const int n_stages = (int)std::min<size_t>(kWsMaxStages, (kWsSmemMax - 1024 - 128) / stage_bytes);
+  if (n_stages < 2) {
+    set_error("DHT tile N=%d does not fit two stages in shared memory", P.NT);
+    return PIC_ERR_ARG;
+  }
+  int tc2 = 32;
+  while (tc2 < 2 * P.NT) tc2 <<= 1;
+  P.tmem_cols = tc2;
+  const int n_tiles_total = P.m_tiles * P.n_tiles * b.n;
+  const int grid = std::min(n_tiles_total, dht_tc_sm_count());
+  const size_t smem = 1024 + (size_t)n_stages * stage_bytes + 128;
   if (bf)
-    k_dht_tc<1><<<grid, kTcThreads, dht_tc_smem_bytes(3, P.NT), s->stream>>>(b, P, maps, s->at<int32_t>(s->lay.err));
+    k_dht_tc_ws<1><<<grid, kWsThreads, smem, s->stream>>>(b, P, maps, s->at<int32_t>(s->lay.err), n_stages,
+                                                          n_tiles_total);
   else
-    k_dht_tc<0><<<grid, kTcThreads, dht_tc_smem_bytes(2, P.NT), s->stream>>>(b, P, maps, s->at<int32_t>(s->lay.err));
+    k_dht_tc_ws<0><<<grid, kWsThreads, smem, s->stream>>>(b, P, maps, s->at<int32_t>(s->lay.err), n_stages,
+                                                          n_tiles_total);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }
