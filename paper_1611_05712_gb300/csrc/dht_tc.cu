@@ -180,21 +180,21 @@ struct TcMaps {
 
 // ---- persistent, warp-specialised form ------------------------------------------------
 // One CTA per SM walks the tiles (m fastest, then n, then batch) with a stride of the grid.
-//   warps 0-3 (producers): each thread owns one row c of the 128-row M tile; per K chunk it
-//     splits its prefetched panel values and writes them swizzled into the stage, then the
-//     warp arrives on full[stage]; thread 0 first arms full[stage] with the matrix tiles'
-//     transaction bytes and issues their TMA copies.  The next chunk's loads (of this or the
-//     next tile) are issued before the wait for a free stage.
-//   warp 8 (MMA): one thread waits full[stage], issues the products into the tile's
+//   warps 0-7 (producers): each thread owns half of one row c of the 128-row M tile; per K
+//     chunk it splits its prefetched panel values and writes them swizzled into the stage,
+//     then the warp arrives on full[stage]; thread 0 first arms full[stage] with the matrix
+//     tiles' transaction bytes and issues their TMA copies.  The next chunk's loads (of this
+//     or the next tile) are issued before the wait for a free stage.
+//   warp 12 (MMA): one thread waits full[stage], issues the products into the tile's
 //     accumulator (two TMEM accumulators of N_T columns, alternating by tile), commits to
 //     empty[stage], and after a tile's last chunk commits to tmem_full[acc].
-//   warps 4-7 (epilogue): wait tmem_full[acc], read their 32 TMEM lanes (rows c) with
+//   warps 8-11 (epilogue): wait tmem_full[acc], read their 32 TMEM lanes (rows c) with
 //     tcgen05.ld and store Y, then arrive on tmem_empty[acc]; the MMA thread waits on it
 //     before it reuses that accumulator two tiles later.
 // So a tile's epilogue runs under the next tile's main loop.  Every wait is bounded; a
 // timeout sets the device error word and a shared abort flag that every loop checks, and
 // before tensor memory is released the CTA waits (bounded) for its copies and MMAs.
-constexpr int kWsThreads = 288;
+constexpr int kWsThreads = 416;   // 8 producer warps, 4 epilogue warps, 1 MMA warp
 constexpr int kWsMaxStages = 4;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dht_tc_ws(DhtBatch bt, TcPara
   const int nK = (P.Nr + KPR - 1) / KPR;
   const uint32_t tmem_cols = (uint32_t)P.tmem_cols;
 
-  if (warp == 8) {
+  if (warp == 12) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(tmem_cols)
                  : "memory");
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dht_tc_ws(DhtBatch bt, TcPara
   }
   if (tid == 0) {
     for (int i = 0; i < n_stages; ++i) {
-      mbar_init(&full[i], 5);    // TMA issuer's arrive.expect_tx + one arrival per producer warp
+      mbar_init(&full[i], 9);    // TMA issuer's arrive.expect_tx + one arrival per producer warp
       mbar_init(&empty[i], 1);   // MMA commit
     }
     for (int i = 0; i < 2; ++i) {
@@ -265,17 +265,19 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dht_tc_ws(DhtBatch bt, TcPara
     atomicOr(err, kErrTimeout);
   };
 
-  if (warp < 4) {
+  if (warp < 8) {
     // ---------------------------------------------------------------- producers
-    const int row = tid;   // 0..127
-    float pv[KPR];
+    constexpr int HALF = KPR / 2;   // K elements (4 swizzle chunks) per thread and chunk
+    const int row = tid & (kTcM - 1);
+    const int half = tid >> 7;      // which 4 of the row's 8 16-byte chunks
+    float pv[HALF];
     auto load = [&](int t, int kc) {
       const WsTile w = ws_tile(t, P);
       const float* __restrict__ X = static_cast<const float*>(bt.X[w.b]);
       const int c = w.c0 + row;
 #pragma unroll
-      for (int e = 0; e < KPR; ++e) {
-        const int j = kc * KPR + e;
+      for (int e = 0; e < HALF; ++e) {
+        const int j = kc * KPR + half * HALF + e;
         pv[e] = (c < P.Nc && j < P.Nr) ? X[(size_t)j * P.Nc + c] : 0.f;
       }
     };
@@ -299,14 +301,15 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dht_tc_ws(DhtBatch bt, TcPara
           last_armed = st;
         }
 #pragma unroll
-        for (int ch = 0; ch < 8; ++ch) {
+        for (int cq = 0; cq < 4; ++cq) {
+          const int ch = half * 4 + cq;
           const uint32_t off = sw128_off(row, ch);
           if (KIND == 0) {
             float hv[4], lv[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
-              hv[e] = tf32_hi(pv[ch * 4 + e]);
-              lv[e] = pv[ch * 4 + e] - hv[e];
+              hv[e] = tf32_hi(pv[cq * 4 + e]);
+              lv[e] = pv[cq * 4 + e] - hv[e];
             }
             *reinterpret_cast<float4*>(sA + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
             *reinterpret_cast<float4*>(sA + a_bytes + off) = make_float4(lv[0], lv[1], lv[2], lv[3]);
@@ -315,8 +318,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dht_tc_ws(DhtBatch bt, TcPara
 #pragma unroll
             for (int e = 0; e < 8; e += 2) {
               uint32_t a0, a1, a2, b0, b1, b2;
-              split_bf16x3(pv[ch * 8 + e], a0, a1, a2);
-              split_bf16x3(pv[ch * 8 + e + 1], b0, b1, b2);
+              split_bf16x3(pv[cq * 8 + e], a0, a1, a2);
+              split_bf16x3(pv[cq * 8 + e + 1], b0, b1, b2);
               w0[e / 2] = a0 | (b0 << 16);
               w1[e / 2] = a1 | (b1 << 16);
               w2[e / 2] = a2 | (b2 << 16);
@@ -339,7 +342,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dht_tc_ws(DhtBatch bt, TcPara
       const uint32_t gl = g == 0 ? 0 : g - 1;
       mbar_wait(&full[last_armed], (gl / (uint32_t)n_stages) & 1);
     }
-  } else if (warp == 8) {
+  } else if (warp == 12) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       uint32_t g = 0, i = 0;
@@ -380,8 +383,8 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dht_tc_ws(DhtBatch bt, TcPara
     }
     __syncwarp();
   } else {
-    // ---------------------------------------------------------------- epilogue (warps 4-7)
-    const int q = warp - 4;   // TMEM lanes 32q..32q+31 = rows c
+    // ---------------------------------------------------------------- epilogue (warps 8-11)
+    const int q = warp - 8;   // TMEM lanes 32q..32q+31 = rows c (warp % 4 == q)
     uint32_t i = 0;
     for (int t = blockIdx.x; t < n_tiles_total && !*abort_flag; t += gridDim.x, ++i) {
       const uint32_t acc = i & 1;
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dht_tc_ws(DhtBatch bt, TcPara
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 8)
+  if (warp == 12)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
