@@ -433,10 +433,14 @@ def run_scan(args):
         dist.barrier()
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
+        if args.profile_range:
+            torch.cuda.profiler.start()
         e0.record(batch.origin)
         batch.launch(launches)
         e1.record(batch.origin)
         e1.synchronize()
+        if args.profile_range:
+            torch.cuda.profiler.stop()
     ms = reduce_max(e0.elapsed_time(e1), dist, dev)
     cycles = 2 * launches
     n_tot = sum(len(p[0]["x"]) for p in parts)

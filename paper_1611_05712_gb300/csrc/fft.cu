@@ -2,8 +2,9 @@
 // quasi-cylindrical scheme (section "Finite order pseudo-spectral solvers").
 //   forward: Fhat(k) = sum_i F(z_i) e^{-2 pi i k i / Nz}
 //   inverse: F(z_i) = (1/Nz) sum_k Fhat(k) e^{+2 pi i k i / Nz}
-// One CTA per row; the row is staged in shared memory and transformed by a mixed-radix
-// (2, 3, 4, 5, 7) self-sorting Stockham sequence of passes between two shared buffers.
+// Power-of-two lengths use radix-8 passes with the values in registers (k_fft_pow2); other
+// 7-smooth lengths a mixed-radix (2, 3, 4, 5, 7) self-sorting Stockham sequence of passes
+// between two shared row buffers (k_fft_rows).  Both read per-pass twiddle tables.
 // The component combination of the quasi-cylindrical scheme is fused into the row load:
 // out = ca * inA + cb * inB, which forms J_+- = (J_r -+ i J_theta)/2 before the forward
 // transform and E_r = E_+ + E_-, E_theta = i (E_+ - E_-) before the inverse one.
@@ -38,90 +39,6 @@ struct FftPlan {
   int n_pass;
   int radix[kMaxRadixPasses];
 };
-
-template <typename R, bool INV>
-__device__ __forceinline__ typename Vec2<R>::T twiddle(const typename Vec2<R>::T* tw, int idx) {
-  typename Vec2<R>::T w;
-  const typename Vec2<R>::T t = tw[idx];
-  w.x = (R)t.x;
-  w.y = INV ? (R)(-t.y) : (R)t.y;
-  return w;
-}
-
-template <typename R, bool INV>
-__global__ void __launch_bounds__(256) k_fft_rows(const typename Vec2<R>::T* __restrict__ in,
-                                                  typename Vec2<R>::T* __restrict__ out,
-                                                  const typename Vec2<R>::T* __restrict__ tw, RowCombine rc,
-                                                  FftPlan plan, int rows_per_comp) {
-  using C2 = typename Vec2<R>::T;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = plan.N;
-  C2* buf0 = reinterpret_cast<C2*>(smem_raw);
-  C2* buf1 = buf0 + N;
-  const int row = blockIdx.x;
-  const int comp = row / rows_per_comp;
-  const int rr = row % rows_per_comp;
-  const C2* a = in + ((size_t)rc.srcA[comp] * rows_per_comp + rr) * N;
-  const int sb = rc.srcB[comp];
-  const C2* b = sb >= 0 ? in + ((size_t)sb * rows_per_comp + rr) * N : nullptr;
-  C2 ca, cb;
-  ca.x = (R)rc.caRe[comp]; ca.y = (R)rc.caIm[comp];
-  cb.x = (R)rc.cbRe[comp]; cb.y = (R)rc.cbIm[comp];
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    C2 v = cmul(ca, a[i]);
-    if (b) v = cadd(v, cmul(cb, b[i]));
-    buf0[i] = v;
-  }
-  __syncthreads();
-  C2* src = buf0;
-  C2* dst = buf1;
-  int L = 1;
-  for (int p = 0; p < plan.n_pass; ++p) {
-    const int Rdx = plan.radix[p];
-    const int stride = N / Rdx;           // input stride of one butterfly
-    const int tstep = stride / L;         // twiddle index step: N/(L*R)
-    for (int t = threadIdx.x; t < stride; t += blockDim.x) {
-      const int k = t % L;
-      const int base = (t / L) * L * Rdx + k;
-      C2 v[7];
-      for (int r = 0; r < Rdx; ++r) v[r] = src[t + r * stride];
-      if (L > 1) {
-        for (int r = 1; r < Rdx; ++r) v[r] = cmul(v[r], twiddle<R, INV>(tw, r * k * tstep));
-      }
-      if (Rdx == 2) {
-        C2 y0 = cadd(v[0], v[1]), y1 = csub(v[0], v[1]);
-        dst[base] = y0;
-        dst[base + L] = y1;
-      } else if (Rdx == 4) {
-        C2 s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
-        C2 s13 = cadd(v[1], v[3]), d13 = mul_mi<C2, INV>(csub(v[1], v[3]));
-        dst[base] = cadd(s02, s13);
-        dst[base + L] = cadd(d02, d13);
-        dst[base + 2 * L] = csub(s02, s13);
-        dst[base + 3 * L] = csub(d02, d13);
-      } else {
-        // generic small DFT: y_s = sum_r v_r w_R^{r s}, w_R = tw[N/R]
-        const int wstep = N / Rdx;
-        for (int s = 0; s < Rdx; ++s) {
-          C2 acc = v[0];
-          for (int r = 1; r < Rdx; ++r) acc = cadd(acc, cmul(v[r], twiddle<R, INV>(tw, ((r * s) % Rdx) * wstep)));
-          dst[base + s * L] = acc;
-        }
-      }
-    }
-    __syncthreads();
-    C2* t2 = src; src = dst; dst = t2;
-    L *= Rdx;
-  }
-  C2* o = out + (size_t)row * N;
-  const R scale = INV ? (R)(1.0 / N) : (R)1;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    C2 v = src[i];
-    v.x *= scale;
-    v.y *= scale;
-    o[i] = v;
-  }
-}
 
 // ---- power-of-two rows ----
 // Self-sorting Stockham passes of radix 8 (then one radix-2 or radix-4 pass when log2 N is
@@ -331,6 +248,110 @@ __global__ void __launch_bounds__(kFftThreads, E == 8 ? 4 : (E == 16 ? 2 : 1)) k
   else pow2_pass<C2, INV, E, 2, PS>(v, c, twp, L, lgL, true);
 }
 
+// ---- any 7-smooth length ----
+// Stockham passes of the plan's radices (4, 2, 3, 5, 7 in the plan's order) between two
+// shared row buffers, one row per CTA; each thread takes butterflies t, t + 256, ... of a
+// pass, holds a butterfly's R values in registers, applies the pass's twiddles from the
+// per-pass table (entry L-1 + (r-1) L + k = w_{LR}^{rk}, read coalesced) and the R-point DFT
+// with the roots of unity w_R^m computed once per pass.
+__device__ __forceinline__ void sincospi_r(float x, float* s, float* c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincospi_r(double x, double* s, double* c) { sincospi(x, s, c); }
+
+template <typename C2, int R> __device__ __forceinline__ void dft_small(C2 (&v)[R], const C2 (&root)[R]) {
+  C2 y[R];
+#pragma unroll
+  for (int s2 = 0; s2 < R; ++s2) {
+    C2 acc = v[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], root[(r * s2) % R]));
+    y[s2] = acc;
+  }
+#pragma unroll
+  for (int s2 = 0; s2 < R; ++s2) v[s2] = y[s2];
+}
+
+template <typename C2, bool INV, int R>
+__device__ __forceinline__ void mixed_pass(const C2* __restrict__ src, C2* __restrict__ dst,
+                                           const C2* __restrict__ twp, int N, int L) {
+  using Re = decltype(src[0].x);
+  C2 root[R];
+#pragma unroll
+  for (int m = 0; m < R; ++m) {   // w_R^m = exp(-+ 2 pi i m / R)
+    Re sn, cs;
+    sincospi_r((Re)(2 * m) / (Re)R, &sn, &cs);
+    root[m].x = cs;
+    root[m].y = INV ? sn : -sn;
+  }
+  const int NR = N / R;
+  for (int t = threadIdx.x; t < NR; t += blockDim.x) {
+    const int j = t / L, k = t - j * L;
+    C2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[t + r * NR];
+    if (L > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], conj_if<C2, INV>(twp[L - 1 + (r - 1) * L + k]));
+    }
+    if (R == 2) dft2<C2, INV>(v);
+    else if (R == 4) dft4<C2, INV>(v);
+    else dft_small<C2, R>(v, root);
+    const int base = j * L * R + k;
+#pragma unroll
+    for (int s2 = 0; s2 < R; ++s2) dst[base + s2 * L] = v[s2];
+  }
+}
+
+template <typename R, bool INV>
+__global__ void __launch_bounds__(256) k_fft_rows(const typename Vec2<R>::T* __restrict__ in,
+                                                  typename Vec2<R>::T* __restrict__ out,
+                                                  const typename Vec2<R>::T* __restrict__ twp, RowCombine rc,
+                                                  FftPlan plan, int rows_per_comp) {
+  using C2 = typename Vec2<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = plan.N;
+  C2* buf0 = reinterpret_cast<C2*>(smem_raw);
+  C2* buf1 = buf0 + N;
+  const int row = blockIdx.x;
+  const int comp = row / rows_per_comp;
+  const int rr = row % rows_per_comp;
+  const C2* a = in + ((size_t)rc.srcA[comp] * rows_per_comp + rr) * N;
+  const int sb = rc.srcB[comp];
+  const C2* b = sb >= 0 ? in + ((size_t)sb * rows_per_comp + rr) * N : nullptr;
+  C2 ca, cb;
+  ca.x = (R)rc.caRe[comp]; ca.y = (R)rc.caIm[comp];
+  cb.x = (R)rc.cbRe[comp]; cb.y = (R)rc.cbIm[comp];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    C2 v = cmul(ca, a[i]);
+    if (b) v = cadd(v, cmul(cb, b[i]));
+    buf0[i] = v;
+  }
+  __syncthreads();
+  C2* src = buf0;
+  C2* dst = buf1;
+  int L = 1;
+  for (int p = 0; p < plan.n_pass; ++p) {
+    const int Rdx = plan.radix[p];
+    switch (Rdx) {
+      case 2: mixed_pass<C2, INV, 2>(src, dst, twp, N, L); break;
+      case 3: mixed_pass<C2, INV, 3>(src, dst, twp, N, L); break;
+      case 4: mixed_pass<C2, INV, 4>(src, dst, twp, N, L); break;
+      case 5: mixed_pass<C2, INV, 5>(src, dst, twp, N, L); break;
+      default: mixed_pass<C2, INV, 7>(src, dst, twp, N, L); break;
+    }
+    __syncthreads();
+    C2* t2 = src; src = dst; dst = t2;
+    L *= Rdx;
+  }
+  C2* o = out + (size_t)row * N;
+  const R scale = INV ? (R)1 / (R)N : (R)1;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    C2 v = src[i];
+    v.x *= scale;
+    v.y *= scale;
+    o[i] = v;
+  }
+}
+
 }  // namespace
 
 // Factor Nz into passes of radix 4, 2, 3, 5, 7 (the Stockham order is free).
@@ -425,8 +446,8 @@ pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& 
   plan.N = c.Nz;
   plan.n_pass = s->n_radix;
   for (int i = 0; i < kMaxRadixPasses; ++i) plan.radix[i] = s->radix[i];
-  const double2* tw = s->at<double2>(s->lay.twiddle);
-  const float2* twf = s->at<float2>(s->lay.twiddle_f);
+  const double2* tw = s->at<double2>(s->lay.twp);
+  const float2* twf = s->at<float2>(s->lay.twp_f);
   const size_t smem = 2 * (size_t)c.Nz * s->cplx_bytes;
   if (c.precision == PIC_FP64) {
     if (inverse) {

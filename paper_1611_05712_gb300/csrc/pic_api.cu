@@ -95,7 +95,6 @@ Layout make_layout(const pic_config& c) {
   L.tz = take((size_t)c.Nz * 8);
   L.tr = take((size_t)c.Nm * c.Nr * 8);
   L.coef = take(6 * G * 8);
-  L.twiddle = take((size_t)c.Nz * 16);
   L.twp = take((size_t)c.Nz * 16);
   if (mixed) {
     for (int b = 0; b < 2; ++b)
@@ -107,7 +106,6 @@ Layout make_layout(const pic_config& c) {
     L.kzmod_f = take((size_t)c.Nz * 4);
     L.tz_f = take((size_t)c.Nz * 4);
     L.tr_f = take((size_t)c.Nm * c.Nr * 4);
-    L.twiddle_f = take((size_t)c.Nz * 8);
     L.twp_f = take((size_t)c.Nz * 8);
     if (c.precision == PIC_MIXED_BF16X6) {
       // three BF16 planes per matrix, rows padded to 16 bytes

@@ -32,14 +32,14 @@ enum : int32_t { kErrNumeric = 1, kErrTimeout = 2, kErrRange = 4 };
 struct Layout {
   size_t E, B, Eh, Bh, dep, srch, tmp, rho_prev_h, rho_ion;   // grids
   size_t kperp, binv, mfwd, svd_w, svd_v, svd_d;                // DHT tables and scratch
-  size_t kzmod, tz, tr, coef, twiddle;                           // PSATD tables
-  size_t twp;        // power-of-two Nz: per-pass twiddle tables of the radix-8 FFT
+  size_t kzmod, tz, tr, coef;                                    // PSATD tables
+  size_t twp;        // per-pass twiddle tables of the row FFT (radix-8 or mixed-radix plan)
   size_t part[2][7], pid[2];                                     // particles (double buffer)
   size_t keys, perm, perm_tmp, count, start, scan_blk, big_list, big_count;
   size_t diag_acc, err;
   // mixed-precision form only (0 otherwise): float copies of the tables, the split DHT
   // matrices, FP32 cell-relative particles and an FP64 staging area for particle IO
-  size_t coef_f, kperp_f, kzmod_f, tz_f, tr_f, twiddle_f, twp_f;
+  size_t coef_f, kperp_f, kzmod_f, tz_f, tr_f, twp_f;
   size_t mfwd_hi, mfwd_lo, binv_hi, binv_lo;   // TF32 form: hi/lo planes; BF16 form: *_hi = 3 planes
   size_t pf[2][13];  // iz, fz, ixy (packed int16 x, y cells), fx, fy, u/c hi (3), u/c lo (3), w, id
   size_t stage64;    // 7 x capacity float64

@@ -346,14 +346,6 @@ __global__ void k_psatd_coef(double* coef, const double* kperp, const double* kz
 }
 
 // tw[k] = exp(-2 pi i k / N), k < N
-__global__ void k_twiddles(double2* tw, int N) {
-  int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  double s, c;
-  sincospi(2.0 * (double)k / (double)N, &s, &c);
-  tw[k] = make_double2(c, -s);
-}
-
 // Power-of-two Nz: twiddles of the radix-8 Stockham passes (radix R, L = product of the
 // earlier radices): entry L-1 + (r-1) L + k holds w_{LR}^{rk} = exp(-2 pi i r k / (L R)),
 // 1 <= r < R, k < L; the passes' tables tile entries 0..N-2 (entry N-1 is unused).
@@ -367,6 +359,33 @@ __global__ void k_twiddles_pow2(double2* tw, int N) {
   int L = 1;
   for (int p = 0; p < n8 + (rem ? 1 : 0); ++p) {
     const int R = p < n8 ? 8 : (1 << rem);
+    if (idx < L - 1 + (R - 1) * L) {
+      const int off = idx - (L - 1);
+      const int r = off / L + 1, k = off % L;
+      double sn, cs;
+      sincospi(2.0 * (double)(r * k) / (double)(L * R), &sn, &cs);
+      tw[idx] = make_double2(cs, -sn);
+      return;
+    }
+    L *= R;
+  }
+}
+
+// Any 7-smooth Nz: twiddles of the mixed-radix Stockham passes radix[0], radix[1], ...
+// (the plan of the row FFT), at the same entries: pass p (radix R, L = product of the
+// earlier radices) holds w_{LR}^{rk} at L-1 + (r-1) L + k.
+struct RadixPlan {
+  int n_pass;
+  int radix[kMaxRadixPasses];
+};
+
+__global__ void k_twiddles_plan(double2* tw, int N, RadixPlan plan) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= N) return;
+  if (idx == N - 1) { tw[idx] = make_double2(1.0, 0.0); return; }
+  int L = 1;
+  for (int p = 0; p < plan.n_pass; ++p) {
+    const int R = plan.radix[p];
     if (idx < L - 1 + (R - 1) * L) {
       const int off = idx - (L - 1);
       const int r = off / L + 1, k = off % L;
@@ -541,22 +560,19 @@ pic_status launch_setup_tables(Sim* s, int32_t order_p) {
 }
 
 pic_status launch_setup_twiddles(Sim* s) {
-  k_twiddles<<<blocks_for(s->cfg.Nz, 128), 128, 0, s->stream>>>(s->at<double2>(s->lay.twiddle),
-                                                                s->cfg.Nz);
-  PIC_LAUNCHED(s);
   const bool pow2 = fft_is_pow2(s->cfg.Nz);
   if (pow2) {
     k_twiddles_pow2<<<blocks_for(s->cfg.Nz, 128), 128, 0, s->stream>>>(s->at<double2>(s->lay.twp), s->cfg.Nz);
-    PIC_LAUNCHED(s);
+  } else {
+    RadixPlan plan{s->n_radix, {}};
+    for (int i = 0; i < kMaxRadixPasses; ++i) plan.radix[i] = s->radix[i];
+    k_twiddles_plan<<<blocks_for(s->cfg.Nz, 128), 128, 0, s->stream>>>(s->at<double2>(s->lay.twp), s->cfg.Nz, plan);
   }
+  PIC_LAUNCHED(s);
   if (s->cfg.precision != PIC_FP64) {
     const size_t n2 = 2 * (size_t)s->cfg.Nz;
-    k_to_float<<<conv_grid(n2), 256, 0, s->stream>>>(s->at<double>(s->lay.twiddle), s->at<float>(s->lay.twiddle_f), n2);
+    k_to_float<<<conv_grid(n2), 256, 0, s->stream>>>(s->at<double>(s->lay.twp), s->at<float>(s->lay.twp_f), n2);
     PIC_LAUNCHED(s);
-    if (pow2) {
-      k_to_float<<<conv_grid(n2), 256, 0, s->stream>>>(s->at<double>(s->lay.twp), s->at<float>(s->lay.twp_f), n2);
-      PIC_LAUNCHED(s);
-    }
   }
   return PIC_OK;
 }
