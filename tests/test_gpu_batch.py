@@ -35,7 +35,8 @@ def _make(w, precision, stream):
     return bd.Sim.from_workload(w, P, npl, beams, precision=precision, stream=stream), (P, npl, beams)
 
 
-@pytest.mark.parametrize("precision,tol", [(bd.PIC_FP64, 1e-12), (bd.PIC_MIXED_TF32X3, 1e-5)])
+@pytest.mark.parametrize("precision,tol", [(bd.PIC_FP64, 1e-12), (bd.PIC_MIXED_TF32X3, 1e-5),
+                                           (bd.PIC_MIXED_BF16X6, 1e-5)])
 def test_batch_graph_matches_individual_stepping(precision, tol):
     import torch
     ws = _members()
