@@ -306,9 +306,21 @@ pic_status pic_copy_buffer(pic_sim* sim, int32_t buffer_id, void* dst, size_t by
 pic_status pic_load_buffer(pic_sim* sim, int32_t buffer_id, const void* src, size_t bytes,
                            int32_t src_on_host);
 
-/* Wait for the stream and report any device error word.  Errors: PIC_ERR_CUDA,
+/* Wait for the stream and report any device error word.  The word is sticky: it stays
+ * set (and keeps being reported) until pic_clear_error.  Errors: PIC_ERR_CUDA,
  * PIC_ERR_NUMERIC, PIC_ERR_TIMEOUT. */
 pic_status pic_sync(pic_sim* sim);
+
+/* Clear the device error word (asynchronous).  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+pic_status pic_clear_error(pic_sim* sim);
+
+/* Health check of the failure path (no counterpart in the paper): one CTA waits, with a
+ * cap of max_polls polls (1 <= max_polls <= 2^24), on an mbarrier that nothing arrives on,
+ * the same bounded wait the tensor-core kernels use, then raises the timeout bit of the
+ * device error word and returns.  The next pic_sync reports PIC_ERR_TIMEOUT and the
+ * handle stays usable after pic_clear_error.  Asynchronous.  Errors: PIC_ERR_ARG,
+ * PIC_ERR_CUDA. */
+pic_status pic_selftest_wait_timeout(pic_sim* sim, int32_t max_polls);
 
 /* Number of kernels this handle has launched so far (host-side count, for accounting). */
 pic_status pic_launch_count(pic_sim* sim, int64_t* launches);

@@ -106,6 +106,8 @@ def load():
         "pic_get_tuning": [P, ctypes.POINTER(PicTuning)],
         "pic_fields_to_spectral": [P],
         "pic_copy_window": [P, I32, I32, I32, P, I32],
+        "pic_clear_error": [P],
+        "pic_selftest_wait_timeout": [P, I32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -220,6 +222,12 @@ class Sim:
 
     def field_step(self, order_p=-1):
         _check(self.lib.pic_field_step(self.h, int(order_p)), "pic_field_step")
+
+    def clear_error(self):
+        _check(self.lib.pic_clear_error(self.h), "pic_clear_error")
+
+    def selftest_wait_timeout(self, max_polls=4096):
+        _check(self.lib.pic_selftest_wait_timeout(self.h, int(max_polls)), "pic_selftest_wait_timeout")
 
     def fields_to_spectral(self):
         _check(self.lib.pic_fields_to_spectral(self.h), "pic_fields_to_spectral")

@@ -422,6 +422,28 @@ __global__ void __launch_bounds__(kWsThreads, 1) k_dht_tc_ws(DhtBatch bt, TcPara
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
+// Health check of the bounded waits: an mbarrier that nothing arrives on, waited on with a
+// cap of max_polls polls; the timeout raises the error bit and the kernel returns.
+__global__ void k_wait_selftest(int32_t* err, uint32_t max_polls) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    const uint32_t a = smem_u32(&bar);
+    bool done = false;
+    for (uint32_t it = 0; it < max_polls && !done; ++it) {
+      uint32_t d;
+      asm volatile(
+          "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+          : "=r"(d)
+          : "r"(a), "r"(0u)
+          : "memory");
+      done = d != 0;
+    }
+    if (!done) atomicOr(err, kErrTimeout);
+  }
+}
+
 }  // namespace
 
 constexpr size_t kWsSmemMax = 227 * 1024;   // dynamic shared memory of the persistent kernel
@@ -581,6 +603,12 @@ pic_status launch_dht_tc(Sim* s, const DhtBatch& b) {
   else
     k_dht_tc_ws<0><<<grid, kWsThreads, smem, s->stream>>>(b, P, maps, s->at<int32_t>(s->lay.err), n_stages,
                                                           n_tiles_total);
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
+pic_status launch_wait_selftest(Sim* s, uint32_t max_polls) {
+  k_wait_selftest<<<1, 32, 0, s->stream>>>(s->at<int32_t>(s->lay.err), max_polls);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }

@@ -569,6 +569,23 @@ pic_status pic_sync(pic_sim* sim) {
   return PIC_OK;
 }
 
+pic_status pic_clear_error(pic_sim* sim) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  PIC_CUDA(cudaMemsetAsync(s->ws + s->lay.err, 0, sizeof(int32_t), s->stream));
+  return PIC_OK;
+}
+
+pic_status pic_selftest_wait_timeout(pic_sim* sim, int32_t max_polls) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (max_polls < 1 || max_polls > (1 << 24)) {
+    set_error("max_polls=%d must be in [1, 2^24]", max_polls);
+    return PIC_ERR_ARG;
+  }
+  return launch_wait_selftest(s, (uint32_t)max_polls);
+}
+
 pic_status pic_write_particles(pic_sim* sim, const double* const soa[7], const int32_t* id, int64_t n,
                                int32_t on_host) {
   Sim* s = reinterpret_cast<Sim*>(sim);

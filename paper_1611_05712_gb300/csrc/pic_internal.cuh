@@ -141,6 +141,7 @@ pic_status launch_gemm_f64(Sim* s, const DhtBatch& b, int ncols);
 pic_status launch_dht_tc(Sim* s, const DhtBatch& b);
 pic_status dht_tc_configure_device();   // once per device, before any tcgen05 DHT launch
 pic_status dht_tc_make_maps(Sim* s);     // once per handle: tensor maps of the split matrices
+pic_status launch_wait_selftest(Sim* s, uint32_t max_polls);   // bounded wait that times out
 
 // ---- launchers (psatd.cu) ----
 pic_status launch_psatd(Sim* s);
