@@ -29,8 +29,8 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2070 MHz 
 BF16_TFLOPS = 1884.9                           # MEASURED_PEAKS.json bf16 burst
 FP64_PROBE_TFLOPS = 1.1947                     # FMA-loop probe on this machine's GB300 at 1987 MHz
 # DRAM bytes per FP64 DHT launch (k_gemm<double>) on this workload, from one ncu capture of
-# the current kernel (forward 71.51 + 27.33 MB, inverse 107.24 + 61.24 MB, mean of the two)
-DHT_F64_TRAFFIC_BYTES = (71.50592 + 27.328 + 107.238912 + 61.2352) / 2 * 1e6
+# the current kernel (forward 71.42 + 27.50 MB, inverse 106.87 + 60.50 MB, mean of the two)
+DHT_F64_TRAFFIC_BYTES = (71.424 + 27.501568 + 106.872064 + 60.499968) / 2 * 1e6
 
 
 def parse():

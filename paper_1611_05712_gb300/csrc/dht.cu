@@ -18,7 +18,6 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_gemm(DhtBatch bt, int Nr, int Nc) {
   const int b = blockIdx.z;
   const R* __restrict__ A = static_cast<const R*>(bt.A[b]);
-  const R* __restrict__ Alo = static_cast<const R*>(bt.Alo[b]);
   const R* __restrict__ X = static_cast<const R*>(bt.X[b]);
   R* __restrict__ Y = static_cast<R*>(bt.Y[b]);
   const int row0 = blockIdx.y * BM, col0 = blockIdx.x * BN;
@@ -37,12 +36,7 @@ __global__ void __launch_bounds__(256) k_gemm(DhtBatch bt, int Nr, int Nc) {
     for (int q = 0; q < 4; ++q) {
       const int r = t >> 2, kk = ((t & 3) << 2) + q;
       const int gr = row0 + r, gk = k0 + kk;
-      R a = (R)0;
-      if (gr < Nr && gk < Nr) {
-        a = A[(size_t)gr * Nr + gk];
-        if (Alo) a += Alo[(size_t)gr * Nr + gk];
-      }
-      As[kk][r] = a;
+      As[kk][r] = (gr < Nr && gk < Nr) ? A[(size_t)gr * Nr + gk] : (R)0;
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -89,7 +83,7 @@ pic_status launch_gemm_f64(Sim* s, const DhtBatch& b, int ncols) {
 
 pic_status launch_dht(Sim* s, const DhtBatch& b) {
   if (s->cfg.precision == PIC_FP64) return launch_gemm_f64(s, b, 2 * s->cfg.Nz);
-  return launch_dht_tc(s, b);   // mixed form: 3-term TF32 on tcgen05 (dht_tc.cu)
+  return launch_dht_tc(s, b);   // mixed forms: split products on tcgen05 (dht_tc.cu)
 }
 
 }  // namespace pic

@@ -192,10 +192,7 @@ pic_status dht_forward(Sim* s, int n_comp) {
       if (s->cfg.precision == PIC_FP64) {
         b.A[b.n] = s->at<double>(s->lay.mfwd) + moff;
       } else {
-        const size_t foff = ((size_t)m * 3 + slot_of[comp]) * c.Nr * split_pitch(c.Nr);
-        b.A[b.n] = s->at<float>(s->lay.mfwd_hi) + foff;
-        b.Alo[b.n] = s->at<float>(s->lay.mfwd_lo) + foff;
-        b.mat[b.n] = (int16_t)(m * 3 + slot_of[comp]);
+        b.mat[b.n] = (int16_t)(m * 3 + slot_of[comp]);   // the tensor maps select the matrix
       }
       b.X[b.n] = s->at<char>(s->lay.tmp) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       b.Y[b.n] = s->at<char>(s->lay.srch) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
@@ -256,9 +253,6 @@ pic_status dht_inverse(Sim* s) {
       if (s->cfg.precision == PIC_FP64) {
         b.A[b.n] = s->at<double>(s->lay.binv) + moff;
       } else {
-        const size_t foff = ((size_t)m * 3 + slot_of[comp % 3]) * c.Nr * split_pitch(c.Nr);
-        b.A[b.n] = s->at<float>(s->lay.binv_hi) + foff;
-        b.Alo[b.n] = s->at<float>(s->lay.binv_lo) + foff;
         b.mat[b.n] = (int16_t)(kMaxModes * 3 + m * 3 + slot_of[comp % 3]);
       }
       b.X[b.n] = s->at<char>(s->lay.Eh) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;

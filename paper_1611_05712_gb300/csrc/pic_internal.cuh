@@ -123,21 +123,21 @@ pic_status fft_configure_device();      // once per device, before any FFT launc
 bool fft_is_pow2(int N);                // rows of power-of-two length use the radix-8 kernel
 
 // ---- launchers (dht.cu) ----
-// out[b] = A[b] (Nr x Nr, row-major [out][red]) * in[b] (Nr x 2Nz reals).  Element type
-// float64 in the FP64 form; float in the mixed form, where A is split as A + Alo.
+// out[b] = A[b] (Nr x Nr, row-major [out][red]) * in[b] (Nr x 2Nz reals).  FP64 form: A[b]
+// points at the float64 matrix.  Mixed forms: mat[b] names the split matrix whose tensor
+// maps the tcgen05 kernel reads (fwd: m*3+slot, inv: kMaxModes*3 + m*3+slot); X, Y float.
 struct DhtBatch {
   int32_t n;
   const void* A[24];
-  const void* Alo[24];   // null: no low part
   const void* X[24];
   void* Y[24];
-  int16_t mat[24];       // mixed form: matrix id (fwd: m*3+slot, inv: kMaxModes*3 + m*3+slot)
+  int16_t mat[24];
 };
 // The DHT of the current precision form (FP64 SIMT, or 3-term TF32 on tcgen05).
 pic_status launch_dht(Sim* s, const DhtBatch& b);
 // FP64 Y = A X with A Nr x Nr and X Nr x ncols (setup products and the FP64 DHT).
 pic_status launch_gemm_f64(Sim* s, const DhtBatch& b, int ncols);
-// Mixed form: Y = (Ahi + Alo) X with 3-term TF32 products on tcgen05 (dht_tc.cu).
+// Mixed forms: Y = A X with split products on tcgen05 (dht_tc.cu); A from the tensor maps.
 pic_status launch_dht_tc(Sim* s, const DhtBatch& b);
 pic_status dht_tc_configure_device();   // once per device, before any tcgen05 DHT launch
 pic_status dht_tc_make_maps(Sim* s);     // once per handle: tensor maps of the split matrices
