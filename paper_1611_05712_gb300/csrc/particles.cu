@@ -716,23 +716,24 @@ __device__ __forceinline__ void deposit_one_f(const GeomF& g, const DepArgsF& a,
   const float vr = c * vx + s * vy, vt = c * vy - s * vx;
   float phr = 1.f, phi = 0.f;   // e^{+i m theta}
   const size_t RZ = (size_t)g.Nr * g.Nz;
+  // lanes visit the 4 nodes in an order rotated by the lane index, so that lanes of one
+  // cell (which share their nodes) hit different nodes in the same instruction
+  const int rot = threadIdx.x & 3;
   for (int m = 0; m < g.Nm; ++m) {
     const float qre = a.q * w * phr, qim = a.q * w * phi;
     const float fs = (m & 1) ? -1.f : 1.f, fv = -fs;
 #pragma unroll
-    for (int dz = 0; dz < 2; ++dz) {
+    for (int q = 0; q < 4; ++q) {
+      const int node = (q + rot) & 3;
+      const int dz = node >> 1, dj = node & 1;
       const int i = dz ? st.i1 : st.i0;
-      const float wz = dz ? st.wz1 : st.wz0;
-#pragma unroll
-      for (int dj = 0; dj < 2; ++dj) {
-        const int j = st.j0 + dj;
-        const float wgt = wz * (dj ? st.wr1 : st.wr0);
-        if (do_rho) dep_node_fb(a.rho + m * RZ, g, bR, 0, m, j, i, wgt, fs, qre, qim, invV);
-        if (do_J) {
-          dep_node_fb(a.J + m * RZ, g, bJ, 0, m, j, i, wgt, fv, qre * vr, qim * vr, invV);
-          dep_node_fb(a.J + g.G + m * RZ, g, bJ, 1, m, j, i, wgt, fv, qre * vt, qim * vt, invV);
-          dep_node_fb(a.J + 2 * g.G + m * RZ, g, bJ, 2, m, j, i, wgt, fs, qre * vz, qim * vz, invV);
-        }
+      const int j = st.j0 + dj;
+      const float wgt = (dz ? st.wz1 : st.wz0) * (dj ? st.wr1 : st.wr0);
+      if (do_rho) dep_node_fb(a.rho + m * RZ, g, bR, 0, m, j, i, wgt, fs, qre, qim, invV);
+      if (do_J) {
+        dep_node_fb(a.J + m * RZ, g, bJ, 0, m, j, i, wgt, fv, qre * vr, qim * vr, invV);
+        dep_node_fb(a.J + g.G + m * RZ, g, bJ, 1, m, j, i, wgt, fv, qre * vt, qim * vt, invV);
+        dep_node_fb(a.J + 2 * g.G + m * RZ, g, bJ, 2, m, j, i, wgt, fs, qre * vz, qim * vz, invV);
       }
     }
     const float nr = phr * c - phi * s, ni = phr * s + phi * c;
