@@ -272,24 +272,25 @@ __device__ void deposit_one(const GridGeom& g, const DepArgs& a, const double* i
   const Stencil st = stencil(g, z, r);
   const double vr = c * vx + s * vy, vt = c * vy - s * vx;
   double phr = 1.0, phi = 0.0;   // e^{+i m theta}
+  // the 4 nodes in an order rotated by the lane index: lanes of one cell (same nodes) then
+  // hit different addresses in one instruction
+  const int rot = threadIdx.x & 3;
   for (int m = 0; m < g.Nm; ++m) {
     const double qre = a.q * w * phr, qim = a.q * w * phi;
     const double fs = (m & 1) ? -1.0 : 1.0;   // scalar / z fold (-1)^m
     const double fv = -fs;                     // r / theta fold (-1)^{m+1}
 #pragma unroll
-    for (int dz = 0; dz < 2; ++dz) {
+    for (int q = 0; q < 4; ++q) {
+      const int node = (q + rot) & 3;
+      const int dz = node >> 1, dj = node & 1;
       const int i = dz ? st.i1 : st.i0;
-      const double wz = dz ? st.wz1 : st.wz0;
-#pragma unroll
-      for (int dj = 0; dj < 2; ++dj) {
-        const int j = st.j0 + dj;
-        const double wgt = wz * (dj ? st.wr1 : st.wr0);
-        if (do_rho) dep_node(a.rho + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fs, qre, qim, invV);
-        if (do_J) {
-          dep_node(a.J + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fv, qre * vr, qim * vr, invV);
-          dep_node(a.J + g.G + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fv, qre * vt, qim * vt, invV);
-          dep_node(a.J + 2 * g.G + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fs, qre * vz, qim * vz, invV);
-        }
+      const int j = st.j0 + dj;
+      const double wgt = (dz ? st.wz1 : st.wz0) * (dj ? st.wr1 : st.wr0);
+      if (do_rho) dep_node(a.rho + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fs, qre, qim, invV);
+      if (do_J) {
+        dep_node(a.J + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fv, qre * vr, qim * vr, invV);
+        dep_node(a.J + g.G + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fv, qre * vt, qim * vt, invV);
+        dep_node(a.J + 2 * g.G + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fs, qre * vz, qim * vz, invV);
       }
     }
     const double nr = phr * c - phi * s, ni = phr * s + phi * c;
