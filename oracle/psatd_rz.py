@@ -37,6 +37,9 @@ Readings where the paper is silent (each repeated where it is used):
   R-init    beam fields from a relativistic spectral Poisson solve.
   R-diag    normalised rms emittance; slice energy spread over 0.5 um slices in
             [zbar - 3 sigma_z, zbar + 3 sigma_z).
+  R-window  moving window on a ring of z columns: removal behind the back edge,
+            re-injection of each column's initial plasma at the front, departing
+            column of E, B zeroed (section "Moving window" below).
 """
 from __future__ import annotations
 
@@ -632,12 +635,17 @@ def make_state(g: Grid, order_p: int, filt: bool, particles: dict, n_neutral: in
                  rho0h, rho_ion, P)
 
 
-def gather_push(st: State):
+def gather_push(st: State, window=None):
     """Gather E^n, B^n at x^n, push u^{n-1/2} -> u^{n+1/2}, move x^n -> x^{n+1/2} -> x^{n+1}.
 
     Returns the real-space current J^{n+1/2} deposited at x^{n+1/2} (R-deposit, R-push).
+    Inactive particles (w = 0, R-window) keep their position and momentum.  With
+    ``window = (back_z, shift)`` an active particle that ends behind the window's back
+    edge is removed after its push and current deposit (``window_removed``, R-window).
     """
     g, P = st.g, st.p
+    act = P["w"] != 0.0
+    z0 = P["z"]
     F = gather(g, st.E, st.B, P["x"], P["y"], P["z"])
     ux, uy, uz = boris_push(P["ux"], P["uy"], P["uz"], *F, st.q, st.m, g.dt)
     ig = inv_gamma(ux, uy, uz)
@@ -647,7 +655,14 @@ def gather_push(st: State):
     J = deposit_current(g, xh, yh, zh, vx, vy, vz, P["w"], st.q)
     x1, y1, z1 = xh + hdt * vx, yh + hdt * vy, wrap_z(g, zh + hdt * vz)
     x1, y1, ux, uy = reflect_r(g, x1, y1, ux, uy)
-    P.update(x=x1, y=y1, z=z1, ux=ux, uy=uy, uz=uz)
+    new = {"x": x1, "y": y1, "z": z1, "ux": ux, "uy": uy, "uz": uz}
+    for k, v in new.items():
+        P[k] = np.where(act, v, P[k])
+    if window is not None:
+        back_z, shift = window
+        gone = act & window_removed(g, z0, hdt * vz, back_z, shift)
+        for k in ("w", "ux", "uy", "uz"):
+            P[k] = np.where(gone, 0.0, P[k])
     return J
 
 
@@ -680,6 +695,137 @@ def pic_step(st: State, n_steps: int = 1):
         rho = deposit_rho(st.g, P["x"], P["y"], P["z"], P["w"], st.q) + st.rho_ion
         field_step(st, rho, J)
     return st
+
+
+# --------------------------------------------------------------------------
+# Moving window (R-window)
+# --------------------------------------------------------------------------
+# The paper follows the beams in co-moving coordinates zeta = z - c t (AMPA, Fig. ez:
+# 35 mm of propagation) without stating the mechanics; R-window is the reading taken.
+#   * The z grid is a ring: after k shifts the window's back column is k mod Nz and its
+#     back edge lies at (k mod Nz) dz; arrays and particle positions never move.
+#   * The window moves one cell at the end of every `period`-th cycle (period 1 when
+#     c dt = dz, a window moving at c).
+#   * Removal: in the push of every cycle, an active particle whose window coordinate
+#     zeta = ((z^n - back) mod L) + (displacement of the step) - (dz if the window moves)
+#     is negative has left through the back edge; its weight and momentum become 0
+#     (inactive).  Its current of that step is still deposited.
+#   * Injection: when the window moves, the departing column c becomes the front column;
+#     the plasma loaded there at set-up (the template: ids of column c in increasing
+#     order) is placed, at rest, into the inactive particles of smallest id.  A template
+#     larger than the inactive pool is cut to the pool's size.
+#   * Fields: after the field step of a moving cycle the departing column's E and B are
+#     zeroed in real space and their transform is subtracted from the spectral state:
+#     F^ <- F^ - forward(F 1_c), F <- F (1 - 1_c).  rho^ and the ion background stay.
+#   * The ion background is fixed per array column; the template reloads each column's
+#     initial plasma, so the fresh front is neutral.
+@dataclass
+class Window:
+    """Moving-window state (R-window)."""
+
+    period: int      # the window moves one cell every `period` cycles
+    cycles: int      # cycles advanced since set-up
+    shifts: int      # cells moved; the back column is shifts mod Nz
+    tpl: dict        # x, y, z, w of the plasma at set-up, indexed by id (ids < n_plasma)
+    col_ids: list    # per column, the template ids loaded there, increasing
+
+
+def window_setup(st: State, n_plasma: int, period: int, n_reserve: int) -> Window:
+    """Append ``n_reserve`` inactive particles (w = u = 0 at the origin, ids np ..) and
+    take the particles with id < n_plasma as the plasma template (R-window).
+    The ids held must be 0 .. np-1."""
+    g, P = st.g, st.p
+    n = P["x"].size
+    if not np.array_equal(np.sort(P["id"]), np.arange(n)):
+        raise ValueError("window: particle ids must be 0 .. np-1")
+    if period < 1 or not 0 <= n_plasma <= n or n_reserve < 0:
+        raise ValueError("window: bad period, n_plasma or n_reserve")
+    for k in ("x", "y", "z", "ux", "uy", "uz", "w"):
+        P[k] = np.concatenate([P[k], np.zeros(n_reserve)])
+    P["id"] = np.concatenate([P["id"], np.arange(n, n + n_reserve, dtype=P["id"].dtype)])
+    where = np.empty(n, dtype=np.int64)
+    where[P["id"][:n]] = np.arange(n)
+    at = where[:n_plasma]
+    tpl = {k: P[k][at].copy() for k in ("x", "y", "z", "w")}
+    col = np.clip(np.floor(tpl["z"] / g.dz).astype(np.int64), 0, g.Nz - 1)
+    col_ids = [np.flatnonzero(col == c) for c in range(g.Nz)]
+    return Window(period, 0, 0, tpl, col_ids)
+
+
+def window_removed(g: Grid, z_old, half_move, back_z: float, shift: bool):
+    """Particles whose window coordinate after this step is negative (R-window):
+    zeta = ((z_old - back) mod L) + half_move + half_move - (dz if the window moves)."""
+    zo = z_old - back_z
+    zo = np.where(zo < 0.0, zo + g.L, zo)
+    zn = (zo + half_move) + half_move - (g.dz if shift else 0.0)
+    return zn < 0.0
+
+
+def window_inject(st: State, win: Window, column: int) -> int:
+    """Load the template of ``column`` into the inactive particles of smallest id, at rest
+    (R-window).  Returns the number of template particles that found no slot."""
+    P = st.p
+    fresh = win.col_ids[column]
+    free = np.sort(P["id"][P["w"] == 0.0])
+    k = min(fresh.size, free.size)
+    where = np.empty(P["id"].size, dtype=np.int64)
+    where[P["id"]] = np.arange(P["id"].size)
+    slots = where[free[:k]]
+    for key in ("x", "y", "z", "w"):
+        P[key][slots] = win.tpl[key][fresh[:k]]
+    for key in ("ux", "uy", "uz"):
+        P[key][slots] = 0.0
+    return int(fresh.size - k)
+
+
+def window_clear_column(st: State, column: int):
+    """Remove the departing column's E and B: real space zeroed there, spectral state
+    minus the forward transform of the column (R-window)."""
+    g, h = st.g, st.h
+    for name, hname in (("E", "Eh"), ("B", "Bh")):
+        F = getattr(st, name)
+        col = []
+        for c in range(3):
+            Fc = np.zeros_like(F[c])
+            Fc[:, :, column] = F[c][:, :, column]
+            col.append(Fc)
+        D = forward_vector(g, h, *col)
+        setattr(st, hname, tuple(getattr(st, hname)[c] - D[c] for c in range(3)))
+        keep = []
+        for c in range(3):
+            Fn = F[c].copy()
+            Fn[:, :, column] = 0.0
+            keep.append(Fn)
+        setattr(st, name, tuple(keep))
+
+
+def pic_step_window(st: State, win: Window, n_steps: int = 1):
+    """n PIC cycles in the moving window (R-window): push with removal, injection when the
+    window moves, sort, rho deposit, field step, column removal.  Returns the number of
+    template particles dropped for want of inactive slots."""
+    g = st.g
+    dropped = 0
+    for _ in range(n_steps):
+        shift = (win.cycles + 1) % win.period == 0
+        column = win.shifts % g.Nz
+        J = gather_push(st, window=(column * g.dz, shift))
+        if shift:
+            dropped += window_inject(st, win, column)
+        sort_particles(st)
+        P = st.p
+        rho = deposit_rho(g, P["x"], P["y"], P["z"], P["w"], st.q) + st.rho_ion
+        field_step(st, rho, J)
+        if shift:
+            window_clear_column(st, column)
+            win.shifts += 1
+        win.cycles += 1
+    return dropped
+
+
+def window_z(g: Grid, win: Window, z):
+    """Window coordinate (z - back edge) mod L of array positions z (R-window)."""
+    zw = z - (win.shifts % g.Nz) * g.dz
+    return np.where(zw < 0.0, zw + g.L, zw)
 
 
 # --------------------------------------------------------------------------
