@@ -26,7 +26,8 @@
  * Ownership: the caller allocates ONE device workspace of pic_required_bytes() bytes
  * (e.g. a torch uint8 tensor) and passes its pointer and a cudaStream_t; the library
  * carves every grid, table and particle array out of it and never allocates or frees
- * device memory itself.  It owns only the opaque host handle (freed by pic_destroy).
+ * device memory itself (the moving window takes a second caller workspace, see
+ * pic_window_setup).  It owns only the opaque host handle (freed by pic_destroy).
  *
  * Errors: every call returns a pic_status; no exception, abort or exit crosses the ABI.
  * pic_last_error() returns a thread-local text for the last failure.  Device-side
@@ -263,6 +264,60 @@ pic_status pic_batch_destroy(pic_batch* batch);
 pic_status pic_fields_to_spectral(pic_sim* sim);
 pic_status pic_copy_window(pic_sim* src, int32_t buffer_id, int32_t src_z0, int32_t nz, pic_sim* dst,
                            int32_t dst_z0);
+
+/* ---- moving window ---------------------------------------------------------------
+ * The paper follows its beams in the co-moving frame zeta = z - c t over 35 mm of
+ * propagation (section "Accurate modeling of plasma accelerators in finite order PSATD",
+ * Fig. ez) and does not state how the window is implemented.  This library moves it on
+ * a ring of z columns: nothing is copied, the window's back column after k shifts is
+ * k mod Nz and its back edge lies at (k mod Nz) dz.  Once set up, every pic_step cycle
+ *   1. pushes as usual, except that inactive particles (w = 0) are skipped, and then
+ *      removes every active particle whose window coordinate
+ *        zeta = ((z^n - back edge) mod L) + (its z displacement in the step) - s dz
+ *      is negative (s = 1 if the window moves at the end of this cycle, else 0): its
+ *      weight and momentum become 0.  Its current of this step is still deposited;
+ *   2. if the window moves: loads the template of the departing column c (the plasma
+ *      particles that lay in column c at set-up, in increasing id order) at rest into the
+ *      inactive particles, smallest id first, each keeping its id; template particles
+ *      beyond the number of inactive particles are dropped and counted;
+ *   3. sorts, deposits rho and advances the fields as usual;
+ *   4. if the window moves: zeroes column c of the real-space E and B and subtracts the
+ *      forward transform (z-FFT, DHT of orders m+1, m-1, m) of that column from the
+ *      spectral E and B; rho^n and the ion background are left as they are.
+ * The window moves at the end of every period-th cycle after set-up (period = 1 gives a
+ * window at c when c dt = dz).  The ion background is fixed per array column and the
+ * template reloads each column's initial plasma, so the front stays neutral.  The stage
+ * entry points (pic_gather_push, pic_sort, ...) do not move the window, pic_write_particles
+ * switches it off, and pic_batch_create refuses handles that have it on.
+ * While the window is on, pic_diagnostics measures z from the back edge ((z - back edge)
+ * mod L).
+ *
+ * pic_window_required_bytes: device workspace bytes for a template of n_plasma particles
+ * on this handle (n_plasma >= 0).
+ * pic_window_setup: take the particles held with id < n_plasma as the template (their
+ * positions and weights as they are now), append n_reserve inactive particles (w = u = 0;
+ * reserve particle k gets id np + k and sits at the centre of cell (k mod Nz,
+ * (k div Nz) mod Nr) on the x axis), and switch the window on.  The ids held must be
+ * exactly 0 .. np-1 and np + n_reserve <= np_capacity.  workspace: device pointer of
+ * >= pic_window_required_bytes, 256-byte aligned, owned by the caller and kept alive
+ * while the handle lives.  Synchronises.  Errors: PIC_ERR_ARG (period < 1, n_plasma or
+ * n_reserve out of range, ids not 0 .. np-1, workspace too small or misaligned, window
+ * already on), PIC_ERR_CUDA, PIC_ERR_OOM (host scratch).
+ * pic_window_state: cycles since set-up, shifts so far, the current back column and the
+ * number of template particles dropped for want of inactive slots (any output may be
+ * NULL).  Synchronises.  Errors: PIC_ERR_STATE (window not set up). */
+typedef struct pic_window_info {
+  int64_t cycles;
+  int64_t shifts;
+  int32_t back_column;
+  int32_t period;
+  int64_t dropped;
+  int64_t n_template;
+} pic_window_info;
+pic_status pic_window_required_bytes(pic_sim* sim, int64_t n_plasma, size_t* bytes);
+pic_status pic_window_setup(pic_sim* sim, int64_t n_plasma, int32_t period, int64_t n_reserve,
+                            void* workspace, size_t workspace_bytes);
+pic_status pic_window_state(pic_sim* sim, pic_window_info* out);
 
 /* ---- tile tuning -----------------------------------------------------------------
  * The paper gives no kernel tiling; these choices belong to this library.  Two tile sizes

@@ -731,17 +731,21 @@ class Window:
 
 
 def window_setup(st: State, n_plasma: int, period: int, n_reserve: int) -> Window:
-    """Append ``n_reserve`` inactive particles (w = u = 0 at the origin, ids np ..) and
-    take the particles with id < n_plasma as the plasma template (R-window).
-    The ids held must be 0 .. np-1."""
+    """Append ``n_reserve`` inactive particles (w = u = 0, ids np ..) and take the
+    particles with id < n_plasma as the plasma template (R-window).  The ids held must be
+    0 .. np-1.  Reserve particle k sits at the centre of cell (k mod Nz, (k div Nz) mod Nr)
+    on the x axis: where an inactive particle sits changes no result, and spreading them
+    keeps the cells of the sort small."""
     g, P = st.g, st.p
     n = P["x"].size
     if not np.array_equal(np.sort(P["id"]), np.arange(n)):
         raise ValueError("window: particle ids must be 0 .. np-1")
     if period < 1 or not 0 <= n_plasma <= n or n_reserve < 0:
         raise ValueError("window: bad period, n_plasma or n_reserve")
-    for k in ("x", "y", "z", "ux", "uy", "uz", "w"):
-        P[k] = np.concatenate([P[k], np.zeros(n_reserve)])
+    k = np.arange(n_reserve)
+    park = {"x": ((k // g.Nz) % g.Nr + 0.5) * g.dr, "z": (k % g.Nz + 0.5) * g.dz}
+    for key in ("x", "y", "z", "ux", "uy", "uz", "w"):
+        P[key] = np.concatenate([P[key], park.get(key, np.zeros(n_reserve))])
     P["id"] = np.concatenate([P["id"], np.arange(n, n + n_reserve, dtype=P["id"].dtype)])
     where = np.empty(n, dtype=np.int64)
     where[P["id"][:n]] = np.arange(n)

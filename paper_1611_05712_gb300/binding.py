@@ -46,6 +46,11 @@ class PicTuning(ctypes.Structure):
                 ("dht_ms", ctypes.c_double), ("deposit_ms", ctypes.c_double)]
 
 
+class PicWindowInfo(ctypes.Structure):
+    _fields_ = [("cycles", ctypes.c_int64), ("shifts", ctypes.c_int64), ("back_column", ctypes.c_int32),
+                ("period", ctypes.c_int32), ("dropped", ctypes.c_int64), ("n_template", ctypes.c_int64)]
+
+
 class PicError(RuntimeError):
     def __init__(self, status, where, text):
         super().__init__(f"{where}: {STATUS.get(status, status)}: {text}")
@@ -108,6 +113,9 @@ def load():
         "pic_copy_window": [P, I32, I32, I32, P, I32],
         "pic_clear_error": [P],
         "pic_selftest_wait_timeout": [P, I32],
+        "pic_window_required_bytes": [P, I64, ctypes.POINTER(SZ)],
+        "pic_window_setup": [P, I64, I32, I64, P, SZ],
+        "pic_window_state": [P, ctypes.POINTER(PicWindowInfo)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -200,6 +208,24 @@ class Sim:
         return out
 
     # -- initial state ----------------------------------------------------------------
+    # -- moving window ---------------------------------------------------------------
+    def window_setup(self, n_plasma, period=1, n_reserve=0):
+        """Switch the moving window on: particles with id < n_plasma become the plasma
+        template, n_reserve inactive particles are appended (pic_window_setup)."""
+        import torch
+        n = ctypes.c_size_t()
+        _check(self.lib.pic_window_required_bytes(self.h, int(n_plasma), ctypes.byref(n)),
+               "pic_window_required_bytes")
+        self.window_ws = torch.empty(n.value + 256, dtype=torch.uint8, device=self.device)
+        ptr = (self.window_ws.data_ptr() + 255) // 256 * 256
+        _check(self.lib.pic_window_setup(self.h, int(n_plasma), int(period), int(n_reserve),
+                                         ctypes.c_void_p(ptr), n.value), "pic_window_setup")
+
+    def window_state(self):
+        info = PicWindowInfo()
+        _check(self.lib.pic_window_state(self.h, ctypes.byref(info)), "pic_window_state")
+        return {k: getattr(info, k) for k, _ in PicWindowInfo._fields_}
+
     def init_background(self, n_neutral):
         _check(self.lib.pic_init_background(self.h, int(n_neutral)), "pic_init_background")
 

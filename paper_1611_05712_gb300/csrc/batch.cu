@@ -58,6 +58,11 @@ extern "C" pic_status pic_batch_create(pic_sim* const* sims, int32_t n_sims, int
       batch_free(b);
       return PIC_ERR_ARG;
     }
+    if (s->win.on) {   // a captured graph would replay one window position forever
+      set_error("simulation %d has a moving window; batches take fixed windows only", i);
+      batch_free(b);
+      return PIC_ERR_ARG;
+    }
     b->sims.push_back(s);
   }
   b->events.resize(n_sims + 1);

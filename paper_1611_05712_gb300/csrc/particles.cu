@@ -311,9 +311,11 @@ __global__ void k_deposit(const Parts p, int64_t np, GridGeom g, DepArgs a, cons
       const double ig = 1.0 / sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
       vx = ux * ig; vy = uy * ig; vz = uz * ig;
     }
+    const double wt = p.w[i];
+    if (wt == 0.0) continue;   // inactive particles add nothing
     const double x = p.x[i], y = p.y[i], z = p.z[i];
     if (!isfinite(x) || !isfinite(y) || !isfinite(z)) { atomicOr(err, kErrNumeric); continue; }
-    deposit_one(g, a, invV, x, y, z, p.w[i], vx, vy, vz, do_rho, do_J);
+    deposit_one(g, a, invV, x, y, z, wt, vx, vy, vz, do_rho, do_J);
   }
 }
 
@@ -325,14 +327,16 @@ __global__ void k_inv_volume(double* invV, int Nr, double dr, double dz) {
 // ------------------------------------------------------------------ a2 + a3 (+ a4 J)
 __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __restrict__ E,
                               const double2* __restrict__ B, double q, double mass, double dt,
-                              DepArgs dep, const double* invV, int fuse, int32_t* err) {
+                              DepArgs dep, const double* invV, int fuse, int32_t* err, WinArgs wa) {
   const size_t RZ = (size_t)g.Nr * g.Nz;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
+    const double w = p.w[i];
+    if (w == 0.0) continue;   // inactive (moving window): neither pushed nor moved
     double x = p.x[i], y = p.y[i], z = p.z[i];
     if (!isfinite(x) || !isfinite(y) || !isfinite(z)) { atomicOr(err, kErrNumeric); continue; }
+    const double z_old = z;
     double ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
-    const double w = p.w[i];
     double r, c, s;
     polar(x, y, r, c, s);
     const Stencil st = stencil(g, z, r);
@@ -388,6 +392,17 @@ __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __
       uy = uy - 2.0 * ur * cy;
       x *= fr;
       y *= fr;
+    }
+    if (wa.on) {
+      // window coordinate after the step: ((z^n - back) mod L) + 2 half moves - s dz
+      double zo = z_old - wa.back_z;
+      if (zo < 0.0) zo += g.L;
+      const double d = __dmul_rn(hdt, vz);
+      const double zn = __dsub_rn(__dadd_rn(__dadd_rn(zo, d), d), wa.shift ? g.dz : 0.0);
+      if (zn < 0.0) {   // left through the back edge: inactive from now on
+        p.w[i] = 0.0;
+        ux = 0.0; uy = 0.0; uz = 0.0;
+      }
     }
     p.x[i] = x; p.y[i] = y; p.z[i] = z;
     p.ux[i] = ux; p.uy[i] = uy; p.uz[i] = uz;
@@ -834,6 +849,8 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_deposit_f32(const PartsF p,
   for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
     const int32_t id = p.id[i];
     if (id < a.id_lo || id >= a.id_hi) continue;
+    const float wt = p.w[i];
+    if (wt == 0.f) continue;   // inactive particles add nothing
     float x, y;
     pos_cells(p, i, x, y);
     const float fz = p.fz[i];
@@ -848,7 +865,7 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_deposit_f32(const PartsF p,
       const float ig = c * rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
       vx = ux * ig; vy = uy * ig; vz = uz * ig;
     }
-    deposit_one_f(g, a, invV, bR, bJ, iz, fz, x, y, p.w[i], vx, vy, vz, do_rho, do_J);
+    deposit_one_f(g, a, invV, bR, bJ, iz, fz, x, y, wt, vx, vy, vz, do_rho, do_J);
   }
   __syncthreads();
   band_flush(band, g, do_rho ? a.rho : a.J, invV);
@@ -873,7 +890,7 @@ __device__ __forceinline__ void advance_z(int& iz, float& fz, float dfz, int Nz)
 __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, int64_t np, GeomF g,
                                   const float2* __restrict__ EBt, float kq, float kqc, float chdt_dr,
                                   float chdt_dz, DepArgsF dep, const float* invV, int fuse, int32_t* err,
-                                  BandArgs ba) {
+                                  BandArgs ba, WinArgs wa) {
   extern __shared__ __align__(16) int32_t band_smem[];
   __shared__ ChunkStats stats_slot;
   const int64_t chunk = ba.chunk;
@@ -892,6 +909,8 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
   band_zero(band);
   __syncthreads();
   for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    const float w = p.w[i];
+    if (w == 0.f) continue;   // inactive (moving window): neither pushed nor moved
     const int32_t cells = p.ixy[i];
     int ix = cell_x(cells), iy = cell_y(cells);
     float fx = p.fx[i], fy = p.fy[i], fz = p.fz[i];
@@ -901,9 +920,12 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
       atomicOr(err, kErrNumeric);
       continue;
     }
+    // window coordinate at x^n in cells (exact for the cells near the back edge)
+    int zrel = iz - wa.back_col;
+    if (zrel < 0) zrel += g.Nz;
+    const float zeta_old = (float)zrel + fz;
     float uxh = p.ux[i], uyh = p.uy[i], uzh = p.uz[i];
     float uxl = p.uxl[i], uyl = p.uyl[i], uzl = p.uzl[i];
-    const float w = p.w[i];
     float r, c, s;
     polar_f(x, y, r, c, s);
     const StencilF st = stencil_f(g, iz, fz, r);
@@ -942,15 +964,16 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
     const float ux = uxh + uxl, uy = uyh + uyl, uz = uzh + uzl;
     const float ig = rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
     const float bx = ux * ig, by = uy * ig, bz = uz * ig;   // v / c
+    const float dzc = bz * chdt_dz;                          // half move in cells
     advance_cell(ix, fx, bx * chdt_dr);
     advance_cell(iy, fy, by * chdt_dr);
-    advance_z(iz, fz, bz * chdt_dz, g.Nz);
+    advance_z(iz, fz, dzc, g.Nz);
     if (fuse)
       deposit_one_f(g, dep, invV, none, band, iz, fz, (float)ix + fx, (float)iy + fy, w, bx * c_light,
                     by * c_light, bz * c_light, false, true);
     advance_cell(ix, fx, bx * chdt_dr);
     advance_cell(iy, fy, by * chdt_dr);
-    advance_z(iz, fz, bz * chdt_dz, g.Nz);
+    advance_z(iz, fz, dzc, g.Nz);
     x = (float)ix + fx;
     y = (float)iy + fy;
     const float r1 = sqrtf(x * x + y * y);
@@ -967,6 +990,11 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
       iy = (int)ky; fy = y - ky;
       if (fx >= 1.f) { fx = 0.f; ix += 1; }
       if (fy >= 1.f) { fy = 0.f; iy += 1; }
+    }
+    if (wa.on && (zeta_old + dzc) + dzc - (wa.shift ? 1.f : 0.f) < 0.f) {
+      p.w[i] = 0.f;   // left through the back edge: inactive from now on
+      uxh = uyh = uzh = 0.f;
+      uxl = uyl = uzl = 0.f;
     }
     p.ixy[i] = pack_cells(ix, iy); p.fx[i] = fx; p.fy[i] = fy; p.fz[i] = fz; p.iz[i] = iz;
     p.ux[i] = uxh; p.uy[i] = uyh; p.uz[i] = uzh;
@@ -1032,23 +1060,32 @@ __global__ void k_p32_to_p64(const PartsF p, int64_t np, double* __restrict__ st
 
 // ------------------------------------------------------------------ a10: diagnostics
 // Particle accessors: float64 particles as stored, or FP32 particles widened to float64.
+// z is measured from z0 (the moving window's back edge, 0 without a window), mod L.
 struct Acc64 {
   Parts p;
+  double z0, L;
   __device__ void get(int64_t i, double& x, double& y, double& z, double& ux, double& uy, double& uz,
                       double& w) const {
     x = p.x[i]; y = p.y[i]; z = p.z[i]; ux = p.ux[i]; uy = p.uy[i]; uz = p.uz[i]; w = p.w[i];
+    if (z0 != 0.0) {
+      z -= z0;
+      if (z < 0.0) z += L;
+    }
   }
   __device__ int32_t id(int64_t i) const { return p.id[i]; }
 };
 struct Acc32 {
   PartsF p;
   double dz, dr;
+  int col0, Nz;   // z is measured from column col0 (the window's back column, 0 without one)
   __device__ void get(int64_t i, double& x, double& y, double& z, double& ux, double& uy, double& uz,
                       double& w) const {
     const int32_t c = p.ixy[i];
     x = ((double)cell_x(c) + (double)p.fx[i]) * dr;
     y = ((double)cell_y(c) + (double)p.fy[i]) * dr;
-    z = ((double)p.iz[i] + (double)p.fz[i]) * dz;
+    int iz = p.iz[i] - col0;
+    if (iz < 0) iz += Nz;
+    z = ((double)iz + (double)p.fz[i]) * dz;
     ux = ((double)p.ux[i] + (double)p.uxl[i]) * kC;
     uy = ((double)p.uy[i] + (double)p.uyl[i]) * kC;
     uz = ((double)p.uz[i] + (double)p.uzl[i]) * kC;
@@ -1203,6 +1240,159 @@ pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* ou
   return PIC_OK;
 }
 
+// ------------------------------------------------------------------ moving window
+// Template of the plasma, by id (ids < n_tpl): FP64 form x, y, z, w; mixed form the
+// cell-relative fields iz, fz, ixy, fx, fy and w.  Both fit in 32 bytes per particle.
+struct WinTpl {
+  double* x; double* y; double* z; double* w;
+};
+struct WinTplF {
+  int32_t* iz; float* fz; int32_t* ixy; float* fx; float* fy; float* w;
+};
+
+WinTpl win_tpl(const Sim* s) {
+  double* b = reinterpret_cast<double*>(s->win.ws + s->win.tpl);
+  const int64_t n = s->win.n_tpl;
+  return WinTpl{b, b + n, b + 2 * n, b + 3 * n};
+}
+WinTplF win_tplf(const Sim* s) {
+  char* b = s->win.ws + s->win.tpl;
+  const size_t n4 = 4 * (size_t)s->win.n_tpl;
+  return WinTplF{reinterpret_cast<int32_t*>(b), reinterpret_cast<float*>(b + n4),
+                 reinterpret_cast<int32_t*>(b + 2 * n4), reinterpret_cast<float*>(b + 3 * n4),
+                 reinterpret_cast<float*>(b + 4 * n4), reinterpret_cast<float*>(b + 5 * n4)};
+}
+
+// Reserve particle k: id id0 + k, inactive, at the centre of cell (k mod Nz, (k div Nz) mod Nr)
+// on the x axis.
+__global__ void k_win_reserve(Parts p, int64_t first, int64_t n, int32_t id0, int Nz, int Nr, double dz,
+                              double dr) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = first + k;
+    p.x[i] = ((double)((k / Nz) % Nr) + 0.5) * dr;
+    p.y[i] = 0.0;
+    p.z[i] = ((double)(k % Nz) + 0.5) * dz;
+    p.ux[i] = 0.0; p.uy[i] = 0.0; p.uz[i] = 0.0; p.w[i] = 0.0;
+    p.id[i] = id0 + (int32_t)k;
+  }
+}
+
+__global__ void k_win_reserve_f32(PartsF p, int64_t first, int64_t n, int32_t id0, int Nz, int Nr) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = first + k;
+    p.iz[i] = (int32_t)(k % Nz);
+    p.fz[i] = 0.5f;
+    p.ixy[i] = pack_cells((int)((k / Nz) % Nr), 0);
+    p.fx[i] = 0.5f;
+    p.fy[i] = 0.f;
+    p.ux[i] = 0.f; p.uy[i] = 0.f; p.uz[i] = 0.f;
+    p.uxl[i] = 0.f; p.uyl[i] = 0.f; p.uzl[i] = 0.f;
+    p.w[i] = 0.f;
+    p.id[i] = id0 + (int32_t)k;
+  }
+}
+
+// Template by id and the column of each template particle.
+__global__ void k_win_template(const Parts p, int64_t np, int64_t n_tpl, WinTpl t, int32_t* col, int Nz,
+                               double dz) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t id = p.id[i];
+    if (id < 0 || id >= n_tpl) continue;
+    const double z = p.z[i];
+    t.x[id] = p.x[i]; t.y[id] = p.y[i]; t.z[id] = z; t.w[id] = p.w[i];
+    col[id] = (int32_t)fmin(fmax(floor(z / dz), 0.0), (double)(Nz - 1));
+  }
+}
+
+__global__ void k_win_template_f32(const PartsF p, int64_t np, int64_t n_tpl, WinTplF t, int32_t* col) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t id = p.id[i];
+    if (id < 0 || id >= n_tpl) continue;
+    t.iz[id] = p.iz[i]; t.fz[id] = p.fz[i]; t.ixy[id] = p.ixy[i];
+    t.fx[id] = p.fx[i]; t.fy[id] = p.fy[i]; t.w[id] = p.w[i];
+    col[id] = p.iz[i];
+  }
+}
+
+// Injection.  flag[id] = 1 and slot[id] = array index for every inactive particle; ranks of
+// the flagged ids (increasing id) come from per-block counts (1024 ids per block), their
+// exclusive scan, and a scan inside each block.
+constexpr int kWinBlock = 1024;
+
+template <typename T>
+__global__ void k_win_mark(const T* __restrict__ w, const int32_t* __restrict__ id, int64_t np, int32_t* flag,
+                           int32_t* slot) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
+    if (w[i] == (T)0) {
+      const int32_t k = id[i];
+      flag[k] = 1;
+      slot[k] = (int32_t)i;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kWinBlock) k_win_bcount(const int32_t* flag, int64_t n, int32_t* bsum) {
+  const int64_t k = blockIdx.x * (int64_t)kWinBlock + threadIdx.x;
+  const int c = __syncthreads_count(k < n ? flag[k] : 0);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = c;
+}
+
+// One CTA: exclusive scan of nb block counts in place; bsum[nb] = number of inactive ids.
+__global__ void __launch_bounds__(kWinBlock) k_win_bscan(int32_t* bsum, int nb) {
+  int32_t carry = 0;
+  for (int base = 0; base < nb; base += kWinBlock) {
+    const int k = base + threadIdx.x;
+    const int32_t v = k < nb ? bsum[k] : 0;
+    int32_t tot;
+    const int32_t ex = block_exclusive_scan(v, &tot);
+    if (k < nb) bsum[k] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+// Rank of id k among the inactive ids (valid where the returned flag is 1).
+__device__ __forceinline__ int32_t win_rank(const int32_t* flag, const int32_t* bsum, int64_t n, int& v) {
+  const int64_t k = blockIdx.x * (int64_t)kWinBlock + threadIdx.x;
+  v = k < n ? flag[k] : 0;
+  int32_t tot;
+  return bsum[blockIdx.x] + block_exclusive_scan(v, &tot);
+}
+
+__global__ void __launch_bounds__(kWinBlock) k_win_inject(const int32_t* flag, const int32_t* slot,
+                                                           const int32_t* bsum, int64_t n, int nb, Parts p,
+                                                           WinTpl t, const int32_t* fresh, int32_t n_fresh,
+                                                           unsigned long long* dropped) {
+  int v;
+  const int32_t r = win_rank(flag, bsum, n, v);
+  if (v && r < n_fresh) {
+    const int32_t src = fresh[r];
+    const int32_t i = slot[blockIdx.x * (int64_t)kWinBlock + threadIdx.x];
+    p.x[i] = t.x[src]; p.y[i] = t.y[src]; p.z[i] = t.z[src]; p.w[i] = t.w[src];
+    p.ux[i] = 0.0; p.uy[i] = 0.0; p.uz[i] = 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && bsum[nb] < n_fresh)
+    atomicAdd(dropped, (unsigned long long)(n_fresh - bsum[nb]));
+}
+
+__global__ void __launch_bounds__(kWinBlock) k_win_inject_f32(const int32_t* flag, const int32_t* slot,
+                                                               const int32_t* bsum, int64_t n, int nb, PartsF p,
+                                                               WinTplF t, const int32_t* fresh, int32_t n_fresh,
+                                                               unsigned long long* dropped) {
+  int v;
+  const int32_t r = win_rank(flag, bsum, n, v);
+  if (v && r < n_fresh) {
+    const int32_t src = fresh[r];
+    const int32_t i = slot[blockIdx.x * (int64_t)kWinBlock + threadIdx.x];
+    p.iz[i] = t.iz[src]; p.fz[i] = t.fz[src]; p.ixy[i] = t.ixy[src];
+    p.fx[i] = t.fx[src]; p.fy[i] = t.fy[src]; p.w[i] = t.w[src];
+    p.ux[i] = 0.f; p.uy[i] = 0.f; p.uz[i] = 0.f;
+    p.uxl[i] = 0.f; p.uyl[i] = 0.f; p.uzl[i] = 0.f;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && bsum[nb] < n_fresh)
+    atomicAdd(dropped, (unsigned long long)(n_fresh - bsum[nb]));
+}
+
 }  // namespace
 
 bool is_mixed(const Sim* s) { return s->cfg.precision != PIC_FP64; }
@@ -1329,7 +1519,7 @@ pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, vo
   return PIC_OK;
 }
 
-pic_status launch_gather_push(Sim* s, int32_t fuse_current) {
+pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa) {
   const size_t G = s->grid_elems();
   int32_t* err = s->at<int32_t>(s->lay.err);
   const pic_config& c = s->cfg;
@@ -1355,7 +1545,7 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current) {
     PIC_LAUNCHED(s);
     k_gather_push_f32<<<(int)((s->np + bp.args.chunk - 1) / bp.args.chunk), kBandThreads, bp.smem, s->stream>>>(
         partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.ebt), kq, kqc,
-        chdt_dr, chdt_dz, a, reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args);
+        chdt_dr, chdt_dz, a, reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args, wa);
   } else {
     DepArgs a;
     a.q = c.q;
@@ -1367,18 +1557,19 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current) {
     if (s->np == 0) return PIC_OK;
     k_gather_push<<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, geom_of(s),
                                                         s->at<double2>(s->lay.E), s->at<double2>(s->lay.B), c.q,
-                                                        c.mass, c.dt, a, inv_volume(s), fuse_current, err);
+                                                        c.mass, c.dt, a, inv_volume(s), fuse_current, err, wa);
   }
   PIC_LAUNCHED(s);
   return PIC_OK;
 }
 
 pic_status launch_diag(Sim* s, int32_t lo, int32_t hi, pic_diag* out, double* slice_sigma, int32_t max_slices) {
+  const int col0 = s->win.on ? (int)(s->win.shifts % s->cfg.Nz) : 0;
   if (is_mixed(s)) {
-    Acc32 a{partsf_of(s, s->cur), s->cfg.dz, s->cfg.dr};
+    Acc32 a{partsf_of(s, s->cur), s->cfg.dz, s->cfg.dr, col0, s->cfg.Nz};
     return run_diag(s, a, lo, hi, out, slice_sigma, max_slices);
   }
-  Acc64 a{parts_of(s, s->cur)};
+  Acc64 a{parts_of(s, s->cur), col0 * s->cfg.dz, s->cfg.Nz * s->cfg.dz};
   return run_diag(s, a, lo, hi, out, slice_sigma, max_slices);
 }
 
@@ -1414,6 +1605,96 @@ pic_status particles_configure_device() {
   PIC_CUDA(cudaFuncSetAttribute(k_deposit_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandBudget));
   PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandBudget));
   if (dev >= 0 && dev < 64) done[dev] = true;
+  return PIC_OK;
+}
+
+// ---- moving window: particle side
+size_t window_layout(const Sim* s, int64_t n_tpl, WindowState* w) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  const pic_config& c = s->cfg;
+  const size_t cap = (size_t)std::max<int64_t>(c.np_capacity, 1);
+  const size_t rows = 6 * (size_t)c.Nm * c.Nr;
+  WindowState t;
+  t.tpl = take(32 * (size_t)std::max<int64_t>(n_tpl, 1));
+  t.colids = take(4 * (size_t)std::max<int64_t>(n_tpl, 1));
+  t.flag = take(4 * cap);
+  t.slot = take(4 * cap);
+  t.bsum = take(4 * (cap / kWinBlock + 2));
+  t.dropped = take(8);
+  t.colv = take(16 * rows);
+  t.hv = take(16 * rows);
+  t.ph = take(16 * (size_t)c.Nz);
+  if (w) {
+    w->tpl = t.tpl; w->colids = t.colids; w->flag = t.flag; w->slot = t.slot; w->bsum = t.bsum;
+    w->dropped = t.dropped; w->colv = t.colv; w->hv = t.hv; w->ph = t.ph;
+  }
+  return off;
+}
+
+pic_status launch_window_reserve(Sim* s, int64_t n_reserve) {
+  if (n_reserve <= 0) return PIC_OK;
+  const int64_t first = s->np;
+  if (is_mixed(s))
+    k_win_reserve_f32<<<pgrid(n_reserve), 256, 0, s->stream>>>(partsf_of(s, s->cur), first, n_reserve,
+                                                                (int32_t)first, s->cfg.Nz, s->cfg.Nr);
+  else
+    k_win_reserve<<<pgrid(n_reserve), 256, 0, s->stream>>>(parts_of(s, s->cur), first, n_reserve, (int32_t)first,
+                                                            s->cfg.Nz, s->cfg.Nr, s->cfg.dz, s->cfg.dr);
+  PIC_LAUNCHED(s);
+  s->np += n_reserve;
+  return PIC_OK;
+}
+
+pic_status window_take_template(Sim* s, int32_t* keys_host) {
+  const int64_t n = s->win.n_tpl;
+  if (n == 0 || s->np == 0) return PIC_OK;
+  int32_t* col = s->at<int32_t>(s->lay.perm_tmp);   // scratch, capacity >= n
+  if (is_mixed(s))
+    k_win_template_f32<<<pgrid(s->np), 256, 0, s->stream>>>(partsf_of(s, s->cur), s->np, n, win_tplf(s), col);
+  else
+    k_win_template<<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, n, win_tpl(s), col, s->cfg.Nz,
+                                                         s->cfg.dz);
+  PIC_LAUNCHED(s);
+  PIC_CUDA(cudaMemcpyAsync(keys_host, col, n * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+  PIC_CUDA(cudaStreamSynchronize(s->stream));
+  return PIC_OK;
+}
+
+pic_status launch_window_inject(Sim* s, int column) {
+  WindowState& w = s->win;
+  const int32_t c0 = w.col_start_host[column], n_fresh = w.col_start_host[column + 1] - c0;
+  if (n_fresh == 0 || w.n_ids == 0) return PIC_OK;
+  int32_t* flag = reinterpret_cast<int32_t*>(w.ws + w.flag);
+  int32_t* slot = reinterpret_cast<int32_t*>(w.ws + w.slot);
+  int32_t* bsum = reinterpret_cast<int32_t*>(w.ws + w.bsum);
+  const int32_t* fresh = reinterpret_cast<const int32_t*>(w.ws + w.colids) + c0;
+  auto* dropped = reinterpret_cast<unsigned long long*>(w.ws + w.dropped);
+  const int nb = (int)((w.n_ids + kWinBlock - 1) / kWinBlock);
+  PIC_CUDA(cudaMemsetAsync(flag, 0, w.n_ids * sizeof(int32_t), s->stream));
+  if (is_mixed(s)) {
+    const PartsF p = partsf_of(s, s->cur);
+    k_win_mark<float><<<pgrid(s->np), 256, 0, s->stream>>>(p.w, p.id, s->np, flag, slot);
+  } else {
+    const Parts p = parts_of(s, s->cur);
+    k_win_mark<double><<<pgrid(s->np), 256, 0, s->stream>>>(p.w, p.id, s->np, flag, slot);
+  }
+  PIC_LAUNCHED(s);
+  k_win_bcount<<<nb, kWinBlock, 0, s->stream>>>(flag, w.n_ids, bsum);
+  PIC_LAUNCHED(s);
+  k_win_bscan<<<1, kWinBlock, 0, s->stream>>>(bsum, nb);
+  PIC_LAUNCHED(s);
+  if (is_mixed(s))
+    k_win_inject_f32<<<nb, kWinBlock, 0, s->stream>>>(flag, slot, bsum, w.n_ids, nb, partsf_of(s, s->cur),
+                                                       win_tplf(s), fresh, n_fresh, dropped);
+  else
+    k_win_inject<<<nb, kWinBlock, 0, s->stream>>>(flag, slot, bsum, w.n_ids, nb, parts_of(s, s->cur), win_tpl(s),
+                                                   fresh, n_fresh, dropped);
+  PIC_LAUNCHED(s);
   return PIC_OK;
 }
 

@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <new>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "pic_internal.cuh"
 
@@ -319,19 +321,39 @@ pic_status field_step(Sim* s, int32_t order_p, Marks* mk = nullptr, int base = 0
   return PIC_OK;
 }
 
-// One PIC cycle; with marks, events 0..8 bracket the eight stages of pic_stage.
+// One PIC cycle; with marks, events 0..8 bracket the eight stages of pic_stage.  With the
+// moving window on, the push removes the particles that leave through the back edge and,
+// when the window moves, the departing column's plasma template is injected after the push
+// (inside the gather_push stage) and the column's fields are removed after the field step
+// (after the last mark).
 pic_status step_once(Sim* s, Marks* mk) {
   Marks none;
   Marks& m = mk ? *mk : none;
   pic_status st;
+  WinArgs wa;
+  if (s->win.on) {
+    wa.on = 1;
+    wa.shift = (s->win.cycles + 1) % s->win.period == 0;
+    wa.back_col = (int32_t)(s->win.shifts % s->cfg.Nz);
+    wa.back_z = wa.back_col * s->cfg.dz;
+  }
   PIC_CUDA(m.mark(0));
-  if ((st = launch_gather_push(s, 1)) != PIC_OK) return st;
+  if ((st = launch_gather_push(s, 1, wa)) != PIC_OK) return st;
+  if (wa.shift && (st = launch_window_inject(s, wa.back_col)) != PIC_OK) return st;
   PIC_CUDA(m.mark(1));
   if ((st = launch_sort(s)) != PIC_OK) return st;
   PIC_CUDA(m.mark(2));
   if ((st = deposit_rho_with_background(s)) != PIC_OK) return st;
   PIC_CUDA(m.mark(3));
-  return field_step(s, -1, mk, 3);   // marks 4..8
+  if ((st = field_step(s, -1, mk, 3)) != PIC_OK) return st;   // marks 4..8
+  if (s->win.on) {
+    if (wa.shift) {
+      if ((st = launch_window_clear(s, wa.back_col)) != PIC_OK) return st;
+      s->win.shifts += 1;
+    }
+    s->win.cycles += 1;
+  }
+  return PIC_OK;
 }
 
 #define CHECK_SIM(s)                                              \
@@ -603,6 +625,7 @@ pic_status pic_write_particles(pic_sim* sim, const double* const soa[7], const i
     PIC_CUDA(cudaMemcpyAsync(dst, id, n * 4, kind, s->stream));
   }
   s->np = n;
+  s->win.on = 0;   // new particles: the window's template and ids no longer apply
   if (mixed) {
     pic_status st = launch_particles_in(s, s->at<int32_t>(s->lay.perm_tmp), n);
     if (st != PIC_OK) return st;
@@ -828,6 +851,112 @@ pic_status pic_load_buffer(pic_sim* sim, int32_t buffer_id, const void* src, siz
                            src_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s->stream));
   if (src_on_host) PIC_CUDA(cudaStreamSynchronize(s->stream));
   if (buffer_id == PIC_BUF_E || buffer_id == PIC_BUF_B) s->fields_ready = 1;
+  return PIC_OK;
+}
+
+pic_status pic_window_required_bytes(pic_sim* sim, int64_t n_plasma, size_t* bytes) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (!bytes || n_plasma < 0 || n_plasma > s->cfg.np_capacity) {
+    set_error("bytes is NULL or n_plasma=%lld outside [0, capacity]", (long long)n_plasma);
+    return PIC_ERR_ARG;
+  }
+  *bytes = window_layout(s, n_plasma, nullptr);
+  return PIC_OK;
+}
+
+pic_status pic_window_setup(pic_sim* sim, int64_t n_plasma, int32_t period, int64_t n_reserve, void* workspace,
+                            size_t workspace_bytes) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (s->win.on) { set_error("the moving window is already on"); return PIC_ERR_ARG; }
+  if (period < 1) { set_error("period=%d must be >= 1", period); return PIC_ERR_ARG; }
+  if (n_plasma < 0 || n_plasma > s->np) {
+    set_error("n_plasma=%lld outside [0, %lld particles held]", (long long)n_plasma, (long long)s->np);
+    return PIC_ERR_ARG;
+  }
+  if (n_reserve < 0 || s->np + n_reserve > s->cfg.np_capacity) {
+    set_error("n_reserve=%lld: %lld + reserve exceeds the capacity %lld", (long long)n_reserve, (long long)s->np,
+              (long long)s->cfg.np_capacity);
+    return PIC_ERR_ARG;
+  }
+  WindowState w;
+  const size_t need = window_layout(s, n_plasma, &w);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < need) {
+    set_error("window workspace must be 256-byte aligned with >= %zu bytes", need);
+    return PIC_ERR_ARG;
+  }
+  // the ids held must be exactly 0 .. np-1 (slots are found by id)
+  const int64_t np = s->np;
+  std::vector<int32_t> ids, cols;
+  std::vector<char> seen;
+  try {
+    ids.resize((size_t)np);
+    seen.assign((size_t)np, 0);
+    cols.resize((size_t)n_plasma);
+  } catch (...) {
+    set_error("host allocation failed");
+    return PIC_ERR_OOM;
+  }
+  const bool mixed = s->cfg.precision != PIC_FP64;
+  const char* id_src = mixed ? s->ws + s->lay.pf[s->cur][kPfId] : s->ws + s->lay.pid[s->cur];
+  if (np > 0) {
+    PIC_CUDA(cudaMemcpyAsync(ids.data(), id_src, np * sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    PIC_CUDA(cudaStreamSynchronize(s->stream));
+  }
+  for (int64_t i = 0; i < np; ++i) {
+    const int32_t k = ids[i];
+    if (k < 0 || k >= np || seen[k]) {
+      set_error("window: particle ids must be exactly 0 .. np-1 (id %d at %lld)", k, (long long)i);
+      return PIC_ERR_ARG;
+    }
+    seen[k] = 1;
+  }
+  w.ws = reinterpret_cast<char*>(workspace);
+  w.period = period;
+  w.n_tpl = n_plasma;
+  s->win = w;
+  pic_status st = window_take_template(s, cols.data());
+  if (st != PIC_OK) return st;
+  // template ids grouped by column, increasing id within a column (counting sort)
+  const int Nz = s->cfg.Nz;
+  std::vector<int32_t> start((size_t)Nz + 1, 0), order;
+  try {
+    order.resize((size_t)std::max<int64_t>(n_plasma, 1));
+  } catch (...) {
+    set_error("host allocation failed");
+    return PIC_ERR_OOM;
+  }
+  for (int64_t k = 0; k < n_plasma; ++k) start[cols[k] + 1] += 1;
+  for (int c = 0; c < Nz; ++c) start[c + 1] += start[c];
+  std::vector<int32_t> cursor(start.begin(), start.end() - 1);
+  for (int64_t k = 0; k < n_plasma; ++k) order[cursor[cols[k]]++] = (int32_t)k;
+  if (n_plasma > 0)
+    PIC_CUDA(cudaMemcpy(s->win.ws + s->win.colids, order.data(), n_plasma * sizeof(int32_t), cudaMemcpyHostToDevice));
+  PIC_CUDA(cudaMemsetAsync(s->win.ws + s->win.dropped, 0, 8, s->stream));
+  if ((st = launch_window_reserve(s, n_reserve)) != PIC_OK) return st;
+  s->win.col_start_host = std::move(start);
+  s->win.n_ids = s->np;
+  s->win.cycles = 0;
+  s->win.shifts = 0;
+  s->win.on = 1;
+  return pic_sync(sim);
+}
+
+pic_status pic_window_state(pic_sim* sim, pic_window_info* out) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (!s->win.on) { set_error("the moving window is not set up"); return PIC_ERR_STATE; }
+  if (!out) { set_error("out is NULL"); return PIC_ERR_ARG; }
+  unsigned long long dropped = 0;
+  PIC_CUDA(cudaMemcpyAsync(&dropped, s->win.ws + s->win.dropped, 8, cudaMemcpyDeviceToHost, s->stream));
+  PIC_CUDA(cudaStreamSynchronize(s->stream));
+  out->cycles = s->win.cycles;
+  out->shifts = s->win.shifts;
+  out->back_column = (int32_t)(s->win.shifts % s->cfg.Nz);
+  out->period = s->win.period;
+  out->dropped = (int64_t)dropped;
+  out->n_template = s->win.n_tpl;
   return PIC_OK;
 }
 

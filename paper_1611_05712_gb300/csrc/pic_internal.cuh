@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/psatd_rz.h"
 
 namespace pic {
@@ -61,6 +63,25 @@ enum {
   kPfCount
 };
 
+// Push arguments of the moving window (pic_window_setup): with on = 1 the push removes
+// the particles that end behind the back edge; shift = 1 when the window moves at the end
+// of this cycle.
+struct WinArgs {
+  int32_t on = 0, shift = 0, back_col = 0;
+  double back_z = 0.0;   // back_col * dz
+};
+
+// Moving-window state of a handle; offsets are bytes into the caller's window workspace.
+struct WindowState {
+  int32_t on = 0, period = 1;
+  int64_t cycles = 0, shifts = 0;
+  int64_t n_tpl = 0;       // template particles (ids < n_tpl)
+  int64_t n_ids = 0;       // ids 0 .. n_ids-1 held (particles plus reserve)
+  char* ws = nullptr;
+  size_t tpl, colids, flag, slot, bsum, dropped, colv, hv, ph;
+  std::vector<int32_t> col_start_host;   // [Nz + 1] template offsets per column
+};
+
 struct Sim {
   pic_config cfg;
   Layout lay;
@@ -82,6 +103,7 @@ struct Sim {
   struct alignas(64) TensorMapBytes {
     unsigned char b[128];
   } tmaps[2 * kMaxModes * 3][3];
+  WindowState win;
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   size_t grid_elems() const { return (size_t)cfg.Nm * cfg.Nr * cfg.Nz; }
@@ -158,12 +180,25 @@ pic_status launch_copy_window(Sim* dst_sim, const char* src, int src_nz, int src
 // ---- launchers (particles.cu) ----
 pic_status launch_sort(Sim* s);
 pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, void* rho_out);
-pic_status launch_gather_push(Sim* s, int32_t fuse_current);
+pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa = WinArgs{});
 pic_status launch_diag(Sim* s, int32_t id_lo, int32_t id_hi, pic_diag* out, double* slice_sigma,
                        int32_t max_slices);
 pic_status build_inv_volume(Sim* s);                        // once, at init
 pic_status particles_configure_device();                    // once per device
 pic_status launch_particles_in(Sim* s, const int32_t* id_dev, int64_t n);   // mixed: stage64 -> FP32
 pic_status launch_particles_out(Sim* s, int32_t* id_dev, int64_t n);        // mixed: FP32 -> stage64
+
+// ---- moving window (particles.cu: particle side; window.cu: field side) ----
+// Byte offsets of the window workspace for a template of n_tpl particles.
+size_t window_layout(const Sim* s, int64_t n_tpl, WindowState* w);
+// Append n_reserve inactive particles (ids np ..); np grows by n_reserve.
+pic_status launch_window_reserve(Sim* s, int64_t n_reserve);
+// Template of the particles with id < n_tpl (by id) into the window workspace; keys_host
+// receives the column of each template particle.  Synchronises.
+pic_status window_take_template(Sim* s, int32_t* keys_host);
+// Template of column `column` into the inactive particles, smallest id first.
+pic_status launch_window_inject(Sim* s, int column);
+// Departing column removed from E, B (real space zeroed, its transform subtracted from Eh, Bh).
+pic_status launch_window_clear(Sim* s, int column);
 
 }  // namespace pic
