@@ -49,12 +49,15 @@ def parse():
     ap.add_argument("--accuracy-cycles", type=int, default=100,
                     help="cycles after which the mixed form's fields and beam quality are "
                          "compared with the FP64 form (0: skip)")
-    ap.add_argument("--workload", choices=["wake", "scan", "large", "guard", "order_sweep"], default="wake",
+    ap.add_argument("--workload", choices=["wake", "scan", "large", "guard", "order_sweep", "window"],
+                    default="wake",
                     help="wake: the 2048x256 wakefield run; scan: many uneven simulations "
                          "(order / resolution scan) advanced by one CUDA graph per launch; "
                          "large: the 8192x1024 3-mode run with ~103M particles, mixed form")
     ap.add_argument("--sims", type=int, default=64, help="simulations in the scan workload")
     ap.add_argument("--sweep-steps", type=int, default=2000, help="cycles per order in the order sweep")
+    ap.add_argument("--window-cycles", type=int, default=8192,
+                    help="cycles of the moving-window propagation after the timed cycles")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket each timed region with cudaProfilerStart/Stop (for "
                          "ncu --profile-from-start off); no work is skipped")
@@ -601,6 +604,105 @@ def run_order_sweep(args):
     return 0
 
 
+def run_window(args):
+    """The wakefield run (2048 x 256, 2 modes, p = 32) in a window moving at c, one cell per
+    cycle: cycles/s with and without the window from the same initial state (the window's
+    cost), then args.window_cycles further cycles checking that the beams keep their window
+    coordinates and that removal and injection keep the plasma balanced."""
+    import torch
+
+    from paper_1611_05712_gb300 import binding as bd
+    from paper_1611_05712_gb300 import workloads as W
+    from paper_1611_05712_gb300.build import build
+    build()
+    prec = {"fp64": bd.PIC_FP64, "mixed": bd.PIC_MIXED_TF32X3, "bf16": bd.PIC_MIXED_BF16X6}[args.precision]
+    mixed = prec != bd.PIC_FP64
+    w = workload(args.order)
+    P, npl, beams = W.particles(w)
+    n = len(P["x"])
+    # inside the wake the plasma electrons move forward and stay longer in the window, so the
+    # window holds more plasma than it was loaded with until the wake fills it: keep a
+    # quarter of the plasma in reserve
+    reserve = npl // 4
+
+    def timed(sim, k):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(sim.stream)
+        sim.step(k)
+        e1.record(sim.stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def make():
+        sim = bd.Sim.from_workload(w, P, npl, beams, precision=prec, capacity=n + reserve)
+        if mixed:
+            sim.autotune()
+        return sim
+
+    s = make()
+    s.step(args.warmup)
+    ms_plain = timed(s, args.steps)
+    s.close()
+
+    s = make()
+    s.window_setup(npl, 1, reserve)
+    d0 = [s.diagnostics(lo, hi) for lo, hi, _ in beams]
+    s.step(args.warmup)
+    l0 = s.launch_count()
+    with ClockSampler(0) as clk:
+        ms_win = timed(s, args.steps)
+    launches = s.launch_count() - l0
+    wall = 0.0
+    samples = []
+    done = 0
+    while done < args.window_cycles:
+        k = min(1024, args.window_cycles - done)
+        t0 = time.perf_counter()
+        s.step(k)
+        s.sync()
+        wall += time.perf_counter() - t0
+        done += k
+        pk = s.read_particles()   # untimed: active plasma count along the propagation
+        act = pk["w"] != 0
+        samples.append([done, int((act & ((pk["id"] < npl) | (pk["id"] >= n))).sum()),
+                        s.window_state()["dropped"]])
+    info = s.window_state()
+    d1 = [s.diagnostics(lo, hi) for lo, hi, _ in beams]
+    parts = s.read_particles()
+    active = parts["w"] != 0
+    plasma_active = int((active & (parts["id"] < npl)).sum()) + int((active & (parts["id"] >= n)).sum())
+    beams_out = {}
+    for (lo, hi, gam), a, b in zip(beams, d0, d1):
+        beams_out[f"gamma_{gam:g}"] = {
+            "z_window_start_um": a["z_mean"] * 1e6, "z_window_end_um": b["z_mean"] * 1e6,
+            "gamma_mean_start": a["gamma_mean"], "gamma_mean_end": b["gamma_mean"],
+            "emit_nx_start": a["emit_nx"], "emit_nx_end": b["emit_nx"],
+            "particles_active": int((active & (parts["id"] >= lo) & (parts["id"] < hi)).sum()), "particles": hi - lo}
+    cfg = config_of(w, n, args.precision)
+    cfg.update({"window": "moves one cell per cycle (c dt = dz)", "reserve": reserve,
+                "propagation_cycles": args.window_cycles,
+                "propagation_um": args.window_cycles * w.dz * 1e6})
+    steps_win = args.steps / (ms_win * 1e-3)
+    print(json.dumps({
+        "metric": "pic_steps_per_s_moving_window", "value": steps_win, "unit": "steps/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_win / args.steps,
+        "ms_per_step_without_window": ms_plain / args.steps,
+        "window_overhead_ms_per_step": (ms_win - ms_plain) / args.steps,
+        "higher_is_better": True, "dtype": {bd.PIC_FP64: "f64", bd.PIC_MIXED_TF32X3: "f32+tf32x3",
+                                            bd.PIC_MIXED_BF16X6: "f32+bf16x6"}[prec],
+        "data": "synthetic", "config": cfg, "gpu_launches": launches, "clocks": clk.summary(),
+        "propagation": {"wall_s": wall, "cycles_per_s": args.window_cycles / wall,
+                        "shifts": info["shifts"], "dropped": info["dropped"],
+                        "plasma_active_start": npl, "plasma_active_end": plasma_active,
+                        "plasma_active_samples": {"columns": ["cycles", "active_plasma", "dropped"],
+                                                  "rows": samples},
+                        "beams": beams_out}}), flush=True)
+    s.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -613,6 +715,8 @@ def main():
         return run_guard(args)
     if args.workload == "order_sweep":
         return run_order_sweep(args)
+    if args.workload == "window":
+        return run_window(args)
     return run_ours(args)
 
 

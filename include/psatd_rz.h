@@ -110,7 +110,7 @@ typedef enum {
   PIC_BUF_HANKEL_INV = 9, /* B_p[j][n] = J_p(k_{m,n} r_j), [Nm][3 (p=m-1,m,m+1)][Nr][Nr]  */
   PIC_BUF_HANKEL_FWD = 10,/* pseudo-inverses M_p[n][j], same shape                      */
   PIC_BUF_KZ_MOD = 11,    /* [k_z]_p per FFT bin [Nz] float64                           */
-  PIC_BUF_KEYS = 12,      /* int32 cell keys iz*Nr+ir of the last sort [np]             */
+  PIC_BUF_KEYS = 12,      /* int32 cell keys iz*Nr+ir of the last sort [np] (>=Nz*Nr: w=0) */
   PIC_BUF_PERM = 13,      /* int32 stable sort permutation of the last sort [np]        */
   PIC_BUF_COUNT_ = 14
 } pic_buffer_id;
@@ -172,7 +172,9 @@ pic_status pic_init_fields(pic_sim* sim);
 /* ---- the PIC cycle ------------------------------------------------------------ */
 
 /* a1: cell keys iz*Nr+ir (iz = floor(z/dz), ir = floor(sqrt(x*x+y*y)/dr), clamped) and a
- * stable counting sort of every particle array by key (ties keep the input order). */
+ * stable counting sort of every particle array by key (ties keep the input order).
+ * Inactive particles (w = 0; see the moving window) take keys from Nz*Nr up and end up, in
+ * no particular order, after all active ones. */
 pic_status pic_sort(pic_sim* sim);
 
 /* a4 at the current positions (no move): what = PIC_DEP_RHO and/or PIC_DEP_J.

@@ -105,10 +105,37 @@ __device__ __forceinline__ double2 interp(const double2* grid, const GridGeom& g
 }
 
 // ------------------------------------------------------------------ a1: keys and sort
+// Inactive particles (w = 0, moving window) take keys past the cells, Nz*Nr + ((i / 32) mod
+// kTailBins): the sort gathers them at the end of the arrays, where whole chunks of them
+// cost the band kernels nothing.  The 32 particles of one aligned group share a sub-bin, so
+// each warp counts and places its inactive particles with one atomic (and the atomics of
+// many warps spread over kTailBins addresses).
+constexpr int kTailBins = 64;
+
+__device__ __forceinline__ int tail_key(int ncell, int64_t i) { return ncell + (int)((i >> 5) & (kTailBins - 1)); }
+
+// Warp-aggregated count of the inactive lanes of this iteration (all share one sub-bin).
+__device__ __forceinline__ void count_inactive(int32_t* count, int key, bool inactive) {
+  const unsigned am = __activemask();
+  const unsigned m = __ballot_sync(am, inactive);
+  if (inactive && (threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(count + key, __popc(m));
+}
+
+// WIN (moving window on): inactive particles take the tail keys.
+template <bool WIN>
 __global__ void k_keys(const Parts p, int64_t np, GridGeom g, int32_t* keys, int32_t* count,
                        int32_t* err) {
+  const int ncell = g.Nz * g.Nr;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if (WIN) {
+      const bool inactive = p.w[i] == 0.0;
+      count_inactive(count, tail_key(ncell, i), inactive);
+      if (inactive) {
+        keys[i] = tail_key(ncell, i);
+        continue;
+      }
+    }
     double x = p.x[i], y = p.y[i], z = p.z[i];
     double r = sqrt(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
     double fz = floor(z / g.dz), fr = floor(r / g.dr);
@@ -195,10 +222,31 @@ __global__ void k_scan_add(int32_t* start, const int32_t* blk, int n, int32_t* c
   }
 }
 
-__global__ void k_scatter(const int32_t* keys, int64_t np, int32_t* cursor, int32_t* tmp) {
+// Counting-sort scatter; the inactive lanes of a warp iteration (one sub-bin, see tail_key)
+// take their places with one atomic.
+template <bool WIN>
+__global__ void k_scatter(const int32_t* keys, int64_t np, int32_t* cursor, int32_t* tmp, int32_t ncell) {
+  const int lane = threadIdx.x & 31;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
-    int32_t pos = atomicAdd(cursor + keys[i], 1);
+    const int32_t key = keys[i];
+    if (!WIN) {
+      tmp[atomicAdd(cursor + key, 1)] = (int32_t)i;
+      continue;
+    }
+    const bool t = key >= ncell;
+    const unsigned am = __activemask();
+    const unsigned m = __ballot_sync(am, t);
+    int32_t pos;
+    if (t) {
+      const int leader = __ffs(m) - 1;
+      int32_t b = 0;
+      if (lane == leader) b = atomicAdd(cursor + key, __popc(m));
+      b = __shfl_sync(m, b, leader);
+      pos = b + __popc(m & ((1u << lane) - 1u));
+    } else {
+      pos = atomicAdd(cursor + key, 1);
+    }
     tmp[pos] = (int32_t)i;
   }
 }
@@ -228,8 +276,14 @@ __global__ void k_cell_sort_small(const int32_t* start, const int32_t* tmp, int3
   }
 }
 
+// With tail = 1 the inactive sub-bins past the ncell cells are copied over as they are
+// (nothing depends on the order of inactive particles).
 __global__ void k_cell_sort_big(const int32_t* start, const int32_t* tmp, int32_t* perm,
-                                const int32_t* big_list, const int32_t* big_count) {
+                                const int32_t* big_list, const int32_t* big_count, int ncell, int tail) {
+  if (tail) {
+    const int32_t b = start[ncell], e = start[ncell + kTailBins];
+    for (int32_t i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) perm[i] = tmp[i];
+  }
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
@@ -246,13 +300,19 @@ __global__ void k_cell_sort_big(const int32_t* start, const int32_t* tmp, int32_
   }
 }
 
-__global__ void k_permute(const Parts src, Parts dst, const int32_t* perm, int64_t np) {
+// dst[i] = src[perm[i]]; with a moving window (slot non-null) the array index of every
+// inactive particle is recorded by id for the next injection.
+template <bool WIN>
+__global__ void k_permute(const Parts src, Parts dst, const int32_t* perm, int64_t np, int32_t* slot) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int32_t k = perm[i];
+    const double w = src.w[k];
+    const int32_t id = src.id[k];
     dst.x[i] = src.x[k]; dst.y[i] = src.y[k]; dst.z[i] = src.z[k];
     dst.ux[i] = src.ux[k]; dst.uy[i] = src.uy[k]; dst.uz[i] = src.uz[k];
-    dst.w[i] = src.w[k]; dst.id[i] = src.id[k];
+    dst.w[i] = w; dst.id[i] = id;
+    if (WIN && w == 0.0) slot[id] = (int32_t)i;
   }
 }
 
@@ -325,6 +385,17 @@ __global__ void k_inv_volume(double* invV, int Nr, double dr, double dz) {
 }
 
 // ------------------------------------------------------------------ a2 + a3 (+ a4 J)
+// Moving window: record a particle that became inactive (flag and slot by id, count per block
+// of 1024 ids).  The records persist: the permute keeps the slots of inactive particles
+// current and the injection clears the records it uses.
+__device__ __forceinline__ void win_mark(const WinArgs& wa, int32_t id, int64_t i) {
+  wa.flag[id] = 1;
+  wa.slot[id] = (int32_t)i;
+  atomicAdd(wa.bcnt + (id >> 10), 1);
+}
+
+// WIN: moving window on (removal behind the back edge); the plain instance has none of it.
+template <bool WIN>
 __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __restrict__ E,
                               const double2* __restrict__ B, double q, double mass, double dt,
                               DepArgs dep, const double* invV, int fuse, int32_t* err, WinArgs wa) {
@@ -393,7 +464,7 @@ __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __
       x *= fr;
       y *= fr;
     }
-    if (wa.on) {
+    if (WIN) {
       // window coordinate after the step: ((z^n - back) mod L) + 2 half moves - s dz
       double zo = z_old - wa.back_z;
       if (zo < 0.0) zo += g.L;
@@ -402,6 +473,7 @@ __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __
       if (zn < 0.0) {   // left through the back edge: inactive from now on
         p.w[i] = 0.0;
         ux = 0.0; uy = 0.0; uz = 0.0;
+        win_mark(wa, p.id[i], i);
       }
     }
     p.x[i] = x; p.y[i] = y; p.z[i] = z;
@@ -762,9 +834,19 @@ __global__ void k_inv_volume_f(float* invV, int Nr, double dr, double dz) {
   if (j < Nr) invV[j] = (float)(1.0 / (2.0 * kPi * ((j + 0.5) * dr) * dr * dz));
 }
 
+template <bool WIN>
 __global__ void k_keys_f32(const PartsF p, int64_t np, GeomF g, int32_t* keys, int32_t* count, int32_t* err) {
+  const int ncell = g.Nz * g.Nr;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if (WIN) {
+      const bool inactive = p.w[i] == 0.f;
+      count_inactive(count, tail_key(ncell, i), inactive);
+      if (inactive) {
+        keys[i] = tail_key(ncell, i);
+        continue;
+      }
+    }
     float x, y;
     pos_cells(p, i, x, y);
     const float r = sqrtf(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)));
@@ -784,7 +866,9 @@ __global__ void k_keys_f32(const PartsF p, int64_t np, GeomF g, int32_t* keys, i
 
 // dst[i] = src[perm[i]] for the 13 arrays; four particles per thread, all loads issued
 // before the stores (the gathered reads are latency-bound).
-__global__ void k_permute_f32(const PartsF src, PartsF dst, const int32_t* __restrict__ perm, int64_t np) {
+template <bool WIN>
+__global__ void k_permute_f32(const PartsF src, PartsF dst, const int32_t* __restrict__ perm, int64_t np,
+                              int32_t* slot) {
   constexpr int U = 4;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < np; i0 += U * stride) {
@@ -815,6 +899,7 @@ __global__ void k_permute_f32(const PartsF src, PartsF dst, const int32_t* __res
       dst.ux[i] = ux[u]; dst.uy[i] = uy[u]; dst.uz[i] = uz[u];
       dst.uxl[i] = uxl[u]; dst.uyl[i] = uyl[u]; dst.uzl[i] = uzl[u];
       dst.w[i] = w[u]; dst.id[i] = id[u];
+      if (WIN && w[u] == 0.f) slot[id[u]] = (int32_t)i;   // moving window: inactive slot by id
     }
   }
 }
@@ -840,8 +925,10 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_deposit_f32(const PartsF p,
   BandF band{nullptr, 0, 0, 0, 0, 1.f, 0, 0, 1};
   if (ba.tz > 0 && do_rho != do_J) {
     const ChunkStats cs = chunk_stats(p, g, b0, b1, &stats_slot, err);
-    band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, do_rho ? 1 : 3,
-                     fabsf(a.q) * __uint_as_float(cs.wmax_bits) * (do_J ? c : 1.f), cs, ba.jw_max, ba.jmargin, ba.lg_chunk);
+    if (cs.wmax_bits != 0u)   // a chunk of inactive particles deposits nothing: no band
+      band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, do_rho ? 1 : 3,
+                       fabsf(a.q) * __uint_as_float(cs.wmax_bits) * (do_J ? c : 1.f), cs, ba.jw_max, ba.jmargin,
+                       ba.lg_chunk);
   }
   band_zero(band);
   const BandF bR = do_rho ? band : none, bJ = do_J ? band : none;   // copies: no address taken
@@ -887,6 +974,7 @@ __device__ __forceinline__ void advance_z(int& iz, float& fz, float dfz, int Nz)
 // One CTA per chunk of `chunk` consecutive (cell-sorted) particles; with tz > 0 the fused J
 // deposit accumulates into a band of tz z-rows from one row below the chunk's first cell
 // (a half step moves a particle by at most half a cell at c dt <= dz).
+template <bool WIN>
 __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, int64_t np, GeomF g,
                                   const float2* __restrict__ EBt, float kq, float kqc, float chdt_dr,
                                   float chdt_dz, DepArgsF dep, const float* invV, int fuse, int32_t* err,
@@ -903,8 +991,10 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
   BandF band{nullptr, 0, 0, 0, 0, 1.f, 0, 0, 1};
   if (fuse && ba.tz > 0) {
     const ChunkStats cs = chunk_stats(p, g, b0, b1, &stats_slot, err);
-    band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, 3,
-                     fabsf(dep.q) * __uint_as_float(cs.wmax_bits) * c_light, cs, ba.jw_max, ba.jmargin, ba.lg_chunk);
+    if (cs.wmax_bits != 0u)   // a chunk of inactive particles deposits nothing: no band
+      band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, 3,
+                       fabsf(dep.q) * __uint_as_float(cs.wmax_bits) * c_light, cs, ba.jw_max, ba.jmargin,
+                       ba.lg_chunk);
   }
   band_zero(band);
   __syncthreads();
@@ -921,9 +1011,12 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
       continue;
     }
     // window coordinate at x^n in cells (exact for the cells near the back edge)
-    int zrel = iz - wa.back_col;
-    if (zrel < 0) zrel += g.Nz;
-    const float zeta_old = (float)zrel + fz;
+    float zeta_old = 0.f;
+    if (WIN) {
+      int zrel = iz - wa.back_col;
+      if (zrel < 0) zrel += g.Nz;
+      zeta_old = (float)zrel + fz;
+    }
     float uxh = p.ux[i], uyh = p.uy[i], uzh = p.uz[i];
     float uxl = p.uxl[i], uyl = p.uyl[i], uzl = p.uzl[i];
     float r, c, s;
@@ -991,10 +1084,11 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
       if (fx >= 1.f) { fx = 0.f; ix += 1; }
       if (fy >= 1.f) { fy = 0.f; iy += 1; }
     }
-    if (wa.on && (zeta_old + dzc) + dzc - (wa.shift ? 1.f : 0.f) < 0.f) {
+    if (WIN && (zeta_old + dzc) + dzc - (wa.shift ? 1.f : 0.f) < 0.f) {
       p.w[i] = 0.f;   // left through the back edge: inactive from now on
       uxh = uyh = uzh = 0.f;
       uxl = uyl = uzl = 0.f;
+      win_mark(wa, p.id[i], i);
     }
     p.ixy[i] = pack_cells(ix, iy); p.fx[i] = fx; p.fy[i] = fy; p.fz[i] = fz; p.iz[i] = iz;
     p.ux[i] = uxh; p.uy[i] = uyh; p.uz[i] = uzh;
@@ -1314,73 +1408,80 @@ __global__ void k_win_template_f32(const PartsF p, int64_t np, int64_t n_tpl, Wi
   }
 }
 
-// Injection.  flag[id] = 1 and slot[id] = array index for every inactive particle; ranks of
-// the flagged ids (increasing id) come from per-block counts (1024 ids per block), their
-// exclusive scan, and a scan inside each block.
+// Injection.  Every inactive particle has flag[id] = 1, slot[id] = its array index and is
+// counted in bcnt[id / 1024] (set at set-up and at removal, slots kept current by the
+// permute); the ranks of the flagged ids (increasing id) come from the exclusive scan of the
+// counts and a scan inside each block.  Injected ids leave the records.
 constexpr int kWinBlock = 1024;
 
+// Every inactive particle recorded (window set-up).
 template <typename T>
-__global__ void k_win_mark(const T* __restrict__ w, const int32_t* __restrict__ id, int64_t np, int32_t* flag,
-                           int32_t* slot) {
+__global__ void k_win_mark_all(const T* __restrict__ w, const int32_t* __restrict__ id, int64_t np, int32_t* flag,
+                               int32_t* slot, int32_t* bcnt) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np; i += (int64_t)gridDim.x * blockDim.x) {
     if (w[i] == (T)0) {
       const int32_t k = id[i];
       flag[k] = 1;
       slot[k] = (int32_t)i;
+      atomicAdd(bcnt + (k >> 10), 1);
     }
   }
 }
 
-__global__ void __launch_bounds__(kWinBlock) k_win_bcount(const int32_t* flag, int64_t n, int32_t* bsum) {
-  const int64_t k = blockIdx.x * (int64_t)kWinBlock + threadIdx.x;
-  const int c = __syncthreads_count(k < n ? flag[k] : 0);
-  if (threadIdx.x == 0) bsum[blockIdx.x] = c;
-}
-
-// One CTA: exclusive scan of nb block counts in place; bsum[nb] = number of inactive ids.
-__global__ void __launch_bounds__(kWinBlock) k_win_bscan(int32_t* bsum, int nb) {
+// One CTA: bstart = exclusive scan of the nb block counts, bstart[nb] = inactive ids in all;
+// template particles without a slot are counted as dropped.
+__global__ void __launch_bounds__(kWinBlock) k_win_bscan(const int32_t* bcnt, int32_t* bstart, int nb,
+                                                          int32_t n_fresh, unsigned long long* dropped) {
   int32_t carry = 0;
   for (int base = 0; base < nb; base += kWinBlock) {
     const int k = base + threadIdx.x;
-    const int32_t v = k < nb ? bsum[k] : 0;
+    const int32_t v = k < nb ? bcnt[k] : 0;
     int32_t tot;
     const int32_t ex = block_exclusive_scan(v, &tot);
-    if (k < nb) bsum[k] = carry + ex;
+    if (k < nb) bstart[k] = carry + ex;
     carry += tot;
   }
-  if (threadIdx.x == 0) bsum[nb] = carry;
+  if (threadIdx.x == 0) {
+    bstart[nb] = carry;
+    if (carry < n_fresh) atomicAdd(dropped, (unsigned long long)(n_fresh - carry));
+  }
 }
 
-// Rank of id k among the inactive ids (valid where the returned flag is 1).
-__device__ __forceinline__ int32_t win_rank(const int32_t* flag, const int32_t* bsum, int64_t n, int& v) {
+// Rank of id k among the inactive ids (valid where v = 1).  An id that receives a template
+// particle (rank < n_fresh) leaves the records.
+__device__ __forceinline__ int32_t win_rank(int32_t* flag, int32_t* bcnt, const int32_t* bstart, int64_t n,
+                                            int32_t n_fresh, int& v) {
   const int64_t k = blockIdx.x * (int64_t)kWinBlock + threadIdx.x;
   v = k < n ? flag[k] : 0;
   int32_t tot;
-  return bsum[blockIdx.x] + block_exclusive_scan(v, &tot);
+  const int32_t r = bstart[blockIdx.x] + block_exclusive_scan(v, &tot);
+  if (v && r < n_fresh) {
+    flag[k] = 0;
+    atomicSub(bcnt + blockIdx.x, 1);
+  }
+  return r;
 }
 
-__global__ void __launch_bounds__(kWinBlock) k_win_inject(const int32_t* flag, const int32_t* slot,
-                                                           const int32_t* bsum, int64_t n, int nb, Parts p,
-                                                           WinTpl t, const int32_t* fresh, int32_t n_fresh,
-                                                           unsigned long long* dropped) {
+__global__ void __launch_bounds__(kWinBlock) k_win_inject(int32_t* flag, int32_t* bcnt, const int32_t* slot,
+                                                           const int32_t* bstart, int64_t n, Parts p, WinTpl t,
+                                                           const int32_t* fresh, int32_t n_fresh) {
+  if (bstart[blockIdx.x] >= n_fresh || bstart[blockIdx.x + 1] == bstart[blockIdx.x]) return;   // no slot used
   int v;
-  const int32_t r = win_rank(flag, bsum, n, v);
+  const int32_t r = win_rank(flag, bcnt, bstart, n, n_fresh, v);
   if (v && r < n_fresh) {
     const int32_t src = fresh[r];
     const int32_t i = slot[blockIdx.x * (int64_t)kWinBlock + threadIdx.x];
     p.x[i] = t.x[src]; p.y[i] = t.y[src]; p.z[i] = t.z[src]; p.w[i] = t.w[src];
     p.ux[i] = 0.0; p.uy[i] = 0.0; p.uz[i] = 0.0;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && bsum[nb] < n_fresh)
-    atomicAdd(dropped, (unsigned long long)(n_fresh - bsum[nb]));
 }
 
-__global__ void __launch_bounds__(kWinBlock) k_win_inject_f32(const int32_t* flag, const int32_t* slot,
-                                                               const int32_t* bsum, int64_t n, int nb, PartsF p,
-                                                               WinTplF t, const int32_t* fresh, int32_t n_fresh,
-                                                               unsigned long long* dropped) {
+__global__ void __launch_bounds__(kWinBlock) k_win_inject_f32(int32_t* flag, int32_t* bcnt, const int32_t* slot,
+                                                               const int32_t* bstart, int64_t n, PartsF p, WinTplF t,
+                                                               const int32_t* fresh, int32_t n_fresh) {
+  if (bstart[blockIdx.x] >= n_fresh || bstart[blockIdx.x + 1] == bstart[blockIdx.x]) return;   // no slot used
   int v;
-  const int32_t r = win_rank(flag, bsum, n, v);
+  const int32_t r = win_rank(flag, bcnt, bstart, n, n_fresh, v);
   if (v && r < n_fresh) {
     const int32_t src = fresh[r];
     const int32_t i = slot[blockIdx.x * (int64_t)kWinBlock + threadIdx.x];
@@ -1389,8 +1490,6 @@ __global__ void __launch_bounds__(kWinBlock) k_win_inject_f32(const int32_t* fla
     p.ux[i] = 0.f; p.uy[i] = 0.f; p.uz[i] = 0.f;
     p.uxl[i] = 0.f; p.uyl[i] = 0.f; p.uzl[i] = 0.f;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0 && bsum[nb] < n_fresh)
-    atomicAdd(dropped, (unsigned long long)(n_fresh - bsum[nb]));
 }
 
 }  // namespace
@@ -1444,31 +1543,51 @@ pic_status launch_sort(Sim* s) {
   int32_t* big_count = s->at<int32_t>(s->lay.big_count);
   int32_t* err = s->at<int32_t>(s->lay.err);
   int32_t* cursor = reinterpret_cast<int32_t*>(s->at<char>(s->lay.scan_blk) + 4 * 4096 * sizeof(int32_t));
-  PIC_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * (ncell + 1), s->stream));
+  int32_t* slot = s->win.on ? reinterpret_cast<int32_t*>(s->win.ws + s->win.slot) : nullptr;
+  PIC_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * (ncell + kTailBins + 1), s->stream));   // cells + inactive
   PIC_CUDA(cudaMemsetAsync(big_count, 0, sizeof(int32_t), s->stream));
   if (np == 0) return PIC_OK;
-  if (is_mixed(s))
-    k_keys_f32<<<pgrid(np), 256, 0, s->stream>>>(partsf_of(s, s->cur), np, geomf_of(s), keys, count, err);
+  const bool win = slot != nullptr;
+  if (is_mixed(s)) {
+    if (win)
+      k_keys_f32<true><<<pgrid(np), 256, 0, s->stream>>>(partsf_of(s, s->cur), np, geomf_of(s), keys, count, err);
+    else
+      k_keys_f32<false><<<pgrid(np), 256, 0, s->stream>>>(partsf_of(s, s->cur), np, geomf_of(s), keys, count, err);
+  } else {
+    if (win)
+      k_keys<true><<<pgrid(np), 256, 0, s->stream>>>(parts_of(s, s->cur), np, geom_of(s), keys, count, err);
+    else
+      k_keys<false><<<pgrid(np), 256, 0, s->stream>>>(parts_of(s, s->cur), np, geom_of(s), keys, count, err);
+  }
+  PIC_LAUNCHED(s);
+  const int nbin = ncell + kTailBins;
+  const int nblk = (nbin + kScanBlock - 1) / kScanBlock;
+  k_scan_local<<<nblk, kScanThreads, 0, s->stream>>>(count, start, blk, nbin);
+  PIC_LAUNCHED(s);
+  k_scan_blocks<<<1, kScanThreads, 0, s->stream>>>(blk, nblk, start, nbin);
+  PIC_LAUNCHED(s);
+  k_scan_add<<<pgrid(nbin), 256, 0, s->stream>>>(start, blk, nbin, cursor);
+  PIC_LAUNCHED(s);
+  if (win)
+    k_scatter<true><<<pgrid(np), 256, 0, s->stream>>>(keys, np, cursor, tmp, ncell);
   else
-    k_keys<<<pgrid(np), 256, 0, s->stream>>>(parts_of(s, s->cur), np, geom_of(s), keys, count, err);
-  PIC_LAUNCHED(s);
-  const int nblk = (ncell + kScanBlock - 1) / kScanBlock;
-  k_scan_local<<<nblk, kScanThreads, 0, s->stream>>>(count, start, blk, ncell);
-  PIC_LAUNCHED(s);
-  k_scan_blocks<<<1, kScanThreads, 0, s->stream>>>(blk, nblk, start, ncell);
-  PIC_LAUNCHED(s);
-  k_scan_add<<<pgrid(ncell), 256, 0, s->stream>>>(start, blk, ncell, cursor);
-  PIC_LAUNCHED(s);
-  k_scatter<<<pgrid(np), 256, 0, s->stream>>>(keys, np, cursor, tmp);
+    k_scatter<false><<<pgrid(np), 256, 0, s->stream>>>(keys, np, cursor, tmp, ncell);
   PIC_LAUNCHED(s);
   k_cell_sort_small<<<pgrid(ncell), 256, 0, s->stream>>>(start, tmp, perm, ncell, big_list, big_count);
   PIC_LAUNCHED(s);
-  k_cell_sort_big<<<152 * 4, 256, 0, s->stream>>>(start, tmp, perm, big_list, big_count);
+  k_cell_sort_big<<<152 * 4, 256, 0, s->stream>>>(start, tmp, perm, big_list, big_count, ncell, win ? 1 : 0);
   PIC_LAUNCHED(s);
   if (is_mixed(s))
-    k_permute_f32<<<pgrid(np), 256, 0, s->stream>>>(partsf_of(s, s->cur), partsf_of(s, 1 - s->cur), perm, np);
+    if (win)
+      k_permute_f32<true><<<pgrid(np), 256, 0, s->stream>>>(partsf_of(s, s->cur), partsf_of(s, 1 - s->cur), perm, np,
+                                                            slot);
+    else
+      k_permute_f32<false><<<pgrid(np), 256, 0, s->stream>>>(partsf_of(s, s->cur), partsf_of(s, 1 - s->cur), perm, np,
+                                                             slot);
+  else if (win)
+    k_permute<true><<<pgrid(np), 256, 0, s->stream>>>(parts_of(s, s->cur), parts_of(s, 1 - s->cur), perm, np, slot);
   else
-    k_permute<<<pgrid(np), 256, 0, s->stream>>>(parts_of(s, s->cur), parts_of(s, 1 - s->cur), perm, np);
+    k_permute<false><<<pgrid(np), 256, 0, s->stream>>>(parts_of(s, s->cur), parts_of(s, 1 - s->cur), perm, np, slot);
   PIC_LAUNCHED(s);
   s->cur = 1 - s->cur;
   return PIC_OK;
@@ -1543,9 +1662,15 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa) {
     k_transpose_rz<<<tgrid, dim3(32, 8), 0, s->stream>>>(s->at<float2>(s->lay.E), s->at<float2>(s->lay.ebt), c.Nr,
                                                           c.Nz);
     PIC_LAUNCHED(s);
-    k_gather_push_f32<<<(int)((s->np + bp.args.chunk - 1) / bp.args.chunk), kBandThreads, bp.smem, s->stream>>>(
-        partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.ebt), kq, kqc,
-        chdt_dr, chdt_dz, a, reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args, wa);
+    const int nblk = (int)((s->np + bp.args.chunk - 1) / bp.args.chunk);
+    if (wa.on)
+      k_gather_push_f32<true><<<nblk, kBandThreads, bp.smem, s->stream>>>(
+          partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.ebt), kq, kqc, chdt_dr, chdt_dz, a,
+          reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args, wa);
+    else
+      k_gather_push_f32<false><<<nblk, kBandThreads, bp.smem, s->stream>>>(
+          partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.ebt), kq, kqc, chdt_dr, chdt_dz, a,
+          reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args, wa);
   } else {
     DepArgs a;
     a.q = c.q;
@@ -1555,9 +1680,16 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa) {
     a.J = s->at<double2>(s->lay.dep) + G;
     if (fuse_current) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * G * sizeof(double2), s->stream));
     if (s->np == 0) return PIC_OK;
-    k_gather_push<<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, geom_of(s),
-                                                        s->at<double2>(s->lay.E), s->at<double2>(s->lay.B), c.q,
-                                                        c.mass, c.dt, a, inv_volume(s), fuse_current, err, wa);
+    if (wa.on)
+      k_gather_push<true><<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, geom_of(s),
+                                                               s->at<double2>(s->lay.E), s->at<double2>(s->lay.B),
+                                                               c.q, c.mass, c.dt, a, inv_volume(s), fuse_current, err,
+                                                               wa);
+    else
+      k_gather_push<false><<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, geom_of(s),
+                                                                s->at<double2>(s->lay.E), s->at<double2>(s->lay.B),
+                                                                c.q, c.mass, c.dt, a, inv_volume(s), fuse_current,
+                                                                err, wa);
   }
   PIC_LAUNCHED(s);
   return PIC_OK;
@@ -1603,7 +1735,10 @@ pic_status particles_configure_device() {
   std::lock_guard<std::mutex> lock(mu);
   if (dev >= 0 && dev < 64 && done[dev]) return PIC_OK;
   PIC_CUDA(cudaFuncSetAttribute(k_deposit_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandBudget));
-  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandBudget));
+  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kBandBudget));
+  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kBandBudget));
   if (dev >= 0 && dev < 64) done[dev] = true;
   return PIC_OK;
 }
@@ -1624,14 +1759,18 @@ size_t window_layout(const Sim* s, int64_t n_tpl, WindowState* w) {
   t.colids = take(4 * (size_t)std::max<int64_t>(n_tpl, 1));
   t.flag = take(4 * cap);
   t.slot = take(4 * cap);
-  t.bsum = take(4 * (cap / kWinBlock + 2));
+  t.bcnt = take(4 * (cap / kWinBlock + 2));
+  t.bstart = take(4 * (cap / kWinBlock + 2));
   t.dropped = take(8);
   t.colv = take(16 * rows);
   t.hv = take(16 * rows);
   t.ph = take(16 * (size_t)c.Nz);
+  t.hvf = take(8 * rows);
+  t.phf = take(8 * (size_t)c.Nz);
   if (w) {
-    w->tpl = t.tpl; w->colids = t.colids; w->flag = t.flag; w->slot = t.slot; w->bsum = t.bsum;
-    w->dropped = t.dropped; w->colv = t.colv; w->hv = t.hv; w->ph = t.ph;
+    w->tpl = t.tpl; w->colids = t.colids; w->flag = t.flag; w->slot = t.slot; w->bcnt = t.bcnt;
+    w->bstart = t.bstart;
+    w->dropped = t.dropped; w->colv = t.colv; w->hv = t.hv; w->ph = t.ph; w->hvf = t.hvf; w->phf = t.phf;
   }
   return off;
 }
@@ -1665,35 +1804,43 @@ pic_status window_take_template(Sim* s, int32_t* keys_host) {
   return PIC_OK;
 }
 
+pic_status launch_window_mark_all(Sim* s) {
+  WindowState& w = s->win;
+  int32_t* flag = reinterpret_cast<int32_t*>(w.ws + w.flag);
+  int32_t* slot = reinterpret_cast<int32_t*>(w.ws + w.slot);
+  int32_t* bcnt = reinterpret_cast<int32_t*>(w.ws + w.bcnt);
+  if (s->np == 0) return PIC_OK;
+  if (is_mixed(s)) {
+    const PartsF p = partsf_of(s, s->cur);
+    k_win_mark_all<float><<<pgrid(s->np), 256, 0, s->stream>>>(p.w, p.id, s->np, flag, slot, bcnt);
+  } else {
+    const Parts p = parts_of(s, s->cur);
+    k_win_mark_all<double><<<pgrid(s->np), 256, 0, s->stream>>>(p.w, p.id, s->np, flag, slot, bcnt);
+  }
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
 pic_status launch_window_inject(Sim* s, int column) {
   WindowState& w = s->win;
   const int32_t c0 = w.col_start_host[column], n_fresh = w.col_start_host[column + 1] - c0;
-  if (n_fresh == 0 || w.n_ids == 0) return PIC_OK;
   int32_t* flag = reinterpret_cast<int32_t*>(w.ws + w.flag);
-  int32_t* slot = reinterpret_cast<int32_t*>(w.ws + w.slot);
-  int32_t* bsum = reinterpret_cast<int32_t*>(w.ws + w.bsum);
+  const int32_t* slot = reinterpret_cast<const int32_t*>(w.ws + w.slot);
+  int32_t* bcnt = reinterpret_cast<int32_t*>(w.ws + w.bcnt);
+  int32_t* bstart = reinterpret_cast<int32_t*>(w.ws + w.bstart);
   const int32_t* fresh = reinterpret_cast<const int32_t*>(w.ws + w.colids) + c0;
   auto* dropped = reinterpret_cast<unsigned long long*>(w.ws + w.dropped);
   const int nb = (int)((w.n_ids + kWinBlock - 1) / kWinBlock);
-  PIC_CUDA(cudaMemsetAsync(flag, 0, w.n_ids * sizeof(int32_t), s->stream));
-  if (is_mixed(s)) {
-    const PartsF p = partsf_of(s, s->cur);
-    k_win_mark<float><<<pgrid(s->np), 256, 0, s->stream>>>(p.w, p.id, s->np, flag, slot);
-  } else {
-    const Parts p = parts_of(s, s->cur);
-    k_win_mark<double><<<pgrid(s->np), 256, 0, s->stream>>>(p.w, p.id, s->np, flag, slot);
-  }
+  if (nb == 0) return PIC_OK;
+  k_win_bscan<<<1, kWinBlock, 0, s->stream>>>(bcnt, bstart, nb, n_fresh, dropped);
   PIC_LAUNCHED(s);
-  k_win_bcount<<<nb, kWinBlock, 0, s->stream>>>(flag, w.n_ids, bsum);
-  PIC_LAUNCHED(s);
-  k_win_bscan<<<1, kWinBlock, 0, s->stream>>>(bsum, nb);
-  PIC_LAUNCHED(s);
+  if (n_fresh == 0) return PIC_OK;
   if (is_mixed(s))
-    k_win_inject_f32<<<nb, kWinBlock, 0, s->stream>>>(flag, slot, bsum, w.n_ids, nb, partsf_of(s, s->cur),
-                                                       win_tplf(s), fresh, n_fresh, dropped);
+    k_win_inject_f32<<<nb, kWinBlock, 0, s->stream>>>(flag, bcnt, slot, bstart, w.n_ids, partsf_of(s, s->cur),
+                                                       win_tplf(s), fresh, n_fresh);
   else
-    k_win_inject<<<nb, kWinBlock, 0, s->stream>>>(flag, slot, bsum, w.n_ids, nb, parts_of(s, s->cur), win_tpl(s),
-                                                   fresh, n_fresh, dropped);
+    k_win_inject<<<nb, kWinBlock, 0, s->stream>>>(flag, bcnt, slot, bstart, w.n_ids, parts_of(s, s->cur), win_tpl(s),
+                                                   fresh, n_fresh);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }

@@ -129,9 +129,9 @@ Layout make_layout(const pic_config& c) {
   L.keys = take(cap * 4);
   L.perm = take(cap * 4);
   L.perm_tmp = take(cap * 4);
-  L.count = take((ncell + 1) * 4);
-  L.start = take((ncell + 1) * 4);
-  L.scan_blk = take(4 * 4096 * 4 + (ncell + 1) * 4);   // block totals, then the scatter cursor
+  L.count = take((ncell + 66) * 4);   // cells plus 64 sub-bins of inactive particles (+1)
+  L.start = take((ncell + 66) * 4);
+  L.scan_blk = take(4 * 4096 * 4 + (ncell + 66) * 4);   // block totals, then the scatter cursor
   L.big_list = take(ncell * 4);
   L.big_count = take(256);
   L.diag_acc = take(diag_acc_doubles() * 8);
@@ -336,6 +336,9 @@ pic_status step_once(Sim* s, Marks* mk) {
     wa.shift = (s->win.cycles + 1) % s->win.period == 0;
     wa.back_col = (int32_t)(s->win.shifts % s->cfg.Nz);
     wa.back_z = wa.back_col * s->cfg.dz;
+    wa.flag = reinterpret_cast<int32_t*>(s->win.ws + s->win.flag);
+    wa.slot = reinterpret_cast<int32_t*>(s->win.ws + s->win.slot);
+    wa.bcnt = reinterpret_cast<int32_t*>(s->win.ws + s->win.bcnt);
   }
   PIC_CUDA(m.mark(0));
   if ((st = launch_gather_push(s, 1, wa)) != PIC_OK) return st;
@@ -468,6 +471,7 @@ pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_byt
 pic_status pic_autotune(pic_sim* sim, pic_tuning* out) {
   Sim* s = reinterpret_cast<Sim*>(sim);
   CHECK_SIM(s);
+  if (pic_status fs = launch_window_flush(s)) return fs;   // pending window-column subtraction
   pic_tuning res{s->tune_nt, s->tune_chunk, 0.0, 0.0};
   if (s->cfg.precision != PIC_FP64) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -535,6 +539,7 @@ pic_status pic_get_tuning(pic_sim* sim, pic_tuning* out) {
 pic_status pic_fields_to_spectral(pic_sim* sim) {
   Sim* s = reinterpret_cast<Sim*>(sim);
   CHECK_SIM(s);
+  s->win.pending = 0;   // the spectral state is rebuilt from the (already cleared) real-space fields
   return fields_forward(s);
 }
 
@@ -606,6 +611,7 @@ pic_status pic_write_particles(pic_sim* sim, const double* const soa[7], const i
                                int32_t on_host) {
   Sim* s = reinterpret_cast<Sim*>(sim);
   CHECK_SIM(s);
+  if (pic_status fs = launch_window_flush(s)) return fs;   // pending window-column subtraction
   if (n < 0 || n > s->cfg.np_capacity) {
     set_error("n=%lld exceeds the capacity %lld", (long long)n, (long long)s->cfg.np_capacity);
     return PIC_ERR_ARG;
@@ -678,6 +684,7 @@ pic_status pic_init_background(pic_sim* sim, int32_t n_neutral) {
 pic_status pic_add_beam_fields(pic_sim* sim, int32_t id_lo, int32_t id_hi, double gamma) {
   Sim* s = reinterpret_cast<Sim*>(sim);
   CHECK_SIM(s);
+  if (pic_status fs = launch_window_flush(s)) return fs;   // pending window-column subtraction
   if (!(gamma >= 1.0)) { set_error("gamma=%g must be >= 1", gamma); return PIC_ERR_ARG; }
   const size_t G = s->grid_elems();
   PIC_CUDA(cudaMemsetAsync(s->ws + s->lay.dep, 0, G * s->cplx_bytes, s->stream));
@@ -690,6 +697,7 @@ pic_status pic_add_beam_fields(pic_sim* sim, int32_t id_lo, int32_t id_hi, doubl
 pic_status pic_init_fields(pic_sim* sim) {
   Sim* s = reinterpret_cast<Sim*>(sim);
   CHECK_SIM(s);
+  if (pic_status fs = launch_window_flush(s)) return fs;   // pending window-column subtraction
   pic_status st = deposit_rho_with_background(s);
   if (st != PIC_OK) return st;
   if ((st = forward_transform(s, 1)) != PIC_OK) return st;
@@ -746,6 +754,7 @@ pic_status pic_psatd(pic_sim* sim) {
 pic_status pic_inverse_transform(pic_sim* sim) {
   Sim* s = reinterpret_cast<Sim*>(sim);
   CHECK_SIM(s);
+  if (pic_status fs = launch_window_flush(s)) return fs;   // pending window-column subtraction
   return inverse_transform(s);
 }
 
@@ -831,6 +840,7 @@ pic_status pic_buffer_bytes(pic_sim* sim, int32_t buffer_id, size_t* bytes) {
 pic_status pic_copy_buffer(pic_sim* sim, int32_t buffer_id, void* dst, size_t bytes, int32_t dst_on_host) {
   Sim* s = reinterpret_cast<Sim*>(sim);
   CHECK_SIM(s);
+  if (pic_status fs = launch_window_flush(s)) return fs;   // pending window-column subtraction
   BufView v;
   if (!buffer_view(s, buffer_id, &v)) { set_error("unknown buffer %d", buffer_id); return PIC_ERR_ARG; }
   if (!dst || bytes != v.bytes) { set_error("buffer %d has %zu bytes, %zu given", buffer_id, v.bytes, bytes); return PIC_ERR_ARG; }
@@ -843,6 +853,7 @@ pic_status pic_copy_buffer(pic_sim* sim, int32_t buffer_id, void* dst, size_t by
 pic_status pic_load_buffer(pic_sim* sim, int32_t buffer_id, const void* src, size_t bytes, int32_t src_on_host) {
   Sim* s = reinterpret_cast<Sim*>(sim);
   CHECK_SIM(s);
+  if (pic_status fs = launch_window_flush(s)) return fs;   // pending window-column subtraction
   BufView v;
   if (!buffer_view(s, buffer_id, &v)) { set_error("unknown buffer %d", buffer_id); return PIC_ERR_ARG; }
   if (buffer_id == PIC_BUF_KEYS || buffer_id == PIC_BUF_PERM) { set_error("buffer %d is read-only", buffer_id); return PIC_ERR_ARG; }
@@ -935,6 +946,10 @@ pic_status pic_window_setup(pic_sim* sim, int64_t n_plasma, int32_t period, int6
     PIC_CUDA(cudaMemcpy(s->win.ws + s->win.colids, order.data(), n_plasma * sizeof(int32_t), cudaMemcpyHostToDevice));
   PIC_CUDA(cudaMemsetAsync(s->win.ws + s->win.dropped, 0, 8, s->stream));
   if ((st = launch_window_reserve(s, n_reserve)) != PIC_OK) return st;
+  // records of the inactive particles (the reserve and any particle held with w = 0)
+  PIC_CUDA(cudaMemsetAsync(s->win.ws + s->win.flag, 0, (size_t)s->np * sizeof(int32_t), s->stream));
+  PIC_CUDA(cudaMemsetAsync(s->win.ws + s->win.bcnt, 0, ((size_t)s->np / 1024 + 2) * sizeof(int32_t), s->stream));
+  if ((st = launch_window_mark_all(s)) != PIC_OK) return st;
   s->win.col_start_host = std::move(start);
   s->win.n_ids = s->np;
   s->win.cycles = 0;

@@ -69,16 +69,22 @@ enum {
 struct WinArgs {
   int32_t on = 0, shift = 0, back_col = 0;
   double back_z = 0.0;   // back_col * dz
+  // a particle the push removes is recorded for the injections:
+  // flag[id] = 1, slot[id] = array index, bcnt[id / 1024] += 1
+  int32_t* flag = nullptr;
+  int32_t* slot = nullptr;
+  int32_t* bcnt = nullptr;
 };
 
 // Moving-window state of a handle; offsets are bytes into the caller's window workspace.
 struct WindowState {
   int32_t on = 0, period = 1;
+  int32_t pending = 0;     // the last departed column's spectral subtraction is not applied yet
   int64_t cycles = 0, shifts = 0;
   int64_t n_tpl = 0;       // template particles (ids < n_tpl)
   int64_t n_ids = 0;       // ids 0 .. n_ids-1 held (particles plus reserve)
   char* ws = nullptr;
-  size_t tpl, colids, flag, slot, bsum, dropped, colv, hv, ph;
+  size_t tpl, colids, flag, slot, bcnt, bstart, dropped, colv, hv, ph, hvf, phf;   // hvf, phf: float copies
   std::vector<int32_t> col_start_host;   // [Nz + 1] template offsets per column
 };
 
@@ -166,6 +172,7 @@ pic_status dht_tc_make_maps(Sim* s);     // once per handle: tensor maps of the 
 pic_status launch_wait_selftest(Sim* s, uint32_t max_polls);   // bounded wait that times out
 
 // ---- launchers (psatd.cu) ----
+// PSATD update; with a pending window-column removal it is applied to Eh, Bh on load.
 pic_status launch_psatd(Sim* s);
 pic_status launch_beam_fields(Sim* s, const void* rho_h, double gamma);  // adds to Eh, Bh
 pic_status launch_filter_copy(Sim* s, void* dst, const void* src);        // dst = T * src
@@ -196,9 +203,14 @@ pic_status launch_window_reserve(Sim* s, int64_t n_reserve);
 // Template of the particles with id < n_tpl (by id) into the window workspace; keys_host
 // receives the column of each template particle.  Synchronises.
 pic_status window_take_template(Sim* s, int32_t* keys_host);
+// Record every inactive particle for the injections (flag, slot, per-block count).
+pic_status launch_window_mark_all(Sim* s);
 // Template of column `column` into the inactive particles, smallest id first.
 pic_status launch_window_inject(Sim* s, int column);
-// Departing column removed from E, B (real space zeroed, its transform subtracted from Eh, Bh).
+// Departing column removed from E, B: real space zeroed now; the subtraction of its transform
+// from Eh, Bh is left pending (applied by the next PSATD or by launch_window_flush).
 pic_status launch_window_clear(Sim* s, int column);
+// Apply a pending spectral subtraction now (before Eh, Bh are read or changed elsewhere).
+pic_status launch_window_flush(Sim* s);
 
 }  // namespace pic

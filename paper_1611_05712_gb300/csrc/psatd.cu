@@ -38,14 +38,24 @@ template <typename R> __device__ __forceinline__ Z<R> zsub(Z<R> a, Z<R> b) { ret
 template <typename R> __device__ __forceinline__ Z<R> zscale(R s, Z<R> a) { return {s * a.re, s * a.im}; }
 template <typename R> __device__ __forceinline__ Z<R> zi(R s, Z<R> a) { return {-s * a.im, s * a.re}; }  // i s a
 
-template <typename R>
+// v -= h p: subtraction of a departed window column's transform (moving window); the
+// mixed form reads h and p rounded to float.
+template <typename R, typename T2>
+__device__ __forceinline__ void col_sub(Z<R>& v, T2 h, T2 p) {
+  v.re -= h.x * p.x - h.y * p.y;
+  v.im -= h.x * p.y + h.y * p.x;
+}
+
+// PEND: a moving-window column removal is pending and applied to E^, B^ as they are loaded.
+template <typename R, bool PEND>
 __global__ void __launch_bounds__(256) k_psatd(typename V2<R>::T* __restrict__ Eh, typename V2<R>::T* __restrict__ Bh,
                                                const typename V2<R>::T* __restrict__ src,
                                                typename V2<R>::T* __restrict__ rho_prev,
                                                const R* __restrict__ coef, const R* __restrict__ kperp,
                                                const R* __restrict__ kzmod, const R* __restrict__ tz,
                                                const R* __restrict__ tr, int Nz, size_t G, double dt,
-                                               int filter) {
+                                               int filter, const typename V2<R>::T* __restrict__ colh,
+                                               const typename V2<R>::T* __restrict__ colph) {
   const R kc = (R)kC, ieps0 = (R)(1.0 / kEps0), idt = (R)(1.0 / dt);
   const R jS_f = (R)(1.0 / (kEps0 * kC)), bS_f = (R)(1.0 / kC), mu0 = (R)kMu0;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < G;
@@ -68,8 +78,14 @@ __global__ void __launch_bounds__(256) k_psatd(typename V2<R>::T* __restrict__ E
     Jp = zadd(Jp, zscale(-h * Kp, Gc));
     Jm = zadd(Jm, zscale(h * Kp, Gc));
     Jz = zadd(Jz, zi(Kz, Gc));
-    const Z<R> Ep = zld<R>(Eh, idx), Em = zld<R>(Eh, G + idx), Ez = zld<R>(Eh, 2 * G + idx);
-    const Z<R> Bp = zld<R>(Bh, idx), Bm = zld<R>(Bh, G + idx), Bz = zld<R>(Bh, 2 * G + idx);
+    Z<R> Ep = zld<R>(Eh, idx), Em = zld<R>(Eh, G + idx), Ez = zld<R>(Eh, 2 * G + idx);
+    Z<R> Bp = zld<R>(Bh, idx), Bm = zld<R>(Bh, G + idx), Bz = zld<R>(Bh, 2 * G + idx);
+    if (PEND) {   // pending removal of the moving window's departed column: F^ -= h[row] p[k]
+      const typename V2<R>::T p = colph[kz];
+      const size_t MN = G / Nz;
+      col_sub(Ep, colh[mn], p); col_sub(Em, colh[MN + mn], p); col_sub(Ez, colh[2 * MN + mn], p);
+      col_sub(Bp, colh[3 * MN + mn], p); col_sub(Bm, colh[4 * MN + mn], p); col_sub(Bz, colh[5 * MN + mn], p);
+    }
     // curls
     const Z<R> cBp = zsub(zscale(Kz, Bp), zi(h * Kp, Bz));
     const Z<R> cBm = zsub(zscale(-Kz, Bm), zi(h * Kp, Bz));
@@ -159,18 +175,25 @@ inline int grid_for(size_t n) {
 pic_status launch_psatd(Sim* s) {
   const pic_config& c = s->cfg;
   const size_t G = s->grid_elems();
+  const bool pend = s->win.pending != 0;
+  s->win.pending = 0;
+  const char* wb = s->win.ws;
   if (c.precision == PIC_FP64) {
-    k_psatd<double><<<grid_for(G), 256, 0, s->stream>>>(
+    auto* k = pend ? k_psatd<double, true> : k_psatd<double, false>;
+    k<<<grid_for(G), 256, 0, s->stream>>>(
         s->at<double2>(s->lay.Eh), s->at<double2>(s->lay.Bh), s->at<double2>(s->lay.srch),
         s->at<double2>(s->lay.rho_prev_h), s->at<double>(s->lay.coef), s->at<double>(s->lay.kperp),
         s->at<double>(s->lay.kzmod), s->at<double>(s->lay.tz), s->at<double>(s->lay.tr), c.Nz, G, c.dt,
-        c.filter);
+        c.filter, pend ? reinterpret_cast<const double2*>(wb + s->win.hv) : nullptr,
+        pend ? reinterpret_cast<const double2*>(wb + s->win.ph) : nullptr);
   } else {
-    k_psatd<float><<<grid_for(G), 256, 0, s->stream>>>(
+    auto* k = pend ? k_psatd<float, true> : k_psatd<float, false>;
+    k<<<grid_for(G), 256, 0, s->stream>>>(
         s->at<float2>(s->lay.Eh), s->at<float2>(s->lay.Bh), s->at<float2>(s->lay.srch),
         s->at<float2>(s->lay.rho_prev_h), s->at<float>(s->lay.coef_f), s->at<float>(s->lay.kperp_f),
         s->at<float>(s->lay.kzmod_f), s->at<float>(s->lay.tz_f), s->at<float>(s->lay.tr_f), c.Nz, G, c.dt,
-        c.filter);
+        c.filter, pend ? reinterpret_cast<const float2*>(wb + s->win.hvf) : nullptr,
+        pend ? reinterpret_cast<const float2*>(wb + s->win.phf) : nullptr);
   }
   PIC_LAUNCHED(s);
   return PIC_OK;

@@ -8,9 +8,11 @@
 //     F^_{+-,z}[m][n][k] -= (M_p F_col_{+-,z}[m])[n] * exp(-2 pi i k c / Nz),
 // the z-DFT of a single column being the column times one phase per frequency bin
 // (forward DFT exp(-i k_z z), no normalisation), and M_p the forward Hankel matrix of order
-// p = m+1 (+), m-1 (-), m (z).  Three kernels: take the column (with F_+- = (F_r -/+ i F_th)/2)
-// and zero it, apply M_p (one warp per output), subtract the phased product from every
-// spectral row.
+// p = m+1 (+), m-1 (-), m (z).  Two kernels at the end of the cycle: take the column (with
+// F_+- = (F_r -/+ i F_th)/2) and zero it in real space; apply M_p (one warp per output) and
+// tabulate the phases.  The subtraction itself is left pending and done by the next PSATD
+// update as it loads the spectral fields (no extra pass over them); a call that reads or
+// changes the spectral fields before then applies it on its own (launch_window_flush).
 #include <math.h>
 
 #include "pic_internal.cuh"
@@ -41,9 +43,24 @@ __global__ void k_win_col_take(T2* EB, size_t G, int Nm, int Nr, int Nz, int col
   base[2 * G] = zero;
 }
 
-// hv[row][n] = sum_j M[m][slot][n][j] colv[row][j] with row = (f*3 + c)*Nm + m.
+// hv[row][n] = sum_j M[m][slot][n][j] colv[row][j] with row = (f*3 + c)*Nm + m; the
+// blocks past the last output tabulate ph[k] = exp(-2 pi i ((k * column) mod Nz) / Nz)
+// (the reduction done in integers).
+// Both are also written rounded to float (hvf, phf) for the mixed form.
 __global__ void k_win_col_hankel(const double* __restrict__ mfwd, int Nm, int Nr, const double2* __restrict__ colv,
-                                 double2* hv) {
+                                 double2* hv, int hankel_blocks, double2* ph, int Nz, int column, float2* hvf,
+                                 float2* phf) {
+  if ((int)blockIdx.x >= hankel_blocks) {
+    const int k = (blockIdx.x - hankel_blocks) * blockDim.x + threadIdx.x;
+    if (k < Nz) {
+      const long long t = ((long long)k * column) % Nz;
+      double sn, cs;
+      sincospi(-2.0 * (double)t / (double)Nz, &sn, &cs);
+      ph[k] = make_double2(cs, sn);
+      phf[k] = make_float2((float)cs, (float)sn);
+    }
+    return;
+  }
   const int lane = threadIdx.x & 31;
   const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // one warp per output
   if (o >= 6 * Nm * Nr) return;
@@ -61,20 +78,14 @@ __global__ void k_win_col_hankel(const double* __restrict__ mfwd, int Nm, int Nr
     re += __shfl_xor_sync(0xffffffffu, re, d);
     im += __shfl_xor_sync(0xffffffffu, im, d);
   }
-  if (lane == 0) hv[o] = make_double2(re, im);
+  if (lane == 0) {
+    hv[o] = make_double2(re, im);
+    hvf[o] = make_float2((float)re, (float)im);
+  }
 }
 
-// ph[k] = exp(-2 pi i ((k * column) mod Nz) / Nz), the reduction done in integers.
-__global__ void k_win_phase(double2* ph, int Nz, int column) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= Nz) return;
-  const long long t = ((long long)k * column) % Nz;
-  double sn, cs;
-  sincospi(-2.0 * (double)t / (double)Nz, &sn, &cs);
-  ph[k] = make_double2(cs, sn);
-}
-
-// Fh[row][k] -= hv[row] ph[k] over the 6*Nm*Nr spectral rows of E and B (adjacent).
+// Fh[row][k] -= hv[row] ph[k] over the 6*Nm*Nr spectral rows of E and B (adjacent): the
+// pending subtraction applied on its own (same arithmetic as the fused PSATD path).
 __global__ void k_win_col_apply64(double2* Fh, int Nz, const double2* __restrict__ hv, const double2* __restrict__ ph) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= Nz) return;
@@ -86,11 +97,11 @@ __global__ void k_win_col_apply64(double2* Fh, int Nz, const double2* __restrict
   *f = v;
 }
 
-__global__ void k_win_col_apply32(float2* Fh, int Nz, const double2* __restrict__ hv, const double2* __restrict__ ph) {
+__global__ void k_win_col_apply32(float2* Fh, int Nz, const float2* __restrict__ hv, const float2* __restrict__ ph) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= Nz) return;
-  const double2 hd = hv[blockIdx.y], pd = ph[k];
-  const float hx = (float)hd.x, hy = (float)hd.y, px = (float)pd.x, py = (float)pd.y;
+  const float2 h = hv[blockIdx.y], p = ph[k];
+  const float hx = h.x, hy = h.y, px = p.x, py = p.y;
   float2* f = Fh + (size_t)blockIdx.y * Nz + k;
   float2 v = *f;
   v.x -= hx * px - hy * py;
@@ -100,7 +111,27 @@ __global__ void k_win_col_apply32(float2* Fh, int Nz, const double2* __restrict_
 
 }  // namespace
 
+pic_status launch_window_flush(Sim* s) {
+  WindowState& w = s->win;
+  if (!w.pending) return PIC_OK;
+  w.pending = 0;
+  const pic_config& c = s->cfg;
+  const double2* hv = reinterpret_cast<const double2*>(w.ws + w.hv);
+  const double2* ph = reinterpret_cast<const double2*>(w.ws + w.ph);
+  const dim3 grid((c.Nz + kWinThreads - 1) / kWinThreads, 6 * c.Nm * c.Nr);
+  if (c.precision == PIC_FP64)
+    k_win_col_apply64<<<grid, kWinThreads, 0, s->stream>>>(s->at<double2>(s->lay.Eh), c.Nz, hv, ph);
+  else
+    k_win_col_apply32<<<grid, kWinThreads, 0, s->stream>>>(s->at<float2>(s->lay.Eh), c.Nz,
+                                                            reinterpret_cast<const float2*>(w.ws + w.hvf),
+                                                            reinterpret_cast<const float2*>(w.ws + w.phf));
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
 pic_status launch_window_clear(Sim* s, int column) {
+  pic_status st = launch_window_flush(s);   // never two pending columns
+  if (st != PIC_OK) return st;
   const pic_config& c = s->cfg;
   WindowState& w = s->win;
   const size_t G = s->grid_elems();
@@ -116,17 +147,13 @@ pic_status launch_window_clear(Sim* s, int column) {
         s->at<float2>(s->lay.E), G, c.Nm, c.Nr, c.Nz, column, colv);
   PIC_LAUNCHED(s);
   const int n_out = 6 * c.Nm * c.Nr;
-  k_win_col_hankel<<<(n_out * 32 + kWinThreads - 1) / kWinThreads, kWinThreads, 0, s->stream>>>(
-      s->at<double>(s->lay.mfwd), c.Nm, c.Nr, colv, hv);
+  const int hb = (n_out * 32 + kWinThreads - 1) / kWinThreads;
+  const int pb = (c.Nz + kWinThreads - 1) / kWinThreads;
+  k_win_col_hankel<<<hb + pb, kWinThreads, 0, s->stream>>>(s->at<double>(s->lay.mfwd), c.Nm, c.Nr, colv, hv, hb, ph,
+                                                           c.Nz, column, reinterpret_cast<float2*>(w.ws + w.hvf),
+                                                           reinterpret_cast<float2*>(w.ws + w.phf));
   PIC_LAUNCHED(s);
-  k_win_phase<<<(c.Nz + kWinThreads - 1) / kWinThreads, kWinThreads, 0, s->stream>>>(ph, c.Nz, column);
-  PIC_LAUNCHED(s);
-  const dim3 grid((c.Nz + kWinThreads - 1) / kWinThreads, n_out);
-  if (c.precision == PIC_FP64)
-    k_win_col_apply64<<<grid, kWinThreads, 0, s->stream>>>(s->at<double2>(s->lay.Eh), c.Nz, hv, ph);
-  else
-    k_win_col_apply32<<<grid, kWinThreads, 0, s->stream>>>(s->at<float2>(s->lay.Eh), c.Nz, hv, ph);
-  PIC_LAUNCHED(s);
+  w.pending = 1;
   return PIC_OK;
 }
 
