@@ -70,7 +70,9 @@ typedef enum {
 } pic_precision;
 
 typedef struct pic_config {
-  int32_t Nz;          /* z nodes (FFT length): 7-smooth, 8 <= Nz <= 4096 (FP64) / 8192 (mixed) */
+  int32_t Nz;          /* z nodes (FFT length), 8 <= Nz <= 4096 (FP64) / 8192 (mixed); a length
+                          that is not 7-smooth goes through Bluestein rows of the next power of
+                          two >= 2 Nz - 1, which caps it at 2048 (FP64) / 4096 (mixed)      */
   int32_t Nr;          /* r nodes, 4 <= Nr <= 1024                                          */
   int32_t Nm;          /* azimuthal modes m = 0..Nm-1, 1 <= Nm <= 4                         */
   int32_t order_p;     /* stencil order p = 2n (even, 2..512); 0 = infinite order           */

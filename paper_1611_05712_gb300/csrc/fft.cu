@@ -4,7 +4,8 @@
 //   inverse: F(z_i) = (1/Nz) sum_k Fhat(k) e^{+2 pi i k i / Nz}
 // Power-of-two lengths use radix-8 passes with the values in registers (k_fft_pow2); other
 // 7-smooth lengths a mixed-radix (2, 3, 4, 5, 7) self-sorting Stockham sequence of passes
-// between two shared row buffers (k_fft_rows).  Both read per-pass twiddle tables.
+// between two shared row buffers (k_fft_rows).  Both read per-pass twiddle tables.  Any
+// other length goes through Bluestein's chirp-z algorithm on power-of-two rows (below).
 // The component combination of the quasi-cylindrical scheme is fused into the row load:
 // out = ca * inA + cb * inB, which forms J_+- = (J_r -+ i J_theta)/2 before the forward
 // transform and E_r = E_+ + E_-, E_theta = i (E_+ - E_-) before the inverse one.
@@ -352,7 +353,72 @@ __global__ void __launch_bounds__(256) k_fft_rows(const typename Vec2<R>::T* __r
   }
 }
 
+// ---- any other length: Bluestein's chirp-z algorithm ----
+// With w_n = exp(i pi n^2 / N) (n^2 reduced mod 2N in integers, tabulated at set-up),
+//   forward: X_k = conj(w_k) sum_n (x_n conj(w_n)) w_{k-n},
+//   inverse: x_n = (1/N) w_n sum_k (X_k w_k) conj(w_{n-k}),
+// since nk = (n^2 + k^2 - (k-n)^2)/2.  The sums are linear convolutions, done as circular
+// ones of power-of-two length M >= 2N - 1 with the radix-8 rows: pre-multiply and zero-pad
+// (k_blue_pre, with the component combination on load), FFT_M, multiply by the spectrum S of
+// the filter b (b_m = w_|m| for |m| < N, placed mod M; conj(S) for the inverse, as b is
+// even), inverse FFT_M, post-multiply (k_blue_post).
+template <typename R, bool INV>
+__global__ void k_blue_pre(const typename Vec2<R>::T* __restrict__ in, typename Vec2<R>::T* __restrict__ a,
+                           const typename Vec2<R>::T* __restrict__ chirp, RowCombine rc, int N, int M,
+                           int rows_per_comp) {
+  using C2 = typename Vec2<R>::T;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const int row = blockIdx.y;
+  C2 v;
+  v.x = 0;
+  v.y = 0;
+  if (j < N) {
+    const int comp = row / rows_per_comp, rr = row - comp * rows_per_comp;
+    C2 ca, cb;
+    ca.x = (R)rc.caRe[comp]; ca.y = (R)rc.caIm[comp];
+    cb.x = (R)rc.cbRe[comp]; cb.y = (R)rc.cbIm[comp];
+    v = cmul(ca, in[((size_t)rc.srcA[comp] * rows_per_comp + rr) * N + j]);
+    const int sb = rc.srcB[comp];
+    if (sb >= 0) v = cadd(v, cmul(cb, in[((size_t)sb * rows_per_comp + rr) * N + j]));
+    v = cmul(v, conj_if<C2, !INV>(chirp[j]));   // forward: conj(w_j); inverse: w_j
+  }
+  a[(size_t)row * M + j] = v;
+}
+
+template <typename R, bool INV>
+__global__ void k_blue_mul(typename Vec2<R>::T* __restrict__ f, const typename Vec2<R>::T* __restrict__ spec, int M) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  typename Vec2<R>::T* p = f + (size_t)blockIdx.y * M + k;
+  *p = cmul(*p, conj_if<typename Vec2<R>::T, INV>(spec[k]));
+}
+
+template <typename R, bool INV>
+__global__ void k_blue_post(const typename Vec2<R>::T* __restrict__ c, typename Vec2<R>::T* __restrict__ out,
+                            const typename Vec2<R>::T* __restrict__ chirp, int N, int M) {
+  using C2 = typename Vec2<R>::T;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= N) return;
+  C2 w = conj_if<C2, !INV>(chirp[k]);   // forward: conj(w_k); inverse: w_k / N
+  if (INV) {
+    w.x /= (R)N;
+    w.y /= (R)N;
+  }
+  out[(size_t)blockIdx.y * N + k] = cmul(c[(size_t)blockIdx.y * M + k], w);
+}
+
 }  // namespace
+
+int bluestein_length(int Nz, int precision) {
+  int n = Nz;
+  for (int f : {2, 3, 5, 7})
+    while (n > 0 && n % f == 0) n /= f;
+  if (n == 1 || Nz < 2) return 0;   // 7-smooth: direct FFT
+  int M = 16;
+  while (M < 2 * Nz - 1) M <<= 1;
+  return M <= (precision == PIC_FP64 ? 4096 : 8192) ? M : 0;
+}
 
 // Factor Nz into passes of radix 4, 2, 3, 5, 7 (the Stockham order is free).
 bool plan_radix(int N, int32_t* radix, int32_t* n_pass) {
@@ -398,10 +464,9 @@ pic_status fft_configure_device() {
 namespace {
 
 template <typename R, bool INV, int E>
-void launch_pow2(Sim* s, const void* in, void* out, const void* twp, const RowCombine& rc, int rows,
+void launch_pow2(Sim* s, int N, const void* in, void* out, const void* twp, const RowCombine& rc, int rows,
                  int rows_per_comp) {
   using C2 = typename Vec2<R>::T;
-  const int N = s->cfg.Nz;
   int lgN = 0;
   while ((1 << lgN) < N) ++lgN;
   constexpr int PS = sizeof(R) == 4 ? 4 : 3;
@@ -413,12 +478,41 @@ void launch_pow2(Sim* s, const void* in, void* out, const void* twp, const RowCo
 }
 
 template <typename R, bool INV>
-void launch_pow2_e(Sim* s, const void* in, void* out, const void* twp, const RowCombine& rc, int rows,
+void launch_pow2_e(Sim* s, int N, const void* in, void* out, const void* twp, const RowCombine& rc, int rows,
                    int rows_per_comp) {
-  const int N = s->cfg.Nz;
-  if (N <= 2048) launch_pow2<R, INV, 8>(s, in, out, twp, rc, rows, rows_per_comp);
-  else if (N == 4096 || sizeof(R) == 8) launch_pow2<R, INV, 16>(s, in, out, twp, rc, rows, rows_per_comp);
-  else launch_pow2<R, INV, sizeof(R) == 8 ? 16 : 32>(s, in, out, twp, rc, rows, rows_per_comp);
+  if (N <= 2048) launch_pow2<R, INV, 8>(s, N, in, out, twp, rc, rows, rows_per_comp);
+  else if (N == 4096 || sizeof(R) == 8) launch_pow2<R, INV, 16>(s, N, in, out, twp, rc, rows, rows_per_comp);
+  else launch_pow2<R, INV, sizeof(R) == 8 ? 16 : 32>(s, N, in, out, twp, rc, rows, rows_per_comp);
+}
+
+// Bluestein rows (see k_blue_pre): five launches between the two row scratches.
+template <typename R, bool INV>
+pic_status launch_bluestein(Sim* s, const void* in, void* out, const RowCombine& rc, int rows, int rows_per_comp) {
+  using C2 = typename Vec2<R>::T;
+  const bool f32 = sizeof(R) == 4;
+  const int N = s->cfg.Nz, M = s->blue_M;
+  C2* a = s->at<C2>(s->lay.blue_a);
+  C2* b = s->at<C2>(s->lay.blue_b);
+  const C2* chirp = s->at<C2>(f32 ? s->lay.chirp_f : s->lay.chirp);
+  const C2* spec = s->at<C2>(f32 ? s->lay.bspec_f : s->lay.bspec);
+  const void* twm = s->at<C2>(f32 ? s->lay.twm_f : s->lay.twm);
+  RowCombine id{};
+  id.n_out = 1;
+  id.srcA[0] = 0;
+  id.srcB[0] = -1;
+  id.caRe[0] = 1.0;
+  const dim3 gm((M + 255) / 256, rows), gn((N + 255) / 256, rows);
+  k_blue_pre<R, INV><<<gm, 256, 0, s->stream>>>((const C2*)in, a, chirp, rc, N, M, rows_per_comp);
+  PIC_LAUNCHED(s);
+  launch_pow2_e<R, false>(s, M, a, b, twm, id, rows, rows);
+  PIC_LAUNCHED(s);
+  k_blue_mul<R, INV><<<gm, 256, 0, s->stream>>>(b, spec, M);
+  PIC_LAUNCHED(s);
+  launch_pow2_e<R, true>(s, M, b, a, twm, id, rows, rows);
+  PIC_LAUNCHED(s);
+  k_blue_post<R, INV><<<gn, 256, 0, s->stream>>>(a, (C2*)out, chirp, N, M);
+  PIC_LAUNCHED(s);
+  return PIC_OK;
 }
 
 }  // namespace
@@ -429,15 +523,22 @@ pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& 
   const pic_config& c = s->cfg;
   const int rows_per_comp = c.Nm * c.Nr;
   const int rows = rc.n_out * rows_per_comp;
+  if (s->blue_M > 0) {
+    if (c.precision == PIC_FP64)
+      return inverse ? launch_bluestein<double, true>(s, in, out, rc, rows, rows_per_comp)
+                     : launch_bluestein<double, false>(s, in, out, rc, rows, rows_per_comp);
+    return inverse ? launch_bluestein<float, true>(s, in, out, rc, rows, rows_per_comp)
+                   : launch_bluestein<float, false>(s, in, out, rc, rows, rows_per_comp);
+  }
   if (fft_is_pow2(c.Nz)) {
     if (c.precision == PIC_FP64) {
       const void* twp = s->at<double2>(s->lay.twp);
-      if (inverse) launch_pow2_e<double, true>(s, in, out, twp, rc, rows, rows_per_comp);
-      else launch_pow2_e<double, false>(s, in, out, twp, rc, rows, rows_per_comp);
+      if (inverse) launch_pow2_e<double, true>(s, c.Nz, in, out, twp, rc, rows, rows_per_comp);
+      else launch_pow2_e<double, false>(s, c.Nz, in, out, twp, rc, rows, rows_per_comp);
     } else {
       const void* twp = s->at<float2>(s->lay.twp_f);
-      if (inverse) launch_pow2_e<float, true>(s, in, out, twp, rc, rows, rows_per_comp);
-      else launch_pow2_e<float, false>(s, in, out, twp, rc, rows, rows_per_comp);
+      if (inverse) launch_pow2_e<float, true>(s, c.Nz, in, out, twp, rc, rows, rows_per_comp);
+      else launch_pow2_e<float, false>(s, c.Nz, in, out, twp, rc, rows, rows_per_comp);
     }
     PIC_LAUNCHED(s);
     return PIC_OK;

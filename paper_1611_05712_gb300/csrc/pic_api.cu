@@ -45,9 +45,16 @@ pic_status validate(const pic_config* c, int32_t* radix, int32_t* n_pass) {
     return PIC_ERR_ARG;
   }
   const int max_nz = c->precision == PIC_FP64 ? 4096 : 8192;   // two shared-memory rows per FFT CTA
-  if (c->Nz < 8 || c->Nz > max_nz || !plan_radix(c->Nz, radix, n_pass)) {
-    set_error("Nz=%d must be a 7-smooth integer in [8, %d]", c->Nz, max_nz);
+  if (c->Nz < 8 || c->Nz > max_nz) {
+    set_error("Nz=%d must be in [8, %d]", c->Nz, max_nz);
     return PIC_ERR_ARG;
+  }
+  if (!plan_radix(c->Nz, radix, n_pass)) {
+    *n_pass = 0;
+    if (bluestein_length(c->Nz, c->precision) == 0) {
+      set_error("Nz=%d is not 7-smooth: Bluestein lengths reach Nz <= %d", c->Nz, max_nz / 2);
+      return PIC_ERR_ARG;
+    }
   }
   if (c->Nr < 4 || c->Nr > kMaxNr) { set_error("Nr=%d must be in [4, %d]", c->Nr, kMaxNr); return PIC_ERR_ARG; }
   if (c->Nm < 1 || c->Nm > kMaxModes) { set_error("Nm=%d must be in [1, %d]", c->Nm, kMaxModes); return PIC_ERR_ARG; }
@@ -98,6 +105,19 @@ Layout make_layout(const pic_config& c) {
   L.tr = take((size_t)c.Nm * c.Nr * 8);
   L.coef = take(6 * G * 8);
   L.twp = take((size_t)c.Nz * 16);
+  const int M = bluestein_length(c.Nz, c.precision);
+  if (M > 0) {
+    L.twm = take((size_t)M * 16);
+    L.chirp = take((size_t)c.Nz * 16);
+    L.bspec = take((size_t)M * 16);
+    if (c.precision != PIC_FP64) {
+      L.twm_f = take((size_t)M * 8);
+      L.chirp_f = take((size_t)c.Nz * 8);
+      L.bspec_f = take((size_t)M * 8);
+    }
+    L.blue_a = take(6 * (size_t)c.Nm * c.Nr * M * cb);
+    L.blue_b = take(6 * (size_t)c.Nm * c.Nr * M * cb);
+  }
   if (mixed) {
     for (int b = 0; b < 2; ++b)
       for (int k = 0; k < kPfCount; ++k) L.pf[b][k] = take(cap * 4);
@@ -445,6 +465,7 @@ pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_byt
   s->cplx_bytes = cfg->precision == PIC_FP64 ? 16 : 8;
   s->tune_nt = 0;
   s->tune_chunk = 1024;
+  s->blue_M = bluestein_length(cfg->Nz, cfg->precision);
   const size_t G = s->grid_elems();
   const size_t cb = s->cplx_bytes;
   auto fail = [&](pic_status e) { delete s; return e; };

@@ -46,8 +46,16 @@ struct Layout {
   size_t pf[2][13];  // iz, fz, ixy (packed int16 x, y cells), fx, fy, u/c hi (3), u/c lo (3), w, id
   size_t stage64;    // 7 x capacity float64
   size_t ebt;        // E, B with r fastest: [6][Nm][Nz][Nr] complex float (gather layout)
+  // Nz that is not 7-smooth (Bluestein, 0 otherwise): twiddles of the power-of-two length M,
+  // the chirp w_n (Nz), the chirp filter's spectrum (M), float copies, two row scratches
+  size_t twm, twm_f, chirp, chirp_f, bspec, bspec_f, blue_a, blue_b;
   size_t total;
 };
+
+// Power-of-two convolution length M >= 2 Nz - 1 of Bluestein's algorithm for an Nz that is
+// not 7-smooth; 0 when Nz is 7-smooth (direct FFT) or when M exceeds the row FFT's limit
+// (4096 FP64, 8192 float).
+int bluestein_length(int Nz, int precision);
 
 // Row pitch (floats) of the split DHT matrices of the mixed form: Nr rounded up to a
 // multiple of 4 so that rows start on 16-byte boundaries (tensor-memory-access copies).
@@ -101,6 +109,7 @@ struct Sim {
   int64_t launches;        // kernels launched by this handle (host-side count)
   int32_t n_radix;
   int32_t radix[kMaxRadixPasses];
+  int32_t blue_M;          // Bluestein convolution length (0: direct FFT of length Nz)
   size_t cplx_bytes;       // 16 (FP64) or 8 (mixed)
   int32_t tune_nt;         // mixed-form DHT N tile (0: built-in rule), see pic_set_tuning
   int32_t tune_chunk;      // particles per CTA of the band kernels

@@ -559,7 +559,53 @@ pic_status launch_setup_tables(Sim* s, int32_t order_p) {
   return PIC_OK;
 }
 
+// Bluestein tables for an Nz that is not 7-smooth: the chirp w_n = exp(i pi t / N) with
+// t = n^2 mod 2N computed in integers, and the spectrum of the even filter b (b_m = w_|m| for
+// |m| < N, indices mod M): S_k = 1 + 2 sum_{j=1}^{N-1} w_j cos(2 pi (jk mod M) / M), summed
+// directly in float64 (once per handle; the arguments 2t/M are exact for M a power of two).
+__global__ void k_blue_chirp(double2* chirp, int N) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  const long long t = ((long long)n * n) % (2LL * N);
+  double sn, cs;
+  sincospi((double)t / (double)N, &sn, &cs);
+  chirp[n] = make_double2(cs, sn);
+}
+
+__global__ void k_blue_spectrum(const double2* __restrict__ chirp, double2* spec, int N, int M) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  double re = 0.0, im = 0.0;
+  for (int j = 1; j < N; ++j) {
+    const long long t = ((long long)j * k) & (M - 1);
+    const double c = cospi(2.0 * (double)t / (double)M);
+    re = fma(chirp[j].x, c, re);
+    im = fma(chirp[j].y, c, im);
+  }
+  spec[k] = make_double2(1.0 + 2.0 * re, 2.0 * im);
+}
+
 pic_status launch_setup_twiddles(Sim* s) {
+  if (s->blue_M > 0) {
+    const int N = s->cfg.Nz, M = s->blue_M;
+    k_twiddles_pow2<<<blocks_for(M, 128), 128, 0, s->stream>>>(s->at<double2>(s->lay.twm), M);
+    PIC_LAUNCHED(s);
+    k_blue_chirp<<<blocks_for(N, 128), 128, 0, s->stream>>>(s->at<double2>(s->lay.chirp), N);
+    PIC_LAUNCHED(s);
+    k_blue_spectrum<<<blocks_for(M, 128), 128, 0, s->stream>>>(s->at<double2>(s->lay.chirp),
+                                                                s->at<double2>(s->lay.bspec), N, M);
+    PIC_LAUNCHED(s);
+    if (s->cfg.precision != PIC_FP64) {
+      const size_t pairs[3][3] = {{s->lay.twm, s->lay.twm_f, 2 * (size_t)M},
+                                  {s->lay.chirp, s->lay.chirp_f, 2 * (size_t)N},
+                                  {s->lay.bspec, s->lay.bspec_f, 2 * (size_t)M}};
+      for (const auto& q : pairs) {
+        k_to_float<<<conv_grid(q[2]), 256, 0, s->stream>>>(s->at<double>(q[0]), s->at<float>(q[1]), q[2]);
+        PIC_LAUNCHED(s);
+      }
+    }
+    return PIC_OK;
+  }
   const bool pow2 = fft_is_pow2(s->cfg.Nz);
   if (pow2) {
     k_twiddles_pow2<<<blocks_for(s->cfg.Nz, 128), 128, 0, s->stream>>>(s->at<double2>(s->lay.twp), s->cfg.Nz);

@@ -6,7 +6,8 @@ guard cells at p = 32), so each z subdomain, extended by enough guard cells on b
 can be advanced with its own Fourier transform of length N_local + 2 g and reproduce the
 global update in its interior; with too few guard cells the periodic wrap of the local
 transform leaves spurious fields.  This module builds that scheme from library handles:
-one local handle of length N_local + 2 g (same Nr, Nm, order, time step and precision)
+one local handle of length N_local + 2 g (same Nr, Nm, order, time step and precision;
+any length the library accepts, lengths that are not 7-smooth going through Bluestein rows)
 is loaded with each subdomain's guarded window of E and B (pic_copy_window), its spectral
 state is set from them (pic_fields_to_spectral), it advances one field step, and its
 interior is written back into an output handle.
@@ -20,13 +21,6 @@ from __future__ import annotations
 from . import binding as bd
 
 
-def smooth7(n: int) -> bool:
-    for f in (2, 3, 5, 7):
-        while n % f == 0:
-            n //= f
-    return n == 1
-
-
 class GuardedDomains:
     """n_domains equal z subdomains of a handle's grid, each advanced with `guard` cells
     of the neighbouring subdomains on both sides."""
@@ -38,8 +32,8 @@ class GuardedDomains:
         self.L = cfg.Nz // n_domains
         self.g = int(guard)
         nz_loc = self.L + 2 * self.g
-        if self.g < 0 or nz_loc > cfg.Nz or not smooth7(nz_loc):
-            raise ValueError(f"local length {nz_loc} must be 7-smooth and at most Nz={cfg.Nz}")
+        if self.g < 0 or nz_loc > cfg.Nz:
+            raise ValueError(f"local length {nz_loc} must be at most Nz={cfg.Nz}")
         lc = bd.make_config(nz_loc, cfg.Nr, cfg.Nm, cfg.dz, cfg.dr, cfg.dt, cfg.order_p, bool(cfg.filter),
                             cfg.precision, 0, cfg.q, cfg.mass)
         self.local = bd.Sim(lc, device=device, stream=stream)

@@ -30,7 +30,7 @@ def test_required_bytes_and_validation(lib):
     n = bd.required_bytes(cfg)
     assert n > 256 * 64 * 2 * 16 * 30
     bad = [
-        dict(Nz=11), dict(Nz=4), dict(Nz=8192), dict(Nr=2), dict(Nr=2048), dict(Nm=0), dict(Nm=5),
+        dict(Nz=2053), dict(Nz=4), dict(Nz=8192), dict(Nr=2), dict(Nr=2048), dict(Nm=0), dict(Nm=5),
         dict(order_p=3), dict(order_p=-2), dict(order_p=1024), dict(dt=0.0), dict(np_capacity=-1),
         dict(precision=7),
     ]
@@ -49,6 +49,18 @@ def test_seven_smooth_lengths_accepted(lib):
         c = bd.make_config(nz, 16, 1, 5e-8, 5e-8, 1e-16, 0, True, bd.PIC_FP64, 10)
         out = ctypes.c_size_t()
         assert lib.pic_required_bytes(ctypes.byref(c), ctypes.byref(out)) == 0, nz
+
+
+def test_non_smooth_lengths_within_the_bluestein_limit(lib):
+    # lengths that are not 7-smooth use power-of-two Bluestein rows of M >= 2 Nz - 1, at most
+    # 4096 (FP64) or 8192 (mixed forms)
+    cases = [(11, bd.PIC_FP64, 0), (61, bd.PIC_FP64, 0), (2039, bd.PIC_FP64, 0), (2053, bd.PIC_FP64, 1),
+             (4093, bd.PIC_FP64, 1), (4093, bd.PIC_MIXED_TF32X3, 0), (4093, bd.PIC_MIXED_BF16X6, 0),
+             (4111, bd.PIC_MIXED_TF32X3, 1), (22, bd.PIC_MIXED_TF32X3, 0)]
+    for nz, prec, want in cases:
+        c = bd.make_config(nz, 16, 1, 5e-8, 5e-8, 1e-16, 0, True, prec, 10)
+        out = ctypes.c_size_t()
+        assert lib.pic_required_bytes(ctypes.byref(c), ctypes.byref(out)) == want, (nz, prec)
 
 
 def test_null_handles_rejected(lib):
