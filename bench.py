@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--accuracy-cycles", type=int, default=100,
                     help="cycles after which the mixed form's fields and beam quality are "
                          "compared with the FP64 form (0: skip)")
-    ap.add_argument("--workload", choices=["wake", "scan", "large", "guard", "order_sweep", "window"],
+    ap.add_argument("--workload", choices=["wake", "scan", "large", "guard", "order_sweep", "window", "fft_lengths"],
                     default="wake",
                     help="wake: the 2048x256 wakefield run; scan: many uneven simulations "
                          "(order / resolution scan) advanced by one CUDA graph per launch; "
@@ -703,6 +703,38 @@ def run_window(args):
     return 0
 
 
+def run_fft_lengths(args):
+    """Cost of the z transforms at lengths that are not 7-smooth (Bluestein rows) against the
+    nearest power of two: the wakefield configuration (256 r nodes, 2 modes, p = 32) at
+    Nz = 2048 and at the prime Nz = 2039, per-stage device times of args.steps cycles."""
+    import dataclasses
+
+    from paper_1611_05712_gb300 import binding as bd
+    from paper_1611_05712_gb300 import workloads as W
+    from paper_1611_05712_gb300.build import build
+    build()
+    prec = {"fp64": bd.PIC_FP64, "mixed": bd.PIC_MIXED_TF32X3, "bf16": bd.PIC_MIXED_BF16X6}[args.precision]
+    out = {}
+    for nz in (2048, 2039):
+        w = dataclasses.replace(W.wake_2048x256(order_p=args.order), Nz=nz)
+        P, npl, beams = W.particles(w)
+        s = bd.Sim.from_workload(w, P, npl, beams, precision=prec)
+        if prec != bd.PIC_FP64:
+            s.autotune()
+        s.step(args.warmup)
+        st, tot = s.step_timed(args.steps)
+        out[str(nz)] = {"ms_per_step": tot / args.steps,
+                        "fft_fwd_ms": st["fft_fwd"] / args.steps, "fft_inv_ms": st["fft_inv"] / args.steps,
+                        "dht_ms": (st["dht_fwd"] + st["dht_inv"]) / args.steps}
+        s.close()
+    print(json.dumps({"metric": "z_transform_cost_by_length", "unit": "ms per cycle", "precision": args.precision,
+                      "config": {"Nr": 256, "Nm": 2, "order_p": args.order, "steps": args.steps,
+                                 "lengths": {"2048": "power of two (radix-8 rows)",
+                                             "2039": "prime (Bluestein, M = 4096)"}},
+                      "by_length": out}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -717,6 +749,8 @@ def main():
         return run_order_sweep(args)
     if args.workload == "window":
         return run_window(args)
+    if args.workload == "fft_lengths":
+        return run_fft_lengths(args)
     return run_ours(args)
 
 

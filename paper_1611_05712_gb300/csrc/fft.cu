@@ -249,6 +249,154 @@ __global__ void __launch_bounds__(kFftThreads, E == 8 ? 4 : (E == 16 ? 2 : 1)) k
   else pow2_pass<C2, INV, E, 2, PS>(v, c, twp, L, lgL, true);
 }
 
+// ---- Bluestein rows in one kernel (see the chirp-z section below for the algorithm) ----
+// The row of power-of-two length M stays on chip: load the N inputs times the chirp (zero
+// beyond N), forward radix-8 passes ending in the shared buffer, multiply by the filter
+// spectrum there, inverse passes, and store the first N outputs times the chirp.  Global
+// traffic is one read and one write of the N-point rows, as for a direct transform.
+template <typename C2, int E>
+__device__ __forceinline__ void blue_load_global(C2 (&v)[E], const RowCtx<C2>& c, const C2* __restrict__ chirp,
+                                                 int N, bool conj_chirp) {
+  using Re = decltype(v[0].x);
+  const int M8 = c.N >> 3;
+#pragma unroll
+  for (int q = 0; q < E / 8; ++q) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int idx = c.tr + q * c.TR + r * M8;
+      C2 x;
+      x.x = (Re)0; x.y = (Re)0;
+      if (c.active && idx < N) {
+        x = cmul(c.ca, c.a[idx]);
+        if (c.b) x = cadd(x, cmul(c.cb, c.b[idx]));
+        C2 w = chirp[idx];
+        if (conj_chirp) w.y = -w.y;
+        x = cmul(x, w);
+      }
+      v[q * 8 + r] = x;
+    }
+  }
+}
+
+// Last inverse pass: outputs idx < N, times post(idx) = 1/M (the inverse FFT_M) times the
+// outer transform's chirp factor (forward: conj(w); inverse: w / N).
+template <typename C2, bool OUTER_INV, int E, int R>
+__device__ __forceinline__ void blue_store_global(C2 (&v)[E], const RowCtx<C2>& c, int L, int lgL,
+                                                  const C2* __restrict__ chirp, int N) {
+  using Re = decltype(v[0].x);
+  const Re scale = (Re)1 / (Re)c.N / (OUTER_INV ? (Re)N : (Re)1);
+#pragma unroll
+  for (int q = 0; q < E / R; ++q) {
+    const int t = c.tr + q * c.TR;
+    const int base = ((t >> lgL) * R) * L + (t & (L - 1));
+#pragma unroll
+    for (int s2 = 0; s2 < R; ++s2) {
+      const int idx = base + s2 * L;
+      if (c.active && idx < N) {
+        C2 w = chirp[idx];
+        if (!OUTER_INV) w.y = -w.y;
+        w.x *= scale;
+        w.y *= scale;
+        c.o[idx] = cmul(v[q * R + s2], w);
+      }
+    }
+  }
+}
+
+template <typename R, bool OUTER_INV, int E>
+__global__ void __launch_bounds__(kFftThreads, E == 8 ? 4 : (E == 16 ? 2 : 1)) k_fft_blue(
+    const typename Vec2<R>::T* __restrict__ in, typename Vec2<R>::T* __restrict__ out,
+    const typename Vec2<R>::T* __restrict__ twm, const typename Vec2<R>::T* __restrict__ chirp,
+    const typename Vec2<R>::T* __restrict__ spec, RowCombine rc, int N, int M, int lgM, int rows, int rows_per_comp) {
+  using C2 = typename Vec2<R>::T;
+  constexpr int PS = sizeof(R) == 4 ? 4 : 3;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RowCtx<C2> c;
+  c.N = M;
+  c.TR = M / E;
+  const int lr = threadIdx.x / c.TR;
+  c.tr = threadIdx.x - lr * c.TR;
+  const int row = blockIdx.x * (kFftThreads / c.TR) + lr;
+  c.active = row < rows;
+  c.buf = reinterpret_cast<C2*>(smem_raw) + (size_t)lr * (M + (M >> PS));
+  const int rrow = c.active ? row : 0;
+  const int comp = rrow / rows_per_comp;
+  const int rr = rrow - comp * rows_per_comp;
+  c.a = in + ((size_t)rc.srcA[comp] * rows_per_comp + rr) * N;
+  const int sb = rc.srcB[comp];
+  c.b = sb >= 0 ? in + ((size_t)sb * rows_per_comp + rr) * N : nullptr;
+  c.ca.x = (R)rc.caRe[comp]; c.ca.y = (R)rc.caIm[comp];
+  c.cb.x = (R)rc.cbRe[comp]; c.cb.y = (R)rc.cbIm[comp];
+  c.o = out + (size_t)rrow * N;
+  C2 v[E];
+  const int n8 = lgM / 3, rem = lgM - 3 * n8;
+  // forward FFT_M of the chirped, zero-padded row; every pass ends in the shared buffer
+  blue_load_global<C2, E>(v, c, chirp, N, !OUTER_INV);
+  int L = 1, lgL = 0;
+  for (int p = 0; p < n8; ++p) {
+    pow2_butterflies<C2, false, E, 8>(v, c, twm, L);
+    pow2_store<C2, false, E, 8, PS>(v, c, L, lgL, false);
+    L <<= 3;
+    lgL += 3;
+    __syncthreads();
+    if (p + 1 < n8) {
+      pow2_load_shared<C2, E, 8, PS>(v, c);
+      __syncthreads();
+    }
+  }
+  if (rem) {
+    if (rem == 2) pow2_load_shared<C2, E, 4, PS>(v, c);
+    else pow2_load_shared<C2, E, 2, PS>(v, c);
+    __syncthreads();
+    if (rem == 2) {
+      pow2_butterflies<C2, false, E, 4>(v, c, twm, L);
+      pow2_store<C2, false, E, 4, PS>(v, c, L, lgL, false);
+    } else {
+      pow2_butterflies<C2, false, E, 2>(v, c, twm, L);
+      pow2_store<C2, false, E, 2, PS>(v, c, L, lgL, false);
+    }
+    __syncthreads();
+  }
+  // times the filter spectrum (conjugated for the inverse outer transform)
+#pragma unroll
+  for (int j = 0; j < E; ++j) {
+    const int k = c.tr + j * c.TR;
+    C2& x = c.buf[padded<PS>(k)];
+    C2 sp = spec[k];
+    if (OUTER_INV) sp.y = -sp.y;
+    x = cmul(x, sp);
+  }
+  __syncthreads();
+  // inverse FFT_M; the last pass stores the first N outputs
+  pow2_load_shared<C2, E, 8, PS>(v, c);
+  __syncthreads();
+  L = 1;
+  lgL = 0;
+  for (int p = 0; p < n8; ++p) {
+    const bool last = p == n8 - 1 && rem == 0;
+    pow2_butterflies<C2, true, E, 8>(v, c, twm, L);
+    if (last) {
+      blue_store_global<C2, OUTER_INV, E, 8>(v, c, L, lgL, chirp, N);
+      return;
+    }
+    pow2_store<C2, true, E, 8, PS>(v, c, L, lgL, false);
+    L <<= 3;
+    lgL += 3;
+    __syncthreads();
+    if (p + 1 < n8) pow2_load_shared<C2, E, 8, PS>(v, c);
+    else if (rem == 2) pow2_load_shared<C2, E, 4, PS>(v, c);
+    else pow2_load_shared<C2, E, 2, PS>(v, c);
+    __syncthreads();
+  }
+  if (rem == 2) {
+    pow2_butterflies<C2, true, E, 4>(v, c, twm, L);
+    blue_store_global<C2, OUTER_INV, E, 4>(v, c, L, lgL, chirp, N);
+  } else {
+    pow2_butterflies<C2, true, E, 2>(v, c, twm, L);
+    blue_store_global<C2, OUTER_INV, E, 2>(v, c, L, lgL, chirp, N);
+  }
+}
+
 // ---- any 7-smooth length ----
 // Stockham passes of the plan's radices (4, 2, 3, 5, 7 in the plan's order) between two
 // shared row buffers, one row per CTA; each thread takes butterflies t, t + 256, ... of a
@@ -358,56 +506,10 @@ __global__ void __launch_bounds__(256) k_fft_rows(const typename Vec2<R>::T* __r
 //   forward: X_k = conj(w_k) sum_n (x_n conj(w_n)) w_{k-n},
 //   inverse: x_n = (1/N) w_n sum_k (X_k w_k) conj(w_{n-k}),
 // since nk = (n^2 + k^2 - (k-n)^2)/2.  The sums are linear convolutions, done as circular
-// ones of power-of-two length M >= 2N - 1 with the radix-8 rows: pre-multiply and zero-pad
-// (k_blue_pre, with the component combination on load), FFT_M, multiply by the spectrum S of
-// the filter b (b_m = w_|m| for |m| < N, placed mod M; conj(S) for the inverse, as b is
-// even), inverse FFT_M, post-multiply (k_blue_post).
-template <typename R, bool INV>
-__global__ void k_blue_pre(const typename Vec2<R>::T* __restrict__ in, typename Vec2<R>::T* __restrict__ a,
-                           const typename Vec2<R>::T* __restrict__ chirp, RowCombine rc, int N, int M,
-                           int rows_per_comp) {
-  using C2 = typename Vec2<R>::T;
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= M) return;
-  const int row = blockIdx.y;
-  C2 v;
-  v.x = 0;
-  v.y = 0;
-  if (j < N) {
-    const int comp = row / rows_per_comp, rr = row - comp * rows_per_comp;
-    C2 ca, cb;
-    ca.x = (R)rc.caRe[comp]; ca.y = (R)rc.caIm[comp];
-    cb.x = (R)rc.cbRe[comp]; cb.y = (R)rc.cbIm[comp];
-    v = cmul(ca, in[((size_t)rc.srcA[comp] * rows_per_comp + rr) * N + j]);
-    const int sb = rc.srcB[comp];
-    if (sb >= 0) v = cadd(v, cmul(cb, in[((size_t)sb * rows_per_comp + rr) * N + j]));
-    v = cmul(v, conj_if<C2, !INV>(chirp[j]));   // forward: conj(w_j); inverse: w_j
-  }
-  a[(size_t)row * M + j] = v;
-}
-
-template <typename R, bool INV>
-__global__ void k_blue_mul(typename Vec2<R>::T* __restrict__ f, const typename Vec2<R>::T* __restrict__ spec, int M) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= M) return;
-  typename Vec2<R>::T* p = f + (size_t)blockIdx.y * M + k;
-  *p = cmul(*p, conj_if<typename Vec2<R>::T, INV>(spec[k]));
-}
-
-template <typename R, bool INV>
-__global__ void k_blue_post(const typename Vec2<R>::T* __restrict__ c, typename Vec2<R>::T* __restrict__ out,
-                            const typename Vec2<R>::T* __restrict__ chirp, int N, int M) {
-  using C2 = typename Vec2<R>::T;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= N) return;
-  C2 w = conj_if<C2, !INV>(chirp[k]);   // forward: conj(w_k); inverse: w_k / N
-  if (INV) {
-    w.x /= (R)N;
-    w.y /= (R)N;
-  }
-  out[(size_t)blockIdx.y * N + k] = cmul(c[(size_t)blockIdx.y * M + k], w);
-}
-
+// ones of power-of-two length M >= 2N - 1: pre-multiply and zero-pad (with the component
+// combination on load), FFT_M, multiply by the spectrum S of the filter b (b_m = w_|m| for
+// |m| < N, placed mod M; conj(S) for the inverse, as b is even), inverse FFT_M,
+// post-multiply -- all in k_fft_blue, one CTA per row (or several short rows).
 }  // namespace
 
 int bluestein_length(int Nz, int precision) {
@@ -457,6 +559,11 @@ pic_status fft_configure_device() {
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<float, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
+  // Bluestein rows of length M = 8192 (float) / 4096 (double)
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_blue<float, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_blue<float, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_blue<double, false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_blue<double, true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
   if (dev >= 0 && dev < 64) done[dev] = true;
   return PIC_OK;
 }
@@ -485,32 +592,30 @@ void launch_pow2_e(Sim* s, int N, const void* in, void* out, const void* twp, co
   else launch_pow2<R, INV, sizeof(R) == 8 ? 16 : 32>(s, N, in, out, twp, rc, rows, rows_per_comp);
 }
 
-// Bluestein rows (see k_blue_pre): five launches between the two row scratches.
-template <typename R, bool INV>
-pic_status launch_bluestein(Sim* s, const void* in, void* out, const RowCombine& rc, int rows, int rows_per_comp) {
+template <typename R, bool INV, int E>
+void launch_blue(Sim* s, const void* in, void* out, const RowCombine& rc, int rows, int rows_per_comp) {
   using C2 = typename Vec2<R>::T;
   const bool f32 = sizeof(R) == 4;
   const int N = s->cfg.Nz, M = s->blue_M;
-  C2* a = s->at<C2>(s->lay.blue_a);
-  C2* b = s->at<C2>(s->lay.blue_b);
-  const C2* chirp = s->at<C2>(f32 ? s->lay.chirp_f : s->lay.chirp);
-  const C2* spec = s->at<C2>(f32 ? s->lay.bspec_f : s->lay.bspec);
-  const void* twm = s->at<C2>(f32 ? s->lay.twm_f : s->lay.twm);
-  RowCombine id{};
-  id.n_out = 1;
-  id.srcA[0] = 0;
-  id.srcB[0] = -1;
-  id.caRe[0] = 1.0;
-  const dim3 gm((M + 255) / 256, rows), gn((N + 255) / 256, rows);
-  k_blue_pre<R, INV><<<gm, 256, 0, s->stream>>>((const C2*)in, a, chirp, rc, N, M, rows_per_comp);
-  PIC_LAUNCHED(s);
-  launch_pow2_e<R, false>(s, M, a, b, twm, id, rows, rows);
-  PIC_LAUNCHED(s);
-  k_blue_mul<R, INV><<<gm, 256, 0, s->stream>>>(b, spec, M);
-  PIC_LAUNCHED(s);
-  launch_pow2_e<R, true>(s, M, b, a, twm, id, rows, rows);
-  PIC_LAUNCHED(s);
-  k_blue_post<R, INV><<<gn, 256, 0, s->stream>>>(a, (C2*)out, chirp, N, M);
+  int lgM = 0;
+  while ((1 << lgM) < M) ++lgM;
+  constexpr int PS = sizeof(R) == 4 ? 4 : 3;
+  const int rpc = kFftThreads / (M / E);
+  const size_t smem = (size_t)rpc * (M + (M >> PS)) * sizeof(C2);
+  const int grid = (rows + rpc - 1) / rpc;
+  k_fft_blue<R, INV, E><<<grid, kFftThreads, smem, s->stream>>>(
+      (const C2*)in, (C2*)out, s->at<C2>(f32 ? s->lay.twm_f : s->lay.twm), s->at<C2>(f32 ? s->lay.chirp_f : s->lay.chirp),
+      s->at<C2>(f32 ? s->lay.bspec_f : s->lay.bspec), rc, N, M, lgM, rows, rows_per_comp);
+}
+
+// Bluestein rows: one fused kernel (k_fft_blue), values per thread chosen as for the
+// power-of-two rows of length M.
+template <typename R, bool INV>
+pic_status launch_bluestein(Sim* s, const void* in, void* out, const RowCombine& rc, int rows, int rows_per_comp) {
+  const int M = s->blue_M;
+  if (M <= 2048) launch_blue<R, INV, 8>(s, in, out, rc, rows, rows_per_comp);
+  else if (M == 4096 || sizeof(R) == 8) launch_blue<R, INV, 16>(s, in, out, rc, rows, rows_per_comp);
+  else launch_blue<R, INV, sizeof(R) == 8 ? 16 : 32>(s, in, out, rc, rows, rows_per_comp);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }

@@ -115,8 +115,6 @@ Layout make_layout(const pic_config& c) {
       L.chirp_f = take((size_t)c.Nz * 8);
       L.bspec_f = take((size_t)M * 8);
     }
-    L.blue_a = take(6 * (size_t)c.Nm * c.Nr * M * cb);
-    L.blue_b = take(6 * (size_t)c.Nm * c.Nr * M * cb);
   }
   if (mixed) {
     for (int b = 0; b < 2; ++b)

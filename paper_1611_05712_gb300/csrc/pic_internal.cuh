@@ -47,8 +47,8 @@ struct Layout {
   size_t stage64;    // 7 x capacity float64
   size_t ebt;        // E, B with r fastest: [6][Nm][Nz][Nr] complex float (gather layout)
   // Nz that is not 7-smooth (Bluestein, 0 otherwise): twiddles of the power-of-two length M,
-  // the chirp w_n (Nz), the chirp filter's spectrum (M), float copies, two row scratches
-  size_t twm, twm_f, chirp, chirp_f, bspec, bspec_f, blue_a, blue_b;
+  // the chirp w_n (Nz), the chirp filter's spectrum (M), float copies
+  size_t twm, twm_f, chirp, chirp_f, bspec, bspec_f;
   size_t total;
 };
 
