@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-form comparison")
-    ap.add_argument("--accuracy-cycles", type=int, default=100,
+    ap.add_argument("--accuracy-cycles", type=int, default=2000,
                     help="cycles after which the mixed form's fields and beam quality are "
                          "compared with the FP64 form (0: skip)")
     ap.add_argument("--workload", choices=["wake", "scan", "large", "guard", "order_sweep", "window", "fft_lengths"],
@@ -288,38 +288,49 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
     return out
 
 
-def accuracy_vs_fp64(w, P, npl, beams, n_cycles, local, prec):
-    """Error of the mixed form against the FP64 form after n_cycles from the same initial
-    state: per field max |mixed - fp64| / max |fp64| over all components and modes, and the
-    relative differences of each beam's normalised emittances and slice energy spread."""
+def accuracy_vs_fp64(w, P, npl, beams, n_cycles, local):
+    """Error of both mixed forms against the FP64 form, run in lockstep from the same initial
+    state, at checkpoints up to n_cycles: per field max |mixed - fp64| / max |fp64| over all
+    components and modes, each beam's relative differences of normalised emittances and
+    slice energy spread, and the worst of those beam differences."""
     import numpy as np
     import torch
 
     from paper_1611_05712_gb300 import binding as bd
-    sims = {}
-    for name, pr in (("fp64", bd.PIC_FP64), ("mixed", prec)):
-        s = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}", precision=pr)
-        s.step(n_cycles)
-        s.sync()
-        sims[name] = s
-    a, b = sims["fp64"], sims["mixed"]
+    forms = (("fp64", bd.PIC_FP64), ("tf32x3", bd.PIC_MIXED_TF32X3), ("bf16x6", bd.PIC_MIXED_BF16X6))
+    sims = {name: bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}", precision=pr) for name, pr in forms}
 
     def rel(x, y):
         return float(np.abs(y - x).max() / max(np.abs(x).max(), 1e-300))
 
-    dep_a, dep_b = a.get("DEP"), b.get("DEP")
-    out = {"cycles": n_cycles,
-           "E": rel(a.get("E"), b.get("E")), "B": rel(a.get("B"), b.get("B")),
-           "J": rel(dep_a[1:], dep_b[1:]), "rho": rel(dep_a[:1], dep_b[:1])}
-    for bi, bm in enumerate(beams):
-        lo, hi = bm[0], bm[1]
-        name = "drive" if bi == 0 and len(beams) > 1 else ("witness" if bi == len(beams) - 1 else f"beam{bi}")
-        da, db = a.diagnostics(lo, hi), b.diagnostics(lo, hi)
-        out[name] = {k: abs(db[k] - da[k]) / max(abs(da[k]), 1e-300)
-                     for k in ("emit_nx", "emit_ny", "sigma_gamma_mean", "gamma_mean")}
+    names = ["drive" if bi == 0 and len(beams) > 1 else ("witness" if bi == len(beams) - 1 else f"beam{bi}")
+             for bi in range(len(beams))]
+    out = {"tf32x3": {}, "bf16x6": {}}
+    done = 0
+    for cp in sorted({c for c in (100, 500, 1000, n_cycles) if c <= n_cycles}):
+        for s in sims.values():
+            s.step(cp - done)
+            s.sync()
+        done = cp
+        a = sims["fp64"]
+        dep_a, E_a, B_a = a.get("DEP"), a.get("E"), a.get("B")
+        ref = [a.diagnostics(lo, hi) for lo, hi, _ in beams]
+        for form in ("tf32x3", "bf16x6"):
+            b = sims[form]
+            dep_b = b.get("DEP")
+            row = {"E": rel(E_a, b.get("E")), "B": rel(B_a, b.get("B")), "J": rel(dep_a[1:], dep_b[1:]),
+                   "rho": rel(dep_a[:1], dep_b[:1])}
+            worst = 0.0
+            for name, (lo, hi, _), da in zip(names, beams, ref):
+                db = b.diagnostics(lo, hi)
+                row[name] = {k: abs(db[k] - da[k]) / max(abs(da[k]), 1e-300)
+                             for k in ("emit_nx", "emit_ny", "sigma_gamma_mean", "gamma_mean")}
+                worst = max(worst, *(row[name][k] for k in ("emit_nx", "emit_ny", "sigma_gamma_mean")))
+            row["worst_beam_metric"] = worst
+            out[form][str(cp)] = row
     for s in sims.values():
         s.close()
-    del sims, a, b
+    del sims
     torch.cuda.empty_cache()
     return out
 
@@ -363,9 +374,11 @@ def run_ours(args):
         "clocks": head["clocks"],
     }
     if args.precision == "fp64" and not args.no_mixed:
-        # the chosen mixed-precision form on the same workload (3-term TF32 DHT), and the
-        # BF16-split variant of it
-        for key, prec in (("mixed_form", bd.PIC_MIXED_TF32X3), ("mixed_form_bf16", bd.PIC_MIXED_BF16X6)):
+        # the two mixed-precision forms on the same workload (3-term TF32 and 6-product BF16
+        # DHT), their accuracy against the FP64 form, and the chosen one
+        acc = accuracy_vs_fp64(w, P, npl, beams, args.accuracy_cycles, local) if args.accuracy_cycles > 0 else {}
+        for key, form, prec in (("mixed_form", "tf32x3", bd.PIC_MIXED_TF32X3),
+                                ("mixed_form_bf16", "bf16x6", bd.PIC_MIXED_BF16X6)):
             mx = measure(args, w, P, npl, beams, prec, dist, dev, world, local)
             line[key] = {
                 "value": mx["steps_per_s"], "unit": "steps/s", "dtype": mx["dtype"],
@@ -373,9 +386,24 @@ def run_ours(args):
                 "speedup_vs_fp64": mx["steps_per_s"] / head["steps_per_s"],
                 "stage_ms_per_step": mx["stage_ms_per_step"], "roofline": mx["roofline"], "e2e": mx["e2e"],
                 "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"], "tuning": mx.get("tuning")}
-            if args.accuracy_cycles > 0:
-                line[key]["accuracy_vs_fp64"] = accuracy_vs_fp64(w, P, npl, beams, args.accuracy_cycles, local,
-                                                                 prec)
+            if acc:
+                line[key]["accuracy_vs_fp64"] = acc[form]
+        if acc:
+            # the chosen form: the fastest whose beam emittances and slice energy spreads stay
+            # within 1e-4 of the FP64 form at the configuration's full length
+            last = str(args.accuracy_cycles)
+            ok = [(line[k]["value"], k) for k, f in (("mixed_form", "tf32x3"), ("mixed_form_bf16", "bf16x6"))
+                  if acc[f][last]["worst_beam_metric"] <= 1e-4]
+            if ok:
+                v, k = max(ok)
+                line["chosen_form"] = {"form": k, "value": v, "unit": "steps/s",
+                                       "speedup_vs_fp64": v / head["steps_per_s"],
+                                       "worst_beam_metric_vs_fp64": acc["tf32x3" if k == "mixed_form" else "bf16x6"][last]
+                                       ["worst_beam_metric"],
+                                       "criterion": f"beam emittances and slice energy spreads within 1e-4 of the "
+                                                    f"FP64 form after {last} cycles"}
+            else:
+                line["chosen_form"] = {"form": None, "criterion": f"no mixed form within 1e-4 after {last} cycles"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, secs = oracle_steps_per_s(w, P, npl, beams, 1)
         line["cpu_baseline"] = {"value": v, "unit": "steps/s", "cores": os.cpu_count(),
