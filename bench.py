@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--accuracy-cycles", type=int, default=2000,
                     help="cycles after which the mixed form's fields and beam quality are "
                          "compared with the FP64 form (0: skip)")
+    ap.add_argument("--sort-interval", type=int, default=4,
+                    help="mixed forms: sort particles by cell on every k-th cycle (pic_set_sort_interval)")
     ap.add_argument("--workload", choices=["wake", "scan", "large", "guard", "order_sweep", "window", "fft_lengths"],
                     default="wake",
                     help="wake: the 2048x256 wakefield run; scan: many uneven simulations "
@@ -200,6 +202,9 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
     sim = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}", precision=prec)
     wit_lo, wit_hi = beams[-1][0], beams[-1][1]
     tuning = sim.autotune() if mixed else None   # untimed: tile sizes for this workload
+    if mixed:
+        sim.set_sort_interval(args.sort_interval)
+        tuning["sort_interval"] = args.sort_interval
     sim.step(args.warmup)
     sim.sync()
     torch.cuda.synchronize(dev)
@@ -288,7 +293,7 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
     return out
 
 
-def accuracy_vs_fp64(w, P, npl, beams, n_cycles, local):
+def accuracy_vs_fp64(w, P, npl, beams, n_cycles, local, sort_interval=1):
     """Error of both mixed forms against the FP64 form, run in lockstep from the same initial
     state, at checkpoints up to n_cycles: per field max |mixed - fp64| / max |fp64| over all
     components and modes, each beam's relative differences of normalised emittances and
@@ -299,6 +304,9 @@ def accuracy_vs_fp64(w, P, npl, beams, n_cycles, local):
     from paper_1611_05712_gb300 import binding as bd
     forms = (("fp64", bd.PIC_FP64), ("tf32x3", bd.PIC_MIXED_TF32X3), ("bf16x6", bd.PIC_MIXED_BF16X6))
     sims = {name: bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}", precision=pr) for name, pr in forms}
+    for name, s in sims.items():
+        if name != "fp64":
+            s.set_sort_interval(sort_interval)   # as in the timed mixed runs
 
     def rel(x, y):
         return float(np.abs(y - x).max() / max(np.abs(x).max(), 1e-300))
@@ -376,7 +384,8 @@ def run_ours(args):
     if args.precision == "fp64" and not args.no_mixed:
         # the two mixed-precision forms on the same workload (3-term TF32 and 6-product BF16
         # DHT), their accuracy against the FP64 form, and the chosen one
-        acc = accuracy_vs_fp64(w, P, npl, beams, args.accuracy_cycles, local) if args.accuracy_cycles > 0 else {}
+        acc = (accuracy_vs_fp64(w, P, npl, beams, args.accuracy_cycles, local, args.sort_interval)
+               if args.accuracy_cycles > 0 else {})
         for key, form, prec in (("mixed_form", "tf32x3", bd.PIC_MIXED_TF32X3),
                                 ("mixed_form_bf16", "bf16x6", bd.PIC_MIXED_BF16X6)):
             mx = measure(args, w, P, npl, beams, prec, dist, dev, world, local)

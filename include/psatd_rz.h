@@ -353,6 +353,16 @@ pic_status pic_autotune(pic_sim* sim, pic_tuning* out);
 pic_status pic_set_tuning(pic_sim* sim, const pic_tuning* tuning);
 pic_status pic_get_tuning(pic_sim* sim, pic_tuning* out);
 
+/* Sort interval (no counterpart in the paper): pic_step runs the cell sort (a1) on every
+ * interval-th cycle only (1 = every cycle, the default; 1 <= interval <= 16).  The sort
+ * changes no particle's state; it orders the particles so that the deposit bands of the
+ * mixed forms and the gathers stay local.  Particles move at most about a cell per cycle,
+ * so the order a few cycles old is still nearly sorted.  What changes is the order of the
+ * float (FP64 form: double) additions of the deposits across CTAs, i.e. their rounding.
+ * The stage entry point pic_sort always sorts.  Errors: PIC_ERR_ARG. */
+pic_status pic_set_sort_interval(pic_sim* sim, int32_t interval);
+pic_status pic_get_sort_interval(pic_sim* sim, int32_t* interval);
+
 /* a10: FP64 diagnostics of the particles with id in [id_lo, id_hi).  slice_sigma (host,
  * may be NULL) receives up to max_slices per-slice std of gamma.  Synchronises. */
 pic_status pic_diagnostics(pic_sim* sim, int32_t id_lo, int32_t id_hi, pic_diag* out,

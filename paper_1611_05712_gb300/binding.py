@@ -116,6 +116,8 @@ def load():
         "pic_window_required_bytes": [P, I64, ctypes.POINTER(SZ)],
         "pic_window_setup": [P, I64, I32, I64, P, SZ],
         "pic_window_state": [P, ctypes.POINTER(PicWindowInfo)],
+        "pic_set_sort_interval": [P, I32],
+        "pic_get_sort_interval": [P, ctypes.POINTER(I32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -299,6 +301,14 @@ class Sim:
     def set_tuning(self, dht_n_tile=0, band_chunk=1024):
         t = PicTuning(dht_n_tile, band_chunk, 0.0, 0.0)
         _check(self.lib.pic_set_tuning(self.h, ctypes.byref(t)), "pic_set_tuning")
+
+    def set_sort_interval(self, k):
+        _check(self.lib.pic_set_sort_interval(self.h, int(k)), "pic_set_sort_interval")
+
+    def get_sort_interval(self):
+        k = ctypes.c_int32()
+        _check(self.lib.pic_get_sort_interval(self.h, ctypes.byref(k)), "pic_get_sort_interval")
+        return k.value
 
     def get_tuning(self):
         t = PicTuning()

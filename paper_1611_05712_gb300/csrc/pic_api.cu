@@ -362,7 +362,8 @@ pic_status step_once(Sim* s, Marks* mk) {
   if ((st = launch_gather_push(s, 1, wa)) != PIC_OK) return st;
   if (wa.shift && (st = launch_window_inject(s, wa.back_col)) != PIC_OK) return st;
   PIC_CUDA(m.mark(1));
-  if ((st = launch_sort(s)) != PIC_OK) return st;
+  if (s->sort_interval <= 1 || s->cycle_idx % s->sort_interval == 0)
+    if ((st = launch_sort(s)) != PIC_OK) return st;
   PIC_CUDA(m.mark(2));
   if ((st = deposit_rho_with_background(s)) != PIC_OK) return st;
   PIC_CUDA(m.mark(3));
@@ -374,6 +375,7 @@ pic_status step_once(Sim* s, Marks* mk) {
     }
     s->win.cycles += 1;
   }
+  s->cycle_idx += 1;
   return PIC_OK;
 }
 
@@ -463,6 +465,8 @@ pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_byt
   s->cplx_bytes = cfg->precision == PIC_FP64 ? 16 : 8;
   s->tune_nt = 0;
   s->tune_chunk = 1024;
+  s->sort_interval = 1;
+  s->cycle_idx = 0;
   s->blue_M = bluestein_length(cfg->Nz, cfg->precision);
   const size_t G = s->grid_elems();
   const size_t cb = s->cplx_bytes;
@@ -545,6 +549,25 @@ pic_status pic_set_tuning(pic_sim* sim, const pic_tuning* t) {
     return PIC_ERR_ARG;
   }
   return apply_tuning(s, t->dht_n_tile, t->band_chunk);
+}
+
+pic_status pic_set_sort_interval(pic_sim* sim, int32_t interval) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (interval < 1 || interval > 16) {
+    set_error("sort interval %d must be in [1, 16]", interval);
+    return PIC_ERR_ARG;
+  }
+  s->sort_interval = interval;
+  return PIC_OK;
+}
+
+pic_status pic_get_sort_interval(pic_sim* sim, int32_t* interval) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (!interval) { set_error("interval is NULL"); return PIC_ERR_ARG; }
+  *interval = s->sort_interval;
+  return PIC_OK;
 }
 
 pic_status pic_get_tuning(pic_sim* sim, pic_tuning* out) {

@@ -113,6 +113,8 @@ struct Sim {
   size_t cplx_bytes;       // 16 (FP64) or 8 (mixed)
   int32_t tune_nt;         // mixed-form DHT N tile (0: built-in rule), see pic_set_tuning
   int32_t tune_chunk;      // particles per CTA of the band kernels
+  int32_t sort_interval;   // pic_step sorts on every sort_interval-th cycle (1: every cycle)
+  int64_t cycle_idx;       // cycles pic_step has run on this handle
   // mixed forms: encoded 2-D tensor maps (CUtensorMap, 128 B each) of the split DHT
   // matrices, [matrix id][plane] (TF32: hi, lo; BF16: three pieces), built at init
   struct alignas(64) TensorMapBytes {

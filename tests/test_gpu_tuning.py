@@ -102,3 +102,37 @@ def test_set_tuning_rejects_bad_values():
     for nt, ch in ((8, 1024), (24, 1024), (272, 1024), (0, 1000), (0, 4096)):
         with pytest.raises(bd.PicError):
             s.set_tuning(dht_n_tile=nt, band_chunk=ch)
+
+
+@pytest.mark.parametrize("precision,tol_f,tol_x,tol_u", [(bd.PIC_FP64, 1e-11, 1e-11, 1e-11),
+                                                          (bd.PIC_MIXED_TF32X3, 1e-4, 1e-5, 1e-4)])
+def test_sort_interval_keeps_parity(precision, tol_f, tol_x, tol_u):
+    # sorting every third cycle changes the order of the deposit additions only
+    from gpu_helpers import by_id
+    w = W.plasma_beam_small(order_p=16)
+    P, npl, beams = W.particles(w)
+    g = O.Grid(w.Nz, w.Nr, w.Nm, w.dz, w.dr, w.dt)
+    s = bd.Sim.from_workload(w, P, npl, beams, precision=precision)
+    s.set_sort_interval(3)
+    assert s.get_sort_interval() == 3
+    Pg = s.read_particles() if precision != bd.PIC_FP64 else P
+    st = O.make_state(g, w.order_p, True, Pg, npl, beams)
+    s.step(5)
+    O.pic_step(st, 5)
+    for name, ref in (("E", st.E), ("B", st.B)):
+        assert rel_err(s.get(name), np.stack(ref)) < tol_f, name
+    got, ref = by_id(s.read_particles()), by_id(st.p)
+    for k in ("x", "y", "z"):
+        assert rel_err(got[k], ref[k]) < tol_x, k
+    for k in ("ux", "uy", "uz"):
+        assert rel_err(got[k], ref[k]) < tol_u, k
+
+
+def test_sort_interval_rejects_bad_values():
+    w = W.tiny(order_p=16, Nz=32, Nr=8, Nm=1, n_beam=16)
+    P, npl, beams = W.particles(w)
+    s = bd.Sim.from_workload(w, P, npl, beams)
+    for k in (0, -1, 17):
+        with pytest.raises(bd.PicError):
+            s.set_sort_interval(k)
+    assert s.get_sort_interval() == 1
