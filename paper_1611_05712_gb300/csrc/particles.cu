@@ -646,11 +646,14 @@ struct DepArgsF {
 // S is chosen per CTA so that |y| <= 2^(46 - log2 chunk) for every contribution of its
 // chunk (2^36 for 1024 particles): |sum of hi| < 2^30 and sum of lo <= 2^(16 + log2 chunk)
 // cannot overflow, and the resolution is 2^-36 (chunk 1024) of the largest possible
-// contribution.
+// contribution.  Mode 0 has a real phase, so only the modes m >= 1 have imaginary planes.
+// A band may carry rho as component 0 beside J in components 1..3, with its own scale.
 struct BandF {
-  int32_t* tile;   // 4 planes (re hi, re lo, im hi, im lo) of P = TZ*ncomp*Nm*JW words, or null
-  int iz_lo, TZ, ncomp, P;   // TZ is a power of two
-  float scale;     // 2^S
+  int32_t* tile;   // planes re hi, re lo (P = TZ*ncomp*Nm*JW words each), then im hi, im lo
+                   // (Pim = TZ*ncomp*(Nm-1)*JW words each), or null
+  int iz_lo, TZ, ncomp, P, Pim;   // TZ is a power of two
+  float scale;     // 2^S of the components >= 1 (all components when scale0 is unused)
+  float scale0;    // 2^S of component 0
   int lgTZ;
   int j_lo, JW;    // r nodes j_lo .. j_lo + JW - 1
 };
@@ -685,14 +688,19 @@ __device__ __forceinline__ void dep_node_fb(float2* grid_cm, const GeomF& g, con
     if (row < 0) row += g.Nz;
     const int jj = j - bd.j_lo;
     if (row < bd.TZ && (unsigned)jj < (unsigned)bd.JW) {
+      const float sc = comp == 0 ? bd.scale0 : bd.scale;
       const int e = ((row * bd.ncomp + comp) * g.Nm + m) * bd.JW + jj;
-      int hr, lr, hi, li;
-      fixed_split(vre * wgt * bd.scale, hr, lr);
-      fixed_split(vim * wgt * bd.scale, hi, li);
+      int hr, lr;
+      fixed_split(vre * wgt * sc, hr, lr);
       atomicAdd(bd.tile + e, hr);
       atomicAdd(bd.tile + bd.P + e, lr);
-      atomicAdd(bd.tile + 2 * bd.P + e, hi);
-      atomicAdd(bd.tile + 3 * bd.P + e, li);
+      if (m > 0) {   // mode 0 has a real phase and no imaginary planes
+        const int ei = ((row * bd.ncomp + comp) * (g.Nm - 1) + m - 1) * bd.JW + jj;
+        int hi, li;
+        fixed_split(vim * wgt * sc, hi, li);
+        atomicAdd(bd.tile + 2 * bd.P + ei, hi);
+        atomicAdd(bd.tile + 2 * bd.P + bd.Pim + ei, li);
+      }
       return;
     }
   }
@@ -737,9 +745,10 @@ __device__ __forceinline__ ChunkStats chunk_stats(const PartsF& p, const GeomF& 
 // +1 node), at most tz_max rows; r nodes from the chunk's lowest stencil node - jmargin to
 // its highest + 1 + jmargin, at most jw_max of them; nodes beyond are simply not banded.
 // bound is an upper bound of |x| over the chunk's contributions.
+// bound0 > 0: component 0 gets its own scale from bound0.
 __device__ __forceinline__ BandF make_band(int32_t* smem, int iz_first, int iz_last, const GeomF& g, int tz_max,
                                            int ncomp, float bound, const ChunkStats& cs, int jw_max, int jmargin,
-                                           int lg_chunk) {
+                                           int lg_chunk, float bound0 = -1.f) {
   const int j_lo = max(0, cs.jmin - jmargin);
   const int j_hi = min(g.Nr - 1, cs.jmax + 1 + jmargin);
   const int JW = max(1, min(jw_max, j_hi - j_lo + 1));
@@ -753,14 +762,19 @@ __device__ __forceinline__ BandF make_band(int32_t* smem, int iz_first, int iz_l
   int e = 0;
   frexpf(bound, &e);   // bound <= 2^e
   const int S = min(max(46 - lg_chunk - e, -126), 126);
+  int S0 = S;
+  if (bound0 > 0.f) {
+    frexpf(bound0, &e);
+    S0 = min(max(46 - lg_chunk - e, -126), 126);
+  }
   return BandF{smem, iz_first == 0 ? g.Nz - 1 : iz_first - 1, rows, ncomp, rows * ncomp * g.Nm * JW,
-               ldexpf(1.f, S), lg, j_lo, JW};
+               rows * ncomp * (g.Nm - 1) * JW, ldexpf(1.f, S), ldexpf(1.f, S0), lg, j_lo, JW};
 }
 
 // Zero a band (all threads of the CTA).
 __device__ __forceinline__ void band_zero(const BandF& bd) {
   if (!bd.tile) return;
-  for (int k = threadIdx.x; k < 4 * bd.P; k += blockDim.x) bd.tile[k] = 0;
+  for (int k = threadIdx.x; k < 2 * (bd.P + bd.Pim); k += blockDim.x) bd.tile[k] = 0;
 }
 
 // Add a band's non-zero entries, times 2^-S / V_j, to the global grids (all threads of the
@@ -770,8 +784,9 @@ __device__ __forceinline__ void band_zero(const BandF& bd) {
 __device__ void band_flush(const BandF& bd, const GeomF& g, float2* grid0, const float* invV) {
   if (!bd.tile) return;
   const size_t RZ = (size_t)g.Nr * g.Nz;
-  const float inv_scale = 1.f / bd.scale;   // power of two: exact
+  const float inv_scale = 1.f / bd.scale, inv_scale0 = 1.f / bd.scale0;   // powers of two: exact
   const int NC = bd.ncomp * g.Nm * bd.JW;   // columns (comp, m, j); entry e = row * NC + col
+  const int NCi = bd.ncomp * (g.Nm - 1) * bd.JW;   // imaginary planes: modes m >= 1
   const float inv_jw = 1.f / (float)bd.JW, inv_nm = 1.f / (float)g.Nm;
   for (int k = threadIdx.x; k < bd.P; k += blockDim.x) {
     const int row = k & (bd.TZ - 1);
@@ -779,13 +794,20 @@ __device__ void band_flush(const BandF& bd, const GeomF& g, float2* grid0, const
     // col / JW and cm / Nm from float reciprocals: (n + 1/2)/d is at least 1/(2d) away from
     // an integer and the product errs by < (n + 1/2) 2^-23 / d, exact for n < 2^22
     const int cm = (int)(((float)col + 0.5f) * inv_jw);
-    const int j = bd.j_lo + col - cm * bd.JW;
+    const int jj = col - cm * bd.JW;
+    const int j = bd.j_lo + jj;
     const int comp = (int)(((float)cm + 0.5f) * inv_nm);
     const int m = cm - comp * g.Nm;
     const int e = row * NC + col;
-    const int hr = bd.tile[e], lr = bd.tile[bd.P + e], hi = bd.tile[2 * bd.P + e], li = bd.tile[3 * bd.P + e];
+    const int hr = bd.tile[e], lr = bd.tile[bd.P + e];
+    int hi = 0, li = 0;
+    if (m > 0) {
+      const int ei = row * NCi + (comp * (g.Nm - 1) + m - 1) * bd.JW + jj;
+      hi = bd.tile[2 * bd.P + ei];
+      li = bd.tile[2 * bd.P + bd.Pim + ei];
+    }
     if ((hr | lr | hi | li) == 0) continue;
-    const float f = inv_scale * invV[j];
+    const float f = (comp == 0 ? inv_scale0 : inv_scale) * invV[j];
     const float vr = __ll2float_rn((long long)hr * 65536 + lr) * f;
     const float vi = __ll2float_rn((long long)hi * 65536 + li) * f;
     int i = bd.iz_lo + row;
@@ -795,9 +817,10 @@ __device__ void band_flush(const BandF& bd, const GeomF& g, float2* grid0, const
 }
 
 // deposit of one particle at (iz+fz, x, y) with velocity (vx, vy, vz) [m/s]
+// jc0: band component of J_r (J_theta, J_z follow); rho is band component 0.
 __device__ __forceinline__ void deposit_one_f(const GeomF& g, const DepArgsF& a, const float* invV, const BandF& bR,
                               const BandF& bJ, int iz, float fz, float x, float y, float w, float vx, float vy,
-                              float vz, bool do_rho, bool do_J) {
+                              float vz, bool do_rho, bool do_J, int jc0 = 0) {
   float r, c, s;
   polar_f(x, y, r, c, s);
   const StencilF st = stencil_f(g, iz, fz, r);
@@ -819,9 +842,9 @@ __device__ __forceinline__ void deposit_one_f(const GeomF& g, const DepArgsF& a,
       const float wgt = (dz ? st.wz1 : st.wz0) * (dj ? st.wr1 : st.wr0);
       if (do_rho) dep_node_fb(a.rho + m * RZ, g, bR, 0, m, j, i, wgt, fs, qre, qim, invV);
       if (do_J) {
-        dep_node_fb(a.J + m * RZ, g, bJ, 0, m, j, i, wgt, fv, qre * vr, qim * vr, invV);
-        dep_node_fb(a.J + g.G + m * RZ, g, bJ, 1, m, j, i, wgt, fv, qre * vt, qim * vt, invV);
-        dep_node_fb(a.J + 2 * g.G + m * RZ, g, bJ, 2, m, j, i, wgt, fs, qre * vz, qim * vz, invV);
+        dep_node_fb(a.J + m * RZ, g, bJ, jc0, m, j, i, wgt, fv, qre * vr, qim * vr, invV);
+        dep_node_fb(a.J + g.G + m * RZ, g, bJ, jc0 + 1, m, j, i, wgt, fv, qre * vt, qim * vt, invV);
+        dep_node_fb(a.J + 2 * g.G + m * RZ, g, bJ, jc0 + 2, m, j, i, wgt, fs, qre * vz, qim * vz, invV);
       }
     }
     const float nr = phr * c - phi * s, ni = phr * s + phi * c;
@@ -921,8 +944,8 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_deposit_f32(const PartsF p,
   const int64_t b0 = blockIdx.x * chunk;
   if (b0 >= np) return;
   const int64_t b1 = b0 + chunk < np ? b0 + chunk : np;
-  BandF none{nullptr, 0, 0, 0, 0, 1.f, 0, 0, 1};
-  BandF band{nullptr, 0, 0, 0, 0, 1.f, 0, 0, 1};
+  BandF none{nullptr, 0, 0, 0, 0, 0, 1.f, 1.f, 0, 0, 1};
+  BandF band{nullptr, 0, 0, 0, 0, 0, 1.f, 1.f, 0, 0, 1};
   if (ba.tz > 0 && do_rho != do_J) {
     const ChunkStats cs = chunk_stats(p, g, b0, b1, &stats_slot, err);
     if (cs.wmax_bits != 0u)   // a chunk of inactive particles deposits nothing: no band
@@ -974,7 +997,9 @@ __device__ __forceinline__ void advance_z(int& iz, float& fz, float dfz, int Nz)
 // One CTA per chunk of `chunk` consecutive (cell-sorted) particles; with tz > 0 the fused J
 // deposit accumulates into a band of tz z-rows from one row below the chunk's first cell
 // (a half step moves a particle by at most half a cell at c dt <= dz).
-template <bool WIN>
+// RHO: also deposit rho^{n+1} at x^{n+1} (band component 0; J in components 1..3, which is
+// the order of the deposit grids, so one flush writes all four).
+template <bool WIN, bool RHO>
 __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, int64_t np, GeomF g,
                                   const float2* __restrict__ EBt, float kq, float kqc, float chdt_dr,
                                   float chdt_dz, DepArgsF dep, const float* invV, int fuse, int32_t* err,
@@ -987,14 +1012,14 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
   const int64_t b0 = blockIdx.x * chunk;
   if (b0 >= np) return;
   const int64_t b1 = b0 + chunk < np ? b0 + chunk : np;
-  const BandF none{nullptr, 0, 0, 0, 0, 1.f, 0, 0, 1};
-  BandF band{nullptr, 0, 0, 0, 0, 1.f, 0, 0, 1};
+  const BandF none{nullptr, 0, 0, 0, 0, 0, 1.f, 1.f, 0, 0, 1};
+  BandF band{nullptr, 0, 0, 0, 0, 0, 1.f, 1.f, 0, 0, 1};
   if (fuse && ba.tz > 0) {
     const ChunkStats cs = chunk_stats(p, g, b0, b1, &stats_slot, err);
+    const float qw = fabsf(dep.q) * __uint_as_float(cs.wmax_bits);
     if (cs.wmax_bits != 0u)   // a chunk of inactive particles deposits nothing: no band
-      band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, 3,
-                       fabsf(dep.q) * __uint_as_float(cs.wmax_bits) * c_light, cs, ba.jw_max, ba.jmargin,
-                       ba.lg_chunk);
+      band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, RHO ? 4 : 3, qw * c_light, cs, ba.jw_max,
+                       ba.jmargin, ba.lg_chunk, RHO ? qw : -1.f);
   }
   band_zero(band);
   __syncthreads();
@@ -1063,7 +1088,7 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
     advance_z(iz, fz, dzc, g.Nz);
     if (fuse)
       deposit_one_f(g, dep, invV, none, band, iz, fz, (float)ix + fx, (float)iy + fy, w, bx * c_light,
-                    by * c_light, bz * c_light, false, true);
+                    by * c_light, bz * c_light, false, true, RHO ? 1 : 0);
     advance_cell(ix, fx, bx * chdt_dr);
     advance_cell(iy, fy, by * chdt_dr);
     advance_z(iz, fz, dzc, g.Nz);
@@ -1093,9 +1118,12 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
     p.ixy[i] = pack_cells(ix, iy); p.fx[i] = fx; p.fy[i] = fy; p.fz[i] = fz; p.iz[i] = iz;
     p.ux[i] = uxh; p.uy[i] = uyh; p.uz[i] = uzh;
     p.uxl[i] = uxl; p.uyl[i] = uyl; p.uzl[i] = uzl;
+    if (RHO)   // rho^{n+1} at x^{n+1}
+      deposit_one_f(g, dep, invV, band, none, iz, fz, (float)ix + fx, (float)iy + fy, w, 0.f, 0.f, 0.f, true,
+                    false);
   }
   __syncthreads();
-  band_flush(band, g, dep.J, invV);
+  band_flush(band, g, RHO ? dep.rho : dep.J, invV);
 }
 
 // float64 SoA (x y z ux uy uz w) <-> FP32 cell-relative particles
@@ -1513,7 +1541,8 @@ BandPlan band_plan(const Sim* s, int ncomp, int jmargin) {
   while ((int64_t(1) << lg) < chunk) ++lg;
   BandPlan bp{BandArgs{chunk, 0, 0, jmargin, lg}, 0};
   if (ncomp <= 0) return bp;
-  const size_t node_bytes = (size_t)ncomp * c.Nm * 4 * sizeof(int32_t);   // one r node of one row
+  // one r node of one row: re hi, re lo for every mode, im hi, im lo for the modes m >= 1
+  const size_t node_bytes = (size_t)ncomp * (4 * c.Nm - 2) * sizeof(int32_t);
   const size_t row_bytes = node_bytes * c.Nr;
   int tz = 0, jw = 0;
   if (kBandBudget / row_bytes >= 4) {
@@ -1638,39 +1667,41 @@ pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, vo
   return PIC_OK;
 }
 
-pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa) {
+pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, bool fuse_rho) {
   const size_t G = s->grid_elems();
   int32_t* err = s->at<int32_t>(s->lay.err);
   const pic_config& c = s->cfg;
   if (is_mixed(s)) {
+    fuse_rho = fuse_rho && fuse_current && !wa.on;
     DepArgsF a;
     a.q = (float)c.q;
     a.id_lo = INT32_MIN;
     a.id_hi = INT32_MAX;
-    a.rho = nullptr;
+    a.rho = fuse_rho ? s->at<float2>(s->lay.dep) : nullptr;
     a.J = s->at<float2>(s->lay.dep) + G;
     if (fuse_current) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * G * sizeof(float2), s->stream));
+    if (fuse_rho)   // rho^{n+1} starts from the immobile background
+      PIC_CUDA(cudaMemcpyAsync(a.rho, s->at<float2>(s->lay.rho_ion), G * sizeof(float2), cudaMemcpyDeviceToDevice,
+                               s->stream));
     if (s->np == 0) return PIC_OK;
     const float kq = (float)(c.q * c.dt / (2.0 * c.mass * kC));
     const float kqc = (float)(c.q * c.dt / (2.0 * c.mass));
     const float chdt_dr = (float)(0.5 * kC * c.dt / c.dr);
     const float chdt_dz = (float)(0.5 * kC * c.dt / c.dz);
-    // a half step moves a particle by at most c dt / 2 in r
-    const BandPlan bp = band_plan(s, fuse_current ? 3 : 0, 1 + (int)std::ceil(0.5 * kC * c.dt / c.dr));
+    // a half step moves a particle by at most c dt / 2 in r (a full step, for rho, c dt)
+    const BandPlan bp = band_plan(s, fuse_current ? (fuse_rho ? 4 : 3) : 0,
+                                  1 + (int)std::ceil((fuse_rho ? 1.0 : 0.5) * kC * c.dt / c.dr));
     // E and B (adjacent, 6 x Nm planes) into the r-fastest gather layout
     dim3 tgrid((c.Nz + 31) / 32, (c.Nr + 31) / 32, 6 * c.Nm);
     k_transpose_rz<<<tgrid, dim3(32, 8), 0, s->stream>>>(s->at<float2>(s->lay.E), s->at<float2>(s->lay.ebt), c.Nr,
                                                           c.Nz);
     PIC_LAUNCHED(s);
     const int nblk = (int)((s->np + bp.args.chunk - 1) / bp.args.chunk);
-    if (wa.on)
-      k_gather_push_f32<true><<<nblk, kBandThreads, bp.smem, s->stream>>>(
-          partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.ebt), kq, kqc, chdt_dr, chdt_dz, a,
-          reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args, wa);
-    else
-      k_gather_push_f32<false><<<nblk, kBandThreads, bp.smem, s->stream>>>(
-          partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.ebt), kq, kqc, chdt_dr, chdt_dz, a,
-          reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args, wa);
+    auto* kern = wa.on ? k_gather_push_f32<true, false>
+                       : (fuse_rho ? k_gather_push_f32<false, true> : k_gather_push_f32<false, false>);
+    kern<<<nblk, kBandThreads, bp.smem, s->stream>>>(
+        partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.ebt), kq, kqc, chdt_dr, chdt_dz, a,
+        reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args, wa);
   } else {
     DepArgs a;
     a.q = c.q;
@@ -1735,9 +1766,11 @@ pic_status particles_configure_device() {
   std::lock_guard<std::mutex> lock(mu);
   if (dev >= 0 && dev < 64 && done[dev]) return PIC_OK;
   PIC_CUDA(cudaFuncSetAttribute(k_deposit_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandBudget));
-  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kBandBudget));
-  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kBandBudget));
+  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kBandBudget));
   if (dev >= 0 && dev < 64) done[dev] = true;
   return PIC_OK;

@@ -358,14 +358,17 @@ pic_status step_once(Sim* s, Marks* mk) {
     wa.slot = reinterpret_cast<int32_t*>(s->win.ws + s->win.slot);
     wa.bcnt = reinterpret_cast<int32_t*>(s->win.ws + s->win.bcnt);
   }
+  // mixed forms without a moving window: rho^{n+1} is deposited by the push itself (the
+  // sort that follows only reorders particles)
+  const bool fuse_rho = s->cfg.precision != PIC_FP64 && !wa.on;
   PIC_CUDA(m.mark(0));
-  if ((st = launch_gather_push(s, 1, wa)) != PIC_OK) return st;
+  if ((st = launch_gather_push(s, 1, wa, fuse_rho)) != PIC_OK) return st;
   if (wa.shift && (st = launch_window_inject(s, wa.back_col)) != PIC_OK) return st;
   PIC_CUDA(m.mark(1));
   if (s->sort_interval <= 1 || s->cycle_idx % s->sort_interval == 0)
     if ((st = launch_sort(s)) != PIC_OK) return st;
   PIC_CUDA(m.mark(2));
-  if ((st = deposit_rho_with_background(s)) != PIC_OK) return st;
+  if (!fuse_rho && (st = deposit_rho_with_background(s)) != PIC_OK) return st;
   PIC_CUDA(m.mark(3));
   if ((st = field_step(s, -1, mk, 3)) != PIC_OK) return st;   // marks 4..8
   if (s->win.on) {

@@ -198,7 +198,8 @@ pic_status launch_copy_window(Sim* dst_sim, const char* src, int src_nz, int src
 // ---- launchers (particles.cu) ----
 pic_status launch_sort(Sim* s);
 pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, void* rho_out);
-pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa = WinArgs{});
+// fuse_rho (mixed forms, no moving window): also deposit rho^{n+1} + background at x^{n+1}.
+pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa = WinArgs{}, bool fuse_rho = false);
 pic_status launch_diag(Sim* s, int32_t id_lo, int32_t id_hi, pic_diag* out, double* slice_sigma,
                        int32_t max_slices);
 pic_status build_inv_volume(Sim* s);                        // once, at init
