@@ -678,34 +678,19 @@ __device__ __forceinline__ void fixed_split(float y, int& hi, int& lo) {
   lo = __float2int_rn(fmaf(-f, 65536.f, y));      // y - 65536 f, exact, in [0, 65536)
 }
 
-__device__ __forceinline__ void dep_node_fb(float2* grid_cm, const GeomF& g, const BandF& bd, int comp, int m,
-                                            int j, int i, float wgt, float fold, float vre, float vim,
-                                            const float* invV) {
-  if (j < 0) { j = -1 - j; wgt *= fold; }
-  if (j >= g.Nr) return;
-  if (bd.tile) {
-    int row = i - bd.iz_lo;
-    if (row < 0) row += g.Nz;
-    const int jj = j - bd.j_lo;
-    if (row < bd.TZ && (unsigned)jj < (unsigned)bd.JW) {
-      const float sc = comp == 0 ? bd.scale0 : bd.scale;
-      const int e = ((row * bd.ncomp + comp) * g.Nm + m) * bd.JW + jj;
-      int hr, lr;
-      fixed_split(vre * wgt * sc, hr, lr);
-      atomicAdd(bd.tile + e, hr);
-      atomicAdd(bd.tile + bd.P + e, lr);
-      if (m > 0) {   // mode 0 has a real phase and no imaginary planes
-        const int ei = ((row * bd.ncomp + comp) * (g.Nm - 1) + m - 1) * bd.JW + jj;
-        int hi, li;
-        fixed_split(vim * wgt * sc, hi, li);
-        atomicAdd(bd.tile + 2 * bd.P + ei, hi);
-        atomicAdd(bd.tile + 2 * bd.P + bd.Pim + ei, li);
-      }
-      return;
-    }
+// Fixed-point add of x (re, im) times 2^S to band entry e (imaginary planes: entry ei, modes
+// m >= 1 only).
+__device__ __forceinline__ void band_add(const BandF& bd, int e, int ei, bool im, float sc, float xr, float xi) {
+  int hr, lr;
+  fixed_split(xr * sc, hr, lr);
+  atomicAdd(bd.tile + e, hr);
+  atomicAdd(bd.tile + bd.P + e, lr);
+  if (im) {
+    int hi, li;
+    fixed_split(xi * sc, hi, li);
+    atomicAdd(bd.tile + 2 * bd.P + ei, hi);
+    atomicAdd(bd.tile + 2 * bd.P + bd.Pim + ei, li);
   }
-  const float f = wgt * invV[j];
-  atomicAdd(grid_cm + (size_t)j * g.Nz + i, make_float2(vre * f, vim * f));
 }
 
 // Largest |w| and radial stencil range over particles [b0, b1) (all threads of the CTA;
@@ -817,7 +802,10 @@ __device__ void band_flush(const BandF& bd, const GeomF& g, float2* grid0, const
 }
 
 // deposit of one particle at (iz+fz, x, y) with velocity (vx, vy, vz) [m/s]
-// jc0: band component of J_r (J_theta, J_z follow); rho is band component 0.
+// Deposit of one particle at (iz+fz, x, y) with velocity (vx, vy, vz) [m/s]: rho (band
+// component 0) and/or J (band components jc0 .. jc0+2).  The geometry of each of the 4 nodes
+// (ghost fold, dropped node Nr, band position) is worked out once per node and mode and
+// shared by the components.  One band at most is in use (bR for rho alone, bJ for J).
 __device__ __forceinline__ void deposit_one_f(const GeomF& g, const DepArgsF& a, const float* invV, const BandF& bR,
                               const BandF& bJ, int iz, float fz, float x, float y, float w, float vx, float vy,
                               float vz, bool do_rho, bool do_J, int jc0 = 0) {
@@ -825,14 +813,17 @@ __device__ __forceinline__ void deposit_one_f(const GeomF& g, const DepArgsF& a,
   polar_f(x, y, r, c, s);
   const StencilF st = stencil_f(g, iz, fz, r);
   const float vr = c * vx + s * vy, vt = c * vy - s * vx;
+  const BandF& bd = do_J ? bJ : bR;
   float phr = 1.f, phi = 0.f;   // e^{+i m theta}
   const size_t RZ = (size_t)g.Nr * g.Nz;
+  const int NC = bd.ncomp * g.Nm * bd.JW, NCi = bd.ncomp * (g.Nm - 1) * bd.JW;
   // lanes visit the 4 nodes in an order rotated by the lane index, so that lanes of one
   // cell (which share their nodes) hit different nodes in the same instruction
   const int rot = threadIdx.x & 3;
   for (int m = 0; m < g.Nm; ++m) {
     const float qre = a.q * w * phr, qim = a.q * w * phi;
-    const float fs = (m & 1) ? -1.f : 1.f, fv = -fs;
+    const float fs = (m & 1) ? -1.f : 1.f, fv = -fs;   // ghost-node signs: scalars and z, r and theta
+    const bool im = m > 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int node = (q + rot) & 3;
@@ -840,11 +831,43 @@ __device__ __forceinline__ void deposit_one_f(const GeomF& g, const DepArgsF& a,
       const int i = dz ? st.i1 : st.i0;
       const int j = st.j0 + dj;
       const float wgt = (dz ? st.wz1 : st.wz0) * (dj ? st.wr1 : st.wr0);
-      if (do_rho) dep_node_fb(a.rho + m * RZ, g, bR, 0, m, j, i, wgt, fs, qre, qim, invV);
+      const bool folded = j < 0;   // ghost node r_{-1} = node 0 seen across the axis
+      const int jn = folded ? -1 - j : j;
+      if (jn >= g.Nr) continue;     // node Nr is dropped
+      int e = -1, ei = 0;
+      if (bd.tile) {
+        int row = i - bd.iz_lo;
+        if (row < 0) row += g.Nz;
+        const int jj = jn - bd.j_lo;
+        if (row < bd.TZ && (unsigned)jj < (unsigned)bd.JW) {
+          e = row * NC + m * bd.JW + jj;
+          ei = row * NCi + (m - 1) * bd.JW + jj;
+        }
+      }
+      const size_t goff = (size_t)m * RZ + (size_t)jn * g.Nz + i;
+      const float ws = folded ? wgt * fs : wgt, wv = folded ? wgt * fv : wgt;
+      if (do_rho) {
+        if (e >= 0) {
+          band_add(bd, e, ei, im, bd.scale0, qre * ws, qim * ws);
+        } else {
+          const float f = ws * invV[jn];
+          atomicAdd(a.rho + goff, make_float2(qre * f, qim * f));
+        }
+      }
       if (do_J) {
-        dep_node_fb(a.J + m * RZ, g, bJ, jc0, m, j, i, wgt, fv, qre * vr, qim * vr, invV);
-        dep_node_fb(a.J + g.G + m * RZ, g, bJ, jc0 + 1, m, j, i, wgt, fv, qre * vt, qim * vt, invV);
-        dep_node_fb(a.J + 2 * g.G + m * RZ, g, bJ, jc0 + 2, m, j, i, wgt, fs, qre * vz, qim * vz, invV);
+        const float xr[3] = {qre * vr, qre * vt, qre * vz}, xi[3] = {qim * vr, qim * vt, qim * vz};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const float wk = k < 2 ? wv : ws;
+          if (e >= 0) {
+            const int cc = jc0 + k;
+            band_add(bd, e + cc * g.Nm * bd.JW, ei + cc * (g.Nm - 1) * bd.JW, im, cc == 0 ? bd.scale0 : bd.scale,
+                     xr[k] * wk, xi[k] * wk);
+          } else {
+            const float f = wk * invV[jn];
+            atomicAdd(a.J + k * g.G + goff, make_float2(xr[k] * f, xi[k] * f));
+          }
+        }
       }
     }
     const float nr = phr * c - phi * s, ni = phr * s + phi * c;
