@@ -463,6 +463,9 @@ def run_scan(args):
         sims = list(ex.map(init, range(len(members))))
     # tile sizes per member, one at a time so that the timings do not overlap
     tunings = [s.autotune() for s in sims]
+    # each graph launch runs 2 cycles: sort on one of them (sort interval 2)
+    for s in sims:
+        s.set_sort_interval(min(args.sort_interval, 2))
     setup_s = time.perf_counter() - t0
     batch = bd.Batch(sims, cycles=2)
     batch.launch(max(1, args.warmup // 2 + 1))
