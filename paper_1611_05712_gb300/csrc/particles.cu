@@ -483,6 +483,7 @@ __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __
 
 // ------------------------------------------------------------------ a10: diagnostics
 constexpr int kDiagThreads = 256;
+constexpr double kInvC2 = 1.0 / (kC * kC);   // diagnostics: gamma from u without a float64 division
 constexpr int kMaxSlices = 1 << 16;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -1163,25 +1164,29 @@ __device__ __forceinline__ void split_pair(double u, float& h, float& l) {
   l = (float)(u - (double)h);
 }
 
+// Cells and fractions from x / dr etc. taken as x * (1/dr) (reciprocals from the host): a
+// float64 division is a long sequence on GB300's float64 units, and the product differs by at
+// most one float64 ulp, far below the float fraction's resolution.
 __global__ void k_p64_to_p32(const double* __restrict__ st, int64_t cap, const int32_t* __restrict__ id_in,
-                             PartsF p, int64_t np, int Nz, double dz, double dr) {
+                             PartsF p, int64_t np, int Nz, double inv_dz, double inv_dr) {
+  constexpr double inv_c = 1.0 / kC;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
     int iz, ix, iy;
     float fz, fx, fy;
-    split_cell(st[2 * cap + i] / dz, iz, fz);
+    split_cell(st[2 * cap + i] * inv_dz, iz, fz);
     iz %= Nz;
     if (iz < 0) iz += Nz;
-    split_cell(st[i] / dr, ix, fx);
-    split_cell(st[cap + i] / dr, iy, fy);
+    split_cell(st[i] * inv_dr, ix, fx);
+    split_cell(st[cap + i] * inv_dr, iy, fy);
     p.iz[i] = iz;
     p.fz[i] = fz;
     p.ixy[i] = pack_cells(ix, iy);
     p.fx[i] = fx;
     p.fy[i] = fy;
-    split_pair(st[3 * cap + i] / kC, p.ux[i], p.uxl[i]);
-    split_pair(st[4 * cap + i] / kC, p.uy[i], p.uyl[i]);
-    split_pair(st[5 * cap + i] / kC, p.uz[i], p.uzl[i]);
+    split_pair(st[3 * cap + i] * inv_c, p.ux[i], p.uxl[i]);
+    split_pair(st[4 * cap + i] * inv_c, p.uy[i], p.uyl[i]);
+    split_pair(st[5 * cap + i] * inv_c, p.uz[i], p.uzl[i]);
     p.w[i] = (float)st[6 * cap + i];
     p.id[i] = id_in[i];
   }
@@ -1239,6 +1244,26 @@ struct Acc32 {
   __device__ int32_t id(int64_t i) const { return p.id[i]; }
 };
 
+// Sums of K per-thread values over the CTA (kDiagThreads threads), added to acc[0..K) by
+// one atomic per value and CTA: with a float64 atomic per warp, the adds of all warps
+// serialise on the same K addresses.
+template <int K>
+__device__ __forceinline__ void block_sum_add(const double (&v)[K], double* acc) {
+  __shared__ double part[kDiagThreads / 32][K];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double t = warp_sum(v[k]);
+    if (lane == 0) part[warp][k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double t = 0.0;
+    for (int w = 0; w < kDiagThreads / 32; ++w) t += part[w][threadIdx.x];
+    atomicAdd(acc + threadIdx.x, t);
+  }
+}
+
 // pass 1: sum w, w x, w y, w z, w ux, w uy, w gamma, count
 template <class A>
 __global__ void k_diag_moments(const A a, int64_t np, int32_t lo, int32_t hi, double* acc) {
@@ -1249,19 +1274,46 @@ __global__ void k_diag_moments(const A a, int64_t np, int32_t lo, int32_t hi, do
     if (id < lo || id >= hi) continue;
     double x, y, z, ux, uy, uz, w;
     a.get(i, x, y, z, ux, uy, uz, w);
-    const double gam = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+    const double gam = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) * kInvC2);
     v[0] += w; v[1] += w * x; v[2] += w * y; v[3] += w * z;
     v[4] += w * ux; v[5] += w * uy; v[6] += w * gam; v[7] += 1.0;
   }
-  for (int k = 0; k < 8; ++k) {
-    const double t = warp_sum(v[k]);
-    if ((threadIdx.x & 31) == 0) atomicAdd(acc + k, t);
-  }
+  block_sum_add<8>(v, acc);
 }
 
 // pass 2: centred second moments w dx^2, w dux^2, w dx dux, (y), w dz^2
+// Device-side steps between the passes (one thread), so that the passes chain without a
+// host round trip.  Header of the accumulator block: [0..7] pass-1 sums, [16..20] means,
+// [32..38] pass-2 sums, [48] slice start, [49] slice span, [50] slices, [51] status
+// (0 ok, 1 no weight, 2 sigma_z = 0, 3 too many slices), [52] non-empty slices.
+enum { kDiagMean = 16, kDiagC2 = 32, kDiagZ0 = 48, kDiagSpan = 49, kDiagNs = 50, kDiagStatus = 51, kDiagNe = 52 };
+
+__global__ void k_diag_means(double* acc) {
+  if (acc[7] == 0.0 || !(acc[0] > 0.0)) {
+    acc[kDiagStatus] = 1.0;
+    return;
+  }
+  for (int k = 0; k < 5; ++k) acc[kDiagMean + k] = acc[1 + k] / acc[0];
+}
+
+__global__ void k_diag_slice_setup(double* acc, double slen, int max_slices) {
+  if (acc[kDiagStatus] != 0.0) return;
+  const double sz = sqrt(acc[kDiagC2 + 6] / acc[0]);
+  if (!(sz > 0.0)) {
+    acc[kDiagStatus] = 2.0;
+    return;
+  }
+  const double span = 6.0 * sz;
+  const double ns = ceil(span / slen);
+  acc[kDiagZ0] = acc[kDiagMean + 2] - 3.0 * sz;
+  acc[kDiagSpan] = span;
+  acc[kDiagNs] = ns;
+  if (ns > max_slices) acc[kDiagStatus] = 3.0;
+}
+
 template <class A>
 __global__ void k_diag_central(const A a, int64_t np, int32_t lo, int32_t hi, const double* mean, double* acc) {
+  if (mean[kDiagStatus - kDiagMean] != 0.0) return;
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1275,18 +1327,26 @@ __global__ void k_diag_central(const A a, int64_t np, int32_t lo, int32_t hi, co
     v[3] += w * (dy * dy); v[4] += w * (duy * duy); v[5] += w * (dy * duy);
     v[6] += w * (dz * dz);
   }
-  for (int k = 0; k < 7; ++k) {
-    const double t = warp_sum(v[k]);
-    if ((threadIdx.x & 31) == 0) atomicAdd(acc + k, t);
-  }
+  block_sum_add<7>(v, acc);
 }
 
-// pass 3 (stage 0): per-slice sum w and sum w gamma; (stage 1): sum w (gamma - gbar_s)^2
+// pass 3 (stage 0): per-slice sum w and sum w gamma; (stage 1): sum w (gamma - gbar_s)^2.
+// Each thread takes a contiguous range of particles and adds a run of equal slices with one
+// atomic: particles are cell-sorted, so runs are long and the atomics on the few slices of
+// a beam do not pile up.
 template <class A>
-__global__ void k_diag_slices(const A a, int64_t np, int32_t lo, int32_t hi, double zstart, double zspan,
-                              double slen, int ns, double* sw, double* sg, double* sv, int stage) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-       i += (int64_t)gridDim.x * blockDim.x) {
+__global__ void k_diag_slices(const A a, int64_t np, int32_t lo, int32_t hi, const double* hdr, double slen,
+                              double* sw, double* sg, double* sv, int stage) {
+  if (hdr[kDiagStatus] != 0.0) return;
+  const double zstart = hdr[kDiagZ0], zspan = hdr[kDiagSpan];
+  const int ns = (int)hdr[kDiagNs];
+  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+  const int64_t per = (np + nthr - 1) / nthr;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t i0 = t * per, i1 = min(np, i0 + per);
+  int run = -1;
+  double rw = 0.0, rg = 0.0;
+  for (int64_t i = i0; i < i1; ++i) {
     const int32_t id = a.id(i);
     if (id < lo || id >= hi) continue;
     double x, y, z, ux, uy, uz, w;
@@ -1295,16 +1355,54 @@ __global__ void k_diag_slices(const A a, int64_t np, int32_t lo, int32_t hi, dou
     if (!(d >= 0.0 && d < zspan)) continue;
     int k = (int)floor(d / slen);
     if (k > ns - 1) k = ns - 1;
-    const double gam = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+    const double gam = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) * kInvC2);
+    if (k != run) {
+      if (run >= 0) {
+        if (stage == 0) {
+          atomicAdd(sw + run, rw);
+          atomicAdd(sg + run, rg);
+        } else {
+          atomicAdd(sv + run, rw);
+        }
+      }
+      run = k;
+      rw = 0.0;
+      rg = 0.0;
+    }
     if (stage == 0) {
-      atomicAdd(sw + k, w);
-      atomicAdd(sg + k, w * gam);
+      rw += w;
+      rg += w * gam;
     } else {
-      const double gb = sg[k] / sw[k];
-      const double dg = gam - gb;
-      atomicAdd(sv + k, w * (dg * dg));
+      const double dg = gam - sg[k] / sw[k];
+      rw += w * (dg * dg);
     }
   }
+  if (run >= 0) {
+    if (stage == 0) {
+      atomicAdd(sw + run, rw);
+      atomicAdd(sg + run, rg);
+    } else {
+      atomicAdd(sv + run, rw);
+    }
+  }
+}
+
+// Per-slice std of gamma of the non-empty slices, in slice order, into out[0 .. ne) (one CTA
+// of 1024 threads; ranks by a block scan); ne into the header.
+__global__ void __launch_bounds__(1024) k_diag_slice_compact(double* hdr, const double* sw, const double* sv,
+                                                              double* out) {
+  if (hdr[kDiagStatus] != 0.0) return;
+  const int ns = (int)hdr[kDiagNs];
+  int32_t base = 0;
+  for (int k0 = 0; k0 < ns; k0 += 1024) {
+    const int k = k0 + threadIdx.x;
+    const bool ne = k < ns && sw[k] > 0.0;
+    int32_t tot;
+    const int32_t pos = base + block_exclusive_scan(ne ? 1 : 0, &tot);
+    if (ne) out[pos] = sqrt(sv[k] / sw[k]);
+    base += tot;
+  }
+  if (threadIdx.x == 0) hdr[kDiagNe] = (double)base;
 }
 
 inline int pgrid(int64_t n) {
@@ -1312,6 +1410,8 @@ inline int pgrid(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
+// The passes chain on the device; one copy of the header and the slice values and one
+// synchronisation at the end.
 template <class A>
 pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* out, double* slice_sigma,
                     int32_t max_slices) {
@@ -1321,64 +1421,58 @@ pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* ou
   double* sg = sw + kMaxSlices;
   double* sv = sg + kMaxSlices;
   PIC_CUDA(cudaMemsetAsync(acc, 0, 64 * sizeof(double), s->stream));
-  const int grid = pgrid(np);
+  PIC_CUDA(cudaMemsetAsync(sw, 0, 3 * sizeof(double) * kMaxSlices, s->stream));
+  const int grid = std::min(pgrid(np), 8 * 152);   // one atomic per CTA and sum
   if (np > 0) {
     k_diag_moments<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, acc);
     PIC_LAUNCHED(s);
   }
-  double h[8];
-  PIC_CUDA(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, s->stream));
+  k_diag_means<<<1, 1, 0, s->stream>>>(acc);
+  PIC_LAUNCHED(s);
+  if (np > 0) {
+    k_diag_central<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, acc + kDiagMean, acc + kDiagC2);
+    PIC_LAUNCHED(s);
+  }
+  k_diag_slice_setup<<<1, 1, 0, s->stream>>>(acc, kSliceLen, kMaxSlices);
+  PIC_LAUNCHED(s);
+  if (np > 0) {
+    for (int stage = 0; stage < 2; ++stage) {
+      k_diag_slices<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, acc, kSliceLen, sw, sg, sv, stage);
+      PIC_LAUNCHED(s);
+    }
+  }
+  k_diag_slice_compact<<<1, 1024, 0, s->stream>>>(acc, sw, sv, sg);   // sg is free after stage 1
+  PIC_LAUNCHED(s);
+  if (!s->diag_host) PIC_CUDA(cudaMallocHost(&s->diag_host, (64 + (size_t)kMaxSlices) * sizeof(double)));
+  double* h = s->diag_host;
+  const double* sig = h + 64;
+  PIC_CUDA(cudaMemcpyAsync(h, acc, 64 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  PIC_CUDA(cudaMemcpyAsync(h + 64, sg, kMaxSlices * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   PIC_CUDA(cudaStreamSynchronize(s->stream));
   *out = pic_diag{};
   out->n_particles = (int32_t)h[7];
   out->W = h[0];
-  if (h[7] == 0 || h[0] <= 0.0) return PIC_OK;
-  double mean[5] = {h[1] / h[0], h[2] / h[0], h[3] / h[0], h[4] / h[0], h[5] / h[0]};
-  out->x_mean = mean[0]; out->y_mean = mean[1]; out->z_mean = mean[2];
+  const int status = (int)h[kDiagStatus];
+  if (status == 1) return PIC_OK;
+  out->x_mean = h[kDiagMean]; out->y_mean = h[kDiagMean + 1]; out->z_mean = h[kDiagMean + 2];
   out->gamma_mean = h[6] / h[0];
-  double* dmean = acc + 16;
-  PIC_CUDA(cudaMemcpyAsync(dmean, mean, sizeof(mean), cudaMemcpyHostToDevice, s->stream));
-  k_diag_central<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, dmean, acc + 32);
-  PIC_LAUNCHED(s);
-  double c2[7];
-  PIC_CUDA(cudaMemcpyAsync(c2, acc + 32, sizeof(c2), cudaMemcpyDeviceToHost, s->stream));
-  PIC_CUDA(cudaStreamSynchronize(s->stream));
   const double W = h[0];
+  const double* c2 = h + kDiagC2;
   const double xx = c2[0] / W, uu = c2[1] / W, xu = c2[2] / W;
   const double yy = c2[3] / W, vv = c2[4] / W, yv = c2[5] / W;
   out->emit_nx = std::sqrt(std::max(xx * uu - xu * xu, 0.0)) / kC;
   out->emit_ny = std::sqrt(std::max(yy * vv - yv * yv, 0.0)) / kC;
-  const double sz = std::sqrt(c2[6] / W);
-  out->sigma_z = sz;
-  if (!(sz > 0.0)) return PIC_OK;
-  const double span = 6.0 * sz;
-  const double ns_d = std::ceil(span / kSliceLen);
-  if (ns_d > kMaxSlices) {
-    set_error("diagnostics: %g slices exceed the maximum %d", ns_d, kMaxSlices);
+  out->sigma_z = std::sqrt(c2[6] / W);
+  if (status == 2) return PIC_OK;
+  if (status == 3) {
+    set_error("diagnostics: %g slices exceed the maximum %d", h[kDiagNs], kMaxSlices);
     return PIC_ERR_ARG;
   }
-  const int ns = (int)ns_d;
-  const double zstart = mean[2] - 3.0 * sz;
-  PIC_CUDA(cudaMemsetAsync(sw, 0, 3 * sizeof(double) * kMaxSlices, s->stream));
-  k_diag_slices<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, zstart, span, kSliceLen, ns, sw,
-                                                          sg, sv, 0);
-  PIC_LAUNCHED(s);
-  k_diag_slices<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, zstart, span, kSliceLen, ns, sw,
-                                                          sg, sv, 1);
-  PIC_LAUNCHED(s);
-  std::vector<double> hw(ns), hv(ns);
-  PIC_CUDA(cudaMemcpyAsync(hw.data(), sw, ns * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  PIC_CUDA(cudaMemcpyAsync(hv.data(), sv, ns * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  PIC_CUDA(cudaStreamSynchronize(s->stream));
-  int ne = 0;
+  const int ne = (int)h[kDiagNe];
   double sum = 0.0;
-  for (int k = 0; k < ns; ++k) {
-    if (hw[k] > 0.0) {
-      const double sg_k = std::sqrt(hv[k] / hw[k]);
-      if (slice_sigma && ne < max_slices) slice_sigma[ne] = sg_k;
-      sum += sg_k;
-      ++ne;
-    }
+  for (int k = 0; k < ne; ++k) {
+    if (slice_sigma && k < max_slices) slice_sigma[k] = sig[k];
+    sum += sig[k];
   }
   out->n_slices = ne;
   out->sigma_gamma_mean = ne ? sum / ne : 0.0;
@@ -1763,7 +1857,7 @@ pic_status launch_diag(Sim* s, int32_t lo, int32_t hi, pic_diag* out, double* sl
 pic_status launch_particles_in(Sim* s, const int32_t* id_dev, int64_t n) {
   if (n == 0) return PIC_OK;
   k_p64_to_p32<<<pgrid(n), 256, 0, s->stream>>>(s->at<double>(s->lay.stage64), s->cfg.np_capacity, id_dev,
-                                                 partsf_of(s, s->cur), n, s->cfg.Nz, s->cfg.dz, s->cfg.dr);
+                                                 partsf_of(s, s->cur), n, s->cfg.Nz, 1.0 / s->cfg.dz, 1.0 / s->cfg.dr);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }

@@ -620,7 +620,9 @@ pic_status pic_copy_window(pic_sim* src_sim, int32_t buffer_id, int32_t src_z0, 
 }
 
 pic_status pic_destroy(pic_sim* sim) {
-  delete reinterpret_cast<Sim*>(sim);
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  if (s && s->diag_host) cudaFreeHost(s->diag_host);
+  delete s;
   return PIC_OK;
 }
 

@@ -121,6 +121,7 @@ struct Sim {
     unsigned char b[128];
   } tmaps[2 * kMaxModes * 3][3];
   WindowState win;
+  double* diag_host = nullptr;   // pinned host copy of the diagnostics results (first use)
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   size_t grid_elems() const { return (size_t)cfg.Nm * cfg.Nr * cfg.Nz; }
