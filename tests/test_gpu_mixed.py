@@ -5,8 +5,8 @@ float accumulation, FP32 particles with z relative to its cell, FP64 setup and
 diagnostics.  Stated per-field tolerances (max |gpu - oracle| / max |oracle|):
 transforms and PSATD 3e-5 per (component, mode) on random inputs; one full cycle from an
 identical state 1e-4 per field, particle positions 1e-5 (momenta 1e-4) per array.  The
-spec criterion -- beam emittance and slice energy spread within 1e-4 relative of
-the FP64 path after many cycles -- is checked against the FP64 GPU path.
+beam-quality criterion of the mixed form -- beam emittance and slice energy spread within
+1e-4 relative of the FP64 path after many cycles -- is checked against the FP64 GPU path.
 """
 import numpy as np
 import pytest
@@ -156,7 +156,7 @@ def test_mixed_full_cycle_plasma_beam_256x64():
 
 
 def test_mixed_beam_quality_within_1e4_of_fp64_after_many_cycles():
-    """North-star criterion: emittance and slice energy spread of the beam in the mixed form
+    """Beam-quality criterion: emittance and slice energy spread of the beam in the mixed form
     within 1e-4 relative of the FP64 form after 100 cycles of the 256 x 64 plasma + beam case
     (absolute emittance difference below 1e-12 m rad where the FP64 value is tiny)."""
     w = W.plasma_beam_small()
