@@ -679,6 +679,7 @@ def run_window(args):
         sim = bd.Sim.from_workload(w, P, npl, beams, precision=prec, capacity=n + reserve)
         if mixed:
             sim.autotune()
+            sim.set_sort_interval(args.sort_interval)
         return sim
 
     s = make()

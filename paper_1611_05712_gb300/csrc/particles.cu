@@ -1133,16 +1133,18 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
       if (fx >= 1.f) { fx = 0.f; ix += 1; }
       if (fy >= 1.f) { fy = 0.f; iy += 1; }
     }
+    bool removed = false;
     if (WIN && (zeta_old + dzc) + dzc - (wa.shift ? 1.f : 0.f) < 0.f) {
       p.w[i] = 0.f;   // left through the back edge: inactive from now on
       uxh = uyh = uzh = 0.f;
       uxl = uyl = uzl = 0.f;
       win_mark(wa, p.id[i], i);
+      removed = true;
     }
     p.ixy[i] = pack_cells(ix, iy); p.fx[i] = fx; p.fy[i] = fy; p.fz[i] = fz; p.iz[i] = iz;
     p.ux[i] = uxh; p.uy[i] = uyh; p.uz[i] = uzh;
     p.uxl[i] = uxl; p.uyl[i] = uyl; p.uzl[i] = uzl;
-    if (RHO)   // rho^{n+1} at x^{n+1}
+    if (RHO && !removed)   // rho^{n+1} at x^{n+1} (a removed particle has left)
       deposit_one_f(g, dep, invV, band, none, iz, fz, (float)ix + fx, (float)iy + fy, w, 0.f, 0.f, 0.f, true,
                     false);
   }
@@ -1621,9 +1623,12 @@ __global__ void __launch_bounds__(kWinBlock) k_win_inject(int32_t* flag, int32_t
   }
 }
 
+// With dep.rho set, a placed particle also deposits its rho (global atomics: a column's
+// worth of particles), for a cycle whose push deposited rho^{n+1} already.
 __global__ void __launch_bounds__(kWinBlock) k_win_inject_f32(int32_t* flag, int32_t* bcnt, const int32_t* slot,
                                                                const int32_t* bstart, int64_t n, PartsF p, WinTplF t,
-                                                               const int32_t* fresh, int32_t n_fresh) {
+                                                               const int32_t* fresh, int32_t n_fresh, GeomF g,
+                                                               DepArgsF dep, const float* invV) {
   if (bstart[blockIdx.x] >= n_fresh || bstart[blockIdx.x + 1] == bstart[blockIdx.x]) return;   // no slot used
   int v;
   const int32_t r = win_rank(flag, bcnt, bstart, n, n_fresh, v);
@@ -1634,6 +1639,12 @@ __global__ void __launch_bounds__(kWinBlock) k_win_inject_f32(int32_t* flag, int
     p.fx[i] = t.fx[src]; p.fy[i] = t.fy[src]; p.w[i] = t.w[src];
     p.ux[i] = 0.f; p.uy[i] = 0.f; p.uz[i] = 0.f;
     p.uxl[i] = 0.f; p.uyl[i] = 0.f; p.uzl[i] = 0.f;
+    if (dep.rho) {
+      const BandF none{nullptr, 0, 0, 0, 0, 0, 1.f, 1.f, 0, 0, 1};
+      const int32_t c = t.ixy[src];
+      deposit_one_f(g, dep, invV, none, none, t.iz[src], t.fz[src], (float)cell_x(c) + t.fx[src],
+                    (float)cell_y(c) + t.fy[src], t.w[src], 0.f, 0.f, 0.f, true, false);
+    }
   }
 }
 
@@ -1789,7 +1800,7 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, b
   int32_t* err = s->at<int32_t>(s->lay.err);
   const pic_config& c = s->cfg;
   if (is_mixed(s)) {
-    fuse_rho = fuse_rho && fuse_current && !wa.on;
+    fuse_rho = fuse_rho && fuse_current;
     DepArgsF a;
     a.q = (float)c.q;
     a.id_lo = INT32_MIN;
@@ -1814,7 +1825,7 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, b
                                                           c.Nz);
     PIC_LAUNCHED(s);
     const int nblk = (int)((s->np + bp.args.chunk - 1) / bp.args.chunk);
-    auto* kern = wa.on ? k_gather_push_f32<true, false>
+    auto* kern = wa.on ? (fuse_rho ? k_gather_push_f32<true, true> : k_gather_push_f32<true, false>)
                        : (fuse_rho ? k_gather_push_f32<false, true> : k_gather_push_f32<false, false>);
     kern<<<nblk, kBandThreads, bp.smem, s->stream>>>(
         partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.ebt), kq, kqc, chdt_dr, chdt_dz, a,
@@ -1888,6 +1899,8 @@ pic_status particles_configure_device() {
   PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kBandBudget));
   PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kBandBudget));
+  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kBandBudget));
   if (dev >= 0 && dev < 64) done[dev] = true;
   return PIC_OK;
@@ -1971,7 +1984,7 @@ pic_status launch_window_mark_all(Sim* s) {
   return PIC_OK;
 }
 
-pic_status launch_window_inject(Sim* s, int column) {
+pic_status launch_window_inject(Sim* s, int column, bool deposit_rho) {
   WindowState& w = s->win;
   const int32_t c0 = w.col_start_host[column], n_fresh = w.col_start_host[column + 1] - c0;
   int32_t* flag = reinterpret_cast<int32_t*>(w.ws + w.flag);
@@ -1985,9 +1998,17 @@ pic_status launch_window_inject(Sim* s, int column) {
   k_win_bscan<<<1, kWinBlock, 0, s->stream>>>(bcnt, bstart, nb, n_fresh, dropped);
   PIC_LAUNCHED(s);
   if (n_fresh == 0) return PIC_OK;
-  if (is_mixed(s))
+  if (is_mixed(s)) {
+    DepArgsF a;
+    a.q = (float)s->cfg.q;
+    a.id_lo = INT32_MIN;
+    a.id_hi = INT32_MAX;
+    a.rho = deposit_rho ? s->at<float2>(s->lay.dep) : nullptr;
+    a.J = nullptr;
     k_win_inject_f32<<<nb, kWinBlock, 0, s->stream>>>(flag, bcnt, slot, bstart, w.n_ids, partsf_of(s, s->cur),
-                                                       win_tplf(s), fresh, n_fresh);
+                                                       win_tplf(s), fresh, n_fresh, geomf_of(s), a,
+                                                       reinterpret_cast<const float*>(inv_volume(s)));
+  }
   else
     k_win_inject<<<nb, kWinBlock, 0, s->stream>>>(flag, bcnt, slot, bstart, w.n_ids, parts_of(s, s->cur), win_tpl(s),
                                                    fresh, n_fresh);

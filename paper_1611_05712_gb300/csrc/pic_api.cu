@@ -358,12 +358,12 @@ pic_status step_once(Sim* s, Marks* mk) {
     wa.slot = reinterpret_cast<int32_t*>(s->win.ws + s->win.slot);
     wa.bcnt = reinterpret_cast<int32_t*>(s->win.ws + s->win.bcnt);
   }
-  // mixed forms without a moving window: rho^{n+1} is deposited by the push itself (the
-  // sort that follows only reorders particles)
-  const bool fuse_rho = s->cfg.precision != PIC_FP64 && !wa.on;
+  // mixed forms: rho^{n+1} is deposited by the push itself (the sort that follows only
+  // reorders particles); particles the moving window injects deposit theirs as they are placed
+  const bool fuse_rho = s->cfg.precision != PIC_FP64;
   PIC_CUDA(m.mark(0));
   if ((st = launch_gather_push(s, 1, wa, fuse_rho)) != PIC_OK) return st;
-  if (wa.shift && (st = launch_window_inject(s, wa.back_col)) != PIC_OK) return st;
+  if (wa.shift && (st = launch_window_inject(s, wa.back_col, fuse_rho)) != PIC_OK) return st;
   PIC_CUDA(m.mark(1));
   if (s->sort_interval <= 1 || s->cycle_idx % s->sort_interval == 0)
     if ((st = launch_sort(s)) != PIC_OK) return st;

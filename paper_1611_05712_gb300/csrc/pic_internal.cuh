@@ -199,7 +199,7 @@ pic_status launch_copy_window(Sim* dst_sim, const char* src, int src_nz, int src
 // ---- launchers (particles.cu) ----
 pic_status launch_sort(Sim* s);
 pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, void* rho_out);
-// fuse_rho (mixed forms, no moving window): also deposit rho^{n+1} + background at x^{n+1}.
+// fuse_rho (mixed forms): also deposit rho^{n+1} + background at x^{n+1}.
 pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa = WinArgs{}, bool fuse_rho = false);
 pic_status launch_diag(Sim* s, int32_t id_lo, int32_t id_hi, pic_diag* out, double* slice_sigma,
                        int32_t max_slices);
@@ -218,8 +218,9 @@ pic_status launch_window_reserve(Sim* s, int64_t n_reserve);
 pic_status window_take_template(Sim* s, int32_t* keys_host);
 // Record every inactive particle for the injections (flag, slot, per-block count).
 pic_status launch_window_mark_all(Sim* s);
-// Template of column `column` into the inactive particles, smallest id first.
-pic_status launch_window_inject(Sim* s, int column);
+// Template of column `column` into the inactive particles, smallest id first; with
+// deposit_rho (mixed forms, whose push deposited rho^{n+1}) the placed particles' rho too.
+pic_status launch_window_inject(Sim* s, int column, bool deposit_rho);
 // Departing column removed from E, B: real space zeroed now; the subtraction of its transform
 // from Eh, Bh is left pending (applied by the next PSATD or by launch_window_flush).
 pic_status launch_window_clear(Sim* s, int column);
