@@ -31,6 +31,10 @@ FP64_PROBE_TFLOPS = 1.1947                     # FMA-loop probe on this pool's G
 # DRAM bytes per FP64 DHT launch (k_gemm<double>) on this workload, from one ncu capture of
 # the current kernel (forward 71.42 + 27.50 MB, inverse 106.87 + 60.50 MB, mean of the two)
 DHT_F64_TRAFFIC_BYTES = (71.424 + 27.501568 + 106.872064 + 60.499968) / 2 * 1e6
+HBM_GBS = 6760.9                                # MEASURED_PEAKS.json copy bandwidth
+# DRAM bytes of one k_gather_push_f32<false, true> launch at cfg2 (dram__bytes_read.sum +
+# dram__bytes_write.sum, profiles/k_gather_push_f32__wake_2048x256_m2_mixed.md)
+PUSH_F32_TRAFFIC_BYTES = (148.93184 + 41.889792) * 1e6
 
 
 def parse():
@@ -280,6 +284,23 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe nominal "
                                    "1.25 TFLOP/s); FMA probe measured 1.195 TFLOP/s",
                     "share_of_step": share}
+    if mixed:
+        # the particle stage (transpose of E, B to the gather layout, then gather, push and the J
+        # and rho deposits): algorithmic bytes per cycle = the transpose's read and write of the
+        # 6 Nm field planes + each particle's FP32 state read (52 B) and written (44 B) + the field
+        # planes read by the gathers + the 4 deposit grids written
+        G = w.Nm * w.Nr * w.Nz
+        bytes_alg = 2 * 6 * G * 8 + n * (52 + 44) + 6 * G * 8 + 4 * G * 8
+        gp_s = stage_ms["gather_push"] / args.steps * 1e-3
+        ach = bytes_alg / gp_s / 1e9
+        roofline_particles = {
+            "bound": "hbm", "achieved": ach, "peak": HBM_GBS, "unit": "GB/s", "frac": ach / HBM_GBS,
+            "traffic": PUSH_F32_TRAFFIC_BYTES if (w.Nz, w.Nr, w.Nm, n) == (2048, 256, 2, 1348576) else None,
+            "kernel": "k_transpose_rz + k_gather_push_f32 (gather, push, J and rho deposits)",
+            "peak_source": "of measured: hbm copy 6760.9 GB/s",
+            "share_of_step": stage_ms["gather_push"] / sum(stage_ms.values()),
+            "note": "bound by instruction issue (67 % issue-active at 47 % of the warp slots, "
+                    "profiles/k_gather_push_f32__wake_2048x256_m2_mixed.md), not by DRAM"}
     out = {"steps_per_s": steps_per_s, "ms_per_step": el_ms / args.steps,
            "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
@@ -287,6 +308,8 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
                      bd.PIC_MIXED_BF16X6: "f32+bf16x6"}[prec]}
     if tuning is not None:
         out["tuning"] = tuning
+    if mixed:
+        out["roofline_particles"] = roofline_particles
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -394,7 +417,8 @@ def run_ours(args):
                 "ms_per_step": mx["ms_per_step"], "particle_updates_per_s": mx["steps_per_s"] * n,
                 "speedup_vs_fp64": mx["steps_per_s"] / head["steps_per_s"],
                 "stage_ms_per_step": mx["stage_ms_per_step"], "roofline": mx["roofline"], "e2e": mx["e2e"],
-                "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"], "tuning": mx.get("tuning")}
+                "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"], "tuning": mx.get("tuning"),
+                "roofline_particles": mx.get("roofline_particles")}
             if acc:
                 line[key]["accuracy_vs_fp64"] = acc[form]
         if acc:
