@@ -205,9 +205,10 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
     mixed = prec != bd.PIC_FP64
     sim = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}", precision=prec)
     wit_lo, wit_hi = beams[-1][0], beams[-1][1]
+    if mixed:   # the sort interval first: the chunk tuning times that many cycles' particle passes
+        sim.set_sort_interval(args.sort_interval)
     tuning = sim.autotune() if mixed else None   # untimed: tile sizes for this workload
     if mixed:
-        sim.set_sort_interval(args.sort_interval)
         tuning["sort_interval"] = args.sort_interval
     sim.step(args.warmup)
     sim.sync()
@@ -486,10 +487,10 @@ def run_scan(args):
     with cf.ThreadPoolExecutor(max_workers=16) as ex:
         sims = list(ex.map(init, range(len(members))))
     # tile sizes per member, one at a time so that the timings do not overlap
-    tunings = [s.autotune() for s in sims]
     # each graph launch runs 2 cycles: sort on one of them (sort interval 2)
     for s in sims:
         s.set_sort_interval(min(args.sort_interval, 2))
+    tunings = [s.autotune() for s in sims]
     setup_s = time.perf_counter() - t0
     batch = bd.Batch(sims, cycles=2)
     batch.launch(max(1, args.warmup // 2 + 1))
@@ -702,8 +703,8 @@ def run_window(args):
     def make():
         sim = bd.Sim.from_workload(w, P, npl, beams, precision=prec, capacity=n + reserve)
         if mixed:
-            sim.autotune()
             sim.set_sort_interval(args.sort_interval)
+            sim.autotune()
         return sim
 
     s = make()
