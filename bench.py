@@ -34,7 +34,7 @@ DHT_F64_TRAFFIC_BYTES = (71.424 + 27.501568 + 106.872064 + 60.499968) / 2 * 1e6
 HBM_GBS = 6760.9                                # MEASURED_PEAKS.json copy bandwidth
 # DRAM bytes of one k_gather_push_f32<false, true> launch at cfg2 (dram__bytes_read.sum +
 # dram__bytes_write.sum, profiles/k_gather_push_f32__wake_2048x256_m2_mixed.md)
-PUSH_F32_TRAFFIC_BYTES = (148.93184 + 41.889792) * 1e6
+PUSH_F32_TRAFFIC_BYTES = (148.891136 + 42.008832) * 1e6
 
 
 def parse():
