@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "mixed", "bf16"], default="fp64",
                     help="fp64: every stage in float64; mixed: float grids and particles, "
                          "3-term TF32 DHT on tcgen05; bf16: the same with the 6-product BF16 DHT")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-form comparison")
     ap.add_argument("--accuracy-cycles", type=int, default=2000,
@@ -195,7 +195,6 @@ def run_reference(args):
 def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
     """Set one simulation up (untimed), warm up, time args.steps cycles with CUDA events
     between the stages, then time args.e2e_steps cycles end to end through the C ABI."""
-    import ctypes
 
     import numpy as np
     import torch
@@ -231,17 +230,20 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
     el_ms = reduce_max(total_ms, dist, dev)
     steps_per_s = weak_throughput(args.steps, world, el_ms)
 
-    # end to end through the C ABI with host buffers: H2D of the step's particles from
-    # pinned memory, one cycle, D2H of the witness-beam diagnostics
+    # end to end through the C ABI with host buffers: every cycle takes a particle set
+    # copied from pinned host memory, steps once and reads the witness-beam diagnostics
+    # back; the copy of the next cycle's set is staged on the library's copy stream while
+    # the current cycle computes (pic_stage_particles / pic_take_particles)
     pinned = {k: torch.from_numpy(np.ascontiguousarray(P[k])).pin_memory() for k in bd.SOA}
-    pinned_id = torch.from_numpy(P["id"]).pin_memory()
-    ptrs = (ctypes.c_void_p * 7)(*[pinned[k].data_ptr() for k in bd.SOA])
+    pinned["id"] = torch.from_numpy(np.ascontiguousarray(P["id"], dtype=np.int32)).pin_memory()
     n_slices = 0
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        bd._check(sim.lib.pic_write_particles(sim.h, ptrs, ctypes.c_void_p(pinned_id.data_ptr()), n, 1),
-                  "pic_write_particles")
+    sim.stage_particles(pinned)
+    for k in range(args.e2e_steps):
+        sim.take_particles()
+        if k + 1 < args.e2e_steps:
+            sim.stage_particles(pinned)
         sim.step(1)
         d = sim.diagnostics(wit_lo, wit_hi)
         n_slices = d["n_slices"]

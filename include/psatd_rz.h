@@ -159,6 +159,31 @@ pic_status pic_read_particles(pic_sim* sim, double* const soa[7], int32_t* id, i
 /* Number of particles currently held. */
 pic_status pic_num_particles(pic_sim* sim, int64_t* n);
 
+/* Staged particle input (data movement only, no step of the method): the host-to-device
+ * copy of the next particle set runs on an internal copy stream while the cycles queued
+ * before it compute, for callers that hand the library a new particle set every cycle.
+ *
+ * pic_stage_bytes: device bytes a staging buffer for n particles needs (7 float64 arrays
+ * and the int32 ids, each array padded to a multiple of 32 elements).  Errors: PIC_ERR_ARG.
+ *
+ * pic_stage_particles: start copying n particles (layout of pic_write_particles; soa and
+ * id in host memory, page-locked for the copy to be asynchronous) into `staging`, a device
+ * buffer of >= pic_stage_bytes(n) bytes, 256-byte aligned, owned by the caller and left
+ * untouched by it until pic_take_particles has returned.  Returns without waiting; the copy
+ * starts once the previous pic_take_particles of this handle has read its staging buffer.
+ * The host arrays must stay valid and unchanged until pic_take_particles returns.
+ * Errors: PIC_ERR_ARG (n < 0 or > capacity, NULL pointers, staging too small or misaligned),
+ * PIC_ERR_STATE (a staged set is waiting to be taken), PIC_ERR_CUDA.
+ *
+ * pic_take_particles: wait on the host for the staged copy, then replace all particles by
+ * the staged set, stream-ordered on the handle's stream (the mixed forms convert straight
+ * from the staging buffer), exactly as pic_write_particles with the same arrays would.
+ * Errors: PIC_ERR_STATE (nothing staged), PIC_ERR_CUDA. */
+pic_status pic_stage_bytes(int64_t n, size_t* bytes);
+pic_status pic_stage_particles(pic_sim* sim, const double* const soa[7], const int32_t* id, int64_t n,
+                               void* staging, size_t staging_bytes);
+pic_status pic_take_particles(pic_sim* sim);
+
 /* Immobile neutralising background: rho_ion = -rho(particles with id < n_neutral). */
 pic_status pic_init_background(pic_sim* sim, int32_t n_neutral);
 

@@ -84,6 +84,9 @@ def load():
         "pic_write_particles": [P, PP, P, I64, I32],
         "pic_read_particles": [P, PP, P, I64, I32],
         "pic_num_particles": [P, ctypes.POINTER(I64)],
+        "pic_stage_bytes": [I64, ctypes.POINTER(SZ)],
+        "pic_stage_particles": [P, PP, P, I64, P, SZ],
+        "pic_take_particles": [P],
         "pic_init_background": [P, I32],
         "pic_add_beam_fields": [P, I32, I32, D],
         "pic_init_fields": [P],
@@ -208,6 +211,42 @@ class Sim:
         _check(self.lib.pic_read_particles(self.h, ptrs, ctypes.c_void_p(out["id"].ctypes.data), n, 1),
                "pic_read_particles")
         return out
+
+    # -- staged particle input ---------------------------------------------------------
+    def stage_particles(self, p: dict):
+        """Start the host-to-device copy of particle set p (host float64 arrays x..w and
+        int32 id: numpy arrays or CPU torch tensors, page-locked for an asynchronous copy)
+        into a device staging buffer on the handle's copy stream (pic_stage_particles).
+        The arrays are kept alive here until take_particles."""
+        import torch
+
+        def host(a, dt):
+            if isinstance(a, torch.Tensor):
+                if a.device.type != "cpu" or a.dtype != dt[1]:
+                    raise TypeError("stage_particles wants CPU tensors of the particle dtypes")
+                a = a.contiguous()
+                return a, a.data_ptr()
+            a = np.ascontiguousarray(a, dtype=dt[0])
+            return a, a.ctypes.data
+
+        n = len(p["x"])
+        arrs = [host(p[k], (np.float64, torch.float64)) for k in SOA]
+        ids = host(p["id"], (np.int32, torch.int32))
+        nb = ctypes.c_size_t()
+        _check(self.lib.pic_stage_bytes(n, ctypes.byref(nb)), "pic_stage_bytes")
+        buf = getattr(self, "_stage_buf", None)
+        if buf is None or buf.numel() < nb.value + 256:
+            buf = self._stage_buf = torch.empty(nb.value + 256, dtype=torch.uint8, device=self.device)
+        ptr = (buf.data_ptr() + 255) // 256 * 256
+        ptrs = (ctypes.c_void_p * 7)(*[a[1] for a in arrs])
+        _check(self.lib.pic_stage_particles(self.h, ptrs, ctypes.c_void_p(ids[1]), n, ctypes.c_void_p(ptr),
+                                            nb.value), "pic_stage_particles")
+        self._staged = (arrs, ids)
+
+    def take_particles(self):
+        """Replace all particles by the staged set (pic_take_particles)."""
+        _check(self.lib.pic_take_particles(self.h), "pic_take_particles")
+        self._staged = None
 
     # -- initial state ----------------------------------------------------------------
     # -- moving window ---------------------------------------------------------------

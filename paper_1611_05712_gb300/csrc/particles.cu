@@ -1864,11 +1864,16 @@ pic_status launch_diag(Sim* s, int32_t lo, int32_t hi, pic_diag* out, double* sl
   return run_diag(s, a, lo, hi, out, slice_sigma, max_slices);
 }
 
-// Mixed form: float64 SoA in the staging area -> FP32 particles of the current buffer.
-pic_status launch_particles_in(Sim* s, const int32_t* id_dev, int64_t n) {
+// Mixed form: float64 SoA (the staging area, or src with its stride) -> FP32 particles of
+// the current buffer.
+pic_status launch_particles_in(Sim* s, const int32_t* id_dev, int64_t n, const double* src, int64_t stride) {
   if (n == 0) return PIC_OK;
-  k_p64_to_p32<<<pgrid(n), 256, 0, s->stream>>>(s->at<double>(s->lay.stage64), s->cfg.np_capacity, id_dev,
-                                                 partsf_of(s, s->cur), n, s->cfg.Nz, 1.0 / s->cfg.dz, 1.0 / s->cfg.dr);
+  if (!src) {
+    src = s->at<double>(s->lay.stage64);
+    stride = s->cfg.np_capacity;
+  }
+  k_p64_to_p32<<<pgrid(n), 256, 0, s->stream>>>(src, stride, id_dev, partsf_of(s, s->cur), n, s->cfg.Nz,
+                                                 1.0 / s->cfg.dz, 1.0 / s->cfg.dr);
   PIC_LAUNCHED(s);
   return PIC_OK;
 }

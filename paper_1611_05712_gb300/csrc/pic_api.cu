@@ -622,6 +622,12 @@ pic_status pic_copy_window(pic_sim* src_sim, int32_t buffer_id, int32_t src_z0, 
 pic_status pic_destroy(pic_sim* sim) {
   Sim* s = reinterpret_cast<Sim*>(sim);
   if (s && s->diag_host) cudaFreeHost(s->diag_host);
+  if (s && s->stage.copy) {   // a staged copy may still be in flight into the caller's buffer
+    cudaStreamSynchronize(s->stage.copy);
+    cudaEventDestroy(s->stage.copied);
+    cudaEventDestroy(s->stage.free_);
+    cudaStreamDestroy(s->stage.copy);
+  }
   delete s;
   return PIC_OK;
 }
@@ -684,6 +690,85 @@ pic_status pic_write_particles(pic_sim* sim, const double* const soa[7], const i
     if (st != PIC_OK) return st;
   }
   if (on_host) PIC_CUDA(cudaStreamSynchronize(s->stream));
+  return PIC_OK;
+}
+
+namespace {
+int64_t stage_stride(int64_t n) { return (n + 31) / 32 * 32; }   // doubles per staged array
+}   // namespace
+
+pic_status pic_stage_bytes(int64_t n, size_t* bytes) {
+  if (!bytes || n < 0) { set_error("pic_stage_bytes: n must be >= 0 and bytes non-NULL"); return PIC_ERR_ARG; }
+  const size_t st = (size_t)stage_stride(n);
+  *bytes = st * 7 * 8 + st * 4;
+  return PIC_OK;
+}
+
+pic_status pic_stage_particles(pic_sim* sim, const double* const soa[7], const int32_t* id, int64_t n,
+                               void* staging, size_t staging_bytes) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  Sim::StageState& g = s->stage;
+  if (g.pending) { set_error("a staged particle set is waiting for pic_take_particles"); return PIC_ERR_STATE; }
+  if (n < 0 || n > s->cfg.np_capacity) {
+    set_error("n=%lld outside [0, capacity %lld]", (long long)n, (long long)s->cfg.np_capacity);
+    return PIC_ERR_ARG;
+  }
+  size_t need = 0;
+  pic_stage_bytes(n, &need);
+  if (n > 0) {
+    if (!soa || !id) { set_error("particle pointers are NULL"); return PIC_ERR_ARG; }
+    for (int k = 0; k < 7; ++k)
+      if (!soa[k]) { set_error("particle array %d is NULL", k); return PIC_ERR_ARG; }
+    if (!staging || staging_bytes < need || reinterpret_cast<uintptr_t>(staging) % 256 != 0) {
+      set_error("staging buffer: %zu bytes at %p, need %zu bytes, 256-byte aligned", staging_bytes, staging, need);
+      return PIC_ERR_ARG;
+    }
+  }
+  if (!g.copy) {
+    PIC_CUDA(cudaStreamCreateWithFlags(&g.copy, cudaStreamNonBlocking));
+    PIC_CUDA(cudaEventCreateWithFlags(&g.copied, cudaEventDisableTiming));
+    PIC_CUDA(cudaEventCreateWithFlags(&g.free_, cudaEventDisableTiming));
+  }
+  const int64_t st = stage_stride(n);
+  char* buf = static_cast<char*>(staging);
+  // the previous take may still be reading this buffer (an event never recorded is complete)
+  PIC_CUDA(cudaStreamWaitEvent(g.copy, g.free_, 0));
+  for (int k = 0; k < 7 && n > 0; ++k)
+    PIC_CUDA(cudaMemcpyAsync(buf + (size_t)k * st * 8, soa[k], (size_t)n * 8, cudaMemcpyHostToDevice, g.copy));
+  if (n > 0) PIC_CUDA(cudaMemcpyAsync(buf + (size_t)7 * st * 8, id, (size_t)n * 4, cudaMemcpyHostToDevice, g.copy));
+  PIC_CUDA(cudaEventRecord(g.copied, g.copy));
+  g.pending = 1;
+  g.n = n;
+  g.buf = buf;
+  g.stride = st;
+  return PIC_OK;
+}
+
+pic_status pic_take_particles(pic_sim* sim) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  Sim::StageState& g = s->stage;
+  if (!g.pending) { set_error("no staged particle set (pic_stage_particles)"); return PIC_ERR_STATE; }
+  g.pending = 0;
+  PIC_CUDA(cudaEventSynchronize(g.copied));   // the caller's host arrays are free from here on
+  PIC_CUDA(cudaStreamWaitEvent(s->stream, g.copied, 0));
+  if (pic_status fs = launch_window_flush(s)) return fs;   // pending window-column subtraction
+  const int64_t n = g.n, st = g.stride;
+  const double* src = reinterpret_cast<const double*>(g.buf);
+  const int32_t* ids = reinterpret_cast<const int32_t*>(g.buf + (size_t)7 * st * 8);
+  s->np = n;
+  s->win.on = 0;   // new particles: the window's template and ids no longer apply
+  if (s->cfg.precision != PIC_FP64) {
+    pic_status r = launch_particles_in(s, ids, n, src, st);
+    if (r != PIC_OK) return r;
+  } else if (n > 0) {
+    for (int k = 0; k < 7; ++k)
+      PIC_CUDA(cudaMemcpyAsync(s->ws + s->lay.part[s->cur][k], src + (size_t)k * st, (size_t)n * 8,
+                               cudaMemcpyDeviceToDevice, s->stream));
+    PIC_CUDA(cudaMemcpyAsync(s->ws + s->lay.pid[s->cur], ids, (size_t)n * 4, cudaMemcpyDeviceToDevice, s->stream));
+  }
+  PIC_CUDA(cudaEventRecord(g.free_, s->stream));
   return PIC_OK;
 }
 

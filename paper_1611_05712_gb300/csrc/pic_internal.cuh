@@ -122,6 +122,17 @@ struct Sim {
   } tmaps[2 * kMaxModes * 3][3];
   WindowState win;
   double* diag_host = nullptr;   // pinned host copy of the diagnostics results (first use)
+  // staged particle input (pic_stage_particles / pic_take_particles): a copy stream and
+  // two events, created on first use
+  struct StageState {
+    cudaStream_t copy = nullptr;
+    cudaEvent_t copied = nullptr;   // the staged copy has landed
+    cudaEvent_t free_ = nullptr;    // the last take has read its staging buffer
+    int pending = 0;
+    int64_t n = 0;
+    char* buf = nullptr;            // caller's device staging buffer
+    int64_t stride = 0;             // doubles per array in buf
+  } stage;
 
   template <typename T> T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
   size_t grid_elems() const { return (size_t)cfg.Nm * cfg.Nr * cfg.Nz; }
@@ -205,7 +216,10 @@ pic_status launch_diag(Sim* s, int32_t id_lo, int32_t id_hi, pic_diag* out, doub
                        int32_t max_slices);
 pic_status build_inv_volume(Sim* s);                        // once, at init
 pic_status particles_configure_device();                    // once per device
-pic_status launch_particles_in(Sim* s, const int32_t* id_dev, int64_t n);   // mixed: stage64 -> FP32
+// mixed: float64 SoA (7 arrays of `stride` doubles from src; stage64 with the capacity as
+// stride when src is null) -> FP32
+pic_status launch_particles_in(Sim* s, const int32_t* id_dev, int64_t n, const double* src = nullptr,
+                               int64_t stride = 0);
 pic_status launch_particles_out(Sim* s, int32_t* id_dev, int64_t n);        // mixed: FP32 -> stage64
 
 // ---- moving window (particles.cu: particle side; window.cu: field side) ----

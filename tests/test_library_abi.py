@@ -67,3 +67,15 @@ def test_null_handles_rejected(lib):
     assert lib.pic_sort(None) == 1
     assert lib.pic_step(None, 1) == 1
     assert lib.pic_init(None, None, 0, None, None) == 1
+
+
+def test_stage_bytes_host_only(lib):
+    # 7 float64 arrays and the int32 ids, each padded to a multiple of 32 elements
+    out = ctypes.c_size_t()
+    for n, padded in ((0, 0), (1, 32), (32, 32), (33, 64), (1348576, 1348576)):
+        assert lib.pic_stage_bytes(n, ctypes.byref(out)) == 0
+        assert out.value == padded * (7 * 8 + 4), n
+    assert lib.pic_stage_bytes(-1, ctypes.byref(out)) == 1
+    assert lib.pic_stage_bytes(4, None) == 1
+    assert lib.pic_stage_particles(None, None, None, 0, None, 0) == 1
+    assert lib.pic_take_particles(None) == 1
