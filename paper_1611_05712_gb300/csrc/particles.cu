@@ -1266,145 +1266,229 @@ __device__ __forceinline__ void block_sum_add(const double (&v)[K], double* acc)
   }
 }
 
-// pass 1: sum w, w x, w y, w z, w ux, w uy, w gamma, count
+// The selected particles (id in [lo, hi)) of one diagnostics call, compacted by the first
+// pass as float64 x, y, z, ux, uy, w, gamma (7 arrays; z is replaced by the slice index,
+// or -1 outside the slice span, in the first slice pass).  Passing over the compacted set
+// spreads the float64 work of a beam (a few CTAs' worth of the cell-sorted arrays) over
+// the whole GPU; float64 arithmetic is slow on GB300.
+struct DiagC {
+  double* v[7];
+};
+
+// Header of the accumulator block: [0..7] pass-1 sums (w, w x, w y, w z, w ux, w uy,
+// w gamma, count), [16..20] means, [32..38] pass-2 sums, [48] slice start, [49] slice span,
+// [50] slices, [51] status (0 ok, 1 no weight, 2 sigma_z = 0, 3 too many slices),
+// [52] non-empty slices, [53] sum of the slice spreads, [56] compacted count (uint64).
+enum {
+  kDiagMean = 16, kDiagC2 = 32, kDiagZ0 = 48, kDiagSpan = 49, kDiagNs = 50, kDiagStatus = 51, kDiagNe = 52,
+  kDiagSigSum = 53, kDiagCount = 56
+};
+
+__device__ __forceinline__ int64_t diag_count(const double* acc) {
+  return (int64_t)*reinterpret_cast<const unsigned long long*>(acc + kDiagCount);
+}
+
+// pass 1: compact the selected particles and sum w, w x, w y, w z, w ux, w uy, w gamma,
+// count.  Each CTA claims its slots with one atomic per iteration (warp ballots, then a
+// prefix over the warps).
 template <class A>
-__global__ void k_diag_moments(const A a, int64_t np, int32_t lo, int32_t hi, double* acc) {
+__global__ void __launch_bounds__(kDiagThreads) k_diag_select(const A a, int64_t np, int32_t lo, int32_t hi,
+                                                               DiagC c, double* acc) {
+  __shared__ int32_t wbase[kDiagThreads / 32];
+  __shared__ unsigned long long sbase;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t id = a.id(i);
-    if (id < lo || id >= hi) continue;
-    double x, y, z, ux, uy, uz, w;
-    a.get(i, x, y, z, ux, uy, uz, w);
-    const double gam = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) * kInvC2);
-    v[0] += w; v[1] += w * x; v[2] += w * y; v[3] += w * z;
-    v[4] += w * ux; v[5] += w * uy; v[6] += w * gam; v[7] += 1.0;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x; b < np; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = b + threadIdx.x;
+    bool sel = false;
+    if (i < np) {
+      const int32_t id = a.id(i);
+      sel = id >= lo && id < hi;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, sel);
+    if (lane == 0) wbase[warp] = __popc(m);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int32_t t = 0;
+      for (int w = 0; w < kDiagThreads / 32; ++w) {
+        const int32_t k = wbase[w];
+        wbase[w] = t;
+        t += k;
+      }
+      sbase = t ? atomicAdd(reinterpret_cast<unsigned long long*>(acc + kDiagCount), (unsigned long long)t) : 0ull;
+    }
+    __syncthreads();
+    if (sel) {
+      const int64_t slot = (int64_t)sbase + wbase[warp] + __popc(m & ((1u << lane) - 1u));
+      double x, y, z, ux, uy, uz, w;
+      a.get(i, x, y, z, ux, uy, uz, w);
+      const double gam = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) * kInvC2);
+      c.v[0][slot] = x; c.v[1][slot] = y; c.v[2][slot] = z;
+      c.v[3][slot] = ux; c.v[4][slot] = uy; c.v[5][slot] = w; c.v[6][slot] = gam;
+      v[0] += w; v[1] += w * x; v[2] += w * y; v[3] += w * z;
+      v[4] += w * ux; v[5] += w * uy; v[6] += w * gam; v[7] += 1.0;
+    }
+    __syncthreads();   // wbase and sbase are rewritten by the next iteration
   }
   block_sum_add<8>(v, acc);
 }
 
-// pass 2: centred second moments w dx^2, w dux^2, w dx dux, (y), w dz^2
-// Device-side steps between the passes (one thread), so that the passes chain without a
-// host round trip.  Header of the accumulator block: [0..7] pass-1 sums, [16..20] means,
-// [32..38] pass-2 sums, [48] slice start, [49] slice span, [50] slices, [51] status
-// (0 ok, 1 no weight, 2 sigma_z = 0, 3 too many slices), [52] non-empty slices.
-enum { kDiagMean = 16, kDiagC2 = 32, kDiagZ0 = 48, kDiagSpan = 49, kDiagNs = 50, kDiagStatus = 51, kDiagNe = 52 };
-
-__global__ void k_diag_means(double* acc) {
-  if (acc[7] == 0.0 || !(acc[0] > 0.0)) {
-    acc[kDiagStatus] = 1.0;
-    return;
+// pass 2: means (thread 0 of each CTA; CTA 0 stores them and the status), then the centred
+// second moments w dx^2, w dux^2, w dx dux, (y), w dz^2 over the compacted particles.
+__global__ void __launch_bounds__(kDiagThreads) k_diag_central(DiagC c, double* acc) {
+  __shared__ double mean[5];
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    ok = acc[7] != 0.0 && acc[0] > 0.0;
+    if (ok)
+      for (int k = 0; k < 5; ++k) mean[k] = acc[1 + k] / acc[0];
+    if (blockIdx.x == 0) {
+      if (!ok) acc[kDiagStatus] = 1.0;
+      else
+        for (int k = 0; k < 5; ++k) acc[kDiagMean + k] = mean[k];
+    }
   }
-  for (int k = 0; k < 5; ++k) acc[kDiagMean + k] = acc[1 + k] / acc[0];
-}
-
-__global__ void k_diag_slice_setup(double* acc, double slen, int max_slices) {
-  if (acc[kDiagStatus] != 0.0) return;
-  const double sz = sqrt(acc[kDiagC2 + 6] / acc[0]);
-  if (!(sz > 0.0)) {
-    acc[kDiagStatus] = 2.0;
-    return;
-  }
-  const double span = 6.0 * sz;
-  const double ns = ceil(span / slen);
-  acc[kDiagZ0] = acc[kDiagMean + 2] - 3.0 * sz;
-  acc[kDiagSpan] = span;
-  acc[kDiagNs] = ns;
-  if (ns > max_slices) acc[kDiagStatus] = 3.0;
-}
-
-template <class A>
-__global__ void k_diag_central(const A a, int64_t np, int32_t lo, int32_t hi, const double* mean, double* acc) {
-  if (mean[kDiagStatus - kDiagMean] != 0.0) return;
+  __syncthreads();
+  if (!ok) return;
+  const int64_t n = diag_count(acc);
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t id = a.id(i);
-    if (id < lo || id >= hi) continue;
-    double x, y, z, ux, uy, uz, w;
-    a.get(i, x, y, z, ux, uy, uz, w);
-    const double dx = x - mean[0], dy = y - mean[1], dz = z - mean[2];
-    const double dux = ux - mean[3], duy = uy - mean[4];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double w = c.v[5][i];
+    const double dx = c.v[0][i] - mean[0], dy = c.v[1][i] - mean[1], dz = c.v[2][i] - mean[2];
+    const double dux = c.v[3][i] - mean[3], duy = c.v[4][i] - mean[4];
     v[0] += w * (dx * dx); v[1] += w * (dux * dux); v[2] += w * (dx * dux);
     v[3] += w * (dy * dy); v[4] += w * (duy * duy); v[5] += w * (dy * duy);
     v[6] += w * (dz * dz);
   }
-  block_sum_add<7>(v, acc);
+  block_sum_add<7>(v, acc + kDiagC2);
 }
 
-// pass 3 (stage 0): per-slice sum w and sum w gamma; (stage 1): sum w (gamma - gbar_s)^2.
-// Each thread takes a contiguous range of particles and adds a run of equal slices with one
-// atomic: particles are cell-sorted, so runs are long and the atomics on the few slices of
-// a beam do not pile up.
-template <class A>
-__global__ void k_diag_slices(const A a, int64_t np, int32_t lo, int32_t hi, const double* hdr, double slen,
-                              double* sw, double* sg, double* sv, int stage) {
-  if (hdr[kDiagStatus] != 0.0) return;
-  const double zstart = hdr[kDiagZ0], zspan = hdr[kDiagSpan];
-  const int ns = (int)hdr[kDiagNs];
+// Slice passes.  Each thread takes a contiguous range of at least per_min compacted
+// particles and adds each run of equal slices with one atomic: the compacted order keeps
+// the cell order within each CTA's claim, so runs are long and the atomics on the few
+// slices of a beam do not pile up.
+__device__ __forceinline__ void diag_range(int64_t n, int per_min, int64_t& i0, int64_t& i1) {
   const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-  const int64_t per = (np + nthr - 1) / nthr;
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t i0 = t * per, i1 = min(np, i0 + per);
+  const int64_t per = max((int64_t)per_min, (n + nthr - 1) / nthr);
+  i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * per;
+  i1 = min(n, i0 + per);
+}
+
+// stage 0: slice layout from sigma_z (thread 0 of each CTA; CTA 0 stores it and the
+// status), the slice index of each particle, per-slice sum w and sum w gamma.
+__global__ void __launch_bounds__(kDiagThreads) k_diag_slices0(DiagC c, double* acc, double slen, int max_slices,
+                                                                int per_min, double* sw, double* sg) {
+  __shared__ double z0, span;
+  __shared__ int ns, st;
+  if (threadIdx.x == 0) {
+    st = (int)acc[kDiagStatus];
+    if (st == 0) {
+      const double sz = sqrt(acc[kDiagC2 + 6] / acc[0]);
+      if (!(sz > 0.0)) {
+        st = 2;
+      } else {
+        span = 6.0 * sz;
+        const double nsd = ceil(span / slen);
+        z0 = acc[kDiagMean + 2] - 3.0 * sz;
+        ns = (int)fmin(nsd, (double)max_slices);
+        if (nsd > max_slices) st = 3;
+        if (blockIdx.x == 0) {
+          acc[kDiagZ0] = z0;
+          acc[kDiagSpan] = span;
+          acc[kDiagNs] = nsd;
+        }
+      }
+      if (blockIdx.x == 0) acc[kDiagStatus] = (double)st;
+    }
+  }
+  __syncthreads();
+  if (st != 0) return;
+  int64_t i0, i1;
+  diag_range(diag_count(acc), per_min, i0, i1);
   int run = -1;
   double rw = 0.0, rg = 0.0;
   for (int64_t i = i0; i < i1; ++i) {
-    const int32_t id = a.id(i);
-    if (id < lo || id >= hi) continue;
-    double x, y, z, ux, uy, uz, w;
-    a.get(i, x, y, z, ux, uy, uz, w);
-    const double d = z - zstart;
-    if (!(d >= 0.0 && d < zspan)) continue;
+    const double d = c.v[2][i] - z0;
+    if (!(d >= 0.0 && d < span)) {
+      c.v[2][i] = -1.0;
+      continue;
+    }
     int k = (int)floor(d / slen);
     if (k > ns - 1) k = ns - 1;
-    const double gam = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) * kInvC2);
+    c.v[2][i] = (double)k;
     if (k != run) {
       if (run >= 0) {
-        if (stage == 0) {
-          atomicAdd(sw + run, rw);
-          atomicAdd(sg + run, rg);
-        } else {
-          atomicAdd(sv + run, rw);
-        }
+        atomicAdd(sw + run, rw);
+        atomicAdd(sg + run, rg);
       }
       run = k;
       rw = 0.0;
       rg = 0.0;
     }
-    if (stage == 0) {
-      rw += w;
-      rg += w * gam;
-    } else {
-      const double dg = gam - sg[k] / sw[k];
-      rw += w * (dg * dg);
-    }
+    const double w = c.v[5][i];
+    rw += w;
+    rg += w * c.v[6][i];
   }
   if (run >= 0) {
-    if (stage == 0) {
-      atomicAdd(sw + run, rw);
-      atomicAdd(sg + run, rg);
-    } else {
-      atomicAdd(sv + run, rw);
-    }
+    atomicAdd(sw + run, rw);
+    atomicAdd(sg + run, rg);
   }
 }
 
+// stage 1: per-slice sum w (gamma - gbar_s)^2, gbar_s = sum w gamma / sum w of the slice
+// (one division per run).
+__global__ void __launch_bounds__(kDiagThreads) k_diag_slices1(DiagC c, const double* acc, int per_min,
+                                                                const double* sw, const double* sg, double* sv) {
+  if (acc[kDiagStatus] != 0.0) return;
+  int64_t i0, i1;
+  diag_range(diag_count(acc), per_min, i0, i1);
+  int run = -1;
+  double rv = 0.0, gbar = 0.0;
+  for (int64_t i = i0; i < i1; ++i) {
+    const int k = (int)c.v[2][i];
+    if (k < 0) continue;
+    if (k != run) {
+      if (run >= 0) atomicAdd(sv + run, rv);
+      run = k;
+      rv = 0.0;
+      gbar = sg[k] / sw[k];
+    }
+    const double dg = c.v[6][i] - gbar;
+    rv += c.v[5][i] * (dg * dg);
+  }
+  if (run >= 0) atomicAdd(sv + run, rv);
+}
+
 // Per-slice std of gamma of the non-empty slices, in slice order, into out[0 .. ne) (one CTA
-// of 1024 threads; ranks by a block scan); ne into the header.
+// of 1024 threads; ranks by a block scan); ne and the sum of the spreads into the header.
 __global__ void __launch_bounds__(1024) k_diag_slice_compact(double* hdr, const double* sw, const double* sv,
                                                               double* out) {
+  __shared__ double part[32];
   if (hdr[kDiagStatus] != 0.0) return;
   const int ns = (int)hdr[kDiagNs];
   int32_t base = 0;
+  double sum = 0.0;
   for (int k0 = 0; k0 < ns; k0 += 1024) {
     const int k = k0 + threadIdx.x;
     const bool ne = k < ns && sw[k] > 0.0;
     int32_t tot;
     const int32_t pos = base + block_exclusive_scan(ne ? 1 : 0, &tot);
-    if (ne) out[pos] = sqrt(sv[k] / sw[k]);
+    if (ne) {
+      const double sg = sqrt(sv[k] / sw[k]);
+      out[pos] = sg;
+      sum += sg;
+    }
     base += tot;
   }
-  if (threadIdx.x == 0) hdr[kDiagNe] = (double)base;
+  sum = warp_sum(sum);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 32; ++w) t += part[w];
+    hdr[kDiagNe] = (double)base;
+    hdr[kDiagSigSum] = t;
+  }
 }
 
 inline int pgrid(int64_t n) {
@@ -1412,8 +1496,21 @@ inline int pgrid(int64_t n) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 16));
 }
 
-// The passes chain on the device; one copy of the header and the slice values and one
-// synchronisation at the end.
+// Compacted-particle storage of the diagnostics: the staging area (mixed forms) or the
+// particle buffer that is not current (FP64 form); both are free between cycles.
+DiagC diag_storage(Sim* s) {
+  DiagC c;
+  const size_t cap = (size_t)s->cfg.np_capacity;
+  for (int k = 0; k < 7; ++k)
+    c.v[k] = s->cfg.precision != PIC_FP64 ? s->at<double>(s->lay.stage64) + k * cap
+                                          : s->at<double>(s->lay.part[1 - s->cur][k]);
+  return c;
+}
+
+constexpr int kDiagPerMin = 8;   // compacted particles per thread at least in the slice passes
+
+// The passes chain on the device; one copy of the header and the requested slice values
+// and one synchronisation at the end.
 template <class A>
 pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* out, double* slice_sigma,
                     int32_t max_slices) {
@@ -1422,34 +1519,31 @@ pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* ou
   double* sw = acc + 64;
   double* sg = sw + kMaxSlices;
   double* sv = sg + kMaxSlices;
+  const DiagC c = diag_storage(s);
   PIC_CUDA(cudaMemsetAsync(acc, 0, 64 * sizeof(double), s->stream));
   PIC_CUDA(cudaMemsetAsync(sw, 0, 3 * sizeof(double) * kMaxSlices, s->stream));
   const int grid = std::min(pgrid(np), 8 * 152);   // one atomic per CTA and sum
   if (np > 0) {
-    k_diag_moments<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, acc);
+    k_diag_select<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, c, acc);
     PIC_LAUNCHED(s);
   }
-  k_diag_means<<<1, 1, 0, s->stream>>>(acc);
+  k_diag_central<<<grid, kDiagThreads, 0, s->stream>>>(c, acc);
   PIC_LAUNCHED(s);
-  if (np > 0) {
-    k_diag_central<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, acc + kDiagMean, acc + kDiagC2);
-    PIC_LAUNCHED(s);
-  }
-  k_diag_slice_setup<<<1, 1, 0, s->stream>>>(acc, kSliceLen, kMaxSlices);
+  const int sgrid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((np + kDiagThreads * kDiagPerMin - 1) / (kDiagThreads * kDiagPerMin), 8 * 152));
+  k_diag_slices0<<<sgrid, kDiagThreads, 0, s->stream>>>(c, acc, kSliceLen, kMaxSlices, kDiagPerMin, sw, sg);
   PIC_LAUNCHED(s);
-  if (np > 0) {
-    for (int stage = 0; stage < 2; ++stage) {
-      k_diag_slices<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, acc, kSliceLen, sw, sg, sv, stage);
-      PIC_LAUNCHED(s);
-    }
-  }
+  k_diag_slices1<<<sgrid, kDiagThreads, 0, s->stream>>>(c, acc, kDiagPerMin, sw, sg, sv);
+  PIC_LAUNCHED(s);
   k_diag_slice_compact<<<1, 1024, 0, s->stream>>>(acc, sw, sv, sg);   // sg is free after stage 1
   PIC_LAUNCHED(s);
   if (!s->diag_host) PIC_CUDA(cudaMallocHost(&s->diag_host, (64 + (size_t)kMaxSlices) * sizeof(double)));
   double* h = s->diag_host;
   const double* sig = h + 64;
+  const int32_t n_copy = slice_sigma ? std::min<int32_t>(std::max<int32_t>(max_slices, 0), kMaxSlices) : 0;
   PIC_CUDA(cudaMemcpyAsync(h, acc, 64 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  PIC_CUDA(cudaMemcpyAsync(h + 64, sg, kMaxSlices * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  if (n_copy > 0)
+    PIC_CUDA(cudaMemcpyAsync(h + 64, sg, n_copy * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   PIC_CUDA(cudaStreamSynchronize(s->stream));
   *out = pic_diag{};
   out->n_particles = (int32_t)h[7];
@@ -1471,13 +1565,9 @@ pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* ou
     return PIC_ERR_ARG;
   }
   const int ne = (int)h[kDiagNe];
-  double sum = 0.0;
-  for (int k = 0; k < ne; ++k) {
-    if (slice_sigma && k < max_slices) slice_sigma[k] = sig[k];
-    sum += sig[k];
-  }
+  for (int k = 0; k < ne && k < n_copy; ++k) slice_sigma[k] = sig[k];
   out->n_slices = ne;
-  out->sigma_gamma_mean = ne ? sum / ne : 0.0;
+  out->sigma_gamma_mean = ne ? h[kDiagSigSum] / ne : 0.0;
   return PIC_OK;
 }
 
