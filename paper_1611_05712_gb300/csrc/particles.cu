@@ -1246,31 +1246,17 @@ struct Acc32 {
   __device__ int32_t id(int64_t i) const { return p.id[i]; }
 };
 
-// Sums of K per-thread values over the CTA (kDiagThreads threads), added to acc[0..K) by
-// one atomic per value and CTA: with a float64 atomic per warp, the adds of all warps
-// serialise on the same K addresses.
-template <int K>
-__device__ __forceinline__ void block_sum_add(const double (&v)[K], double* acc) {
-  __shared__ double part[kDiagThreads / 32][K];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const double t = warp_sum(v[k]);
-    if (lane == 0) part[warp][k] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x < K) {
-    double t = 0.0;
-    for (int w = 0; w < kDiagThreads / 32; ++w) t += part[w][threadIdx.x];
-    atomicAdd(acc + threadIdx.x, t);
-  }
-}
+// Diagnostics grid: at most kDiagMaxGrid CTAs of kDiagThreads threads.  Sums over the
+// particles are formed per CTA, stored as per-CTA partials and added in CTA order by the
+// last CTA to finish (an integer ticket): float64 atomics from every CTA onto the same few
+// addresses serialise in L2, and the fixed order makes the results reproducible.
+constexpr int kDiagMaxGrid = 8 * 152;
 
-// The selected particles (id in [lo, hi)) of one diagnostics call, compacted by the first
-// pass as float64 x, y, z, ux, uy, w, gamma (7 arrays; z is replaced by the slice index,
-// or -1 outside the slice span, in the first slice pass).  Passing over the compacted set
-// spreads the float64 work of a beam (a few CTAs' worth of the cell-sorted arrays) over
-// the whole GPU; float64 arithmetic is slow on GB300.
+// The selected particles (id in [lo, hi)) of one diagnostics call, compacted in array order
+// as float64 x, y, z, ux, uy, w, gamma (7 arrays; z is replaced by the slice index, or -1
+// outside the slice span, in the first slice pass).  The passes over the compacted set
+// spread the float64 work of a beam (a few CTAs' worth of the cell-sorted arrays) over the
+// whole GPU; float64 arithmetic is slow on GB300.
 struct DiagC {
   double* v[7];
 };
@@ -1278,30 +1264,117 @@ struct DiagC {
 // Header of the accumulator block: [0..7] pass-1 sums (w, w x, w y, w z, w ux, w uy,
 // w gamma, count), [16..20] means, [32..38] pass-2 sums, [48] slice start, [49] slice span,
 // [50] slices, [51] status (0 ok, 1 no weight, 2 sigma_z = 0, 3 too many slices),
-// [52] non-empty slices, [53] sum of the slice spreads, [56] compacted count (uint64).
+// [52] non-empty slices, [53] sum of the slice spreads, [56] compacted count (uint64),
+// [57], [58] tickets of the two reductions (uint32).  After the header, the slice sums,
+// the inverse cell volumes, then the per-CTA partials and counts (diag_parts).
 enum {
   kDiagMean = 16, kDiagC2 = 32, kDiagZ0 = 48, kDiagSpan = 49, kDiagNs = 50, kDiagStatus = 51, kDiagNe = 52,
-  kDiagSigSum = 53, kDiagCount = 56
+  kDiagSigSum = 53, kDiagCount = 56, kDiagTicket = 57
+};
+
+struct DiagParts {
+  double* p1;     // [kDiagMaxGrid][8]
+  double* p2;     // [kDiagMaxGrid][8]
+  int64_t* cnt;   // [kDiagMaxGrid]
 };
 
 __device__ __forceinline__ int64_t diag_count(const double* acc) {
   return (int64_t)*reinterpret_cast<const unsigned long long*>(acc + kDiagCount);
 }
 
-// pass 1: compact the selected particles and sum w, w x, w y, w z, w ux, w uy, w gamma,
-// count.  Each CTA claims its slots with one atomic per iteration (warp ballots, then a
-// prefix over the warps).
+// CTA sums of K per-thread values into part[blockIdx.x][0..K); the last CTA adds the
+// partials of all CTAs in CTA order into out[0..K).  Every CTA of the grid calls it.
+template <int K>
+__device__ void block_partials(const double (&v)[K], double* part, unsigned* ticket, double* out) {
+  static_assert(K <= kDiagThreads / 32, "one warp per value in the final sum");
+  __shared__ double wsum[kDiagThreads / 32][K];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const double t = warp_sum(v[k]);
+    if (lane == 0) wsum[warp][k] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double t = 0.0;
+    for (int w = 0; w < kDiagThreads / 32; ++w) t += wsum[w][threadIdx.x];
+    part[blockIdx.x * 8 + threadIdx.x] = t;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (warp < K) {
+    double t = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) t += __ldcg(part + b * 8 + warp);
+    t = warp_sum(t);
+    if (lane == 0) out[warp] = t;
+  }
+}
+
+// CTA b of the selection passes walks particles [b C, (b+1) C), C = ceil(np / grid) rounded
+// up to whole iterations of the CTA.
+__device__ __forceinline__ void diag_chunk(int64_t np, int64_t& b0, int64_t& b1) {
+  const int64_t per = ((np + gridDim.x - 1) / gridDim.x + kDiagThreads - 1) / kDiagThreads * kDiagThreads;
+  b0 = blockIdx.x * per;
+  b1 = min(np, b0 + per);
+}
+
+// pass 0: number of selected particles of each CTA's chunk.
+template <class A>
+__global__ void __launch_bounds__(kDiagThreads) k_diag_count(const A a, int64_t np, int32_t lo, int32_t hi,
+                                                              DiagParts dp) {
+  __shared__ int32_t wc[kDiagThreads / 32];
+  int64_t b0, b1;
+  diag_chunk(np, b0, b1);
+  int32_t c = 0;
+  for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
+    const int32_t id = a.id(i);
+    c += (id >= lo && id < hi) ? 1 : 0;
+  }
+  c = __reduce_add_sync(0xffffffffu, c);
+  if ((threadIdx.x & 31) == 0) wc[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kDiagThreads / 32; ++w) t += wc[w];
+    dp.cnt[blockIdx.x] = t;
+  }
+}
+
+// pass 1: compact the selected particles in array order (each CTA's offset is the sum of
+// the counts of the CTAs before it) and sum w, w x, w y, w z, w ux, w uy, w gamma, count.
 template <class A>
 __global__ void __launch_bounds__(kDiagThreads) k_diag_select(const A a, int64_t np, int32_t lo, int32_t hi,
-                                                               DiagC c, double* acc) {
+                                                               DiagC c, DiagParts dp, double* acc) {
+  __shared__ int64_t wred[kDiagThreads / 32];
   __shared__ int32_t wbase[kDiagThreads / 32];
-  __shared__ unsigned long long sbase;
+  __shared__ int64_t base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // offset of this CTA: sum of the counts of CTAs 0 .. blockIdx.x - 1
+  int64_t s = 0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) s += dp.cnt[b];
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+  if (lane == 0) wred[warp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kDiagThreads / 32; ++w) t += wred[w];
+    base = t;
+    if (blockIdx.x == gridDim.x - 1)   // the total, for the passes over the compacted set
+      *reinterpret_cast<unsigned long long*>(acc + kDiagCount) = (unsigned long long)(t + dp.cnt[blockIdx.x]);
+  }
+  __syncthreads();
+  int64_t b0, b1;
+  diag_chunk(np, b0, b1);
   double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int64_t b = blockIdx.x * (int64_t)blockDim.x; b < np; b += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = b + threadIdx.x;
+  for (int64_t it = b0; it < b1; it += blockDim.x) {
+    const int64_t i = it + threadIdx.x;
     bool sel = false;
-    if (i < np) {
+    if (i < b1) {
       const int32_t id = a.id(i);
       sel = id >= lo && id < hi;
     }
@@ -1315,11 +1388,11 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_select(const A a, int64_t
         wbase[w] = t;
         t += k;
       }
-      sbase = t ? atomicAdd(reinterpret_cast<unsigned long long*>(acc + kDiagCount), (unsigned long long)t) : 0ull;
+      wred[0] = t;
     }
     __syncthreads();
     if (sel) {
-      const int64_t slot = (int64_t)sbase + wbase[warp] + __popc(m & ((1u << lane) - 1u));
+      const int64_t slot = base + wbase[warp] + __popc(m & ((1u << lane) - 1u));
       double x, y, z, ux, uy, uz, w;
       a.get(i, x, y, z, ux, uy, uz, w);
       const double gam = sqrt(1.0 + (ux * ux + uy * uy + uz * uz) * kInvC2);
@@ -1328,14 +1401,15 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_select(const A a, int64_t
       v[0] += w; v[1] += w * x; v[2] += w * y; v[3] += w * z;
       v[4] += w * ux; v[5] += w * uy; v[6] += w * gam; v[7] += 1.0;
     }
-    __syncthreads();   // wbase and sbase are rewritten by the next iteration
+    __syncthreads();   // all reads of wbase and wred[0] done before thread 0 rewrites them
+    if (threadIdx.x == 0) base += wred[0];
   }
-  block_sum_add<8>(v, acc);
+  block_partials<8>(v, dp.p1, reinterpret_cast<unsigned*>(acc + kDiagTicket), acc);
 }
 
 // pass 2: means (thread 0 of each CTA; CTA 0 stores them and the status), then the centred
 // second moments w dx^2, w dux^2, w dx dux, (y), w dz^2 over the compacted particles.
-__global__ void __launch_bounds__(kDiagThreads) k_diag_central(DiagC c, double* acc) {
+__global__ void __launch_bounds__(kDiagThreads) k_diag_central(DiagC c, DiagParts dp, double* acc) {
   __shared__ double mean[5];
   __shared__ int ok;
   if (threadIdx.x == 0) {
@@ -1349,7 +1423,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_central(DiagC c, double* 
     }
   }
   __syncthreads();
-  if (!ok) return;
+  if (!ok) return;   // every CTA: no reduction follows
   const int64_t n = diag_count(acc);
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -1360,24 +1434,36 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_central(DiagC c, double* 
     v[3] += w * (dy * dy); v[4] += w * (duy * duy); v[5] += w * (dy * duy);
     v[6] += w * (dz * dz);
   }
-  block_sum_add<7>(v, acc + kDiagC2);
+  block_partials<7>(v, dp.p2, reinterpret_cast<unsigned*>(acc + kDiagTicket) + 2, acc + kDiagC2);
 }
 
-// Slice passes.  Each thread takes a contiguous range of at least per_min compacted
-// particles and adds each run of equal slices with one atomic: the compacted order keeps
-// the cell order within each CTA's claim, so runs are long and the atomics on the few
-// slices of a beam do not pile up.
-__device__ __forceinline__ void diag_range(int64_t n, int per_min, int64_t& i0, int64_t& i1) {
-  const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
-  const int64_t per = max((int64_t)per_min, (n + nthr - 1) / nthr);
-  i0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * per;
-  i1 = min(n, i0 + per);
+// Slice passes: one compacted particle per thread and iteration; each warp adds each run of
+// lanes with equal slices with one atomic from the run's first lane (a segmented sum over
+// the warp).  The compacted order keeps the cell order, so a warp's 32 consecutive
+// particles usually fall in one or two slices.
+__device__ __forceinline__ unsigned run_heads(int key) {
+  const int lane = threadIdx.x & 31;
+  const int prev = __shfl_up_sync(0xffffffffu, key, 1);
+  return __ballot_sync(0xffffffffu, lane == 0 || key != prev);
+}
+
+// Sum of v over this lane and the following lanes of its run (heads: first lanes of the
+// runs); the first lane of a run receives the run's total.
+__device__ __forceinline__ double run_sum(double v, unsigned heads) {
+  const int lane = threadIdx.x & 31;
+  const unsigned after = heads & ~((2u << lane) - 1u);   // run starts after this lane
+  const int end = after ? __ffs(after) - 1 : 32;
+  for (int d = 1; d < 32; d <<= 1) {
+    const double o = __shfl_down_sync(0xffffffffu, v, d);
+    if (lane + d < end) v += o;
+  }
+  return v;
 }
 
 // stage 0: slice layout from sigma_z (thread 0 of each CTA; CTA 0 stores it and the
 // status), the slice index of each particle, per-slice sum w and sum w gamma.
 __global__ void __launch_bounds__(kDiagThreads) k_diag_slices0(DiagC c, double* acc, double slen, int max_slices,
-                                                                int per_min, double* sw, double* sg) {
+                                                                double* sw, double* sg) {
   __shared__ double z0, span;
   __shared__ int ns, st;
   if (threadIdx.x == 0) {
@@ -1403,60 +1489,53 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_slices0(DiagC c, double* 
   }
   __syncthreads();
   if (st != 0) return;
-  int64_t i0, i1;
-  diag_range(diag_count(acc), per_min, i0, i1);
-  int run = -1;
-  double rw = 0.0, rg = 0.0;
-  for (int64_t i = i0; i < i1; ++i) {
-    const double d = c.v[2][i] - z0;
-    if (!(d >= 0.0 && d < span)) {
-      c.v[2][i] = -1.0;
-      continue;
-    }
-    int k = (int)floor(d / slen);
-    if (k > ns - 1) k = ns - 1;
-    c.v[2][i] = (double)k;
-    if (k != run) {
-      if (run >= 0) {
-        atomicAdd(sw + run, rw);
-        atomicAdd(sg + run, rg);
+  const int64_t n = diag_count(acc);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); b < n; b += stride) {
+    const int64_t i = b + (threadIdx.x & 31);   // the warp's lanes: 32 consecutive particles
+    int k = -1;
+    double w = 0.0, wg = 0.0;
+    if (i < n) {
+      const double d = c.v[2][i] - z0;
+      if (d >= 0.0 && d < span) {
+        k = (int)floor(d / slen);
+        if (k > ns - 1) k = ns - 1;
+        w = c.v[5][i];
+        wg = w * c.v[6][i];
       }
-      run = k;
-      rw = 0.0;
-      rg = 0.0;
+      c.v[2][i] = (double)k;
     }
-    const double w = c.v[5][i];
-    rw += w;
-    rg += w * c.v[6][i];
-  }
-  if (run >= 0) {
-    atomicAdd(sw + run, rw);
-    atomicAdd(sg + run, rg);
+    const unsigned heads = run_heads(k);
+    w = run_sum(w, heads);
+    wg = run_sum(wg, heads);
+    if (k >= 0 && ((heads >> (threadIdx.x & 31)) & 1u)) {
+      atomicAdd(sw + k, w);
+      atomicAdd(sg + k, wg);
+    }
   }
 }
 
-// stage 1: per-slice sum w (gamma - gbar_s)^2, gbar_s = sum w gamma / sum w of the slice
-// (one division per run).
-__global__ void __launch_bounds__(kDiagThreads) k_diag_slices1(DiagC c, const double* acc, int per_min,
-                                                                const double* sw, const double* sg, double* sv) {
+// stage 1: per-slice sum w (gamma - gbar_s)^2, gbar_s = sum w gamma / sum w of the slice.
+__global__ void __launch_bounds__(kDiagThreads) k_diag_slices1(DiagC c, const double* acc, const double* sw,
+                                                                const double* sg, double* sv) {
   if (acc[kDiagStatus] != 0.0) return;
-  int64_t i0, i1;
-  diag_range(diag_count(acc), per_min, i0, i1);
-  int run = -1;
-  double rv = 0.0, gbar = 0.0;
-  for (int64_t i = i0; i < i1; ++i) {
-    const int k = (int)c.v[2][i];
-    if (k < 0) continue;
-    if (k != run) {
-      if (run >= 0) atomicAdd(sv + run, rv);
-      run = k;
-      rv = 0.0;
-      gbar = sg[k] / sw[k];
+  const int64_t n = diag_count(acc);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); b < n; b += stride) {
+    const int64_t i = b + (threadIdx.x & 31);
+    int k = -1;
+    double v = 0.0;
+    if (i < n) {
+      k = (int)c.v[2][i];
+      if (k >= 0 && sw[k] > 0.0) {   // a slice of zero weight has no spread
+        const double dg = c.v[6][i] - sg[k] / sw[k];
+        v = c.v[5][i] * (dg * dg);
+      }
     }
-    const double dg = c.v[6][i] - gbar;
-    rv += c.v[5][i] * (dg * dg);
+    const unsigned heads = run_heads(k);
+    v = run_sum(v, heads);
+    if (k >= 0 && ((heads >> (threadIdx.x & 31)) & 1u)) atomicAdd(sv + k, v);
   }
-  if (run >= 0) atomicAdd(sv + run, rv);
 }
 
 // Per-slice std of gamma of the non-empty slices, in slice order, into out[0 .. ne) (one CTA
@@ -1507,7 +1586,12 @@ DiagC diag_storage(Sim* s) {
   return c;
 }
 
-constexpr int kDiagPerMin = 8;   // compacted particles per thread at least in the slice passes
+constexpr size_t kDiagPartsDoubles = 2 * 8 * (size_t)kDiagMaxGrid + kDiagMaxGrid;
+
+DiagParts diag_parts(Sim* s) {
+  double* p = s->at<double>(s->lay.diag_acc) + 64 + 3 * (size_t)kMaxSlices + kMaxNr;
+  return DiagParts{p, p + 8 * kDiagMaxGrid, reinterpret_cast<int64_t*>(p + 16 * kDiagMaxGrid)};
+}
 
 // The passes chain on the device; one copy of the header and the requested slice values
 // and one synchronisation at the end.
@@ -1520,20 +1604,21 @@ pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* ou
   double* sg = sw + kMaxSlices;
   double* sv = sg + kMaxSlices;
   const DiagC c = diag_storage(s);
+  const DiagParts dp = diag_parts(s);
   PIC_CUDA(cudaMemsetAsync(acc, 0, 64 * sizeof(double), s->stream));
   PIC_CUDA(cudaMemsetAsync(sw, 0, 3 * sizeof(double) * kMaxSlices, s->stream));
-  const int grid = std::min(pgrid(np), 8 * 152);   // one atomic per CTA and sum
+  const int grid = std::min(pgrid(np), kDiagMaxGrid);
   if (np > 0) {
-    k_diag_select<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, c, acc);
+    k_diag_count<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, dp);
+    PIC_LAUNCHED(s);
+    k_diag_select<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, c, dp, acc);
     PIC_LAUNCHED(s);
   }
-  k_diag_central<<<grid, kDiagThreads, 0, s->stream>>>(c, acc);
+  k_diag_central<<<grid, kDiagThreads, 0, s->stream>>>(c, dp, acc);
   PIC_LAUNCHED(s);
-  const int sgrid = (int)std::max<int64_t>(
-      1, std::min<int64_t>((np + kDiagThreads * kDiagPerMin - 1) / (kDiagThreads * kDiagPerMin), 8 * 152));
-  k_diag_slices0<<<sgrid, kDiagThreads, 0, s->stream>>>(c, acc, kSliceLen, kMaxSlices, kDiagPerMin, sw, sg);
+  k_diag_slices0<<<grid, kDiagThreads, 0, s->stream>>>(c, acc, kSliceLen, kMaxSlices, sw, sg);
   PIC_LAUNCHED(s);
-  k_diag_slices1<<<sgrid, kDiagThreads, 0, s->stream>>>(c, acc, kDiagPerMin, sw, sg, sv);
+  k_diag_slices1<<<grid, kDiagThreads, 0, s->stream>>>(c, acc, sw, sg, sv);
   PIC_LAUNCHED(s);
   k_diag_slice_compact<<<1, 1024, 0, s->stream>>>(acc, sw, sv, sg);   // sg is free after stage 1
   PIC_LAUNCHED(s);
@@ -1977,7 +2062,7 @@ pic_status launch_particles_out(Sim* s, int32_t* id_dev, int64_t n) {
   return PIC_OK;
 }
 
-size_t diag_acc_doubles() { return 64 + 3 * (size_t)kMaxSlices + kMaxNr; }
+size_t diag_acc_doubles() { return 64 + 3 * (size_t)kMaxSlices + kMaxNr + kDiagPartsDoubles; }
 
 // The band kernels may use up to kBandBudget bytes of dynamic shared memory; the limit is
 // raised once per device (a per-launch change would race between host threads).
