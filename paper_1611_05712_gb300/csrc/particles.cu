@@ -1284,15 +1284,17 @@ __device__ __forceinline__ int64_t diag_count(const double* acc) {
 
 // CTA sums of K per-thread values into part[blockIdx.x][0..K); the last CTA adds the
 // partials of all CTAs in CTA order into out[0..K).  Every CTA of the grid calls it.
+// active: this thread added something (a warp without one skips its float64 shuffle sums).
 template <int K>
-__device__ void block_partials(const double (&v)[K], double* part, unsigned* ticket, double* out) {
+__device__ void block_partials(const double (&v)[K], bool active, double* part, unsigned* ticket, double* out) {
   static_assert(K <= kDiagThreads / 32, "one warp per value in the final sum");
   __shared__ double wsum[kDiagThreads / 32][K];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool any = __any_sync(0xffffffffu, active);
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const double t = warp_sum(v[k]);
+    const double t = any ? warp_sum(v[k]) : 0.0;
     if (lane == 0) wsum[warp][k] = t;
   }
   __syncthreads();
@@ -1404,7 +1406,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_select(const A a, int64_t
     __syncthreads();   // all reads of wbase and wred[0] done before thread 0 rewrites them
     if (threadIdx.x == 0) base += wred[0];
   }
-  block_partials<8>(v, dp.p1, reinterpret_cast<unsigned*>(acc + kDiagTicket), acc);
+  block_partials<8>(v, v[7] != 0.0, dp.p1, reinterpret_cast<unsigned*>(acc + kDiagTicket), acc);
 }
 
 // pass 2: means (thread 0 of each CTA; CTA 0 stores them and the status), then the centred
@@ -1426,6 +1428,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_central(DiagC c, DiagPart
   if (!ok) return;   // every CTA: no reduction follows
   const int64_t n = diag_count(acc);
   double v[7] = {0, 0, 0, 0, 0, 0, 0};
+  const bool active = blockIdx.x * (int64_t)blockDim.x + threadIdx.x < n;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double w = c.v[5][i];
     const double dx = c.v[0][i] - mean[0], dy = c.v[1][i] - mean[1], dz = c.v[2][i] - mean[2];
@@ -1434,7 +1437,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_central(DiagC c, DiagPart
     v[3] += w * (dy * dy); v[4] += w * (duy * duy); v[5] += w * (dy * duy);
     v[6] += w * (dz * dz);
   }
-  block_partials<7>(v, dp.p2, reinterpret_cast<unsigned*>(acc + kDiagTicket) + 2, acc + kDiagC2);
+  block_partials<7>(v, active, dp.p2, reinterpret_cast<unsigned*>(acc + kDiagTicket) + 2, acc + kDiagC2);
 }
 
 // Slice passes: one compacted particle per thread and iteration; each warp adds each run of
@@ -1614,7 +1617,8 @@ pic_status run_diag(Sim* s, const A& acc_p, int32_t lo, int32_t hi, pic_diag* ou
     k_diag_select<A><<<grid, kDiagThreads, 0, s->stream>>>(acc_p, np, lo, hi, c, dp, acc);
     PIC_LAUNCHED(s);
   }
-  k_diag_central<<<grid, kDiagThreads, 0, s->stream>>>(c, dp, acc);
+  // one CTA per SM: a few compacted particles per thread amortise the CTA's float64 sums
+  k_diag_central<<<std::min(grid, 152), kDiagThreads, 0, s->stream>>>(c, dp, acc);
   PIC_LAUNCHED(s);
   k_diag_slices0<<<grid, kDiagThreads, 0, s->stream>>>(c, acc, kSliceLen, kMaxSlices, sw, sg);
   PIC_LAUNCHED(s);
