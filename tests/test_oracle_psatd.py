@@ -211,3 +211,23 @@ def test_unit_pulse_reach_vs_order():
     assert reach[4] > 4 and reach[8] > 8
     assert reach[4] / 4 > reach[64] / 64
     assert 0.5 * 64 < reach[64] < 3 * 64
+
+
+def test_source_filter_z_factor_is_the_binomial_stencil():
+    # multiplying by cos^2(k_z dz/2) in Fourier space is the periodic (1/4, 1/2, 1/4) stencil
+    # along z; the filter separates into a radial factor per (m, n) times this z factor
+    g, h, _ = _setup(Nz=32, Nr=8, Nm=2)
+    T = O.source_filter(g, h)
+    rng = np.random.default_rng(12)
+    f = _rand(rng, 32)
+    want = 0.25 * np.roll(f, 1) + 0.5 * f + 0.25 * np.roll(f, -1)
+    for m in range(2):
+        for n in (0, 3, 7):
+            tz = T[m][n] / T[m][n][0]
+            assert np.allclose(O.ifft_z(tz * O.fft_z(f)), want, rtol=0, atol=1e-13)
+    # the radial factor is cos^2(k_perp dr / 2): 1 in the long-wavelength limit, falling
+    # with k_perp, within (0, 1]
+    tr = T[:, :, 0]
+    assert np.all(tr > 0) and np.all(tr <= 1)
+    assert np.all(np.diff(tr, axis=1) < 0)
+    assert tr[0][0] == pytest.approx(1.0, abs=0.05)
