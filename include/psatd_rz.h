@@ -388,8 +388,17 @@ pic_status pic_get_tuning(pic_sim* sim, pic_tuning* out);
 pic_status pic_set_sort_interval(pic_sim* sim, int32_t interval);
 pic_status pic_get_sort_interval(pic_sim* sim, int32_t* interval);
 
-/* a10: FP64 diagnostics of the particles with id in [id_lo, id_hi).  slice_sigma (host,
- * may be NULL) receives up to max_slices per-slice std of gamma.  Synchronises. */
+/* a10: FP64 beam diagnostics of the particles with id in [id_lo, id_hi) (section
+ * "Accurate modeling of plasma accelerators in finite order PSATD": normalised rms
+ * emittance and slice energy spread; the fields of pic_diag).  Slices are 0.5 um long from
+ * z_mean - 3 sigma_z, covering particles with 0 <= z - z_mean + 3 sigma_z < 6 sigma_z;
+ * per non-empty slice the weighted std of gamma.  With the moving window on, z is measured
+ * from the window's back edge.  slice_sigma (host, may be NULL) receives the first
+ * min(n_slices, max_slices) per-slice values; sigma_gamma_mean is their mean over all
+ * non-empty slices.  No selected particle or zero total weight: only n_particles and W are
+ * set.  sigma_z = 0: no slices.  More than 65,536 slices: PIC_ERR_ARG.  The passes keep a
+ * compacted float64 copy of the selection in scratch memory that holds no state between
+ * calls.  Synchronises the handle's stream. */
 pic_status pic_diagnostics(pic_sim* sim, int32_t id_lo, int32_t id_hi, pic_diag* out,
                            double* slice_sigma, int32_t max_slices);
 
