@@ -47,7 +47,7 @@ def parse():
     ap.add_argument("--precision", choices=["fp64", "mixed", "bf16"], default="fp64",
                     help="fp64: every stage in float64; mixed: float grids and particles, "
                          "3-term TF32 DHT on tcgen05; bf16: the same with the 6-product BF16 DHT")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-form comparison")
     ap.add_argument("--accuracy-cycles", type=int, default=2000,
