@@ -355,6 +355,9 @@ class Sim:
         return {"dht_n_tile": t.dht_n_tile, "band_chunk": t.band_chunk}
 
     def diagnostics(self, id_lo, id_hi, max_slices=4096):
+        """Beam diagnostics of the particles with id in [id_lo, id_hi) (pic_diagnostics):
+        the pic_diag fields as a dict, plus "slice_sigma_gamma", the first
+        min(n_slices, max_slices) per-slice spreads of gamma."""
         d = PicDiag()
         sl = np.zeros(max_slices)
         _check(self.lib.pic_diagnostics(self.h, int(id_lo), int(id_hi), ctypes.byref(d),
