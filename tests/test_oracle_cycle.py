@@ -54,3 +54,22 @@ def test_rigid_relativistic_beam_fields_co_move(small):
     moved = np.abs(E1 - np.roll(E0, shift, axis=-1)).max() / np.abs(E0).max()
     static = np.abs(E1 - E0).max() / np.abs(E0).max()
     assert moved < 0.02 and static > 0.1
+
+
+@pytest.mark.parametrize("order_p", [0, 32])
+def test_initial_beam_fields_are_boosted_coulomb_fields(small, order_p):
+    """A rigid beam moving along +z at beta carries B = (beta/c) z_hat x E (the Lorentz
+    transform of its rest-frame field): B_r = -beta E_theta / c, B_theta = beta E_r / c,
+    B_z = 0, mode by mode in real space (R-init; the plasma is neutral at t = 0)."""
+    w, g, P, npl, beams = small
+    st = O.make_state(g, order_p, True, P, npl, beams)
+    (_, _, gam), = beams
+    beta = np.sqrt(1.0 - 1.0 / gam ** 2)
+    Er, Et, Ez = st.E
+    Br, Bt, Bz = st.B
+    scale = beta * np.abs(Er).max() / O.C_LIGHT
+    assert scale > 0
+    assert np.abs(Bt - beta * Er / O.C_LIGHT).max() < 1e-12 * scale
+    assert np.abs(Br + beta * Et / O.C_LIGHT).max() < 1e-12 * scale
+    assert np.abs(Bz).max() < 1e-12 * scale
+    assert np.abs(Ez).max() > 1e-3 * np.abs(Er).max() / gam ** 2   # the longitudinal field exists
