@@ -429,25 +429,33 @@ pic_status pic_selftest_wait_timeout(pic_sim* sim, int32_t max_polls);
 pic_status pic_launch_count(pic_sim* sim, int64_t* launches);
 
 /* ---- allocation-free variant ----------------------------------------------------
- * The paper has no counterpart to this entry point; it exists for callers that cannot
- * allocate device memory when they need the sort: code inside another framework's step
- * while that step is being captured into a CUDA graph (cudaMalloc is not allowed during
- * capture), or applications that give this library a fixed memory budget at start-up
- * and forbid allocation afterwards.  It computes exactly what pic_sort computes (cell
- * keys iz*Nr+ir and the stable permutation), but takes the particle coordinates and the
- * output arrays as plain device pointers and needs no pic_sim workspace.
+ * The paper has no counterpart to this entry point.  It exists for callers that cannot
+ * allocate device memory when they need the sort: applications that give this library a
+ * fixed memory budget at start-up and forbid allocation afterwards, or hosts whose own
+ * allocator owns the device and keeps cudaMalloc away from the libraries they load.
+ * It computes the cell keys iz*Nr+ir and the stable permutation of pic_sort on a
+ * PIC_FP64 handle without a moving window (the same float64 key arithmetic), but takes
+ * the particle coordinates and the output arrays as plain device pointers and needs no
+ * pic_sim workspace.  Differences from pic_sort: non-finite coordinates get key 0
+ * silently (pic_sort also raises PIC_ERR_NUMERIC on its handle); the mixed-precision
+ * handles compute their keys from cell-relative float32 positions, and a moving window
+ * gives inactive particles keys past the cells, neither of which applies here.
  *   x, y, z: device float64 [n]; keys, perm: device int32 [n] (outputs, caller-owned).
  *   Limits: 0 <= n <= 262144 and Nz*Nr <= 65536; larger sizes return PIC_ERR_ARG with a
  *   message.  dz, dr > 0.  stream: cudaStream_t (NULL = legacy default stream).
- * Its scratch (2.1 MB) is a fixed __device__ array inside the library: every GPU that
+ * Cost: O(n) plus the ordering of each cell's entries, at most 128^2/32 comparisons per
+ * lane for cells of up to 128 entries and an O(c log c) CTA sort for larger ones, so a
+ * cell holding all n particles stays a few passes over them.
+ * Its scratch (1.84 MB) is a fixed __device__ array inside the library: every GPU that
  * loads the library holds it until the process exits.  The call allocates nothing
  * (no cudaMalloc/cudaFree, no allocating library routine).  All calls share that array
  * and the counts are cleared at the start of each call, so calls whose kernels overlap
  * on the GPU (different streams, or different host threads on one device) race and must
  * be serialised by the caller.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Asynchronous on the stream; non-finite coordinates get
- * key 0.  Errors: PIC_ERR_ARG, PIC_ERR_CUDA. */
+ * device address (cudaGetSymbolAddress) with that device current and keeps it for the
+ * life of the process: do not use the call across a reset of the device
+ * (cudaDeviceReset) in the same process.  Asynchronous on the stream.  Errors:
+ * PIC_ERR_ARG, PIC_ERR_CUDA. */
 pic_status pic_sort_keys_noalloc(const double* x, const double* y, const double* z, int64_t n,
                                  int32_t Nz, int32_t Nr, double dz, double dr, int32_t* keys,
                                  int32_t* perm, void* stream);

@@ -15,6 +15,7 @@
 #include <mutex>
 #include <vector>
 
+#include "cell_sort.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -253,7 +254,8 @@ __global__ void k_scatter(const int32_t* keys, int64_t np, int32_t* cursor, int3
 
 // Within each cell, order the particle indices ascending (this makes the counting sort
 // stable and deterministic).  Cells with <= 16 particles: insertion sort by one thread;
-// larger ones are queued for the warp kernel.
+// cells up to kWarpCellMax are queued at the front of big_list for a warp each, larger
+// ones at its back for a CTA each (big_count[0], big_count[1]; cell_sort.cuh).
 constexpr int kSmallCell = 16;
 __global__ void k_cell_sort_small(const int32_t* start, const int32_t* tmp, int32_t* perm, int ncell,
                                   int32_t* big_list, int32_t* big_count) {
@@ -261,8 +263,8 @@ __global__ void k_cell_sort_small(const int32_t* start, const int32_t* tmp, int3
     const int s0 = start[c], n = start[c + 1] - s0;
     if (n == 0) continue;
     if (n > kSmallCell) {
-      int slot = atomicAdd(big_count, 1);
-      big_list[slot] = c;
+      if (n <= kWarpCellMax) big_list[atomicAdd(big_count, 1)] = c;
+      else big_list[ncell - 1 - atomicAdd(big_count + 1, 1)] = c;
       continue;
     }
     int32_t v[kSmallCell];
@@ -277,26 +279,29 @@ __global__ void k_cell_sort_small(const int32_t* start, const int32_t* tmp, int3
 }
 
 // With tail = 1 the inactive sub-bins past the ncell cells are copied over as they are
-// (nothing depends on the order of inactive particles).
-__global__ void k_cell_sort_big(const int32_t* start, const int32_t* tmp, int32_t* perm,
-                                const int32_t* big_list, const int32_t* big_count, int ncell, int tail) {
+// (nothing depends on the order of inactive particles).  The cells queued at the back of
+// big_list are sorted by whole CTAs, which use the cell's range of tmp as their second
+// buffer.
+__global__ void __launch_bounds__(256) k_cell_sort_big(const int32_t* start, int32_t* tmp, int32_t* perm,
+                                                       const int32_t* big_list, const int32_t* big_count,
+                                                       int ncell, int tail) {
+  __shared__ int32_t sm[kCellChunk];
   if (tail) {
     const int32_t b = start[ncell], e = start[ncell + kTailBins];
     for (int32_t i = b + blockIdx.x * blockDim.x + threadIdx.x; i < e; i += gridDim.x * blockDim.x) perm[i] = tmp[i];
   }
-  const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
-  const int nbig = *big_count;
-  for (int b = gw; b < nbig; b += nw) {
+  const int nmid = big_count[0], nhuge = big_count[1];
+  for (int b = gw; b < nmid; b += nw) {
     const int c = big_list[b];
-    const int s0 = start[c], n = start[c + 1] - s0;
-    for (int k = lane; k < n; k += 32) {
-      const int32_t e = tmp[s0 + k];
-      int rank = 0;
-      for (int q = 0; q < n; ++q) rank += (tmp[s0 + q] < e);
-      perm[s0 + rank] = e;
-    }
+    const int s0 = start[c];
+    warp_rank_cell(tmp + s0, perm + s0, start[c + 1] - s0);
+  }
+  for (int b = blockIdx.x; b < nhuge; b += gridDim.x) {
+    const int c = big_list[ncell - 1 - b];
+    const int s0 = start[c];
+    cta_sort_cell(tmp + s0, perm + s0, tmp + s0, start[c + 1] - s0, sm);
   }
 }
 
@@ -1881,7 +1886,7 @@ pic_status launch_sort(Sim* s) {
   int32_t* cursor = reinterpret_cast<int32_t*>(s->at<char>(s->lay.scan_blk) + 4 * 4096 * sizeof(int32_t));
   int32_t* slot = s->win.on ? reinterpret_cast<int32_t*>(s->win.ws + s->win.slot) : nullptr;
   PIC_CUDA(cudaMemsetAsync(count, 0, sizeof(int32_t) * (ncell + kTailBins + 1), s->stream));   // cells + inactive
-  PIC_CUDA(cudaMemsetAsync(big_count, 0, sizeof(int32_t), s->stream));
+  PIC_CUDA(cudaMemsetAsync(big_count, 0, 2 * sizeof(int32_t), s->stream));
   if (np == 0) return PIC_OK;
   const bool win = slot != nullptr;
   if (is_mixed(s)) {

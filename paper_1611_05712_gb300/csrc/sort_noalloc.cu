@@ -1,17 +1,20 @@
 // Allocation-free cell-key sort: pic_sort_keys_noalloc (declared in include/psatd_rz.h).
 //
-// Some callers cannot allocate device memory at the moment they need the sort: code
-// running inside another framework's step that is being captured into a CUDA graph
-// (cudaMalloc is not allowed during capture), or embedding applications that hand this
-// library a fixed memory budget and forbid any allocation after start-up.  This entry
-// point needs no workspace from them: its scratch (per-cell counts, offsets, scatter
-// cursors, the unsorted index list) lives in one file-scope __device__ array of fixed
-// size, which every GPU that loads the library holds until the process exits.
+// Some callers cannot allocate device memory at the moment they need the sort:
+// applications that hand this library a fixed memory budget at start-up and forbid any
+// allocation afterwards, or hosts whose own allocator owns the whole device and keeps
+// cudaMalloc out of reach of the libraries they load.  This entry point needs no
+// workspace from them: its scratch (per-cell counts, offsets, scatter cursors, the
+// unsorted index list, the queue of crowded cells) lives in one file-scope __device__
+// array of fixed size, which every GPU that loads the library holds until the process
+// exits.
 //
-// It computes the same cell keys and the same stable permutation as the sort stage of
-// the PIC cycle (pic_sort), with kernels of its own.
+// It computes the cell keys and the stable permutation of the sort stage of the FP64
+// PIC cycle without a moving window (pic_sort on a PIC_FP64 handle), with kernels of its
+// own; the ordering of crowded cells shares cell_sort.cuh with pic_sort.
 #include <mutex>
 
+#include "cell_sort.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -19,19 +22,24 @@ namespace {
 
 constexpr int kNaMaxCells = 65536;          // Nz * Nr
 constexpr int kNaMaxParticles = 262144;
+constexpr int kNaMaxHuge = kNaMaxParticles / (kWarpCellMax + 1) + 1;   // cells sorted by a CTA
 constexpr int kNaMaxDevices = 64;
-// int32 layout: count[cells + 1] | start[cells + 1] | cursor[cells] | tmp[particles]
+// int32 layout: count[cells + 1] | start[cells + 1] | cursor[cells] | tmp[particles] |
+// nhuge[1] | huge[kNaMaxHuge]
 constexpr size_t kNaCount = 0;
 constexpr size_t kNaStart = kNaCount + kNaMaxCells + 1;
 constexpr size_t kNaCursor = kNaStart + kNaMaxCells + 1;
 constexpr size_t kNaTmp = kNaCursor + kNaMaxCells;
-constexpr size_t kNaInts = kNaTmp + kNaMaxParticles;   // 2.1 MB
+constexpr size_t kNaNHuge = kNaTmp + kNaMaxParticles;
+constexpr size_t kNaHuge = kNaNHuge + 1;
+constexpr size_t kNaInts = kNaHuge + kNaMaxHuge;   // 1.84 MB
 
 static __device__ __align__(256) int32_t g_sort_scratch[kNaInts];
 
 __global__ void k_na_zero(int32_t* sc, int ncell) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= ncell; i += gridDim.x * blockDim.x)
     sc[kNaCount + i] = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sc[kNaNHuge] = 0;
 }
 
 __global__ void k_na_keys(const double* x, const double* y, const double* z, int n, int Nz, int Nr,
@@ -96,18 +104,29 @@ __global__ void k_na_scatter(const int32_t* keys, int n, int32_t* sc) {
 }
 
 // One warp per cell: the indices of a cell, ranked ascending, give the stable order.
-__global__ void k_na_cell_rank(const int32_t* sc, int ncell, int32_t* perm) {
-  const int lane = threadIdx.x & 31;
+// Cells of more than kWarpCellMax entries are queued for k_na_cell_big.
+__global__ void k_na_cell_rank(int32_t* sc, int ncell, int32_t* perm) {
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncell; c += nw) {
     const int s0 = sc[kNaStart + c], cnt = sc[kNaStart + c + 1] - s0;
-    const int32_t* t = sc + kNaTmp + s0;
-    for (int k = lane; k < cnt; k += 32) {
-      const int32_t e = t[k];
-      int rank = 0;
-      for (int q = 0; q < cnt; ++q) rank += (t[q] < e);
-      perm[s0 + rank] = e;
+    if (cnt <= kWarpCellMax) {
+      warp_rank_cell(sc + kNaTmp + s0, perm + s0, cnt);
+    } else if ((threadIdx.x & 31) == 0) {
+      sc[kNaHuge + atomicAdd(sc + kNaNHuge, 1)] = c;
     }
+  }
+}
+
+// One CTA per queued cell: O(n log n) ordering (cell_sort.cuh), the cell's range of the
+// index list serving as the second buffer.
+__global__ void __launch_bounds__(256) k_na_cell_big(int32_t* sc, int32_t* perm) {
+  __shared__ int32_t sm[kCellChunk];
+  const int nh = sc[kNaNHuge];
+  for (int b = blockIdx.x; b < nh; b += gridDim.x) {
+    const int c = sc[kNaHuge + b];
+    const int s0 = sc[kNaStart + c], cnt = sc[kNaStart + c + 1] - s0;
+    int32_t* t = sc + kNaTmp + s0;
+    cta_sort_cell(t, perm + s0, t, cnt, sm);
   }
 }
 
@@ -172,6 +191,8 @@ extern "C" pic_status pic_sort_keys_noalloc(const double* x, const double* y, co
     PIC_CUDA(cudaGetLastError());
     const int cb = (ncell * 32 + 255) / 256 < 2432 ? (ncell * 32 + 255) / 256 : 2432;
     k_na_cell_rank<<<cb, 256, 0, s>>>(sc, ncell, perm);
+    PIC_CUDA(cudaGetLastError());
+    k_na_cell_big<<<152, 256, 0, s>>>(sc, perm);
     PIC_CUDA(cudaGetLastError());
   }
   return PIC_OK;

@@ -59,3 +59,30 @@ def test_copy_window_rejects_bad_arguments():
     got = b.get("E")
     assert np.array_equal(got[..., 8:24], np.concatenate([E[..., 56:], E[..., :8]], axis=-1))
     assert np.abs(got[..., :8]).max() == 0.0 and np.abs(got[..., 24:]).max() == 0.0
+
+
+def test_sort_of_one_cell_holding_every_particle_is_bounded():
+    """pic_sort with 300,000 particles in one cell (FP64 handle): the cell's entries are
+    ordered by an O(n log n) CTA sort, the permutation is the identity (stable order of
+    equal keys, as the oracle's stable sort gives) and the sort stays in milliseconds."""
+    import torch
+    n, Nz, Nr = 300000, 64, 32
+    cfg = bd.make_config(Nz, Nr, 1, DZ, DZ, DZ / O.C_LIGHT, 0, True, bd.PIC_FP64, n)
+    s = bd.Sim(cfg)
+    P = {k: np.zeros(n) for k in bd.SOA} | {"id": np.arange(n, dtype=np.int32)}
+    P["x"][:], P["y"][:], P["z"][:], P["w"][:] = 3.3 * DZ, 1.1 * DZ, 7.5 * DZ, 1.0
+    s.write_particles(P)
+    s.sort()
+    s.sync()
+    g = O.Grid(Nz, Nr, 1, DZ, DZ, DZ / O.C_LIGHT)
+    okeys = O.cell_keys(g, P["x"], P["y"], P["z"])
+    assert np.array_equal(s.get("KEYS"), okeys)
+    assert np.array_equal(s.get("PERM"), O.sort_permutation(okeys))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s.stream)
+    s.sort()
+    e1.record(s.stream)
+    s.sync()
+    torch.cuda.synchronize()
+    assert e0.elapsed_time(e1) < 200.0
+    s.close()
