@@ -657,15 +657,16 @@ def run_order_sweep(args):
             s.autotune()
         s.step(args.sweep_steps)
         d = s.diagnostics(lo, hi)
-        runs[p] = (d, ncr.ez_plane(s.get("E")))
+        runs[p] = (d, ncr.ez_plane(s.get("E")), ncr.beam_of(s.read_particles(), lo, hi))
         s.close()
-    ref_d, ref_ez = runs[0]
+    ref_d, ref_ez, ref_beam = runs[0]
     res = {}
     for p in (4, 8, 16, 32, 64, 128, 256):
-        d, ez = runs[p]
+        d, ez, beam = runs[p]
         res[str(p)] = {"err_eps_x": ncr.err_emittance(d["emit_nx"], ref_d["emit_nx"]),
                        "err_eps_y": ncr.err_emittance(d["emit_ny"], ref_d["emit_ny"]),
-                       "err_sigma_gamma": ncr.err_sigma_gamma(d["slice_sigma_gamma"], ref_d["slice_sigma_gamma"]),
+                       # both runs sliced on the infinite-order run's grid
+                       "err_sigma_gamma": ncr.err_sigma_gamma_runs(beam, ref_beam),
                        "err_ez": ncr.err_ez(ez, ref_ez), "err_ez_l2": ncr.err_ez_l2(ez, ref_ez)}
     print(json.dumps({"metric": "ncr_order_sweep", "unit": "relative error vs infinite order",
                       "config": {"workload": w.name, "cycles": args.sweep_steps, "precision": args.precision,

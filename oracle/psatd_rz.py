@@ -951,3 +951,31 @@ def err_ez(ez_f, ez_inf):
     Ff = np.fft.fft2(np.asarray(ez_f, dtype=np.float64))
     Fi = np.fft.fft2(np.asarray(ez_inf, dtype=np.float64))
     return float(np.sqrt(np.mean(np.abs((Ff - Fi) / Fi) ** 2)))
+
+
+def slice_sigma_gamma_on_grid(z, gamma, w, z_start, n_slices, slice_len: float = SLICE_LEN):
+    """Per-slice weighted std of gamma on a given grid of n_slices slices of slice_len from
+    z_start (AMPA: slices of 0.5 um; R-diag); NaN where a slice is empty.  Used to pair the
+    slices of two runs on one grid (the reference run's) for Err_sigma_gamma."""
+    out = np.full(n_slices, np.nan)
+    members = [[] for _ in range(n_slices)]
+    for zi, gi, wi in zip(z, gamma, w):
+        k = math.floor((zi - z_start) / slice_len)
+        if 0 <= k < n_slices:
+            members[k].append((wi, gi))
+    for k, mem in enumerate(members):
+        if not mem:
+            continue
+        ws = sum(a for a, _ in mem)
+        gm = sum(a * b for a, b in mem) / ws
+        out[k] = math.sqrt(sum(a * (b - gm) ** 2 for a, b in mem) / ws)
+    return out
+
+
+def ncr_resonance_kperp(kz, dz: float, order_p: int, beta: float):
+    """k_perp of the modes that numerical Cherenkov radiation excites for a beam at beta c
+    (NCR, Eq. resonance_k rearranged): beta^2 k_z^2 = k_perp^2 + [k_z]_p^2, so
+    k_perp = sqrt(beta^2 k_z^2 - [k_z]_p^2) where that is real, NaN elsewhere."""
+    kz = np.asarray(kz, dtype=np.float64)
+    d = beta * beta * kz * kz - modified_kz(kz, dz, order_p) ** 2
+    return np.where(d > 0.0, np.sqrt(np.maximum(d, 0.0)), np.nan)

@@ -47,6 +47,49 @@ def test_package_measures_agree_with_the_oracle():
     assert np.allclose(ncr.ez_plane(E), O.field_on_plane(list(E[2])), rtol=1e-14, atol=0)
     a, b = rng.normal(size=(8, 16)) + 3.0, rng.normal(size=(8, 16)) + 3.0
     assert ncr.err_ez(a, b) == pytest.approx(O.err_ez(a, b), rel=1e-13)
-    s1, s2 = rng.uniform(1, 2, 12), rng.uniform(1, 2, 10)
-    assert ncr.err_sigma_gamma(s1, s2) == pytest.approx(O.err_sigma_gamma(s1[:10], s2), rel=1e-14)
+    s1, s2 = rng.uniform(1, 2, 12), rng.uniform(1, 2, 12)
+    assert ncr.err_sigma_gamma(s1, s2) == pytest.approx(O.err_sigma_gamma(s1, s2), rel=1e-14)
+    with pytest.raises(ValueError):
+        ncr.err_sigma_gamma(s1, s2[:10])    # unpaired slices are refused, not truncated
     assert ncr.err_emittance(2.5, 2.0) == pytest.approx(O.err_emittance(2.5, 2.0))
+
+
+def test_slice_spreads_on_a_common_grid_agree_with_the_oracle():
+    """Both runs are sliced on the reference run's grid (z_start = zbar - 3 sigma_z of the
+    reference), so slice i is the same interval of z in both; a run whose beam moved by a
+    fraction of a slice still pairs slice by slice.  The package's binned version agrees
+    with the oracle's loop version, and a beam compared with itself gives 0."""
+    rng = np.random.default_rng(12)
+    n = 4000
+    z_ref = rng.normal(30e-6, 2e-6, n)
+    g_ref = rng.normal(400.0, 0.4, n)
+    w = rng.uniform(0.5, 1.5, n)
+    z_f = z_ref + 0.3e-6                         # shifted by 0.6 of a slice
+    g_f = g_ref * (1.0 + 1e-3 * rng.normal(size=n))
+    z0, ns = ncr.slice_grid(z_ref, w)
+    W = w.sum()
+    zbar = (w * z_ref).sum() / W
+    sz = np.sqrt((w * (z_ref - zbar) ** 2).sum() / W)
+    assert z0 == pytest.approx(zbar - 3 * sz, rel=1e-12) and ns == int(np.ceil(6 * sz / O.SLICE_LEN))
+    for zz, gg in ((z_ref, g_ref), (z_f, g_f)):
+        a = ncr.slice_sigma_gamma(zz, gg, w, z0, ns)
+        b = O.slice_sigma_gamma_on_grid(zz, gg, w, z0, ns)
+        assert np.array_equal(np.isnan(a), np.isnan(b))
+        assert np.allclose(a[~np.isnan(a)], b[~np.isnan(b)], rtol=1e-10, atol=0)
+    ref = {"z": z_ref, "gamma": g_ref, "w": w}
+    assert ncr.err_sigma_gamma_runs(ref, ref) == 0.0
+    e = ncr.err_sigma_gamma_runs({"z": z_f, "gamma": g_f, "w": w}, ref)
+    a = O.slice_sigma_gamma_on_grid(z_f, g_f, w, z0, ns)
+    b = O.slice_sigma_gamma_on_grid(z_ref, g_ref, w, z0, ns)
+    ok = ~np.isnan(a) & ~np.isnan(b) & (b > 0)
+    assert e == pytest.approx(O.err_sigma_gamma(a[ok], b[ok]), rel=1e-9)
+
+
+def test_resonance_curve_of_the_package_agrees_with_the_oracle():
+    g = O.Grid(128, 32, 1, 0.05e-6, 0.05e-6, 0.05e-6 / O.C_LIGHT)
+    beta = 0.9999
+    for p in (4, 8, 32):
+        want = O.ncr_resonance_kperp(g.kz, g.dz, p, beta)
+        got = ncr.resonance_kperp(g.kz, O.modified_kz(g.kz, g.dz, p), beta)
+        assert np.array_equal(np.isnan(got), np.isnan(want))
+        assert np.allclose(got[~np.isnan(got)], want[~np.isnan(want)], rtol=1e-9)   # cancellation near threshold
