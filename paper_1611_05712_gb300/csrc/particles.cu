@@ -571,98 +571,144 @@ GeomF geomf_of(const Sim* s) {
   return g;
 }
 
-struct StencilF {
-  int i0, i1, j0;
-  float wz0, wz1, wr0, wr1;
-};
-
-// r in cells (r / dr)
-__device__ __forceinline__ StencilF stencil_f(const GeomF& g, int iz, float fz, float r) {
-  StencilF st;
-  st.i0 = iz;
-  st.i1 = iz + 1 == g.Nz ? 0 : iz + 1;
-  st.wz1 = fz;
-  st.wz0 = 1.f - fz;
-  const float v = r - 0.5f;
-  const float fj = floorf(v);
-  st.j0 = (int)fminf(fmaxf(fj, -1.f), (float)g.Nr);
-  st.wr1 = v - fj;
-  st.wr0 = 1.f - st.wr1;
-  return st;
-}
-
-__device__ __forceinline__ void polar_f(float x, float y, float& r, float& c, float& s) {
-  r = sqrtf(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)));
-  if (r > 0.f) { c = x / r; s = y / r; } else { c = 1.f; s = 0.f; }
-}
-
-// Transpose of [plane][Nr][Nz] complex planes into [plane][Nz][Nr] (32 x 32 tiles staged in
-// shared memory, both sides coalesced): the gather reads the 4 nodes of a warp's
-// particles, which sit in consecutive r cells of one z row, from consecutive addresses.
-__global__ void k_transpose_rz(const float2* __restrict__ src, float2* __restrict__ dst, int Nr, int Nz) {
-  __shared__ float2 tile[32][33];
-  const size_t plane = (size_t)blockIdx.z * Nr * Nz;
-  const int z0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int r = r0 + k, z = z0 + threadIdx.x;
-    if (r < Nr && z < Nz) tile[k][threadIdx.x] = src[plane + (size_t)r * Nz + z];
+// ------------------------------------------------------------------ mixed form: gather layout
+// E and B of every mode at one node, contiguous: ebn[(i Nr + j) NV + c Nm + m] with
+// NV = 6 Nm and c = E_r, E_theta, E_z, B_r, B_theta, B_z.  A particle's 4 nodes are then
+// two runs (z rows i0, i1) of two adjacent nodes, each node one 16-byte-aligned run of NV
+// complex values read with vector loads.  Built from the [c][m][r][z] planes by
+// k_nodes_rz through shared memory, in tiles of 32 z x tr r nodes and all NV planes.
+__global__ void __launch_bounds__(256) k_nodes_rz(const float2* __restrict__ src, float2* __restrict__ dst, int Nr,
+                                                  int Nz, int NV, int tr) {
+  extern __shared__ float2 node_tile[];   // [32][tr NV + 1]: odd pitch, conflict-free columns
+  const int pitch = tr * NV + 1;
+  const int z0 = blockIdx.x * 32, r0 = blockIdx.y * tr;
+  const int nr = min(tr, Nr - r0), nz = min(32, Nz - z0);
+  const int RZ = Nr * Nz;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int q = ty; q < NV * tr; q += 8) {
+    const int v = q / tr, rr = q - v * tr;
+    if (rr < nr && tx < nz) node_tile[tx * pitch + rr * NV + v] = src[v * RZ + (r0 + rr) * Nz + z0 + tx];
   }
   __syncthreads();
-  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
-    const int z = z0 + k, r = r0 + threadIdx.x;
-    if (r < Nr && z < Nz) dst[plane + (size_t)z * Nr + r] = tile[threadIdx.x][k];
+  const int run = nr * NV;   // contiguous output values of one z row
+  for (int e = threadIdx.x; e < nz * run; e += 256) {
+    const int zz = e / run, k = e - zz * run;
+    dst[((z0 + zz) * Nr + r0) * NV + k] = node_tile[zz * pitch + k];
   }
 }
 
-// Linear interpolation of one complex mode component from the r-fastest copy
-// ([Nz][Nr] plane), with the axis fold of node -1.
-__device__ __forceinline__ float2 interp_t(const float2* grid, const GeomF& g, const StencilF& st, float fold) {
-  float re = 0.f, im = 0.f;
-#pragma unroll
-  for (int dj = 0; dj < 2; ++dj) {
-    int j = st.j0 + dj;
-    float wr = dj ? st.wr1 : st.wr0;
-    if (j < 0) { j = -1 - j; wr *= fold; }
-    if (j >= g.Nr) continue;
-    const float2 a = grid[(size_t)st.i0 * g.Nr + j];
-    const float2 b = grid[(size_t)st.i1 * g.Nr + j];
-    re += wr * (st.wz0 * a.x + st.wz1 * b.x);
-    im += wr * (st.wz0 * a.y + st.wz1 * b.y);
+// Radial nodes of a particle at r (in cells; node j sits at r = j + 1/2) as a pair of
+// adjacent nodes jb, jb + 1 with weights.  Node jb has one weight per fold class: in the
+// axis cell (r < 1/2) the ghost node r = -1/2 is node 0 seen across the axis, so node 0
+// carries wr1 + wr0 (class P: scalars and z components of even modes, r and theta
+// components of odd modes) or wr1 - wr0 (class M: the others), and node 1 nothing.  In
+// the last cell node Nr is dropped (jb = Nr - 2 carries nothing).  Needs Nr >= 2.
+struct RadW {
+  int jb;
+  float aP, aM, b;
+};
+
+__device__ __forceinline__ RadW radial_nodes(float r, int Nr) {
+  const float v = r - 0.5f;
+  const float fj = floorf(v);
+  const float t = v - fj;   // weight of node j0 + 1
+  const int j0 = (int)fj;   // >= -1 for r >= 0
+  RadW w;
+  if (j0 < 0) {
+    w.jb = 0; w.aP = 1.f; w.aM = 2.f * t - 1.f; w.b = 0.f;
+  } else if (j0 >= Nr - 1) {
+    w.jb = Nr - 2; w.aP = 0.f; w.aM = 0.f; w.b = j0 == Nr - 1 ? 1.f - t : 0.f;
+  } else {
+    w.jb = j0; w.aP = 1.f - t; w.aM = w.aP; w.b = t;
   }
-  return make_float2(re, im);
+  return w;
+}
+
+// Fold class of component type zlike (scalars, z components) in mode m: P when the ghost
+// node's sign is +1 ((-1)^m for zlike, -(-1)^m for r and theta components).
+__host__ __device__ constexpr bool class_p(bool zlike, int m) { return zlike == ((m & 1) == 0); }
+
+// r, cos(theta), sin(theta) of (x, y) in cells (theta = 0 on the axis).
+__device__ __forceinline__ void polar_rcp(float x, float y, float& r, float& c, float& s) {
+  const float r2 = __fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y));
+  if (r2 > 0.f) {
+    const float ir = rsqrtf(r2);
+    r = r2 * ir; c = x * ir; s = y * ir;
+  } else {
+    r = 0.f; c = 1.f; s = 0.f;
+  }
+}
+
+// Fields at a particle: F = (E_r, E_theta, E_z, B_r, B_theta, B_z) of
+// Re[F_0 + 2 sum_{m>=1} F_m e^{-i m theta}] interpolated linearly from the 4 nodes.
+template <int NM>
+__device__ __forceinline__ void gather_nodes(const float2* __restrict__ ebn, int Nr, int i0, int i1, float wz0,
+                                             float wz1, const RadW& rw, float c, float s, float F[6]) {
+  constexpr int NV = 6 * NM;
+  float pr[NM], pi[NM];   // e^{-i m theta}, then times the mode multiplicity (2 for m >= 1)
+  pr[0] = 1.f; pi[0] = 0.f;
+#pragma unroll
+  for (int m = 1; m < NM; ++m) {
+    pr[m] = pr[m - 1] * c + pi[m - 1] * s;
+    pi[m] = pi[m - 1] * c - pr[m - 1] * s;
+  }
+#pragma unroll
+  for (int m = 1; m < NM; ++m) { pr[m] *= 2.f; pi[m] *= 2.f; }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) F[k] = 0.f;
+#pragma unroll
+  for (int row = 0; row < 2; ++row) {
+    const float wz = row ? wz1 : wz0;
+    const float4* nd = reinterpret_cast<const float4*>(ebn + ((row ? i1 : i0) * Nr + rw.jb) * NV);
+#pragma unroll
+    for (int node = 0; node < 2; ++node) {
+      const float wP = wz * (node ? rw.b : rw.aP), wM = wz * (node ? rw.b : rw.aM);
+#pragma unroll
+      for (int q = 0; q < NV / 2; ++q) {
+        const float4 d = __ldg(nd + node * (NV / 2) + q);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int v = 2 * q + h, comp = v / NM, m = v - comp * NM;
+          const float w = class_p(comp % 3 == 2, m) ? wP : wM;
+          const float re = h ? d.z : d.x, im = h ? d.w : d.y;
+          F[comp] = fmaf(w * pr[m], re, F[comp]);
+          F[comp] = fmaf(-w * pi[m], im, F[comp]);
+        }
+      }
+    }
+  }
 }
 
 struct DepArgsF {
-  float2* rho;
-  float2* J;
+  float2* rho;   // [Nm][Nr][Nz] or null
+  float2* J;     // [3][Nm][Nr][Nz] (J_r, J_theta, J_z) or null
   float q;
   int32_t id_lo, id_hi;
 };
 
-// A CTA's band of TZ z-rows x JW r nodes (all modes and ncomp components) in shared memory,
-// starting at row iz_lo and node j_lo.  Deposits to nodes in the band go to shared memory;
-// nodes outside it go straight to the global grid, so the result does not depend on how
-// particles move.
+// Shared-memory band of a CTA: TZ z rows (a power of two) from row iz_lo and JW r nodes
+// from node j_lo, node-major.  Node (row, jj) starts at word row RS + jj NWP; it holds NC
+// components (rho first when the band carries it, then J_r, J_theta, J_z), each with, per
+// mode, two int32 words (hi, lo) of the real part and, for m >= 1, two of the imaginary
+// part (mode 0 has a real phase): CW = 4 Nm - 2 words per component.  NWP = NC CW + 1 is
+// odd, so that consecutive nodes start in different banks, and the row stride RS is
+// padded to RS mod 32 = 8, so that the 4 rows read together by the flush do too.
 //
-// The band holds fixed-point sums: a contribution x (charge times weights, before the
-// 1/V_j factor) is y = x 2^S rounded to an integer and split as y = 2^16 hi + lo with
-// 0 <= lo <= 2^16, and hi and lo are added to two int32 planes.  Integer shared-memory
-// atomics are native (float ones are compare-and-swap loops), and integer sums do not
-// depend on the order of the adds.
-// S is chosen per CTA so that |y| <= 2^(46 - log2 chunk) for every contribution of its
-// chunk (2^36 for 1024 particles): |sum of hi| < 2^30 and sum of lo <= 2^(16 + log2 chunk)
-// cannot overflow, and the resolution is 2^-36 (chunk 1024) of the largest possible
-// contribution.  Mode 0 has a real phase, so only the modes m >= 1 have imaginary planes.
-// A band may carry rho as component 0 beside J in components 1..3, with its own scale.
+// Values are 48-bit fixed point: a contribution x (charge times weights, before the 1/V_j
+// factor) becomes y = x 2^S rounded to an integer, y = 2^16 hi + lo with |lo| <= 2^15,
+// and hi and lo are added with integer shared-memory atomics (native, where float ones
+// are compare-and-swap loops, and independent of the order of the adds).  S is chosen per
+// CTA so that |y| <= 2^(46 - log2 chunk) for every contribution of its chunk; an entry
+// takes at most one add per particle, so |sum y| <= 2^46, |sum hi| < 2^31 and
+// |sum lo| <= 2^(15 + log2 chunk).  rho has its own scale (scale0).
 struct BandF {
-  int32_t* tile;   // planes re hi, re lo (P = TZ*ncomp*Nm*JW words each), then im hi, im lo
-                   // (Pim = TZ*ncomp*(Nm-1)*JW words each), or null
-  int iz_lo, TZ, ncomp, P, Pim;   // TZ is a power of two
-  float scale;     // 2^S of the components >= 1 (all components when scale0 is unused)
-  float scale0;    // 2^S of component 0
-  int lgTZ;
-  int j_lo, JW;    // r nodes j_lo .. j_lo + JW - 1
+  int32_t* tile;   // null: no band, every deposit goes to the global grids
+  int iz_lo, TZ, lgTZ, j_lo, JW, RS;
+  float scale, scale0;
 };
+
+__host__ __device__ constexpr int band_node_words(int nm, int nc) { return nc * (4 * nm - 2) + 1; }
+__host__ __device__ constexpr int mode_word(int m) { return m == 0 ? 0 : 4 * m - 2; }
 
 // Launch-wide band parameters: chunk of particles per CTA, at most tz rows (a power of two,
 // 0: no band) and jw_max r nodes; jmargin = r nodes a particle can move before it deposits.
@@ -678,25 +724,27 @@ struct ChunkStats {
   int jmin, jmax;       // range of the particles' lower radial stencil node floor(r/dr - 1/2)
 };
 
-__device__ __forceinline__ void fixed_split(float y, int& hi, int& lo) {
-  const float f = floorf(y * (1.f / 65536.f));   // exact: power-of-two scaling of an integer-valued float
-  hi = (int)f;
-  lo = __float2int_rn(fmaf(-f, 65536.f, y));      // y - 65536 f, exact, in [0, 65536)
+constexpr float kFxHi = 824633720832.f;   // 1.5 2^39: adding it rounds |y| < 2^38 to a multiple of 2^16
+constexpr float kFxLo = 12582912.f;       // 1.5 2^23: adding it rounds |d| < 2^22 to an integer
+
+// Adds a ws, rounded to 48-bit fixed point, to the word pair p[0] (hi), p[1] (lo).  The
+// split uses the magic-number sums above (float adds and integer subtractions of the bit
+// patterns): t - kFxHi = round(a ws / 2^16) 2^16 exactly, and d = a ws - (t - kFxHi) is
+// exact within one rounding and below 2^15 + 1 in magnitude.
+__device__ __forceinline__ void fx_add(int32_t* p, float a, float ws) {
+  const float t = fmaf(a, ws, kFxHi);
+  const float d = fmaf(a, ws, -(t - kFxHi));
+  atomicAdd(p, __float_as_int(t) - __float_as_int(kFxHi));
+  atomicAdd(p + 1, __float_as_int(d + kFxLo) - __float_as_int(kFxLo));
 }
 
-// Fixed-point add of x (re, im) times 2^S to band entry e (imaginary planes: entry ei, modes
-// m >= 1 only).
-__device__ __forceinline__ void band_add(const BandF& bd, int e, int ei, bool im, float sc, float xr, float xi) {
-  int hr, lr;
-  fixed_split(xr * sc, hr, lr);
-  atomicAdd(bd.tile + e, hr);
-  atomicAdd(bd.tile + bd.P + e, lr);
-  if (im) {
-    int hi, li;
-    fixed_split(xi * sc, hi, li);
-    atomicAdd(bd.tile + 2 * bd.P + ei, hi);
-    atomicAdd(bd.tile + 2 * bd.P + bd.Pim + ei, li);
-  }
+// 2^16 hi + lo as the correctly rounded float, with 32-bit integer operations only: the
+// carry of lo moves into hi, then the sum is (h >> 8) 2^24 + ((h & 255) 2^16 + (lo & 65535)),
+// two terms that floats hold exactly, added by one fused multiply-add.
+__device__ __forceinline__ float fx_value(int32_t hi, int32_t lo) {
+  const int32_t h = hi + (lo >> 16);
+  const int32_t l = lo & 0xffff;
+  return fmaf((float)(h >> 8), 16777216.f, (float)(((h & 0xff) << 16) | l));
 }
 
 // Largest |w| and radial stencil range over particles [b0, b1) (all threads of the CTA;
@@ -734,150 +782,189 @@ __device__ __forceinline__ ChunkStats chunk_stats(const PartsF& p, const GeomF& 
 // Band of a chunk of cell-sorted particles whose first and last cells are iz_first, iz_last:
 // rows from iz_first - 1 to iz_last + 2 (moves of up to half a cell per half step, and the
 // +1 node), at most tz_max rows; r nodes from the chunk's lowest stencil node - jmargin to
-// its highest + 1 + jmargin, at most jw_max of them; nodes beyond are simply not banded.
-// bound is an upper bound of |x| over the chunk's contributions.
-// bound0 > 0: component 0 gets its own scale from bound0.
+// its highest + 1 + jmargin (at least 2, at most jw_max); particles whose nodes are not all
+// inside deposit to the global grids.  bound (bound0) is an upper bound of |x| over the
+// chunk's J (rho) contributions.
 __device__ __forceinline__ BandF make_band(int32_t* smem, int iz_first, int iz_last, const GeomF& g, int tz_max,
-                                           int ncomp, float bound, const ChunkStats& cs, int jw_max, int jmargin,
-                                           int lg_chunk, float bound0 = -1.f) {
-  const int j_lo = max(0, cs.jmin - jmargin);
-  const int j_hi = min(g.Nr - 1, cs.jmax + 1 + jmargin);
-  const int JW = max(1, min(jw_max, j_hi - j_lo + 1));
+                                           int nwp, const ChunkStats& cs, int jw_max, int jmargin, int lg_chunk,
+                                           float bound, float bound0) {
+  const int j_lo = min(max(0, cs.jmin - jmargin), g.Nr - 2);
+  const int j_hi = min(g.Nr - 1, max(cs.jmax + 1 + jmargin, j_lo + 1));
+  const int JW = max(2, min(jw_max, j_hi - j_lo + 1));
   if (iz_first < 0 || iz_first >= g.Nz) iz_first = 0;
   if (iz_last < 0 || iz_last >= g.Nz) iz_last = iz_first;
   int span = iz_last - iz_first;
   if (span < 0) span += g.Nz;
   int lg = 2;   // rows: the smallest power of two >= span + 4, at most tz_max (a power of two)
   while ((1 << lg) < span + 4 && (2 << lg) <= tz_max) ++lg;
-  const int rows = 1 << lg;
   int e = 0;
   frexpf(bound, &e);   // bound <= 2^e
   const int S = min(max(46 - lg_chunk - e, -126), 126);
-  int S0 = S;
-  if (bound0 > 0.f) {
-    frexpf(bound0, &e);
-    S0 = min(max(46 - lg_chunk - e, -126), 126);
-  }
-  return BandF{smem, iz_first == 0 ? g.Nz - 1 : iz_first - 1, rows, ncomp, rows * ncomp * g.Nm * JW,
-               rows * ncomp * (g.Nm - 1) * JW, ldexpf(1.f, S), ldexpf(1.f, S0), lg, j_lo, JW};
+  frexpf(bound0, &e);
+  const int S0 = min(max(46 - lg_chunk - e, -126), 126);
+  int RS = JW * nwp;
+  RS += (40 - RS % 32) % 32;   // RS mod 32 = 8
+  return BandF{smem, iz_first == 0 ? g.Nz - 1 : iz_first - 1, 1 << lg, lg, j_lo, JW, RS, ldexpf(1.f, S),
+               ldexpf(1.f, S0)};
 }
 
 // Zero a band (all threads of the CTA).
 __device__ __forceinline__ void band_zero(const BandF& bd) {
   if (!bd.tile) return;
-  for (int k = threadIdx.x; k < 2 * (bd.P + bd.Pim); k += blockDim.x) bd.tile[k] = 0;
+  const int n = bd.TZ * bd.RS;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) bd.tile[k] = 0;
 }
 
-// Add a band's non-zero entries, times 2^-S / V_j, to the global grids (all threads of the
-// CTA).  grid0 is component 0 of the band; component c lives c * G further.  Consecutive
-// threads take consecutive rows of one (component, mode, r) column, which are adjacent in
-// global memory.
-__device__ void band_flush(const BandF& bd, const GeomF& g, float2* grid0, const float* invV) {
-  if (!bd.tile) return;
-  const size_t RZ = (size_t)g.Nr * g.Nz;
-  const float inv_scale = 1.f / bd.scale, inv_scale0 = 1.f / bd.scale0;   // powers of two: exact
-  const int NC = bd.ncomp * g.Nm * bd.JW;   // columns (comp, m, j); entry e = row * NC + col
-  const int NCi = bd.ncomp * (g.Nm - 1) * bd.JW;   // imaginary planes: modes m >= 1
-  const float inv_jw = 1.f / (float)bd.JW, inv_nm = 1.f / (float)g.Nm;
-  for (int k = threadIdx.x; k < bd.P; k += blockDim.x) {
-    const int row = k & (bd.TZ - 1);
-    const int col = k >> bd.lgTZ;
-    // col / JW and cm / Nm from float reciprocals: (n + 1/2)/d is at least 1/(2d) away from
-    // an integer and the product errs by < (n + 1/2) 2^-23 / d, exact for n < 2^22
-    const int cm = (int)(((float)col + 0.5f) * inv_jw);
-    const int jj = col - cm * bd.JW;
-    const int j = bd.j_lo + jj;
-    const int comp = (int)(((float)cm + 0.5f) * inv_nm);
-    const int m = cm - comp * g.Nm;
-    const int e = row * NC + col;
-    const int hr = bd.tile[e], lr = bd.tile[bd.P + e];
-    int hi = 0, li = 0;
-    if (m > 0) {
-      const int ei = row * NCi + (comp * (g.Nm - 1) + m - 1) * bd.JW + jj;
-      hi = bd.tile[2 * bd.P + ei];
-      li = bd.tile[2 * bd.P + bd.Pim + ei];
+// Fixed-point adds of one node: rho (DO_RHO, component 0) and J (DO_J, components NC-3..NC-1).
+// sP, sM: the node's weight in fold classes P and M; qr, qi: charge times e^{+i m theta};
+// vel: (v_r, v_theta, v_z).
+template <int NM, int NC, bool DO_RHO, bool DO_J>
+__device__ __forceinline__ void band_node(int32_t* e, float sP, float sM, const BandF& bd, const float* qr,
+                                          const float* qi, const float* vel) {
+  constexpr int CW = 4 * NM - 2;
+  if (DO_RHO) {
+    const float wP = sP * bd.scale0, wM = sM * bd.scale0;
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+      const float ws = class_p(true, m) ? wP : wM;
+      fx_add(e + mode_word(m), qr[m], ws);
+      if (m) fx_add(e + mode_word(m) + 2, qi[m], ws);
     }
-    if ((hr | lr | hi | li) == 0) continue;
-    const float f = (comp == 0 ? inv_scale0 : inv_scale) * invV[j];
-    const float vr = __ll2float_rn((long long)hr * 65536 + lr) * f;
-    const float vi = __ll2float_rn((long long)hi * 65536 + li) * f;
-    int i = bd.iz_lo + row;
-    if (i >= g.Nz) i -= g.Nz;
-    atomicAdd(grid0 + comp * g.G + m * RZ + (size_t)j * g.Nz + i, make_float2(vr, vi));
+  }
+  if (DO_J) {
+    const float wP = sP * bd.scale, wM = sM * bd.scale;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      int32_t* ek = e + (NC - 3 + k) * CW;
+#pragma unroll
+      for (int m = 0; m < NM; ++m) {
+        const float ws = class_p(k == 2, m) ? wP : wM;
+        fx_add(ek + mode_word(m), vel[k] * qr[m], ws);
+        if (m) fx_add(ek + mode_word(m) + 2, vel[k] * qi[m], ws);
+      }
+    }
   }
 }
 
-// deposit of one particle at (iz+fz, x, y) with velocity (vx, vy, vz) [m/s]
-// Deposit of one particle at (iz+fz, x, y) with velocity (vx, vy, vz) [m/s]: rho (band
-// component 0) and/or J (band components jc0 .. jc0+2).  The geometry of each of the 4 nodes
-// (ghost fold, dropped node Nr, band position) is worked out once per node and mode and
-// shared by the components.  One band at most is in use (bR for rho alone, bJ for J).
-__device__ __forceinline__ void deposit_one_f(const GeomF& g, const DepArgsF& a, const float* invV, const BandF& bR,
-                              const BandF& bJ, int iz, float fz, float x, float y, float w, float vx, float vy,
-                              float vz, bool do_rho, bool do_J, int jc0 = 0) {
-  float r, c, s;
-  polar_f(x, y, r, c, s);
-  const StencilF st = stencil_f(g, iz, fz, r);
-  const float vr = c * vx + s * vy, vt = c * vy - s * vx;
-  const BandF& bd = do_J ? bJ : bR;
-  float phr = 1.f, phi = 0.f;   // e^{+i m theta}
-  const size_t RZ = (size_t)g.Nr * g.Nz;
-  const int NC = bd.ncomp * g.Nm * bd.JW, NCi = bd.ncomp * (g.Nm - 1) * bd.JW;
-  // lanes visit the 4 nodes in an order rotated by the lane index, so that lanes of one
-  // cell (which share their nodes) hit different nodes in the same instruction
-  const int rot = threadIdx.x & 3;
-  for (int m = 0; m < g.Nm; ++m) {
-    const float qre = a.q * w * phr, qim = a.q * w * phi;
-    const float fs = (m & 1) ? -1.f : 1.f, fv = -fs;   // ghost-node signs: scalars and z, r and theta
-    const bool im = m > 0;
+// One node's contributions straight into the global grids (float atomics, 1/V_j applied):
+// the path of the nodes that lie outside a CTA's band.
+template <int NM, bool DO_RHO, bool DO_J>
+__device__ __forceinline__ void global_node(const GeomF& g, const DepArgsF& a, const float* invV, int i, int j,
+                                            float sP, float sM, const float* qr, const float* qi, const float* vel) {
+  const int RZ = g.Nr * g.Nz, G = (int)g.G;
+  const float iv = invV[j];
+  const int off = j * g.Nz + i;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int node = (q + rot) & 3;
-      const int dz = node >> 1, dj = node & 1;
-      const int i = dz ? st.i1 : st.i0;
-      const int j = st.j0 + dj;
-      const float wgt = (dz ? st.wz1 : st.wz0) * (dj ? st.wr1 : st.wr0);
-      const bool folded = j < 0;   // ghost node r_{-1} = node 0 seen across the axis
-      const int jn = folded ? -1 - j : j;
-      if (jn >= g.Nr) continue;     // node Nr is dropped
-      int e = -1, ei = 0;
-      if (bd.tile) {
-        int row = i - bd.iz_lo;
-        if (row < 0) row += g.Nz;
-        const int jj = jn - bd.j_lo;
-        if (row < bd.TZ && (unsigned)jj < (unsigned)bd.JW) {
-          e = row * NC + m * bd.JW + jj;
-          ei = row * NCi + (m - 1) * bd.JW + jj;
-        }
-      }
-      const size_t goff = (size_t)m * RZ + (size_t)jn * g.Nz + i;
-      const float ws = folded ? wgt * fs : wgt, wv = folded ? wgt * fv : wgt;
-      if (do_rho) {
-        if (e >= 0) {
-          band_add(bd, e, ei, im, bd.scale0, qre * ws, qim * ws);
-        } else {
-          const float f = ws * invV[jn];
-          atomicAdd(a.rho + goff, make_float2(qre * f, qim * f));
-        }
-      }
-      if (do_J) {
-        const float xr[3] = {qre * vr, qre * vt, qre * vz}, xi[3] = {qim * vr, qim * vt, qim * vz};
+  for (int m = 0; m < NM; ++m) {
+    if (DO_RHO) {
+      const float f = (class_p(true, m) ? sP : sM) * iv;
+      atomicAdd(a.rho + m * RZ + off, make_float2(qr[m] * f, qi[m] * f));
+    }
+    if (DO_J) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const float wk = k < 2 ? wv : ws;
-          if (e >= 0) {
-            const int cc = jc0 + k;
-            band_add(bd, e + cc * g.Nm * bd.JW, ei + cc * (g.Nm - 1) * bd.JW, im, cc == 0 ? bd.scale0 : bd.scale,
-                     xr[k] * wk, xi[k] * wk);
-          } else {
-            const float f = wk * invV[jn];
-            atomicAdd(a.J + k * g.G + goff, make_float2(xr[k] * f, xi[k] * f));
-          }
-        }
+      for (int k = 0; k < 3; ++k) {
+        const float f = (class_p(k == 2, m) ? sP : sM) * iv * vel[k];
+        atomicAdd(a.J + k * G + m * RZ + off, make_float2(qr[m] * f, qi[m] * f));
       }
     }
-    const float nr = phr * c - phi * s, ni = phr * s + phi * c;
-    phr = nr; phi = ni;
+  }
+}
+
+// Deposit of one particle at (iz + fz, x, y) (cells) with weight w and velocity
+// (vx, vy, vz) [m/s]: rho (DO_RHO) and/or J (DO_J) with weight e^{+i m theta} per mode
+// (the projection onto the e^{-i m theta} modes), linear weights, the axis fold of the
+// ghost node and node Nr dropped (radial_nodes).  Each node goes into the band when it lies
+// inside, else straight into the global grids.  Lanes visit the 4 nodes in an order
+// rotated by the lane index, so that lanes of one cell (which share their nodes) add to
+// different nodes in the same instruction.
+template <int NM, int NC, bool DO_RHO, bool DO_J>
+__device__ __forceinline__ void deposit_nodes(const BandF& bd, const GeomF& g, const DepArgsF& a, const float* invV,
+                                              int iz, float fz, float x, float y, float w, float vx, float vy,
+                                              float vz) {
+  constexpr int NWP = band_node_words(NM, NC);
+  float r, c, s;
+  polar_rcp(x, y, r, c, s);
+  const RadW rw = radial_nodes(r, g.Nr);
+  float qr[NM], qi[NM];
+  qr[0] = a.q * w; qi[0] = 0.f;
+#pragma unroll
+  for (int m = 1; m < NM; ++m) {
+    qr[m] = qr[m - 1] * c - qi[m - 1] * s;
+    qi[m] = qr[m - 1] * s + qi[m - 1] * c;
+  }
+  const float vel[3] = {c * vx + s * vy, c * vy - s * vx, vz};
+  int row0 = iz - bd.iz_lo;
+  if (row0 < 0) row0 += g.Nz;
+  const int jj = rw.jb - bd.j_lo;
+  const int rot = threadIdx.x & 3;
+#pragma unroll 1
+  for (int q = 0; q < 4; ++q) {
+    const int node = (q + rot) & 3, row = node >> 1, nb = node & 1;
+    const float wz = row ? fz : 1.f - fz;
+    const float sP = wz * (nb ? rw.b : rw.aP), sM = wz * (nb ? rw.b : rw.aM);
+    if (sP == 0.f && sM == 0.f) continue;
+    const int brow = row0 + row, bj = jj + nb;
+    if (bd.tile && brow < bd.TZ && (unsigned)bj < (unsigned)bd.JW)
+      band_node<NM, NC, DO_RHO, DO_J>(bd.tile + brow * bd.RS + bj * NWP, sP, sM, bd, qr, qi, vel);
+    else
+      global_node<NM, DO_RHO, DO_J>(g, a, invV, row ? (iz + 1 == g.Nz ? 0 : iz + 1) : iz, rw.jb + nb, sP, sM, qr,
+                                    qi, vel);
+  }
+}
+
+// Add a band's non-zero entries, times 2^-S / V_j, to the global grids (all threads of the
+// CTA): rho (component 0 when RHO0) and J_r, J_theta, J_z (the next three, G apart in J).
+// Consecutive threads take consecutive rows of one (node, component, mode), adjacent in
+// global memory.
+template <int NM, int NC, bool RHO0>
+__device__ void band_flush(const BandF& bd, const GeomF& g, float2* rho, float2* J, const float* invV) {
+  if (!bd.tile) return;
+  constexpr int CW = 4 * NM - 2, NWP = band_node_words(NM, NC), NCM = NC * NM;
+  const int RZ = g.Nr * g.Nz, G = (int)g.G;
+  const float inv_s = 1.f / bd.scale, inv_s0 = 1.f / bd.scale0;   // powers of two: exact
+  const int total = (bd.JW * NCM) << bd.lgTZ;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int row = idx & (bd.TZ - 1);
+    const int q = idx >> bd.lgTZ;
+    const int jj = q / NCM;
+    const int cm = q - jj * NCM;
+    const int k = cm / NM, m = cm - k * NM;
+    const int32_t* e = bd.tile + row * bd.RS + jj * NWP + k * CW + mode_word(m);
+    const int32_t hr = e[0], lr = e[1];
+    const int32_t hi = m ? e[2] : 0, li = m ? e[3] : 0;
+    if ((hr | lr | hi | li) == 0) continue;
+    const int j = bd.j_lo + jj;
+    const float f = (RHO0 && k == 0 ? inv_s0 : inv_s) * invV[j];
+    int i = bd.iz_lo + row;
+    if (i >= g.Nz) i -= g.Nz;
+    float2* grid = RHO0 && k == 0 ? rho : J + (k - (RHO0 ? 1 : 0)) * G;
+    atomicAdd(grid + m * RZ + j * g.Nz + i, make_float2(fx_value(hr, lr) * f, fx_value(hi, li) * f));
+  }
+}
+
+// rho of one particle straight into the global grid (any Nm; the moving window's injection).
+__device__ __forceinline__ void deposit_rho_global(const GeomF& g, float2* rho, const float* invV, float q, int iz,
+                                                   float fz, float x, float y, float w) {
+  float r, c, s;
+  polar_rcp(x, y, r, c, s);
+  const RadW rw = radial_nodes(r, g.Nr);
+  const int RZ = g.Nr * g.Nz;
+  for (int row = 0; row < 2; ++row) {
+    const int i = row ? (iz + 1 == g.Nz ? 0 : iz + 1) : iz;
+    const float wz = row ? fz : 1.f - fz;
+    for (int node = 0; node < 2; ++node) {
+      const float sP = wz * (node ? rw.b : rw.aP), sM = wz * (node ? rw.b : rw.aM);
+      if (sP == 0.f && sM == 0.f) continue;
+      const int j = rw.jb + node;
+      float pr = q * w, pi = 0.f;
+      for (int m = 0; m < g.Nm; ++m) {
+        const float f = (class_p(true, m) ? sP : sM) * invV[j];
+        atomicAdd(rho + m * RZ + j * g.Nz + i, make_float2(pr * f, pi * f));
+        const float nr = pr * c - pi * s;
+        pi = pr * s + pi * c;
+        pr = nr;
+      }
+    }
   }
 }
 
@@ -956,34 +1043,34 @@ __global__ void k_permute_f32(const PartsF src, PartsF dst, const int32_t* __res
   }
 }
 
-// One CTA per chunk of `chunk` consecutive (cell-sorted) particles; with tz > 0 and a single
-// deposit kind the CTA accumulates into a band of tz z-rows starting one row below its
-// first particle's cell.
-// Threads per CTA of the band kernels: one band (up to kBandBudget bytes) per CTA, two CTAs
-// per SM; 512 threads x 64 registers x 2 CTAs fill the register file.
+// One CTA per chunk of `chunk` consecutive (cell-sorted) particles.  Threads per CTA of the
+// band kernels: one band (up to kBandBudget bytes) per CTA, two CTAs per SM; 512 threads x
+// 64 registers x 2 CTAs fill the register file.
 constexpr int kBandThreads = 512;
 
+// rho and/or J of the particles with id in [id_lo, id_hi) at their current positions
+// (the stage call pic_deposit, the ion background, the beams' initial fields).
+// KIND 1: rho (band of 1 component), 2: J (3), 3: both (4, rho first).
+template <int NM, int KIND>
 __global__ void __launch_bounds__(kBandThreads, 2) k_deposit_f32(const PartsF p, int64_t np, GeomF g, DepArgsF a,
                                                                    const float* invV, int32_t* err, BandArgs ba) {
+  constexpr bool DO_RHO = KIND & 1, DO_J = (KIND & 2) != 0;
+  constexpr int NC = (DO_RHO ? 1 : 0) + (DO_J ? 3 : 0);
   extern __shared__ __align__(16) int32_t band_smem[];
   __shared__ ChunkStats stats_slot;
-  const int64_t chunk = ba.chunk;
-  const bool do_rho = a.rho != nullptr, do_J = a.J != nullptr;
-  const float c = (float)kC;
-  const int64_t b0 = blockIdx.x * chunk;
+  const float c_light = (float)kC;
+  const int64_t b0 = blockIdx.x * ba.chunk;
   if (b0 >= np) return;
-  const int64_t b1 = b0 + chunk < np ? b0 + chunk : np;
-  BandF none{nullptr, 0, 0, 0, 0, 0, 1.f, 1.f, 0, 0, 1};
-  BandF band{nullptr, 0, 0, 0, 0, 0, 1.f, 1.f, 0, 0, 1};
-  if (ba.tz > 0 && do_rho != do_J) {
+  const int64_t b1 = b0 + ba.chunk < np ? b0 + ba.chunk : np;
+  BandF band{nullptr, 0, 0, 0, 0, 1, 0, 1.f, 1.f};
+  if (ba.tz > 0) {
     const ChunkStats cs = chunk_stats(p, g, b0, b1, &stats_slot, err);
+    const float qw = fabsf(a.q) * __uint_as_float(cs.wmax_bits);
     if (cs.wmax_bits != 0u)   // a chunk of inactive particles deposits nothing: no band
-      band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, do_rho ? 1 : 3,
-                       fabsf(a.q) * __uint_as_float(cs.wmax_bits) * (do_J ? c : 1.f), cs, ba.jw_max, ba.jmargin,
-                       ba.lg_chunk);
+      band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, band_node_words(NM, NC), cs, ba.jw_max,
+                       ba.jmargin, ba.lg_chunk, qw * c_light, qw);
   }
   band_zero(band);
-  const BandF bR = do_rho ? band : none, bJ = do_J ? band : none;   // copies: no address taken
   __syncthreads();
   for (int64_t i = b0 + threadIdx.x; i < b1; i += blockDim.x) {
     const int32_t id = p.id[i];
@@ -999,15 +1086,15 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_deposit_f32(const PartsF p,
       continue;
     }
     float vx = 0.f, vy = 0.f, vz = 0.f;
-    if (do_J) {
+    if (DO_J) {
       const float ux = p.ux[i] + p.uxl[i], uy = p.uy[i] + p.uyl[i], uz = p.uz[i] + p.uzl[i];
-      const float ig = c * rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
+      const float ig = c_light * rsqrtf(1.f + ux * ux + uy * uy + uz * uz);
       vx = ux * ig; vy = uy * ig; vz = uz * ig;
     }
-    deposit_one_f(g, a, invV, bR, bJ, iz, fz, x, y, wt, vx, vy, vz, do_rho, do_J);
+    deposit_nodes<NM, NC, DO_RHO, DO_J>(band, g, a, invV, iz, fz, x, y, wt, vx, vy, vz);
   }
   __syncthreads();
-  band_flush(band, g, do_rho ? a.rho : a.J, invV);
+  band_flush<NM, NC, DO_RHO>(band, g, a.rho, a.J, invV);
 }
 
 // Advance (iz, fz) by dfz cells, periodic in iz.
@@ -1021,34 +1108,32 @@ __device__ __forceinline__ void advance_z(int& iz, float& fz, float dfz, int Nz)
   if (iz < 0) iz += Nz;
 }
 
-// a2 + a3 (+ a4 J at x^{n+1/2}) in float: gather with mode sum, Boris push of u/c, two half
-// moves (z in cell units), specular reflection at r >= R.
-// One CTA per chunk of `chunk` consecutive (cell-sorted) particles; with tz > 0 the fused J
-// deposit accumulates into a band of tz z-rows from one row below the chunk's first cell
-// (a half step moves a particle by at most half a cell at c dt <= dz).
+// a2 + a3 (+ a4 J at x^{n+1/2}) in float: gather with mode sum from the node-major copy of
+// E and B, Boris push of u/c, two half moves (z in cell units), specular reflection at
+// r >= R.  One CTA per chunk of `chunk` consecutive (cell-sorted) particles; with fuse and
+// tz > 0 the J deposit accumulates into a band of z rows from one row below the chunk's
+// first cell (a half step moves a particle by at most half a cell at c dt <= dz).
 // RHO: also deposit rho^{n+1} at x^{n+1} (band component 0; J in components 1..3, which is
 // the order of the deposit grids, so one flush writes all four).
-template <bool WIN, bool RHO>
+template <int NM, bool WIN, bool RHO>
 __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, int64_t np, GeomF g,
-                                  const float2* __restrict__ EBt, float kq, float kqc, float chdt_dr,
+                                  const float2* __restrict__ ebn, float kq, float kqc, float chdt_dr,
                                   float chdt_dz, DepArgsF dep, const float* invV, int fuse, int32_t* err,
                                   BandArgs ba, WinArgs wa) {
+  constexpr int NC = RHO ? 4 : 3;
   extern __shared__ __align__(16) int32_t band_smem[];
   __shared__ ChunkStats stats_slot;
-  const int64_t chunk = ba.chunk;
-  const size_t RZ = (size_t)g.Nr * g.Nz;
   const float c_light = (float)kC;
-  const int64_t b0 = blockIdx.x * chunk;
+  const int64_t b0 = blockIdx.x * ba.chunk;
   if (b0 >= np) return;
-  const int64_t b1 = b0 + chunk < np ? b0 + chunk : np;
-  const BandF none{nullptr, 0, 0, 0, 0, 0, 1.f, 1.f, 0, 0, 1};
-  BandF band{nullptr, 0, 0, 0, 0, 0, 1.f, 1.f, 0, 0, 1};
+  const int64_t b1 = b0 + ba.chunk < np ? b0 + ba.chunk : np;
+  BandF band{nullptr, 0, 0, 0, 0, 1, 0, 1.f, 1.f};
   if (fuse && ba.tz > 0) {
     const ChunkStats cs = chunk_stats(p, g, b0, b1, &stats_slot, err);
     const float qw = fabsf(dep.q) * __uint_as_float(cs.wmax_bits);
     if (cs.wmax_bits != 0u)   // a chunk of inactive particles deposits nothing: no band
-      band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, RHO ? 4 : 3, qw * c_light, cs, ba.jw_max,
-                       ba.jmargin, ba.lg_chunk, RHO ? qw : -1.f);
+      band = make_band(band_smem, p.iz[b0], p.iz[b1 - 1], g, ba.tz, band_node_words(NM, NC), cs, ba.jw_max,
+                       ba.jmargin, ba.lg_chunk, qw * c_light, qw);
   }
   band_zero(band);
   __syncthreads();
@@ -1071,25 +1156,12 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
       if (zrel < 0) zrel += g.Nz;
       zeta_old = (float)zrel + fz;
     }
+    float r, c, s;
+    polar_rcp(x, y, r, c, s);
+    float F[6];
+    gather_nodes<NM>(ebn, g.Nr, iz, iz + 1 == g.Nz ? 0 : iz + 1, 1.f - fz, fz, radial_nodes(r, g.Nr), c, s, F);
     float uxh = p.ux[i], uyh = p.uy[i], uzh = p.uz[i];
     float uxl = p.uxl[i], uyl = p.uyl[i], uzl = p.uzl[i];
-    float r, c, s;
-    polar_f(x, y, r, c, s);
-    const StencilF st = stencil_f(g, iz, fz, r);
-    float F[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-    float phr = 1.f, phi = 0.f;   // e^{-i m theta}
-    for (int m = 0; m < g.Nm; ++m) {
-      const float fs = (m & 1) ? -1.f : 1.f, fv = -fs;
-      const float mult = m == 0 ? 1.f : 2.f;
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        const float2* base = EBt + (size_t)k * g.G + m * RZ;   // E r, th, z, then B r, th, z
-        const float2 v = interp_t(base, g, st, (k % 3) == 2 ? fs : fv);
-        F[k] += mult * (v.x * phr - v.y * phi);
-      }
-      const float nr = phr * c + phi * s, ni = phi * c - phr * s;
-      phr = nr; phi = ni;
-    }
     const float Ex = F[0] * c - F[1] * s, Ey = F[0] * s + F[1] * c, Ez = F[2];
     const float Bx = F[3] * c - F[4] * s, By = F[3] * s + F[4] * c, Bz = F[5];
     // Boris on u/c: u- = u + kq E, t = kqc B / gamma-, kq = q dt/(2 m c), kqc = q dt/(2 m).
@@ -1116,8 +1188,8 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
     advance_cell(iy, fy, by * chdt_dr);
     advance_z(iz, fz, dzc, g.Nz);
     if (fuse)
-      deposit_one_f(g, dep, invV, none, band, iz, fz, (float)ix + fx, (float)iy + fy, w, bx * c_light,
-                    by * c_light, bz * c_light, false, true, RHO ? 1 : 0);
+      deposit_nodes<NM, NC, false, true>(band, g, dep, invV, iz, fz, (float)ix + fx, (float)iy + fy, w,
+                                         bx * c_light, by * c_light, bz * c_light);
     advance_cell(ix, fx, bx * chdt_dr);
     advance_cell(iy, fy, by * chdt_dr);
     advance_z(iz, fz, dzc, g.Nz);
@@ -1149,12 +1221,11 @@ __global__ void __launch_bounds__(kBandThreads, 2) k_gather_push_f32(PartsF p, i
     p.ixy[i] = pack_cells(ix, iy); p.fx[i] = fx; p.fy[i] = fy; p.fz[i] = fz; p.iz[i] = iz;
     p.ux[i] = uxh; p.uy[i] = uyh; p.uz[i] = uzh;
     p.uxl[i] = uxl; p.uyl[i] = uyl; p.uzl[i] = uzl;
-    if (RHO && !removed)   // rho^{n+1} at x^{n+1} (a removed particle has left)
-      deposit_one_f(g, dep, invV, band, none, iz, fz, (float)ix + fx, (float)iy + fy, w, 0.f, 0.f, 0.f, true,
-                    false);
+    if (RHO && fuse && !removed)   // rho^{n+1} at x^{n+1} (a removed particle has left)
+      deposit_nodes<NM, NC, true, false>(band, g, dep, invV, iz, fz, x, y, w, 0.f, 0.f, 0.f);
   }
   __syncthreads();
-  band_flush(band, g, RHO ? dep.rho : dep.J, invV);
+  band_flush<NM, NC, RHO>(band, g, dep.rho, dep.J, invV);
 }
 
 // float64 SoA (x y z ux uy uz w) <-> FP32 cell-relative particles
@@ -1824,10 +1895,9 @@ __global__ void __launch_bounds__(kWinBlock) k_win_inject_f32(int32_t* flag, int
     p.ux[i] = 0.f; p.uy[i] = 0.f; p.uz[i] = 0.f;
     p.uxl[i] = 0.f; p.uyl[i] = 0.f; p.uzl[i] = 0.f;
     if (dep.rho) {
-      const BandF none{nullptr, 0, 0, 0, 0, 0, 1.f, 1.f, 0, 0, 1};
       const int32_t c = t.ixy[src];
-      deposit_one_f(g, dep, invV, none, none, t.iz[src], t.fz[src], (float)cell_x(c) + t.fx[src],
-                    (float)cell_y(c) + t.fy[src], t.w[src], 0.f, 0.f, 0.f, true, false);
+      deposit_rho_global(g, dep.rho, invV, dep.q, t.iz[src], t.fz[src], (float)cell_x(c) + t.fx[src],
+                         (float)cell_y(c) + t.fy[src], t.w[src]);
     }
   }
 }
@@ -1836,12 +1906,46 @@ __global__ void __launch_bounds__(kWinBlock) k_win_inject_f32(int32_t* flag, int
 
 bool is_mixed(const Sim* s) { return s->cfg.precision != PIC_FP64; }
 
+// Kernel instances of the mixed form by mode count (1..kMaxModes).
+using DepositKernel = void (*)(const PartsF, int64_t, GeomF, DepArgsF, const float*, int32_t*, BandArgs);
+using GatherPushKernel = void (*)(PartsF, int64_t, GeomF, const float2* __restrict__, float, float, float, float,
+                                  DepArgsF, const float*, int, int32_t*, BandArgs, WinArgs);
+
+template <int NM>
+DepositKernel deposit_kernel_nm(int kind) {
+  return kind == 1 ? k_deposit_f32<NM, 1> : kind == 2 ? k_deposit_f32<NM, 2> : k_deposit_f32<NM, 3>;
+}
+
+DepositKernel deposit_kernel(int nm, int kind) {
+  switch (nm) {
+    case 1: return deposit_kernel_nm<1>(kind);
+    case 2: return deposit_kernel_nm<2>(kind);
+    case 3: return deposit_kernel_nm<3>(kind);
+    default: return deposit_kernel_nm<4>(kind);
+  }
+}
+
+template <int NM>
+GatherPushKernel gather_push_kernel_nm(bool win, bool rho) {
+  return win ? (rho ? k_gather_push_f32<NM, true, true> : k_gather_push_f32<NM, true, false>)
+             : (rho ? k_gather_push_f32<NM, false, true> : k_gather_push_f32<NM, false, false>);
+}
+
+GatherPushKernel gather_push_kernel(int nm, bool win, bool rho) {
+  switch (nm) {
+    case 1: return gather_push_kernel_nm<1>(win, rho);
+    case 2: return gather_push_kernel_nm<2>(win, rho);
+    case 3: return gather_push_kernel_nm<3>(win, rho);
+    default: return gather_push_kernel_nm<4>(win, rho);
+  }
+}
+
 // Shared-memory bands for the deposits: chunks of cell-sorted particles per CTA (1024, or
 // the tuned size: a power of two) and a
 // band of ncomp components (all modes, 16 bytes per complex node) within kBandBudget, so
 // that two CTAs fit on an SM: 8 or 4 full z-rows when they fit, else 4 rows of as many r
 // nodes as fit (at least 16).  jmargin: r nodes a particle can move before it deposits.
-constexpr size_t kBandBudget = 100 * 1024;
+constexpr size_t kBandBudget = 104 * 1024;
 struct BandPlan {
   BandArgs args;
   size_t smem;
@@ -1853,21 +1957,22 @@ BandPlan band_plan(const Sim* s, int ncomp, int jmargin) {
   while ((int64_t(1) << lg) < chunk) ++lg;
   BandPlan bp{BandArgs{chunk, 0, 0, jmargin, lg}, 0};
   if (ncomp <= 0) return bp;
-  // one r node of one row: re hi, re lo for every mode, im hi, im lo for the modes m >= 1
-  const size_t node_bytes = (size_t)ncomp * (4 * c.Nm - 2) * sizeof(int32_t);
-  const size_t row_bytes = node_bytes * c.Nr;
+  // one r node of one row: re hi, re lo for every mode, im hi, im lo for the modes m >= 1,
+  // plus one padding word; a row is padded by up to 31 words (BandF)
+  const size_t node_words = (size_t)band_node_words(c.Nm, ncomp);
+  const size_t row_bytes = (node_words * c.Nr + 31) * sizeof(int32_t);
   int tz = 0, jw = 0;
   if (kBandBudget / row_bytes >= 4) {
     tz = kBandBudget / row_bytes >= 8 ? 8 : 4;   // a power of two (Nz >= 8)
     jw = c.Nr;
   } else {
     tz = 4;
-    jw = (int)(kBandBudget / (4 * node_bytes));
+    jw = std::min(c.Nr, (int)((kBandBudget / (4 * sizeof(int32_t)) - 31) / node_words));
     if (jw < 16) return bp;
   }
   bp.args.tz = tz;
   bp.args.jw_max = jw;
-  bp.smem = (size_t)tz * jw * node_bytes;
+  bp.smem = (size_t)tz * (jw * node_words + 31) * sizeof(int32_t);
   return bp;
 }
 
@@ -1960,9 +2065,11 @@ pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, vo
     a.J = (what & PIC_DEP_J) ? s->at<float2>(s->lay.dep) + G : nullptr;
     if (a.J) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * G * sizeof(float2), s->stream));
     if (s->np == 0) return PIC_OK;
-    const bool single = (a.rho != nullptr) != (a.J != nullptr);
-    const BandPlan bp = band_plan(s, single ? (a.rho ? 1 : 3) : 0, 1);
-    k_deposit_f32<<<(int)((s->np + bp.args.chunk - 1) / bp.args.chunk), kBandThreads, bp.smem, s->stream>>>(
+    const int kind = (a.rho ? 1 : 0) | (a.J ? 2 : 0);
+    if (kind == 0) return PIC_OK;
+    const BandPlan bp = band_plan(s, (kind & 1 ? 1 : 0) + (kind & 2 ? 3 : 0), 1);
+    auto* kern = deposit_kernel(s->cfg.Nm, kind);
+    kern<<<(int)((s->np + bp.args.chunk - 1) / bp.args.chunk), kBandThreads, bp.smem, s->stream>>>(
         partsf_of(s, s->cur), s->np, geomf_of(s), a, reinterpret_cast<const float*>(inv_volume(s)), err, bp.args);
   } else {
     DepArgs a;
@@ -2003,14 +2110,14 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, b
     // a half step moves a particle by at most c dt / 2 in r (a full step, for rho, c dt)
     const BandPlan bp = band_plan(s, fuse_current ? (fuse_rho ? 4 : 3) : 0,
                                   1 + (int)std::ceil((fuse_rho ? 1.0 : 0.5) * kC * c.dt / c.dr));
-    // E and B (adjacent, 6 x Nm planes) into the r-fastest gather layout
-    dim3 tgrid((c.Nz + 31) / 32, (c.Nr + 31) / 32, 6 * c.Nm);
-    k_transpose_rz<<<tgrid, dim3(32, 8), 0, s->stream>>>(s->at<float2>(s->lay.E), s->at<float2>(s->lay.ebt), c.Nr,
-                                                          c.Nz);
+    // E and B (adjacent, 6 x Nm planes) into the node-major gather layout
+    const int NV = 6 * c.Nm, tr = NV <= 12 ? 8 : 4;
+    dim3 tgrid((c.Nz + 31) / 32, (c.Nr + tr - 1) / tr);
+    k_nodes_rz<<<tgrid, 256, 32 * (tr * NV + 1) * sizeof(float2), s->stream>>>(
+        s->at<float2>(s->lay.E), s->at<float2>(s->lay.ebt), c.Nr, c.Nz, NV, tr);
     PIC_LAUNCHED(s);
     const int nblk = (int)((s->np + bp.args.chunk - 1) / bp.args.chunk);
-    auto* kern = wa.on ? (fuse_rho ? k_gather_push_f32<true, true> : k_gather_push_f32<true, false>)
-                       : (fuse_rho ? k_gather_push_f32<false, true> : k_gather_push_f32<false, false>);
+    auto* kern = gather_push_kernel(c.Nm, wa.on != 0, fuse_rho);
     kern<<<nblk, kBandThreads, bp.smem, s->stream>>>(
         partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.ebt), kq, kqc, chdt_dr, chdt_dz, a,
         reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args, wa);
@@ -2082,15 +2189,14 @@ pic_status particles_configure_device() {
   PIC_CUDA(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lock(mu);
   if (dev >= 0 && dev < 64 && done[dev]) return PIC_OK;
-  PIC_CUDA(cudaFuncSetAttribute(k_deposit_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBandBudget));
-  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kBandBudget));
-  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kBandBudget));
-  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kBandBudget));
-  PIC_CUDA(cudaFuncSetAttribute(k_gather_push_f32<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kBandBudget));
+  for (int nm = 1; nm <= kMaxModes; ++nm) {
+    for (int kind = 1; kind <= 3; ++kind)
+      PIC_CUDA(cudaFuncSetAttribute(deposit_kernel(nm, kind), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kBandBudget));
+    for (int v = 0; v < 4; ++v)
+      PIC_CUDA(cudaFuncSetAttribute(gather_push_kernel(nm, v & 1, v & 2), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kBandBudget));
+  }
   if (dev >= 0 && dev < 64) done[dev] = true;
   return PIC_OK;
 }
