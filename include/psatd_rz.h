@@ -235,15 +235,16 @@ pic_status pic_step(pic_sim* sim, int32_t n_steps);
 
 /* Stages of one cycle, in order, as timed by pic_step_timed. */
 typedef enum {
-  PIC_STAGE_GATHER_PUSH = 0,  /* a2 + a3 + a4 (J at x^{n+1/2})          */
-  PIC_STAGE_SORT = 1,         /* a1                                     */
-  PIC_STAGE_DEPOSIT = 2,      /* a4 (rho at x^{n+1})                    */
-  PIC_STAGE_FFT_FWD = 3,      /* a5                                     */
-  PIC_STAGE_DHT_FWD = 4,      /* a6                                     */
-  PIC_STAGE_PSATD = 5,        /* a7                                     */
-  PIC_STAGE_DHT_INV = 6,      /* a8                                     */
-  PIC_STAGE_FFT_INV = 7,      /* a9                                     */
-  PIC_NSTAGES = 8
+  PIC_STAGE_GATHER_LAYOUT = 0, /* mixed forms: E, B copied node-major for the gather (FP64: empty) */
+  PIC_STAGE_GATHER_PUSH = 1,  /* a2 + a3 + a4 (J at x^{n+1/2}; mixed forms: and rho at x^{n+1}) */
+  PIC_STAGE_SORT = 2,         /* a1                                     */
+  PIC_STAGE_DEPOSIT = 3,      /* a4 (rho at x^{n+1}, FP64 form)         */
+  PIC_STAGE_FFT_FWD = 4,      /* a5                                     */
+  PIC_STAGE_DHT_FWD = 5,      /* a6                                     */
+  PIC_STAGE_PSATD = 6,        /* a7                                     */
+  PIC_STAGE_DHT_INV = 7,      /* a8                                     */
+  PIC_STAGE_FFT_INV = 8,      /* a9                                     */
+  PIC_NSTAGES = 9
 } pic_stage;
 
 /* pic_step with CUDA events recorded on the handle's stream between the stages.

@@ -23,7 +23,7 @@ BUF = dict(E=0, B=1, EH=2, BH=3, DEP=4, SRC_H=5, RHO_PREV_H=6, RHO_ION=7, KPERP=
 STATUS = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_CUDA", 3: "PIC_ERR_OOM",
           4: "PIC_ERR_TIMEOUT", 5: "PIC_ERR_NUMERIC", 6: "PIC_ERR_STATE"}
 SOA = ("x", "y", "z", "ux", "uy", "uz", "w")
-STAGES = ("gather_push", "sort", "deposit", "fft_fwd", "dht_fwd", "psatd", "dht_inv", "fft_inv")
+STAGES = ("gather_layout", "gather_push", "sort", "deposit", "fft_fwd", "dht_fwd", "psatd", "dht_inv", "fft_inv")
 
 
 class PicConfig(ctypes.Structure):

@@ -554,11 +554,14 @@ pic_status fft_configure_device() {
   PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
-  // power-of-two rows: one padded row buffer, largest for Nz = 8192 float / 4096 double
+  // power-of-two rows: one padded row buffer
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<float, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<float, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
+  // float64 rows of 8192 (one row per CTA, 32 values per thread): 8192 + 1024 padded doubles
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 9216 * 16));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 9216 * 16));
   // Bluestein rows of length M = 8192 (float) / 4096 (double)
   PIC_CUDA(cudaFuncSetAttribute(k_fft_blue<float, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_blue<float, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
@@ -588,8 +591,8 @@ template <typename R, bool INV>
 void launch_pow2_e(Sim* s, int N, const void* in, void* out, const void* twp, const RowCombine& rc, int rows,
                    int rows_per_comp) {
   if (N <= 2048) launch_pow2<R, INV, 8>(s, N, in, out, twp, rc, rows, rows_per_comp);
-  else if (N == 4096 || sizeof(R) == 8) launch_pow2<R, INV, 16>(s, N, in, out, twp, rc, rows, rows_per_comp);
-  else launch_pow2<R, INV, sizeof(R) == 8 ? 16 : 32>(s, N, in, out, twp, rc, rows, rows_per_comp);
+  else if (N == 4096) launch_pow2<R, INV, 16>(s, N, in, out, twp, rc, rows, rows_per_comp);
+  else launch_pow2<R, INV, 32>(s, N, in, out, twp, rc, rows, rows_per_comp);
 }
 
 template <typename R, bool INV, int E>

@@ -2086,7 +2086,7 @@ pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, vo
   return PIC_OK;
 }
 
-pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, bool fuse_rho) {
+pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, bool fuse_rho, cudaEvent_t after_layout) {
   const size_t G = s->grid_elems();
   int32_t* err = s->at<int32_t>(s->lay.err);
   const pic_config& c = s->cfg;
@@ -2116,12 +2116,14 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, b
     k_nodes_rz<<<tgrid, 256, 32 * (tr * NV + 1) * sizeof(float2), s->stream>>>(
         s->at<float2>(s->lay.E), s->at<float2>(s->lay.ebt), c.Nr, c.Nz, NV, tr);
     PIC_LAUNCHED(s);
+    if (after_layout) PIC_CUDA(cudaEventRecord(after_layout, s->stream));
     const int nblk = (int)((s->np + bp.args.chunk - 1) / bp.args.chunk);
     auto* kern = gather_push_kernel(c.Nm, wa.on != 0, fuse_rho);
     kern<<<nblk, kBandThreads, bp.smem, s->stream>>>(
         partsf_of(s, s->cur), s->np, geomf_of(s), s->at<float2>(s->lay.ebt), kq, kqc, chdt_dr, chdt_dz, a,
         reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args, wa);
   } else {
+    if (after_layout) PIC_CUDA(cudaEventRecord(after_layout, s->stream));   // no separate layout
     DepArgs a;
     a.q = c.q;
     a.id_lo = INT32_MIN;

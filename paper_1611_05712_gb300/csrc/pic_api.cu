@@ -44,9 +44,12 @@ pic_status validate(const pic_config* c, int32_t* radix, int32_t* n_pass) {
     set_error("precision %d is not a pic_precision", c->precision);
     return PIC_ERR_ARG;
   }
-  const int max_nz = c->precision == PIC_FP64 ? 4096 : 8192;   // two shared-memory rows per FFT CTA
+  // power-of-two rows hold one row per FFT CTA in shared memory, other lengths two (the
+  // float64 form's rows of other lengths therefore stop at 4096)
+  const bool pow2 = (c->Nz & (c->Nz - 1)) == 0;
+  const int max_nz = c->precision == PIC_FP64 && !pow2 ? 4096 : 8192;
   if (c->Nz < 8 || c->Nz > max_nz) {
-    set_error("Nz=%d must be in [8, %d]", c->Nz, max_nz);
+    set_error("Nz=%d must be in [8, %d]%s", c->Nz, max_nz, max_nz == 4096 ? " (float64 rows of a length that is not a power of two)" : "");
     return PIC_ERR_ARG;
   }
   if (!plan_radix(c->Nz, radix, n_pass)) {
@@ -339,7 +342,7 @@ pic_status field_step(Sim* s, int32_t order_p, Marks* mk = nullptr, int base = 0
   return PIC_OK;
 }
 
-// One PIC cycle; with marks, events 0..8 bracket the eight stages of pic_stage.  With the
+// One PIC cycle; with marks, events 0..9 bracket the nine stages of pic_stage.  With the
 // moving window on, the push removes the particles that leave through the back edge and,
 // when the window moves, the departing column's plasma template is injected after the push
 // (inside the gather_push stage) and the column's fields are removed after the field step
@@ -362,15 +365,15 @@ pic_status step_once(Sim* s, Marks* mk) {
   // reorders particles); particles the moving window injects deposit theirs as they are placed
   const bool fuse_rho = s->cfg.precision != PIC_FP64;
   PIC_CUDA(m.mark(0));
-  if ((st = launch_gather_push(s, 1, wa, fuse_rho)) != PIC_OK) return st;
+  if ((st = launch_gather_push(s, 1, wa, fuse_rho, m.ev ? m.ev[1] : nullptr)) != PIC_OK) return st;
   if (wa.shift && (st = launch_window_inject(s, wa.back_col, fuse_rho)) != PIC_OK) return st;
-  PIC_CUDA(m.mark(1));
+  PIC_CUDA(m.mark(2));
   if (s->sort_interval <= 1 || s->cycle_idx % s->sort_interval == 0)
     if ((st = launch_sort(s)) != PIC_OK) return st;
-  PIC_CUDA(m.mark(2));
-  if (!fuse_rho && (st = deposit_rho_with_background(s)) != PIC_OK) return st;
   PIC_CUDA(m.mark(3));
-  if ((st = field_step(s, -1, mk, 3)) != PIC_OK) return st;   // marks 4..8
+  if (!fuse_rho && (st = deposit_rho_with_background(s)) != PIC_OK) return st;
+  PIC_CUDA(m.mark(4));
+  if ((st = field_step(s, -1, mk, 4)) != PIC_OK) return st;   // marks 5..9
   if (s->win.on) {
     if (wa.shift) {
       if ((st = launch_window_clear(s, wa.back_col)) != PIC_OK) return st;

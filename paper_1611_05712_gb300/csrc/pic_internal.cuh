@@ -211,7 +211,10 @@ pic_status launch_copy_window(Sim* dst_sim, const char* src, int src_nz, int src
 pic_status launch_sort(Sim* s);
 pic_status launch_deposit(Sim* s, int32_t what, int32_t id_lo, int32_t id_hi, void* rho_out);
 // fuse_rho (mixed forms): also deposit rho^{n+1} + background at x^{n+1}.
-pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa = WinArgs{}, bool fuse_rho = false);
+// after_layout (optional): recorded on the handle's stream once the gather layout is built
+// (before the particle kernel), for the stage timing.
+pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa = WinArgs{}, bool fuse_rho = false,
+                              cudaEvent_t after_layout = nullptr);
 pic_status launch_diag(Sim* s, int32_t id_lo, int32_t id_hi, pic_diag* out, double* slice_sigma,
                        int32_t max_slices);
 pic_status build_inv_volume(Sim* s);                        // once, at init

@@ -91,6 +91,16 @@ def large_8192x1024(order_p: int = 32, seed: int = 5, ppc=(2, 2, 3)) -> Workload
                 5000, seed)
 
 
+def large_crop_1024x128(order_p: int = 32, seed: int = 6) -> Workload:
+    """A crop of the large run that the oracle finishes in seconds: 1024 x 128 grid, 3 modes,
+    order 32, 1e17 cm^-3 plasma at 12 macroparticles per cell (2 z x 2 r x 3 theta), and
+    drive and witness beams scaled into the 51.2 um x 6.4 um box (15,625 macroparticles each,
+    1/64 of the large run's, the charge per macroparticle of the large run)."""
+    drive = Beam(15625, 2000.0, 180e-12 / 64, 2.0e-6, 1.0e-6, 38e-6, 0.0)
+    witness = Beam(15625, 400.0, 50e-12 / 64, 0.5e-6, 0.3e-6, 20e-6, 0.0)
+    return _cfg("large_crop_1024x128_m3", 1024, 128, 3, order_p, 1e17, (2, 2, 3), [drive, witness], 1, seed)
+
+
 def tiny(order_p: int = 0, seed: int = 3, Nz=16, Nr=8, Nm=2, n_beam=64) -> Workload:
     """A grid the oracle finishes instantly, for brute-force and stage tests."""
     beam = Beam(n_beam, 50.0, 1e-15, 2 * 0.05e-6, 2 * 0.05e-6, Nz * 0.05e-6 / 2, 1e-2)

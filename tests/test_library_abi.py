@@ -30,7 +30,7 @@ def test_required_bytes_and_validation(lib):
     n = bd.required_bytes(cfg)
     assert n > 256 * 64 * 2 * 16 * 30
     bad = [
-        dict(Nz=2053), dict(Nz=4), dict(Nz=8192), dict(Nr=2), dict(Nr=2048), dict(Nm=0), dict(Nm=5),
+        dict(Nz=2053), dict(Nz=4), dict(Nz=16384), dict(Nz=6000), dict(Nr=2), dict(Nr=2048), dict(Nm=0), dict(Nm=5),
         dict(order_p=3), dict(order_p=-2), dict(order_p=1024), dict(dt=0.0), dict(np_capacity=-1),
         dict(precision=7),
     ]
@@ -45,7 +45,8 @@ def test_required_bytes_and_validation(lib):
 
 
 def test_seven_smooth_lengths_accepted(lib):
-    for nz in (8, 12, 60, 210, 343, 525, 2048, 4096, 3000):
+    # float64 rows: powers of two up to 8192, other 7-smooth lengths up to 4096
+    for nz in (8, 12, 60, 210, 343, 525, 2048, 4096, 3000, 8192):
         c = bd.make_config(nz, 16, 1, 5e-8, 5e-8, 1e-16, 0, True, bd.PIC_FP64, 10)
         out = ctypes.c_size_t()
         assert lib.pic_required_bytes(ctypes.byref(c), ctypes.byref(out)) == 0, nz
