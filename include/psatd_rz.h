@@ -36,7 +36,8 @@
  * PIC_ERR_TIMEOUT.
  *
  * Asynchrony: all calls enqueue work on the handle's stream and return, except
- * pic_init (synchronises once after setup), pic_diagnostics, pic_read_particles,
+ * pic_init (synchronises during set-up: after each sweep of the Hankel matrices' Jacobi SVD
+ * and at its end), pic_diagnostics, pic_read_particles,
  * pic_copy_buffer with a host destination, and pic_sync.
  */
 #ifndef PSATD_RZ_H

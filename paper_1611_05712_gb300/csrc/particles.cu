@@ -577,9 +577,20 @@ GeomF geomf_of(const Sim* s) {
 // two runs (z rows i0, i1) of two adjacent nodes, each node one 16-byte-aligned run of NV
 // complex values read with vector loads.  Built from the [c][m][r][z] planes by
 // k_nodes_rz through shared memory, in tiles of 32 z x tr r nodes and all NV planes.
+// The same launch clears the current grids for the push's deposit (n_zero values from
+// zero2) and starts the charge grid from the ion background (n_copy values, csrc2 to
+// cdst2), spread over all its threads, so that no separate memset and copy run.
 __global__ void __launch_bounds__(256) k_nodes_rz(const float2* __restrict__ src, float2* __restrict__ dst, int Nr,
-                                                  int Nz, int NV, int tr) {
+                                                  int Nz, int NV, int tr, float2* __restrict__ zero2, int n_zero,
+                                                  float2* __restrict__ cdst2, const float2* __restrict__ csrc2,
+                                                  int n_copy) {
   extern __shared__ float2 node_tile[];   // [32][tr NV + 1]: odd pitch, conflict-free columns
+  {
+    const int nthr = gridDim.x * gridDim.y * blockDim.x;
+    const int t0 = (blockIdx.y * gridDim.x + blockIdx.x) * blockDim.x + threadIdx.x;
+    for (int i = t0; i < n_zero; i += nthr) zero2[i] = make_float2(0.f, 0.f);
+    for (int i = t0; i < n_copy; i += nthr) cdst2[i] = csrc2[i];
+  }
   const int pitch = tr * NV + 1;
   const int z0 = blockIdx.x * 32, r0 = blockIdx.y * tr;
   const int nr = min(tr, Nr - r0), nz = min(32, Nz - z0);
@@ -2098,11 +2109,14 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, b
     a.id_hi = INT32_MAX;
     a.rho = fuse_rho ? s->at<float2>(s->lay.dep) : nullptr;
     a.J = s->at<float2>(s->lay.dep) + G;
-    if (fuse_current) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * G * sizeof(float2), s->stream));
-    if (fuse_rho)   // rho^{n+1} starts from the immobile background
-      PIC_CUDA(cudaMemcpyAsync(a.rho, s->at<float2>(s->lay.rho_ion), G * sizeof(float2), cudaMemcpyDeviceToDevice,
-                               s->stream));
-    if (s->np == 0) return PIC_OK;
+    if (s->np == 0) {
+      if (fuse_current) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * G * sizeof(float2), s->stream));
+      if (fuse_rho)   // rho^{n+1} starts from the immobile background
+        PIC_CUDA(cudaMemcpyAsync(a.rho, s->at<float2>(s->lay.rho_ion), G * sizeof(float2), cudaMemcpyDeviceToDevice,
+                                 s->stream));
+      if (after_layout) PIC_CUDA(cudaEventRecord(after_layout, s->stream));
+      return PIC_OK;
+    }
     const float kq = (float)(c.q * c.dt / (2.0 * c.mass * kC));
     const float kqc = (float)(c.q * c.dt / (2.0 * c.mass));
     const float chdt_dr = (float)(0.5 * kC * c.dt / c.dr);
@@ -2114,7 +2128,8 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, b
     const int NV = 6 * c.Nm, tr = NV <= 12 ? 8 : 4;
     dim3 tgrid((c.Nz + 31) / 32, (c.Nr + tr - 1) / tr);
     k_nodes_rz<<<tgrid, 256, 32 * (tr * NV + 1) * sizeof(float2), s->stream>>>(
-        s->at<float2>(s->lay.E), s->at<float2>(s->lay.ebt), c.Nr, c.Nz, NV, tr);
+        s->at<float2>(s->lay.E), s->at<float2>(s->lay.ebt), c.Nr, c.Nz, NV, tr, a.J, fuse_current ? (int)(3 * G) : 0,
+        a.rho, s->at<float2>(s->lay.rho_ion), fuse_rho ? (int)G : 0);
     PIC_LAUNCHED(s);
     if (after_layout) PIC_CUDA(cudaEventRecord(after_layout, s->stream));
     const int nblk = (int)((s->np + bp.args.chunk - 1) / bp.args.chunk);

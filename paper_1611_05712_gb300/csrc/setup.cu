@@ -137,83 +137,82 @@ __global__ void k_hankel_inv(double* binv, const double* kperp, int Nm, int Nr, 
 }
 
 // ---------------------------------------------------------------------------------
-// One-sided Jacobi SVD, one CTA per matrix.  wt[c][j] = B[j][c] (column c stored
-// contiguously), vt[c][i] = V[i][c], initialised to the identity.  Column pairs are
-// visited in round-robin order (nn-1 rounds of nn/2 disjoint pairs per sweep), one
-// warp per pair.  At the end d[c] = 1/sigma_c^2 for kept columns, 0 otherwise, so that
+// One-sided Jacobi SVD of all 3 Nm Hankel matrices together.  wt[c][j] = B[j][c] (column
+// c stored contiguously), vt[c][i] = V[i][c], initialised to the identity.  Column pairs
+// are visited in round-robin order (nn-1 rounds of nn/2 disjoint pairs per sweep); the
+// pairs of a round are independent, so one launch per round rotates every pair of every
+// matrix at once, one warp per pair.  The host checks after each sweep whether any pair
+// was rotated.  At the end d[c] = 1/sigma_c^2 for kept columns, 0 otherwise, so that
 // pinv(B)[n][j] = sum_c vt[c][n] wt[c][j] d[c].
 // ---------------------------------------------------------------------------------
 constexpr int kSvdThreads = 1024;
+constexpr int kSvdRoundThreads = 256;
 constexpr int kSvdMaxSweeps = 60;
 
-__global__ void __launch_bounds__(kSvdThreads) k_jacobi_svd(const double* binv, double* wt_all,
-                                                            double* vt_all, double* d_all, int Nr,
-                                                            double tol, int32_t* err) {
+__global__ void k_svd_init(const double* binv, double* wt_all, double* vt_all, int Nr, int nmat) {
+  const size_t Nr2 = (size_t)Nr * Nr, total = Nr2 * nmat;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t mat = idx / Nr2;
+    const int e = (int)(idx - mat * Nr2);
+    const int c = e / Nr, j = e - c * Nr;
+    wt_all[idx] = binv[mat * Nr2 + (size_t)j * Nr + c];
+    vt_all[idx] = (c == j) ? 1.0 : 0.0;
+  }
+}
+
+// Pair k of round `round` (nn columns, the padding column of an odd Nr never rotates).
+__global__ void __launch_bounds__(kSvdRoundThreads) k_jacobi_round(double* wt_all, double* vt_all, int Nr, int nn,
+                                                                  int round, double tol, int32_t* rotated) {
+  const int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (k >= nn / 2) return;
+  const size_t off = (size_t)blockIdx.y * Nr * Nr;
+  double* wt = wt_all + off;
+  double* vt = vt_all + off;
+  int p, q;
+  if (k == 0) { p = nn - 1; q = round; }
+  else { p = (round + k) % (nn - 1); q = (round - k + nn - 1) % (nn - 1); }
+  if (p >= Nr || q >= Nr) return;
+  if (p > q) { const int t = p; p = q; q = t; }
+  double* wp = wt + (size_t)p * Nr;
+  double* wq = wt + (size_t)q * Nr;
+  double a = 0.0, b = 0.0, g = 0.0;
+  for (int j = lane; j < Nr; j += 32) {
+    const double x = wp[j], y = wq[j];
+    a = fma(x, x, a); b = fma(y, y, b); g = fma(x, y, g);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    g += __shfl_xor_sync(0xffffffffu, g, o);
+  }
+  if (a == 0.0 || b == 0.0 || fabs(g) <= tol * sqrt(a * b)) return;
+  const double zeta = (b - a) / (2.0 * g);
+  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+  for (int j = lane; j < Nr; j += 32) {
+    const double x = wp[j], y = wq[j];
+    wp[j] = c * x - s * y;
+    wq[j] = s * x + c * y;
+  }
+  double* vp = vt + (size_t)p * Nr;
+  double* vq = vt + (size_t)q * Nr;
+  for (int j = lane; j < Nr; j += 32) {
+    const double x = vp[j], y = vq[j];
+    vp[j] = c * x - s * y;
+    vq[j] = s * x + c * y;
+  }
+  if (lane == 0) *rotated = 1;
+}
+
+// Singular values (column norms of the rotated W) and the cutoff relative to the largest:
+// one CTA per matrix.
+__global__ void __launch_bounds__(kSvdThreads) k_svd_values(const double* wt_all, double* d_all, int Nr) {
   const int mat = blockIdx.x;
-  const double* B = binv + (size_t)mat * Nr * Nr;
-  double* wt = wt_all + (size_t)mat * Nr * Nr;
-  double* vt = vt_all + (size_t)mat * Nr * Nr;
+  const double* wt = wt_all + (size_t)mat * Nr * Nr;
   double* d = d_all + (size_t)mat * Nr;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
-  for (int idx = tid; idx < Nr * Nr; idx += blockDim.x) {
-    int c = idx / Nr, j = idx % Nr;
-    wt[idx] = B[(size_t)j * Nr + c];
-    vt[idx] = (c == j) ? 1.0 : 0.0;
-  }
-  __shared__ int rotated;
   __shared__ double smax;
-  __syncthreads();
-  const int nn = Nr + (Nr & 1);
-  bool converged = false;
-  for (int sweep = 0; sweep < kSvdMaxSweeps; ++sweep) {
-    if (tid == 0) rotated = 0;
-    __syncthreads();
-    for (int round = 0; round < nn - 1; ++round) {
-      for (int k = warp; k < nn / 2; k += nwarps) {
-        int p, q;
-        if (k == 0) { p = nn - 1; q = round; }
-        else { p = (round + k) % (nn - 1); q = (round - k + nn - 1) % (nn - 1); }
-        if (p >= Nr || q >= Nr) continue;  // padding column of an odd Nr
-        if (p > q) { int t = p; p = q; q = t; }
-        double* wp = wt + (size_t)p * Nr;
-        double* wq = wt + (size_t)q * Nr;
-        double a = 0.0, b = 0.0, g = 0.0;
-        for (int j = lane; j < Nr; j += 32) {
-          double x = wp[j], y = wq[j];
-          a = fma(x, x, a); b = fma(y, y, b); g = fma(x, y, g);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          b += __shfl_xor_sync(0xffffffffu, b, o);
-          g += __shfl_xor_sync(0xffffffffu, g, o);
-        }
-        if (a == 0.0 || b == 0.0 || fabs(g) <= tol * sqrt(a * b)) continue;
-        double zeta = (b - a) / (2.0 * g);
-        double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
-        for (int j = lane; j < Nr; j += 32) {
-          double x = wp[j], y = wq[j];
-          wp[j] = c * x - s * y;
-          wq[j] = s * x + c * y;
-        }
-        double* vp = vt + (size_t)p * Nr;
-        double* vq = vt + (size_t)q * Nr;
-        for (int j = lane; j < Nr; j += 32) {
-          double x = vp[j], y = vq[j];
-          vp[j] = c * x - s * y;
-          vq[j] = s * x + c * y;
-        }
-        if (lane == 0) rotated = 1;
-      }
-      __syncthreads();
-    }
-    if (rotated == 0) { converged = true; break; }
-    __syncthreads();
-  }
-  if (!converged && tid == 0) atomicOr(err, kErrTimeout);
-  // singular values, cutoff relative to the largest
-  if (tid == 0) smax = 0.0;
-  __syncthreads();
   for (int c = warp; c < Nr; c += nwarps) {
     double a = 0.0;
     for (int j = lane; j < Nr; j += 32) a = fma(wt[(size_t)c * Nr + j], wt[(size_t)c * Nr + j], a);
@@ -228,7 +227,7 @@ __global__ void __launch_bounds__(kSvdThreads) k_jacobi_svd(const double* binv, 
   }
   __syncthreads();
   for (int c = tid; c < Nr; c += blockDim.x) {
-    double sig = sqrt(d[c]);
+    const double sig = sqrt(d[c]);
     d[c] = (sig > kPinvRcond * smax) ? 1.0 / d[c] : 0.0;
   }
 }
@@ -513,7 +512,30 @@ pic_status launch_setup_hankel(Sim* s) {
   // rotate while |w_p.w_q| > tol |w_p||w_q|; the computed dot product carries a rounding
   // floor of about eps*sqrt(Nr), so the threshold sits above it
   double tol = 2e-15 * std::sqrt((double)Nr);
-  k_jacobi_svd<<<Nm * 3, kSvdThreads, 0, s->stream>>>(binv, wt, vt, d, Nr, tol, err);
+  const int nmat = Nm * 3, nn = Nr + (Nr & 1);
+  k_svd_init<<<(int)std::min<size_t>(blocks_for((size_t)nmat * Nr * Nr, 256), 152 * 16), 256, 0, s->stream>>>(
+      binv, wt, vt, Nr, nmat);
+  PIC_LAUNCHED(s);
+  // the sort's counter word is free during set-up: it records whether a sweep rotated
+  int32_t* rotated = s->at<int32_t>(s->lay.big_count);
+  const dim3 rgrid((unsigned)blocks_for((size_t)(nn / 2) * 32, kSvdRoundThreads), (unsigned)nmat);
+  bool converged = false;
+  for (int sweep = 0; sweep < kSvdMaxSweeps && !converged; ++sweep) {
+    PIC_CUDA(cudaMemsetAsync(rotated, 0, sizeof(int32_t), s->stream));
+    for (int round = 0; round < nn - 1; ++round) {
+      k_jacobi_round<<<rgrid, kSvdRoundThreads, 0, s->stream>>>(wt, vt, Nr, nn, round, tol, rotated);
+      PIC_LAUNCHED(s);
+    }
+    int32_t h = 1;
+    PIC_CUDA(cudaMemcpyAsync(&h, rotated, sizeof(int32_t), cudaMemcpyDeviceToHost, s->stream));
+    PIC_CUDA(cudaStreamSynchronize(s->stream));
+    converged = h == 0;
+  }
+  if (!converged) {
+    set_error("Jacobi SVD of the Hankel matrices did not converge in %d sweeps", kSvdMaxSweeps);
+    return PIC_ERR_TIMEOUT;
+  }
+  k_svd_values<<<nmat, kSvdThreads, 0, s->stream>>>(wt, d, Nr);
   PIC_LAUNCHED(s);
   double* mfwd = s->at<double>(s->lay.mfwd);
   dim3 g(blocks_for(Nr, 32), blocks_for(Nr, 32), Nm * 3);
