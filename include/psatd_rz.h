@@ -380,6 +380,21 @@ pic_status pic_autotune(pic_sim* sim, pic_tuning* out);
 pic_status pic_set_tuning(pic_sim* sim, const pic_tuning* tuning);
 pic_status pic_get_tuning(pic_sim* sim, pic_tuning* out);
 
+/* DHT path of the FP64 form (no counterpart in the paper; the paper's Hankel transform is
+ * the operation, this chooses how the FP64 product is computed):
+ *   PIC_DHT_AUTO        sliced tensor-core product when Nr <= 256, else the SIMT GEMM
+ *                       (the default);
+ *   PIC_DHT_F64_GEMM    FP64 SIMT GEMM on the FP64 units;
+ *   PIC_DHT_F64_SLICED  every row of the matrix and column of the panel scaled by a power
+ *                       of two and cut into seven 7-bit slices (exact BF16 numbers); the
+ *                       slice products accumulate exactly in FP32 on the tensor cores and
+ *                       are combined in FP64: agrees with the FP64 product to about 2^-49
+ *                       of (row max x column max x Nr).  Needs Nr <= 256.
+ * Errors: PIC_ERR_ARG (unknown path, or SLICED with Nr > 256 or a mixed form). */
+typedef enum { PIC_DHT_AUTO = 0, PIC_DHT_F64_GEMM = 1, PIC_DHT_F64_SLICED = 2 } pic_dht_path;
+pic_status pic_set_dht_path(pic_sim* sim, int32_t path);
+pic_status pic_get_dht_path(pic_sim* sim, int32_t* path);
+
 /* Sort interval (no counterpart in the paper): pic_step runs the cell sort (a1) on every
  * interval-th cycle only (1 = every cycle, the default; 1 <= interval <= 16).  The sort
  * changes no particle's state; it orders the particles so that the deposit bands of the

@@ -18,6 +18,7 @@ HEADER = os.path.join(os.path.dirname(PKG), "include", "psatd_rz.h")
 
 PIC_FP64, PIC_MIXED_TF32X3, PIC_MIXED_BF16X6 = 0, 1, 2
 PIC_DEP_RHO, PIC_DEP_J = 1, 2
+PIC_DHT_AUTO, PIC_DHT_F64_GEMM, PIC_DHT_F64_SLICED = 0, 1, 2
 BUF = dict(E=0, B=1, EH=2, BH=3, DEP=4, SRC_H=5, RHO_PREV_H=6, RHO_ION=7, KPERP=8,
            HANKEL_INV=9, HANKEL_FWD=10, KZ_MOD=11, KEYS=12, PERM=13)
 STATUS = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_CUDA", 3: "PIC_ERR_OOM",
@@ -121,6 +122,8 @@ def load():
         "pic_window_state": [P, ctypes.POINTER(PicWindowInfo)],
         "pic_set_sort_interval": [P, I32],
         "pic_get_sort_interval": [P, ctypes.POINTER(I32)],
+        "pic_set_dht_path": [P, I32],
+        "pic_get_dht_path": [P, ctypes.POINTER(I32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -340,6 +343,15 @@ class Sim:
     def set_tuning(self, dht_n_tile=0, band_chunk=1024):
         t = PicTuning(dht_n_tile, band_chunk, 0.0, 0.0)
         _check(self.lib.pic_set_tuning(self.h, ctypes.byref(t)), "pic_set_tuning")
+
+    def set_dht_path(self, path):
+        """FP64 form: PIC_DHT_AUTO, PIC_DHT_F64_GEMM or PIC_DHT_F64_SLICED."""
+        _check(self.lib.pic_set_dht_path(self.h, int(path)), "pic_set_dht_path")
+
+    def get_dht_path(self):
+        k = ctypes.c_int32()
+        _check(self.lib.pic_get_dht_path(self.h, ctypes.byref(k)), "pic_get_dht_path")
+        return k.value
 
     def set_sort_interval(self, k):
         _check(self.lib.pic_set_sort_interval(self.h, int(k)), "pic_set_sort_interval")

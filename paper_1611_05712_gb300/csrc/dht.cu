@@ -82,7 +82,8 @@ pic_status launch_gemm_f64(Sim* s, const DhtBatch& b, int ncols) {
 }
 
 pic_status launch_dht(Sim* s, const DhtBatch& b) {
-  if (s->cfg.precision == PIC_FP64) return launch_gemm_f64(s, b, 2 * s->cfg.Nz);
+  if (s->cfg.precision == PIC_FP64)
+    return f64s_active(s) ? launch_dht_f64s(s, b) : launch_gemm_f64(s, b, 2 * s->cfg.Nz);
   return launch_dht_tc(s, b);   // mixed forms: split products on tcgen05 (dht_tc.cu)
 }
 

@@ -32,6 +32,7 @@
 #include <mutex>
 
 #include "pic_internal.cuh"
+#include "tc_common.cuh"
 
 namespace pic {
 namespace {
@@ -39,7 +40,6 @@ namespace {
 constexpr int kTcM = 128;          // rows of D (columns c of Xf) per CTA
 constexpr int kTcMaxN = 256;       // largest N tile, TF32 form
 constexpr int kTcMaxNBf16 = 128;   // largest N tile, BF16 form (three planes per operand)
-constexpr uint32_t kTcWaitCap = 1u << 26;   // mbarrier polls before giving up
 
 struct TcParams {
   int Nr;        // K extent and rows of A
@@ -49,10 +49,6 @@ struct TcParams {
   int tmem_cols; // power of two >= max(32, NT)
   int m_tiles;   // 128-column tiles per batch
 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 // Byte offset of 16-byte chunk `ch` (0..7) of row `row` in a K-major SW128 tile.
 __device__ __forceinline__ uint32_t sw128_off(int row, int ch) {
@@ -76,39 +72,11 @@ __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float(b);
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-// Bounded wait for completion `parity` of an mbarrier; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  const uint32_t a = smem_u32(bar);
-  for (uint32_t it = 0; it < kTcWaitCap; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                        uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
@@ -151,17 +119,6 @@ __device__ __forceinline__ void split_bf16x3(float x, uint32_t& b0, uint32_t& b1
   b2 = __bfloat16_as_ushort(__float2bfloat16_rn(r2));
 }
 
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// One arrival on `bar` that also expects `bytes` of asynchronous-copy transactions.
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
 // 2-D tiled tensor copy global -> shared (box at inner coordinate x, row y), completing
 // its bytes on `bar`.  x is a multiple of 32 floats, so the start is 128-byte aligned.
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar) {
@@ -196,10 +153,6 @@ struct TcMaps {
 // before tensor memory is released the CTA waits (bounded) for its copies and MMAs.
 constexpr int kWsThreads = 416;   // 8 producer warps, 4 epilogue warps, 1 MMA warp
 constexpr int kWsMaxStages = 4;
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 
 struct WsTile {
   int b, n0, c0;
@@ -512,6 +465,8 @@ EncodeTiledFn encode_fn() {
 }
 
 }  // namespace
+
+void* tensor_map_encoder() { return reinterpret_cast<void*>(encode_fn()); }
 
 // Tensor maps of the split matrices: 2-D views of each plane (Nr columns j, Nr rows n,
 // rows padded to 16 bytes), box of one 128-byte swizzle row of j (32 float or 64 BF16

@@ -119,6 +119,13 @@ Layout make_layout(const pic_config& c) {
       L.bspec_f = take((size_t)M * 8);
     }
   }
+  if (f64s_supported(c)) {
+    const size_t pitch = (size_t)split_pitch_b16(c.Nr), Nc = 2 * (size_t)c.Nz, nmat = 6 * (size_t)c.Nm;
+    L.f64s_mat = take(nmat * kF64sSlices * c.Nr * pitch * 2);
+    L.f64s_rowexp = take(nmat * c.Nr * 4);
+    L.f64s_panel = take(nmat * kF64sSlices * Nc * pitch * 2);
+    L.f64s_colexp = take(nmat * Nc * 4);
+  }
   if (mixed) {
     for (int b = 0; b < 2; ++b)
       for (int k = 0; k < kPfCount; ++k) L.pf[b][k] = take(cap * 4);
@@ -212,11 +219,8 @@ pic_status dht_forward(Sim* s, int n_comp) {
   for (int comp = 0; comp < n_comp; ++comp)
     for (int m = 0; m < c.Nm; ++m) {
       const size_t moff = ((size_t)m * 3 + slot_of[comp]) * Nr2;
-      if (s->cfg.precision == PIC_FP64) {
-        b.A[b.n] = s->at<double>(s->lay.mfwd) + moff;
-      } else {
-        b.mat[b.n] = (int16_t)(m * 3 + slot_of[comp]);   // the tensor maps select the matrix
-      }
+      if (s->cfg.precision == PIC_FP64) b.A[b.n] = s->at<double>(s->lay.mfwd) + moff;
+      b.mat[b.n] = (int16_t)(m * 3 + slot_of[comp]);   // the tensor maps select the matrix
       b.X[b.n] = s->at<char>(s->lay.tmp) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       b.Y[b.n] = s->at<char>(s->lay.srch) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       ++b.n;
@@ -245,11 +249,8 @@ pic_status fields_forward(Sim* s) {
   for (int comp = 0; comp < 6; ++comp)
     for (int m = 0; m < c.Nm; ++m) {
       const int slot = slot_of[comp % 3];
-      if (c.precision == PIC_FP64) {
-        b.A[b.n] = s->at<double>(s->lay.mfwd) + ((size_t)m * 3 + slot) * Nr2;
-      } else {
-        b.mat[b.n] = (int16_t)(m * 3 + slot);
-      }
+      if (c.precision == PIC_FP64) b.A[b.n] = s->at<double>(s->lay.mfwd) + ((size_t)m * 3 + slot) * Nr2;
+      b.mat[b.n] = (int16_t)(m * 3 + slot);
       b.X[b.n] = s->at<char>(s->lay.tmp) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       b.Y[b.n] = s->at<char>(s->lay.Eh) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       ++b.n;
@@ -273,11 +274,8 @@ pic_status dht_inverse(Sim* s) {
   for (int comp = 0; comp < 6; ++comp)
     for (int m = 0; m < c.Nm; ++m) {
       const size_t moff = ((size_t)m * 3 + slot_of[comp % 3]) * Nr2;
-      if (s->cfg.precision == PIC_FP64) {
-        b.A[b.n] = s->at<double>(s->lay.binv) + moff;
-      } else {
-        b.mat[b.n] = (int16_t)(kMaxModes * 3 + m * 3 + slot_of[comp % 3]);
-      }
+      if (s->cfg.precision == PIC_FP64) b.A[b.n] = s->at<double>(s->lay.binv) + moff;
+      b.mat[b.n] = (int16_t)(kMaxModes * 3 + m * 3 + slot_of[comp % 3]);
       b.X[b.n] = s->at<char>(s->lay.Eh) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       b.Y[b.n] = s->at<char>(s->lay.tmp) + ((size_t)comp * G + (size_t)m * c.Nr * c.Nz) * s->cplx_bytes;
       ++b.n;
@@ -471,6 +469,7 @@ pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_byt
   s->cplx_bytes = cfg->precision == PIC_FP64 ? 16 : 8;
   s->tune_nt = 0;
   s->tune_chunk = 1024;
+  s->dht_path = PIC_DHT_AUTO;
   s->sort_interval = 1;
   s->cycle_idx = 0;
   s->blue_M = bluestein_length(cfg->Nz, cfg->precision);
@@ -487,6 +486,8 @@ pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_byt
   if ((st = fft_configure_device()) != PIC_OK) return fail(st);
   if ((st = dht_tc_configure_device()) != PIC_OK) return fail(st);
   if ((st = dht_tc_make_maps(s)) != PIC_OK) return fail(st);
+  if ((st = f64s_configure_device()) != PIC_OK) return fail(st);
+  if ((st = f64s_make_maps(s)) != PIC_OK) return fail(st);
   if ((st = particles_configure_device()) != PIC_OK) return fail(st);
   if ((st = launch_setup_twiddles(s)) != PIC_OK) return fail(st);
   if ((st = launch_setup_hankel(s)) != PIC_OK) return fail(st);
@@ -573,6 +574,29 @@ pic_status pic_get_sort_interval(pic_sim* sim, int32_t* interval) {
   CHECK_SIM(s);
   if (!interval) { set_error("interval is NULL"); return PIC_ERR_ARG; }
   *interval = s->sort_interval;
+  return PIC_OK;
+}
+
+pic_status pic_set_dht_path(pic_sim* sim, int32_t path) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (path != PIC_DHT_AUTO && path != PIC_DHT_F64_GEMM && path != PIC_DHT_F64_SLICED) {
+    set_error("dht path %d is not a pic_dht_path", path);
+    return PIC_ERR_ARG;
+  }
+  if (path == PIC_DHT_F64_SLICED && !f64s_supported(s->cfg)) {
+    set_error("the sliced FP64 DHT needs the FP64 form and Nr <= %d", kF64sMaxNr);
+    return PIC_ERR_ARG;
+  }
+  s->dht_path = path;
+  return PIC_OK;
+}
+
+pic_status pic_get_dht_path(pic_sim* sim, int32_t* path) {
+  Sim* s = reinterpret_cast<Sim*>(sim);
+  CHECK_SIM(s);
+  if (!path) { set_error("path is NULL"); return PIC_ERR_ARG; }
+  *path = s->dht_path;
   return PIC_OK;
 }
 

@@ -49,6 +49,9 @@ struct Layout {
   // Nz that is not 7-smooth (Bluestein, 0 otherwise): twiddles of the power-of-two length M,
   // the chirp w_n (Nz), the chirp filter's spectrum (M), float copies
   size_t twm, twm_f, chirp, chirp_f, bspec, bspec_f;
+  // FP64 form with Nr <= 256: the sliced tensor-core DHT (BF16 slice planes of the matrices
+  // and of the current panels, their row and column exponents)
+  size_t f64s_mat, f64s_rowexp, f64s_panel, f64s_colexp;
   size_t total;
 };
 
@@ -113,6 +116,7 @@ struct Sim {
   size_t cplx_bytes;       // 16 (FP64) or 8 (mixed)
   int32_t tune_nt;         // mixed-form DHT N tile (0: built-in rule), see pic_set_tuning
   int32_t tune_chunk;      // particles per CTA of the band kernels
+  int32_t dht_path;        // FP64 form: pic_dht_path (automatic, SIMT GEMM or sliced tensor cores)
   int32_t sort_interval;   // pic_step sorts on every sort_interval-th cycle (1: every cycle)
   int64_t cycle_idx;       // cycles pic_step has run on this handle
   // mixed forms: encoded 2-D tensor maps (CUtensorMap, 128 B each) of the split DHT
@@ -120,6 +124,7 @@ struct Sim {
   struct alignas(64) TensorMapBytes {
     unsigned char b[128];
   } tmaps[2 * kMaxModes * 3][3];
+  TensorMapBytes f64s_maps[2];   // FP64 form: panel planes, matrix planes (sliced DHT)
   WindowState win;
   double* diag_host = nullptr;   // pinned host copy of the diagnostics results (first use)
   // staged particle input (pic_stage_particles / pic_take_particles): a copy stream and
@@ -193,6 +198,17 @@ pic_status launch_dht_tc(Sim* s, const DhtBatch& b);
 pic_status dht_tc_configure_device();   // once per device, before any tcgen05 DHT launch
 pic_status dht_tc_make_maps(Sim* s);     // once per handle: tensor maps of the split matrices
 pic_status launch_wait_selftest(Sim* s, uint32_t max_polls);   // bounded wait that times out
+void* tensor_map_encoder();              // the driver's cuTensorMapEncodeTiled, or null
+int dht_tc_sm_count();                   // SMs of the current device
+// FP64 form, Nr <= kF64sMaxNr: the DHT from exact BF16 slice products on tcgen05 (dht_f64s.cu)
+constexpr int kF64sSlices = 7;
+constexpr int kF64sMaxNr = 256;
+bool f64s_supported(const pic_config& c);
+bool f64s_active(const Sim* s);
+pic_status f64s_configure_device();
+pic_status f64s_make_maps(Sim* s);
+pic_status launch_f64s_setup(Sim* s);
+pic_status launch_dht_f64s(Sim* s, const DhtBatch& b);
 
 // ---- launchers (psatd.cu) ----
 // PSATD update; with a pending window-column removal it is applied to Eh, Bh on load.

@@ -562,7 +562,7 @@ pic_status launch_setup_hankel(Sim* s) {
                                                                        Nm * Nr, c.dr);
   PIC_LAUNCHED(s);
   if (c.precision != PIC_FP64) return convert_hankel_tables(s);
-  return PIC_OK;
+  return launch_f64s_setup(s);
 }
 
 pic_status launch_setup_tables(Sim* s, int32_t order_p) {
