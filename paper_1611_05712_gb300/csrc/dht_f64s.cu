@@ -23,7 +23,7 @@
 // for Nr <= 256 (the exactness bound above); larger Nr keep the FP64 SIMT GEMM.
 //
 // Pieces: k_f64s_matrix slices the matrices at set-up (7 BF16 planes each, K-major);
-// per DHT k_f64s_colexp finds the column exponents and k_f64s_panel slices the panels
+// per DHT k_f64s_colmax finds the column maxima and k_f64s_panel slices the panels
 // into K-major planes; k_dht_f64s is a persistent warp-specialised tcgen05 kernel: one
 // thread issues the tensor-memory-access copies of both operands (7 planes each, 64-byte
 // swizzle, 32 K elements per stage) into a ring of 3 stages, one thread issues the 28
@@ -107,37 +107,48 @@ __global__ void k_f64s_matrix(const double* __restrict__ A, int nmat, int Nr, in
   }
 }
 
-// Per DHT: colexp[b][c] = exponent above max_j |X_b[j][c]|.  One thread per column.
-__global__ void k_f64s_colexp(DhtBatch bt, int Nr, int Nc, int32_t* __restrict__ colexp) {
-  const int b = blockIdx.y;
+// Per DHT: colmax[b][c] = max_j |X_b[j][c]| as the bits of a non-negative double (which
+// order like the values), so that CTAs over slices of j combine with integer atomicMax;
+// colmax starts at 0.  Grid: (columns / 256, rows / 32, items).
+constexpr int kColRows = 32;
+__global__ void k_f64s_colmax(DhtBatch bt, int Nr, int Nc, unsigned long long* __restrict__ colmax) {
+  const int b = blockIdx.z;
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= Nc) return;
   const double* X = static_cast<const double*>(bt.X[b]);
+  const int j0 = blockIdx.y * kColRows, j1 = min(Nr, j0 + kColRows);
   double m = 0.0;
-  for (int j = 0; j < Nr; ++j) m = fmax(m, fabs(X[(size_t)j * Nc + c]));
-  colexp[(size_t)b * Nc + c] = exp_above(m);
+#pragma unroll 8
+  for (int j = j0; j < j1; ++j) m = fmax(m, fabs(X[(size_t)j * Nc + c]));
+  if (m > 0.0) atomicMax(colmax + (size_t)b * Nc + c, (unsigned long long)__double_as_longlong(m));
 }
 
 // Per DHT: the panels into 7 K-major BF16 planes [b * 7 + plane][c][jpad].  Tiles of
 // 64 columns x 32 rows j through shared memory: reads along c, writes along j.
 constexpr int kPanelC = 64, kPanelJ = 32;
 __global__ void __launch_bounds__(256) k_f64s_panel(DhtBatch bt, int Nr, int Nc, int jpad,
-                                                    const int32_t* __restrict__ colexp,
-                                                    uint16_t* __restrict__ planes) {
+                                                    const unsigned long long* __restrict__ colmax,
+                                                    int32_t* __restrict__ colexp, uint16_t* __restrict__ planes) {
   __shared__ uint16_t tile[kSlices][kPanelC][kPanelJ + 2];
   const int b = blockIdx.z;
   const int c0 = blockIdx.x * kPanelC, j0 = blockIdx.y * kPanelJ;
   const double* X = static_cast<const double*>(bt.X[b]);
   const int tc = threadIdx.x & (kPanelC - 1), tj = threadIdx.x >> 6;   // 64 x 4
   const int c = c0 + tc;
-  const int E = c < Nc ? colexp[(size_t)b * Nc + c] : 0;
-  for (int jj = tj; jj < kPanelJ; jj += 4) {
-    const int j = j0 + jj;
-    uint16_t sl[kSlices];
-    const double x = (c < Nc && j < Nr) ? X[(size_t)j * Nc + c] : 0.0;
-    slice7(x, E, sl);
+  const int E = c < Nc ? exp_above(__longlong_as_double((long long)colmax[(size_t)b * Nc + c])) : 0;
+  if (blockIdx.y == 0 && tj == 0 && c < Nc) colexp[(size_t)b * Nc + c] = E;   // for the epilogue
+  double xv[kPanelJ / 4];   // all loads first, then the slicing
 #pragma unroll
-    for (int i = 0; i < kSlices; ++i) tile[i][tc][jj] = sl[i];
+  for (int u = 0; u < kPanelJ / 4; ++u) {
+    const int j = j0 + tj + 4 * u;
+    xv[u] = (c < Nc && j < Nr) ? X[(size_t)j * Nc + c] : 0.0;
+  }
+#pragma unroll
+  for (int u = 0; u < kPanelJ / 4; ++u) {
+    uint16_t sl[kSlices];
+    slice7(xv[u], E, sl);
+#pragma unroll
+    for (int i = 0; i < kSlices; ++i) tile[i][tc][tj + 4 * u] = sl[i];
   }
   __syncthreads();
   // out: for each plane and column, kPanelJ consecutive j (64 bytes); 16 threads per row
@@ -336,28 +347,41 @@ __global__ void __launch_bounds__(kF64sThreads, 1) k_dht_f64s(DhtBatch bt, F64sP
       const int Ec = c < P.Nc ? colexp[(size_t)w.b * P.Nc + c] : 0;
       const int32_t* rexp = rowexp + (size_t)P.mat[w.b] * P.Nr;
       for (int j0 = 0; j0 < kF64sN; j0 += 8) {
-        double y[8];
+        // the group sums of 8 columns: groups 0..3 exact integers below 2^24 in float,
+        // groups 4..6 below 2^25 within one rounding
+        uint32_t r[kSlices][8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) y[e] = 0.0;
-#pragma unroll
-        for (int grp = kSlices - 1; grp >= 0; --grp) {   // smallest weights first
-          uint32_t r[8];
+        for (int grp = 0; grp < kSlices; ++grp) {
           const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + set * kSetCols + grp * kF64sN + (uint32_t)j0;
           asm volatile(
               "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+              : "=r"(r[grp][0]), "=r"(r[grp][1]), "=r"(r[grp][2]), "=r"(r[grp][3]), "=r"(r[grp][4]),
+                "=r"(r[grp][5]), "=r"(r[grp][6]), "=r"(r[grp][7])
               : "r"(taddr)
               : "memory");
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          const double wgt = __longlong_as_double((long long)(1023 - kSliceBits * (grp + 2)) << 52);   // 2^(-W (g+2))
-#pragma unroll
-          for (int e = 0; e < 8; ++e) y[e] = fma((double)__uint_as_float(r[e]), wgt, y[e]);
         }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (c < P.Nc) {
 #pragma unroll
           for (int e = 0; e < 8; ++e) {
             const int n = w.n0 + j0 + e;
-            if (n < P.Nr) Y[(size_t)n * P.Nc + c] = ldexp(y[e], Ec + rexp[n]);
+            if (n >= P.Nr) continue;
+            // sum_g acc_g 2^(-7(g+2)) = T 2^-49 with
+            //   T = (((a0 2^7 + a1) 2^7 + a2) 2^7 + a3) 2^14 + (a4 2^7 + a5 + a6 2^-7):
+            // the exact groups 0..3 in integer arithmetic, the inexact tail (weight
+            // <= 2^-42) in float rounded to an integer; |T| < 2^58.  Then one conversion
+            // and one power-of-two scaling in FP64 (GB300's FP64 unit is the scarce one)
+            const long long a0 = __float2int_rn(__uint_as_float(r[0][e]));
+            const long long a1 = __float2int_rn(__uint_as_float(r[1][e]));
+            const long long a2 = __float2int_rn(__uint_as_float(r[2][e]));
+            const long long a3 = __float2int_rn(__uint_as_float(r[3][e]));
+            const float tail = fmaf(__uint_as_float(r[6][e]), 1.f / 128.f,
+                                    fmaf(__uint_as_float(r[4][e]), 128.f, __uint_as_float(r[5][e])));
+            const long long T = (((a0 * 128 + a1) * 128 + a2) * 128 + a3) * 16384 + __float2ll_rn(tail);
+            const int k = Ec + rexp[n] - kSliceBits * kSlices;   // 2^(E_c + E_n - 49)
+            const double scale = (k >= -1022 && k <= 1023) ? __longlong_as_double((long long)(1023 + k) << 52)
+                                                           : ldexp(1.0, k);
+            Y[(size_t)n * P.Nc + c] = (double)T * scale;
           }
         }
       }
@@ -482,10 +506,12 @@ pic_status launch_dht_f64s(Sim* s, const DhtBatch& b) {
     P.mat[i] = (int16_t)(dir * 3 * Nm + mi);
   }
   int32_t* colexp = s->at<int32_t>(s->lay.f64s_colexp);
-  k_f64s_colexp<<<dim3(blocks_for(Nc, 256), b.n), 256, 0, s->stream>>>(b, Nr, Nc, colexp);
+  unsigned long long* colmax = reinterpret_cast<unsigned long long*>(colexp + (size_t)6 * Nm * Nc);
+  PIC_CUDA(cudaMemsetAsync(colmax, 0, (size_t)b.n * Nc * sizeof(unsigned long long), s->stream));
+  k_f64s_colmax<<<dim3(blocks_for(Nc, 256), blocks_for(Nr, kColRows), b.n), 256, 0, s->stream>>>(b, Nr, Nc, colmax);
   PIC_LAUNCHED(s);
   k_f64s_panel<<<dim3(blocks_for(Nc, kPanelC), blocks_for(Nr, kPanelJ), b.n), 256, 0, s->stream>>>(
-      b, Nr, Nc, pitch, colexp, s->at<uint16_t>(s->lay.f64s_panel));
+      b, Nr, Nc, pitch, colmax, colexp, s->at<uint16_t>(s->lay.f64s_panel));
   PIC_LAUNCHED(s);
   F64sMaps maps;
   maps.panel = s->f64s_maps[0];

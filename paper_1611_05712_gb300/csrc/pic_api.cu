@@ -124,7 +124,7 @@ Layout make_layout(const pic_config& c) {
     L.f64s_mat = take(nmat * kF64sSlices * c.Nr * pitch * 2);
     L.f64s_rowexp = take(nmat * c.Nr * 4);
     L.f64s_panel = take(nmat * kF64sSlices * Nc * pitch * 2);
-    L.f64s_colexp = take(nmat * Nc * 4);
+    L.f64s_colexp = take(nmat * Nc * 4 + nmat * Nc * 8);   // exponents, then the column maxima
   }
   if (mixed) {
     for (int b = 0; b < 2; ++b)

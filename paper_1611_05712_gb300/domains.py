@@ -25,7 +25,8 @@ class GuardedDomains:
     """n_domains equal z subdomains of a handle's grid, each advanced with `guard` cells
     of the neighbouring subdomains on both sides."""
 
-    def __init__(self, cfg: bd.PicConfig, n_domains: int, guard: int, device="cuda:0", stream=None):
+    def __init__(self, cfg: bd.PicConfig, n_domains: int, guard: int, device="cuda:0", stream=None,
+                 dht_path=None):
         if n_domains < 1 or cfg.Nz % n_domains:
             raise ValueError(f"Nz={cfg.Nz} is not a multiple of n_domains={n_domains}")
         self.n = n_domains
@@ -37,6 +38,8 @@ class GuardedDomains:
         lc = bd.make_config(nz_loc, cfg.Nr, cfg.Nm, cfg.dz, cfg.dr, cfg.dt, cfg.order_p, bool(cfg.filter),
                             cfg.precision, 0, cfg.q, cfg.mass)
         self.local = bd.Sim(lc, device=device, stream=stream)
+        if dht_path is not None:   # FP64 form: the DHT path of the local handle (pic_set_dht_path)
+            self.local.set_dht_path(dht_path)
         # source-free: zero deposit and previous spectral charge, kept zero by the steps
         self.local.set("DEP", self.local.zeros("DEP"))
         self.local.set("RHO_PREV_H", self.local.zeros("RHO_PREV_H"))
