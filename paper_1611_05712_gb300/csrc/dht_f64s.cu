@@ -46,9 +46,10 @@ namespace {
 constexpr int kSlices = kF64sSlices;   // S
 constexpr int kSliceBits = 7;       // W
 constexpr int kF64sM = 128;         // panel columns c per tile (TMEM lanes)
-constexpr int kF64sN = 32;          // matrix rows n per tile
+constexpr int kF64sN = 64;          // matrix rows n per tile
+constexpr int kF64sSets = 1;        // accumulator sets in TMEM (7 groups x kF64sN columns each)
 constexpr int kF64sKC = 32;         // K elements per stage (one 64-byte swizzle row of BF16)
-constexpr int kF64sStages = 3;
+constexpr int kF64sStages = 2;
 constexpr int kF64sThreads = 256;   // warp 0: copies, warp 1: MMA, warps 4..7: epilogue
 constexpr uint32_t kF64sPlaneA = kF64sM * 64;   // bytes of one panel plane per stage
 constexpr uint32_t kF64sPlaneB = kF64sN * 64;   // bytes of one matrix plane per stage
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kF64sThreads, 1) k_dht_f64s(DhtBatch bt, F64sP
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nK = (P.Nr + kF64sKC - 1) / kF64sKC;
-  constexpr uint32_t kTmemCols = 512;                 // 2 sets x 7 groups x 32 columns = 448
+  constexpr uint32_t kTmemCols = 512;                 // sets x 7 groups x kF64sN columns <= 512
   constexpr uint32_t kSetCols = kSlices * kF64sN;
 
   if (warp == 1) {
@@ -298,7 +299,7 @@ __global__ void __launch_bounds__(kF64sThreads, 1) k_dht_f64s(DhtBatch bt, F64sP
       uint64_t* last_bar = nullptr;
       uint32_t last_parity = 0;
       for (int t = blockIdx.x; t < P.tiles_total && !*abort_flag; t += gridDim.x, ++i) {
-        const uint32_t set = i & 1, set_use = i >> 1;
+        const uint32_t set = i % kF64sSets, set_use = i / kF64sSets;
         if (set_use > 0 && !mbar_wait(&tempty[set], (set_use - 1) & 1)) { fail(); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d0 = tmem + set * kSetCols;
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(kF64sThreads, 1) k_dht_f64s(DhtBatch bt, F64sP
         if (!ok) break;
         mma_commit(&tfull[set]);
         last_bar = &tfull[set];
-        last_parity = (i >> 1) & 1;
+        last_parity = (i / kF64sSets) & 1;
       }
       if (*abort_flag && last_bar) mbar_wait(last_bar, last_parity);
     }
@@ -338,8 +339,8 @@ __global__ void __launch_bounds__(kF64sThreads, 1) k_dht_f64s(DhtBatch bt, F64sP
     const int q = warp - 4;   // TMEM lanes 32q .. 32q + 31 (warp % 4 == q)
     uint32_t i = 0;
     for (int t = blockIdx.x; t < P.tiles_total && !*abort_flag; t += gridDim.x, ++i) {
-      const uint32_t set = i & 1;
-      if (!mbar_wait(&tfull[set], (i >> 1) & 1)) { fail(); break; }
+      const uint32_t set = i % kF64sSets;
+      if (!mbar_wait(&tfull[set], (i / kF64sSets) & 1)) { fail(); break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const F64sTile w = f64s_tile(t, P);
       double* __restrict__ Y = static_cast<double*>(bt.Y[w.b]);
@@ -398,6 +399,8 @@ __global__ void __launch_bounds__(kF64sThreads, 1) k_dht_f64s(DhtBatch bt, F64sP
 }
 
 constexpr size_t kF64sSmem = 1024 + (size_t)kF64sStages * kF64sStageBytes + 256;
+static_assert(kF64sSets * kSlices * kF64sN <= 512, "accumulators exceed tensor memory");
+static_assert(kF64sSmem <= 227 * 1024, "stages exceed shared memory");
 
 int f64s_pitch(int Nr) { return split_pitch_b16(Nr); }   // BF16 row pitch, 16-byte rows
 
