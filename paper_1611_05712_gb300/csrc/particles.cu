@@ -37,18 +37,27 @@ Parts parts_of(Sim* s, int which) {
 struct GridGeom {
   int Nz, Nr, Nm;
   double dz, dr, L, R;
-  size_t G;   // Nm*Nr*Nz
+  size_t G;      // Nm*Nr*Nz
+  double inv_dr; // 1/dr (float64 divisions are long sequences on GB300's float64 unit)
 };
 
 GridGeom geom_of(const Sim* s) {
   const pic_config& c = s->cfg;
-  GridGeom g{c.Nz, c.Nr, c.Nm, c.dz, c.dr, c.Nz * c.dz, c.Nr * c.dr, s->grid_elems()};
+  GridGeom g{c.Nz, c.Nr, c.Nm, c.dz, c.dr, c.Nz * c.dz, c.Nr * c.dr, s->grid_elems(), 1.0 / c.dr};
   return g;
 }
 
+constexpr double kInvC2 = 1.0 / (kC * kC);   // gamma from u without a float64 division
+
+// r, cos(theta), sin(theta) of (x, y); one division (cos and sin from 1/r).
 __device__ __forceinline__ void polar(double x, double y, double& r, double& c, double& s) {
   r = sqrt(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
-  if (r > 0.0) { c = x / r; s = y / r; } else { c = 1.0; s = 0.0; }
+  if (r > 0.0) {
+    const double ir = 1.0 / r;
+    c = x * ir; s = y * ir;
+  } else {
+    c = 1.0; s = 0.0;
+  }
 }
 
 struct Stencil {
@@ -67,7 +76,9 @@ __device__ __forceinline__ Stencil stencil(const GridGeom& g, double z, double r
   st.i1 = (int)((i0 + 1) % g.Nz);
   st.wz0 = 1.0 - sz;
   st.wz1 = sz;
-  double v = r / g.dr - 0.5;
+  // z / dz stays a correctly rounded division (one ulp of it is ~Nz ulps of a weight);
+  // r / dr (r < R) as a product with 1/dr
+  double v = r * g.inv_dr - 0.5;
   double fj = floor(v);
   double t = v - fj;
   // r >= 0 gives fj >= -1; beyond the last node every weight is dropped anyway
@@ -373,7 +384,7 @@ __global__ void k_deposit(const Parts p, int64_t np, GridGeom g, DepArgs a, cons
     double vx = 0.0, vy = 0.0, vz = 0.0;
     if (do_J) {
       const double ux = p.ux[i], uy = p.uy[i], uz = p.uz[i];
-      const double ig = 1.0 / sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+      const double ig = rsqrt(1.0 + (ux * ux + uy * uy + uz * uz) * kInvC2);
       vx = ux * ig; vy = uy * ig; vz = uz * ig;
     }
     const double wt = p.w[i];
@@ -402,8 +413,8 @@ __device__ __forceinline__ void win_mark(const WinArgs& wa, int32_t id, int64_t 
 // WIN: moving window on (removal behind the back edge); the plain instance has none of it.
 template <bool WIN>
 __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __restrict__ E,
-                              const double2* __restrict__ B, double q, double mass, double dt,
-                              DepArgs dep, const double* invV, int fuse, int32_t* err, WinArgs wa) {
+                              const double2* __restrict__ B, double k, double dt, DepArgs dep,
+                              const double* invV, int fuse, int32_t* err, WinArgs wa) {
   const size_t RZ = (size_t)g.Nr * g.Nz;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -432,11 +443,11 @@ __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __
     }
     const double Ex = F[0] * c - F[1] * s, Ey = F[0] * s + F[1] * c, Ez = F[2];
     const double Bx = F[3] * c - F[4] * s, By = F[3] * s + F[4] * c, Bz = F[5];
-    // Boris
-    const double k = q * dt / (2.0 * mass);
+    // Boris with k = q dt / (2 m) (from the host); 1/gamma^- once for the three t
     const double umx = ux + k * Ex, umy = uy + k * Ey, umz = uz + k * Ez;
-    const double gm = sqrt(1.0 + (umx * umx + umy * umy + umz * umz) / (kC * kC));
-    const double tx = k * Bx / gm, ty = k * By / gm, tz = k * Bz / gm;
+    const double igm = rsqrt(1.0 + (umx * umx + umy * umy + umz * umz) * kInvC2);
+    const double kb = k * igm;
+    const double tx = kb * Bx, ty = kb * By, tz = kb * Bz;
     const double upx = umx + (umy * tz - umz * ty);
     const double upy = umy + (umz * tx - umx * tz);
     const double upz = umz + (umx * ty - umy * tx);
@@ -445,7 +456,7 @@ __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __
     ux = umx + (upy * sz - upz * sy) + k * Ex;
     uy = umy + (upz * sx - upx * sz) + k * Ey;
     uz = umz + (upx * sy - upy * sx) + k * Ez;
-    const double ig = 1.0 / sqrt(1.0 + (ux * ux + uy * uy + uz * uz) / (kC * kC));
+    const double ig = rsqrt(1.0 + (ux * ux + uy * uy + uz * uz) * kInvC2);
     const double vx = ux * ig, vy = uy * ig, vz = uz * ig;
     const double hdt = 0.5 * dt;
     x = __dadd_rn(x, __dmul_rn(hdt, vx));   // no FMA: one ulp of z is ~L/dz ulps of a weight
@@ -461,8 +472,9 @@ __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __
     if (z < 0.0) z += g.L;
     const double r1 = sqrt(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
     if (r1 >= g.R) {
-      const double cx = x / r1, cy = y / r1;
-      const double fr = (2.0 * g.R - r1) / r1;
+      const double ir1 = 1.0 / r1;
+      const double cx = x * ir1, cy = y * ir1;
+      const double fr = (2.0 * g.R - r1) * ir1;
       const double ur = ux * cx + uy * cy;
       ux = ux - 2.0 * ur * cx;
       uy = uy - 2.0 * ur * cy;
@@ -488,7 +500,6 @@ __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __
 
 // ------------------------------------------------------------------ a10: diagnostics
 constexpr int kDiagThreads = 256;
-constexpr double kInvC2 = 1.0 / (kC * kC);   // diagnostics: gamma from u without a float64 division
 constexpr int kMaxSlices = 1 << 16;
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -2139,6 +2150,7 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, b
         reinterpret_cast<const float*>(inv_volume(s)), fuse_current, err, bp.args, wa);
   } else {
     if (after_layout) PIC_CUDA(cudaEventRecord(after_layout, s->stream));   // no separate layout
+    const double kq = c.q * c.dt / (2.0 * c.mass);
     DepArgs a;
     a.q = c.q;
     a.id_lo = INT32_MIN;
@@ -2150,13 +2162,11 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, b
     if (wa.on)
       k_gather_push<true><<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, geom_of(s),
                                                                s->at<double2>(s->lay.E), s->at<double2>(s->lay.B),
-                                                               c.q, c.mass, c.dt, a, inv_volume(s), fuse_current, err,
-                                                               wa);
+                                                               kq, c.dt, a, inv_volume(s), fuse_current, err, wa);
     else
       k_gather_push<false><<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, geom_of(s),
                                                                 s->at<double2>(s->lay.E), s->at<double2>(s->lay.B),
-                                                                c.q, c.mass, c.dt, a, inv_volume(s), fuse_current,
-                                                                err, wa);
+                                                                kq, c.dt, a, inv_volume(s), fuse_current, err, wa);
   }
   PIC_LAUNCHED(s);
   return PIC_OK;
