@@ -54,6 +54,14 @@ struct FftPlan {
 // tables of all passes tile entries 0..N-2), so a warp reads consecutive entries.
 constexpr int kFftThreads = 256;
 
+// Resident CTAs per SM asked of the register allocator for E values per thread.  Float rows
+// of 4096 and 8192 points (E = 16, 32) trade a few spilled bytes for 3 and 2 CTAs per SM:
+// with one CTA per SM a row's loads, passes and stores ran one after another on the SM
+// (8192-point rows of 3 x 1024 x 8192 fields: 1.89 -> 1.14 ms per forward transform).
+template <typename R> constexpr int fft_min_ctas(int E) {
+  return E == 8 ? 4 : (E == 16 ? (sizeof(R) == 4 ? 3 : 2) : (sizeof(R) == 4 ? 2 : 1));
+}
+
 template <typename C2, bool INV> __device__ __forceinline__ C2 conj_if(C2 w) {
   if (INV) w.y = -w.y;
   return w;
@@ -150,7 +158,34 @@ __device__ __forceinline__ void pow2_load_shared(C2 (&v)[E], const RowCtx<C2>& c
   }
 }
 
-// Twiddles w_{LR}^{rk} and the R-point DFTs of a pass.
+// Twiddles w^r = w_{LR}^{rk}, r = 1 .. R-1, of butterfly k of pass (R, L).  Float rows read
+// w^1 from the table and form the other powers with at most three products each (w^2 = w w,
+// w^3 = w^2 w, w^4 = w^2 w^2, w^5 = w^4 w, w^6 = w^4 w^2, w^7 = w^4 w^3), a few float
+// roundings from the tabulated values: one table read per butterfly instead of R - 1, which
+// the register budget of 16 and 32 values per thread could not keep in flight.  Double rows
+// read every power: their products would run on the float64 unit, which bounds those rows.
+template <typename C2, int R>
+__device__ __forceinline__ void pass_twiddles(C2 (&w)[R], const C2* __restrict__ twp, int L, int k) {
+  using Re = decltype(w[0].x);
+  if constexpr (sizeof(Re) == 4) {
+    w[1] = twp[L - 1 + k];
+    if constexpr (R > 2) {
+      w[2] = cmul(w[1], w[1]);
+      w[3] = cmul(w[2], w[1]);
+    }
+    if constexpr (R > 4) {
+      w[4] = cmul(w[2], w[2]);
+      w[5] = cmul(w[4], w[1]);
+      w[6] = cmul(w[4], w[2]);
+      w[7] = cmul(w[4], w[3]);
+    }
+  } else {
+#pragma unroll
+    for (int r = 1; r < R; ++r) w[r] = twp[L - 1 + (r - 1) * L + k];
+  }
+}
+
+// Twiddles and the R-point DFTs of a pass.
 template <typename C2, bool INV, int E, int R>
 __device__ __forceinline__ void pow2_butterflies(C2 (&v)[E], const RowCtx<C2>& c, const C2* __restrict__ twp,
                                                  int L) {
@@ -158,8 +193,10 @@ __device__ __forceinline__ void pow2_butterflies(C2 (&v)[E], const RowCtx<C2>& c
   for (int q = 0; q < E / R; ++q) {
     if (L > 1) {
       const int k = (c.tr + q * c.TR) & (L - 1);
+      C2 w[R];
+      pass_twiddles<C2, R>(w, twp, L, k);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], conj_if<C2, INV>(twp[L - 1 + (r - 1) * L + k]));
+      for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], conj_if<C2, INV>(w[r]));
     }
     if (R == 8) dft8<C2, INV>(&v[q * R]);
     else if (R == 4) dft4<C2, INV>(&v[q * R]);
@@ -204,7 +241,7 @@ __device__ __forceinline__ void pow2_pass(C2 (&v)[E], const RowCtx<C2>& c, const
 // One CTA of 256 threads transforms 256 E / N rows (N <= 2048: E = 8; N = 4096, 8192: one
 // row with E = 16, 32).
 template <typename R, bool INV, int E>
-__global__ void __launch_bounds__(kFftThreads, E == 8 ? 4 : (E == 16 ? 2 : 1)) k_fft_pow2(const typename Vec2<R>::T* __restrict__ in,
+__global__ void __launch_bounds__(kFftThreads, fft_min_ctas<R>(E)) k_fft_pow2(const typename Vec2<R>::T* __restrict__ in,
                                                           typename Vec2<R>::T* __restrict__ out,
                                                           const typename Vec2<R>::T* __restrict__ twp,
                                                           RowCombine rc, int N, int lgN, int rows,
@@ -304,7 +341,7 @@ __device__ __forceinline__ void blue_store_global(C2 (&v)[E], const RowCtx<C2>& 
 }
 
 template <typename R, bool OUTER_INV, int E>
-__global__ void __launch_bounds__(kFftThreads, E == 8 ? 4 : (E == 16 ? 2 : 1)) k_fft_blue(
+__global__ void __launch_bounds__(kFftThreads, fft_min_ctas<R>(E)) k_fft_blue(
     const typename Vec2<R>::T* __restrict__ in, typename Vec2<R>::T* __restrict__ out,
     const typename Vec2<R>::T* __restrict__ twm, const typename Vec2<R>::T* __restrict__ chirp,
     const typename Vec2<R>::T* __restrict__ spec, RowCombine rc, int N, int M, int lgM, int rows, int rows_per_comp) {
@@ -398,55 +435,133 @@ __global__ void __launch_bounds__(kFftThreads, E == 8 ? 4 : (E == 16 ? 2 : 1)) k
 }
 
 // ---- any 7-smooth length ----
-// Stockham passes of the plan's radices (4, 2, 3, 5, 7 in the plan's order) between two
-// shared row buffers, one row per CTA; each thread takes butterflies t, t + 256, ... of a
-// pass, holds a butterfly's R values in registers, applies the pass's twiddles from the
-// per-pass table (entry L-1 + (r-1) L + k = w_{LR}^{rk}, read coalesced) and the R-point DFT
-// with the roots of unity w_R^m computed once per pass.
-__device__ __forceinline__ void sincospi_r(float x, float* s, float* c) { sincospif(x, s, c); }
-__device__ __forceinline__ void sincospi_r(double x, double* s, double* c) { sincospi(x, s, c); }
-
-template <typename C2, int R> __device__ __forceinline__ void dft_small(C2 (&v)[R], const C2 (&root)[R]) {
-  C2 y[R];
-#pragma unroll
-  for (int s2 = 0; s2 < R; ++s2) {
-    C2 acc = v[0];
-#pragma unroll
-    for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(v[r], root[(r * s2) % R]));
-    y[s2] = acc;
-  }
-#pragma unroll
-  for (int s2 = 0; s2 < R; ++s2) v[s2] = y[s2];
+// Stockham passes of the plan's radices (8, 4, 2, 3, 5, 7 in the plan's order), one row per
+// CTA; each thread takes butterflies t, t + 256, ... of a pass and holds a butterfly's R
+// values in registers.  The first pass reads the combined row straight from global memory
+// and the last pass writes the row there (L = N / R, so its butterflies store in natural
+// order); the passes between exchange values through two shared row buffers.  Twiddles as
+// in the power-of-two rows (pass_twiddles); the R-point DFTs of odd R use the symmetric
+// form y_m, y_{R-m} = v_0 + sum_s (v_s + v_{R-s}) cos(2 pi s m / R)
+// -+ i sum_s (v_s - v_{R-s}) sin(2 pi s m / R) (s = 1 .. (R-1)/2), with the cosines and
+// sines of the R-th roots of unity as constants.
+// cos(2 pi j / R) and sin(2 pi j / R), 0 <= j <= (R - 1) / 2, R = 3, 5, 7.
+__host__ __device__ constexpr double root_cos(int R, int j) {
+  return j == 0 ? 1.0
+       : R == 3 ? -0.5
+       : R == 5 ? (j == 1 ? 0.3090169943749474241023 : -0.8090169943749474241023)
+       : (j == 1 ? 0.6234898018587335305250 : j == 2 ? -0.2225209339563144042889 : -0.9009688679024191262361);
+}
+__host__ __device__ constexpr double root_sin(int R, int j) {
+  return j == 0 ? 0.0
+       : R == 3 ? 0.8660254037844386467637
+       : R == 5 ? (j == 1 ? 0.9510565162951535721164 : 0.5877852522924731291687)
+       : (j == 1 ? 0.7818314824680298087084 : j == 2 ? 0.9749279121818236070181 : 0.4338837391175581204758);
 }
 
-template <typename C2, bool INV, int R>
-__device__ __forceinline__ void mixed_pass(const C2* __restrict__ src, C2* __restrict__ dst,
-                                           const C2* __restrict__ twp, int N, int L) {
-  using Re = decltype(src[0].x);
-  C2 root[R];
+// y_m = sum_r v_r w_R^{rm}, w_R = exp(-+ 2 pi i / R), R odd.
+template <typename C2, bool INV, int R> __device__ __forceinline__ void dft_odd(C2* v) {
+  using Re = decltype(v[0].x);
+  constexpr int H = (R - 1) / 2;
+  C2 sp[H + 1], sm[H + 1];
 #pragma unroll
-  for (int m = 0; m < R; ++m) {   // w_R^m = exp(-+ 2 pi i m / R)
-    Re sn, cs;
-    sincospi_r((Re)(2 * m) / (Re)R, &sn, &cs);
-    root[m].x = cs;
-    root[m].y = INV ? sn : -sn;
+  for (int q = 1; q <= H; ++q) {
+    sp[q] = cadd(v[q], v[R - q]);
+    sm[q] = csub(v[q], v[R - q]);
   }
+  C2 y0 = v[0];
+#pragma unroll
+  for (int q = 1; q <= H; ++q) y0 = cadd(y0, sp[q]);
+#pragma unroll
+  for (int m = 1; m <= H; ++m) {
+    C2 a = v[0], bsum;
+    bsum.x = (Re)0; bsum.y = (Re)0;
+#pragma unroll
+    for (int q = 1; q <= H; ++q) {
+      const int j = (q * m) % R;                       // cos, sin of 2 pi j / R
+      const int jj = j <= H ? j : R - j;
+      const Re cs = (Re)root_cos(R, jj);
+      const Re sn = j <= H ? (Re)root_sin(R, jj) : -(Re)root_sin(R, jj);
+      a.x += cs * sp[q].x; a.y += cs * sp[q].y;
+      bsum.x += sn * sm[q].x; bsum.y += sn * sm[q].y;
+    }
+    // forward: y_m = a - i bsum, y_{R-m} = a + i bsum; inverse: the other way round
+    C2 lo, hi;
+    lo.x = a.x + bsum.y; lo.y = a.y - bsum.x;   // a - i bsum
+    hi.x = a.x - bsum.y; hi.y = a.y + bsum.x;   // a + i bsum
+    v[m] = INV ? hi : lo;
+    v[R - m] = INV ? lo : hi;
+  }
+  v[0] = y0;
+}
+
+// Sources and destinations of a pass: the shared buffers, or (first pass) the combined
+// input row / (last pass) the output row scaled for the inverse transform.
+template <typename C2> struct MixedIO {
+  const C2* a;
+  const C2* b;     // second source row of the combination or null
+  C2 ca, cb;
+  C2* o;
+  decltype(C2{}.x) scale;
+};
+
+template <typename C2, bool INV, int R, bool FIRST, bool LAST>
+__device__ __forceinline__ void mixed_pass(const C2* __restrict__ src, C2* __restrict__ dst,
+                                           const C2* __restrict__ twp, const MixedIO<C2>& io, int N, int L) {
   const int NR = N / R;
+  const float invL = 1.0f / (float)L;
   for (int t = threadIdx.x; t < NR; t += blockDim.x) {
-    const int j = t / L, k = t - j * L;
+    // j = t / L, k = t mod L (t, L < 2^13: the float quotient is off by at most one)
+    int j = (int)((float)t * invL);
+    int k = t - j * L;
+    if (k >= L) { ++j; k -= L; }
+    if (k < 0) { --j; k += L; }
     C2 v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[t + r * NR];
-    if (L > 1) {
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], conj_if<C2, INV>(twp[L - 1 + (r - 1) * L + k]));
+    for (int r = 0; r < R; ++r) {
+      const int i = t + r * NR;
+      if (FIRST) {
+        C2 x = cmul(io.ca, io.a[i]);
+        if (io.b) x = cadd(x, cmul(io.cb, io.b[i]));
+        v[r] = x;
+      } else {
+        v[r] = src[i];
+      }
     }
-    if (R == 2) dft2<C2, INV>(v);
-    else if (R == 4) dft4<C2, INV>(v);
-    else dft_small<C2, R>(v, root);
+    if (!FIRST) {   // L = 1 in the first pass: no twiddles
+      C2 w[R];
+      pass_twiddles<C2, R>(w, twp, L, k);
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], conj_if<C2, INV>(w[r]));
+    }
+    if constexpr (R == 2) dft2<C2, INV>(v);
+    else if constexpr (R == 4) dft4<C2, INV>(v);
+    else if constexpr (R == 8) dft8<C2, INV>(v);
+    else dft_odd<C2, INV, R>(v);
     const int base = j * L * R + k;
 #pragma unroll
-    for (int s2 = 0; s2 < R; ++s2) dst[base + s2 * L] = v[s2];
+    for (int s2 = 0; s2 < R; ++s2) {
+      if (LAST) {
+        C2 y = v[s2];
+        y.x *= io.scale;
+        y.y *= io.scale;
+        io.o[base + s2 * L] = y;
+      } else {
+        dst[base + s2 * L] = v[s2];
+      }
+    }
+  }
+}
+
+template <typename C2, bool INV, bool FIRST, bool LAST>
+__device__ __forceinline__ void mixed_pass_r(int Rdx, const C2* src, C2* dst, const C2* __restrict__ twp,
+                                             const MixedIO<C2>& io, int N, int L) {
+  switch (Rdx) {
+    case 2: mixed_pass<C2, INV, 2, FIRST, LAST>(src, dst, twp, io, N, L); break;
+    case 3: mixed_pass<C2, INV, 3, FIRST, LAST>(src, dst, twp, io, N, L); break;
+    case 4: mixed_pass<C2, INV, 4, FIRST, LAST>(src, dst, twp, io, N, L); break;
+    case 5: mixed_pass<C2, INV, 5, FIRST, LAST>(src, dst, twp, io, N, L); break;
+    case 7: mixed_pass<C2, INV, 7, FIRST, LAST>(src, dst, twp, io, N, L); break;
+    default: mixed_pass<C2, INV, 8, FIRST, LAST>(src, dst, twp, io, N, L); break;
   }
 }
 
@@ -463,42 +578,37 @@ __global__ void __launch_bounds__(256) k_fft_rows(const typename Vec2<R>::T* __r
   const int row = blockIdx.x;
   const int comp = row / rows_per_comp;
   const int rr = row % rows_per_comp;
-  const C2* a = in + ((size_t)rc.srcA[comp] * rows_per_comp + rr) * N;
+  MixedIO<C2> io;
+  io.a = in + ((size_t)rc.srcA[comp] * rows_per_comp + rr) * N;
   const int sb = rc.srcB[comp];
-  const C2* b = sb >= 0 ? in + ((size_t)sb * rows_per_comp + rr) * N : nullptr;
-  C2 ca, cb;
-  ca.x = (R)rc.caRe[comp]; ca.y = (R)rc.caIm[comp];
-  cb.x = (R)rc.cbRe[comp]; cb.y = (R)rc.cbIm[comp];
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    C2 v = cmul(ca, a[i]);
-    if (b) v = cadd(v, cmul(cb, b[i]));
-    buf0[i] = v;
+  io.b = sb >= 0 ? in + ((size_t)sb * rows_per_comp + rr) * N : nullptr;
+  io.ca.x = (R)rc.caRe[comp]; io.ca.y = (R)rc.caIm[comp];
+  io.cb.x = (R)rc.cbRe[comp]; io.cb.y = (R)rc.cbIm[comp];
+  io.o = out + (size_t)row * N;
+  io.scale = INV ? (R)1 / (R)N : (R)1;
+  // radices packed 4 bits each (a parameter array indexed at run time would be copied to
+  // the stack)
+  unsigned long long radix = 0;
+#pragma unroll
+  for (int p = 0; p < kMaxRadixPasses; ++p) radix |= (unsigned long long)plan.radix[p] << (4 * p);
+  const int np = plan.n_pass;
+  if (np == 1) {
+    mixed_pass_r<C2, INV, true, true>((int)(radix & 15), buf0, buf1, twp, io, N, 1);
+    return;
   }
+  mixed_pass_r<C2, INV, true, false>((int)(radix & 15), buf0, buf0, twp, io, N, 1);
   __syncthreads();
   C2* src = buf0;
   C2* dst = buf1;
-  int L = 1;
-  for (int p = 0; p < plan.n_pass; ++p) {
-    const int Rdx = plan.radix[p];
-    switch (Rdx) {
-      case 2: mixed_pass<C2, INV, 2>(src, dst, twp, N, L); break;
-      case 3: mixed_pass<C2, INV, 3>(src, dst, twp, N, L); break;
-      case 4: mixed_pass<C2, INV, 4>(src, dst, twp, N, L); break;
-      case 5: mixed_pass<C2, INV, 5>(src, dst, twp, N, L); break;
-      default: mixed_pass<C2, INV, 7>(src, dst, twp, N, L); break;
-    }
+  int L = (int)(radix & 15);
+  for (int p = 1; p < np - 1; ++p) {
+    const int Rp = (int)((radix >> (4 * p)) & 15);
+    mixed_pass_r<C2, INV, false, false>(Rp, src, dst, twp, io, N, L);
     __syncthreads();
     C2* t2 = src; src = dst; dst = t2;
-    L *= Rdx;
+    L *= Rp;
   }
-  C2* o = out + (size_t)row * N;
-  const R scale = INV ? (R)1 / (R)N : (R)1;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    C2 v = src[i];
-    v.x *= scale;
-    v.y *= scale;
-    o[i] = v;
-  }
+  mixed_pass_r<C2, INV, false, true>((int)((radix >> (4 * (np - 1))) & 15), src, dst, twp, io, N, L);
 }
 
 // ---- any other length: Bluestein's chirp-z algorithm ----
@@ -522,10 +632,10 @@ int bluestein_length(int Nz, int precision) {
   return M <= (precision == PIC_FP64 ? 4096 : 8192) ? M : 0;
 }
 
-// Factor Nz into passes of radix 4, 2, 3, 5, 7 (the Stockham order is free).
+// Factor Nz into passes of radix 8, 4, 2, 3, 5, 7 (the Stockham order is free).
 bool plan_radix(int N, int32_t* radix, int32_t* n_pass) {
   int n = N, k = 0;
-  const int order[5] = {4, 2, 3, 5, 7};
+  const int order[6] = {8, 4, 2, 3, 5, 7};
   for (int f : order) {
     while (n % f == 0) {
       if (k >= kMaxRadixPasses) return false;

@@ -39,7 +39,7 @@ def crand(rng, shape, scale=1.0):
 
 
 SHAPES = [(16, 8, 2), (60, 33, 3), (256, 64, 2), (2048, 256, 2), (32, 4, 1), (128, 8, 1), (1024, 8, 1),
-          (4096, 8, 1), (8192, 8, 2)]
+          (4096, 8, 1), (8192, 8, 2), (24, 4, 2), (343, 4, 1), (1000, 8, 2), (3456, 4, 3)]
 
 
 @pytest.mark.parametrize("Nz,Nr,Nm", SHAPES)

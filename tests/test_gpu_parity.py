@@ -42,8 +42,11 @@ def crand(rng, shape, scale=1.0):
 
 SHAPES = [(8, 4, 1), (16, 8, 2), (60, 33, 3), (256, 64, 2), (525, 48, 2), (2048, 256, 2)]
 # every power-of-two pass structure of the radix-8 row transform (last pass radix 2, 4 or
-# 8; 8, 16 values per thread) plus the mixed-radix rows of other 7-smooth lengths
-FFT_SHAPES = SHAPES + [(32, 4, 1), (128, 8, 2), (512, 4, 1), (1024, 8, 1), (4096, 8, 2), (8192, 8, 2)]
+# 8; 8, 16 values per thread) plus the mixed-radix rows of other 7-smooth lengths: two
+# passes (24 = 8 x 3: the first from and the last to global memory only), radix 8 before
+# odd radices (72, 1000, 3456), odd radices only (343, 2835)
+FFT_SHAPES = SHAPES + [(32, 4, 1), (128, 8, 2), (512, 4, 1), (1024, 8, 1), (4096, 8, 2), (8192, 8, 2),
+                       (24, 4, 2), (72, 4, 1), (343, 4, 1), (1000, 8, 2), (2835, 4, 1), (3456, 4, 3)]
 
 
 # ---------------------------------------------------------------------------- setup (a0)
