@@ -2,9 +2,10 @@
 // quasi-cylindrical scheme (section "Finite order pseudo-spectral solvers").
 //   forward: Fhat(k) = sum_i F(z_i) e^{-2 pi i k i / Nz}
 //   inverse: F(z_i) = (1/Nz) sum_k Fhat(k) e^{+2 pi i k i / Nz}
-// Power-of-two lengths use radix-8 passes with the values in registers (k_fft_pow2); other
-// 7-smooth lengths a mixed-radix (2, 3, 4, 5, 7) self-sorting Stockham sequence of passes
-// between two shared row buffers (k_fft_rows).  Both read per-pass twiddle tables.  Any
+// Power-of-two lengths use radix-8 passes with the values in registers (k_fft_pow2 for
+// double rows; k_fft_pow2_tma for float rows, persistent and fed by bulk copies); other
+// 7-smooth lengths a mixed-radix (8, 4, 2, 3, 5, 7) self-sorting Stockham sequence of passes
+// between two shared row buffers (k_fft_rows).  All read per-pass twiddle tables.  Any
 // other length goes through Bluestein's chirp-z algorithm on power-of-two rows (below).
 // The component combination of the quasi-cylindrical scheme is fused into the row load:
 // out = ca * inA + cb * inB, which forms J_+- = (J_r -+ i J_theta)/2 before the forward
@@ -12,6 +13,7 @@
 #include <mutex>
 
 #include "pic_internal.cuh"
+#include "tc_common.cuh"
 
 namespace pic {
 namespace {
@@ -54,10 +56,10 @@ struct FftPlan {
 // tables of all passes tile entries 0..N-2), so a warp reads consecutive entries.
 constexpr int kFftThreads = 256;
 
-// Resident CTAs per SM asked of the register allocator for E values per thread.  Float rows
-// of 4096 and 8192 points (E = 16, 32) trade a few spilled bytes for 3 and 2 CTAs per SM:
-// with one CTA per SM a row's loads, passes and stores ran one after another on the SM
-// (8192-point rows of 3 x 1024 x 8192 fields: 1.89 -> 1.14 ms per forward transform).
+// Resident CTAs per SM asked of the register allocator for E values per thread (double rows
+// and the Bluestein rows).  Float rows of 4096 and 8192 points (E = 16, 32) trade a few
+// spilled bytes for 3 and 2 CTAs per SM: with one CTA per SM a row's loads, passes and
+// stores ran one after another on the SM.
 template <typename R> constexpr int fft_min_ctas(int E) {
   return E == 8 ? 4 : (E == 16 ? (sizeof(R) == 4 ? 3 : 2) : (sizeof(R) == 4 ? 2 : 1));
 }
@@ -238,8 +240,8 @@ __device__ __forceinline__ void pow2_pass(C2 (&v)[E], const RowCtx<C2>& c, const
   pow2_store<C2, INV, E, R, PS>(v, c, L, lgL, last);
 }
 
-// One CTA of 256 threads transforms 256 E / N rows (N <= 2048: E = 8; N = 4096, 8192: one
-// row with E = 16, 32).
+// Double rows: one CTA of 256 threads transforms 256 E / N rows (N <= 2048: E = 8; N = 4096,
+// 8192: one row with E = 16, 32).  Float rows take k_fft_pow2_tma below.
 template <typename R, bool INV, int E>
 __global__ void __launch_bounds__(kFftThreads, fft_min_ctas<R>(E)) k_fft_pow2(const typename Vec2<R>::T* __restrict__ in,
                                                           typename Vec2<R>::T* __restrict__ out,
@@ -284,6 +286,109 @@ __global__ void __launch_bounds__(kFftThreads, fft_min_ctas<R>(E)) k_fft_pow2(co
   }
   if (rem == 2) pow2_pass<C2, INV, E, 4, PS>(v, c, twp, L, lgL, true);
   else pow2_pass<C2, INV, E, 2, PS>(v, c, twp, L, lgL, true);
+}
+
+// ---- power-of-two float rows: persistent CTAs fed by bulk copies ----
+// (3 x 1024 x 8192 rows, forward: 1.14 ms with k_fft_pow2 at 2 CTAs per SM, 1.89 ms at
+// one, 0.66 ms here.)
+// One CTA of 512 threads per SM (two for E = 8) walks groups of G = 512 E / N rows of one
+// component (groups do not cross components, so each source is one contiguous run of G
+// rows).  A group's source rows arrive in a shared staging area by one bulk copy per source
+// (cp.async.bulk, completion counted on an mbarrier); as soon as every thread holds its
+// first-pass inputs in registers, thread 0 starts the copy of the CTA's next group, which
+// then runs under the passes and stores of this one.  The passes are those of k_fft_pow2
+// (the first reads the combination from the staging area, the last writes the row to
+// global memory).  The float rows are bound by memory latency otherwise: a CTA that loads
+// its row itself waits for it before every row.
+constexpr int kFftTmaThreads = 512;
+
+template <int E> constexpr int fft_tma_ctas() { return E == 8 ? 2 : 1; }
+
+// Float rows: E = 16 values per thread for N >= 4096, else 8; G = 512 E / N rows per group.
+inline int fft_tma_e(int N) { return N >= 4096 ? 16 : 8; }
+inline size_t fft_tma_smem(int N) {
+  const int G = kFftTmaThreads * fft_tma_e(N) / N;
+  return ((size_t)2 * G * N + (size_t)G * (N + (N >> 4))) * sizeof(float2) + 16;
+}
+
+template <bool INV, int E>
+__global__ void __launch_bounds__(kFftTmaThreads, fft_tma_ctas<E>())
+    k_fft_pow2_tma(const float2* __restrict__ in, float2* __restrict__ out, const float2* __restrict__ twp,
+                   RowCombine rc, int N, int lgN, int rows_per_comp, int n_comp, int G, int32_t* err) {
+  using C2 = float2;
+  constexpr int PS = 4;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int padN = N + (N >> PS);
+  C2* stage_a = reinterpret_cast<C2*>(smem_raw);
+  C2* stage_b = stage_a + (size_t)G * N;
+  C2* cbuf = stage_b + (size_t)G * N;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(cbuf + (size_t)G * padN);
+  const int gpc = (rows_per_comp + G - 1) / G;   // groups per component
+  const int n_groups = gpc * n_comp;
+  RowCtx<C2> c;
+  c.N = N;
+  c.TR = N / E;
+  const int lr = threadIdx.x / c.TR;              // row of the group
+  c.tr = threadIdx.x - lr * c.TR;
+  c.buf = cbuf + (size_t)lr * padN;
+  const int n8 = lgN / 3, rem = lgN - 3 * n8;
+
+  auto issue = [&](int g) {                      // thread 0: the copies of group g
+    const int comp = g / gpc, r0 = (g - comp * gpc) * G;
+    const uint32_t bytes = (uint32_t)(min(G, rows_per_comp - r0) * N * (int)sizeof(C2));
+    const int sb = rc.srcB[comp];
+    mbar_arrive_expect_tx(bar, sb >= 0 ? 2 * bytes : bytes);
+    bulk_g2s(stage_a, in + ((size_t)rc.srcA[comp] * rows_per_comp + r0) * N, bytes, bar);
+    if (sb >= 0) bulk_g2s(stage_b, in + ((size_t)sb * rows_per_comp + r0) * N, bytes, bar);
+  };
+
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && (int)blockIdx.x < n_groups) issue(blockIdx.x);
+  uint32_t parity = 0;
+  for (int g = blockIdx.x; g < n_groups; g += gridDim.x, parity ^= 1u) {
+    const int comp = g / gpc, r0 = (g - comp * gpc) * G;
+    const int rr = r0 + lr;
+    c.active = rr < rows_per_comp;
+    c.a = stage_a + (size_t)lr * N;
+    c.b = rc.srcB[comp] >= 0 ? stage_b + (size_t)lr * N : nullptr;
+    c.ca.x = (float)rc.caRe[comp]; c.ca.y = (float)rc.caIm[comp];
+    c.cb.x = (float)rc.cbRe[comp]; c.cb.y = (float)rc.cbIm[comp];
+    c.o = out + ((size_t)comp * rows_per_comp + (c.active ? rr : 0)) * N;
+    const bool ok = mbar_wait(bar, parity);
+    if (__syncthreads_or(!ok)) {                 // the copy did not complete: give up
+      if (threadIdx.x == 0) {
+        atomicOr(err, kErrTimeout);
+        mbar_wait(bar, parity);                  // bounded: let a late copy land first
+      }
+      return;
+    }
+    C2 v[E];
+    pow2_load_global<C2, E>(v, c);
+    __syncthreads();                             // staging read in full
+    if (threadIdx.x == 0 && g + (int)gridDim.x < n_groups) issue(g + gridDim.x);
+    int L = 1, lgL = 0;
+    bool done = false;
+    for (int p = 0; p < n8; ++p) {
+      const bool last = p == n8 - 1 && rem == 0;
+      pow2_pass<C2, INV, E, 8, PS>(v, c, twp, L, lgL, last);
+      if (last) { done = true; break; }
+      L <<= 3;
+      lgL += 3;
+      __syncthreads();   // the pass's outputs are in the buffer
+      if (p + 1 < n8) pow2_load_shared<C2, E, 8, PS>(v, c);
+      else if (rem == 2) pow2_load_shared<C2, E, 4, PS>(v, c);
+      else pow2_load_shared<C2, E, 2, PS>(v, c);
+      __syncthreads();   // the buffer is read in full before it is rewritten
+    }
+    if (!done) {
+      if (rem == 2) pow2_pass<C2, INV, E, 4, PS>(v, c, twp, L, lgL, true);
+      else pow2_pass<C2, INV, E, 2, PS>(v, c, twp, L, lgL, true);
+    }
+  }
 }
 
 // ---- Bluestein rows in one kernel (see the chirp-z section below for the algorithm) ----
@@ -664,9 +769,11 @@ pic_status fft_configure_device() {
   PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_rows<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFftSmemMax));
-  // power-of-two rows: one padded row buffer
-  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<float, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
-  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<float, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
+  // power-of-two rows: one padded row buffer (float: staging areas as well)
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2_tma<false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_tma_smem(8192)));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2_tma<true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_tma_smem(8192)));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2_tma<false, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_tma_smem(1024)));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2_tma<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_tma_smem(1024)));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
   // float64 rows of 8192 (one row per CTA, 32 values per thread): 8192 + 1024 padded doubles
@@ -695,6 +802,26 @@ void launch_pow2(Sim* s, int N, const void* in, void* out, const void* twp, cons
   const int grid = (rows + rpc - 1) / rpc;
   k_fft_pow2<R, INV, E><<<grid, kFftThreads, smem, s->stream>>>((const C2*)in, (C2*)out, (const C2*)twp, rc, N,
                                                                 lgN, rows, rows_per_comp);
+}
+
+template <bool INV, int E>
+void launch_pow2_tma_e(Sim* s, int N, const void* in, void* out, const void* twp, const RowCombine& rc,
+                       int rows_per_comp) {
+  int lgN = 0;
+  while ((1 << lgN) < N) ++lgN;
+  const int G = kFftTmaThreads * E / N;
+  const int n_groups = (rows_per_comp + G - 1) / G * rc.n_out;
+  const int grid = std::min(n_groups, dht_tc_sm_count() * fft_tma_ctas<E>());
+  k_fft_pow2_tma<INV, E><<<grid, kFftTmaThreads, fft_tma_smem(N), s->stream>>>(
+      (const float2*)in, (float2*)out, (const float2*)twp, rc, N, lgN, rows_per_comp, rc.n_out, G,
+      s->at<int32_t>(s->lay.err));
+}
+
+template <bool INV>
+void launch_pow2_tma(Sim* s, int N, const void* in, void* out, const void* twp, const RowCombine& rc,
+                     int rows_per_comp) {
+  if (fft_tma_e(N) == 16) launch_pow2_tma_e<INV, 16>(s, N, in, out, twp, rc, rows_per_comp);
+  else launch_pow2_tma_e<INV, 8>(s, N, in, out, twp, rc, rows_per_comp);
 }
 
 template <typename R, bool INV>
@@ -755,8 +882,8 @@ pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& 
       else launch_pow2_e<double, false>(s, c.Nz, in, out, twp, rc, rows, rows_per_comp);
     } else {
       const void* twp = s->at<float2>(s->lay.twp_f);
-      if (inverse) launch_pow2_e<float, true>(s, c.Nz, in, out, twp, rc, rows, rows_per_comp);
-      else launch_pow2_e<float, false>(s, c.Nz, in, out, twp, rc, rows, rows_per_comp);
+      if (inverse) launch_pow2_tma<true>(s, c.Nz, in, out, twp, rc, rows_per_comp);
+      else launch_pow2_tma<false>(s, c.Nz, in, out, twp, rc, rows_per_comp);
     }
     PIC_LAUNCHED(s);
     return PIC_OK;
