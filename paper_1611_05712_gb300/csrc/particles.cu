@@ -70,10 +70,13 @@ __device__ __forceinline__ Stencil stencil(const GridGeom& g, double z, double r
   double u = z / g.dz;
   double fi = floor(u);
   double sz = u - fi;
-  long long i0 = (long long)fi % g.Nz;
-  if (i0 < 0) i0 += g.Nz;
+  long long i0 = (long long)fi;
+  if (i0 < 0 || i0 >= g.Nz) {   // z outside [0, L): wrap (the push keeps z inside)
+    i0 %= g.Nz;
+    if (i0 < 0) i0 += g.Nz;
+  }
   st.i0 = (int)i0;
-  st.i1 = (int)((i0 + 1) % g.Nz);
+  st.i1 = st.i0 + 1 == g.Nz ? 0 : st.i0 + 1;
   st.wz0 = 1.0 - sz;
   st.wz1 = sz;
   // z / dz stays a correctly rounded division (one ulp of it is ~Nz ulps of a weight);
@@ -88,32 +91,28 @@ __device__ __forceinline__ Stencil stencil(const GridGeom& g, double z, double r
   return st;
 }
 
-// Atomically add val * weight at node (j, i) of a complex grid [Nr][Nz] with the fold.
-__device__ __forceinline__ void dep_node(double2* grid, const GridGeom& g, int j, int i, double wgt,
-                                         double fold, double vre, double vim, const double* invV) {
-  if (j < 0) { j = -1 - j; wgt *= fold; }
-  if (j >= g.Nr) return;
-  const double f = wgt * invV[j];
-  double* p = reinterpret_cast<double*>(grid + (size_t)j * g.Nz + i);
-  atomicAdd(p, vre * f);
-  atomicAdd(p + 1, vim * f);
-}
+// Gather weights of a particle's 4 nodes n = 2 dz + dj (rows i0, i1; radial nodes j0, j0 + 1):
+// w_z w_r, 0 for a dropped node (j >= Nr, read at a valid address); the ghost node r = -dr/2
+// of the axis cell (j0 = -1) is read at node 0 and takes its field's fold sign.
+struct GatherNodes {
+  double w[4];
+  size_t off[4];   // j Nz + i
+  bool ghost;
+};
 
-__device__ __forceinline__ double2 interp(const double2* grid, const GridGeom& g, const Stencil& st,
-                                          double fold) {
-  double re = 0.0, im = 0.0;
+__device__ __forceinline__ GatherNodes gather_nodes(const GridGeom& g, const Stencil& st) {
+  GatherNodes gn;
 #pragma unroll
-  for (int dj = 0; dj < 2; ++dj) {
-    int j = st.j0 + dj;
-    double wr = dj ? st.wr1 : st.wr0;
-    if (j < 0) { j = -1 - j; wr *= fold; }
-    if (j >= g.Nr) continue;
-    double2 a = grid[(size_t)j * g.Nz + st.i0];
-    double2 b = grid[(size_t)j * g.Nz + st.i1];
-    re += wr * (st.wz0 * a.x + st.wz1 * b.x);
-    im += wr * (st.wz0 * a.y + st.wz1 * b.y);
+  for (int n = 0; n < 4; ++n) {
+    const int dz = n >> 1, dj = n & 1;
+    const int j = st.j0 + dj;
+    const bool keep = j < g.Nr;
+    const int jj = (j < 0 || !keep) ? 0 : j;
+    gn.w[n] = keep ? (dz ? st.wz1 : st.wz0) * (dj ? st.wr1 : st.wr0) : 0.0;
+    gn.off[n] = (size_t)jj * g.Nz + (dz ? st.i1 : st.i0);
   }
-  return make_double2(re, im);
+  gn.ghost = st.j0 < 0;
+  return gn;
 }
 
 // ------------------------------------------------------------------ a1: keys and sort
@@ -340,33 +339,67 @@ struct DepArgs {
   int32_t id_lo, id_hi;
 };
 
+// x with its sign flipped when neg (integer operations: the float64 unit bounds these kernels).
+__device__ __forceinline__ double flip_sign(double x, bool neg) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
+}
+
+__device__ __forceinline__ void dep2(double2* p, double re, double im) {
+  double* d = reinterpret_cast<double*>(p);
+  atomicAdd(d, re);
+  atomicAdd(d + 1, im);
+}
+
+// Deposit of one particle: rho (do_rho) and/or J (do_J) with weight e^{+i m theta} per mode,
+// linear weights; the ghost node r = -dr/2 of the axis cell is node 0 seen across the axis
+// (fold sign (-1)^m for rho and J_z, (-1)^{m+1} for J_r and J_theta) and node Nr is dropped.
+// Each node's weight / V_j and address are formed once; lanes visit the 4 nodes in an
+// order rotated by the lane index, so that lanes of one cell (same nodes) add to different
+// nodes in one instruction.
 __device__ void deposit_one(const GridGeom& g, const DepArgs& a, const double* invV, double x,
                             double y, double z, double w, double vx, double vy, double vz,
                             bool do_rho, bool do_J) {
   double r, c, s;
   polar(x, y, r, c, s);
   const Stencil st = stencil(g, z, r);
-  const double vr = c * vx + s * vy, vt = c * vy - s * vx;
-  double phr = 1.0, phi = 0.0;   // e^{+i m theta}
-  // the 4 nodes in an order rotated by the lane index: lanes of one cell (same nodes) then
-  // hit different addresses in one instruction
+  const size_t RZ = (size_t)g.Nr * g.Nz;
   const int rot = threadIdx.x & 3;
+  const bool ghost = st.j0 < 0;
+  double fq[4];
+  size_t oq[4];
+  bool inner[4];   // node of the lower radial pair (the ghost node when ghost)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int node = (q + rot) & 3, dz = node >> 1, dj = node & 1;
+    const int j = st.j0 + dj;
+    const bool keep = j < g.Nr;
+    const int jj = (j < 0 || !keep) ? 0 : j;
+    fq[q] = keep ? (dz ? st.wz1 : st.wz0) * (dj ? st.wr1 : st.wr0) * invV[jj] : 0.0;
+    oq[q] = (size_t)jj * g.Nz + (dz ? st.i1 : st.i0);
+    inner[q] = dj == 0;
+  }
+  const double vr = c * vx + s * vy, vt = c * vy - s * vx;
+  const double qw = a.q * w;
+  double phr = 1.0, phi = 0.0;   // e^{+i m theta}
   for (int m = 0; m < g.Nm; ++m) {
-    const double qre = a.q * w * phr, qim = a.q * w * phi;
-    const double fs = (m & 1) ? -1.0 : 1.0;   // scalar / z fold (-1)^m
-    const double fv = -fs;                     // r / theta fold (-1)^{m+1}
+    const double qre = qw * phr, qim = qw * phi;
+    const bool negS = ghost && (m & 1), negV = ghost && !(m & 1);
+    double Ar = 0.0, Br = 0.0, At = 0.0, Bt = 0.0, Az = 0.0, Bz = 0.0;
+    if (do_J) {
+      Ar = qre * vr; Br = qim * vr;
+      At = qre * vt; Bt = qim * vt;
+      Az = qre * vz; Bz = qim * vz;
+    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      const int node = (q + rot) & 3;
-      const int dz = node >> 1, dj = node & 1;
-      const int i = dz ? st.i1 : st.i0;
-      const int j = st.j0 + dj;
-      const double wgt = (dz ? st.wz1 : st.wz0) * (dj ? st.wr1 : st.wr0);
-      if (do_rho) dep_node(a.rho + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fs, qre, qim, invV);
+      if (fq[q] == 0.0) continue;
+      const double fS = flip_sign(fq[q], inner[q] && negS), fV = flip_sign(fq[q], inner[q] && negV);
+      const size_t o = (size_t)m * RZ + oq[q];
+      if (do_rho) dep2(a.rho + o, qre * fS, qim * fS);
       if (do_J) {
-        dep_node(a.J + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fv, qre * vr, qim * vr, invV);
-        dep_node(a.J + g.G + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fv, qre * vt, qim * vt, invV);
-        dep_node(a.J + 2 * g.G + (size_t)m * g.Nr * g.Nz, g, j, i, wgt, fs, qre * vz, qim * vz, invV);
+        dep2(a.J + o, Ar * fV, Br * fV);
+        dep2(a.J + g.G + o, At * fV, Bt * fV);
+        dep2(a.J + 2 * g.G + o, Az * fS, Bz * fS);
       }
     }
     const double nr = phr * c - phi * s, ni = phr * s + phi * c;
@@ -412,7 +445,7 @@ __device__ __forceinline__ void win_mark(const WinArgs& wa, int32_t id, int64_t 
 
 // WIN: moving window on (removal behind the back edge); the plain instance has none of it.
 template <bool WIN>
-__global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __restrict__ E,
+__global__ void __launch_bounds__(256, 2) k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __restrict__ E,
                               const double2* __restrict__ B, double k, double dt, DepArgs dep,
                               const double* invV, int fuse, int32_t* err, WinArgs wa) {
   const size_t RZ = (size_t)g.Nr * g.Nz;
@@ -427,16 +460,34 @@ __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __
     double r, c, s;
     polar(x, y, r, c, s);
     const Stencil st = stencil(g, z, r);
-    double F[6] = {0, 0, 0, 0, 0, 0};   // E_r, E_t, E_z, B_r, B_t, B_z
-    double phr = 1.0, phi = 0.0;        // e^{-i m theta}
-    for (int m = 0; m < g.Nm; ++m) {
-      const double fs = (m & 1) ? -1.0 : 1.0, fv = -fs;
-      const double mult = m == 0 ? 1.0 : 2.0;
+    // F = Re sum_m mult_m e^{-i m theta} sum_n w_n F_m(node n), mult_0 = 1, mult_m = 2; per
+    // mode the node weights are multiplied by mult e^{-i m theta} once for the 6 components,
+    // and the ghost nodes (n = 0, 2) are summed apart so that the fold is one sign flip.
+    const GatherNodes gn = gather_nodes(g, st);
+    double F[6];   // E_r, E_t, E_z, B_r, B_t, B_z
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {   // mode 0: real phase, fold +1 for E_z, B_z and -1 for r, theta
+      const double2* base = (k < 3 ? E : B) + (size_t)(k % 3) * g.G;
+      const double in = gn.w[0] * base[gn.off[0]].x + gn.w[2] * base[gn.off[2]].x;
+      const double out = gn.w[1] * base[gn.off[1]].x + gn.w[3] * base[gn.off[3]].x;
+      F[k] = out + flip_sign(in, gn.ghost && (k % 3) != 2);
+    }
+    double phr = c, phi = -s;   // e^{-i m theta}, m = 1
+    for (int m = 1; m < g.Nm; ++m) {
+      double a[4], b[4];
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        a[n] = 2.0 * gn.w[n] * phr;
+        b[n] = 2.0 * gn.w[n] * phi;
+      }
+      const bool negS = gn.ghost && (m & 1), negV = gn.ghost && !(m & 1);
 #pragma unroll
       for (int k = 0; k < 6; ++k) {
         const double2* base = (k < 3 ? E : B) + (size_t)(k % 3) * g.G + (size_t)m * RZ;
-        const double2 v = interp(base, g, st, (k % 3) == 2 ? fs : fv);
-        F[k] += mult * (v.x * phr - v.y * phi);
+        const double2 v0 = base[gn.off[0]], v1 = base[gn.off[1]], v2 = base[gn.off[2]], v3 = base[gn.off[3]];
+        const double in = a[0] * v0.x - b[0] * v0.y + a[2] * v2.x - b[2] * v2.y;
+        const double out = a[1] * v1.x - b[1] * v1.y + a[3] * v3.x - b[3] * v3.y;
+        F[k] += out + flip_sign(in, (k % 3) == 2 ? negS : negV);
       }
       const double nr = phr * c + phi * s, ni = phi * c - phr * s;   // times e^{-i theta}
       phr = nr; phi = ni;
@@ -481,6 +532,9 @@ __global__ void k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __
       x *= fr;
       y *= fr;
     }
+    // rho^{n+1} at x^{n+1} (without the moving window; with it the deposit stage runs after
+    // the injection)
+    if (!WIN && dep.rho) deposit_one(g, dep, invV, x, y, z, w, 0.0, 0.0, 0.0, true, false);
     if (WIN) {
       // window coordinate after the step: ((z^n - back) mod L) + 2 half moves - s dz
       double zo = z_old - wa.back_z;
@@ -2151,13 +2205,17 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, b
   } else {
     if (after_layout) PIC_CUDA(cudaEventRecord(after_layout, s->stream));   // no separate layout
     const double kq = c.q * c.dt / (2.0 * c.mass);
+    fuse_rho = fuse_rho && fuse_current && !wa.on;
     DepArgs a;
     a.q = c.q;
     a.id_lo = INT32_MIN;
     a.id_hi = INT32_MAX;
-    a.rho = nullptr;
+    a.rho = fuse_rho ? s->at<double2>(s->lay.dep) : nullptr;
     a.J = s->at<double2>(s->lay.dep) + G;
     if (fuse_current) PIC_CUDA(cudaMemsetAsync(a.J, 0, 3 * G * sizeof(double2), s->stream));
+    if (fuse_rho)   // rho^{n+1} starts from the immobile background
+      PIC_CUDA(cudaMemcpyAsync(a.rho, s->at<double2>(s->lay.rho_ion), G * sizeof(double2), cudaMemcpyDeviceToDevice,
+                               s->stream));
     if (s->np == 0) return PIC_OK;
     if (wa.on)
       k_gather_push<true><<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, geom_of(s),

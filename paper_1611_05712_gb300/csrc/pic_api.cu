@@ -359,9 +359,10 @@ pic_status step_once(Sim* s, Marks* mk) {
     wa.slot = reinterpret_cast<int32_t*>(s->win.ws + s->win.slot);
     wa.bcnt = reinterpret_cast<int32_t*>(s->win.ws + s->win.bcnt);
   }
-  // mixed forms: rho^{n+1} is deposited by the push itself (the sort that follows only
-  // reorders particles); particles the moving window injects deposit theirs as they are placed
-  const bool fuse_rho = s->cfg.precision != PIC_FP64;
+  // rho^{n+1} is deposited by the push itself (the sort that follows only reorders
+  // particles); with the moving window the mixed forms' injected particles deposit theirs as
+  // they are placed, and the FP64 form deposits rho in its own stage after the injection
+  const bool fuse_rho = s->cfg.precision != PIC_FP64 || !s->win.on;
   PIC_CUDA(m.mark(0));
   if ((st = launch_gather_push(s, 1, wa, fuse_rho, m.ev ? m.ev[1] : nullptr)) != PIC_OK) return st;
   if (wa.shift && (st = launch_window_inject(s, wa.back_col, fuse_rho)) != PIC_OK) return st;
