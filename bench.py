@@ -26,6 +26,25 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12   # 152 SMs x 2 DFMA/clk x 2070 MHz (nominal 1.25)
+
+
+def fp64_particle_flops(Nm):
+    """Algorithmic float64 operations of one particle's pass in the FP64 form (gather, push,
+    J at x^{n+1/2}, rho at x^{n+1}), each multiply, add, divide and square root counted once:
+      polar decomposition 7 (x^2, y^2, add, sqrt, 2 divides) and stencil 7 at each of the
+      three positions; 4 node weights (gather) and 8 node weights / V_j (each deposit);
+      phases e^{-+i m theta}: 6 per mode m >= 2 in the gather and each deposit;
+      interpolation + mode sum of 6 components: 8 (mode 0, real part) + 21 per mode m >= 1
+      (4 complex node terms 16, real part of the phase product 3, x 2 and accumulate 2);
+      (r, theta) -> (x, y) of E and B 12; Boris 58; 1/gamma and v 11; two half moves 12;
+      J: q w and its phases 1 + 2 (Nm - 1), q w e^{i m theta} v_k 3 (2 Nm - 1), node products
+      and adds 24 (2 Nm - 1); rho: 1 + 2 (Nm - 1) and 8 (2 Nm - 1)."""
+    ph = 6 * max(Nm - 2, 0)
+    gather = 7 + 7 + 4 + ph + 6 * (8 + 21 * (Nm - 1)) + 12
+    push = 58 + 11 + 12
+    dep_j = 7 + 7 + 8 + ph + 1 + 2 * (Nm - 1) + 3 * (2 * Nm - 1) + 24 * (2 * Nm - 1)
+    dep_rho = 7 + 7 + 8 + ph + 1 + 2 * (Nm - 1) + 8 * (2 * Nm - 1)
+    return gather + push + dep_j + dep_rho
 FP64_PROBE_TFLOPS = 1.1947                     # FMA-loop probe on this pool's GB300 at 1987 MHz
 # DRAM bytes per FP64 DHT launch (k_gemm<double>) on this workload, from one ncu capture of
 # the current kernel (forward 71.42 + 27.50 MB, inverse 106.87 + 60.50 MB, mean of the two)
@@ -326,6 +345,22 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe nominal "
                                    "1.25 TFLOP/s); FMA probe measured 1.195 TFLOP/s",
                     "share_of_step": share}
+    roofline_particles = None
+    if not mixed:
+        # the FP64 particle kernel against the derived FP64 peak, algorithmic operations of
+        # fp64_particle_flops per particle (rho^{n+1} fused when the window is off)
+        gp_s = stage_ms["gather_push"] / args.steps * 1e-3
+        flops = n * fp64_particle_flops(w.Nm)
+        ach = flops / gp_s / 1e12
+        roofline_particles = {
+            "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+            "algorithmic_flops": flops, "flops_per_particle": fp64_particle_flops(w.Nm),
+            "kernel": "k_gather_push<false> (gather, Boris push, J at x^{n+1/2}, rho at x^{n+1}; FP64)",
+            "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe nominal 1.25 TFLOP/s)",
+            "share_of_step": stage_ms["gather_push"] / sum(stage_ms.values()),
+            "note": "divides and square roots count once but run as FP64 instruction sequences; the FP64 "
+                    "pipe is the binding unit (profiles/k_gather_push__wake_2048x256_m2_fp64.md)"}
     if mixed:
         # the particle kernel (gather, push, J and rho deposits) against the survey's
         # algorithmic bytes: 56 B per particle (FP32 cell-relative state read and written,
@@ -351,15 +386,18 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
                               "frac": lay_bytes / max(lay_s, 1e-12) / 1e9 / pk["hbm_gbs"]},
             "note": "bound by instruction issue and L1 latency (profiles/k_gather_push_f32__wake_2048x256_m2_mixed.md), "
                     "not by DRAM"}
+    # `roofline` is the kernel with the largest share of the cycle; the other one beside it
+    dominant = roofline
+    if roofline_particles is not None and roofline_particles["share_of_step"] > roofline["share_of_step"]:
+        dominant = roofline_particles
     out = {"steps_per_s": steps_per_s, "ms_per_step": el_ms / args.steps,
            "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
-           "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+           "roofline": dominant, "roofline_dht": roofline, "roofline_particles": roofline_particles,
+           "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
            "dtype": {bd.PIC_FP64: "f64", bd.PIC_MIXED_TF32X3: "f32+tf32x3",
                      bd.PIC_MIXED_BF16X6: "f32+bf16x6"}[prec]}
     if tuning is not None:
         out["tuning"] = tuning
-    if mixed:
-        out["roofline_particles"] = roofline_particles
     sim.close()
     del sim
     torch.cuda.empty_cache()
@@ -451,8 +489,9 @@ def run_ours(args):
         "dtype": head["dtype"], "data": "synthetic", "config": config_of(w, n, args.precision),
         "particle_updates_per_s": head["steps_per_s"] * n,
         "stage_ms_per_step": head["stage_ms_per_step"],
-        "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
-        "clocks": head["clocks"],
+        "roofline": head["roofline"], "roofline_dht": head["roofline_dht"],
+        "roofline_particles": head["roofline_particles"],
+        "e2e": head["e2e"], "gpu_launches": head["gpu_launches"], "clocks": head["clocks"],
     }
     if args.precision == "fp64" and not args.no_mixed:
         # the two mixed-precision forms on the same workload (3-term TF32 and 6-product BF16
@@ -466,9 +505,9 @@ def run_ours(args):
                 "value": mx["steps_per_s"], "unit": "steps/s", "dtype": mx["dtype"],
                 "ms_per_step": mx["ms_per_step"], "particle_updates_per_s": mx["steps_per_s"] * n,
                 "speedup_vs_fp64": mx["steps_per_s"] / head["steps_per_s"],
-                "stage_ms_per_step": mx["stage_ms_per_step"], "roofline": mx["roofline"], "e2e": mx["e2e"],
-                "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"], "tuning": mx.get("tuning"),
-                "roofline_particles": mx.get("roofline_particles")}
+                "stage_ms_per_step": mx["stage_ms_per_step"], "roofline": mx["roofline"],
+                "roofline_dht": mx["roofline_dht"], "roofline_particles": mx["roofline_particles"], "e2e": mx["e2e"],
+                "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"], "tuning": mx.get("tuning")}
             if acc:
                 line[key]["accuracy_vs_fp64"] = acc[form]
         if acc:
@@ -498,7 +537,7 @@ def run_ours(args):
         # mixed form, with its accuracy against the FP64 form) and the batched scan
         large = measure_large(args, local, None, 1, args.large_accuracy_cycles)
         line["large"] = {k: large[k] for k in ("value", "unit", "ms_per_step", "particle_updates_per_s", "dtype",
-                                               "stage_ms_per_step", "roofline", "roofline_particles", "e2e",
+                                               "stage_ms_per_step", "roofline", "roofline_dht", "roofline_particles", "e2e",
                                                "clocks", "tuning", "config")}
         if "accuracy_vs_fp64" in large:
             line["large"]["accuracy_vs_fp64"] = large["accuracy_vs_fp64"]
@@ -696,7 +735,7 @@ def measure_large(args, local, dist=None, world=1, accuracy_cycles=0, crop=False
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": mx["dtype"],
         "data": "synthetic", "config": cfg, "particle_updates_per_s": mx["steps_per_s"] * n,
         "stage_ms_per_step": mx["stage_ms_per_step"], "roofline": mx["roofline"],
-        "roofline_particles": mx.get("roofline_particles"), "e2e": mx["e2e"],
+        "roofline_dht": mx["roofline_dht"], "roofline_particles": mx["roofline_particles"], "e2e": mx["e2e"],
         "gpu_launches": mx["gpu_launches"], "clocks": mx["clocks"], "tuning": mx.get("tuning"),
     }
     if accuracy_cycles > 0:
