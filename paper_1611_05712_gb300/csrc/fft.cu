@@ -37,6 +37,49 @@ template <typename T, bool INV> __device__ __forceinline__ T mul_mi(T a) {
   return r;
 }
 
+// v with its sign flipped when neg, by integer operations (no float64 instruction).
+__device__ __forceinline__ double neg_if(double v, bool neg) {
+  return __longlong_as_double(__double_as_longlong(v) ^ (neg ? (long long)0x8000000000000000ULL : 0LL));
+}
+__device__ __forceinline__ float neg_if(float v, bool neg) {
+  return __int_as_float(__float_as_int(v) ^ (neg ? (int)0x80000000u : 0));
+}
+
+// c x for a combination coefficient c of kind 0 (real), 1 (imaginary) or 2 (general); in
+// double rows a coefficient +-1 or +-i (unit != 0) costs sign flips only and a real or
+// imaginary one two multiplies (those rows are bound by the float64 unit).  Float rows
+// multiply in full: branches there would keep the row loads from issuing together.
+template <typename T>
+__device__ __forceinline__ T coef_mul(T c, int kind, int unit, T x) {
+  if constexpr (sizeof(x.x) == 4) return cmul(c, x);
+  T r;
+  if (kind == 0) {
+    if (unit) { r.x = neg_if(x.x, unit < 0); r.y = neg_if(x.y, unit < 0); }
+    else { r.x = c.x * x.x; r.y = c.x * x.y; }
+  } else if (kind == 1) {   // i c.y x = (-c.y x.y, c.y x.x)
+    if (unit) { r.x = neg_if(x.y, unit > 0); r.y = neg_if(x.x, unit < 0); }
+    else { r.x = -c.y * x.y; r.y = c.y * x.x; }
+  } else {
+    r = cmul(c, x);
+  }
+  return r;
+}
+
+// The combination coefficients of component comp for rows of type R.
+template <typename R, typename C2>
+__device__ __forceinline__ void row_coefs(const RowCombine& rc, int comp, C2& ca, C2& cb, int& ka, int& kb, int& ua,
+                                          int& ub) {
+  if constexpr (sizeof(R) == 4) {
+    ca.x = rc.fcaRe[comp]; ca.y = rc.fcaIm[comp];
+    cb.x = rc.fcbRe[comp]; cb.y = rc.fcbIm[comp];
+  } else {
+    ca.x = rc.caRe[comp]; ca.y = rc.caIm[comp];
+    cb.x = rc.cbRe[comp]; cb.y = rc.cbIm[comp];
+  }
+  ka = rc.kindA[comp]; kb = rc.kindB[comp];
+  ua = rc.unitA[comp]; ub = rc.unitB[comp];
+}
+
 struct FftPlan {
   int N;
   int n_pass;
@@ -120,6 +163,7 @@ template <typename C2> struct RowCtx {
   const C2* a;    // source rows of the combination (b may be null)
   const C2* b;
   C2 ca, cb;
+  int ka, kb, ua, ub;   // coefficient kinds and units (coef_mul)
   C2* o;          // destination row
   C2* buf;        // padded shared row buffer
   int N, tr, TR;
@@ -141,8 +185,8 @@ __device__ __forceinline__ void pow2_load_global(C2 (&v)[E], const RowCtx<C2>& c
       C2 x;
       x.x = (Re)0; x.y = (Re)0;
       if (c.active) {
-        x = cmul(c.ca, c.a[idx]);
-        if (c.b) x = cadd(x, cmul(c.cb, c.b[idx]));
+        x = coef_mul(c.ca, c.ka, c.ua, c.a[idx]);
+        if (c.b) x = cadd(x, coef_mul(c.cb, c.kb, c.ub, c.b[idx]));
       }
       v[q * 8 + r] = x;
     }
@@ -265,8 +309,7 @@ __global__ void __launch_bounds__(kFftThreads, fft_min_ctas<R>(E)) k_fft_pow2(co
   c.a = in + ((size_t)rc.srcA[comp] * rows_per_comp + rr) * N;
   const int sb = rc.srcB[comp];
   c.b = sb >= 0 ? in + ((size_t)sb * rows_per_comp + rr) * N : nullptr;
-  c.ca.x = (R)rc.caRe[comp]; c.ca.y = (R)rc.caIm[comp];
-  c.cb.x = (R)rc.cbRe[comp]; c.cb.y = (R)rc.cbIm[comp];
+  row_coefs<R>(rc, comp, c.ca, c.cb, c.ka, c.kb, c.ua, c.ub);
   c.o = out + (size_t)rrow * N;
   C2 v[E];
   const int n8 = lgN / 3, rem = lgN - 3 * n8;   // n8 >= 1 radix-8 passes, then radix 2^rem
@@ -317,7 +360,7 @@ __global__ void __launch_bounds__(kFftTmaThreads, fft_tma_ctas<E>())
                    RowCombine rc, int N, int lgN, int rows_per_comp, int n_comp, int G, int32_t* err) {
   using C2 = float2;
   constexpr int PS = 4;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   const int padN = N + (N >> PS);
   C2* stage_a = reinterpret_cast<C2*>(smem_raw);
   C2* stage_b = stage_a + (size_t)G * N;
@@ -355,8 +398,7 @@ __global__ void __launch_bounds__(kFftTmaThreads, fft_tma_ctas<E>())
     c.active = rr < rows_per_comp;
     c.a = stage_a + (size_t)lr * N;
     c.b = rc.srcB[comp] >= 0 ? stage_b + (size_t)lr * N : nullptr;
-    c.ca.x = (float)rc.caRe[comp]; c.ca.y = (float)rc.caIm[comp];
-    c.cb.x = (float)rc.cbRe[comp]; c.cb.y = (float)rc.cbIm[comp];
+    row_coefs<float>(rc, comp, c.ca, c.cb, c.ka, c.kb, c.ua, c.ub);
     c.o = out + ((size_t)comp * rows_per_comp + (c.active ? rr : 0)) * N;
     const bool ok = mbar_wait(bar, parity);
     if (__syncthreads_or(!ok)) {                 // the copy did not complete: give up
@@ -409,8 +451,8 @@ __device__ __forceinline__ void blue_load_global(C2 (&v)[E], const RowCtx<C2>& c
       C2 x;
       x.x = (Re)0; x.y = (Re)0;
       if (c.active && idx < N) {
-        x = cmul(c.ca, c.a[idx]);
-        if (c.b) x = cadd(x, cmul(c.cb, c.b[idx]));
+        x = coef_mul(c.ca, c.ka, c.ua, c.a[idx]);
+        if (c.b) x = cadd(x, coef_mul(c.cb, c.kb, c.ub, c.b[idx]));
         C2 w = chirp[idx];
         if (conj_chirp) w.y = -w.y;
         x = cmul(x, w);
@@ -467,8 +509,7 @@ __global__ void __launch_bounds__(kFftThreads, fft_min_ctas<R>(E)) k_fft_blue(
   c.a = in + ((size_t)rc.srcA[comp] * rows_per_comp + rr) * N;
   const int sb = rc.srcB[comp];
   c.b = sb >= 0 ? in + ((size_t)sb * rows_per_comp + rr) * N : nullptr;
-  c.ca.x = (R)rc.caRe[comp]; c.ca.y = (R)rc.caIm[comp];
-  c.cb.x = (R)rc.cbRe[comp]; c.cb.y = (R)rc.cbIm[comp];
+  row_coefs<R>(rc, comp, c.ca, c.cb, c.ka, c.kb, c.ua, c.ub);
   c.o = out + (size_t)rrow * N;
   C2 v[E];
   const int n8 = lgM / 3, rem = lgM - 3 * n8;
@@ -605,6 +646,7 @@ template <typename C2> struct MixedIO {
   const C2* a;
   const C2* b;     // second source row of the combination or null
   C2 ca, cb;
+  int ka, kb, ua, ub;
   C2* o;
   decltype(C2{}.x) scale;
 };
@@ -625,8 +667,8 @@ __device__ __forceinline__ void mixed_pass(const C2* __restrict__ src, C2* __res
     for (int r = 0; r < R; ++r) {
       const int i = t + r * NR;
       if (FIRST) {
-        C2 x = cmul(io.ca, io.a[i]);
-        if (io.b) x = cadd(x, cmul(io.cb, io.b[i]));
+        C2 x = coef_mul(io.ca, io.ka, io.ua, io.a[i]);
+        if (io.b) x = cadd(x, coef_mul(io.cb, io.kb, io.ub, io.b[i]));
         v[r] = x;
       } else {
         v[r] = src[i];
@@ -687,8 +729,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(const typename Vec2<R>::T* __r
   io.a = in + ((size_t)rc.srcA[comp] * rows_per_comp + rr) * N;
   const int sb = rc.srcB[comp];
   io.b = sb >= 0 ? in + ((size_t)sb * rows_per_comp + rr) * N : nullptr;
-  io.ca.x = (R)rc.caRe[comp]; io.ca.y = (R)rc.caIm[comp];
-  io.cb.x = (R)rc.cbRe[comp]; io.cb.y = (R)rc.cbIm[comp];
+  row_coefs<R>(rc, comp, io.ca, io.cb, io.ka, io.kb, io.ua, io.ub);
   io.o = out + (size_t)row * N;
   io.scale = INV ? (R)1 / (R)N : (R)1;
   // radices packed 4 bits each (a parameter array indexed at run time would be copied to
@@ -864,7 +905,24 @@ pic_status launch_bluestein(Sim* s, const void* in, void* out, const RowCombine&
 
 bool fft_is_pow2(int N) { return N >= 8 && (N & (N - 1)) == 0; }
 
-pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& rc, bool inverse) {
+// Kind, unit and float copies of each combination coefficient (RowCombine).
+static void finish_row_combine(RowCombine& rc) {
+  auto classify = [](double re, double im, int8_t& kind, int8_t& unit) {
+    kind = im == 0.0 ? 0 : (re == 0.0 ? 1 : 2);
+    const double v = kind == 0 ? re : im;
+    unit = kind < 2 && (v == 1.0 || v == -1.0) ? (v > 0 ? 1 : -1) : 0;
+  };
+  for (int k = 0; k < 6; ++k) {
+    classify(rc.caRe[k], rc.caIm[k], rc.kindA[k], rc.unitA[k]);
+    classify(rc.cbRe[k], rc.cbIm[k], rc.kindB[k], rc.unitB[k]);
+    rc.fcaRe[k] = (float)rc.caRe[k]; rc.fcaIm[k] = (float)rc.caIm[k];
+    rc.fcbRe[k] = (float)rc.cbRe[k]; rc.fcbIm[k] = (float)rc.cbIm[k];
+  }
+}
+
+pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& rc_in, bool inverse) {
+  RowCombine rc = rc_in;
+  finish_row_combine(rc);
   const pic_config& c = s->cfg;
   const int rows_per_comp = c.Nm * c.Nr;
   const int rows = rc.n_out * rows_per_comp;

@@ -173,6 +173,11 @@ struct RowCombine {
   int32_t n_out;
   int32_t srcA[6], srcB[6];   // srcB < 0: none
   double caRe[6], caIm[6], cbRe[6], cbIm[6];
+  // filled by launch_fft_rows from the coefficients above: kind 0 real, 1 imaginary, 2
+  // general; unit +1 / -1 when the coefficient is +-1 (kind 0) or +-i (kind 1), else 0;
+  // float copies for the float rows (no float64 conversions in those kernels)
+  int8_t kindA[6], kindB[6], unitA[6], unitB[6];
+  float fcaRe[6], fcaIm[6], fcbRe[6], fcbIm[6];
 };
 pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& rc, bool inverse);
 pic_status fft_configure_device();      // once per device, before any FFT launch
