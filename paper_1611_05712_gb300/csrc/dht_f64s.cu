@@ -18,7 +18,8 @@
 //     2^(-W (g+2))): groups 0..3 (at most 4 products each) are exact, groups 4..6 add an
 //     FP32 rounding of relative size 2^-24 at weight <= 2^-42; products with i + j >= S
 //     are left out (weight <= 2^-63);
-//   * the epilogue sums the 7 group accumulators in FP64 and scales by 2^(E_c + E_n).
+//   * the epilogue combines the 7 group accumulators in 64-bit integer arithmetic,
+//     converts once to FP64 and scales by 2^(E_c + E_n).
 // The result agrees with the FP64 product to about 2^-49 of max|A_n| max|X_c| K.  Used
 // for Nr <= 256 (the exactness bound above); larger Nr keep the FP64 SIMT GEMM.
 //
@@ -26,9 +27,9 @@
 // per DHT k_f64s_colmax finds the column maxima and k_f64s_panel slices the panels
 // into K-major planes; k_dht_f64s is a persistent warp-specialised tcgen05 kernel: one
 // thread issues the tensor-memory-access copies of both operands (7 planes each, 64-byte
-// swizzle, 32 K elements per stage) into a ring of 3 stages, one thread issues the 28
-// slice products per 16 K elements into 7 TMEM accumulators (two sets, alternating by
-// tile), and 4 epilogue warps combine a set in FP64 and store Y while the next tile runs.
+// swizzle, 32 K elements per stage) into a ring of stages, one thread issues the 28 slice
+// products per 16 K elements into 7 TMEM accumulators of a 128 x 64 tile, and 4 epilogue
+// warps combine them and store Y.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -368,21 +369,32 @@ __global__ void __launch_bounds__(kF64sThreads, 1) k_dht_f64s(DhtBatch bt, F64sP
             const int n = w.n0 + j0 + e;
             if (n >= P.Nr) continue;
             // sum_g acc_g 2^(-7(g+2)) = T 2^-49 with
-            //   T = (((a0 2^7 + a1) 2^7 + a2) 2^7 + a3) 2^14 + (a4 2^7 + a5 + a6 2^-7):
-            // the exact groups 0..3 in integer arithmetic, the inexact tail (weight
-            // <= 2^-42) in float rounded to an integer; |T| < 2^58.  Then one conversion
-            // and one power-of-two scaling in FP64 (GB300's FP64 unit is the scarce one)
+            //   T = (((a0 2^7 + a1) 2^7 + a2) 2^7 + a3) 2^14 + a4 2^7 + a5 + round(a6 2^-7),
+            // all in integer arithmetic: a0..a3 are exact integers below 2^24, a4..a6
+            // integer-valued floats below 2^25 (their sums were rounded at weight <= 2^-42);
+            // |T| < 2^58.  Then one int -> double conversion, the only float64 instruction
+            // (GB300's float64 unit is the scarce one), and the scaling by 2^k as an addition
+            // to the exponent field while the result stays normal.
             const long long a0 = __float2int_rn(__uint_as_float(r[0][e]));
             const long long a1 = __float2int_rn(__uint_as_float(r[1][e]));
             const long long a2 = __float2int_rn(__uint_as_float(r[2][e]));
             const long long a3 = __float2int_rn(__uint_as_float(r[3][e]));
-            const float tail = fmaf(__uint_as_float(r[6][e]), 1.f / 128.f,
-                                    fmaf(__uint_as_float(r[4][e]), 128.f, __uint_as_float(r[5][e])));
-            const long long T = (((a0 * 128 + a1) * 128 + a2) * 128 + a3) * 16384 + __float2ll_rn(tail);
+            const long long a4 = __float2int_rn(__uint_as_float(r[4][e]));
+            const long long a5 = __float2int_rn(__uint_as_float(r[5][e]));
+            const long long a6 = __float2int_rn(__uint_as_float(r[6][e]) * (1.f / 128.f));
+            const long long T = (((a0 * 128 + a1) * 128 + a2) * 128 + a3) * 16384 + a4 * 128 + a5 + a6;
             const int k = Ec + rexp[n] - kSliceBits * kSlices;   // 2^(E_c + E_n - 49)
-            const double scale = (k >= -1022 && k <= 1023) ? __longlong_as_double((long long)(1023 + k) << 52)
-                                                           : ldexp(1.0, k);
-            Y[(size_t)n * P.Nc + c] = (double)T * scale;
+            const double t = (double)T;
+            long long bits = __double_as_longlong(t);
+            const int ex = (int)((bits >> 52) & 0x7ff) + k;
+            double y;
+            if (T != 0 && ex > 0 && ex < 2047) {
+              bits += (long long)k * (1LL << 52);
+              y = __longlong_as_double(bits);
+            } else {
+              y = t * ldexp(1.0, k);   // zero, or a result outside the normal range
+            }
+            Y[(size_t)n * P.Nc + c] = y;
           }
         }
       }
