@@ -97,11 +97,13 @@ def test_order_sweep_errors_match_the_oracle(gpu_runs):
                 "ez": O.err_ez(ref[p]["ez"], ref[0]["ez"]),
                 "ez_l2": float(np.linalg.norm(np.fft.fft2(ref[p]["ez"]) - np.fft.fft2(ref[0]["ez"]))
                                / np.linalg.norm(np.fft.fft2(ref[0]["ez"])))}
-        # Err_Ez as printed divides Fourier cell by cell by the infinite-order spectrum, so the
-        # cells where that nearly vanishes, and which the two runs' rounding differs in
-        # relatively most, dominate it: 1e-3 there, 1e-6 for the other measures
+        # Err_Ez as printed is the rms over Fourier cells of |dF / F_inf|, so the cells where
+        # F_inf nearly vanishes (its value there is rounding noise of the infinite-order run)
+        # dominate it, and two FP64 runs that differ only in rounding order (atomic order,
+        # fused multiply-adds) give values a few 1e-3 apart while the other measures agree
+        # to 1e-9: 1e-2 there, 1e-6 for the other measures
         for k in got:
-            assert got[k] == pytest.approx(want[k], rel=1e-3 if k == "ez" else 1e-6), (p, k, got[k], want[k])
+            assert got[k] == pytest.approx(want[k], rel=1e-2 if k == "ez" else 1e-6), (p, k, got[k], want[k])
         errs[p] = got
     # the measures fall as the order grows (the paper's order study)
     assert errs[4]["ez_l2"] > errs[16]["ez_l2"]
