@@ -11,6 +11,7 @@
 // out = ca * inA + cb * inB, which forms J_+- = (J_r -+ i J_theta)/2 before the forward
 // transform and E_r = E_+ + E_-, E_theta = i (E_+ - E_-) before the inverse one.
 #include <mutex>
+#include <type_traits>
 
 #include "pic_internal.cuh"
 #include "tc_common.cuh"
@@ -21,6 +22,81 @@ namespace {
 template <typename R> struct Vec2;
 template <> struct Vec2<double> { using T = double2; };
 template <> struct Vec2<float> { using T = float2; };
+
+// ---- double-word arithmetic for the FP64 rows ----
+// GB300 runs float64 at 1/64 of its float32 rate, and the FP64 form's row FFT was bound by
+// the float64 unit.  Its butterflies now run on the float32 units with each real number an
+// unevaluated sum of two floats, hi + lo with |lo| <= ulp(hi)/2: about 48 significant bits
+// (double-word arithmetic after Dekker, Numer. Math. 18, 1971, with error-free products
+// from fused multiply-adds).  Sum: the exact sum of the high parts (Knuth's two-sum) plus
+// the low parts, renormalised: error below 2u^2 (|x| + |y|), u = 2^-24, which is the
+// absolute error an FFT's error bound is made of.  Product: the exact product of the high
+// parts (one fma) plus the cross terms: error below a few u^2 |x y|.  Rows are read and
+// written as doubles; the conversions use integer operations and, on the way out, one
+// float64 addition per value.
+struct dw {
+  float hi, lo;
+  dw() = default;
+  __host__ __device__ constexpr dw(float h, float l) : hi(h), lo(l) {}
+  __host__ __device__ constexpr explicit dw(int v) : hi((float)v), lo(0.f) {}
+};
+struct dw2 {
+  dw x, y;
+};
+template <> struct Vec2<dw> { using T = dw2; };
+
+__device__ __forceinline__ dw dw_fast_two_sum(float a, float b) {   // |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return dw(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dw operator+(dw x, dw y) {
+  const float s = __fadd_rn(x.hi, y.hi);
+  const float bb = __fsub_rn(s, x.hi);
+  const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));   // s + e = x.hi + y.hi
+  return dw_fast_two_sum(s, __fadd_rn(e, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ dw operator-(dw x) { return dw(-x.hi, -x.lo); }
+__device__ __forceinline__ dw operator-(dw x, dw y) { return x + (-y); }
+__device__ __forceinline__ dw operator*(dw x, dw y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);   // p + e = x.hi y.hi exactly
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return dw_fast_two_sum(p, e);
+}
+
+// double -> double word: hi = x with its mantissa cut to 24 bits, lo = the remaining 29
+// bits rounded to a float (integer operations and one int -> float conversion); the
+// float64 conversions only for 0 < |x| < 2^-74 or |x| >= 2^128 (outside the float range
+// of hi and lo).
+__device__ __forceinline__ dw dw_from_double(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if ((b << 1) == 0ull) return dw(__uint_as_float(sign), 0.f);
+  if (e < -74 || e > 127) {
+    const float h = (float)x;
+    return dw(h, (float)(x - (double)h));
+  }
+  const unsigned long long m = b & 0xfffffffffffffull;
+  const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
+  const unsigned r = (unsigned)(m & 0x1fffffffull);   // weight 2^(e - 52) per unit
+  float lo = 0.f;
+  if (r != 0u) lo = __uint_as_float((__float_as_uint(__uint2float_rn(r)) + ((unsigned)(e - 52) << 23)) | sign);
+  return dw(hi, lo);
+}
+
+// float -> double exactly, by the bits (0 and subnormal floats through the conversion).
+__device__ __forceinline__ double dw_widen(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xffu;
+  if (ef == 0u || ef == 0xffu) return (double)f;
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(ef - 127 + 1023) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
+}
+__device__ __forceinline__ double dw_to_double(dw v) { return dw_widen(v.hi) + dw_widen(v.lo); }
 
 template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
   T r;
@@ -72,6 +148,9 @@ __device__ __forceinline__ void row_coefs(const RowCombine& rc, int comp, C2& ca
   if constexpr (sizeof(R) == 4) {
     ca.x = rc.fcaRe[comp]; ca.y = rc.fcaIm[comp];
     cb.x = rc.fcbRe[comp]; cb.y = rc.fcbIm[comp];
+  } else if constexpr (std::is_same<R, dw>::value) {   // the coefficients are exact in float
+    ca.x = dw(rc.fcaRe[comp], 0.f); ca.y = dw(rc.fcaIm[comp], 0.f);
+    cb.x = dw(rc.fcbRe[comp], 0.f); cb.y = dw(rc.fcbIm[comp], 0.f);
   } else {
     ca.x = rc.caRe[comp]; ca.y = rc.caIm[comp];
     cb.x = rc.cbRe[comp]; cb.y = rc.cbIm[comp];
@@ -79,6 +158,32 @@ __device__ __forceinline__ void row_coefs(const RowCombine& rc, int comp, C2& ca
   ka = rc.kindA[comp]; kb = rc.kindB[comp];
   ua = rc.unitA[comp]; ub = rc.unitB[comp];
 }
+
+// 1/sqrt(2) and 1/N in the row arithmetic R.
+template <typename R> __device__ __forceinline__ R inv_sqrt2() { return (R)0.70710678118654752440; }
+template <> __device__ __forceinline__ dw inv_sqrt2<dw>() { return dw(0.70710676908493042f, 1.2101617485882343e-08f); }
+template <typename R> __device__ __forceinline__ R inv_len(int N) { return (R)1 / (R)N; }
+template <> __device__ __forceinline__ dw inv_len<dw>(int N) { return dw(1.f / (float)N, 0.f); }   // N a power of two
+
+__device__ __forceinline__ dw neg_if(dw v, bool neg) { return dw(neg_if(v.hi, neg), neg_if(v.lo, neg)); }
+
+// Element type of the rows in global memory for row arithmetic R (double-word rows are
+// stored as doubles), and the conversions between the two.
+template <typename R> struct GlobalOf { using T = typename Vec2<R>::T; };
+template <> struct GlobalOf<dw> { using T = double2; };
+template <typename C2, typename G2> __device__ __forceinline__ C2 from_global(const G2& v) {
+  if constexpr (std::is_same<C2, G2>::value) {
+    return v;
+  } else {
+    C2 r;
+    r.x = dw_from_double(v.x);
+    r.y = dw_from_double(v.y);
+    return r;
+  }
+}
+__device__ __forceinline__ double2 to_global(const dw2& v) { return make_double2(dw_to_double(v.x), dw_to_double(v.y)); }
+__device__ __forceinline__ float2 to_global(const float2& v) { return v; }
+__device__ __forceinline__ double2 to_global(const double2& v) { return v; }
 
 struct FftPlan {
   int N;
@@ -131,7 +236,7 @@ template <typename C2, bool INV> __device__ __forceinline__ void dft4(C2* v) {
 // b_r = (v_r - v_{r+4}) w_8^r.
 template <typename C2, bool INV> __device__ __forceinline__ void dft8(C2* v) {
   using R = decltype(v[0].x);
-  const R h = (R)0.70710678118654752440;   // 1/sqrt(2)
+  const R h = inv_sqrt2<R>();
   C2 a[4], b[4];
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
@@ -159,12 +264,12 @@ template <typename C2, bool INV> __device__ __forceinline__ void dft8(C2* v) {
 }
 
 // Per-row context of the power-of-two kernel.
-template <typename C2> struct RowCtx {
-  const C2* a;    // source rows of the combination (b may be null)
-  const C2* b;
+template <typename C2, typename G2 = C2> struct RowCtx {
+  const G2* a;    // source rows of the combination (b may be null), in global memory
+  const G2* b;
   C2 ca, cb;
   int ka, kb, ua, ub;   // coefficient kinds and units (coef_mul)
-  C2* o;          // destination row
+  G2* o;          // destination row
   C2* buf;        // padded shared row buffer
   int N, tr, TR;
   bool active;    // false for the idle row slots of the last CTA
@@ -173,8 +278,8 @@ template <typename C2> struct RowCtx {
 template <int PS> __device__ __forceinline__ int padded(int i) { return i + (i >> PS); }
 
 // Inputs of the first pass (radix 8): v[8q + r] = (ca a + cb b)[t + r N/8], t = tr + q TR.
-template <typename C2, int E>
-__device__ __forceinline__ void pow2_load_global(C2 (&v)[E], const RowCtx<C2>& c) {
+template <typename C2, int E, typename G2>
+__device__ __forceinline__ void pow2_load_global(C2 (&v)[E], const RowCtx<C2, G2>& c) {
   using Re = decltype(v[0].x);
   const int N8 = c.N >> 3;
 #pragma unroll
@@ -185,8 +290,8 @@ __device__ __forceinline__ void pow2_load_global(C2 (&v)[E], const RowCtx<C2>& c
       C2 x;
       x.x = (Re)0; x.y = (Re)0;
       if (c.active) {
-        x = coef_mul(c.ca, c.ka, c.ua, c.a[idx]);
-        if (c.b) x = cadd(x, coef_mul(c.cb, c.kb, c.ub, c.b[idx]));
+        x = coef_mul(c.ca, c.ka, c.ua, from_global<C2>(c.a[idx]));
+        if (c.b) x = cadd(x, coef_mul(c.cb, c.kb, c.ub, from_global<C2>(c.b[idx])));
       }
       v[q * 8 + r] = x;
     }
@@ -194,8 +299,8 @@ __device__ __forceinline__ void pow2_load_global(C2 (&v)[E], const RowCtx<C2>& c
 }
 
 // Inputs of a later pass of radix R from the shared row buffer.
-template <typename C2, int E, int R, int PS>
-__device__ __forceinline__ void pow2_load_shared(C2 (&v)[E], const RowCtx<C2>& c) {
+template <typename C2, int E, int R, int PS, typename G2>
+__device__ __forceinline__ void pow2_load_shared(C2 (&v)[E], const RowCtx<C2, G2>& c) {
   const int NR = c.N / R;
 #pragma unroll
   for (int q = 0; q < E / R; ++q) {
@@ -232,8 +337,8 @@ __device__ __forceinline__ void pass_twiddles(C2 (&w)[R], const C2* __restrict__
 }
 
 // Twiddles and the R-point DFTs of a pass.
-template <typename C2, bool INV, int E, int R>
-__device__ __forceinline__ void pow2_butterflies(C2 (&v)[E], const RowCtx<C2>& c, const C2* __restrict__ twp,
+template <typename C2, bool INV, int E, int R, typename G2>
+__device__ __forceinline__ void pow2_butterflies(C2 (&v)[E], const RowCtx<C2, G2>& c, const C2* __restrict__ twp,
                                                  int L) {
 #pragma unroll
   for (int q = 0; q < E / R; ++q) {
@@ -252,10 +357,10 @@ __device__ __forceinline__ void pow2_butterflies(C2 (&v)[E], const RowCtx<C2>& c
 
 // Outputs of a pass: out[j L R + s L + k] = y_s, to the shared buffer or (last pass, L =
 // N/R) to the destination row, scaled by 1/N for the inverse transform.
-template <typename C2, bool INV, int E, int R, int PS>
-__device__ __forceinline__ void pow2_store(C2 (&v)[E], const RowCtx<C2>& c, int L, int lgL, bool last) {
+template <typename C2, bool INV, int E, int R, int PS, typename G2>
+__device__ __forceinline__ void pow2_store(C2 (&v)[E], const RowCtx<C2, G2>& c, int L, int lgL, bool last) {
   using Re = decltype(v[0].x);
-  const Re scale = INV ? (Re)1 / (Re)c.N : (Re)1;
+  const Re scale = INV ? inv_len<Re>(c.N) : (Re)1;
 #pragma unroll
   for (int q = 0; q < E / R; ++q) {
     const int t = c.tr + q * c.TR;
@@ -266,9 +371,11 @@ __device__ __forceinline__ void pow2_store(C2 (&v)[E], const RowCtx<C2>& c, int 
       if (last) {
         if (c.active) {
           C2 y = v[q * R + s2];
-          y.x *= scale;
-          y.y *= scale;
-          c.o[idx] = y;
+          if (INV) {
+            y.x = y.x * scale;
+            y.y = y.y * scale;
+          }
+          c.o[idx] = to_global(y);
         }
       } else {
         c.buf[padded<PS>(idx)] = v[q * R + s2];
@@ -277,8 +384,8 @@ __device__ __forceinline__ void pow2_store(C2 (&v)[E], const RowCtx<C2>& c, int 
   }
 }
 
-template <typename C2, bool INV, int E, int R, int PS>
-__device__ __forceinline__ void pow2_pass(C2 (&v)[E], const RowCtx<C2>& c, const C2* __restrict__ twp, int L,
+template <typename C2, bool INV, int E, int R, int PS, typename G2>
+__device__ __forceinline__ void pow2_pass(C2 (&v)[E], const RowCtx<C2, G2>& c, const C2* __restrict__ twp, int L,
                                           int lgL, bool last) {
   pow2_butterflies<C2, INV, E, R>(v, c, twp, L);
   pow2_store<C2, INV, E, R, PS>(v, c, L, lgL, last);
@@ -287,15 +394,16 @@ __device__ __forceinline__ void pow2_pass(C2 (&v)[E], const RowCtx<C2>& c, const
 // Double rows: one CTA of 256 threads transforms 256 E / N rows (N <= 2048: E = 8; N = 4096,
 // 8192: one row with E = 16, 32).  Float rows take k_fft_pow2_tma below.
 template <typename R, bool INV, int E>
-__global__ void __launch_bounds__(kFftThreads, fft_min_ctas<R>(E)) k_fft_pow2(const typename Vec2<R>::T* __restrict__ in,
-                                                          typename Vec2<R>::T* __restrict__ out,
+__global__ void __launch_bounds__(kFftThreads, fft_min_ctas<R>(E)) k_fft_pow2(const typename GlobalOf<R>::T* __restrict__ in,
+                                                          typename GlobalOf<R>::T* __restrict__ out,
                                                           const typename Vec2<R>::T* __restrict__ twp,
                                                           RowCombine rc, int N, int lgN, int rows,
                                                           int rows_per_comp) {
   using C2 = typename Vec2<R>::T;
+  using G2 = typename GlobalOf<R>::T;
   constexpr int PS = sizeof(R) == 4 ? 4 : 3;   // one pad element per 128 bytes
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  RowCtx<C2> c;
+  RowCtx<C2, G2> c;
   c.N = N;
   c.TR = N / E;
   const int lr = threadIdx.x / c.TR;
@@ -817,9 +925,13 @@ pic_status fft_configure_device() {
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2_tma<true, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_tma_smem(1024)));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<dw, false, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<dw, true, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4608 * 16));
   // float64 rows of 8192 (one row per CTA, 32 values per thread): 8192 + 1024 padded doubles
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 9216 * 16));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<double, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 9216 * 16));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<dw, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 9216 * 16));
+  PIC_CUDA(cudaFuncSetAttribute(k_fft_pow2<dw, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 9216 * 16));
   // Bluestein rows of length M = 8192 (float) / 4096 (double)
   PIC_CUDA(cudaFuncSetAttribute(k_fft_blue<float, false, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
   PIC_CUDA(cudaFuncSetAttribute(k_fft_blue<float, true, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 8704 * 8));
@@ -841,7 +953,8 @@ void launch_pow2(Sim* s, int N, const void* in, void* out, const void* twp, cons
   const int rpc = kFftThreads / (N / E);
   const size_t smem = (size_t)rpc * (N + (N >> PS)) * sizeof(C2);
   const int grid = (rows + rpc - 1) / rpc;
-  k_fft_pow2<R, INV, E><<<grid, kFftThreads, smem, s->stream>>>((const C2*)in, (C2*)out, (const C2*)twp, rc, N,
+  using G2 = typename GlobalOf<R>::T;
+  k_fft_pow2<R, INV, E><<<grid, kFftThreads, smem, s->stream>>>((const G2*)in, (G2*)out, (const C2*)twp, rc, N,
                                                                 lgN, rows, rows_per_comp);
 }
 
@@ -934,10 +1047,14 @@ pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& 
                    : launch_bluestein<float, false>(s, in, out, rc, rows, rows_per_comp);
   }
   if (fft_is_pow2(c.Nz)) {
-    if (c.precision == PIC_FP64) {
+    if (c.precision == PIC_FP64 && s->dht_path == PIC_DHT_F64_GEMM) {   // IEEE float64 throughout
       const void* twp = s->at<double2>(s->lay.twp);
       if (inverse) launch_pow2_e<double, true>(s, c.Nz, in, out, twp, rc, rows, rows_per_comp);
       else launch_pow2_e<double, false>(s, c.Nz, in, out, twp, rc, rows, rows_per_comp);
+    } else if (c.precision == PIC_FP64) {   // double-word butterflies on the float32 units
+      const void* twp = s->at<dw2>(s->lay.twp_dw);
+      if (inverse) launch_pow2_e<dw, true>(s, c.Nz, in, out, twp, rc, rows, rows_per_comp);
+      else launch_pow2_e<dw, false>(s, c.Nz, in, out, twp, rc, rows, rows_per_comp);
     } else {
       const void* twp = s->at<float2>(s->lay.twp_f);
       if (inverse) launch_pow2_tma<true>(s, c.Nz, in, out, twp, rc, rows_per_comp);

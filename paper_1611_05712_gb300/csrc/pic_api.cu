@@ -108,6 +108,7 @@ Layout make_layout(const pic_config& c) {
   L.tr = take((size_t)c.Nm * c.Nr * 8);
   L.coef = take(6 * G * 8);
   L.twp = take((size_t)c.Nz * 16);
+  if (c.precision == PIC_FP64) L.twp_dw = take((size_t)c.Nz * 16);
   const int M = bluestein_length(c.Nz, c.precision);
   if (M > 0) {
     L.twm = take((size_t)M * 16);

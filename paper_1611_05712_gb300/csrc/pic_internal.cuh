@@ -36,6 +36,7 @@ struct Layout {
   size_t kperp, binv, mfwd, svd_w, svd_v, svd_d;                // DHT tables and scratch
   size_t kzmod, tz, tr, coef;                                    // PSATD tables
   size_t twp;        // per-pass twiddle tables of the row FFT (radix-8 or mixed-radix plan)
+  size_t twp_dw;     // the same as double words (hi, lo float pairs), FP64 form
   size_t part[2][7], pid[2];                                     // particles (double buffer)
   size_t keys, perm, perm_tmp, count, start, scan_blk, big_list, big_count;
   size_t diag_acc, err;

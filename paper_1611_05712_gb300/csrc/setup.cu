@@ -405,6 +405,15 @@ __global__ void k_to_float(const double* __restrict__ in, float* __restrict__ ou
     out[i] = (float)in[i];
 }
 
+// x -> (hi, lo) = (float(x), float(x - hi)): a double word of about 48 bits.
+__global__ void k_to_double_word(const double* __restrict__ in, float2* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const double x = in[i];
+    const float h = (float)x;
+    out[i] = make_float2(h, (float)(x - (double)h));
+  }
+}
+
 // Split of FP64 matrices (rows of Nr) for 3-term TF32 products: hi = the value rounded to
 // TF32 (10 explicit mantissa bits, low 13 bits of the float zero), lo = float(value - hi).
 // Output rows have a pitch of `pitch` >= Nr floats (16-byte multiple for the tensor-memory
@@ -637,11 +646,14 @@ pic_status launch_setup_twiddles(Sim* s) {
     k_twiddles_plan<<<blocks_for(s->cfg.Nz, 128), 128, 0, s->stream>>>(s->at<double2>(s->lay.twp), s->cfg.Nz, plan);
   }
   PIC_LAUNCHED(s);
+  const size_t n2 = 2 * (size_t)s->cfg.Nz;
   if (s->cfg.precision != PIC_FP64) {
-    const size_t n2 = 2 * (size_t)s->cfg.Nz;
     k_to_float<<<conv_grid(n2), 256, 0, s->stream>>>(s->at<double>(s->lay.twp), s->at<float>(s->lay.twp_f), n2);
-    PIC_LAUNCHED(s);
+  } else {   // double words for the FP64 rows: hi = float(x), lo = float(x - hi)
+    k_to_double_word<<<conv_grid(n2), 256, 0, s->stream>>>(s->at<double>(s->lay.twp), s->at<float2>(s->lay.twp_dw),
+                                                           n2);
   }
+  PIC_LAUNCHED(s);
   return PIC_OK;
 }
 
