@@ -14,6 +14,7 @@
 #include <type_traits>
 
 #include "pic_internal.cuh"
+#include "dword.cuh"
 #include "tc_common.cuh"
 
 namespace pic {
@@ -23,80 +24,7 @@ template <typename R> struct Vec2;
 template <> struct Vec2<double> { using T = double2; };
 template <> struct Vec2<float> { using T = float2; };
 
-// ---- double-word arithmetic for the FP64 rows ----
-// GB300 runs float64 at 1/64 of its float32 rate, and the FP64 form's row FFT was bound by
-// the float64 unit.  Its butterflies now run on the float32 units with each real number an
-// unevaluated sum of two floats, hi + lo with |lo| <= ulp(hi)/2: about 48 significant bits
-// (double-word arithmetic after Dekker, Numer. Math. 18, 1971, with error-free products
-// from fused multiply-adds).  Sum: the exact sum of the high parts (Knuth's two-sum) plus
-// the low parts, renormalised: error below 2u^2 (|x| + |y|), u = 2^-24, which is the
-// absolute error an FFT's error bound is made of.  Product: the exact product of the high
-// parts (one fma) plus the cross terms: error below a few u^2 |x y|.  Rows are read and
-// written as doubles; the conversions use integer operations and, on the way out, one
-// float64 addition per value.
-struct dw {
-  float hi, lo;
-  dw() = default;
-  __host__ __device__ constexpr dw(float h, float l) : hi(h), lo(l) {}
-  __host__ __device__ constexpr explicit dw(int v) : hi((float)v), lo(0.f) {}
-};
-struct dw2 {
-  dw x, y;
-};
 template <> struct Vec2<dw> { using T = dw2; };
-
-__device__ __forceinline__ dw dw_fast_two_sum(float a, float b) {   // |a| >= |b| or a = 0
-  const float s = __fadd_rn(a, b);
-  return dw(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
-__device__ __forceinline__ dw operator+(dw x, dw y) {
-  const float s = __fadd_rn(x.hi, y.hi);
-  const float bb = __fsub_rn(s, x.hi);
-  const float e = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));   // s + e = x.hi + y.hi
-  return dw_fast_two_sum(s, __fadd_rn(e, __fadd_rn(x.lo, y.lo)));
-}
-__device__ __forceinline__ dw operator-(dw x) { return dw(-x.hi, -x.lo); }
-__device__ __forceinline__ dw operator-(dw x, dw y) { return x + (-y); }
-__device__ __forceinline__ dw operator*(dw x, dw y) {
-  const float p = __fmul_rn(x.hi, y.hi);
-  float e = __fmaf_rn(x.hi, y.hi, -p);   // p + e = x.hi y.hi exactly
-  e = __fmaf_rn(x.hi, y.lo, e);
-  e = __fmaf_rn(x.lo, y.hi, e);
-  return dw_fast_two_sum(p, e);
-}
-
-// double -> double word: hi = x with its mantissa cut to 24 bits, lo = the remaining 29
-// bits rounded to a float (integer operations and one int -> float conversion); the
-// float64 conversions only for 0 < |x| < 2^-74 or |x| >= 2^128 (outside the float range
-// of hi and lo).
-__device__ __forceinline__ dw dw_from_double(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int e = (int)((b >> 52) & 0x7ff) - 1023;
-  if ((b << 1) == 0ull) return dw(__uint_as_float(sign), 0.f);
-  if (e < -74 || e > 127) {
-    const float h = (float)x;
-    return dw(h, (float)(x - (double)h));
-  }
-  const unsigned long long m = b & 0xfffffffffffffull;
-  const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
-  const unsigned r = (unsigned)(m & 0x1fffffffull);   // weight 2^(e - 52) per unit
-  float lo = 0.f;
-  if (r != 0u) lo = __uint_as_float((__float_as_uint(__uint2float_rn(r)) + ((unsigned)(e - 52) << 23)) | sign);
-  return dw(hi, lo);
-}
-
-// float -> double exactly, by the bits (0 and subnormal floats through the conversion).
-__device__ __forceinline__ double dw_widen(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ef = (u >> 23) & 0xffu;
-  if (ef == 0u || ef == 0xffu) return (double)f;
-  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(ef - 127 + 1023) << 52) |
-                               ((unsigned long long)(u & 0x7fffffu) << 29);
-  return __longlong_as_double((long long)d);
-}
-__device__ __forceinline__ double dw_to_double(dw v) { return dw_widen(v.hi) + dw_widen(v.lo); }
 
 template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
   T r;
@@ -165,7 +93,6 @@ template <> __device__ __forceinline__ dw inv_sqrt2<dw>() { return dw(0.70710676
 template <typename R> __device__ __forceinline__ R inv_len(int N) { return (R)1 / (R)N; }
 template <> __device__ __forceinline__ dw inv_len<dw>(int N) { return dw(1.f / (float)N, 0.f); }   // N a power of two
 
-__device__ __forceinline__ dw neg_if(dw v, bool neg) { return dw(neg_if(v.hi, neg), neg_if(v.lo, neg)); }
 
 // Element type of the rows in global memory for row arithmetic R (double-word rows are
 // stored as doubles), and the conversions between the two.
