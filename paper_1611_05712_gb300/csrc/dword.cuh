@@ -2,13 +2,14 @@
 //
 // GB300 runs float64 at 1/64 of its float32 rate, and the FP64 form's row FFT was bound by
 // the float64 unit.  Its butterflies run on the float32 units with each real number an
-// unevaluated sum of two floats, hi + lo with |lo| <= ulp(hi)/2: about
-// 48 significant bits (double-word arithmetic after Dekker, Numer. Math. 18, 1971, with
-// error-free products from fused multiply-adds).  Sum: the exact sum of the high parts
-// (Knuth's two-sum) plus the low parts, renormalised: error below 2u^2 (|x| + |y|),
-// u = 2^-24, an absolute error of the kind an FFT's error bound is made of.  Product: the exact product of the high parts (one fma) plus the cross
-// terms: error below a few u^2 |x y|.  Grids stay doubles in memory; the conversions use
-// integer operations and, on the way out, one float64 addition per value.
+// unevaluated sum of two floats, hi + lo with |lo| <= ulp(hi)/2: about 48 significant bits
+// (double-word arithmetic after Dekker, Numer. Math. 18, 1971, with error-free products
+// from fused multiply-adds).  Sum: the exact sum of the high parts (Knuth's two-sum) plus
+// the low parts, renormalised: error below 2u^2 (|x| + |y|), u = 2^-24, an absolute error
+// of the kind an FFT's error bound is made of.  Product: the exact product of the high
+// parts (one fma) plus the cross terms: error below a few u^2 |x y|.  Grids stay doubles
+// in memory; the conversions use integer operations and, on the way out, one float64
+// addition per value.
 #pragma once
 
 #include <stdint.h>
