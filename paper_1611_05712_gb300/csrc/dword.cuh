@@ -52,34 +52,42 @@ __device__ __forceinline__ dw operator*(dw x, dw y) {
 }
 
 // double -> double word: hi = x with its mantissa cut to 24 bits, lo = the remaining 29
-// bits rounded to a float (integer operations and one int -> float conversion); the
-// float64 conversions only for 0 < |x| < 2^-74 or |x| >= 2^128 (outside the float range
-// of hi and lo).
+// bits rounded to nearest (even) to a float, all in integer operations (a conversion
+// instruction would run on the float64 unit).  |x| >= 2^128 gives +-inf, |x| < 2^-126 +-0,
+// and for 2^-126 <= |x| < 2^-74 (where lo would leave the float range) lo = 0.
 __device__ __forceinline__ dw dw_from_double(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
   const int e = (int)((b >> 52) & 0x7ff) - 1023;
-  if ((b << 1) == 0ull) return dw(__uint_as_float(sign), 0.f);
-  if (e < -74 || e > 127) {
-    const float h = (float)x;
-    return dw(h, (float)(x - (double)h));
-  }
+  if (e < -126) return dw(__uint_as_float(sign), 0.f);
+  if (e > 127) return dw(__uint_as_float(sign | 0x7f800000u), 0.f);
   const unsigned long long m = b & 0xfffffffffffffull;
   const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
-  const unsigned r = (unsigned)(m & 0x1fffffffull);   // weight 2^(e - 52) per unit
-  float lo = 0.f;
-  if (r != 0u) lo = __uint_as_float((__float_as_uint(__uint2float_rn(r)) + ((unsigned)(e - 52) << 23)) | sign);
+  unsigned r = (unsigned)(m & 0x1fffffffull);   // weight 2^(e - 52) per unit
+  if (r == 0u || e < -74) return dw(hi, 0.f);
+  int p = 31 - __clz(r);                           // leading bit of r, 0 .. 28
+  if (p > 23) {                                    // round to 24 bits, ties to even
+    const int sh = p - 23;
+    const unsigned rem = r & ((1u << sh) - 1u), half = 1u << (sh - 1);
+    r >>= sh;
+    if (rem > half || (rem == half && (r & 1u))) ++r;
+    if (r == (1u << 24)) { r >>= 1; ++p; }
+  } else {
+    r <<= 23 - p;
+  }
+  const float lo = __uint_as_float(sign | ((unsigned)(p + e - 52 + 127) << 23) | (r & 0x7fffffu));
   return dw(hi, lo);
 }
 
-// float -> double exactly, by the bits (0 and subnormal floats through the conversion).
+// float -> double exactly, by the bits (subnormal floats as 0).
 __device__ __forceinline__ double dw_widen(float f) {
   const unsigned u = __float_as_uint(f);
   const unsigned ef = (u >> 23) & 0xffu;
-  if (ef == 0u || ef == 0xffu) return (double)f;
-  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(ef - 127 + 1023) << 52) |
-                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long d =
+      ef == 0u ? sgn
+               : sgn | ((unsigned long long)(ef == 0xffu ? 0x7ffu : ef - 127 + 1023) << 52) |
+                     ((unsigned long long)(u & 0x7fffffu) << 29);
   return __longlong_as_double((long long)d);
 }
 __device__ __forceinline__ double dw_to_double(dw v) { return dw_widen(v.hi) + dw_widen(v.lo); }
