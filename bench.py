@@ -87,7 +87,8 @@ def parse():
                     help="cycles after which the mixed form's fields and beam quality are "
                          "compared with the FP64 form (0: skip)")
     ap.add_argument("--sort-interval", type=int, default=4,
-                    help="mixed forms: sort particles by cell on every k-th cycle (pic_set_sort_interval)")
+                    help="sort particles by cell on every k-th cycle (pic_set_sort_interval), all forms: "
+                         "the order only serves memory locality; results change by rounding only")
     ap.add_argument("--workload", choices=["wake", "scan", "large", "crop", "guard", "order_sweep", "window",
                                            "fft_lengths"],
                     default="wake",
@@ -117,10 +118,13 @@ def workload(order, rank=0):
     return W.wake_2048x256(order_p=order, seed=2 + rank)
 
 
-def config_of(w, n, precision="fp64"):
-    return {"workload": w.name, "Nz": w.Nz, "Nr": w.Nr, "Nm": w.Nm, "order_p": w.order_p,
-            "particles": n, "dz_m": w.dz, "dt_s": w.dt, "precision": precision,
-            "l2": "no flush: working set (fields + particles, ~0.8 GB) exceeds the 129 MB L2"}
+def config_of(w, n, precision="fp64", sort_interval=None):
+    c = {"workload": w.name, "Nz": w.Nz, "Nr": w.Nr, "Nm": w.Nm, "order_p": w.order_p,
+         "particles": n, "dz_m": w.dz, "dt_s": w.dt, "precision": precision,
+         "l2": "no flush: working set (fields + particles, ~0.8 GB) exceeds the 129 MB L2"}
+    if sort_interval is not None:
+        c["sort_interval"] = sort_interval
+    return c
 
 
 # ------------------------------------------------------------------------- clocks
@@ -246,11 +250,10 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
     mixed = prec != bd.PIC_FP64
     sim = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}", precision=prec)
     wit_lo, wit_hi = beams[-1][0], beams[-1][1]
-    if mixed:   # the sort interval first: the chunk tuning times that many cycles' particle passes
-        sim.set_sort_interval(args.sort_interval)
-    tuning = sim.autotune() if mixed else None   # untimed: tile sizes for this workload
-    if mixed:
-        tuning["sort_interval"] = args.sort_interval
+    # the sort interval first: the chunk tuning times that many cycles' particle passes
+    sim.set_sort_interval(args.sort_interval)
+    tuning = sim.autotune() if mixed else {}   # untimed: tile sizes for this workload
+    tuning["sort_interval"] = args.sort_interval
     sim.step(args.warmup)
     sim.sync()
     torch.cuda.synchronize(dev)
@@ -416,8 +419,7 @@ def accuracy_vs_fp64(w, P, npl, beams, n_cycles, local, sort_interval=1):
     forms = (("fp64", bd.PIC_FP64), ("tf32x3", bd.PIC_MIXED_TF32X3), ("bf16x6", bd.PIC_MIXED_BF16X6))
     sims = {name: bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}", precision=pr) for name, pr in forms}
     for name, s in sims.items():
-        if name != "fp64":
-            s.set_sort_interval(sort_interval)   # as in the timed mixed runs
+        s.set_sort_interval(sort_interval)   # as in the timed runs
 
     def rel(x, y):
         return float(np.abs(y - x).max() / max(np.abs(x).max(), 1e-300))
@@ -486,7 +488,7 @@ def run_ours(args):
         "metric": "pic_steps_per_s", "value": head["steps_per_s"], "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": head["dtype"], "data": "synthetic", "config": config_of(w, n, args.precision),
+        "dtype": head["dtype"], "data": "synthetic", "config": config_of(w, n, args.precision, args.sort_interval),
         "particle_updates_per_s": head["steps_per_s"] * n,
         "stage_ms_per_step": head["stage_ms_per_step"],
         "roofline": head["roofline"], "roofline_dht": head["roofline_dht"],
@@ -671,6 +673,7 @@ def accuracy_large(w, P, npl, beams, n_cycles, local, sort_interval):
         return float(np.abs(y - x).max() / max(np.abs(x).max(), 1e-300))
 
     ref = bd.Sim.from_workload(w, P, npl, beams, device=f"cuda:{local}", precision=bd.PIC_FP64)
+    ref.set_sort_interval(sort_interval)
     t0 = time.perf_counter()
     ref.step(n_cycles)
     ref.sync()
