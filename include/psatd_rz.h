@@ -380,16 +380,22 @@ pic_status pic_autotune(pic_sim* sim, pic_tuning* out);
 pic_status pic_set_tuning(pic_sim* sim, const pic_tuning* tuning);
 pic_status pic_get_tuning(pic_sim* sim, pic_tuning* out);
 
-/* DHT path of the FP64 form (no counterpart in the paper; the paper's Hankel transform is
- * the operation, this chooses how the FP64 product is computed):
+/* Transform arithmetic of the FP64 form (no counterpart in the paper; the paper's Hankel and
+ * Fourier transforms are the operations, this chooses how their float64 results are
+ * computed).  The DHT path:
  *   PIC_DHT_AUTO        sliced tensor-core product when Nr <= 256, else the SIMT GEMM
  *                       (the default);
- *   PIC_DHT_F64_GEMM    FP64 SIMT GEMM on the FP64 units;
+ *   PIC_DHT_F64_GEMM    FP64 SIMT GEMM on the FP64 units, and the z-FFT rows in IEEE float64
+ *                       too (the reference arithmetic for studies of rounding floors);
  *   PIC_DHT_F64_SLICED  every row of the matrix and column of the panel scaled by a power
  *                       of two and cut into seven 7-bit slices (exact BF16 numbers); the
  *                       slice products accumulate exactly in FP32 on the tensor cores and
  *                       are combined in FP64: agrees with the FP64 product to about 2^-49
  *                       of (row max x column max x Nr).  Needs Nr <= 256.
+ * With AUTO and SLICED the power-of-two z-FFT rows run in double words (each value a sum
+ * of two floats, about 48 bits, on the float32 units; rows stay float64 in memory): values
+ * with 2^-74 <= |x| < 2^128 keep that precision, smaller ones fall to float precision and
+ * below 2^-126 to zero, larger ones overflow; SI grids of plasma runs lie well inside.
  * Errors: PIC_ERR_ARG (unknown path, or SLICED with Nr > 256 or a mixed form). */
 typedef enum { PIC_DHT_AUTO = 0, PIC_DHT_F64_GEMM = 1, PIC_DHT_F64_SLICED = 2 } pic_dht_path;
 pic_status pic_set_dht_path(pic_sim* sim, int32_t path);

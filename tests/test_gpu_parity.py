@@ -93,6 +93,41 @@ def test_inverse_transform(Nz, Nr, Nm):
     assert per_slice_err(B, np.stack(O.inverse_vector(g, h, *Bh))) < TOL
 
 
+@pytest.mark.parametrize("scale", [1e-20, 1e25])
+def test_forward_transform_over_the_double_word_range(scale):
+    """The FP64 form's power-of-two z-FFT runs in double words (hi + lo floats): values from
+    2^-74 to 2^128 keep their ~48 bits, so source grids scaled by 1e-20 and 1e25 (SI grids of
+    plasma runs lie between) still meet the FP64 parity bar."""
+    Nz, Nr, Nm = 256, 16, 2
+    s, g = make(Nz, Nr, Nm)
+    h = O.hankel_setup(g)
+    rng = np.random.default_rng(11)
+    dep = crand(rng, (4, Nm, Nr, Nz), scale)
+    s.set("DEP", dep)
+    s.forward_transform()
+    ref = O.forward_sources(g, h, dep[0], dep[1], dep[2], dep[3])
+    assert per_slice_err(s.get("SRC_H"), np.stack(ref)) < TOL
+
+
+def test_ieee_transform_path_matches_the_oracle():
+    """pic_set_dht_path(PIC_DHT_F64_GEMM) keeps the FP64 rows and the DHT in IEEE float64
+    (the reference arithmetic for rounding-floor studies): same transforms, same bar."""
+    Nz, Nr, Nm = 2048, 64, 2
+    s, g = make(Nz, Nr, Nm)
+    s.set_dht_path(bd.PIC_DHT_F64_GEMM)
+    h = O.hankel_setup(g)
+    rng = np.random.default_rng(12)
+    dep = crand(rng, (4, Nm, Nr, Nz))
+    s.set("DEP", dep)
+    s.forward_transform()
+    ref = O.forward_sources(g, h, dep[0], dep[1], dep[2], dep[3])
+    assert per_slice_err(s.get("SRC_H"), np.stack(ref)) < TOL
+    Eh = crand(rng, (3, Nm, Nr, Nz))
+    s.set("EH", Eh)
+    s.inverse_transform()
+    assert per_slice_err(s.get("E"), np.stack(O.inverse_vector(g, h, *Eh))) < TOL
+
+
 # ---------------------------------------------------------------------------- PSATD (a7)
 @pytest.mark.parametrize("Nz,Nr,Nm", [(16, 8, 2), (60, 33, 3), (2048, 256, 2)])
 @pytest.mark.parametrize("p,filt,cfl", [(0, True, 1.0), (16, False, 0.5), (32, True, 3.0)])
