@@ -393,9 +393,11 @@ pic_status pic_get_tuning(pic_sim* sim, pic_tuning* out);
  *                       are combined in FP64: agrees with the FP64 product to about 2^-49
  *                       of (row max x column max x Nr).  Needs Nr <= 256.
  * With AUTO and SLICED the power-of-two z-FFT rows run in double words (each value a sum
- * of two floats, about 48 bits, on the float32 units; rows stay float64 in memory): values
- * with 2^-74 <= |x| < 2^128 keep that precision, smaller ones fall to float precision and
- * below 2^-126 to zero, larger ones overflow; SI grids of plasma runs lie well inside.
+ * of two floats, about 48 bits, on the float32 units; rows stay float64 in memory): the
+ * pairs hold about 48 bits relative to a row's largest value while that lies between
+ * about 2^-100 and 2^127 (the low parts' absolute resolution is 2^-149); values below
+ * 2^-126 enter as zero and values from 2^128 on overflow; SI grids of plasma runs lie
+ * well inside.
  * Errors: PIC_ERR_ARG (unknown path, or SLICED with Nr > 256 or a mixed form). */
 typedef enum { PIC_DHT_AUTO = 0, PIC_DHT_F64_GEMM = 1, PIC_DHT_F64_SLICED = 2 } pic_dht_path;
 pic_status pic_set_dht_path(pic_sim* sim, int32_t path);

@@ -52,9 +52,10 @@ __device__ __forceinline__ dw operator*(dw x, dw y) {
 }
 
 // double -> double word: hi = x with its mantissa cut to 24 bits, lo = the remaining 29
-// bits rounded to nearest (even) to a float, all in integer operations (a conversion
-// instruction would run on the float64 unit).  |x| >= 2^128 gives +-inf, |x| < 2^-126 +-0,
-// and for 2^-126 <= |x| < 2^-74 (where lo would leave the float range) lo = 0.
+// bits rounded to nearest (even) to a float, subnormal where it falls below the normal
+// range, all in integer operations (a conversion instruction would run on the float64
+// unit).  |x| >= 2^128 gives +-inf and |x| < 2^-126 +-0; in between the pair keeps about
+// 48 bits while |x| >= 2^-74 and fewer below, losing at most 2^-150 of absolute value.
 __device__ __forceinline__ dw dw_from_double(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
@@ -63,31 +64,47 @@ __device__ __forceinline__ dw dw_from_double(double x) {
   if (e > 127) return dw(__uint_as_float(sign | 0x7f800000u), 0.f);
   const unsigned long long m = b & 0xfffffffffffffull;
   const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
-  unsigned r = (unsigned)(m & 0x1fffffffull);   // weight 2^(e - 52) per unit
-  if (r == 0u || e < -74) return dw(hi, 0.f);
+  unsigned r = (unsigned)(m & 0x1fffffffull);   // the rest: r 2^(e - 52)
+  if (r == 0u) return dw(hi, 0.f);
   int p = 31 - __clz(r);                           // leading bit of r, 0 .. 28
-  if (p > 23) {                                    // round to 24 bits, ties to even
-    const int sh = p - 23;
+  int sh = p - 23;                                 // right shift to 24 significant bits
+  if (p + e - 52 + 127 < 1) sh = -(e - 52 + 149);  // shift so that one unit is 2^-149
+  unsigned q;
+  if (sh > 0) {                                    // round to nearest, ties to even
+    if (sh >= 32) return dw(hi, 0.f);
     const unsigned rem = r & ((1u << sh) - 1u), half = 1u << (sh - 1);
-    r >>= sh;
-    if (rem > half || (rem == half && (r & 1u))) ++r;
-    if (r == (1u << 24)) { r >>= 1; ++p; }
+    q = r >> sh;
+    if (rem > half || (rem == half && (q & 1u))) ++q;
   } else {
-    r <<= 23 - p;
+    q = r << (-sh);
   }
-  const float lo = __uint_as_float(sign | ((unsigned)(p + e - 52 + 127) << 23) | (r & 0x7fffffu));
-  return dw(hi, lo);
+  unsigned lob;
+  if (p + e - 52 + 127 < 1) {
+    lob = q;                                       // subnormal (a carry into bit 23 is the smallest normal)
+  } else {
+    int pe = p;
+    if (q == (1u << 24)) { q >>= 1; ++pe; }
+    lob = ((unsigned)(pe + e - 52 + 127) << 23) | (q & 0x7fffffu);
+  }
+  return dw(hi, __uint_as_float(sign | lob));
 }
 
-// float -> double exactly, by the bits (subnormal floats as 0).
+// float -> double exactly, by the bits.
 __device__ __forceinline__ double dw_widen(float f) {
   const unsigned u = __float_as_uint(f);
-  const unsigned ef = (u >> 23) & 0xffu;
+  const unsigned ef = (u >> 23) & 0xffu, mf = u & 0x7fffffu;
   const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
-  const unsigned long long d =
-      ef == 0u ? sgn
-               : sgn | ((unsigned long long)(ef == 0xffu ? 0x7ffu : ef - 127 + 1023) << 52) |
-                     ((unsigned long long)(u & 0x7fffffu) << 29);
+  unsigned long long d;
+  if (ef == 0u) {   // 0 or subnormal: mf 2^-149
+    if (mf == 0u) {
+      d = sgn;
+    } else {
+      const int p = 31 - __clz(mf);
+      d = sgn | ((unsigned long long)(1023 - 149 + p) << 52) | (((unsigned long long)mf << (52 - p)) & 0xfffffffffffffull);
+    }
+  } else {
+    d = sgn | ((unsigned long long)(ef == 0xffu ? 0x7ffu : ef - 127 + 1023) << 52) | ((unsigned long long)mf << 29);
+  }
   return __longlong_as_double((long long)d);
 }
 __device__ __forceinline__ double dw_to_double(dw v) { return dw_widen(v.hi) + dw_widen(v.lo); }

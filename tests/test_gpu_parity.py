@@ -93,11 +93,12 @@ def test_inverse_transform(Nz, Nr, Nm):
     assert per_slice_err(B, np.stack(O.inverse_vector(g, h, *Bh))) < TOL
 
 
-@pytest.mark.parametrize("scale", [1e-20, 1e25])
+@pytest.mark.parametrize("scale", [1e-30, 1e-20, 1e25])
 def test_forward_transform_over_the_double_word_range(scale):
-    """The FP64 form's power-of-two z-FFT runs in double words (hi + lo floats): values from
-    2^-74 to 2^128 keep their ~48 bits, so source grids scaled by 1e-20 and 1e25 (SI grids of
-    plasma runs lie between) still meet the FP64 parity bar."""
+    """The FP64 form's power-of-two z-FFT runs in double words (hi + lo floats): rows whose
+    largest value lies between about 2^-100 and 2^127 keep ~48 bits relative to it (the low
+    parts reach down to float subnormals), so source grids scaled by 1e-30, 1e-20 and 1e25
+    (SI grids of plasma runs lie between) still meet the FP64 parity bar."""
     Nz, Nr, Nm = 256, 16, 2
     s, g = make(Nz, Nr, Nm)
     h = O.hankel_setup(g)
