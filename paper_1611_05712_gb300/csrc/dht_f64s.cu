@@ -51,7 +51,7 @@ constexpr int kF64sN = 64;          // matrix rows n per tile
 constexpr int kF64sSets = 1;        // accumulator sets in TMEM (7 groups x kF64sN columns each)
 constexpr int kF64sKC = 32;         // K elements per stage (one 64-byte swizzle row of BF16)
 constexpr int kF64sStages = 2;
-constexpr int kF64sThreads = 256;   // warp 0: copies, warps 1-2: MMA, warps 4..7: epilogue
+constexpr int kF64sThreads = 256;   // warp 0: copies, warps 1-3: MMA, warps 4..7: epilogue
 constexpr uint32_t kF64sPlaneA = kF64sM * 64;   // bytes of one panel plane per stage
 constexpr uint32_t kF64sPlaneB = kF64sN * 64;   // bytes of one matrix plane per stage
 constexpr uint32_t kF64sStageBytes = kSlices * (kF64sPlaneA + kF64sPlaneB);
@@ -237,10 +237,10 @@ __global__ void __launch_bounds__(kF64sThreads, 1) k_dht_f64s(DhtBatch bt, F64sP
   if (tid == 0) {
     for (int i = 0; i < kF64sStages; ++i) {
       mbar_init(&full[i], 1);    // the copy issuer's arrive.expect_tx
-      mbar_init(&empty[i], 2);   // one MMA commit per issuing warp
+      mbar_init(&empty[i], 3);   // one MMA commit per issuing warp
     }
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&tfull[i], 2);   // both issuing warps' commits after a tile's last chunk
+      mbar_init(&tfull[i], 3);   // the issuing warps' commits after a tile's last chunk
       mbar_init(&tempty[i], 4);  // one arrival per epilogue warp
     }
     *abort_flag = 0;
@@ -293,14 +293,14 @@ __global__ void __launch_bounds__(kF64sThreads, 1) k_dht_f64s(DhtBatch bt, F64sP
       }
     }
     __syncwarp();
-  } else if (warp == 1 || warp == 2) {
+  } else if (warp >= 1 && warp <= 3) {
     // ---------------------------------------------------------------- MMA issuers
-    // Two warps issue the products, each into its own accumulator groups (so every group's
-    // first, overwriting product comes from one thread): warp 1 groups 0, 1, 2, 6 (13
-    // products per 16 K), warp 2 groups 3, 4, 5 (15).  One thread issuing all 28 left the
-    // tensor pipe three quarters idle.
+    // Three warps issue the products, each into its own accumulator groups (so every
+    // group's first, overwriting product comes from one thread): warp 1 groups 0, 1, 6 (10
+    // products per 16 K), warp 2 groups 2, 5 (9), warp 3 groups 3, 4 (9).  One thread
+    // issuing all 28 left the tensor pipe three quarters idle.
     if (lane == 0) {
-      const uint32_t gmask = warp == 1 ? 0x47u : 0x38u;   // groups of this warp
+      const uint32_t gmask = warp == 1 ? 0x43u : (warp == 2 ? 0x24u : 0x18u);   // groups of this warp
       uint32_t g = 0, i = 0;
       uint64_t* last_bar = nullptr;
       uint32_t last_parity = 0;
