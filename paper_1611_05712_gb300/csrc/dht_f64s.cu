@@ -51,7 +51,7 @@ constexpr int kF64sN = 64;          // matrix rows n per tile
 constexpr int kF64sSets = 1;        // accumulator sets in TMEM (7 groups x kF64sN columns each)
 constexpr int kF64sKC = 32;         // K elements per stage (one 64-byte swizzle row of BF16)
 constexpr int kF64sStages = 2;
-constexpr int kF64sThreads = 384;   // warp 0: copies, warps 1-3: MMA, warps 4..11: epilogue
+constexpr int kF64sThreads = 640;   // warp 0: copies, warps 1-3: MMA, warps 4..19: epilogue
 constexpr uint32_t kF64sPlaneA = kF64sM * 64;   // bytes of one panel plane per stage
 constexpr uint32_t kF64sPlaneB = kF64sN * 64;   // bytes of one matrix plane per stage
 constexpr uint32_t kF64sStageBytes = kSlices * (kF64sPlaneA + kF64sPlaneB);
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kF64sThreads, 1) k_dht_f64s(DhtBatch bt, F64sP
     }
     for (int i = 0; i < 2; ++i) {
       mbar_init(&tfull[i], 3);   // the issuing warps' commits after a tile's last chunk
-      mbar_init(&tempty[i], 8);  // one arrival per epilogue warp
+      mbar_init(&tempty[i], 16);  // one arrival per epilogue warp
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -342,10 +342,10 @@ __global__ void __launch_bounds__(kF64sThreads, 1) k_dht_f64s(DhtBatch bt, F64sP
     }
     __syncwarp();
   } else if (warp >= 4) {
-    // ---------------------------------------------------------------- epilogue (warps 4-11)
-    // two warps per TMEM lane quarter (warp % 4 == q: lanes 32q .. 32q + 31), each taking
-    // half of the tile's columns
-    const int q = warp & 3, jh = ((warp - 4) >> 2) * (kF64sN / 2);
+    // ---------------------------------------------------------------- epilogue (warps 4-19)
+    // four warps per TMEM lane quarter (warp % 4 == q: lanes 32q .. 32q + 31), each taking
+    // a quarter of the tile's columns
+    const int q = warp & 3, jh = ((warp - 4) >> 2) * (kF64sN / 4);
     uint32_t i = 0;
     for (int t = blockIdx.x; t < P.tiles_total && !*abort_flag; t += gridDim.x, ++i) {
       const uint32_t set = i % kF64sSets;
@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(kF64sThreads, 1) k_dht_f64s(DhtBatch bt, F64sP
       const int c = w.c0 + q * 32 + lane;
       const int Ec = c < P.Nc ? colexp[(size_t)w.b * P.Nc + c] : 0;
       const int32_t* rexp = rowexp + (size_t)P.mat[w.b] * P.Nr;
-      for (int j0 = jh; j0 < jh + kF64sN / 2; j0 += 8) {
+      for (int j0 = jh; j0 < jh + kF64sN / 4; j0 += 8) {
         // the group sums of 8 columns: groups 0..3 exact integers below 2^24 in float,
         // groups 4..6 below 2^25 within one rounding
         uint32_t r[kSlices][8];
