@@ -27,9 +27,9 @@
 // per DHT k_f64s_colmax finds the column maxima and k_f64s_panel slices the panels
 // into K-major planes; k_dht_f64s is a persistent warp-specialised tcgen05 kernel: one
 // thread issues the tensor-memory-access copies of both operands (7 planes each, 64-byte
-// swizzle, 32 K elements per stage) into a ring of stages, one thread issues the 28 slice
-// products per 16 K elements into 7 TMEM accumulators of a 128 x 64 tile, and 4 epilogue
-// warps combine them and store Y.
+// swizzle, 32 K elements per stage) into a ring of stages, three threads (one per warp,
+// each owning whole groups) issue the 28 slice products per 16 K elements into 7 TMEM
+// accumulators of a 128 x 64 tile, and 16 epilogue warps combine them and store Y.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
