@@ -119,10 +119,15 @@ __global__ void k_f64s_colmax(DhtBatch bt, int Nr, int Nc, unsigned long long* _
   if (c >= Nc) return;
   const double* X = static_cast<const double*>(bt.X[b]);
   const int j0 = blockIdx.y * kColRows, j1 = min(Nr, j0 + kColRows);
-  double m = 0.0;
+  // |x| as the bits with the sign cleared (non-negative doubles order like their bits):
+  // integer compares, where fmax would run on the float64 unit
+  unsigned long long m = 0ull;
 #pragma unroll 8
-  for (int j = j0; j < j1; ++j) m = fmax(m, fabs(X[(size_t)j * Nc + c]));
-  if (m > 0.0) atomicMax(colmax + (size_t)b * Nc + c, (unsigned long long)__double_as_longlong(m));
+  for (int j = j0; j < j1; ++j) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(X[(size_t)j * Nc + c]) & 0x7fffffffffffffffull;
+    m = a > m ? a : m;
+  }
+  if (m) atomicMax(colmax + (size_t)b * Nc + c, m);
 }
 
 // Per DHT: the panels into 7 K-major BF16 planes [b * 7 + plane][c][jpad].  Tiles of
