@@ -397,7 +397,11 @@ pic_status pic_get_tuning(pic_sim* sim, pic_tuning* out);
  * pairs hold about 48 bits relative to a row's largest value while that lies between
  * about 2^-100 and 2^127 (the low parts' absolute resolution is 2^-149); values below
  * 2^-126 enter as zero and values from 2^128 on overflow; SI grids of plasma runs lie
- * well inside.
+ * well inside.  With them the inverse rows also leave a double-word copy of PIC_BUF_E and
+ * PIC_BUF_B in the workspace, kept current by every call that writes those buffers, and
+ * pic_gather_push reads that copy and forms the mode sum in double words too (error a few
+ * 2^-48 of the sum of the weighted terms' magnitudes); with F64_GEMM, or an Nz that is not
+ * a power of two, the gather reads the float64 grids.
  * Errors: PIC_ERR_ARG (unknown path, or SLICED with Nr > 256 or a mixed form). */
 typedef enum { PIC_DHT_AUTO = 0, PIC_DHT_F64_GEMM = 1, PIC_DHT_F64_SLICED = 2 } pic_dht_path;
 pic_status pic_set_dht_path(pic_sim* sim, int32_t path);

@@ -197,6 +197,7 @@ template <typename C2, typename G2 = C2> struct RowCtx {
   C2 ca, cb;
   int ka, kb, ua, ub;   // coefficient kinds and units (coef_mul)
   G2* o;          // destination row
+  float4* odw;    // double-word copy of the destination row (double-word rows only; may be null)
   C2* buf;        // padded shared row buffer
   int N, tr, TR;
   bool active;    // false for the idle row slots of the last CTA
@@ -303,6 +304,9 @@ __device__ __forceinline__ void pow2_store(C2 (&v)[E], const RowCtx<C2, G2>& c, 
             y.y = y.y * scale;
           }
           c.o[idx] = to_global(y);
+          if constexpr (std::is_same<C2, dw2>::value) {
+            if (c.odw) c.odw[idx] = make_float4(y.x.hi, y.x.lo, y.y.hi, y.y.lo);
+          }
         }
       } else {
         c.buf[padded<PS>(idx)] = v[q * R + s2];
@@ -346,6 +350,10 @@ __global__ void __launch_bounds__(kFftThreads, fft_min_ctas<R>(E)) k_fft_pow2(co
   c.b = sb >= 0 ? in + ((size_t)sb * rows_per_comp + rr) * N : nullptr;
   row_coefs<R>(rc, comp, c.ca, c.cb, c.ka, c.kb, c.ua, c.ub);
   c.o = out + (size_t)rrow * N;
+  c.odw = nullptr;
+  if constexpr (std::is_same<C2, dw2>::value) {
+    if (rc.out_dw) c.odw = reinterpret_cast<float4*>(rc.out_dw) + (size_t)rrow * N;
+  }
   C2 v[E];
   const int n8 = lgN / 3, rem = lgN - 3 * n8;   // n8 >= 1 radix-8 passes, then radix 2^rem
   pow2_load_global<C2, E>(v, c);
@@ -546,6 +554,10 @@ __global__ void __launch_bounds__(kFftThreads, fft_min_ctas<R>(E)) k_fft_blue(
   c.b = sb >= 0 ? in + ((size_t)sb * rows_per_comp + rr) * N : nullptr;
   row_coefs<R>(rc, comp, c.ca, c.cb, c.ka, c.kb, c.ua, c.ub);
   c.o = out + (size_t)rrow * N;
+  c.odw = nullptr;
+  if constexpr (std::is_same<C2, dw2>::value) {
+    if (rc.out_dw) c.odw = reinterpret_cast<float4*>(rc.out_dw) + (size_t)rrow * N;
+  }
   C2 v[E];
   const int n8 = lgM / 3, rem = lgM - 3 * n8;
   // forward FFT_M of the chirped, zero-padded row; every pass ends in the shared buffer

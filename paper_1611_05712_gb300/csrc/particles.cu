@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "cell_sort.cuh"
+#include "dword.cuh"
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -113,6 +114,92 @@ __device__ __forceinline__ GatherNodes gather_nodes(const GridGeom& g, const Ste
   }
   gn.ghost = st.j0 < 0;
   return gn;
+}
+
+// Gather in double words (FP64 form): the mode sum of the gather above with every product
+// and sum on the float32 units, from the double-word copy of E, B that the inverse row FFT
+// writes ([6][Nm][Nr][Nz] float4: re.hi, re.lo, im.hi, im.lo).  Each component is one dot
+// product of double words, accumulated after Ogita, Rump and Oishi's Dot2 (SIAM J. Sci.
+// Comput. 26, 2005): the products of the high parts enter a float sum through an
+// error-free two-sum, whose errors, with each product's rounding error (one fma) and its
+// cross terms, collect in a second float.  The error stays below a few 2^-48 times the sum
+// of the terms' magnitudes (n u^2 for n <= 4 Nm terms, u = 2^-24, plus the operands' own
+// double-word rounding), against the n 2^-53 of a float64 sum; GB300 runs float64 at 1/64 of
+// its float32 rate, and the float64 unit bounds the particle pass.
+struct Dot2 {
+  float s, c;   // running sum and collected errors: the value is s + c
+};
+
+__device__ __forceinline__ void dot2_add(Dot2& a, dw x, float yh, float yl) {
+  const float p = __fmul_rn(x.hi, yh);
+  const float e = __fmaf_rn(x.hi, yh, -p);   // p + e = x.hi yh exactly
+  const float t = __fadd_rn(a.s, p);         // two-sum: t + err = s + p exactly
+  const float bb = __fsub_rn(t, a.s);
+  const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+  a.s = t;
+  a.c = __fadd_rn(a.c, __fadd_rn(err, __fmaf_rn(x.hi, yl, __fmaf_rn(x.lo, yh, e))));
+}
+
+__device__ __forceinline__ dw dw_twice(dw x) { return dw(__fmul_rn(2.f, x.hi), __fmul_rn(2.f, x.lo)); }
+
+// F_k = Re sum_m mult_m e^{-i m theta} sum_n w_n F_{k,m}(node n) as in k_gather_push, with
+// 2 Re(e^{-i m theta} v) = 2 cos(m theta) Re v + 2 sin(m theta) Im v; the inner nodes (n = 0,
+// 2) take their field's fold sign through sign-flipped copies of their weights.
+__device__ __forceinline__ void gather_dw(const GridGeom& g, const GatherNodes& gn, double c, double s,
+                                          const float4* __restrict__ EB, double (&F)[6]) {
+  const size_t RZ = (size_t)g.Nr * g.Nz;
+  dw w[4];
+#pragma unroll
+  for (int n = 0; n < 4; ++n) w[n] = dw_from_double(gn.w[n]);
+  Dot2 acc[6];
+  {   // mode 0: real part; fold +1 for z components, -1 for r and theta
+    const dw f0 = neg_if(w[0], gn.ghost), f2 = neg_if(w[2], gn.ghost);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {   // real parts only: (re.hi, re.lo) of each float4
+      const float2* base = reinterpret_cast<const float2*>(EB + (size_t)k * g.G);
+      const bool zc = (k % 3) == 2;
+      const float2 v0 = base[2 * gn.off[0]], v1 = base[2 * gn.off[1]], v2 = base[2 * gn.off[2]],
+                   v3 = base[2 * gn.off[3]];
+      acc[k].s = 0.f;
+      acc[k].c = 0.f;
+      dot2_add(acc[k], zc ? w[0] : f0, v0.x, v0.y);
+      dot2_add(acc[k], w[1], v1.x, v1.y);
+      dot2_add(acc[k], zc ? w[2] : f2, v2.x, v2.y);
+      dot2_add(acc[k], w[3], v3.x, v3.y);
+    }
+  }
+  const dw c1 = dw_from_double(c), s1 = dw_from_double(s);
+  dw cm = c1, sm = s1;   // cos(m theta), sin(m theta)
+  for (int m = 1; m < g.Nm; ++m) {
+    const dw c2 = dw_twice(cm), s2 = dw_twice(sm);
+    dw A[4], S[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      A[n] = w[n] * c2;
+      S[n] = w[n] * s2;
+    }
+    // fold signs of the inner nodes: z components (-1)^m, r and theta (-1)^{m+1}
+    const bool negZ = gn.ghost && (m & 1), negV = gn.ghost && !(m & 1);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float4* base = EB + (size_t)k * g.G + (size_t)m * RZ;
+      const bool neg = (k % 3) == 2 ? negZ : negV;
+      const float4 v0 = base[gn.off[0]], v1 = base[gn.off[1]], v2 = base[gn.off[2]], v3 = base[gn.off[3]];
+      dot2_add(acc[k], neg_if(A[0], neg), v0.x, v0.y);
+      dot2_add(acc[k], neg_if(S[0], neg), v0.z, v0.w);
+      dot2_add(acc[k], A[1], v1.x, v1.y);
+      dot2_add(acc[k], S[1], v1.z, v1.w);
+      dot2_add(acc[k], neg_if(A[2], neg), v2.x, v2.y);
+      dot2_add(acc[k], neg_if(S[2], neg), v2.z, v2.w);
+      dot2_add(acc[k], A[3], v3.x, v3.y);
+      dot2_add(acc[k], S[3], v3.z, v3.w);
+    }
+    const dw nc = cm * c1 - sm * s1, ns = sm * c1 + cm * s1;   // times e^{i theta}
+    cm = nc;
+    sm = ns;
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) F[k] = dw_widen(acc[k].s) + dw_widen(acc[k].c);   // one rounding
 }
 
 // ------------------------------------------------------------------ a1: keys and sort
@@ -444,10 +531,12 @@ __device__ __forceinline__ void win_mark(const WinArgs& wa, int32_t id, int64_t 
 }
 
 // WIN: moving window on (removal behind the back edge); the plain instance has none of it.
-template <bool WIN>
+// DWG: gather from the double-word copy of E, B (gather_dw) instead of the float64 grids.
+template <bool WIN, bool DWG>
 __global__ void __launch_bounds__(256, 2) k_gather_push(Parts p, int64_t np, GridGeom g, const double2* __restrict__ E,
-                              const double2* __restrict__ B, double k, double dt, DepArgs dep,
-                              const double* invV, int fuse, int32_t* err, WinArgs wa) {
+                              const double2* __restrict__ B, const float4* __restrict__ EBdw, double k,
+                              double dt, DepArgs dep, const double* invV, int fuse, int32_t* err,
+                              WinArgs wa) {
   const size_t RZ = (size_t)g.Nr * g.Nz;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < np;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -465,6 +554,9 @@ __global__ void __launch_bounds__(256, 2) k_gather_push(Parts p, int64_t np, Gri
     // and the ghost nodes (n = 0, 2) are summed apart so that the fold is one sign flip.
     const GatherNodes gn = gather_nodes(g, st);
     double F[6];   // E_r, E_t, E_z, B_r, B_t, B_z
+    if constexpr (DWG) {
+      gather_dw(g, gn, c, s, EBdw, F);
+    } else {
 #pragma unroll
     for (int k = 0; k < 6; ++k) {   // mode 0: real phase, fold +1 for E_z, B_z and -1 for r, theta
       const double2* base = (k < 3 ? E : B) + (size_t)(k % 3) * g.G;
@@ -491,6 +583,7 @@ __global__ void __launch_bounds__(256, 2) k_gather_push(Parts p, int64_t np, Gri
       }
       const double nr = phr * c + phi * s, ni = phi * c - phr * s;   // times e^{-i theta}
       phr = nr; phi = ni;
+    }
     }
     const double Ex = F[0] * c - F[1] * s, Ey = F[0] * s + F[1] * c, Ez = F[2];
     const double Bx = F[3] * c - F[4] * s, By = F[3] * s + F[4] * c, Bz = F[5];
@@ -2217,14 +2310,24 @@ pic_status launch_gather_push(Sim* s, int32_t fuse_current, const WinArgs& wa, b
       PIC_CUDA(cudaMemcpyAsync(a.rho, s->at<double2>(s->lay.rho_ion), G * sizeof(double2), cudaMemcpyDeviceToDevice,
                                s->stream));
     if (s->np == 0) return PIC_OK;
-    if (wa.on)
-      k_gather_push<true><<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, geom_of(s),
-                                                               s->at<double2>(s->lay.E), s->at<double2>(s->lay.B),
-                                                               kq, c.dt, a, inv_volume(s), fuse_current, err, wa);
+    const double2* E = s->at<double2>(s->lay.E);
+    const double2* B = s->at<double2>(s->lay.B);
+    const float4* ebdw = eb_dw_active(s) ? s->at<float4>(s->lay.ebdw) : nullptr;
+    const Parts p = parts_of(s, s->cur);
+    const GridGeom g = geom_of(s);
+    const int grid = pgrid(s->np);
+    if (wa.on && ebdw)
+      k_gather_push<true, true><<<grid, 256, 0, s->stream>>>(p, s->np, g, E, B, ebdw, kq, c.dt, a, inv_volume(s),
+                                                             fuse_current, err, wa);
+    else if (wa.on)
+      k_gather_push<true, false><<<grid, 256, 0, s->stream>>>(p, s->np, g, E, B, ebdw, kq, c.dt, a, inv_volume(s),
+                                                              fuse_current, err, wa);
+    else if (ebdw)
+      k_gather_push<false, true><<<grid, 256, 0, s->stream>>>(p, s->np, g, E, B, ebdw, kq, c.dt, a, inv_volume(s),
+                                                              fuse_current, err, wa);
     else
-      k_gather_push<false><<<pgrid(s->np), 256, 0, s->stream>>>(parts_of(s, s->cur), s->np, geom_of(s),
-                                                                s->at<double2>(s->lay.E), s->at<double2>(s->lay.B),
-                                                                kq, c.dt, a, inv_volume(s), fuse_current, err, wa);
+      k_gather_push<false, false><<<grid, 256, 0, s->stream>>>(p, s->np, g, E, B, ebdw, kq, c.dt, a,
+                                                               inv_volume(s), fuse_current, err, wa);
   }
   PIC_LAUNCHED(s);
   return PIC_OK;

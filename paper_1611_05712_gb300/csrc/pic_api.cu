@@ -109,6 +109,7 @@ Layout make_layout(const pic_config& c) {
   L.coef = take(6 * G * 8);
   L.twp = take((size_t)c.Nz * 16);
   if (c.precision == PIC_FP64) L.twp_dw = take((size_t)c.Nz * 16);
+  if (c.precision == PIC_FP64 && fft_is_pow2(c.Nz)) L.ebdw = take(6 * G * 16);
   const int M = bluestein_length(c.Nz, c.precision);
   if (M > 0) {
     L.twm = take((size_t)M * 16);
@@ -294,6 +295,7 @@ pic_status fft_inverse(Sim* s) {
     rc.srcA[o + 1] = o; rc.caIm[o + 1] = 1.0; rc.srcB[o + 1] = o + 1; rc.cbIm[o + 1] = -1.0;
     rc.srcA[o + 2] = o + 2; rc.caRe[o + 2] = 1.0; rc.srcB[o + 2] = -1;
   }
+  rc.out_dw = eb_dw_active(s) ? s->at<char>(s->lay.ebdw) : nullptr;
   return launch_fft_rows(s, s->at<char>(s->lay.tmp), s->at<char>(s->lay.E), rc, true);
 }
 
@@ -481,6 +483,8 @@ pic_status pic_init(const pic_config* cfg, void* workspace, size_t workspace_byt
   cudaError_t ce;
   if ((ce = cudaMemsetAsync(s->ws + L.E, 0, 6 * G * cb, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
   if ((ce = cudaMemsetAsync(s->ws + L.Eh, 0, 6 * G * cb, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
+  if (L.ebdw && (ce = cudaMemsetAsync(s->ws + L.ebdw, 0, 6 * G * 16, s->stream)) != cudaSuccess)
+    return fail(cuda_status(ce, "memset"));
   if ((ce = cudaMemsetAsync(s->ws + L.rho_prev_h, 0, G * cb, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
   if ((ce = cudaMemsetAsync(s->ws + L.rho_ion, 0, G * cb, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
   if ((ce = cudaMemsetAsync(s->ws + L.dep, 0, 4 * G * cb, s->stream)) != cudaSuccess) return fail(cuda_status(ce, "memset"));
@@ -590,7 +594,9 @@ pic_status pic_set_dht_path(pic_sim* sim, int32_t path) {
     set_error("the sliced FP64 DHT needs the FP64 form and Nr <= %d", kF64sMaxNr);
     return PIC_ERR_ARG;
   }
+  const bool was_dw = eb_dw_active(s);
   s->dht_path = path;
+  if (eb_dw_active(s) && !was_dw) return refresh_eb_dw(s);   // E, B came from IEEE rows meanwhile
   return PIC_OK;
 }
 
@@ -644,8 +650,10 @@ pic_status pic_copy_window(pic_sim* src_sim, int32_t buffer_id, int32_t src_z0, 
   BufView va, vb;
   buffer_view(a, buffer_id, &va);
   buffer_view(b, buffer_id, &vb);
-  return launch_copy_window(b, a->ws + va.off, a->cfg.Nz, src_z0, b->ws + vb.off, b->cfg.Nz, dst_z0, nz,
-                            ncomp * a->cfg.Nm * a->cfg.Nr);
+  pic_status st = launch_copy_window(b, a->ws + va.off, a->cfg.Nz, src_z0, b->ws + vb.off, b->cfg.Nz, dst_z0, nz,
+                                     ncomp * a->cfg.Nm * a->cfg.Nr);
+  if (st == PIC_OK && ncomp == 3 && eb_dw_active(b)) st = refresh_eb_dw(b);
+  return st;
 }
 
 pic_status pic_destroy(pic_sim* sim) {
@@ -1022,7 +1030,10 @@ pic_status pic_load_buffer(pic_sim* sim, int32_t buffer_id, const void* src, siz
   PIC_CUDA(cudaMemcpyAsync(s->ws + v.off, src, bytes,
                            src_on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s->stream));
   if (src_on_host) PIC_CUDA(cudaStreamSynchronize(s->stream));
-  if (buffer_id == PIC_BUF_E || buffer_id == PIC_BUF_B) s->fields_ready = 1;
+  if (buffer_id == PIC_BUF_E || buffer_id == PIC_BUF_B) {
+    s->fields_ready = 1;
+    if (eb_dw_active(s)) return refresh_eb_dw(s);
+  }
   return PIC_OK;
 }
 

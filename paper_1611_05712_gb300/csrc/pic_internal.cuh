@@ -37,6 +37,10 @@ struct Layout {
   size_t kzmod, tz, tr, coef;                                    // PSATD tables
   size_t twp;        // per-pass twiddle tables of the row FFT (radix-8 or mixed-radix plan)
   size_t twp_dw;     // the same as double words (hi, lo float pairs), FP64 form
+  // FP64 form with power-of-two Nz (0 otherwise): E, B as double words, [6][Nm][Nr][Nz]
+  // float4 (re.hi, re.lo, im.hi, im.lo), written beside E, B by the inverse row FFT and read
+  // by the gather
+  size_t ebdw;
   size_t part[2][7], pid[2];                                     // particles (double buffer)
   size_t keys, perm, perm_tmp, count, start, scan_blk, big_list, big_count;
   size_t diag_acc, err;
@@ -179,8 +183,14 @@ struct RowCombine {
   // float copies for the float rows (no float64 conversions in those kernels)
   int8_t kindA[6], kindB[6], unitA[6], unitB[6];
   float fcaRe[6], fcaIm[6], fcbRe[6], fcbIm[6];
+  // optional second destination of the double-word rows (power-of-two FP64 rows): the
+  // outputs as float4 (re.hi, re.lo, im.hi, im.lo) in the layout of `out`; null for none
+  void* out_dw;
 };
 pic_status launch_fft_rows(Sim* s, const void* in, void* out, const RowCombine& rc, bool inverse);
+// The double-word copy of E, B is kept (FP64 form, power-of-two rows in double words).
+bool eb_dw_active(const Sim* s);
+pic_status refresh_eb_dw(Sim* s);       // rebuild it from E, B after a write of those
 pic_status fft_configure_device();      // once per device, before any FFT launch
 bool fft_is_pow2(int N);                // rows of power-of-two length use the radix-8 kernel
 

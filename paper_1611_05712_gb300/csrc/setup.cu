@@ -657,4 +657,15 @@ pic_status launch_setup_twiddles(Sim* s) {
   return PIC_OK;
 }
 
+bool eb_dw_active(const Sim* s) {
+  return s->lay.ebdw != 0 && s->blue_M == 0 && s->dht_path != PIC_DHT_F64_GEMM;
+}
+
+pic_status refresh_eb_dw(Sim* s) {
+  const size_t n = 12 * s->grid_elems();   // 6 complex planes of float64
+  k_to_double_word<<<conv_grid(n), 256, 0, s->stream>>>(s->at<double>(s->lay.E), s->at<float2>(s->lay.ebdw), n);
+  PIC_LAUNCHED(s);
+  return PIC_OK;
+}
+
 }  // namespace pic

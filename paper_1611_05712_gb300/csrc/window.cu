@@ -22,9 +22,12 @@ namespace {
 
 constexpr int kWinThreads = 256;
 
-// colv[(f*3 + c)*Nm + m][j], f = E, B; c = +, -, z.  Grid: 2*Nm*Nr threads.
+// colv[(f*3 + c)*Nm + m][j], f = E, B; c = +, -, z.  Grid: 2*Nm*Nr threads.  EBdw, when
+// given, is the double-word copy of E, B (same layout, float4 elements): its column is
+// zeroed as well.
 template <typename T2>
-__global__ void k_win_col_take(T2* EB, size_t G, int Nm, int Nr, int Nz, int column, double2* colv) {
+__global__ void k_win_col_take(T2* EB, size_t G, int Nm, int Nr, int Nz, int column, double2* colv,
+                               float4* EBdw) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * Nm * Nr) return;
   const int f = t / (Nm * Nr), mj = t - f * Nm * Nr;
@@ -41,6 +44,13 @@ __global__ void k_win_col_take(T2* EB, size_t G, int Nm, int Nr, int Nz, int col
   base[0] = zero;
   base[G] = zero;
   base[2 * G] = zero;
+  if (EBdw) {
+    float4* bdw = EBdw + (size_t)f * 3 * G + (size_t)mj * Nz + column;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    bdw[0] = z4;
+    bdw[G] = z4;
+    bdw[2 * G] = z4;
+  }
 }
 
 // hv[row][n] = sum_j M[m][slot][n][j] colv[row][j] with row = (f*3 + c)*Nm + m; the
@@ -141,10 +151,11 @@ pic_status launch_window_clear(Sim* s, int column) {
   const int n_take = 2 * c.Nm * c.Nr;
   if (c.precision == PIC_FP64)
     k_win_col_take<double2><<<(n_take + kWinThreads - 1) / kWinThreads, kWinThreads, 0, s->stream>>>(
-        s->at<double2>(s->lay.E), G, c.Nm, c.Nr, c.Nz, column, colv);
+        s->at<double2>(s->lay.E), G, c.Nm, c.Nr, c.Nz, column, colv,
+        eb_dw_active(s) ? s->at<float4>(s->lay.ebdw) : nullptr);
   else
     k_win_col_take<float2><<<(n_take + kWinThreads - 1) / kWinThreads, kWinThreads, 0, s->stream>>>(
-        s->at<float2>(s->lay.E), G, c.Nm, c.Nr, c.Nz, column, colv);
+        s->at<float2>(s->lay.E), G, c.Nm, c.Nr, c.Nz, column, colv, nullptr);
   PIC_LAUNCHED(s);
   const int n_out = 6 * c.Nm * c.Nr;
   const int hb = (n_out * 32 + kWinThreads - 1) / kWinThreads;

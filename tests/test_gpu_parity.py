@@ -232,6 +232,46 @@ def test_gather_push(Nz, Nr, Nm, n):
     assert per_slice_err(s.get("DEP")[1:], np.stack(J)) < TOL
 
 
+@pytest.mark.parametrize("Nz,Nr,Nm,n", [(64, 33, 2, 6000), (256, 64, 3, 36384)])
+def test_gather_push_from_rest(Nz, Nr, Nm, n):
+    """Particles at rest: the momentum after one push is the gathered field itself (2 k E to
+    first order), so the gather's arithmetic is measured at full scale, not against the
+    momentum a particle already has.  A third of the particles sit in the axis cell (ghost
+    node fold).  The FP64 form gathers from the double-word copy of E, B (products and sums
+    on the float32 units, error a few 2^-48 of the summed terms); the IEEE path
+    (PIC_DHT_F64_GEMM) gathers from the float64 grids: both against the oracle, and against
+    each other."""
+    rng = np.random.default_rng(29)
+    g = O.Grid(Nz, Nr, Nm, DZ, DZ, DZ / O.C_LIGHT)
+    P = _particles(g, n, rng)
+    k0 = n // 3
+    r = g.dr * rng.uniform(0, 1, k0)
+    th = rng.uniform(0, 2 * np.pi, k0)
+    P["x"][10:10 + k0] = r * np.cos(th)
+    P["y"][10:10 + k0] = r * np.sin(th)
+    for k in ("ux", "uy", "uz"):
+        P[k][:] = 0.0
+    E = crand(rng, (3, Nm, Nr, Nz), 1e12)
+    B = crand(rng, (3, Nm, Nr, Nz), 1e12 / O.C_LIGHT)
+    zero = np.zeros((Nm, Nr, Nz), complex)
+    st = O.State(g, 0, False, -O.Q_E, O.M_E, None, None, None, tuple(E), tuple(B), None, None,
+                 zero, zero, {k: v.copy() for k, v in P.items()})
+    O.gather_push(st)
+    got = {}
+    for path in (bd.PIC_DHT_AUTO, bd.PIC_DHT_F64_GEMM):
+        s, _ = make(Nz, Nr, Nm, cap=n)
+        s.set_dht_path(path)
+        s.write_particles(P)
+        s.set("E", E)
+        s.set("B", B)
+        s.gather_push(fuse_current=True)
+        got[path] = s.read_particles()
+        for k in ("ux", "uy", "uz", "x", "y", "z"):
+            assert rel_err(got[path][k], st.p[k]) < TOL, (path, k)
+    for k in ("ux", "uy", "uz"):
+        assert rel_err(got[bd.PIC_DHT_AUTO][k], got[bd.PIC_DHT_F64_GEMM][k]) < 1e-13, k
+
+
 # ---------------------------------------------------------------------------- full cycle
 def _compare_state(s, st, tol):
     """Physical states are compared per field (all components and modes share one scale):
