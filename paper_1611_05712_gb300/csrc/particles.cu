@@ -39,25 +39,28 @@ struct GridGeom {
   int Nz, Nr, Nm;
   double dz, dr, L, R;
   size_t G;      // Nm*Nr*Nz
-  double inv_dr; // 1/dr (float64 divisions are long sequences on GB300's float64 unit)
+  double inv_dr; // 1/dr, 1/dz correctly rounded (float64 divisions are long sequences on
+  double inv_dz; // GB300's float64 unit)
 };
 
 GridGeom geom_of(const Sim* s) {
   const pic_config& c = s->cfg;
-  GridGeom g{c.Nz, c.Nr, c.Nm, c.dz, c.dr, c.Nz * c.dz, c.Nr * c.dr, s->grid_elems(), 1.0 / c.dr};
+  GridGeom g{c.Nz, c.Nr, c.Nm, c.dz, c.dr, c.Nz * c.dz, c.Nr * c.dr, s->grid_elems(), 1.0 / c.dr, 1.0 / c.dz};
   return g;
 }
 
 constexpr double kInvC2 = 1.0 / (kC * kC);   // gamma from u without a float64 division
 
-// r, cos(theta), sin(theta) of (x, y); one division (cos and sin from 1/r).
+// r, cos(theta), sin(theta) of (x, y) from one reciprocal square root (CUDA's rsqrt, within
+// one ulp): with q = x^2 + y^2, r = q rsqrt(q) and (cos, sin) = (x, y) rsqrt(q), within about
+// two ulps, without a square root and a division.  The axis (q = 0) takes theta = 0.
 __device__ __forceinline__ void polar(double x, double y, double& r, double& c, double& s) {
-  r = sqrt(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
-  if (r > 0.0) {
-    const double ir = 1.0 / r;
-    c = x * ir; s = y * ir;
+  const double r2 = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
+  if (r2 > 0.0) {
+    const double ir = rsqrt(r2);
+    r = r2 * ir; c = x * ir; s = y * ir;
   } else {
-    c = 1.0; s = 0.0;
+    r = 0.0; c = 1.0; s = 0.0;
   }
 }
 
@@ -68,7 +71,13 @@ struct Stencil {
 
 __device__ __forceinline__ Stencil stencil(const GridGeom& g, double z, double r) {
   Stencil st;
-  double u = z / g.dz;
+  // u = z / dz correctly rounded without a division: q = z (1/dz), then twice q <- q + (z -
+  // q dz) (1/dz), the remainder exact in one fma; the first correction makes q a faithful
+  // quotient and the second returns the correctly rounded one (Markstein, IBM J. Res. Dev.
+  // 34, 1990), 1/dz being the correctly rounded reciprocal from the host.
+  double u = __dmul_rn(z, g.inv_dz);
+  u = __fma_rn(__fma_rn(-u, g.dz, z), g.inv_dz, u);
+  u = __fma_rn(__fma_rn(-u, g.dz, z), g.inv_dz, u);
   double fi = floor(u);
   double sz = u - fi;
   long long i0 = (long long)fi;
@@ -80,8 +89,8 @@ __device__ __forceinline__ Stencil stencil(const GridGeom& g, double z, double r
   st.i1 = st.i0 + 1 == g.Nz ? 0 : st.i0 + 1;
   st.wz0 = 1.0 - sz;
   st.wz1 = sz;
-  // z / dz stays a correctly rounded division (one ulp of it is ~Nz ulps of a weight);
-  // r / dr (r < R) as a product with 1/dr
+  // z / dz stays correctly rounded (one ulp of it is ~Nz ulps of a weight); r / dr (r < R)
+  // as a product with 1/dr
   double v = r * g.inv_dr - 0.5;
   double fj = floor(v);
   double t = v - fj;
@@ -443,11 +452,10 @@ __device__ __forceinline__ void dep2(double2* p, double re, double im) {
 // Each node's weight / V_j and address are formed once; lanes visit the 4 nodes in an
 // order rotated by the lane index, so that lanes of one cell (same nodes) add to different
 // nodes in one instruction.
-__device__ void deposit_one(const GridGeom& g, const DepArgs& a, const double* invV, double x,
-                            double y, double z, double w, double vx, double vy, double vz,
-                            bool do_rho, bool do_J) {
-  double r, c, s;
-  polar(x, y, r, c, s);
+// deposit_at takes the particle's radius and azimuth (r, cos, sin) already formed.
+__device__ void deposit_at(const GridGeom& g, const DepArgs& a, const double* invV, double r,
+                           double c, double s, double z, double w, double vx, double vy, double vz,
+                           bool do_rho, bool do_J) {
   const Stencil st = stencil(g, z, r);
   const size_t RZ = (size_t)g.Nr * g.Nz;
   const int rot = threadIdx.x & 3;
@@ -492,6 +500,14 @@ __device__ void deposit_one(const GridGeom& g, const DepArgs& a, const double* i
     const double nr = phr * c - phi * s, ni = phr * s + phi * c;
     phr = nr; phi = ni;
   }
+}
+
+__device__ __forceinline__ void deposit_one(const GridGeom& g, const DepArgs& a, const double* invV,
+                                            double x, double y, double z, double w, double vx,
+                                            double vy, double vz, bool do_rho, bool do_J) {
+  double r, c, s;
+  polar(x, y, r, c, s);
+  deposit_at(g, a, invV, r, c, s, z, w, vx, vy, vz, do_rho, do_J);
 }
 
 __global__ void k_deposit(const Parts p, int64_t np, GridGeom g, DepArgs a, const double* invV,
@@ -614,20 +630,21 @@ __global__ void __launch_bounds__(256, 2) k_gather_push(Parts p, int64_t np, Gri
     z = __dadd_rn(z, __dmul_rn(hdt, vz));
     if (z >= g.L) z -= g.L;
     if (z < 0.0) z += g.L;
-    const double r1 = sqrt(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
-    if (r1 >= g.R) {
-      const double ir1 = 1.0 / r1;
-      const double cx = x * ir1, cy = y * ir1;
-      const double fr = (2.0 * g.R - r1) * ir1;
-      const double ur = ux * cx + uy * cy;
-      ux = ux - 2.0 * ur * cx;
-      uy = uy - 2.0 * ur * cy;
+    // one polar decomposition at x^{n+1} serves the wall and the rho deposit
+    double r1, c1, s1;
+    polar(x, y, r1, c1, s1);
+    if (r1 >= g.R) {   // specular reflection (rare: the particle crossed the wall)
+      const double fr = (2.0 * g.R - r1) / r1;
+      const double ur = ux * c1 + uy * s1;
+      ux = ux - 2.0 * ur * c1;
+      uy = uy - 2.0 * ur * s1;
       x *= fr;
       y *= fr;
+      polar(x, y, r1, c1, s1);
     }
     // rho^{n+1} at x^{n+1} (without the moving window; with it the deposit stage runs after
     // the injection)
-    if (!WIN && dep.rho) deposit_one(g, dep, invV, x, y, z, w, 0.0, 0.0, 0.0, true, false);
+    if (!WIN && dep.rho) deposit_at(g, dep, invV, r1, c1, s1, z, w, 0.0, 0.0, 0.0, true, false);
     if (WIN) {
       // window coordinate after the step: ((z^n - back) mod L) + 2 half moves - s dz
       double zo = z_old - wa.back_z;
