@@ -359,11 +359,13 @@ def measure(args, w, P, npl, beams, prec, dist, dev, world, local):
             "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
             "algorithmic_flops": flops, "flops_per_particle": fp64_particle_flops(w.Nm),
-            "kernel": "k_gather_push<false> (gather, Boris push, J at x^{n+1/2}, rho at x^{n+1}; FP64)",
+            "kernel": "k_gather_push<false, true> (gather in double words, Boris push, J at x^{n+1/2}, "
+                      "rho at x^{n+1}; FP64)",
             "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (recipe nominal 1.25 TFLOP/s)",
             "share_of_step": stage_ms["gather_push"] / sum(stage_ms.values()),
-            "note": "divides and square roots count once but run as FP64 instruction sequences; the FP64 "
-                    "pipe is the binding unit (profiles/k_gather_push__wake_2048x256_m2_fp64.md)"}
+            "note": "operations counted in float64 as the algorithm states them; the kernel runs the gather's "
+                    "interpolation and mode sum in double words on the FP32 units and the rest on the FP64 "
+                    "pipe, the binding unit (profiles/k_gather_push__wake_2048x256_m2_fp64.md)"}
     if mixed:
         # the particle kernel (gather, push, J and rho deposits) against the survey's
         # algorithmic bytes: 56 B per particle (FP32 cell-relative state read and written,
