@@ -206,6 +206,40 @@ def oracle_steps_per_s(w, P, npl, beams, n_steps):
     return n_steps / dt, dt
 
 
+def oracle_crop_baseline(args):
+    """The oracle beside the large run: one cycle of its 1024 x 128 x 3 crop (a full cycle
+    of the 8192 x 1024 x 3 grid with 102.7M particles does not fit a bounded host sample)."""
+    from paper_1611_05712_gb300 import workloads as W
+    wc = W.large_crop_1024x128(order_p=args.order)
+    Pc, nplc, beamsc = W.particles(wc)
+    v, secs = oracle_steps_per_s(wc, Pc, nplc, beamsc, 1)
+    return {"value": v, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "particle_updates_per_s": v * len(Pc["x"]),
+            "sample": f"1 full cycle of the 1024x128x3 crop of this workload ({len(Pc['x'])} particles, "
+                      f"{secs:.1f} s; numpy FP64 oracle): cycles/s of the crop, not scaled to the full grid"}
+
+
+def oracle_scan_baseline(n_sample=4):
+    """The oracle beside the scan: one cycle of each of n_sample members taken evenly through
+    the 64 members ordered by cell count; value = the sample's member-cycles per second."""
+    from paper_1611_05712_gb300 import workloads as W
+    members = [W.scan_member(s) for s in range(64)]
+    order = sorted(range(64), key=lambda i: members[i].Nz * members[i].Nr)
+    step = len(order) // n_sample
+    pick = [order[step // 2 + k * step] for k in range(n_sample)]
+    total = 0.0
+    names = []
+    for i in pick:
+        m = members[i]
+        Pm, nplm, beamsm = W.particles(m)
+        _, secs = oracle_steps_per_s(m, Pm, nplm, beamsm, 1)
+        total += secs
+        names.append(f"{m.Nz}x{m.Nr}x{m.Nm}")
+    return {"value": n_sample / total, "unit": "sim-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"1 cycle each of {n_sample} members spread evenly over the cell-count order "
+                      f"({', '.join(names)}; {total:.1f} s; numpy FP64 oracle)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -554,6 +588,10 @@ def run_ours(args):
                                 "kind": "oracle",
                                 "sample": f"1 full cycle of the same workload ({secs:.1f} s; numpy FP64 "
                                           "oracle, BLAS threads = host cores)"}
+        if "large" in line:
+            line["large"]["cpu_baseline"] = oracle_crop_baseline(args)
+        if "scan" in line:
+            line["scan"]["cpu_baseline"] = oracle_scan_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -9,6 +9,12 @@
 // grad X = (-K_perp X/2, K_perp X/2, i K_z X),
 // curl V = (K_z V+ - i K_perp Vz/2, -K_z V- - i K_perp Vz/2, i K_perp (V+ + V-)),
 // div V = K_perp (V+ - V-) + i K_z Vz.
+// The float64 update never forms the corrected current J + grad G: in E' it enters as
+// -(S/K)/(eps0 c) J - grad Y with Y = (S/K)/(eps0 c) G - (a_n rho^{n+1} + a_p rho^n)/eps0,
+// and in B' only through its curl, which is curl J (curl grad = 0 for these operators: K_z
+// (-K_perp G/2) - i (K_perp/2) (i K_z G) = 0, and so on), so B' = C B + curl W with W = mu0
+// (1-C)/K^2 J - (S/K)/c E, one curl instead of two: fewer float64 operations, which bound the
+// FP64 form's update.  The float update (bound by memory) keeps the steps written out.
 // One thread per spectral cell; every grid is read once and written once.  R = double in
 // the FP64 form, float (with float coefficient tables) in the mixed form.
 #include "pic_internal.cuh"
@@ -72,41 +78,76 @@ __global__ void __launch_bounds__(256) k_psatd(typename V2<R>::T* __restrict__ E
     const R C = coef[idx], SK = coef[G + idx], omc = coef[2 * G + idx];
     const R an = coef[3 * G + idx], ap = coef[4 * G + idx], iK2 = coef[5 * G + idx];
     const R h = (R)0.5;
-    // current correction
-    const Z<R> divJ = zadd(zscale(Kp, zsub(Jp, Jm)), zi(Kz, Jz));
-    const Z<R> Gc = zscale(iK2, zadd(zscale(idt, zsub(rn, rp)), divJ));
-    Jp = zadd(Jp, zscale(-h * Kp, Gc));
-    Jm = zadd(Jm, zscale(h * Kp, Gc));
-    Jz = zadd(Jz, zi(Kz, Gc));
-    Z<R> Ep = zld<R>(Eh, idx), Em = zld<R>(Eh, G + idx), Ez = zld<R>(Eh, 2 * G + idx);
-    Z<R> Bp = zld<R>(Bh, idx), Bm = zld<R>(Bh, G + idx), Bz = zld<R>(Bh, 2 * G + idx);
-    if (PEND) {   // pending removal of the moving window's departed column: F^ -= h[row] p[k]
-      const typename V2<R>::T p = colph[kz];
-      const size_t MN = G / Nz;
-      col_sub(Ep, colh[mn], p); col_sub(Em, colh[MN + mn], p); col_sub(Ez, colh[2 * MN + mn], p);
-      col_sub(Bp, colh[3 * MN + mn], p); col_sub(Bm, colh[4 * MN + mn], p); col_sub(Bz, colh[5 * MN + mn], p);
+    if constexpr (sizeof(R) == 8) {   // float64: the folded update (fewer float64 operations)
+      // current correction: G only (the corrected current is never formed, see below)
+      const Z<R> divJ = zadd(zscale(Kp, zsub(Jp, Jm)), zi(Kz, Jz));
+      const Z<R> Gc = zscale(iK2, zadd(zscale(idt, zsub(rn, rp)), divJ));
+      Z<R> Ep = zld<R>(Eh, idx), Em = zld<R>(Eh, G + idx), Ez = zld<R>(Eh, 2 * G + idx);
+      Z<R> Bp = zld<R>(Bh, idx), Bm = zld<R>(Bh, G + idx), Bz = zld<R>(Bh, 2 * G + idx);
+      if (PEND) {   // pending removal of the moving window's departed column: F^ -= h[row] p[k]
+        const typename V2<R>::T p = colph[kz];
+        const size_t MN = G / Nz;
+        col_sub(Ep, colh[mn], p); col_sub(Em, colh[MN + mn], p); col_sub(Ez, colh[2 * MN + mn], p);
+        col_sub(Bp, colh[3 * MN + mn], p); col_sub(Bm, colh[4 * MN + mn], p); col_sub(Bz, colh[5 * MN + mn], p);
+      }
+      const R hK = h * Kp;
+      const Z<R> cBp = zsub(zscale(Kz, Bp), zi(hK, Bz));
+      const Z<R> cBm = zsub(zscale(-Kz, Bm), zi(hK, Bz));
+      const Z<R> cBz = zi(Kp, zadd(Bp, Bm));
+      const Z<R> X = zscale(ieps0, zadd(zscale(an, rn), zscale(ap, rp)));
+      const R cSK = kc * SK, jS = SK * jS_f, bS = SK * bS_f, jB = mu0 * omc;
+      // E' = C E + c (S/K) curl B - (S/K)/(eps0 c) J - grad Y,  Y = (S/K)/(eps0 c) G - X
+      const Z<R> Y = zsub(zscale(jS, Gc), X);
+      const Z<R> nEp = zadd(zadd(zscale(C, Ep), zscale(cSK, cBp)), zadd(zscale(-jS, Jp), zscale(hK, Y)));
+      const Z<R> nEm = zadd(zadd(zscale(C, Em), zscale(cSK, cBm)), zsub(zscale(-jS, Jm), zscale(hK, Y)));
+      const Z<R> nEz = zadd(zadd(zscale(C, Ez), zscale(cSK, cBz)), zsub(zscale(-jS, Jz), zi(Kz, Y)));
+      // B' = C B + curl W,  W = mu0 (1-C)/K^2 J - (S/K)/c E  (old E; curl grad G = 0)
+      const Z<R> Wp = zsub(zscale(jB, Jp), zscale(bS, Ep));
+      const Z<R> Wm = zsub(zscale(jB, Jm), zscale(bS, Em));
+      const Z<R> Wz = zsub(zscale(jB, Jz), zscale(bS, Ez));
+      const Z<R> nBp = zadd(zscale(C, Bp), zsub(zscale(Kz, Wp), zi(hK, Wz)));
+      const Z<R> nBm = zadd(zscale(C, Bm), zsub(zscale(-Kz, Wm), zi(hK, Wz)));
+      const Z<R> nBz = zadd(zscale(C, Bz), zi(Kp, zadd(Wp, Wm)));
+      zst<R>(Eh, idx, nEp); zst<R>(Eh, G + idx, nEm); zst<R>(Eh, 2 * G + idx, nEz);
+      zst<R>(Bh, idx, nBp); zst<R>(Bh, G + idx, nBm); zst<R>(Bh, 2 * G + idx, nBz);
+      zst<R>(rho_prev, idx, rn);
+    } else {   // float: written out (the folded form ran 7 % slower in this memory-bound kernel)
+      // current correction
+      const Z<R> divJ = zadd(zscale(Kp, zsub(Jp, Jm)), zi(Kz, Jz));
+      const Z<R> Gc = zscale(iK2, zadd(zscale(idt, zsub(rn, rp)), divJ));
+      Jp = zadd(Jp, zscale(-h * Kp, Gc));
+      Jm = zadd(Jm, zscale(h * Kp, Gc));
+      Jz = zadd(Jz, zi(Kz, Gc));
+      Z<R> Ep = zld<R>(Eh, idx), Em = zld<R>(Eh, G + idx), Ez = zld<R>(Eh, 2 * G + idx);
+      Z<R> Bp = zld<R>(Bh, idx), Bm = zld<R>(Bh, G + idx), Bz = zld<R>(Bh, 2 * G + idx);
+      if (PEND) {   // pending removal of the moving window's departed column: F^ -= h[row] p[k]
+        const typename V2<R>::T p = colph[kz];
+        const size_t MN = G / Nz;
+        col_sub(Ep, colh[mn], p); col_sub(Em, colh[MN + mn], p); col_sub(Ez, colh[2 * MN + mn], p);
+        col_sub(Bp, colh[3 * MN + mn], p); col_sub(Bm, colh[4 * MN + mn], p); col_sub(Bz, colh[5 * MN + mn], p);
+      }
+      // curls
+      const Z<R> cBp = zsub(zscale(Kz, Bp), zi(h * Kp, Bz));
+      const Z<R> cBm = zsub(zscale(-Kz, Bm), zi(h * Kp, Bz));
+      const Z<R> cBz = zi(Kp, zadd(Bp, Bm));
+      const Z<R> cEp = zsub(zscale(Kz, Ep), zi(h * Kp, Ez));
+      const Z<R> cEm = zsub(zscale(-Kz, Em), zi(h * Kp, Ez));
+      const Z<R> cEz = zi(Kp, zadd(Ep, Em));
+      const Z<R> cJp = zsub(zscale(Kz, Jp), zi(h * Kp, Jz));
+      const Z<R> cJm = zsub(zscale(-Kz, Jm), zi(h * Kp, Jz));
+      const Z<R> cJz = zi(Kp, zadd(Jp, Jm));
+      const Z<R> X = zscale(ieps0, zadd(zscale(an, rn), zscale(ap, rp)));
+      const R cSK = kc * SK, jS = SK * jS_f, bS = SK * bS_f, jB = mu0 * omc;
+      const Z<R> nEp = zadd(zadd(zscale(C, Ep), zscale(cSK, cBp)), zadd(zscale(-jS, Jp), zscale(-h * Kp, X)));
+      const Z<R> nEm = zadd(zadd(zscale(C, Em), zscale(cSK, cBm)), zadd(zscale(-jS, Jm), zscale(h * Kp, X)));
+      const Z<R> nEz = zadd(zadd(zscale(C, Ez), zscale(cSK, cBz)), zadd(zscale(-jS, Jz), zi(Kz, X)));
+      const Z<R> nBp = zadd(zadd(zscale(C, Bp), zscale(-bS, cEp)), zscale(jB, cJp));
+      const Z<R> nBm = zadd(zadd(zscale(C, Bm), zscale(-bS, cEm)), zscale(jB, cJm));
+      const Z<R> nBz = zadd(zadd(zscale(C, Bz), zscale(-bS, cEz)), zscale(jB, cJz));
+      zst<R>(Eh, idx, nEp); zst<R>(Eh, G + idx, nEm); zst<R>(Eh, 2 * G + idx, nEz);
+      zst<R>(Bh, idx, nBp); zst<R>(Bh, G + idx, nBm); zst<R>(Bh, 2 * G + idx, nBz);
+      zst<R>(rho_prev, idx, rn);
     }
-    // curls
-    const Z<R> cBp = zsub(zscale(Kz, Bp), zi(h * Kp, Bz));
-    const Z<R> cBm = zsub(zscale(-Kz, Bm), zi(h * Kp, Bz));
-    const Z<R> cBz = zi(Kp, zadd(Bp, Bm));
-    const Z<R> cEp = zsub(zscale(Kz, Ep), zi(h * Kp, Ez));
-    const Z<R> cEm = zsub(zscale(-Kz, Em), zi(h * Kp, Ez));
-    const Z<R> cEz = zi(Kp, zadd(Ep, Em));
-    const Z<R> cJp = zsub(zscale(Kz, Jp), zi(h * Kp, Jz));
-    const Z<R> cJm = zsub(zscale(-Kz, Jm), zi(h * Kp, Jz));
-    const Z<R> cJz = zi(Kp, zadd(Jp, Jm));
-    const Z<R> X = zscale(ieps0, zadd(zscale(an, rn), zscale(ap, rp)));
-    const R cSK = kc * SK, jS = SK * jS_f, bS = SK * bS_f, jB = mu0 * omc;
-    const Z<R> nEp = zadd(zadd(zscale(C, Ep), zscale(cSK, cBp)), zadd(zscale(-jS, Jp), zscale(-h * Kp, X)));
-    const Z<R> nEm = zadd(zadd(zscale(C, Em), zscale(cSK, cBm)), zadd(zscale(-jS, Jm), zscale(h * Kp, X)));
-    const Z<R> nEz = zadd(zadd(zscale(C, Ez), zscale(cSK, cBz)), zadd(zscale(-jS, Jz), zi(Kz, X)));
-    const Z<R> nBp = zadd(zadd(zscale(C, Bp), zscale(-bS, cEp)), zscale(jB, cJp));
-    const Z<R> nBm = zadd(zadd(zscale(C, Bm), zscale(-bS, cEm)), zscale(jB, cJm));
-    const Z<R> nBz = zadd(zadd(zscale(C, Bz), zscale(-bS, cEz)), zscale(jB, cJz));
-    zst<R>(Eh, idx, nEp); zst<R>(Eh, G + idx, nEm); zst<R>(Eh, 2 * G + idx, nEz);
-    zst<R>(Bh, idx, nBp); zst<R>(Bh, G + idx, nBm); zst<R>(Bh, 2 * G + idx, nBz);
-    zst<R>(rho_prev, idx, rn);
   }
 }
 
