@@ -449,9 +449,10 @@ __device__ __forceinline__ void dep2(double2* p, double re, double im) {
 // Deposit of one particle: rho (do_rho) and/or J (do_J) with weight e^{+i m theta} per mode,
 // linear weights; the ghost node r = -dr/2 of the axis cell is node 0 seen across the axis
 // (fold sign (-1)^m for rho and J_z, (-1)^{m+1} for J_r and J_theta) and node Nr is dropped.
-// Each node's weight / V_j and address are formed once; lanes visit the 4 nodes in an
-// order rotated by the lane index, so that lanes of one cell (same nodes) add to different
-// nodes in one instruction.
+// The mode-independent products are formed once per node: g = q w w_z w_r / V_j and g v_k;
+// each mode multiplies them by its phase (mode 0: real, so its imaginary parts, which would
+// receive zeros, are left alone).  Lanes visit the 4 nodes in an order rotated by the lane
+// index, so that lanes of one cell (same nodes) add to different nodes in one instruction.
 // deposit_at takes the particle's radius and azimuth (r, cos, sin) already formed.
 __device__ void deposit_at(const GridGeom& g, const DepArgs& a, const double* invV, double r,
                            double c, double s, double z, double w, double vx, double vy, double vz,
@@ -460,45 +461,57 @@ __device__ void deposit_at(const GridGeom& g, const DepArgs& a, const double* in
   const size_t RZ = (size_t)g.Nr * g.Nz;
   const int rot = threadIdx.x & 3;
   const bool ghost = st.j0 < 0;
-  double fq[4];
-  size_t oq[4];
-  bool inner[4];   // node of the lower radial pair (the ghost node when ghost)
+  const double qw = a.q * w;
+  double rad[2];   // q w w_r / V_j of the radial nodes j0, j0 + 1 (0 for the dropped node Nr)
+  int jn[2];       // their grid rows (the ghost node j = -1 is row 0)
+#pragma unroll
+  for (int dj = 0; dj < 2; ++dj) {
+    const int j = st.j0 + dj;
+    const bool keep = j < g.Nr;
+    jn[dj] = (j < 0 || !keep) ? 0 : j;
+    rad[dj] = keep ? (dj ? st.wr1 : st.wr0) * (invV[jn[dj]] * qw) : 0.0;
+  }
+  const double vr = c * vx + s * vy, vt = c * vy - s * vx;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int node = (q + rot) & 3, dz = node >> 1, dj = node & 1;
-    const int j = st.j0 + dj;
-    const bool keep = j < g.Nr;
-    const int jj = (j < 0 || !keep) ? 0 : j;
-    fq[q] = keep ? (dz ? st.wz1 : st.wz0) * (dj ? st.wr1 : st.wr0) * invV[jj] : 0.0;
-    oq[q] = (size_t)jj * g.Nz + (dz ? st.i1 : st.i0);
-    inner[q] = dj == 0;
-  }
-  const double vr = c * vx + s * vy, vt = c * vy - s * vx;
-  const double qw = a.q * w;
-  double phr = 1.0, phi = 0.0;   // e^{+i m theta}
-  for (int m = 0; m < g.Nm; ++m) {
-    const double qre = qw * phr, qim = qw * phi;
-    const bool negS = ghost && (m & 1), negV = ghost && !(m & 1);
-    double Ar = 0.0, Br = 0.0, At = 0.0, Bt = 0.0, Az = 0.0, Bz = 0.0;
+    const double gq = (dz ? st.wz1 : st.wz0) * (dj ? rad[1] : rad[0]);
+    if (gq == 0.0) continue;
+    const size_t o = (size_t)(dj ? jn[1] : jn[0]) * g.Nz + (dz ? st.i1 : st.i0);
+    const bool fold = ghost && dj == 0;   // the ghost node: fold signs apply
+    double gr = 0.0, gt = 0.0, gz = 0.0;
     if (do_J) {
-      Ar = qre * vr; Br = qim * vr;
-      At = qre * vt; Bt = qim * vt;
-      Az = qre * vz; Bz = qim * vz;
+      gr = gq * vr;
+      gt = gq * vt;
+      gz = gq * vz;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (fq[q] == 0.0) continue;
-      const double fS = flip_sign(fq[q], inner[q] && negS), fV = flip_sign(fq[q], inner[q] && negV);
-      const size_t o = (size_t)m * RZ + oq[q];
-      if (do_rho) dep2(a.rho + o, qre * fS, qim * fS);
+    // mode 0: fold +1 for rho and J_z, -1 for J_r and J_theta
+    if (do_rho) atomicAdd(reinterpret_cast<double*>(a.rho + o), gq);
+    if (do_J) {
+      atomicAdd(reinterpret_cast<double*>(a.J + o), flip_sign(gr, fold));
+      atomicAdd(reinterpret_cast<double*>(a.J + g.G + o), flip_sign(gt, fold));
+      atomicAdd(reinterpret_cast<double*>(a.J + 2 * g.G + o), gz);
+    }
+    double pr = c, pi = s;   // e^{+i m theta}
+    for (int m = 1; m < g.Nm; ++m) {
+      const bool negS = fold && (m & 1), negV = fold && !(m & 1);
+      const size_t om = (size_t)m * RZ + o;
+      if (do_rho) {
+        const double v = flip_sign(gq, negS);
+        dep2(a.rho + om, v * pr, v * pi);
+      }
       if (do_J) {
-        dep2(a.J + o, Ar * fV, Br * fV);
-        dep2(a.J + g.G + o, At * fV, Bt * fV);
-        dep2(a.J + 2 * g.G + o, Az * fS, Bz * fS);
+        const double jr = flip_sign(gr, negV), jt = flip_sign(gt, negV), jz = flip_sign(gz, negS);
+        dep2(a.J + om, jr * pr, jr * pi);
+        dep2(a.J + g.G + om, jt * pr, jt * pi);
+        dep2(a.J + 2 * g.G + om, jz * pr, jz * pi);
+      }
+      if (m + 1 < g.Nm) {
+        const double nr = pr * c - pi * s, ni = pr * s + pi * c;
+        pr = nr;
+        pi = ni;
       }
     }
-    const double nr = phr * c - phi * s, ni = phr * s + phi * c;
-    phr = nr; phi = ni;
   }
 }
 
