@@ -136,7 +136,7 @@ constexpr int kPanelC = 64, kPanelJ = 32;
 __global__ void __launch_bounds__(256) k_f64s_panel(DhtBatch bt, int Nr, int Nc, int jpad,
                                                     const unsigned long long* __restrict__ colmax,
                                                     int32_t* __restrict__ colexp, uint16_t* __restrict__ planes) {
-  __shared__ uint16_t tile[kSlices][kPanelC][kPanelJ + 2];
+  __shared__ __align__(16) uint16_t tile[kSlices][kPanelC][kPanelJ + 2];   // rows of 68 bytes
   const int b = blockIdx.z;
   const int c0 = blockIdx.x * kPanelC, j0 = blockIdx.y * kPanelJ;
   const double* X = static_cast<const double*>(bt.X[b]);
@@ -158,16 +158,20 @@ __global__ void __launch_bounds__(256) k_f64s_panel(DhtBatch bt, int Nr, int Nc,
     for (int i = 0; i < kSlices; ++i) tile[i][tc][tj + 4 * u] = sl[i];
   }
   __syncthreads();
-  // out: for each plane and column, kPanelJ consecutive j (64 bytes); 16 threads per row
+  // out: for each plane and column, kPanelJ consecutive j (64 bytes) as four 16-byte
+  // stores of 8 j each (jpad and j0 are multiples of 8, so a group is inside the row or past
+  // it whole; the tile's rows start on 4-byte boundaries: pitch 68 bytes)
   const size_t plane_elems = (size_t)Nc * jpad;
-  for (int idx = threadIdx.x; idx < kSlices * kPanelC * (kPanelJ / 2); idx += blockDim.x) {
-    const int i = idx / (kPanelC * (kPanelJ / 2));
-    const int rem = idx - i * kPanelC * (kPanelJ / 2);
-    const int cc = rem / (kPanelJ / 2), jh = rem - cc * (kPanelJ / 2);
-    const int cg = c0 + cc, jg = j0 + 2 * jh;
+  constexpr int kQ = kPanelJ / 8;
+  for (int idx = threadIdx.x; idx < kSlices * kPanelC * kQ; idx += blockDim.x) {
+    const int i = idx / (kPanelC * kQ);
+    const int rem = idx - i * kPanelC * kQ;
+    const int cc = rem / kQ, jq = rem - cc * kQ;
+    const int cg = c0 + cc, jg = j0 + 8 * jq;
     if (cg < Nc && jg < jpad) {
-      const uint32_t v = (uint32_t)tile[i][cc][2 * jh] | ((uint32_t)tile[i][cc][2 * jh + 1] << 16);
-      *reinterpret_cast<uint32_t*>(planes + ((size_t)b * kSlices + i) * plane_elems + (size_t)cg * jpad + jg) = v;
+      const uint32_t* t32 = reinterpret_cast<const uint32_t*>(&tile[i][cc][8 * jq]);
+      const uint4 v = make_uint4(t32[0], t32[1], t32[2], t32[3]);
+      *reinterpret_cast<uint4*>(planes + ((size_t)b * kSlices + i) * plane_elems + (size_t)cg * jpad + jg) = v;
     }
   }
 }

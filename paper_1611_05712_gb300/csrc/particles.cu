@@ -69,15 +69,19 @@ struct Stencil {
   double wz0, wz1, wr0, wr1;
 };
 
+// x / d correctly rounded without a division, from inv_d = the correctly rounded 1/d: q =
+// x inv_d, then twice q <- q + (x - q d) inv_d, the remainder exact in one fma; the first
+// correction makes q a faithful quotient and the second returns the correctly rounded one
+// (Markstein, IBM J. Res. Dev. 34, 1990).  An infinite or NaN x gives NaN.
+__device__ __forceinline__ double div_rn(double x, double d, double inv_d) {
+  double q = __dmul_rn(x, inv_d);
+  q = __fma_rn(__fma_rn(-q, d, x), inv_d, q);
+  return __fma_rn(__fma_rn(-q, d, x), inv_d, q);
+}
+
 __device__ __forceinline__ Stencil stencil(const GridGeom& g, double z, double r) {
   Stencil st;
-  // u = z / dz correctly rounded without a division: q = z (1/dz), then twice q <- q + (z -
-  // q dz) (1/dz), the remainder exact in one fma; the first correction makes q a faithful
-  // quotient and the second returns the correctly rounded one (Markstein, IBM J. Res. Dev.
-  // 34, 1990), 1/dz being the correctly rounded reciprocal from the host.
-  double u = __dmul_rn(z, g.inv_dz);
-  u = __fma_rn(__fma_rn(-u, g.dz, z), g.inv_dz, u);
-  u = __fma_rn(__fma_rn(-u, g.dz, z), g.inv_dz, u);
+  double u = div_rn(z, g.dz, g.inv_dz);
   double fi = floor(u);
   double sz = u - fi;
   long long i0 = (long long)fi;
@@ -245,7 +249,7 @@ __global__ void k_keys(const Parts p, int64_t np, GridGeom g, int32_t* keys, int
     }
     double x = p.x[i], y = p.y[i], z = p.z[i];
     double r = sqrt(__dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y)));
-    double fz = floor(z / g.dz), fr = floor(r / g.dr);
+    double fz = floor(div_rn(z, g.dz, g.inv_dz)), fr = floor(div_rn(r, g.dr, g.inv_dr));
     if (!(fz == fz) || !(fr == fr) || isinf(fz) || isinf(fr)) {
       atomicOr(err, kErrNumeric);
       fz = 0.0; fr = 0.0;
