@@ -483,7 +483,8 @@ pic_status pic_launch_count(pic_sim* sim, int64_t* launches);
  * be serialised by the caller.  The first call on each device looks up the array's
  * device address (cudaGetSymbolAddress) with that device current and keeps it for the
  * life of the process: do not use the call across a reset of the device
- * (cudaDeviceReset) in the same process.  Asynchronous on the stream.  Errors:
+ * (cudaDeviceReset) in the same process.  Asynchronous on the stream; after that first
+ * call it enqueues kernels only, so it may be captured into a CUDA graph.  Errors:
  * PIC_ERR_ARG, PIC_ERR_CUDA. */
 pic_status pic_sort_keys_noalloc(const double* x, const double* y, const double* z, int64_t n,
                                  int32_t Nz, int32_t Nr, double dz, double dr, int32_t* keys,

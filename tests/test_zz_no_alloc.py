@@ -6,8 +6,8 @@ the device): its scratch is a fixed array inside the library.  Here it must give
 same cell keys and the same stable permutation, bit for bit, as pic_sort through a
 pic_sim handle and as the oracle's cell keys and stable sort, on two calls in a row (the
 second on a different grid and particle set, so stale scratch contents from the first
-call would show); order a cell that holds every particle in bounded time; and reject
-sizes beyond its limits.
+call would show); order a cell that holds every particle in bounded time; replay from a
+captured CUDA graph; and reject sizes beyond its limits.
 """
 import ctypes
 
@@ -113,6 +113,48 @@ def test_noalloc_sort_of_one_cell_holding_every_particle_is_bounded():
     ms = e0.elapsed_time(e1)
     assert ms < 200.0, ms
     assert np.array_equal(pt.cpu().numpy(), np.arange(n, dtype=np.int32))
+
+
+def test_noalloc_sort_replays_from_a_captured_graph():
+    """The call only enqueues kernels on its stream once the first call has looked up its
+    scratch array, so it can be captured into a CUDA graph: captured on one particle set,
+    then replayed after a second set is written into the same input buffers, the graph
+    gives the keys and permutation that pic_sort gives for the second set, bit for bit."""
+    import torch
+    lib = _lib()
+    dev = torch.device("cuda:0")
+    Nz, Nr, n = 128, 64, 20000
+    P0, P1 = _particles(Nz, Nr, n, 3), _particles(Nz, Nr, n, 4)
+    bufs = {k: torch.from_numpy(P0[k]).to(dev) for k in ("x", "y", "z")}
+    keys = torch.full((n,), -7, dtype=torch.int32, device=dev)
+    perm = torch.full((n,), -7, dtype=torch.int32, device=dev)
+    side = torch.cuda.Stream(dev)
+
+    def call(stream):
+        return lib.pic_sort_keys_noalloc(bufs["x"].data_ptr(), bufs["y"].data_ptr(), bufs["z"].data_ptr(), n,
+                                         Nz, Nr, DZ, DZ, keys.data_ptr(), perm.data_ptr(), stream.cuda_stream)
+
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        assert call(side) == 0   # outside the capture: the scratch address lookup
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        st = call(torch.cuda.current_stream(dev))
+    assert st == 0, lib.pic_last_error().decode()
+    for k in ("x", "y", "z"):
+        bufs[k].copy_(torch.from_numpy(P1[k]))
+    torch.cuda.synchronize(dev)
+    graph.replay()
+    torch.cuda.synchronize(dev)
+    cfg = bd.make_config(Nz, Nr, 1, DZ, DZ, DZ / 3e8, 0, True, bd.PIC_FP64, n)
+    s = bd.Sim(cfg)
+    s.write_particles(P1)
+    s.sort()
+    keys_ref, perm_ref = s.get("KEYS"), s.get("PERM")
+    s.close()
+    assert np.array_equal(keys.cpu().numpy(), keys_ref)
+    assert np.array_equal(perm.cpu().numpy(), perm_ref)
 
 
 def test_noalloc_sort_rejects_sizes_beyond_its_limits():
