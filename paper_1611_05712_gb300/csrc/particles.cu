@@ -136,9 +136,10 @@ __device__ __forceinline__ GatherNodes gather_nodes(const GridGeom& g, const Ste
 // Comput. 26, 2005): the products of the high parts enter a float sum through an
 // error-free two-sum, whose errors, with each product's rounding error (one fma) and its
 // cross terms, collect in a second float.  The error stays below a few 2^-48 times the sum
-// of the terms' magnitudes (n u^2 for n <= 4 Nm terms, u = 2^-24, plus the operands' own
-// double-word rounding), against the n 2^-53 of a float64 sum; GB300 runs float64 at 1/64 of
-// its float32 rate, and the float64 unit bounds the particle pass.
+// of the terms' magnitudes (n u^2 for the n = 8 Nm - 4 terms of a component, u = 2^-24,
+// plus the operands' own double-word rounding), against the n 2^-53 of a float64 sum;
+// GB300 runs float64 at 1/64 of its float32 rate, and the float64 unit bounds the particle
+// pass.
 struct Dot2 {
   float s, c;   // running sum and collected errors: the value is s + c
 };
